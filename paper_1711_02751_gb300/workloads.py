@@ -1,0 +1,143 @@
+"""Seeded synthetic workloads (initial states, bottoms, time steps) for the shallow-water runs.
+
+This module holds input generation only: it evaluates closed-form initial conditions at
+node coordinates that the caller supplies, and the time-step rule below.  It contains
+none of the discretisation's arithmetic and is shared by the tests, the benchmark and
+the oracle-side checks so that both sides see identical inputs.
+
+All states are returned as (h, hu, hv, b) arrays of shape [n_el, (k+1)^2] in the node
+order of the library (element e = ey*N + ex, node n = j*(k+1) + i, i along x).
+
+Workloads (unit square, periodic, g = 1, H0 = 1):
+
+* ``bump8``      8 x 8 quads, k = 2, flat bottom, h = 1 + 0.01 exp(-r^2 / 0.01) centred
+                 at (0.5, 0.5), u = v = 0, 100 steps.
+* ``large512``   512 x 512 quads, k = 3, b = 0.1 sin(2 pi x) sin(2 pi y), h = 1 - b + 16
+                 seeded Gaussian bumps (amplitude U[0.005, 0.02], width U[0.02, 0.08],
+                 centre U[0,1]^2, minimum-image distance), velocity from a seeded smooth
+                 random streamfunction scaled to max |u| = 0.05, 200 steps.
+* ``sized(N, k)`` the large512 recipe on another mesh (parity cases that span several
+                 tiles and a ragged tail).
+
+Time step (the advective CFL 0.5 of the workload definition): the Courant number of
+the paper's planar tests is Cr = (max|u| + sqrt(phi)) dt / dx_min with dx_min the
+smallest physical spacing of the GLL nodes; the advective step is
+dt = 0.5 dx_min / U_adv, U_adv = max(max_nodes |u|, 0.05 sqrt(g H0)).
+"""
+import math
+
+import numpy as np
+
+G = 1.0
+H0 = 1.0
+
+
+def _min_image(d):
+    return d - np.round(d)
+
+
+def gaussian_bumps(x, y, rng, n_bumps):
+    """Sum of n_bumps seeded periodic Gaussian bumps a exp(-d^2 / w^2)."""
+    out = np.zeros_like(x)
+    for _ in range(n_bumps):
+        cx, cy = rng.uniform(0.0, 1.0, size=2)
+        amp = rng.uniform(0.005, 0.02)
+        wid = rng.uniform(0.02, 0.08)
+        d2 = _min_image(x - cx) ** 2 + _min_image(y - cy) ** 2
+        out += amp * np.exp(-d2 / wid ** 2)
+    return out
+
+
+def streamfunction_velocity(x, y, rng, umax=0.05, kmax=4):
+    """Divergence-free (u, v) = (d_y psi, -d_x psi) of a seeded smooth periodic psi.
+
+    psi = sum_{(m,n) != 0, |m|,|n| <= kmax} a_mn sin(2 pi (m x + n y) + theta_mn),
+    a_mn ~ N(0,1) / (m^2 + n^2), theta ~ U[0, 2 pi); scaled so max over nodes |u| = umax.
+    """
+    u = np.zeros_like(x)
+    v = np.zeros_like(x)
+    for m in range(-kmax, kmax + 1):
+        for n in range(-kmax, kmax + 1):
+            if m == 0 and n == 0:
+                continue
+            a = rng.standard_normal() / (m * m + n * n)
+            th = rng.uniform(0.0, 2.0 * math.pi)
+            c = np.cos(2.0 * math.pi * (m * x + n * y) + th)
+            u += a * 2.0 * math.pi * n * c
+            v -= a * 2.0 * math.pi * m * c
+    speed = np.sqrt(u * u + v * v).max()
+    return u * (umax / speed), v * (umax / speed)
+
+
+def bump8_state(x, y):
+    """The 8 x 8, k = 2 flat-bottom workload at node coordinates x, y [n_el, Np]."""
+    b = np.zeros_like(x)
+    h = 1.0 + 0.01 * np.exp(-((x - 0.5) ** 2 + (y - 0.5) ** 2) / 0.01)
+    return h, np.zeros_like(x), np.zeros_like(x), b
+
+
+def large_state(x, y, seed=2000, n_bumps=16, umax=0.05):
+    """The variable-bottom workload (bumps + streamfunction velocity) at nodes x, y."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    b = 0.1 * np.sin(2.0 * math.pi * x) * np.sin(2.0 * math.pi * y)
+    h = H0 - b + gaussian_bumps(x, y, rng, n_bumps)
+    u, v = streamfunction_velocity(x, y, rng, umax=umax)
+    return h, h * u, h * v, b
+
+
+def lake_at_rest_state(x, y, amp=0.1):
+    """Still water over the sinusoidal bottom: h = H0 - b, u = v = 0."""
+    b = amp * np.sin(2.0 * math.pi * x) * np.sin(2.0 * math.pi * y)
+    return H0 - b, np.zeros_like(x), np.zeros_like(x), b
+
+
+def standing_wave_state(x, y, eps=1e-3, t=0.0):
+    """Linear standing gravity wave on a flat bottom (closed form of the linear PDE).
+
+    phi_eta = eps cos(2 pi x) cos(2 pi y) cos(w t), U = eps/sqrt2 sin cos sin(w t),
+    V = eps/sqrt2 cos sin sin(w t), w = 2 pi sqrt(2), with g = H0 = 1.
+    """
+    w = 2.0 * math.pi * math.sqrt(2.0)
+    cx, sx = np.cos(2 * math.pi * x), np.sin(2 * math.pi * x)
+    cy, sy = np.cos(2 * math.pi * y), np.sin(2 * math.pi * y)
+    eta = eps * cx * cy * math.cos(w * t)
+    U = eps / math.sqrt(2.0) * sx * cy * math.sin(w * t)
+    V = eps / math.sqrt(2.0) * cx * sy * math.sin(w * t)
+    return H0 + eta / G, U / G, V / G, np.zeros_like(x)
+
+
+def advective_dt(x, h, hu, hv, n_side, cfl=0.5, g=G, H0_=H0):
+    """dt = cfl * dx_min / U_adv from node coordinates x [n_el, Np] of element rows.
+
+    dx_min is the smallest spacing between distinct x-coordinates inside one element.
+    """
+    xs = np.unique(np.round(x[0], 15))
+    dx_min = float(np.min(np.diff(xs)))
+    speed = np.sqrt(hu ** 2 + hv ** 2) / h
+    u_adv = max(float(speed.max()), 0.05 * math.sqrt(g * H0_))
+    return cfl * dx_min / u_adv
+
+
+def courant(dx_min, dt, max_speed_plus_celerity):
+    """The paper's Courant number (max|u| + sqrt(phi)) dt / dx_min."""
+    return max_speed_plus_celerity * dt / dx_min
+
+
+WORKLOADS = {
+    "bump8": {"N": 8, "k": 2, "steps": 100, "state": "bump8"},
+    "large512": {"N": 512, "k": 3, "steps": 200, "state": "large"},
+}
+
+
+def make_state(name, x, y, seed=None):
+    """Dispatch to a state generator by workload name."""
+    kind = WORKLOADS[name]["state"] if name in WORKLOADS else name
+    if kind == "bump8":
+        return bump8_state(x, y)
+    if kind == "large":
+        return large_state(x, y, seed=2000 if seed is None else seed)
+    if kind == "lake":
+        return lake_at_rest_state(x, y)
+    if kind == "standing":
+        return standing_wave_state(x, y)
+    raise KeyError(name)
