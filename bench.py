@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark of the IMEX HDG-DG hot path: DOF-steps/s on the 512 x 512, k = 3 workload.
+
+One bench "step" is one IMEX HDG-DG time step (ARS2: two implicit stages, three DG
+residuals, the stage combinations) of the whole mesh, inputs resident in HBM.  Prints one
+JSON line.  See the design notes for the workload recipe and the roofline arithmetic.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--workload large512|bump8]
+
+N > 1 runs N independent replicas (one process per GPU under torchrun, each its own
+seeded instance; the path has no data exchange), value = DOF-steps/s summed over ranks
+(max-over-ranks time).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF-steps/s of IMEX HDG-DG at rel L2≤1e-6 vs FP64 form; p50/p99 latency"
+UNIT = "DOF-steps/s"
+WORKLOADS = {"large512": (512, 3), "bump8": (8, 2)}
+CPU_SAMPLE = (64, 3)       # oracle sample: the large512 recipe on 64 x 64, k = 3
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="large512", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--sample-steps", type=int, default=5, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def _workload_state(name, x, y, rank):
+    from paper_1711_02751_gb300 import workloads as W
+    if name == "bump8":
+        return W.bump8_state(x, y)
+    return W.large_state(x, y, seed=2000 + rank)
+
+
+# ---- oracle timing (the CPU baseline and the reference arm) ----------------------------------
+def _oracle_sample(n_steps, warmup):
+    """Time the FP64 oracle on a bounded sample: the large512 recipe on 64 x 64, k = 3, with dt
+    scaled to keep the same gravity Courant number (dt * 512 / 64), scipy GMRES trace solve."""
+    from oracle import imex, swe
+    from paper_1711_02751_gb300 import workloads as W
+    N, k = CPU_SAMPLE
+    m = swe.Mesh(N, k)
+    x, y = m.x.reshape(m.n_el, -1), m.y.reshape(m.n_el, -1)
+    h, hu, hv, b = W.large_state(x, y)
+    xl, _ = _library_free_coords(512, 3)
+    dt_full = W.advective_dt(xl, np.ones((1, 16)), np.zeros((1, 16)), np.zeros((1, 16)), 512)
+    dt = dt_full * 512 / N
+    q, phiB = swe.to_state(h, hu, hv, b, W.G, W.H0)
+    st = imex.Stepper(m, phiB, dt, solver="gmres", rtol=1e-13)
+    for _ in range(warmup):
+        q = st.step(q)
+    times = []
+    for _ in range(n_steps):
+        t0 = time.perf_counter()
+        q = st.step(q)
+        times.append(time.perf_counter() - t0)
+    dof = 3 * m.n_el * m.P ** 2
+    return dof, times
+
+
+def _library_free_coords(N, k):
+    """x coordinates of one element row from the oracle's GLL tables (oracle-side only)."""
+    from oracle.gll import gll_nodes_weights
+    xi, _ = gll_nodes_weights(k)
+    x = np.broadcast_to(((1.0 + xi) / 2.0) / N, (k + 1, k + 1)).reshape(1, -1)
+    return x, None
+
+
+def _cpu_baseline_child(args):
+    dof, times = _oracle_sample(args.sample_steps, 1)
+    print(json.dumps({"dof": dof, "times": times}))
+
+
+def _run_cpu_child(sample_steps):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-child",
+                        "--sample-steps", str(sample_steps)], capture_output=True, text=True, env=env,
+                       timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle baseline failed: " + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["dof"], d["times"]
+
+
+def cpu_baseline(sample_steps=5):
+    dof, times = _run_cpu_child(sample_steps)
+    value = dof * len(times) / sum(times)
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle, large512 recipe on 64x64 k=3 (DOF {dof}), dt*512/64 "
+                      f"(same gravity Courant), scipy GMRES rtol 1e-13, {len(times)} steps timed "
+                      f"after 1 warm-up, setup excluded, 1 thread"}
+
+
+def reference_arm(args, rank, world):
+    """The oracle as it stands, timed on host cores on a bounded sample of the workload."""
+    if rank != 0:
+        return
+    dof, times = _run_cpu_child(args.steps + args.warmup)
+    times = times[args.warmup:] if len(times) > args.warmup else times
+    total = sum(times)
+    value = dof * len(times) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload} (oracle sample: 64x64 k=3)", "sample": "bounded"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "large512 recipe on 64x64 k=3, dt*512/64, one oracle step per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- clocks during the timed region ------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) == 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---- roofline --------------------------------------------------------------------------------
+def _algorithmic(N, k, cls):
+    """(bytes, flops) one launch group of a kernel class moves / performs at FP64."""
+    P = k + 1
+    NF, NV, Np = 3 * P, 3 * P * P, P * P
+    n_el, n_edges = N * N, 2 * N * N
+    if cls == "spmv":   # 6 off-diagonal NF x NF blocks + column ids + x and y once
+        return n_edges * (6 * NF * NF * 8 + 6 * 4 + 2 * NF * 8), n_edges * NF * (12 * NF + 1)
+    if cls == "condense":   # A^{-1} once, R1 in, Z out; then Z face values + phiB in, g out
+        return (n_el * (NV * NV * 8 + 2 * NV * 8) + n_edges * NF * 8 * 3,
+                n_el * 2 * NV * NV)
+    if cls == "recover":    # boundary columns of A^{-1}, Z, R1 in, Q, L out, traces in
+        nb = 3 * (4 * P - 4)
+        return n_el * (NV * nb * 8 + 4 * NV * 8) + n_edges * NF * 8, n_el * 2 * NV * nb
+    if cls == "dg":
+        return n_el * (2 * NV + Np) * 8, n_el * Np * 60
+    return None, None
+
+
+def _traffic_for(cls, N, k):
+    """dram bytes per launch from a committed ncu summary, if it is for the current kernel source."""
+    try:
+        d = json.load(open(PROFILE_TRAFFIC))
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_1711_02751_gb300", "csrc", d.get("source", ""))
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except Exception:
+        return None
+    e = d.get("kernels", {}).get(cls)
+    if not e or e.get("source_sha") != sha:
+        return None
+    return e["dram_bytes_per_launch"] * (N * N) / e["n_el"]
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+def main():
+    args = _args()
+    if args.cpu_baseline_child:
+        _cpu_baseline_child(args)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1711_02751_gb300 import hdgdg as hd
+    from paper_1711_02751_gb300 import workloads as W
+
+    N, k = WORKLOADS[args.workload]
+    x, y = hd.node_coords(N, k)
+    h, hu, hv, b = _workload_state(args.workload, x, y, rank)
+    dt = W.advective_dt(x, h, hu, hv, N)
+    stream = torch.cuda.Stream()          # a real stream: the legacy default stream has handle 0
+    torch.cuda.set_stream(stream)
+    sim = hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, stream=stream.cuda_stream)
+    sim.set_state(h, hu, hv)
+    dof = 3 * N * N * (k + 1) ** 2
+
+    fp64_tflops = hd.measure_fp64_tflops()
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, inputs resident, events on the library's stream ----
+    clocks = ClockSampler()
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.3)
+    sim.set_kernel_timing(True)
+    l0 = sim.stats()["kernel_launches"]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
+    for i in range(args.steps):
+        sim.step(1)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ktimes = sim.kernel_times()
+    st = sim.stats()
+    launches = st["kernel_launches"] - l0
+    clk = clocks.stop() if rank == 0 else None
+    per_step = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    ms_total = evs[0].elapsed_time(evs[-1])
+    if dist:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    value = world * dof * args.steps / (ms_total / 1e3)
+
+    # ---- e2e: the same steps through host buffers, copies inside the timed region ----
+    e2e = None
+    if not args.no_e2e:
+        n = N * N * (k + 1) ** 2
+        bufs = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(6)]
+        for bsrc, a in zip(bufs[:3], (h, hu, hv)):
+            bsrc.numpy()[:] = a.ravel()
+        ptrs_in = [bb.data_ptr() for bb in bufs[:3]]
+        ptrs_out = [bb.data_ptr() for bb in bufs[3:]]
+        sim.set_state_ptrs(*ptrs_in)
+        sim.step(1)
+        sim.get_state_ptrs(*ptrs_out)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            sim.set_state_ptrs(*ptrs_in)
+            sim.step(1)
+            sim.get_state_ptrs(*ptrs_out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms_e2e], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        e2e = {"value": world * dof * args.steps / (ms_e2e / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": 3 * n * 8, "d2h_bytes_per_step": 3 * n * 8}
+    sim.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel class ----
+    peaks = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    dom = max((c for c in ktimes if ktimes[c][1] > 0 and _algorithmic(N, k, c)[0]),
+              key=lambda c: ktimes[c][0])
+    tot_ms, n_l = ktimes[dom]
+    avg_s = tot_ms / n_l / 1e3
+    byt, flo = _algorithmic(N, k, dom)
+    t_hbm, t_alu = byt / (hbm * 1e9), flo / (fp64_tflops * 1e12)
+    if t_hbm >= t_alu:
+        roof = {"bound": "hbm", "achieved": byt / avg_s / 1e9, "peak": hbm, "unit": "GB/s"}
+    else:
+        roof = {"bound": "alu", "achieved": flo / avg_s / 1e12, "peak": fp64_tflops, "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    tr = _traffic_for(dom, N, k)
+    roof["traffic"] = tr
+    roof["kernel"] = dom
+    roof["avg_launch_ms"] = avg_s * 1e3
+    roof["algorithmic_bytes"] = byt
+    roof["algorithmic_flops"] = flo
+    roof["peak_source"] = ("measured FP64 FMA probe in bench.py" if roof["bound"] == "alu"
+                           else "MEASURED_PEAKS.json hbm_gbs (of measured)")
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline()
+        except Exception as ex:   # reported, never silently replaced
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"[:300]}
+
+    per_step_sorted = sorted(per_step)
+    p50 = statistics.median(per_step)
+    p99 = per_step_sorted[min(len(per_step) - 1, math.ceil(0.99 * len(per_step)) - 1)]
+    breakdown = {c: {"ms": round(v[0], 3), "groups": v[1]} for c, v in ktimes.items()}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: periodic {N}x{N} quads, k={k}, ARS2, "
+                                   f"dt={dt:.6g} (advective CFL 0.5), FP64",
+                       "dof": dof, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (A^-1 and trace matrix are GBs)"},
+            "latency_ms": {"p50": p50, "p99": p99},
+            "krylov_iterations_per_stage": st["krylov_iterations"] / max(1, 2 * st["steps"]),
+            "gpu_launches": launches, "roofline": roof, "kernel_breakdown_ms": breakdown,
+            "fp64_fma_tflops_measured": fp64_tflops, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * hdgdg.h -- C ABI of the GB300 (sm_103a) IMEX HDG-DG shallow-water library.
+ *
+ * Method: Kang, Giraldo, Bui-Thanh, "IMEX HDG-DG: a coupled implicit hybridized
+ * discontinuous Galerkin and explicit discontinuous Galerkin approach for shallow water
+ * systems", arXiv:1711.02751.  The library advances the planar shallow-water system
+ * (Sec. 3.1, eq. psweGov) on a periodic N x N uniform quadrilateral mesh of the unit
+ * square with degree-k tensor-product Gauss-Lobatto nodes, by the IMEX HDG-DG scheme of
+ * Algorithm 1 (Sec. 6): per stage, the explicit DG residual of the nonlinear flux
+ * (eq. WeakForm_DG with the Rusanov flux, eq. Full_russanov / Linear_russanov), the
+ * implicit HDG solve of the linear gravity-wave part (static condensation, eq.
+ * linearizedHDGsystem_schur; global trace solve; local recovery, eq.
+ * recover_volume_unknowns), and the stage combination (eq. hdgIMEXRK_qi / qn).
+ *
+ * Conventions shared by every entry point
+ * -----------------------------------------
+ * Mesh: element e = ey * N + ex; node n = j * (k+1) + i of an element, i along x, at GLL
+ *   point xi_i: x = (ex + (1 + xi_i) / 2) / N, y = (ey + (1 + xi_j) / 2) / N.
+ * Edges: edge r < N^2 is the right face of element r (normal +x); edge N^2 + r is the top
+ *   face of element r (normal +y).  Trace vectors are [edge][field c][node b], b along the
+ *   edge (y for right faces, x for top faces), fields (phi_hat, U_hat, V_hat).
+ * User state: h (total depth), hu, hv as host arrays [n_el][(k+1)^2], double.
+ * Internal state q = (phi_eta, U, V) = (g (h - B), g hu, g hv), B = H0 - b, phi_B = g B
+ *   (Sec. 3, "phi = g H, U = phi u"); the row-level entry points take q as host arrays
+ *   [3][n_el][(k+1)^2].
+ * Ownership: the caller owns every host buffer it passes; the library copies in/out and
+ *   owns all device memory it allocates.  A handle is not thread safe; distinct handles
+ *   are independent.  All device work of a handle is issued on the stream given at
+ *   create (the library makes its own non-blocking stream when NULL is given).
+ * Errors: every call returns a status; on failure hdgdg_last_error(sim) holds a message.
+ *   Entry points that return HDGDG_ECUDA leave the handle usable only for destroy.
+ */
+#ifndef HDGDG_H
+#define HDGDG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HDGDG_OK = 0,
+    HDGDG_EINVAL = 1,          /* bad argument or unsupported configuration */
+    HDGDG_ENOMEM = 2,          /* device or host allocation failed */
+    HDGDG_ECUDA = 3,           /* a CUDA runtime call or kernel launch failed */
+    HDGDG_ENOTCONVERGED = 4,   /* trace Krylov solve missed its tolerance within its cap */
+    HDGDG_ENONFINITE = 5,      /* NaN or Inf in an input (or produced by a step) */
+    HDGDG_ESTATE = 6           /* call made in the wrong order (e.g. step before set_state) */
+} hdgdg_status;
+
+enum { HDGDG_ARS2 = 0, HDGDG_ARS3 = 1 };          /* IMEX schemes named in Sec. 6 */
+enum { HDGDG_FP64 = 0 };                          /* arithmetic of the path */
+
+typedef struct {
+    int n_side;          /* N >= 2: elements per side of the periodic unit square */
+    int degree_k;        /* polynomial degree k, 1 <= k <= 5 */
+    double g;            /* gravitational acceleration (> 0) */
+    double H0;           /* reference depth: B = H0 - b */
+    int scheme;          /* HDGDG_ARS2 (ARS(2,3,2)) or HDGDG_ARS3 (ARS(4,4,3)) */
+    double dt;           /* time step (> 0) */
+    int precision;       /* HDGDG_FP64 */
+    double krylov_rtol;  /* GMRES stop: ||g - S qhat|| <= rtol ||g||; <= 0 selects 1e-13 */
+    int krylov_restart;  /* GMRES(m) restart length m; <= 0 selects 20 */
+    int krylov_maxit;    /* cap on GMRES iterations per stage solve; <= 0 selects 2000 */
+    int linear_only;     /* 1: drop NL (linear gravity-wave runs); 0: full method */
+} hdgdg_config;
+
+typedef struct {
+    long long steps;              /* time steps completed since set_state */
+    long long krylov_iterations;  /* GMRES iterations summed over all stage solves */
+    int last_krylov_iterations;   /* iterations of the most recent stage solve */
+    double last_rel_residual;     /* ||g - S qhat|| / ||g|| of the most recent stage solve */
+    double mass;                  /* sum_e J sum_ij w_i w_j phi_eta of the current state */
+    long long kernel_launches;    /* CUDA kernels this handle launched in hdgdg_step since set_state */
+} hdgdg_stats;
+
+/* Kernel classes of the per-kernel timers (hdgdg_kernel_time). */
+enum {
+    HDGDG_KT_SPMV = 0,      /* trace-matrix product of the Krylov loop (one kernel per launch) */
+    HDGDG_KT_ORTHO = 1,     /* Gram-Schmidt dots, updates and normalisation of one iteration */
+    HDGDG_KT_CONDENSE = 2,  /* A^{-1} R1 and the trace right-hand side */
+    HDGDG_KT_RECOVER = 3,   /* local recovery of Q and L_i */
+    HDGDG_KT_DG = 4,        /* DG residual of the nonlinear part */
+    HDGDG_KT_COMBINE = 5,   /* stage combinations and the final update */
+    HDGDG_KT_COUNT = 6
+};
+
+typedef struct hdgdg_sim hdgdg_sim;
+
+/* Device bytes the library will allocate for this configuration (for admission by
+ * memory budget).  Returns 0 for an invalid configuration.  No GPU call is made. */
+size_t hdgdg_bytes_required(const hdgdg_config* cfg);
+
+/* GLL node coordinates x, y (host, [n_el][(k+1)^2] each) of the mesh of cfg, in the
+ * node order above.  No GPU call is made.  EINVAL on a bad configuration or NULL. */
+hdgdg_status hdgdg_node_coords(const hdgdg_config* cfg, double* x, double* y);
+
+/* Build a simulation: mesh, GLL tables, the bottom phi_B = g (H0 - b), and the
+ * time-invariant implicit-stage operators of Sec. 6 -- per-element A^{-1} and the
+ * condensed trace matrix S = D - C A^{-1} B (eq. linearizedHDGsystem_schur), assembled
+ * once into edge-block CSR with its block-Jacobi preconditioner folded in (the
+ * operators are the same for every stage and step because the implicit diagonal is
+ * constant, Sec. 7.1).  bottom_b: host [n_el][(k+1)^2] (NULL = flat, b = 0).
+ * cuda_stream: a cudaStream_t to issue work on, or NULL.  On success *out owns the
+ * handle; release it with hdgdg_destroy.  Fails with EINVAL, ENOMEM, ENONFINITE or ECUDA;
+ * when the failure happens after the handle exists, *out still receives it so that
+ * hdgdg_last_error can explain the failure -- its only other valid use is hdgdg_destroy. */
+hdgdg_status hdgdg_create(const hdgdg_config* cfg, const double* bottom_b, void* cuda_stream,
+                          hdgdg_sim** out);
+
+/* Copy a user state (host arrays h, hu, hv [n_el][(k+1)^2]) in and reset the step
+ * counters.  ENONFINITE if any value is not finite or h - B leaves phi = g h <= 0. */
+hdgdg_status hdgdg_set_state(hdgdg_sim* sim, const double* h, const double* hu, const double* hv);
+
+/* Advance n_steps >= 0 time steps of Algorithm 1.  Synchronises the stream on return.
+ * ENOTCONVERGED if a trace solve misses krylov_rtol within krylov_maxit (the state is
+ * left at the last completed step); ENONFINITE if a step produced NaN/Inf (state left at
+ * the last finite step); ESTATE before set_state. */
+hdgdg_status hdgdg_step(hdgdg_sim* sim, int n_steps);
+
+/* Copy the current state out to host arrays h, hu, hv [n_el][(k+1)^2]. */
+hdgdg_status hdgdg_get_state(hdgdg_sim* sim, double* h, double* hu, double* hv);
+
+/* Counters of the run so far; computes the mass of the current state on the device. */
+hdgdg_status hdgdg_get_stats(hdgdg_sim* sim, hdgdg_stats* out);
+
+/* Message of the last failure on this handle ("" if none; a static message if sim is NULL). */
+const char* hdgdg_last_error(const hdgdg_sim* sim);
+
+/* Release every device and host resource of the handle (NULL is a no-op). */
+void hdgdg_destroy(hdgdg_sim* sim);
+
+/* ---- row-level entry points (one step of the hot path each; host buffers) ---------- */
+
+/* M^{-1} NL(q) of Sec. 4.3 (DG volume term plus Rusanov face terms of the nonlinear
+ * flux F_NL = F - F_L) for the internal state q [3][n_el][(k+1)^2]; out has the same
+ * layout.  The bottom is the handle's. */
+hdgdg_status hdgdg_eval_nl(hdgdg_sim* sim, const double* q, double* out);
+
+/* Right-hand side of the condensed trace system for stage data R1 [3][n_el][(k+1)^2]:
+ * g = -C A^{-1} R1 (eq. linearizedHDGsystem_schur with R2 = 0), one conservation row per
+ * trace node in POINTWISE form, i.e. eq. HDGcont divided by the positive face quadrature
+ * weight (h/2) w_b of the node.  out: [edge][c][b]. */
+hdgdg_status hdgdg_condense_rhs(hdgdg_sim* sim, const double* R1, double* out);
+
+/* y = S x for the condensed trace matrix S = D - C A^{-1} B in the pointwise row scaling
+ * of hdgdg_condense_rhs.  x, y: [edge][c][b]. */
+hdgdg_status hdgdg_trace_apply(hdgdg_sim* sim, const double* x, double* y);
+
+/* One implicit stage solve (Algorithm 1, the "else" branch): condense, GMRES on the trace
+ * system, recover Q = A^{-1}(R1 - B qhat).  R1, Q: [3][n_el][(k+1)^2]; qhat: [edge][c][b]
+ * (may be NULL).  *iterations (may be NULL) receives the GMRES iteration count. */
+hdgdg_status hdgdg_stage_solve(hdgdg_sim* sim, const double* R1, double* Q, double* qhat,
+                               int* iterations);
+
+/* ---- measurement helpers --------------------------------------------------------- */
+
+/* Switch the per-kernel-class timers on (1) or off (0) and zero them.  When on, the
+ * library brackets each timed launch group with CUDA events on the handle's stream and
+ * accumulates their elapsed times; timing adds two event records per group. */
+hdgdg_status hdgdg_set_kernel_timing(hdgdg_sim* sim, int on);
+
+/* Accumulated device time (ms) and number of timed launch groups of kernel class cls
+ * (HDGDG_KT_*) since the timers were last switched on.  EINVAL for a bad class. */
+hdgdg_status hdgdg_kernel_time(hdgdg_sim* sim, int cls, double* total_ms, long long* launches);
+
+/* Measured FP64 fused-multiply-add throughput of the current device in TFLOP/s (2 flops
+ * per FMA), from a register-resident FMA chain kernel timed with CUDA events.  Used as
+ * the denominator of ALU-bound roofline fractions.  ECUDA on failure. */
+hdgdg_status hdgdg_measure_fp64_tflops(double* tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HDGDG_H */

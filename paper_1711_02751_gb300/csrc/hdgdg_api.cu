@@ -1,0 +1,761 @@
+// C ABI and host driver of the IMEX HDG-DG hot path (Algorithm 1 of arXiv:1711.02751).
+//
+// Host side: GLL tables, mesh geometry and the bottom are prepared on the CPU once; every
+// per-stage operation runs in the CUDA kernels of this library.  One time step of
+// Algorithm 1:
+//   for each stage i: if a~_ii = 0 then Q = q^n
+//                     else R1 = q^n + sum_{j<i} (a_ij dtM^{-1}NL_j + a~_ij dtM^{-1}L_j)  (combine)
+//                          g = -C A^{-1} R1                                          (condense)
+//                          S qhat = g by block-Jacobi GMRES(m)                          (Krylov)
+//                          Q = A^{-1}(R1 - B qhat), dtM^{-1}L_i = (Q - R1)/a~_ii        (recover)
+//                     dtM^{-1}NL_i = dt M^{-1} NL(Q)                                    (DG residual)
+//   q^{n+1} = q^n + sum_i (b_i dtM^{-1}NL_i + b~_i dtM^{-1}L_i)                          (combine)
+// The identity M^{-1} L_i = (Q - R1)/(dt a~_ii) holds exactly for the recovered Q because
+// the local rows of the stage system are solved exactly (eq. IMEXRKDiscretizedForm).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hdgdg.h"
+#include "internal.h"
+
+using namespace hdgdg;
+
+namespace {
+
+constexpr int kMaxStages = 5;
+
+struct Plan {
+    size_t n = 0, nt = 0;
+    int NV = 0, NF = 0, NT = 0, m = 0, s = 0;
+    size_t persistent = 0, setup_temp = 0;
+};
+
+bool valid(const hdgdg_config* c) {
+    return c && c->n_side >= 2 && c->n_side <= 32768 && c->degree_k >= 1 && c->degree_k <= kMaxP - 1 &&
+           std::isfinite(c->g) && c->g > 0.0 && std::isfinite(c->H0) && std::isfinite(c->dt) &&
+           c->dt > 0.0 && (c->scheme == HDGDG_ARS2 || c->scheme == HDGDG_ARS3) &&
+           c->precision == HDGDG_FP64 && (c->linear_only == 0 || c->linear_only == 1);
+}
+
+int restart_of(const hdgdg_config* c) { return c->krylov_restart > 0 ? c->krylov_restart : 20; }
+
+Plan make_plan(const hdgdg_config* c) {
+    Plan p;
+    const size_t N = (size_t)c->n_side, P = (size_t)c->degree_k + 1;
+    const size_t n_el = N * N, n_edges = 2 * N * N, Np = P * P;
+    p.n = n_el * Np;
+    p.NV = (int)(3 * Np);
+    p.NF = (int)(3 * P);
+    p.NT = (int)(12 * P);
+    p.nt = n_edges * p.NF;
+    p.m = restart_of(c);
+    p.s = c->scheme == HDGDG_ARS2 ? 3 : 5;
+    const size_t d = sizeof(double);
+    size_t b = 0;
+    b += p.n * d + n_edges * P * d;                           // phiB, tau
+    b += n_el * (size_t)p.NV * p.NV * d;                      // A^{-1}
+    b += n_edges * 6 * (size_t)p.NF * p.NF * d;               // S~
+    b += n_edges * 6 * sizeof(int);                           // columns
+    b += 2 * n_edges * (size_t)p.NF * p.NF * d;               // M^{-1}, S_rr
+    b += (5 + 2 * (size_t)p.s) * 3 * p.n * d;                 // q, q_new, R1, Z, Q, NL_i, L_i
+    b += (4 + (size_t)p.m + 1) * p.nt * d;                    // g, x~, qhat, w, Krylov basis
+    b += (dot_scratch_doubles(p.m + 1) + mass_scratch_doubles() + 4 * (size_t)(p.m + 2) + 16) * d;
+    b += 64;                                                  // flags
+    p.persistent = b;
+    p.setup_temp = n_el * (size_t)p.NT * p.NT * d + n_edges * 7 * (size_t)p.NF * p.NF * d;
+    return p;
+}
+
+// Host GLL tables: nodes by Newton on (1 - x^2) P_k'(x) = 0 in the form x P_k - P_{k-1} = 0
+// (equivalent on the interior), weights 2 / (k (k+1) P_k^2), and the closed-form GLL
+// differentiation matrix D_ij = P_k(x_i) / (P_k(x_j) (x_i - x_j)), D_00 = -k(k+1)/4,
+// D_kk = k(k+1)/4, zero elsewhere on the diagonal.
+void legendre(int k, double x, double* pk, double* pkm1) {
+    double p0 = 1.0, p1 = x;
+    if (k == 0) { *pk = 1.0; *pkm1 = 0.0; return; }
+    for (int n = 1; n < k; ++n) {
+        const double p2 = ((2.0 * n + 1.0) * x * p1 - n * p0) / (n + 1.0);
+        p0 = p1;
+        p1 = p2;
+    }
+    *pk = p1;
+    *pkm1 = p0;
+}
+
+void gll_tables(int k, double* x, double* w, double* D) {
+    const int P = k + 1;
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < P; ++i) {
+        double xi = -std::cos(pi * i / k);
+        if (i > 0 && i < k) {
+            for (int it = 0; it < 100; ++it) {
+                // Newton on f(x) = x P_k - P_{k-1}; f'(x) = (k+1) P_k (Legendre identity)
+                double pk, pkm1;
+                legendre(k, xi, &pk, &pkm1);
+                const double dx = (xi * pk - pkm1) / ((k + 1.0) * pk);
+                xi -= dx;
+                if (std::fabs(dx) < 1e-16) break;
+            }
+        }
+        x[i] = xi;
+    }
+    double Pk[kMaxP];
+    for (int i = 0; i < P; ++i) {
+        double pkm1;
+        legendre(k, x[i], &Pk[i], &pkm1);
+        w[i] = 2.0 / (k * (k + 1.0) * Pk[i] * Pk[i]);
+    }
+    for (int i = 0; i < P; ++i)
+        for (int j = 0; j < P; ++j) {
+            double v = 0.0;
+            if (i != j) v = Pk[i] / (Pk[j] * (x[i] - x[j]));
+            else if (i == 0) v = -0.25 * k * (k + 1.0);
+            else if (i == k) v = 0.25 * k * (k + 1.0);
+            D[i * P + j] = v;
+        }
+}
+
+Geom make_geom(const hdgdg_config* c, double* xi_out) {
+    Geom g;
+    std::memset(&g, 0, sizeof(g));
+    g.N = c->n_side;
+    g.P = c->degree_k + 1;
+    g.Np = g.P * g.P;
+    g.n_el = g.N * g.N;
+    g.n_edges = 2 * g.n_el;
+    g.h = 1.0 / g.N;
+    g.two_over_h = 2.0 * g.N;
+    g.J = 0.25 * g.h * g.h;
+    double xi[kMaxP];
+    gll_tables(c->degree_k, xi, g.w, g.D);
+    g.inv_w0 = 1.0 / g.w[0];
+    for (int i = 0; i < g.P; ++i)
+        for (int a = 0; a < g.P; ++a) g.Dhat[i * g.P + a] = (g.w[a] / g.w[i]) * g.D[a * g.P + i];
+    if (xi_out)
+        for (int i = 0; i < g.P; ++i) xi_out[i] = xi[i];
+    return g;
+}
+
+void scheme_tables(int scheme, double A[kMaxStages][kMaxStages], double At[kMaxStages][kMaxStages],
+                   double* b, double* bt, int* s) {
+    std::memset(A, 0, sizeof(double) * kMaxStages * kMaxStages);
+    std::memset(At, 0, sizeof(double) * kMaxStages * kMaxStages);
+    if (scheme == HDGDG_ARS2) {
+        // ARS(2,3,2), Ascher-Ruuth-Spiteri 1997: gamma = 1 - 1/sqrt 2, delta = -2 sqrt 2 / 3
+        const double gm = 1.0 - 1.0 / std::sqrt(2.0), dl = -2.0 * std::sqrt(2.0) / 3.0;
+        *s = 3;
+        A[1][0] = gm;
+        A[2][0] = dl;
+        A[2][1] = 1.0 - dl;
+        At[1][1] = gm;
+        At[2][1] = 1.0 - gm;
+        At[2][2] = gm;
+        b[0] = 0.0; b[1] = 1.0 - gm; b[2] = gm;
+        bt[0] = 0.0; bt[1] = 1.0 - gm; bt[2] = gm;
+    } else {
+        // ARS(4,4,3), Ascher-Ruuth-Spiteri 1997, implicit diagonal 1/2
+        *s = 5;
+        const double a[5][5] = {{0, 0, 0, 0, 0},
+                                {1.0 / 2, 0, 0, 0, 0},
+                                {11.0 / 18, 1.0 / 18, 0, 0, 0},
+                                {5.0 / 6, -5.0 / 6, 1.0 / 2, 0, 0},
+                                {1.0 / 4, 7.0 / 4, 3.0 / 4, -7.0 / 4, 0}};
+        const double at[5][5] = {{0, 0, 0, 0, 0},
+                                 {0, 1.0 / 2, 0, 0, 0},
+                                 {0, 1.0 / 6, 1.0 / 2, 0, 0},
+                                 {0, -1.0 / 2, 1.0 / 2, 1.0 / 2, 0},
+                                 {0, 3.0 / 2, -3.0 / 2, 1.0 / 2, 1.0 / 2}};
+        for (int i = 0; i < 5; ++i)
+            for (int j = 0; j < 5; ++j) { A[i][j] = a[i][j]; At[i][j] = at[i][j]; }
+        for (int j = 0; j < 5; ++j) { b[j] = a[4][j]; bt[j] = at[4][j]; }
+    }
+}
+
+}  // namespace
+
+struct hdgdg_sim {
+    hdgdg_config cfg;
+    Plan plan;
+    Geom g;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    int s = 0;
+    double A[kMaxStages][kMaxStages], At[kMaxStages][kMaxStages], b[kMaxStages], bt[kMaxStages];
+    double a_ii = 0.0;
+    // device memory
+    std::vector<void*> allocs;
+    double *phiB = nullptr, *tau = nullptr, *Ainv = nullptr, *Stil = nullptr, *Minv = nullptr, *Srr = nullptr;
+    int* Scol = nullptr;
+    double *q = nullptr, *q_new = nullptr, *R1 = nullptr, *Z = nullptr, *Qs = nullptr;
+    double *NLs[kMaxStages] = {}, *Ls[kMaxStages] = {};
+    double *gvec = nullptr, *xt = nullptr, *lam = nullptr, *w = nullptr, *V = nullptr;
+    double *red = nullptr, *mred = nullptr, *dvals = nullptr;
+    unsigned* flags = nullptr;
+    double* hbuf = nullptr;   // pinned host scratch
+    // run state
+    bool have_state = false;
+    hdgdg_stats stats{};
+    // per-kernel-class timers
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Pending { cudaEvent_t a, b; int cls; };
+    std::vector<Pending> pending;
+    double kt_ms[HDGDG_KT_COUNT] = {};
+    long long kt_n[HDGDG_KT_COUNT] = {};
+};
+
+namespace {
+
+hdgdg_status fail(hdgdg_sim* s, hdgdg_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (s) s->err = buf;
+    return st;
+}
+
+#define CU(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(sim, HDGDG_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                                     \
+    } while (0)
+
+template <typename T>
+hdgdg_status dalloc(hdgdg_sim* sim, T** p, size_t count) {
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(sim, HDGDG_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+                    cudaGetErrorString(e));
+    }
+    sim->allocs.push_back(v);
+    *p = static_cast<T*>(v);
+    return HDGDG_OK;
+}
+
+#define TRY(x)                               \
+    do {                                     \
+        hdgdg_status st_ = (x);              \
+        if (st_ != HDGDG_OK) return st_;     \
+    } while (0)
+
+// Slots of the small device array dvals
+inline double* dv_h1(hdgdg_sim* s) { return s->dvals; }
+inline double* dv_h2(hdgdg_sim* s) { return s->dvals + (s->plan.m + 2); }
+inline double* dv_nrm(hdgdg_sim* s) { return s->dvals + 2 * (s->plan.m + 2); }
+inline double* dv_coef(hdgdg_sim* s) { return s->dvals + 2 * (s->plan.m + 2) + 8; }
+
+cudaEvent_t take_event(hdgdg_sim* sim) {
+    if (!sim->ev_pool.empty()) {
+        cudaEvent_t e = sim->ev_pool.back();
+        sim->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Bracket a launch group of class cls with events (no-op unless timing is on).
+struct TimedGroup {
+    hdgdg_sim* sim;
+    int cls;
+    cudaEvent_t a = nullptr;
+    TimedGroup(hdgdg_sim* s, int c) : sim(s), cls(c) {
+        if (sim->timing && (a = take_event(sim))) cudaEventRecord(a, sim->stream);
+    }
+    ~TimedGroup() {
+        if (!a) return;
+        cudaEvent_t b = take_event(sim);
+        if (!b) { sim->ev_pool.push_back(a); return; }
+        cudaEventRecord(b, sim->stream);
+        sim->pending.push_back({a, b, cls});
+    }
+};
+
+void flush_timers(hdgdg_sim* sim) {
+    for (auto& p : sim->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            sim->kt_ms[p.cls] += ms;
+            sim->kt_n[p.cls] += 1;
+        }
+        sim->ev_pool.push_back(p.a);
+        sim->ev_pool.push_back(p.b);
+    }
+    sim->pending.clear();
+}
+
+hdgdg_status sync(hdgdg_sim* sim) {
+    CU(cudaStreamSynchronize(sim->stream));
+    flush_timers(sim);
+    return HDGDG_OK;
+}
+
+// ||v||^2 into dv_nrm, copied to host hbuf[0]
+hdgdg_status norm2_to_host(hdgdg_sim* sim, const double* v, double* out) {
+    CU(launch_multidot(v, 0, 1, v, sim->plan.nt, sim->red, dv_nrm(sim), sim->stream));
+    CU(cudaMemcpyAsync(sim->hbuf, dv_nrm(sim), sizeof(double), cudaMemcpyDeviceToHost, sim->stream));
+    TRY(sync(sim));
+    *out = sim->hbuf[0];
+    return HDGDG_OK;
+}
+
+// Right-preconditioned GMRES(m) with CGS2 on S~ x~ = g, then qhat = M^{-1} x~.
+hdgdg_status gmres(hdgdg_sim* sim, const double* g, double* qhat, int* iters, double* relres) {
+    const size_t n = sim->plan.nt;
+    const int m = sim->plan.m;
+    const double rtol = sim->cfg.krylov_rtol > 0.0 ? sim->cfg.krylov_rtol : 1e-13;
+    const int maxit = sim->cfg.krylov_maxit > 0 ? sim->cfg.krylov_maxit : 2000;
+    cudaStream_t st = sim->stream;
+    *iters = 0;
+    double bn2;
+    TRY(norm2_to_host(sim, g, &bn2));
+    if (!std::isfinite(bn2)) return fail(sim, HDGDG_ENONFINITE, "non-finite trace right-hand side");
+    if (bn2 == 0.0) {
+        CU(cudaMemsetAsync(qhat, 0, n * sizeof(double), st));
+        *relres = 0.0;
+        return HDGDG_OK;
+    }
+    const double bnorm = std::sqrt(bn2), tol = rtol * bnorm;
+    CU(cudaMemsetAsync(sim->xt, 0, n * sizeof(double), st));
+    CU(cudaMemcpyAsync(sim->w, g, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), sv(m + 1), y(m);
+    auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+    double rnorm = bnorm;
+    CU(launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st));
+    int total = 0;
+    while (true) {
+        CU(launch_scale_by_rnorm(sim->w, dv_nrm(sim), sim->V, n, st));
+        std::fill(sv.begin(), sv.end(), 0.0);
+        sv[0] = rnorm;
+        int jend = 0;
+        for (int j = 0; j < m; ++j) {
+            double* Vj = sim->V + (size_t)j * n;
+            {
+                TimedGroup tg(sim, HDGDG_KT_SPMV);
+                CU(launch_spmv_pre(sim->g, sim->Stil, sim->Scol, Vj, sim->w, st));
+            }
+            {
+                TimedGroup tg(sim, HDGDG_KT_ORTHO);
+                CU(launch_multidot(sim->V, n, j + 1, sim->w, n, sim->red, dv_h1(sim), st));
+                CU(launch_multiaxpy(sim->V, n, j + 1, dv_h1(sim), 1.0, sim->w, n, st));
+                CU(launch_multidot(sim->V, n, j + 1, sim->w, n, sim->red, dv_h2(sim), st));
+                CU(launch_multiaxpy(sim->V, n, j + 1, dv_h2(sim), 1.0, sim->w, n, st));
+                CU(launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st));
+                CU(launch_scale_by_rnorm(sim->w, dv_nrm(sim), sim->V + (size_t)(j + 1) * n, n, st));
+            }
+            CU(cudaMemcpyAsync(sim->hbuf, sim->dvals, (2 * (m + 2) + 1) * sizeof(double),
+                               cudaMemcpyDeviceToHost, st));
+            TRY(sync(sim));
+            const double* h1 = sim->hbuf;
+            const double* h2 = sim->hbuf + (m + 2);
+            for (int i = 0; i <= j; ++i) Hij(i, j) = h1[i] + h2[i];
+            Hij(j + 1, j) = std::sqrt(sim->hbuf[2 * (m + 2)]);
+            for (int i = 0; i < j; ++i) {
+                const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+                Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
+                Hij(i, j) = t;
+            }
+            const double den = std::hypot(Hij(j, j), Hij(j + 1, j));
+            cs[j] = den > 0.0 ? Hij(j, j) / den : 1.0;
+            sn[j] = den > 0.0 ? Hij(j + 1, j) / den : 0.0;
+            const double hsub = Hij(j + 1, j);
+            Hij(j, j) = den;
+            Hij(j + 1, j) = 0.0;
+            sv[j + 1] = -sn[j] * sv[j];
+            sv[j] = cs[j] * sv[j];
+            ++total;
+            jend = j + 1;
+            if (!std::isfinite(sv[j + 1]))
+                return fail(sim, HDGDG_ENONFINITE, "non-finite GMRES residual at iteration %d", total);
+            if (std::fabs(sv[j + 1]) <= tol || total >= maxit || hsub == 0.0) break;
+        }
+        for (int i = jend - 1; i >= 0; --i) {
+            double acc = sv[i];
+            for (int k = i + 1; k < jend; ++k) acc -= Hij(i, k) * y[k];
+            y[i] = acc / Hij(i, i);
+        }
+        CU(cudaMemcpyAsync(dv_coef(sim), y.data(), jend * sizeof(double), cudaMemcpyHostToDevice, st));
+        CU(launch_multiaxpy(sim->V, n, jend, dv_coef(sim), -1.0, sim->xt, n, st));
+        // true residual r = g - S~ x~
+        CU(launch_spmv_pre(sim->g, sim->Stil, sim->Scol, sim->xt, sim->w, st));
+        CombineTerms t{};
+        t.n = 1;
+        t.X[0] = sim->w;
+        t.c[0] = -1.0;
+        CU(launch_combine(n, g, t, sim->w, nullptr, st));
+        double rn2;
+        TRY(norm2_to_host(sim, sim->w, &rn2));   // also leaves ||r||^2 in dv_nrm for the restart
+        rnorm = std::sqrt(rn2);
+        if (rnorm <= tol) break;
+        if (total >= maxit) {
+            *iters = total;
+            *relres = rnorm / bnorm;
+            sim->stats.last_krylov_iterations = total;
+            sim->stats.last_rel_residual = *relres;
+            return fail(sim, HDGDG_ENOTCONVERGED,
+                        "GMRES: relative residual %.3e > %.3e after %d iterations", rnorm / bnorm,
+                        rtol, total);
+        }
+    }
+    CU(launch_block_diag(sim->g, sim->Minv, sim->xt, qhat, st));
+    *iters = total;
+    *relres = rnorm / bnorm;
+    sim->stats.last_krylov_iterations = total;
+    sim->stats.last_rel_residual = *relres;
+    sim->stats.krylov_iterations += total;
+    return HDGDG_OK;
+}
+
+double beta_of(const hdgdg_sim* sim) { return sim->cfg.dt * sim->a_ii * sim->g.two_over_h * sim->g.inv_w0; }
+
+// One implicit stage: R1 (device) -> Q, Lst = dt M^{-1} L (device); qhat left in sim->lam.
+hdgdg_status stage_solve_dev(hdgdg_sim* sim, const double* R1, double* Q, double* Lst, int* its) {
+    double rr;
+    {
+        TimedGroup tg(sim, HDGDG_KT_CONDENSE);
+        CU(launch_condense(sim->g, sim->Ainv, R1, sim->phiB, sim->tau, sim->Z, sim->gvec, sim->stream));
+    }
+    TRY(gmres(sim, sim->gvec, sim->lam, its, &rr));
+    {
+        TimedGroup tg(sim, HDGDG_KT_RECOVER);
+        CU(launch_recover(sim->g, sim->Ainv, sim->Z, R1, sim->tau, sim->lam, beta_of(sim), 1.0 / sim->a_ii,
+                          Q, Lst, sim->stream));
+    }
+    return HDGDG_OK;
+}
+
+hdgdg_status one_step(hdgdg_sim* sim) {
+    const size_t n3 = 3 * sim->plan.n;
+    cudaStream_t st = sim->stream;
+    for (int i = 0; i < sim->s; ++i) {
+        const double* Qi = sim->q;
+        if (sim->At[i][i] != 0.0) {
+            CombineTerms t{};
+            for (int j = 0; j < i; ++j) {
+                if (sim->A[i][j] != 0.0 && !sim->cfg.linear_only) { t.X[t.n] = sim->NLs[j]; t.c[t.n++] = sim->A[i][j]; }
+                if (sim->At[i][j] != 0.0) { t.X[t.n] = sim->Ls[j]; t.c[t.n++] = sim->At[i][j]; }
+            }
+            {
+                TimedGroup tg(sim, HDGDG_KT_COMBINE);
+                CU(launch_combine(n3, sim->q, t, sim->R1, nullptr, st));
+            }
+            int its = 0;
+            TRY(stage_solve_dev(sim, sim->R1, sim->Qs, sim->Ls[i], &its));
+            Qi = sim->Qs;
+        }
+        if (!sim->cfg.linear_only) {
+            TimedGroup tg(sim, HDGDG_KT_DG);
+            CU(launch_dg_nl(sim->g, Qi, sim->phiB, sim->cfg.dt, sim->NLs[i], st));
+        }
+    }
+    CombineTerms t{};
+    for (int i = 0; i < sim->s; ++i) {
+        if (sim->b[i] != 0.0 && !sim->cfg.linear_only) { t.X[t.n] = sim->NLs[i]; t.c[t.n++] = sim->b[i]; }
+        if (sim->bt[i] != 0.0) { t.X[t.n] = sim->Ls[i]; t.c[t.n++] = sim->bt[i]; }
+    }
+    CU(cudaMemsetAsync(sim->flags, 0, sizeof(unsigned), st));
+    {
+        TimedGroup tg(sim, HDGDG_KT_COMBINE);
+        CU(launch_combine(n3, sim->q, t, sim->q_new, sim->flags, st));
+    }
+    unsigned flag = 0;
+    CU(cudaMemcpyAsync(&sim->hbuf[0], sim->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    TRY(sync(sim));
+    std::memcpy(&flag, &sim->hbuf[0], sizeof(unsigned));
+    if (flag) return fail(sim, HDGDG_ENONFINITE, "step %lld produced a non-finite state", sim->stats.steps + 1);
+    std::swap(sim->q, sim->q_new);
+    sim->stats.steps += 1;
+    return HDGDG_OK;
+}
+
+hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
+    const hdgdg_config* c = &sim->cfg;
+    const Plan& p = sim->plan;
+    const Geom& g = sim->g;
+    const int P = g.P, Np = g.Np;
+    // phi_B = g (H0 - b) at the nodes; tau = max of sqrt(phi_B) over both sides of each edge node
+    std::vector<double> phiB(p.n), tau((size_t)g.n_edges * P);
+    for (size_t k = 0; k < p.n; ++k) {
+        const double b = bottom_b ? bottom_b[k] : 0.0;
+        phiB[k] = c->g * (c->H0 - b);
+        if (!std::isfinite(phiB[k])) return fail(sim, HDGDG_ENONFINITE, "non-finite bottom at node %zu", k);
+        if (!(phiB[k] > 0.0))
+            return fail(sim, HDGDG_EINVAL, "reference depth H0 - b must be positive (node %zu)", k);
+    }
+    for (int r = 0; r < g.n_edges; ++r) {
+        int em, fm, ep, fp;
+        edge_sides(r, g.N, &em, &fm, &ep, &fp);
+        for (int b = 0; b < P; ++b) {
+            const double a1 = std::sqrt(phiB[(size_t)em * Np + face_node(fm, b, P)]);
+            const double a2 = std::sqrt(phiB[(size_t)ep * Np + face_node(fp, b, P)]);
+            tau[(size_t)r * P + b] = a1 > a2 ? a1 : a2;
+        }
+    }
+    TRY(dalloc(sim, &sim->phiB, p.n));
+    TRY(dalloc(sim, &sim->tau, tau.size()));
+    TRY(dalloc(sim, &sim->Ainv, (size_t)g.n_el * p.NV * p.NV));
+    TRY(dalloc(sim, &sim->Stil, (size_t)g.n_edges * 6 * p.NF * p.NF));
+    TRY(dalloc(sim, &sim->Scol, (size_t)g.n_edges * 6));
+    TRY(dalloc(sim, &sim->Minv, (size_t)g.n_edges * p.NF * p.NF));
+    TRY(dalloc(sim, &sim->Srr, (size_t)g.n_edges * p.NF * p.NF));
+    for (double** v : {&sim->q, &sim->q_new, &sim->R1, &sim->Z, &sim->Qs}) TRY(dalloc(sim, v, 3 * p.n));
+    for (int i = 0; i < p.s; ++i) {
+        TRY(dalloc(sim, &sim->NLs[i], 3 * p.n));
+        TRY(dalloc(sim, &sim->Ls[i], 3 * p.n));
+    }
+    for (double** v : {&sim->gvec, &sim->xt, &sim->lam, &sim->w}) TRY(dalloc(sim, v, p.nt));
+    TRY(dalloc(sim, &sim->V, (size_t)(p.m + 1) * p.nt));
+    TRY(dalloc(sim, &sim->red, dot_scratch_doubles(p.m + 1)));
+    TRY(dalloc(sim, &sim->mred, mass_scratch_doubles()));
+    TRY(dalloc(sim, &sim->dvals, 4 * (size_t)(p.m + 2) + 16));
+    TRY(dalloc(sim, &sim->flags, 16));
+    CU(cudaMallocHost(&sim->hbuf, (4 * (size_t)(p.m + 2) + 16) * sizeof(double)));
+    for (int i = 0; i < p.s; ++i) {
+        CU(cudaMemsetAsync(sim->NLs[i], 0, 3 * p.n * sizeof(double), sim->stream));
+        CU(cudaMemsetAsync(sim->Ls[i], 0, 3 * p.n * sizeof(double), sim->stream));
+    }
+    CU(cudaMemcpyAsync(sim->phiB, phiB.data(), p.n * sizeof(double), cudaMemcpyHostToDevice, sim->stream));
+    CU(cudaMemcpyAsync(sim->tau, tau.data(), tau.size() * sizeof(double), cudaMemcpyHostToDevice, sim->stream));
+    // setup-only temporaries: element Schur blocks and the full 7-block rows
+    double *Se = nullptr, *S7 = nullptr;
+    CU(cudaMalloc(&Se, (size_t)g.n_el * p.NT * p.NT * sizeof(double)));
+    cudaError_t e2 = cudaMalloc(&S7, (size_t)g.n_edges * 7 * p.NF * p.NF * sizeof(double));
+    if (e2 != cudaSuccess) {
+        cudaFree(Se);
+        cudaGetLastError();
+        return fail(sim, HDGDG_ENOMEM, "setup temporaries: %s", cudaGetErrorString(e2));
+    }
+    int* dsing = reinterpret_cast<int*>(sim->flags) + 1;
+    CU(cudaMemsetAsync(dsing, 0, sizeof(int), sim->stream));
+    cudaError_t e = launch_build_local(g, sim->phiB, sim->tau, c->dt * sim->a_ii, sim->Ainv, Se, dsing, sim->stream);
+    if (e == cudaSuccess)
+        e = launch_assemble_trace(g, Se, S7, sim->Srr, sim->Minv, sim->Stil, sim->Scol, dsing, sim->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
+    cudaFree(Se);
+    cudaFree(S7);
+    if (e != cudaSuccess) return fail(sim, HDGDG_ECUDA, "operator setup failed: %s", cudaGetErrorString(e));
+    int sing = 0;
+    CU(cudaMemcpy(&sing, dsing, sizeof(int), cudaMemcpyDeviceToHost));
+    if (sing) return fail(sim, HDGDG_EINVAL, "a local operator block is singular");
+    return HDGDG_OK;
+}
+
+hdgdg_status upload3(hdgdg_sim* sim, double* dst, const double* src, size_t count) {
+    CU(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyHostToDevice, sim->stream));
+    return HDGDG_OK;
+}
+
+hdgdg_status download(hdgdg_sim* sim, double* dst, const double* src, size_t count) {
+    CU(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDeviceToHost, sim->stream));
+    return sync(sim);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t hdgdg_bytes_required(const hdgdg_config* cfg) {
+    if (!valid(cfg)) return 0;
+    const Plan p = make_plan(cfg);
+    return p.persistent + p.setup_temp;
+}
+
+hdgdg_status hdgdg_node_coords(const hdgdg_config* cfg, double* x, double* y) {
+    if (!valid(cfg) || !x || !y) return HDGDG_EINVAL;
+    double xi[kMaxP];
+    Geom g = make_geom(cfg, xi);
+    for (int e = 0; e < g.n_el; ++e) {
+        const int ex = e % g.N, ey = e / g.N;
+        for (int j = 0; j < g.P; ++j)
+            for (int i = 0; i < g.P; ++i) {
+                x[(size_t)e * g.Np + j * g.P + i] = (ex + (1.0 + xi[i]) / 2.0) / g.N;
+                y[(size_t)e * g.Np + j * g.P + i] = (ey + (1.0 + xi[j]) / 2.0) / g.N;
+            }
+    }
+    return HDGDG_OK;
+}
+
+const char* hdgdg_last_error(const hdgdg_sim* sim) {
+    if (!sim) return "no handle";
+    return sim->err.c_str();
+}
+
+void hdgdg_destroy(hdgdg_sim* sim) {
+    if (!sim) return;
+    if (sim->stream) cudaStreamSynchronize(sim->stream);
+    flush_timers(sim);
+    for (cudaEvent_t e : sim->ev_pool) cudaEventDestroy(e);
+    for (void* p : sim->allocs) cudaFree(p);
+    if (sim->hbuf) cudaFreeHost(sim->hbuf);
+    if (sim->own_stream && sim->stream) cudaStreamDestroy(sim->stream);
+    delete sim;
+}
+
+hdgdg_status hdgdg_create(const hdgdg_config* cfg, const double* bottom_b, void* cuda_stream,
+                          hdgdg_sim** out) {
+    if (!out) return HDGDG_EINVAL;
+    *out = nullptr;
+    if (!valid(cfg)) return HDGDG_EINVAL;
+    hdgdg_sim* sim = new (std::nothrow) hdgdg_sim();
+    if (!sim) return HDGDG_ENOMEM;
+    sim->cfg = *cfg;
+    sim->plan = make_plan(cfg);
+    sim->g = make_geom(cfg, nullptr);
+    scheme_tables(cfg->scheme, sim->A, sim->At, sim->b, sim->bt, &sim->s);
+    sim->a_ii = sim->At[1][1];
+    for (int i = 0; i < sim->s; ++i) {
+        if (sim->At[i][i] != 0.0 && sim->At[i][i] != sim->a_ii) {
+            hdgdg_destroy(sim);
+            return HDGDG_EINVAL;
+        }
+    }
+    if (cuda_stream) {
+        sim->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&sim->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            hdgdg_destroy(sim);
+            return HDGDG_ECUDA;
+        }
+        sim->own_stream = true;
+    }
+    hdgdg_status st = setup(sim, bottom_b);
+    if (st != HDGDG_OK) {
+        // keep the handle so the caller can read the message; it may only be destroyed
+        *out = sim;
+        return st;
+    }
+    *out = sim;
+    return HDGDG_OK;
+}
+
+hdgdg_status hdgdg_set_state(hdgdg_sim* sim, const double* h, const double* hu, const double* hv) {
+    if (!sim || !h || !hu || !hv) return fail(sim, HDGDG_EINVAL, "NULL argument to set_state");
+    const size_t n = sim->plan.n;
+    double* stg = sim->NLs[0];
+    TRY(upload3(sim, stg, h, n));
+    TRY(upload3(sim, stg + n, hu, n));
+    TRY(upload3(sim, stg + 2 * n, hv, n));
+    CU(cudaMemsetAsync(sim->flags, 0, sizeof(unsigned), sim->stream));
+    CU(launch_user_to_state(sim->g, stg, stg + n, stg + 2 * n, sim->phiB, sim->cfg.g, sim->q, sim->flags,
+                            sim->stream));
+    CU(cudaMemcpyAsync(sim->hbuf, sim->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, sim->stream));
+    TRY(sync(sim));
+    unsigned bad = 0;
+    std::memcpy(&bad, sim->hbuf, sizeof(unsigned));
+    if (bad) {
+        sim->have_state = false;
+        return fail(sim, HDGDG_ENONFINITE, "state has a non-finite value or non-positive depth");
+    }
+    sim->have_state = true;
+    sim->stats = hdgdg_stats{};
+    return HDGDG_OK;
+}
+
+hdgdg_status hdgdg_step(hdgdg_sim* sim, int n_steps) {
+    if (!sim) return HDGDG_EINVAL;
+    if (n_steps < 0) return fail(sim, HDGDG_EINVAL, "n_steps < 0");
+    if (!sim->have_state) return fail(sim, HDGDG_ESTATE, "step before set_state");
+    for (int k = 0; k < n_steps; ++k) {
+        const long long l0 = launches_total();
+        const hdgdg_status st = one_step(sim);
+        sim->stats.kernel_launches += launches_total() - l0;
+        if (st != HDGDG_OK) return st;
+    }
+    return HDGDG_OK;
+}
+
+hdgdg_status hdgdg_get_state(hdgdg_sim* sim, double* h, double* hu, double* hv) {
+    if (!sim || !h || !hu || !hv) return fail(sim, HDGDG_EINVAL, "NULL argument to get_state");
+    if (!sim->have_state) return fail(sim, HDGDG_ESTATE, "get_state before set_state");
+    const size_t n = sim->plan.n;
+    double* stg = sim->NLs[0];
+    CU(launch_state_to_user(sim->g, sim->q, sim->phiB, sim->cfg.g, stg, stg + n, stg + 2 * n, sim->stream));
+    CU(cudaMemcpyAsync(h, stg, n * sizeof(double), cudaMemcpyDeviceToHost, sim->stream));
+    CU(cudaMemcpyAsync(hu, stg + n, n * sizeof(double), cudaMemcpyDeviceToHost, sim->stream));
+    CU(cudaMemcpyAsync(hv, stg + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost, sim->stream));
+    return sync(sim);
+}
+
+hdgdg_status hdgdg_get_stats(hdgdg_sim* sim, hdgdg_stats* out) {
+    if (!sim || !out) return fail(sim, HDGDG_EINVAL, "NULL argument to get_stats");
+    if (sim->have_state) {
+        CU(launch_mass(sim->g, sim->q, sim->mred, dv_nrm(sim), sim->stream));
+        CU(cudaMemcpyAsync(sim->hbuf, dv_nrm(sim), sizeof(double), cudaMemcpyDeviceToHost, sim->stream));
+        TRY(sync(sim));
+        sim->stats.mass = sim->hbuf[0];
+    }
+    *out = sim->stats;
+    return HDGDG_OK;
+}
+
+hdgdg_status hdgdg_eval_nl(hdgdg_sim* sim, const double* q, double* out) {
+    if (!sim || !q || !out) return fail(sim, HDGDG_EINVAL, "NULL argument to eval_nl");
+    const size_t n3 = 3 * sim->plan.n;
+    TRY(upload3(sim, sim->R1, q, n3));
+    CU(launch_dg_nl(sim->g, sim->R1, sim->phiB, 1.0, sim->Qs, sim->stream));
+    return download(sim, out, sim->Qs, n3);
+}
+
+hdgdg_status hdgdg_condense_rhs(hdgdg_sim* sim, const double* R1, double* out) {
+    if (!sim || !R1 || !out) return fail(sim, HDGDG_EINVAL, "NULL argument to condense_rhs");
+    TRY(upload3(sim, sim->R1, R1, 3 * sim->plan.n));
+    CU(launch_condense(sim->g, sim->Ainv, sim->R1, sim->phiB, sim->tau, sim->Z, sim->gvec, sim->stream));
+    return download(sim, out, sim->gvec, sim->plan.nt);
+}
+
+hdgdg_status hdgdg_trace_apply(hdgdg_sim* sim, const double* x, double* y) {
+    if (!sim || !x || !y) return fail(sim, HDGDG_EINVAL, "NULL argument to trace_apply");
+    TRY(upload3(sim, sim->lam, x, sim->plan.nt));
+    CU(launch_block_diag(sim->g, sim->Srr, sim->lam, sim->xt, sim->stream));          // u = S_rr x
+    CU(launch_spmv_pre(sim->g, sim->Stil, sim->Scol, sim->xt, sim->gvec, sim->stream));  // y = S~ u
+    return download(sim, y, sim->gvec, sim->plan.nt);
+}
+
+hdgdg_status hdgdg_stage_solve(hdgdg_sim* sim, const double* R1, double* Q, double* qhat, int* iterations) {
+    if (!sim || !R1 || !Q) return fail(sim, HDGDG_EINVAL, "NULL argument to stage_solve");
+    const size_t n3 = 3 * sim->plan.n;
+    TRY(upload3(sim, sim->R1, R1, n3));
+    int its = 0;
+    TRY(stage_solve_dev(sim, sim->R1, sim->Qs, sim->Ls[0], &its));
+    if (iterations) *iterations = its;
+    TRY(download(sim, Q, sim->Qs, n3));
+    if (qhat) TRY(download(sim, qhat, sim->lam, sim->plan.nt));
+    return HDGDG_OK;
+}
+
+hdgdg_status hdgdg_set_kernel_timing(hdgdg_sim* sim, int on) {
+    if (!sim) return HDGDG_EINVAL;
+    TRY(sync(sim));
+    sim->timing = on != 0;
+    for (int c = 0; c < HDGDG_KT_COUNT; ++c) { sim->kt_ms[c] = 0.0; sim->kt_n[c] = 0; }
+    return HDGDG_OK;
+}
+
+hdgdg_status hdgdg_kernel_time(hdgdg_sim* sim, int cls, double* total_ms, long long* launches) {
+    if (!sim || cls < 0 || cls >= HDGDG_KT_COUNT || !total_ms || !launches)
+        return fail(sim, HDGDG_EINVAL, "bad argument to kernel_time");
+    TRY(sync(sim));
+    *total_ms = sim->kt_ms[cls];
+    *launches = sim->kt_n[cls];
+    return HDGDG_OK;
+}
+
+hdgdg_status hdgdg_measure_fp64_tflops(double* tflops) {
+    if (!tflops) return HDGDG_EINVAL;
+    return measure_fp64_fma(tflops) == cudaSuccess ? HDGDG_OK : HDGDG_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// Internal declarations shared by the translation units of libhdgdg (not part of the ABI).
+//
+// Data layout in device memory (FP64):
+//   state / stage vectors   [field c (phi_eta, U, V)][element e][node n = j*P + i]
+//   trace vectors           [edge r][field c][node b]                (n_f = 3P per edge)
+//   A^{-1} per element      [e][column s][row r], r, s = c*P*P + j*P + i  (column major)
+//   preconditioned trace    [edge][slot 0..5][column jj][row ii]  of S~ = S M^{-1},
+//     matrix (off-diagonal    slot order: the three other faces of the edge's minus
+//     blocks only; the        element (ascending local face), then those of its plus
+//     diagonal block is I)    element; column edge index in Scol[edge][slot]
+//   block-Jacobi blocks     [edge][column jj][row ii] of M^{-1} = S_rr^{-1} and of S_rr
+//
+// Local faces of an element: 0 = x-minus (left), 1 = x-plus (right), 2 = y-minus, 3 = y-plus.
+// Edge r < N^2 is face 1 of element r; edge N^2 + r is face 3 of element r.  The element on
+// face 1/3 is the edge's "minus" side (normal +x / +y), the element on face 0/2 its "plus" side.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace hdgdg {
+
+constexpr int kMaxP = 6;   // degree k <= 5
+
+// Mesh and GLL tables, passed by value to kernels.
+struct Geom {
+    int N, P, Np, n_el, n_edges;
+    double h;                   // element size 1/N
+    double two_over_h;          // d(xi)/dx
+    double inv_w0;              // 1 / w_0 (= 1 / w_k): face lift of the collocated mass matrix
+    double J;                   // area Jacobian (h/2)^2
+    double w[kMaxP];            // GLL weights
+    double D[kMaxP * kMaxP];    // D[r*P + c] = l_c'(xi_r)
+    double Dhat[kMaxP * kMaxP]; // Dhat[i*P + a] = (w_a / w_i) D[a*P + i]: weak-form volume lift
+};
+
+__host__ __device__ inline int face_node(int f, int b, int P) {
+    return f == 0 ? b * P : f == 1 ? b * P + P - 1 : f == 2 ? b : (P - 1) * P + b;
+}
+
+__host__ __device__ inline int edge_of_face(int e, int f, int N) {
+    const int ex = e % N, ey = e / N;
+    switch (f) {
+        case 0: return ey * N + (ex + N - 1) % N;
+        case 1: return e;
+        case 2: return N * N + ((ey + N - 1) % N) * N + ex;
+        default: return N * N + e;
+    }
+}
+
+__host__ __device__ inline int neighbour(int e, int f, int N) {
+    const int ex = e % N, ey = e / N;
+    switch (f) {
+        case 0: return ey * N + (ex + N - 1) % N;
+        case 1: return ey * N + (ex + 1) % N;
+        case 2: return ((ey + N - 1) % N) * N + ex;
+        default: return ((ey + 1) % N) * N + ex;
+    }
+}
+
+// Minus / plus element and their faces for edge r.
+__host__ __device__ inline void edge_sides(int r, int N, int* em, int* fm, int* ep, int* fp) {
+    if (r < N * N) { *em = r; *fm = 1; *ep = neighbour(r, 1, N); *fp = 0; }
+    else { const int e = r - N * N; *em = e; *fm = 3; *ep = neighbour(e, 3, N); *fp = 2; }
+}
+
+// Kernels launched by this library since load (every launcher adds its own launches).
+long long launches_total();
+void count_launches(int n);
+
+// ---- kernel launchers (each returns the launch error) -------------------------------
+// out = scale * M^{-1} NL(q)
+cudaError_t launch_dg_nl(const Geom& g, const double* q, const double* phiB, double scale,
+                         double* out, cudaStream_t s);
+
+struct CombineTerms {
+    const double* X[10];
+    double c[10];
+    int n;
+};
+// out = base + sum_t c_t X_t over n doubles (out may alias base)
+cudaError_t launch_combine(size_t n, const double* base, const CombineTerms& t, double* out,
+                           unsigned* nonfinite_flag, cudaStream_t s);
+
+// Setup: per element A^{-1} (column major) and the element Schur block S_e (pointwise rows).
+cudaError_t launch_build_local(const Geom& g, const double* phiB, const double* tau_edge,
+                               double dta, double* Ainv, double* Se, int* singular, cudaStream_t s);
+// Setup: edge-block rows of S from S_e, S_rr^{-1}, S~ = S M^{-1} and the column indices.
+cudaError_t launch_assemble_trace(const Geom& g, const double* Se, double* S7, double* Srr,
+                                  double* Minv, double* Stil, int* Scol, int* singular,
+                                  cudaStream_t s);
+
+// Condensation: Z = A^{-1} R1 per element, then g = -C Z edge by edge (pointwise rows).
+cudaError_t launch_condense(const Geom& g, const double* Ainv, const double* R1, const double* phiB,
+                            const double* tau_edge, double* Z, double* gvec, cudaStream_t s);
+// Recovery: Q = Z + beta A^{-1} (tau qhat) on boundary nodes; Lst = (Q - R1) / a_ii.
+cudaError_t launch_recover(const Geom& g, const double* Ainv, const double* Z, const double* R1,
+                           const double* tau_edge, const double* qhat, double beta, double inv_aii,
+                           double* Q, double* Lst, cudaStream_t s);
+
+// Krylov set on trace vectors of n = n_edges * nf doubles.
+// y = x + sum_slots S~ x[col]   (S~ with identity diagonal blocks)
+cudaError_t launch_spmv_pre(const Geom& g, const double* Stil, const int* Scol, const double* x,
+                            double* y, cudaStream_t s);
+// y = B x for a block-diagonal matrix B given as [edge][col][row] blocks
+cudaError_t launch_block_diag(const Geom& g, const double* Bd, const double* x, double* y,
+                              cudaStream_t s);
+// out[j] = <V_j, w>, j < nv, V_j = V + j * ldv; uses partial-sum scratch of
+// dot_scratch_doubles(nv) doubles.  Deterministic (fixed grid, fixed order).
+size_t dot_scratch_doubles(int nv);
+cudaError_t launch_multidot(const double* V, size_t ldv, int nv, const double* w, size_t n,
+                            double* scratch, double* out, cudaStream_t s);
+// w = w - sum_j coef[j] V_j   (coef on the device)
+cudaError_t launch_multiaxpy(const double* V, size_t ldv, int nv, const double* coef, double sign,
+                             double* w, size_t n, cudaStream_t s);
+// v = w / sqrt(*nrm2)
+cudaError_t launch_scale_by_rnorm(const double* w, const double* nrm2, double* v, size_t n,
+                                  cudaStream_t s);
+
+// User-state conversion and diagnostics.
+cudaError_t launch_user_to_state(const Geom& g, const double* h, const double* hu, const double* hv,
+                                 const double* phiB, double gacc, double* q, unsigned* bad,
+                                 cudaStream_t s);
+cudaError_t launch_state_to_user(const Geom& g, const double* q, const double* phiB, double gacc,
+                                 double* h, double* hu, double* hv, cudaStream_t s);
+size_t mass_scratch_doubles();
+cudaError_t launch_mass(const Geom& g, const double* q, double* scratch, double* out, cudaStream_t s);
+
+cudaError_t measure_fp64_fma(double* tflops);
+
+}  // namespace hdgdg

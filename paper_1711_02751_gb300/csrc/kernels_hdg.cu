@@ -1,0 +1,465 @@
+// HDG implicit-stage operators: setup (local inverses, condensed trace matrix) and the
+// per-stage condensation and recovery kernels.
+//
+// Stage system (Sec. 6, eq. linearizedHDGsystem): [[A, B], [C, D]] [Q; Qhat] = [R1; 0] with
+//   A = I - dt a M^{-1} dL/dQ,  B = -dt a M^{-1} dL/dQhat,  C = dFlx/dQ,  D = dFlx/dQhat,
+// L(q, qhat) = (F_L, grad v) + (s, v) - <Fhat_L . n, v> (eq. SemiDiscretizedForm_ode) and
+// the hybridised Lax-Friedrichs flux of eq. linear_hdgflux3,
+//   n . Fhat_L = (n.U + tau (phi - phi_hat), n_x phi_B phi + tau (U - U_hat),
+//                 n_y phi_B phi + tau (V - V_hat)),  tau = max_pm sqrt(phi_B).
+// With collocated GLL faces the conservation condition (eq. HDGcont) holds node by node;
+// this library keeps its rows in pointwise form (divided by the face weight (h/2) w_b), so
+//   C rows at a face node of an element: (n_x U + n_y V + tau phi, n_x phi_B phi + tau U,
+//   n_y phi_B phi + tau V), and D = -tau per side (diagonal).
+// B acts only on boundary volume nodes: B = -beta tau with beta = dt a (2/h) / w_0.
+// Schur complement (eq. linearizedHDGsystem_schur): S = D - C A^{-1} B, rhs -C A^{-1} R1;
+// recovery (eq. recover_volume_unknowns): Q = A^{-1}(R1 - B Qhat).
+#include "internal.h"
+
+namespace hdgdg {
+namespace {
+
+// In-place Gauss-Jordan inversion of the n x n matrix in the left half of the row-major
+// augmented array M[n][2n] (right half must hold I); partial pivoting; whole CTA.
+// On return the right half holds the inverse.  *singular set if a pivot is 0.
+__device__ void gauss_jordan(double* M, int n, int* singular, int* s_piv) {
+    const int ld = 2 * n;
+    for (int k = 0; k < n; ++k) {
+        if (threadIdx.x == 0) {
+            int p = k;
+            double best = fabs(M[k * ld + k]);
+            for (int r = k + 1; r < n; ++r) {
+                const double v = fabs(M[r * ld + k]);
+                if (v > best) { best = v; p = r; }
+            }
+            *s_piv = p;
+            if (best == 0.0) *singular = 1;
+        }
+        __syncthreads();
+        const int p = *s_piv;
+        if (p != k) {
+            for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+                const double t = M[k * ld + c];
+                M[k * ld + c] = M[p * ld + c];
+                M[p * ld + c] = t;
+            }
+            __syncthreads();
+        }
+        const double piv = M[k * ld + k];
+        __syncthreads();
+        const double inv = piv != 0.0 ? 1.0 / piv : 0.0;
+        for (int c = threadIdx.x; c < ld; c += blockDim.x) M[k * ld + c] *= inv;
+        __syncthreads();
+        for (int t = threadIdx.x; t < n * ld; t += blockDim.x) {
+            const int r = t / ld, c = t % ld;
+            if (r == k || c == k) continue;
+            M[r * ld + c] -= M[r * ld + k] * M[k * ld + c];
+        }
+        __syncthreads();
+        for (int r = threadIdx.x; r < n; r += blockDim.x)
+            if (r != k) M[r * ld + k] = 0.0;
+        __syncthreads();
+    }
+}
+
+// One CTA per element.  Builds A_e, inverts it, writes A^{-1} (column major) and the
+// element Schur block S_e = D_e - C_e A^{-1} B_e in local trace order (f, c, b).
+template <int P>
+__global__ void build_local_kernel(Geom g, const double* __restrict__ phiB,
+                                   const double* __restrict__ tau_edge, double dta,
+                                   double* __restrict__ Ainv, double* __restrict__ Se,
+                                   int* singular) {
+    constexpr int Np = P * P, NV = 3 * Np, NT = 12 * P;
+    extern __shared__ double sm[];
+    double* M = sm;                       // [NV][2 NV]
+    double* pb = M + NV * 2 * NV;         // [Np]
+    double* tau = pb + Np;                // [4][P]
+    __shared__ int s_piv;
+    const int e = blockIdx.x;
+    const int ld = 2 * NV;
+
+    for (int n = threadIdx.x; n < Np; n += blockDim.x) pb[n] = phiB[(size_t)e * Np + n];
+    for (int t = threadIdx.x; t < 4 * P; t += blockDim.x)
+        tau[t] = tau_edge[(size_t)edge_of_face(e, t / P, g.N) * P + t % P];
+    for (int t = threadIdx.x; t < NV * ld; t += blockDim.x) {
+        const int r = t / ld, c = t % ld;
+        M[t] = (c == r || c == r + NV) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+
+    // A = I - dta * d(M^{-1} L)/dQ, one row per thread
+    const double th = g.two_over_h;
+    for (int r = threadIdx.x; r < NV; r += blockDim.x) {
+        const int c = r / Np, n = r % Np, i = n % P, j = n / P;
+        double* row = M + r * ld;
+        if (c == 0) {   // phi row: volume term of (U, V) fluxes
+            for (int a = 0; a < P; ++a) {
+                row[1 * Np + j * P + a] -= dta * th * g.Dhat[i * P + a];
+                row[2 * Np + a * P + i] -= dta * th * g.Dhat[j * P + a];
+            }
+        } else if (c == 1) {   // U row: volume term of phi_eta phi_B along x, source phi_eta d_x phi_B
+            double dB = 0.0;
+            for (int a = 0; a < P; ++a) {
+                row[0 * Np + j * P + a] -= dta * th * g.Dhat[i * P + a] * pb[j * P + a];
+                dB += g.D[i * P + a] * pb[j * P + a];
+            }
+            row[0 * Np + n] -= dta * th * dB;
+        } else {   // V row
+            double dB = 0.0;
+            for (int a = 0; a < P; ++a) {
+                row[0 * Np + a * P + i] -= dta * th * g.Dhat[j * P + a] * pb[a * P + i];
+                dB += g.D[j * P + a] * pb[a * P + i];
+            }
+            row[0 * Np + n] -= dta * th * dB;
+        }
+        // faces through the node: -(2/h)/w0 * d(Fhat.n)/dQ, with the minus sign of -<.,.>
+        const double lift = th * g.inv_w0;
+        for (int f = 0; f < 4; ++f) {
+            const bool on = (f == 0 && i == 0) || (f == 1 && i == P - 1) || (f == 2 && j == 0) ||
+                            (f == 3 && j == P - 1);
+            if (!on) continue;
+            const int b = (f < 2) ? j : i;
+            const double t = tau[f * P + b];
+            const double nx = f == 0 ? -1.0 : f == 1 ? 1.0 : 0.0;
+            const double ny = f == 2 ? -1.0 : f == 3 ? 1.0 : 0.0;
+            // M^{-1} L contains -lift * (Fhat . n); A = I - dta M^{-1} dL/dQ adds +dta*lift*d(Fhat.n)/dQ
+            const double k = dta * lift;
+            if (c == 0) {
+                row[1 * Np + n] += k * nx;
+                row[2 * Np + n] += k * ny;
+                row[0 * Np + n] += k * t;
+            } else if (c == 1) {
+                row[0 * Np + n] += k * nx * pb[n];
+                row[1 * Np + n] += k * t;
+            } else {
+                row[0 * Np + n] += k * ny * pb[n];
+                row[2 * Np + n] += k * t;
+            }
+        }
+    }
+    __syncthreads();
+    gauss_jordan(M, NV, singular, &s_piv);
+
+    // A^{-1}[r][s] = M[r][NV + s]; store column major
+    double* Ae = Ainv + (size_t)e * NV * NV;
+    for (int t = threadIdx.x; t < NV * NV; t += blockDim.x) {
+        const int s = t / NV, r = t % NV;
+        Ae[t] = M[r * ld + NV + s];
+    }
+
+    // S_e[(f1,c1,b1)][(f2,c2,b2)] = -tau1 delta + beta tau2 (C-row combination of A^{-1})
+    const double beta = dta * th * g.inv_w0;
+    double* S = Se + (size_t)e * NT * NT;
+    for (int t = threadIdx.x; t < NT * NT; t += blockDim.x) {
+        const int rr = t / NT, cc = t % NT;
+        const int f1 = rr / (3 * P), c1 = (rr / P) % 3, b1 = rr % P;
+        const int f2 = cc / (3 * P), c2 = (cc / P) % 3, b2 = cc % P;
+        const int n1 = face_node(f1, b1, P), n2 = face_node(f2, b2, P);
+        const double t1 = tau[f1 * P + b1], t2 = tau[f2 * P + b2];
+        const double nx = f1 == 0 ? -1.0 : f1 == 1 ? 1.0 : 0.0;
+        const double ny = f1 == 2 ? -1.0 : f1 == 3 ? 1.0 : 0.0;
+        const int col = NV + c2 * Np + n2;
+        const double aph = M[(0 * Np + n1) * ld + col];
+        const double aU = M[(1 * Np + n1) * ld + col];
+        const double aV = M[(2 * Np + n1) * ld + col];
+        double cz;
+        if (c1 == 0) cz = nx * aU + ny * aV + t1 * aph;
+        else if (c1 == 1) cz = nx * pb[n1] * aph + t1 * aU;
+        else cz = ny * pb[n1] * aph + t1 * aV;
+        double v = beta * t2 * cz;
+        if (rr == cc) v -= t1;
+        S[t] = v;
+    }
+}
+
+// One CTA per edge: gathers the 7 blocks of its row of S from the two elements' S_e.
+// S7 layout [edge][slot][row ii][col jj] (row major), slot 0 = diagonal block.
+template <int P>
+__global__ void gather_rows_kernel(Geom g, const double* __restrict__ Se, double* __restrict__ S7,
+                                   double* __restrict__ Srr, int* __restrict__ Scol) {
+    constexpr int NF = 3 * P, NT = 12 * P;
+    const int r = blockIdx.x;
+    int em, fm, ep, fp;
+    edge_sides(r, g.N, &em, &fm, &ep, &fp);
+    const double* Sm = Se + (size_t)em * NT * NT;
+    const double* Sp = Se + (size_t)ep * NT * NT;
+    double* row = S7 + (size_t)r * 7 * NF * NF;
+    for (int t = threadIdx.x; t < 7 * NF * NF; t += blockDim.x) {
+        const int slot = t / (NF * NF), ii = (t / NF) % NF, jj = t % NF;
+        double v;
+        if (slot == 0) {
+            v = Sm[(fm * NF + ii) * NT + fm * NF + jj] + Sp[(fp * NF + ii) * NT + fp * NF + jj];
+        } else {
+            const int side = (slot - 1) / 3, k = (slot - 1) % 3;
+            const int fs = side == 0 ? fm : fp;
+            const int fo = k < fs ? k : k + 1;        // k-th face other than fs, ascending
+            const double* Sx = side == 0 ? Sm : Sp;
+            v = Sx[(fs * NF + ii) * NT + fo * NF + jj];
+        }
+        row[t] = v;
+        if (slot == 0) Srr[(size_t)r * NF * NF + jj * NF + ii] = v;   // column major copy
+    }
+    if (threadIdx.x < 6) {
+        const int slot = threadIdx.x + 1;
+        const int side = (slot - 1) / 3, k = (slot - 1) % 3;
+        const int fs = side == 0 ? fm : fp;
+        const int fo = k < fs ? k : k + 1;
+        Scol[(size_t)r * 6 + threadIdx.x] = edge_of_face(side == 0 ? em : ep, fo, g.N);
+    }
+}
+
+// One CTA per edge: M^{-1} = S_rr^{-1}, stored column major.
+template <int P>
+__global__ void invert_diag_kernel(const double* __restrict__ S7, double* __restrict__ Minv,
+                                   int* singular) {
+    constexpr int NF = 3 * P;
+    __shared__ double M[NF * 2 * NF];
+    __shared__ int s_piv;
+    const int r = blockIdx.x;
+    const double* blk = S7 + (size_t)r * 7 * NF * NF;
+    for (int t = threadIdx.x; t < NF * 2 * NF; t += blockDim.x) {
+        const int ii = t / (2 * NF), c = t % (2 * NF);
+        M[t] = c < NF ? blk[ii * NF + c] : (c - NF == ii ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    gauss_jordan(M, NF, singular, &s_piv);
+    for (int t = threadIdx.x; t < NF * NF; t += blockDim.x) {
+        const int jj = t / NF, ii = t % NF;
+        Minv[(size_t)r * NF * NF + t] = M[ii * 2 * NF + NF + jj];
+    }
+}
+
+// S~[r][slot] = S[r][slot] M^{-1}_{col}, slots 1..6, stored [edge][slot-1][col jj][row ii].
+template <int P>
+__global__ void precondition_kernel(int n_edges, const double* __restrict__ S7,
+                                    const double* __restrict__ Minv, const int* __restrict__ Scol,
+                                    double* __restrict__ Stil) {
+    constexpr int NF = 3 * P;
+    const int r = blockIdx.x;
+    for (int t = threadIdx.x; t < 6 * NF * NF; t += blockDim.x) {
+        const int sl = t / (NF * NF), jj = (t / NF) % NF, ii = t % NF;
+        const double* S = S7 + ((size_t)r * 7 + sl + 1) * NF * NF;           // row major
+        const double* Mi = Minv + (size_t)Scol[(size_t)r * 6 + sl] * NF * NF;  // column major
+        double acc = 0.0;
+        for (int k = 0; k < NF; ++k) acc += S[ii * NF + k] * Mi[jj * NF + k];
+        Stil[((size_t)r * 6 + sl) * NF * NF + jj * NF + ii] = acc;
+    }
+}
+
+// Z = A^{-1} R1: one thread per (element, row); R1 staged in shared memory.
+template <int P>
+__global__ void apply_ainv_kernel(Geom g, const double* __restrict__ Ainv, const double* __restrict__ R1,
+                                  double* __restrict__ Z) {
+    constexpr int Np = P * P, NV = 3 * Np;
+    constexpr int EPB = (256 / NV) > 0 ? 256 / NV : 1;
+    __shared__ double sx[EPB][NV];
+    const int le = threadIdx.x / NV, r = threadIdx.x % NV;
+    const int e = blockIdx.x * EPB + le;
+    const size_t fs = (size_t)g.n_el * Np;
+    const bool live = e < g.n_el && le < EPB;
+    if (live) sx[le][r] = R1[(r / Np) * fs + (size_t)e * Np + r % Np];
+    __syncthreads();
+    if (!live) return;
+    const double* A = Ainv + (size_t)e * NV * NV;
+    double acc = 0.0;
+#pragma unroll 8
+    for (int s = 0; s < NV; ++s) acc += A[s * NV + r] * sx[le][s];
+    Z[(r / Np) * fs + (size_t)e * Np + r % Np] = acc;
+}
+
+// g = -C Z at every trace node: one thread per (edge, b).
+template <int P>
+__global__ void edge_rhs_kernel(Geom g, const double* __restrict__ Z, const double* __restrict__ phiB,
+                                const double* __restrict__ tau_edge, double* __restrict__ gvec) {
+    constexpr int Np = P * P, NF = 3 * P;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.n_edges * P) return;
+    const int r = t / P, b = t % P;
+    int em, fm, ep, fp;
+    edge_sides(r, g.N, &em, &fm, &ep, &fp);
+    const size_t fs = (size_t)g.n_el * Np;
+    const double tau = tau_edge[(size_t)r * P + b];
+    const bool xedge = fm == 1;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int side = 0; side < 2; ++side) {
+        const int e = side == 0 ? em : ep;
+        const int f = side == 0 ? fm : fp;
+        const size_t o = (size_t)e * Np + face_node(f, b, P);
+        const double zph = Z[o], zU = Z[fs + o], zV = Z[2 * fs + o], pb = phiB[o];
+        const double sgn = side == 0 ? 1.0 : -1.0;
+        const double nx = xedge ? sgn : 0.0, ny = xedge ? 0.0 : sgn;
+        acc[0] += nx * zU + ny * zV + tau * zph;
+        acc[1] += nx * pb * zph + tau * zU;
+        acc[2] += ny * pb * zph + tau * zV;
+    }
+    double* out = gvec + (size_t)r * NF;
+    out[0 * P + b] = -acc[0];
+    out[1 * P + b] = -acc[1];
+    out[2 * P + b] = -acc[2];
+}
+
+// Q = Z + beta A^{-1}_{:, boundary} (tau qhat);  Lst = (Q - R1) * inv_aii.
+template <int P>
+__global__ void recover_kernel(Geom g, const double* __restrict__ Ainv, const double* __restrict__ Z,
+                               const double* __restrict__ R1, const double* __restrict__ tau_edge,
+                               const double* __restrict__ qhat, double beta, double inv_aii,
+                               double* __restrict__ Q, double* __restrict__ Lst) {
+    constexpr int Np = P * P, NV = 3 * Np, NF = 3 * P;
+    constexpr int EPB = (256 / NV) > 0 ? 256 / NV : 1;
+    __shared__ double su[EPB][NV];
+    const int le = threadIdx.x / NV, r = threadIdx.x % NV;
+    const int e = blockIdx.x * EPB + le;
+    const size_t fs = (size_t)g.n_el * Np;
+    const bool live = e < g.n_el && le < EPB;
+    if (live) {
+        const int c = r / Np, n = r % Np, i = n % P, j = n / P;
+        double u = 0.0;
+        for (int f = 0; f < 4; ++f) {
+            const bool on = (f == 0 && i == 0) || (f == 1 && i == P - 1) || (f == 2 && j == 0) ||
+                            (f == 3 && j == P - 1);
+            if (!on) continue;
+            const int b = (f < 2) ? j : i;
+            const int ed = edge_of_face(e, f, g.N);
+            u += tau_edge[(size_t)ed * P + b] * qhat[(size_t)ed * NF + c * P + b];
+        }
+        su[le][r] = u;
+    }
+    __syncthreads();
+    if (!live) return;
+    const double* A = Ainv + (size_t)e * NV * NV;
+    double acc = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        for (int n = 0; n < Np; ++n) {
+            const int i = n % P, j = n / P;
+            if (i != 0 && i != P - 1 && j != 0 && j != P - 1) continue;
+            const int s = c * Np + n;
+            acc += A[s * NV + r] * su[le][s];
+        }
+    }
+    const size_t o = (r / Np) * fs + (size_t)e * Np + r % Np;
+    const double q = Z[o] + beta * acc;
+    Q[o] = q;
+    Lst[o] = (q - R1[o]) * inv_aii;
+}
+
+template <int P>
+cudaError_t build_local_launch(const Geom& g, const double* phiB, const double* tau_edge, double dta,
+                               double* Ainv, double* Se, int* singular, cudaStream_t s) {
+    constexpr int NV = 3 * P * P;
+    const size_t smem = (size_t)(NV * 2 * NV + P * P + 4 * P) * sizeof(double);
+    cudaError_t err = cudaFuncSetAttribute(build_local_kernel<P>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    build_local_kernel<P><<<g.n_el, 128, smem, s>>>(g, phiB, tau_edge, dta, Ainv, Se, singular);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t assemble_launch(const Geom& g, const double* Se, double* S7, double* Srr, double* Minv,
+                            double* Stil, int* Scol, int* singular, cudaStream_t s) {
+    gather_rows_kernel<P><<<g.n_edges, 128, 0, s>>>(g, Se, S7, Srr, Scol);
+    count_launches(1);
+    invert_diag_kernel<P><<<g.n_edges, 64, 0, s>>>(S7, Minv, singular);
+    count_launches(1);
+    precondition_kernel<P><<<g.n_edges, 128, 0, s>>>(g.n_edges, S7, Minv, Scol, Stil);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t condense_launch(const Geom& g, const double* Ainv, const double* R1, const double* phiB,
+                            const double* tau_edge, double* Z, double* gvec, cudaStream_t s) {
+    constexpr int NV = 3 * P * P;
+    constexpr int EPB = (256 / NV) > 0 ? 256 / NV : 1;
+    apply_ainv_kernel<P><<<(g.n_el + EPB - 1) / EPB, EPB * NV, 0, s>>>(g, Ainv, R1, Z);
+    count_launches(1);
+    const int n = g.n_edges * P;
+    edge_rhs_kernel<P><<<(n + 255) / 256, 256, 0, s>>>(g, Z, phiB, tau_edge, gvec);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t recover_launch(const Geom& g, const double* Ainv, const double* Z, const double* R1,
+                           const double* tau_edge, const double* qhat, double beta, double inv_aii,
+                           double* Q, double* Lst, cudaStream_t s) {
+    constexpr int NV = 3 * P * P;
+    constexpr int EPB = (256 / NV) > 0 ? 256 / NV : 1;
+    recover_kernel<P><<<(g.n_el + EPB - 1) / EPB, EPB * NV, 0, s>>>(g, Ainv, Z, R1, tau_edge, qhat,
+                                                                    beta, inv_aii, Q, Lst);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+#define HDGDG_DISPATCH_P(CALL)                 \
+    switch (g.P) {                             \
+        case 2: return CALL<2>;                \
+        case 3: return CALL<3>;                \
+        case 4: return CALL<4>;                \
+        case 5: return CALL<5>;                \
+        case 6: return CALL<6>;                \
+        default: return cudaErrorInvalidValue; \
+    }
+
+cudaError_t launch_build_local(const Geom& g, const double* phiB, const double* tau_edge, double dta,
+                               double* Ainv, double* Se, int* singular, cudaStream_t s) {
+#define CALL(P) build_local_launch<P>(g, phiB, tau_edge, dta, Ainv, Se, singular, s)
+    switch (g.P) {
+        case 2: return CALL(2);
+        case 3: return CALL(3);
+        case 4: return CALL(4);
+        case 5: return CALL(5);
+        case 6: return CALL(6);
+        default: return cudaErrorInvalidValue;
+    }
+#undef CALL
+}
+
+cudaError_t launch_assemble_trace(const Geom& g, const double* Se, double* S7, double* Srr,
+                                  double* Minv, double* Stil, int* Scol, int* singular,
+                                  cudaStream_t s) {
+#define CALL(P) assemble_launch<P>(g, Se, S7, Srr, Minv, Stil, Scol, singular, s)
+    switch (g.P) {
+        case 2: return CALL(2);
+        case 3: return CALL(3);
+        case 4: return CALL(4);
+        case 5: return CALL(5);
+        case 6: return CALL(6);
+        default: return cudaErrorInvalidValue;
+    }
+#undef CALL
+}
+
+cudaError_t launch_condense(const Geom& g, const double* Ainv, const double* R1, const double* phiB,
+                            const double* tau_edge, double* Z, double* gvec, cudaStream_t s) {
+#define CALL(P) condense_launch<P>(g, Ainv, R1, phiB, tau_edge, Z, gvec, s)
+    switch (g.P) {
+        case 2: return CALL(2);
+        case 3: return CALL(3);
+        case 4: return CALL(4);
+        case 5: return CALL(5);
+        case 6: return CALL(6);
+        default: return cudaErrorInvalidValue;
+    }
+#undef CALL
+}
+
+cudaError_t launch_recover(const Geom& g, const double* Ainv, const double* Z, const double* R1,
+                           const double* tau_edge, const double* qhat, double beta, double inv_aii,
+                           double* Q, double* Lst, cudaStream_t s) {
+#define CALL(P) recover_launch<P>(g, Ainv, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s)
+    switch (g.P) {
+        case 2: return CALL(2);
+        case 3: return CALL(3);
+        case 4: return CALL(4);
+        case 5: return CALL(5);
+        case 6: return CALL(6);
+        default: return cudaErrorInvalidValue;
+    }
+#undef CALL
+}
+
+}  // namespace hdgdg

@@ -1,0 +1,202 @@
+// Krylov kernel set for the condensed trace system (Sec. 6, eq. linearizedHDGsystem_schur).
+//
+// The paper factorises the trace matrix once with a sparse direct LU; here the system is
+// solved by right-preconditioned GMRES(m) with classical Gram-Schmidt applied twice.  The
+// block-Jacobi preconditioner (inverse of each edge's diagonal n_f x n_f block) is folded
+// into the stored matrix once at setup, S~ = S M^{-1}, so the diagonal blocks of S~ are the
+// identity and are not stored.  All reductions use a fixed grid and a fixed summation
+// order, so results are bitwise reproducible run to run.
+#include "internal.h"
+
+namespace hdgdg {
+namespace {
+
+constexpr int kDotBlocks = 608;    // 4 x 152 SMs
+constexpr int kDotThreads = 256;
+constexpr int kDotChunk = 8;       // vectors reduced per pass over w
+
+// y[r][ii] = x[r][ii] + sum_{slot, jj} S~[r][slot][jj][ii] x[col(r,slot)][jj]
+template <int NF>
+__global__ void __launch_bounds__(256)
+spmv_pre_kernel(int n_edges, const double* __restrict__ Stil, const int* __restrict__ Scol,
+                const double* __restrict__ x, double* __restrict__ y) {
+    constexpr int EPB = 256 / NF;
+    const int le = threadIdx.x / NF, ii = threadIdx.x % NF;
+    const int r = blockIdx.x * EPB + le;
+    if (le >= EPB || r >= n_edges) return;
+    const double* S = Stil + (size_t)r * 6 * NF * NF;
+    double acc = x[(size_t)r * NF + ii];
+#pragma unroll
+    for (int sl = 0; sl < 6; ++sl) {
+        const double* xc = x + (size_t)__ldg(Scol + (size_t)r * 6 + sl) * NF;
+        const double* Sb = S + sl * NF * NF;
+#pragma unroll
+        for (int jj = 0; jj < NF; ++jj) acc += Sb[jj * NF + ii] * xc[jj];
+    }
+    y[(size_t)r * NF + ii] = acc;
+}
+
+// y[r] = B_r x[r] for column-major NF x NF blocks
+template <int NF>
+__global__ void __launch_bounds__(256)
+block_diag_kernel(int n_edges, const double* __restrict__ Bd, const double* __restrict__ x,
+                  double* __restrict__ y) {
+    constexpr int EPB = 256 / NF;
+    const int le = threadIdx.x / NF, ii = threadIdx.x % NF;
+    const int r = blockIdx.x * EPB + le;
+    if (le >= EPB || r >= n_edges) return;
+    const double* B = Bd + (size_t)r * NF * NF;
+    const double* xr = x + (size_t)r * NF;
+    double acc = 0.0;
+#pragma unroll
+    for (int jj = 0; jj < NF; ++jj) acc += B[jj * NF + ii] * xr[jj];
+    y[(size_t)r * NF + ii] = acc;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// partial[blk][j] = sum over this block's slice of V_j . w, for j in [j0, j0 + nj)
+template <int CH>
+__global__ void __launch_bounds__(kDotThreads)
+multidot_partial_kernel(const double* __restrict__ V, size_t ldv, int j0, int nj,
+                        const double* __restrict__ w, size_t n, double* __restrict__ partial,
+                        int ldp) {
+    __shared__ double sh[CH][kDotThreads / 32];
+    double acc[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) acc[c] = 0.0;
+    for (size_t idx = blockIdx.x * (size_t)kDotThreads + threadIdx.x; idx < n;
+         idx += (size_t)gridDim.x * kDotThreads) {
+        const double wv = w[idx];
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+            if (c < nj) acc[c] += V[(size_t)(j0 + c) * ldv + idx] * wv;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        const double s = warp_sum(acc[c]);
+        if (lane == 0) sh[c][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < CH && (int)threadIdx.x < nj) {
+        double s = 0.0;
+        for (int k = 0; k < kDotThreads / 32; ++k) s += sh[threadIdx.x][k];
+        partial[(size_t)blockIdx.x * ldp + j0 + threadIdx.x] = s;
+    }
+}
+
+// out[j] = sum_blk partial[blk][j]: one warp per j, fixed order
+__global__ void multidot_final_kernel(const double* __restrict__ partial, int nblk, int ldp, int nj,
+                                      double* __restrict__ out) {
+    const int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (j >= nj) return;
+    double s = 0.0;
+    for (int k = lane; k < nblk; k += 32) s += partial[(size_t)k * ldp + j];
+    s = warp_sum(s);
+    if (lane == 0) out[j] = s;
+}
+
+__global__ void multiaxpy_kernel(const double* __restrict__ V, size_t ldv, int nv,
+                                 const double* __restrict__ coef, double sign, double* __restrict__ w,
+                                 size_t n) {
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        double acc = w[idx];
+        for (int j = 0; j < nv; ++j) acc -= sign * coef[j] * V[(size_t)j * ldv + idx];
+        w[idx] = acc;
+    }
+}
+
+__global__ void scale_kernel(const double* __restrict__ w, const double* __restrict__ nrm2,
+                             double* __restrict__ v, size_t n) {
+    const double s = 1.0 / sqrt(*nrm2);
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (size_t)gridDim.x * blockDim.x)
+        v[idx] = w[idx] * s;
+}
+
+int stream_grid(size_t n) {
+    size_t b = (n + 255) / 256;
+    if (b > 152 * 8) b = 152 * 8;
+    return b > 0 ? (int)b : 1;
+}
+
+template <int NF>
+cudaError_t spmv_launch(int n_edges, const double* Stil, const int* Scol, const double* x, double* y,
+                        cudaStream_t s) {
+    constexpr int EPB = 256 / NF;
+    spmv_pre_kernel<NF><<<(n_edges + EPB - 1) / EPB, EPB * NF, 0, s>>>(n_edges, Stil, Scol, x, y);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <int NF>
+cudaError_t block_diag_launch(int n_edges, const double* Bd, const double* x, double* y, cudaStream_t s) {
+    constexpr int EPB = 256 / NF;
+    block_diag_kernel<NF><<<(n_edges + EPB - 1) / EPB, EPB * NF, 0, s>>>(n_edges, Bd, x, y);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_spmv_pre(const Geom& g, const double* Stil, const int* Scol, const double* x,
+                            double* y, cudaStream_t s) {
+    switch (g.P) {
+        case 2: return spmv_launch<6>(g.n_edges, Stil, Scol, x, y, s);
+        case 3: return spmv_launch<9>(g.n_edges, Stil, Scol, x, y, s);
+        case 4: return spmv_launch<12>(g.n_edges, Stil, Scol, x, y, s);
+        case 5: return spmv_launch<15>(g.n_edges, Stil, Scol, x, y, s);
+        case 6: return spmv_launch<18>(g.n_edges, Stil, Scol, x, y, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_block_diag(const Geom& g, const double* Bd, const double* x, double* y,
+                              cudaStream_t s) {
+    switch (g.P) {
+        case 2: return block_diag_launch<6>(g.n_edges, Bd, x, y, s);
+        case 3: return block_diag_launch<9>(g.n_edges, Bd, x, y, s);
+        case 4: return block_diag_launch<12>(g.n_edges, Bd, x, y, s);
+        case 5: return block_diag_launch<15>(g.n_edges, Bd, x, y, s);
+        case 6: return block_diag_launch<18>(g.n_edges, Bd, x, y, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t dot_scratch_doubles(int nv) { return (size_t)kDotBlocks * (size_t)nv; }
+
+cudaError_t launch_multidot(const double* V, size_t ldv, int nv, const double* w, size_t n,
+                            double* scratch, double* out, cudaStream_t s) {
+    for (int j0 = 0; j0 < nv; j0 += kDotChunk) {
+        const int nj = nv - j0 < kDotChunk ? nv - j0 : kDotChunk;
+        multidot_partial_kernel<kDotChunk><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, j0, nj, w, n,
+                                                                               scratch, nv);
+        count_launches(1);
+    }
+    multidot_final_kernel<<<(nv + 7) / 8, 256, 0, s>>>(scratch, kDotBlocks, nv, nv, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_multiaxpy(const double* V, size_t ldv, int nv, const double* coef, double sign,
+                             double* w, size_t n, cudaStream_t s) {
+    multiaxpy_kernel<<<stream_grid(n), 256, 0, s>>>(V, ldv, nv, coef, sign, w, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_by_rnorm(const double* w, const double* nrm2, double* v, size_t n,
+                                  cudaStream_t s) {
+    scale_kernel<<<stream_grid(n), 256, 0, s>>>(w, nrm2, v, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace hdgdg

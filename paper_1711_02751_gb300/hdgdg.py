@@ -1,0 +1,231 @@
+"""Python binding of libhdgdg (ctypes): argument marshalling only, same names as the C ABI.
+
+Every step of the hot path runs in the CUDA library; there is no Python or CPU fallback.
+If the shared library is missing this module raises at first use.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhdgdg.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ENONFINITE, ESTATE = range(7)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTCONVERGED", "ENONFINITE", "ESTATE"]
+SCHEMES = {"ars2": 0, "ars3": 1}
+
+EXPORTS = ["hdgdg_bytes_required", "hdgdg_node_coords", "hdgdg_create", "hdgdg_set_state",
+           "hdgdg_step", "hdgdg_get_state", "hdgdg_get_stats", "hdgdg_last_error", "hdgdg_destroy",
+           "hdgdg_eval_nl", "hdgdg_condense_rhs", "hdgdg_trace_apply", "hdgdg_stage_solve",
+           "hdgdg_measure_fp64_tflops", "hdgdg_set_kernel_timing", "hdgdg_kernel_time"]
+KERNEL_CLASSES = ["spmv", "ortho", "condense", "recover", "dg", "combine"]
+
+
+class HdgdgError(RuntimeError):
+    def __init__(self, status, message):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"hdgdg {name}: {message}")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("n_side", ctypes.c_int), ("degree_k", ctypes.c_int), ("g", ctypes.c_double),
+                ("H0", ctypes.c_double), ("scheme", ctypes.c_int), ("dt", ctypes.c_double),
+                ("precision", ctypes.c_int), ("krylov_rtol", ctypes.c_double),
+                ("krylov_restart", ctypes.c_int), ("krylov_maxit", ctypes.c_int),
+                ("linear_only", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_longlong), ("krylov_iterations", ctypes.c_longlong),
+                ("last_krylov_iterations", ctypes.c_int), ("last_rel_residual", ctypes.c_double),
+                ("mass", ctypes.c_double), ("kernel_launches", ctypes.c_longlong)]
+
+
+_lib = None
+_P = ctypes.POINTER(ctypes.c_double)
+
+
+def lib():
+    """Load libhdgdg.so (built in-tree by ``paper_1711_02751_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1711_02751_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        L.hdgdg_bytes_required.restype = ctypes.c_size_t
+        L.hdgdg_bytes_required.argtypes = [ctypes.POINTER(Config)]
+        L.hdgdg_node_coords.argtypes = [ctypes.POINTER(Config), _P, _P]
+        L.hdgdg_create.argtypes = [ctypes.POINTER(Config), _P, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+        L.hdgdg_set_state.argtypes = [ctypes.c_void_p, _P, _P, _P]
+        L.hdgdg_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.hdgdg_get_state.argtypes = [ctypes.c_void_p, _P, _P, _P]
+        L.hdgdg_get_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(Stats)]
+        L.hdgdg_last_error.restype = ctypes.c_char_p
+        L.hdgdg_last_error.argtypes = [ctypes.c_void_p]
+        L.hdgdg_destroy.restype = None
+        L.hdgdg_destroy.argtypes = [ctypes.c_void_p]
+        L.hdgdg_eval_nl.argtypes = [ctypes.c_void_p, _P, _P]
+        L.hdgdg_condense_rhs.argtypes = [ctypes.c_void_p, _P, _P]
+        L.hdgdg_trace_apply.argtypes = [ctypes.c_void_p, _P, _P]
+        L.hdgdg_stage_solve.argtypes = [ctypes.c_void_p, _P, _P, _P, ctypes.POINTER(ctypes.c_int)]
+        L.hdgdg_measure_fp64_tflops.argtypes = [_P]
+        L.hdgdg_set_kernel_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.hdgdg_kernel_time.argtypes = [ctypes.c_void_p, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_longlong)]
+        for name in EXPORTS:
+            getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_P)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.size != int(np.prod(shape)):
+        raise ValueError(f"expected {int(np.prod(shape))} values, got {a.size}")
+    return a
+
+
+def make_config(N, k, dt, g=1.0, H0=1.0, scheme="ars2", krylov_rtol=0.0, krylov_restart=0,
+                krylov_maxit=0, linear_only=False):
+    return Config(int(N), int(k), float(g), float(H0), SCHEMES[scheme], float(dt), 0,
+                  float(krylov_rtol), int(krylov_restart), int(krylov_maxit), int(bool(linear_only)))
+
+
+def bytes_required(cfg):
+    return int(lib().hdgdg_bytes_required(ctypes.byref(cfg)))
+
+
+def node_coords(N, k):
+    """GLL node coordinates (x, y), each [N*N, (k+1)^2], from the library's own tables."""
+    cfg = make_config(N, k, 1.0)
+    x = np.empty((N * N, (k + 1) ** 2))
+    y = np.empty_like(x)
+    st = lib().hdgdg_node_coords(ctypes.byref(cfg), _ptr(x), _ptr(y))
+    if st != OK:
+        raise HdgdgError(st, "node_coords")
+    return x, y
+
+
+def measure_fp64_tflops():
+    out = ctypes.c_double(0.0)
+    st = lib().hdgdg_measure_fp64_tflops(ctypes.byref(out))
+    if st != OK:
+        raise HdgdgError(st, "measure_fp64_tflops")
+    return out.value
+
+
+class Sim:
+    """One simulation handle (hdgdg_create ... hdgdg_destroy)."""
+
+    def __init__(self, N, k, dt, bottom=None, g=1.0, H0=1.0, scheme="ars2", stream=None,
+                 krylov_rtol=0.0, krylov_restart=0, krylov_maxit=0, linear_only=False):
+        self.N, self.k, self.P = int(N), int(k), int(k) + 1
+        self.n_el, self.Np = self.N * self.N, self.P * self.P
+        self.n_edges = 2 * self.n_el
+        self.cfg = make_config(N, k, dt, g, H0, scheme, krylov_rtol, krylov_restart, krylov_maxit,
+                               linear_only)
+        self._h = ctypes.c_void_p(None)
+        b = None if bottom is None else _f64(bottom, (self.n_el, self.Np))
+        st = lib().hdgdg_create(ctypes.byref(self.cfg), None if b is None else _ptr(b),
+                                ctypes.c_void_p(stream) if stream else None, ctypes.byref(self._h))
+        if st != OK:
+            msg = self.last_error() if self._h else "create"
+            self.close()
+            raise HdgdgError(st, msg)
+
+    # -- lifecycle --------------------------------------------------------------------
+    def close(self):
+        if self._h:
+            lib().hdgdg_destroy(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def last_error(self):
+        return lib().hdgdg_last_error(self._h).decode()
+
+    def _check(self, st):
+        if st != OK:
+            raise HdgdgError(st, self.last_error())
+
+    # -- state ------------------------------------------------------------------------
+    def set_state(self, h, hu, hv):
+        sh = (self.n_el, self.Np)
+        h, hu, hv = _f64(h, sh), _f64(hu, sh), _f64(hv, sh)
+        self._check(lib().hdgdg_set_state(self._h, _ptr(h), _ptr(hu), _ptr(hv)))
+
+    def set_state_ptrs(self, h_ptr, hu_ptr, hv_ptr):
+        """set_state from raw host addresses (e.g. pinned buffers); sizes as in set_state."""
+        self._check(lib().hdgdg_set_state(self._h, ctypes.cast(h_ptr, _P), ctypes.cast(hu_ptr, _P),
+                                          ctypes.cast(hv_ptr, _P)))
+
+    def step(self, n_steps=1):
+        self._check(lib().hdgdg_step(self._h, int(n_steps)))
+
+    def get_state(self):
+        out = [np.empty((self.n_el, self.Np)) for _ in range(3)]
+        self._check(lib().hdgdg_get_state(self._h, *[_ptr(a) for a in out]))
+        return tuple(out)
+
+    def get_state_ptrs(self, h_ptr, hu_ptr, hv_ptr):
+        self._check(lib().hdgdg_get_state(self._h, ctypes.cast(h_ptr, _P), ctypes.cast(hu_ptr, _P),
+                                          ctypes.cast(hv_ptr, _P)))
+
+    def stats(self):
+        s = Stats()
+        self._check(lib().hdgdg_get_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def set_kernel_timing(self, on=True):
+        self._check(lib().hdgdg_set_kernel_timing(self._h, int(bool(on))))
+
+    def kernel_times(self):
+        """{class: (total_ms, launch groups)} of the per-kernel-class timers."""
+        out = {}
+        for c, name in enumerate(KERNEL_CLASSES):
+            ms, n = ctypes.c_double(0.0), ctypes.c_longlong(0)
+            self._check(lib().hdgdg_kernel_time(self._h, c, ctypes.byref(ms), ctypes.byref(n)))
+            out[name] = (ms.value, n.value)
+        return out
+
+    # -- row-level entry points --------------------------------------------------------
+    def eval_nl(self, q):
+        q = _f64(q, (3, self.n_el, self.Np))
+        out = np.empty((3, self.n_el, self.Np))
+        self._check(lib().hdgdg_eval_nl(self._h, _ptr(q), _ptr(out)))
+        return out
+
+    def condense_rhs(self, R1):
+        R1 = _f64(R1, (3, self.n_el, self.Np))
+        out = np.empty((self.n_edges, 3, self.P))
+        self._check(lib().hdgdg_condense_rhs(self._h, _ptr(R1), _ptr(out)))
+        return out
+
+    def trace_apply(self, x):
+        x = _f64(x, (self.n_edges, 3, self.P))
+        out = np.empty((self.n_edges, 3, self.P))
+        self._check(lib().hdgdg_trace_apply(self._h, _ptr(x), _ptr(out)))
+        return out
+
+    def stage_solve(self, R1):
+        R1 = _f64(R1, (3, self.n_el, self.Np))
+        Q = np.empty((3, self.n_el, self.Np))
+        lam = np.empty((self.n_edges, 3, self.P))
+        its = ctypes.c_int(0)
+        self._check(lib().hdgdg_stage_solve(self._h, _ptr(R1), _ptr(Q), _ptr(lam), ctypes.byref(its)))
+        return Q, lam, its.value

@@ -1,0 +1,226 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, row by row and step by step.
+
+Tolerances: FP64 rounding for the single-kernel rows (1e-12 of the field's max), and the
+relative L2 bounds of the method's FP64 contract for whole steps: <= 1e-11 after one
+step and <= 1e-9 after 100 steps, per field (eta = h - B, hu, hv).
+"""
+import numpy as np
+import pytest
+
+from oracle import hdg, imex, swe
+from paper_1711_02751_gb300 import workloads as W
+
+from _common import dt_of, flat, oracle_state, user_state
+
+pytestmark = pytest.mark.gpu
+
+hd = pytest.importorskip("paper_1711_02751_gb300.hdgdg")
+rng = np.random.Generator(np.random.PCG64(2024))
+
+
+def _sim(m, b, dt, **kw):
+    return hd.Sim(m.N, m.k, dt, bottom=b, g=W.G, H0=W.H0, **kw)
+
+
+def _q_of(m, h, hu, hv, b):
+    q, _ = swe.to_state(h, hu, hv, b, W.G, W.H0)
+    return q
+
+
+def _rel(m, qa, qo):
+    return [imex.rel_l2(m, qa[c], qo[c]) for c in range(3)]
+
+
+# ---- a2 + a3: DG residual of the nonlinear part -------------------------------------------
+@pytest.mark.parametrize("N,k,kind", [(8, 2, "bump8"), (13, 3, "large"), (5, 1, "large"), (7, 4, "large"),
+                                      (4, 5, "large"), (3, 2, "large"), (2, 3, "large")])
+def test_eval_nl_matches_oracle(N, k, kind):
+    m, h, hu, hv, b = user_state(N, k, kind)
+    q, phiB = oracle_state(m, h, hu, hv, b)
+    q = q + 0.003 * rng.standard_normal(q.shape)          # discontinuous across faces
+    ref = flat(swe.minv(m, swe.NL(m, q, phiB)))
+    with _sim(m, b, 0.01) as s:
+        got = s.eval_nl(flat(q))
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-12 * scale
+
+
+# ---- a4: condensation right-hand side --------------------------------------------------------
+@pytest.mark.parametrize("N,k", [(4, 2), (6, 3), (3, 4), (9, 1)])
+def test_condense_rhs_matches_oracle(N, k):
+    m, h, hu, hv, b = user_state(N, k, "large")
+    q, phiB = oracle_state(m, h, hu, hv, b)
+    dt = 0.4 / N
+    st = imex.Stepper(m, phiB, dt, solver="dense")
+    R1 = q + 0.01 * rng.standard_normal(q.shape)
+    ref = st.cond.rhs(R1).reshape(m.n_edges, 3, m.P)
+    ref = ref / (m.face_jac * m.w)[None, None, :]           # library rows are pointwise
+    with _sim(m, b, dt) as s:
+        got = s.condense_rhs(flat(R1))
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+# ---- a5 operator: condensed trace matrix ------------------------------------------------------
+@pytest.mark.parametrize("N,k", [(2, 2), (3, 3), (5, 2), (4, 4)])
+def test_trace_matrix_matches_oracle(N, k):
+    m, h, hu, hv, b = user_state(N, k, "large")
+    q, phiB = oracle_state(m, h, hu, hv, b)
+    dt = 0.4 / N
+    st = imex.Stepper(m, phiB, dt, solver="dense")
+    S = st.cond.S.toarray()
+    W_ = np.tile(m.face_jac * m.w, m.n_edges * 3)
+    x = rng.standard_normal(m.n_edges * 3 * m.P)
+    ref = (S @ x) / W_
+    with _sim(m, b, dt) as s:
+        got = s.trace_apply(x.reshape(m.n_edges, 3, m.P)).ravel()
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+# ---- a4-a6: one implicit stage ----------------------------------------------------------------
+@pytest.mark.parametrize("N,k,dt", [(8, 2, 0.625), (6, 3, 0.05), (11, 3, 0.02), (3, 4, 0.1)])
+def test_stage_solve_matches_oracle(N, k, dt):
+    m, h, hu, hv, b = user_state(N, k, "large" if N != 8 else "bump8")
+    q, phiB = oracle_state(m, h, hu, hv, b)
+    st = imex.Stepper(m, phiB, dt, solver="lu")
+    R1 = q + 0.01 * rng.standard_normal(q.shape)
+    Qo, lo = st.cond.solve(R1)
+    with _sim(m, b, dt) as s:
+        Q, lam, its = s.stage_solve(flat(R1))
+    assert its > 0
+    for c in range(3):
+        assert imex.rel_l2(m, Q[c].reshape(m.x.shape), Qo[c]) <= 1e-11
+    assert np.abs(lam - lo).max() <= 1e-10 * np.abs(lo).max()
+
+
+# ---- whole steps (a1-a8) ------------------------------------------------------------------------
+def _run_pair(N, k, kind, n_steps, scheme="ars2", dt=None, linear_only=False):
+    m, h, hu, hv, b = user_state(N, k, kind)
+    q, phiB = oracle_state(m, h, hu, hv, b)
+    dt = dt if dt is not None else dt_of(m, h, hu, hv)
+    qo = imex.Stepper(m, phiB, dt, scheme=scheme, solver="lu", linear_only=linear_only).run(q, n_steps)
+    with _sim(m, b, dt, scheme=scheme, linear_only=linear_only) as s:
+        s.set_state(h, hu, hv)
+        s.step(n_steps)
+        out = s.get_state()
+        stats = s.stats()
+    return m, _q_of(m, *out, b), qo, stats
+
+
+def test_bump8_one_step():
+    m, qa, qo, _ = _run_pair(8, 2, "bump8", 1)
+    assert max(_rel(m, qa, qo)) <= 1e-11
+
+
+def test_bump8_hundred_steps():
+    """The 8 x 8, k = 2 workload at its advective CFL 0.5 (gravity Courant 10), 100 steps."""
+    m, qa, qo, stats = _run_pair(8, 2, "bump8", 100)
+    assert stats["steps"] == 100
+    assert max(_rel(m, qa, qo)) <= 1e-9
+
+
+@pytest.mark.parametrize("N,k,steps", [(16, 3, 1), (16, 3, 10), (9, 4, 3), (12, 2, 5)])
+def test_variable_bottom_steps(N, k, steps):
+    m, qa, qo, _ = _run_pair(N, k, "large", steps)
+    assert max(_rel(m, qa, qo)) <= (1e-11 if steps == 1 else 1e-10)
+
+
+def test_ars3_steps():
+    m, qa, qo, _ = _run_pair(8, 3, "large", 3, scheme="ars3")
+    assert max(_rel(m, qa, qo)) <= 1e-11
+
+
+def test_linear_only_steps():
+    m, qa, qo, _ = _run_pair(8, 3, "standing", 5, dt=0.02, linear_only=True)
+    assert max(_rel(m, qa, qo)) <= 1e-11
+
+
+def test_mass_conserved_on_gpu():
+    m, h, hu, hv, b = user_state(16, 3, "large")
+    dt = dt_of(m, h, hu, hv)
+    with _sim(m, b, dt) as s:
+        s.set_state(h, hu, hv)
+        m0 = s.stats()["mass"]
+        s.step(5)
+        m1 = s.stats()["mass"]
+    q, _ = oracle_state(m, h, hu, hv, b)
+    assert abs(m0 - imex.mass(m, q)) <= 1e-14 * abs(m0) + 1e-17
+    assert abs(m1 - m0) <= 1e-12 * abs(m0)
+
+
+def test_lake_at_rest_bitwise_on_gpu():
+    m, h, hu, hv, b = user_state(8, 3, "lake")
+    with _sim(m, b, 0.05) as s:
+        s.set_state(h, hu, hv)
+        s.step(3)
+        h1, hu1, hv1 = s.get_state()
+    assert np.array_equal(hu1, np.zeros_like(hu1)) and np.array_equal(hv1, np.zeros_like(hv1))
+    assert np.array_equal(h1, h)
+
+
+def test_runs_are_bitwise_reproducible():
+    m, h, hu, hv, b = user_state(12, 3, "large")
+    dt = dt_of(m, h, hu, hv)
+    outs = []
+    for _ in range(2):
+        with _sim(m, b, dt) as s:
+            s.set_state(h, hu, hv)
+            s.step(3)
+            outs.append(s.get_state())
+    for a, c in zip(*outs):
+        assert np.array_equal(a, c)
+
+
+def test_checkpoint_resume_is_bitwise():
+    m, h, hu, hv, b = user_state(8, 3, "large")
+    dt = dt_of(m, h, hu, hv)
+    with _sim(m, b, dt) as s:
+        s.set_state(h, hu, hv)
+        s.step(4)
+        full = s.get_state()
+    with _sim(m, b, dt) as s:
+        s.set_state(h, hu, hv)
+        s.step(2)
+        mid = s.get_state()
+    with _sim(m, b, dt) as s:
+        s.set_state(*mid)
+        s.step(2)
+        resumed = s.get_state()
+    # the state passes through (h, hu, hv) at the checkpoint, a round trip of g (h - B)
+    for a, c in zip(full, resumed):
+        assert np.abs(a - c).max() <= 1e-14 * max(1.0, np.abs(a).max())
+
+
+# ---- error paths (host-side failures; no GPU fault) -----------------------------------------
+def test_nonfinite_state_is_rejected():
+    m, h, hu, hv, b = user_state(4, 2, "large")
+    with _sim(m, b, 0.05) as s:
+        bad = h.copy()
+        bad[3, 2] = np.nan
+        with pytest.raises(hd.HdgdgError) as ei:
+            s.set_state(bad, hu, hv)
+        assert ei.value.status == hd.ENONFINITE
+        with pytest.raises(hd.HdgdgError) as ei:
+            s.step(1)
+        assert ei.value.status == hd.ESTATE
+
+
+def test_krylov_cap_surfaces_as_status_and_keeps_state():
+    m, h, hu, hv, b = user_state(8, 3, "large")
+    with _sim(m, b, 0.05, krylov_maxit=1) as s:
+        s.set_state(h, hu, hv)
+        with pytest.raises(hd.HdgdgError) as ei:
+            s.step(1)
+        assert ei.value.status == hd.ENOTCONVERGED
+        st = s.stats()
+        assert st["steps"] == 0 and st["last_krylov_iterations"] == 1
+        h1, hu1, hv1 = s.get_state()
+    assert np.abs(h1 - h).max() <= 1e-15 and np.abs(hu1 - hu).max() <= 1e-17
+
+
+def test_bad_config_is_rejected():
+    with pytest.raises(hd.HdgdgError) as ei:
+        hd.Sim(1, 2, 0.1)
+    assert ei.value.status == hd.EINVAL
+    x = np.zeros((16, 9))
+    with pytest.raises(hd.HdgdgError):
+        hd.Sim(4, 2, 0.1, bottom=x + 2.0)       # H0 - b <= 0
