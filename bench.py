@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DOF-steps/s of IMEX HDG-DG at rel L2≤1e-6 vs FP64 form; p50/p99 latency"
 UNIT = "DOF-steps/s"
-WORKLOADS = {"large512": (512, 3), "bump8": (8, 2)}
+WORKLOADS = {"large512": (512, 3), "bump8": (8, 2), "mid128": (128, 3)}
 CPU_SAMPLE = (64, 3)       # oracle sample: the large512 recipe on 64 x 64, k = 3
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -42,6 +42,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="large512", choices=sorted(WORKLOADS))
+    ap.add_argument("--restart", type=int, default=0, help="GMRES restart length (0: library default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
@@ -251,7 +252,7 @@ def main():
     dt = W.advective_dt(x, h, hu, hv, N)
     stream = torch.cuda.Stream()          # a real stream: the legacy default stream has handle 0
     torch.cuda.set_stream(stream)
-    sim = hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, stream=stream.cuda_stream)
+    sim = hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, stream=stream.cuda_stream, krylov_restart=args.restart)
     sim.set_state(h, hu, hv)
     dof = 3 * N * N * (k + 1) ** 2
 
@@ -367,6 +368,7 @@ def main():
             "config": {"workload": f"{args.workload}: periodic {N}x{N} quads, k={k}, ARS2, "
                                    f"dt={dt:.6g} (advective CFL 0.5), FP64",
                        "dof": dof, "parallelism": "replicas" if world > 1 else "single",
+                       "gmres_restart": args.restart or 20, "krylov_rtol": 1e-15,
                        "l2": "inputs larger than L2 (A^-1 and trace matrix are GBs)"},
             "latency_ms": {"p50": p50, "p99": p99},
             "krylov_iterations_per_stage": st["krylov_iterations"] / max(1, 2 * st["steps"]),

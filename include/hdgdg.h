@@ -60,8 +60,10 @@ typedef struct {
     int scheme;          /* HDGDG_ARS2 (ARS(2,3,2)) or HDGDG_ARS3 (ARS(4,4,3)) */
     double dt;           /* time step (> 0) */
     int precision;       /* HDGDG_FP64 */
-    double krylov_rtol;  /* GMRES stop: ||g - S qhat|| <= rtol ||g||; <= 0 selects 1e-13 */
-    int krylov_restart;  /* GMRES(m) restart length m; <= 0 selects 20 */
+    double krylov_rtol;  /* GMRES stop: ||g - S qhat|| <= rtol ||g||; <= 0 selects 1e-15.
+                            A restart cycle that fails to halve a true residual already below
+                            1e-12 ||g|| ends the solve as converged (FP64 rounding floor). */
+    int krylov_restart;  /* GMRES(m) restart length m <= 31; <= 0 selects 20 */
     int krylov_maxit;    /* cap on GMRES iterations per stage solve; <= 0 selects 2000 */
     int linear_only;     /* 1: drop NL (linear gravity-wave runs); 0: full method */
 } hdgdg_config;

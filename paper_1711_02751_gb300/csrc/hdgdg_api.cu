@@ -34,11 +34,14 @@ struct Plan {
     size_t persistent = 0, setup_temp = 0;
 };
 
+constexpr int kMaxRestart = 31;   // the fused Gram-Schmidt kernels keep up to 32 basis vectors in registers
+
 bool valid(const hdgdg_config* c) {
     return c && c->n_side >= 2 && c->n_side <= 32768 && c->degree_k >= 1 && c->degree_k <= kMaxP - 1 &&
            std::isfinite(c->g) && c->g > 0.0 && std::isfinite(c->H0) && std::isfinite(c->dt) &&
            c->dt > 0.0 && (c->scheme == HDGDG_ARS2 || c->scheme == HDGDG_ARS3) &&
-           c->precision == HDGDG_FP64 && (c->linear_only == 0 || c->linear_only == 1);
+           c->precision == HDGDG_FP64 && (c->linear_only == 0 || c->linear_only == 1) &&
+           c->krylov_restart <= kMaxRestart;
 }
 
 int restart_of(const hdgdg_config* c) { return c->krylov_restart > 0 ? c->krylov_restart : 20; }
@@ -63,7 +66,7 @@ Plan make_plan(const hdgdg_config* c) {
     b += 2 * n_edges * (size_t)p.NF * p.NF * d;               // M^{-1}, S_rr
     b += (5 + 2 * (size_t)p.s) * 3 * p.n * d;                 // q, q_new, R1, Z, Q, NL_i, L_i
     b += (4 + (size_t)p.m + 1) * p.nt * d;                    // g, x~, qhat, w, Krylov basis
-    b += (dot_scratch_doubles(p.m + 1) + mass_scratch_doubles() + 4 * (size_t)(p.m + 2) + 16) * d;
+    b += (dot_scratch_doubles(p.m + 2) + mass_scratch_doubles() + 4 * (size_t)(p.m + 2) + 16) * d;
     b += 64;                                                  // flags
     p.persistent = b;
     p.setup_temp = n_el * (size_t)p.NT * p.NT * d + n_edges * 7 * (size_t)p.NF * p.NF * d;
@@ -315,7 +318,10 @@ hdgdg_status norm2_to_host(hdgdg_sim* sim, const double* v, double* out) {
 hdgdg_status gmres(hdgdg_sim* sim, const double* g, double* qhat, int* iters, double* relres) {
     const size_t n = sim->plan.nt;
     const int m = sim->plan.m;
-    const double rtol = sim->cfg.krylov_rtol > 0.0 ? sim->cfg.krylov_rtol : 1e-13;
+    const double rtol = sim->cfg.krylov_rtol > 0.0 ? sim->cfg.krylov_rtol : 1e-15;
+    // A restart cycle that cannot halve the true residual once it is already below
+    // kStagnation * ||g|| has reached the rounding floor of the FP64 residual: accept it.
+    constexpr double kStagnation = 1e-12;
     const int maxit = sim->cfg.krylov_maxit > 0 ? sim->cfg.krylov_maxit : 2000;
     cudaStream_t st = sim->stream;
     *iters = 0;
@@ -347,21 +353,20 @@ hdgdg_status gmres(hdgdg_sim* sim, const double* g, double* qhat, int* iters, do
                 CU(launch_spmv_pre(sim->g, sim->Stil, sim->Scol, Vj, sim->w, st));
             }
             {
+                // classical Gram-Schmidt, twice: h1 = V^T w, w1 = w - V h1, h2 = V^T w1,
+                // V_{j+1} = (w1 - V h2) / ||w1 - V h2||; the column of H is h1 + h2
                 TimedGroup tg(sim, HDGDG_KT_ORTHO);
                 CU(launch_multidot(sim->V, n, j + 1, sim->w, n, sim->red, dv_h1(sim), st));
-                CU(launch_multiaxpy(sim->V, n, j + 1, dv_h1(sim), 1.0, sim->w, n, st));
-                CU(launch_multidot(sim->V, n, j + 1, sim->w, n, sim->red, dv_h2(sim), st));
-                CU(launch_multiaxpy(sim->V, n, j + 1, dv_h2(sim), 1.0, sim->w, n, st));
-                CU(launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st));
-                CU(launch_scale_by_rnorm(sim->w, dv_nrm(sim), sim->V + (size_t)(j + 1) * n, n, st));
+                CU(launch_cgs2_tail(sim->V, n, j + 1, dv_h1(sim), sim->w, n, sim->red, dv_h2(sim),
+                                    dv_nrm(sim), dv_nrm(sim) + 1, sim->V + (size_t)(j + 1) * n, st));
             }
-            CU(cudaMemcpyAsync(sim->hbuf, sim->dvals, (2 * (m + 2) + 1) * sizeof(double),
+            CU(cudaMemcpyAsync(sim->hbuf, sim->dvals, (2 * (m + 2) + 2) * sizeof(double),
                                cudaMemcpyDeviceToHost, st));
             TRY(sync(sim));
             const double* h1 = sim->hbuf;
             const double* h2 = sim->hbuf + (m + 2);
             for (int i = 0; i <= j; ++i) Hij(i, j) = h1[i] + h2[i];
-            Hij(j + 1, j) = std::sqrt(sim->hbuf[2 * (m + 2)]);
+            Hij(j + 1, j) = sim->hbuf[2 * (m + 2) + 1];
             for (int i = 0; i < j; ++i) {
                 const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
                 Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
@@ -397,8 +402,10 @@ hdgdg_status gmres(hdgdg_sim* sim, const double* g, double* qhat, int* iters, do
         CU(launch_combine(n, g, t, sim->w, nullptr, st));
         double rn2;
         TRY(norm2_to_host(sim, sim->w, &rn2));   // also leaves ||r||^2 in dv_nrm for the restart
+        const double prev = rnorm;
         rnorm = std::sqrt(rn2);
         if (rnorm <= tol) break;
+        if (rnorm <= kStagnation * bnorm && rnorm > 0.5 * prev) break;
         if (total >= maxit) {
             *iters = total;
             *relres = rnorm / bnorm;
@@ -517,7 +524,7 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
     }
     for (double** v : {&sim->gvec, &sim->xt, &sim->lam, &sim->w}) TRY(dalloc(sim, v, p.nt));
     TRY(dalloc(sim, &sim->V, (size_t)(p.m + 1) * p.nt));
-    TRY(dalloc(sim, &sim->red, dot_scratch_doubles(p.m + 1)));
+    TRY(dalloc(sim, &sim->red, dot_scratch_doubles(p.m + 2)));
     TRY(dalloc(sim, &sim->mred, mass_scratch_doubles()));
     TRY(dalloc(sim, &sim->dvals, 4 * (size_t)(p.m + 2) + 16));
     TRY(dalloc(sim, &sim->flags, 16));

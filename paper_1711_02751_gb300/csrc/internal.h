@@ -115,6 +115,13 @@ cudaError_t launch_multidot(const double* V, size_t ldv, int nv, const double* w
 // w = w - sum_j coef[j] V_j   (coef on the device)
 cudaError_t launch_multiaxpy(const double* V, size_t ldv, int nv, const double* coef, double sign,
                              double* w, size_t n, cudaStream_t s);
+// Fused tail of classical Gram-Schmidt applied twice, given h1 = V^T w on the device:
+// w1 = w - V h1 (in place), h2 = V^T w1, ||w1||^2 -> *nw1, hn = sqrt(||w1||^2 - ||h2||^2),
+// vout = (w1 - V h2) / hn.  nv <= cgs2_max_vectors(); scratch of dot_scratch_doubles(nv + 1).
+int cgs2_max_vectors();
+cudaError_t launch_cgs2_tail(const double* V, size_t ldv, int nv, const double* h1, double* w, size_t n,
+                             double* scratch, double* h2, double* nw1, double* hn, double* vout,
+                             cudaStream_t s);
 // v = w / sqrt(*nrm2)
 cudaError_t launch_scale_by_rnorm(const double* w, const double* nrm2, double* v, size_t n,
                                   cudaStream_t s);

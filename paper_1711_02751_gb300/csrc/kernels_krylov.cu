@@ -121,6 +121,77 @@ __global__ void scale_kernel(const double* __restrict__ w, const double* __restr
         v[idx] = w[idx] * s;
 }
 
+// Second Gram-Schmidt pass fused with the update of the first: w1 = w - sum_j h1_j V_j (w
+// overwritten), and partial sums of V_j . w1 (j < NJ) and w1 . w1, the V_j kept in registers.
+template <int NJ>
+__global__ void __launch_bounds__(kDotThreads)
+axpy_dot_kernel(const double* __restrict__ V, size_t ldv, const double* __restrict__ h1,
+                double* __restrict__ w, size_t n, double* __restrict__ partial, int ldp) {
+    __shared__ double sh[NJ + 1][kDotThreads / 32];
+    double hc[NJ], acc[NJ + 1];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) { hc[j] = __ldg(h1 + j); acc[j] = 0.0; }
+    acc[NJ] = 0.0;
+    for (size_t idx = blockIdx.x * (size_t)kDotThreads + threadIdx.x; idx < n;
+         idx += (size_t)gridDim.x * kDotThreads) {
+        double v[NJ];
+        double x = w[idx];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            v[j] = V[(size_t)j * ldv + idx];
+            x -= hc[j] * v[j];
+        }
+        w[idx] = x;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) acc[j] += v[j] * x;
+        acc[NJ] += x * x;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c <= NJ; ++c) {
+        const double s = warp_sum(acc[c]);
+        if (lane == 0) sh[c][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x <= NJ) {
+        double s = 0.0;
+        for (int k = 0; k < kDotThreads / 32; ++k) s += sh[threadIdx.x][k];
+        partial[(size_t)blockIdx.x * ldp + threadIdx.x] = s;
+    }
+}
+
+// hn = sqrt(||w1||^2 - ||h2||^2), the norm of w2 = w1 - V h2 for an orthonormal V (one thread).
+__global__ void finish_norm_kernel(const double* __restrict__ h2, int nj, const double* __restrict__ nw1,
+                                   double* __restrict__ hn) {
+    double s = *nw1;
+    for (int j = 0; j < nj; ++j) s -= h2[j] * h2[j];
+    *hn = s > 0.0 ? sqrt(s) : 0.0;
+}
+
+// V_{j+1} = (w1 - sum_j h2_j V_j) / hn
+template <int NJ>
+__global__ void __launch_bounds__(256)
+axpy_scale_kernel(const double* __restrict__ V, size_t ldv, const double* __restrict__ h2,
+                  const double* __restrict__ hn, const double* __restrict__ w, double* __restrict__ vout,
+                  size_t n) {
+    double hc[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) hc[j] = __ldg(h2 + j);
+    const double inv = 1.0 / *hn;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        double x = w[idx];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) x -= hc[j] * V[(size_t)j * ldv + idx];
+        vout[idx] = x * inv;
+    }
+}
+
+template <int NJ>
+cudaError_t cgs2_tail_launch(const double* V, size_t ldv, const double* h1, double* w, size_t n,
+                             double* scratch, double* h2, double* nw1, double* hn, double* vout,
+                             cudaStream_t s);
+
 int stream_grid(size_t n) {
     size_t b = (n + 255) / 256;
     if (b > 152 * 8) b = 152 * 8;
@@ -144,7 +215,41 @@ cudaError_t block_diag_launch(int n_edges, const double* Bd, const double* x, do
     return cudaGetLastError();
 }
 
+template <int NJ>
+cudaError_t cgs2_tail_launch(const double* V, size_t ldv, const double* h1, double* w, size_t n,
+                             double* scratch, double* h2, double* nw1, double* hn, double* vout,
+                             cudaStream_t s) {
+    axpy_dot_kernel<NJ><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, h1, w, n, scratch, NJ + 1);
+    count_launches(1);
+    // scratch holds [blk][NJ + 1]: the first NJ columns reduce to h2, the last to ||w1||^2
+    multidot_final_kernel<<<(NJ + 1 + 7) / 8, 256, 0, s>>>(scratch, kDotBlocks, NJ + 1, NJ, h2);
+    count_launches(1);
+    multidot_final_kernel<<<1, 32, 0, s>>>(scratch + NJ, kDotBlocks, NJ + 1, 1, nw1);
+    count_launches(1);
+    finish_norm_kernel<<<1, 1, 0, s>>>(h2, NJ, nw1, hn);
+    count_launches(1);
+    axpy_scale_kernel<NJ><<<stream_grid(n), 256, 0, s>>>(V, ldv, h2, hn, w, vout, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+int cgs2_max_vectors() { return 32; }
+
+cudaError_t launch_cgs2_tail(const double* V, size_t ldv, int nv, const double* h1, double* w, size_t n,
+                             double* scratch, double* h2, double* nw1, double* hn, double* vout,
+                             cudaStream_t s) {
+    switch (nv) {
+#define CASE(J) case J: return cgs2_tail_launch<J>(V, ldv, h1, w, n, scratch, h2, nw1, hn, vout, s);
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
+        CASE(12) CASE(13) CASE(14) CASE(15) CASE(16) CASE(17) CASE(18) CASE(19) CASE(20) CASE(21)
+        CASE(22) CASE(23) CASE(24) CASE(25) CASE(26) CASE(27) CASE(28) CASE(29) CASE(30) CASE(31)
+        CASE(32)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_spmv_pre(const Geom& g, const double* Stil, const int* Scol, const double* x,
                             double* y, cudaStream_t s) {
