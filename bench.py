@@ -33,6 +33,7 @@ UNIT = "DOF-steps/s"
 WORKLOADS = {"large512": (512, 3), "bump8": (8, 2), "mid128": (128, 3)}
 CPU_SAMPLE = (64, 3)       # oracle sample: the large512 recipe on 64 x 64, k = 3
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def _args():
@@ -43,6 +44,8 @@ def _args():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="large512", choices=sorted(WORKLOADS))
     ap.add_argument("--restart", type=int, default=0, help="GMRES restart length (0: library default)")
+    ap.add_argument("--precisions", default="fp64,mixed",
+                    help="forms to time; the headline is mixed when within 1e-6 of fp64")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
@@ -182,13 +185,14 @@ class ClockSampler:
 
 
 # ---- roofline --------------------------------------------------------------------------------
-def _algorithmic(N, k, cls):
-    """(bytes, flops) one launch group of a kernel class moves / performs at FP64."""
+def _algorithmic(N, k, cls, precision="fp64"):
+    """(bytes, flops) one launch group of a kernel class moves / performs."""
     P = k + 1
     NF, NV, Np = 3 * P, 3 * P * P, P * P
     n_el, n_edges = N * N, 2 * N * N
     if cls == "spmv":   # 6 off-diagonal NF x NF blocks + column ids + x and y once
-        return n_edges * (6 * NF * NF * 8 + 6 * 4 + 2 * NF * 8), n_edges * NF * (12 * NF + 1)
+        w = 4 if precision == "mixed" else 8
+        return n_edges * (6 * NF * NF * w + 6 * 4 + 2 * NF * w), n_edges * NF * (12 * NF + 1)
     if cls == "condense":   # A^{-1} once, R1 in, Z out; then Z face values + phiB in, g out
         return (n_el * (NV * NV * 8 + 2 * NV * 8) + n_edges * NF * 8 * 3,
                 n_el * 2 * NV * NV)
@@ -200,7 +204,7 @@ def _algorithmic(N, k, cls):
     return None, None
 
 
-def _traffic_for(cls, N, k):
+def _traffic_for(cls, N, k, precision="fp64"):
     """dram bytes per launch from a committed ncu summary, if it is for the current kernel source."""
     try:
         d = json.load(open(PROFILE_TRAFFIC))
@@ -211,7 +215,7 @@ def _traffic_for(cls, N, k):
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     except Exception:
         return None
-    e = d.get("kernels", {}).get(cls)
+    e = d.get("kernels", {}).get(f"{cls}_{precision}")
     if not e or e.get("source_sha") != sha:
         return None
     return e["dram_bytes_per_launch"] * (N * N) / e["n_el"]
@@ -222,6 +226,96 @@ def _peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+def _timed_steps(sim, stream, steps, dist):
+    """K steps of a resident instance, CUDA events on the library's stream around each."""
+    import torch
+    sim.set_kernel_timing(True)
+    l0 = sim.stats()["kernel_launches"]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    evs[0].record(stream)
+    for i in range(steps):
+        sim.step(1)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    per_step = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+    ms_total = evs[0].elapsed_time(evs[-1])
+    if dist:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    st = sim.stats()
+    return {"ms_total": ms_total, "per_step": per_step, "ktimes": sim.kernel_times(), "stats": st,
+            "launches": st["kernel_launches"] - l0}
+
+
+def _e2e(sim, stream, steps, dist, h, hu, hv):
+    """The same steps through host buffers: pinned H2D of the state, step, D2H of the result."""
+    import torch
+    n = h.size
+    bufs = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(6)]
+    for bsrc, a in zip(bufs[:3], (h, hu, hv)):
+        bsrc.numpy()[:] = a.ravel()
+    ptrs_in = [bb.data_ptr() for bb in bufs[:3]]
+    ptrs_out = [bb.data_ptr() for bb in bufs[3:]]
+    sim.set_state_ptrs(*ptrs_in)
+    sim.step(1)
+    sim.get_state_ptrs(*ptrs_out)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        sim.set_state_ptrs(*ptrs_in)
+        sim.step(1)
+        sim.get_state_ptrs(*ptrs_out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, 3 * n * 8
+
+
+def _roofline(N, k, ktimes, precision, fp64_tflops, hbm):
+    dom = max((c for c in ktimes if ktimes[c][1] > 0 and _algorithmic(N, k, c, precision)[0]),
+              key=lambda c: ktimes[c][0])
+    tot_ms, n_l = ktimes[dom]
+    avg_s = tot_ms / n_l / 1e3
+    byt, flo = _algorithmic(N, k, dom, precision)
+    alu_peak = fp64_tflops if (precision == "fp64" or dom != "spmv") else FP32_NOMINAL_TFLOPS
+    t_hbm, t_alu = byt / (hbm * 1e9), flo / (alu_peak * 1e12)
+    if t_hbm >= t_alu:
+        roof = {"bound": "hbm", "achieved": byt / avg_s / 1e9, "peak": hbm, "unit": "GB/s"}
+    else:
+        roof = {"bound": "alu", "achieved": flo / avg_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = _traffic_for(dom, N, k, precision)
+    roof.update({"kernel": dom, "avg_launch_ms": avg_s * 1e3, "algorithmic_bytes": byt,
+                 "algorithmic_flops": flo,
+                 "peak_source": ("FP64 FMA rate measured in bench.py by the library's probe (of measured)"
+                                 if roof["bound"] == "alu" and alu_peak == fp64_tflops else
+                                 "MEASURED_PEAKS.json hbm_gbs (of measured)" if roof["bound"] == "hbm"
+                                 else "nominal FP32 rate 152 SMs x 128 lanes x 2 x 2.07 GHz")})
+    return roof
+
+
+def _rel_l2_nodal(a, b, B):
+    """Per-field relative L2 over the nodes of (eta = h - B, hu, hv), unweighted."""
+    out = {}
+    for name, x, y in (("eta", a[0] - B, b[0] - B), ("hu", a[1], b[1]), ("hv", a[2], b[2])):
+        den = float(np.sqrt(np.sum(y * y)))
+        out[name] = float(np.sqrt(np.sum((x - y) ** 2))) / den if den > 0 else float(np.sqrt(np.sum(x * x)))
+    return out
 
 
 def main():
@@ -250,106 +344,63 @@ def main():
     x, y = hd.node_coords(N, k)
     h, hu, hv, b = _workload_state(args.workload, x, y, rank)
     dt = W.advective_dt(x, h, hu, hv, N)
+    B = W.H0 - b
     stream = torch.cuda.Stream()          # a real stream: the legacy default stream has handle 0
     torch.cuda.set_stream(stream)
-    sim = hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, stream=stream.cuda_stream, krylov_restart=args.restart)
-    sim.set_state(h, hu, hv)
     dof = 3 * N * N * (k + 1) ** 2
-
     fp64_tflops = hd.measure_fp64_tflops()
-    for _ in range(args.warmup):
-        sim.step(1)
-    torch.cuda.synchronize()
 
-    # ---- timed region: K steps, inputs resident, events on the library's stream ----
-    clocks = ClockSampler()
-    if rank == 0:
-        clocks.start()
-        time.sleep(0.3)
-    sim.set_kernel_timing(True)
-    l0 = sim.stats()["kernel_launches"]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    evs[0].record(stream)
-    for i in range(args.steps):
-        sim.step(1)
-        evs[i + 1].record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ktimes = sim.kernel_times()
-    st = sim.stats()
-    launches = st["kernel_launches"] - l0
-    clk = clocks.stop() if rank == 0 else None
-    per_step = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
-    ms_total = evs[0].elapsed_time(evs[-1])
-    if dist:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    value = world * dof * args.steps / (ms_total / 1e3)
-
-    # ---- e2e: the same steps through host buffers, copies inside the timed region ----
-    e2e = None
-    if not args.no_e2e:
-        n = N * N * (k + 1) ** 2
-        bufs = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(6)]
-        for bsrc, a in zip(bufs[:3], (h, hu, hv)):
-            bsrc.numpy()[:] = a.ravel()
-        ptrs_in = [bb.data_ptr() for bb in bufs[:3]]
-        ptrs_out = [bb.data_ptr() for bb in bufs[3:]]
-        sim.set_state_ptrs(*ptrs_in)
-        sim.step(1)
-        sim.get_state_ptrs(*ptrs_out)
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            sim.set_state_ptrs(*ptrs_in)
+    forms = {}
+    finals = {}
+    clk = None
+    for precision in args.precisions.split(","):
+        sim = hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, stream=stream.cuda_stream,
+                     krylov_restart=args.restart, precision=precision)
+        sim.set_state(h, hu, hv)
+        for _ in range(args.warmup):
             sim.step(1)
-            sim.get_state_ptrs(*ptrs_out)
-        e1.record(stream)
         torch.cuda.synchronize()
-        ms_e2e = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms_e2e], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e2e = float(t.item())
-        e2e = {"value": world * dof * args.steps / (ms_e2e / 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": 3 * n * 8, "d2h_bytes_per_step": 3 * n * 8}
-    sim.close()
-
+        clocks = ClockSampler()
+        if rank == 0:
+            clocks.start()
+            time.sleep(0.3)
+        r = _timed_steps(sim, stream, args.steps, dist)
+        c = clocks.stop() if rank == 0 else None
+        finals[precision] = sim.get_state()
+        e2e = None
+        if not args.no_e2e:
+            ms_e2e, nbytes = _e2e(sim, stream, args.steps, dist, h, hu, hv)
+            e2e = {"value": world * dof * args.steps / (ms_e2e / 1e3), "unit": UNIT,
+                   "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+        sim.close()
+        forms[precision] = {"r": r, "clocks": c, "e2e": e2e}
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
 
-    # ---- roofline of the dominant kernel class ----
     peaks = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    dom = max((c for c in ktimes if ktimes[c][1] > 0 and _algorithmic(N, k, c)[0]),
-              key=lambda c: ktimes[c][0])
-    tot_ms, n_l = ktimes[dom]
-    avg_s = tot_ms / n_l / 1e3
-    byt, flo = _algorithmic(N, k, dom)
-    t_hbm, t_alu = byt / (hbm * 1e9), flo / (fp64_tflops * 1e12)
-    if t_hbm >= t_alu:
-        roof = {"bound": "hbm", "achieved": byt / avg_s / 1e9, "peak": hbm, "unit": "GB/s"}
-    else:
-        roof = {"bound": "alu", "achieved": flo / avg_s / 1e12, "peak": fp64_tflops, "unit": "TFLOP/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    tr = _traffic_for(dom, N, k)
-    roof["traffic"] = tr
-    roof["kernel"] = dom
-    roof["avg_launch_ms"] = avg_s * 1e3
-    roof["algorithmic_bytes"] = byt
-    roof["algorithmic_flops"] = flo
-    roof["peak_source"] = ("measured FP64 FMA probe in bench.py" if roof["bound"] == "alu"
-                           else "MEASURED_PEAKS.json hbm_gbs (of measured)")
+    err = None
+    if "fp64" in finals and "mixed" in finals:
+        err = _rel_l2_nodal(finals["mixed"], finals["fp64"], B)
+    # headline: the fastest form whose state stays within 1e-6 of the FP64 form
+    head = "fp64"
+    if "mixed" in forms and (err is not None and max(err.values()) <= 1e-6 or "fp64" not in forms):
+        head = "mixed"
+    summary = {}
+    for p, f in forms.items():
+        r = f["r"]
+        summary[p] = {"value": world * dof * args.steps / (r["ms_total"] / 1e3),
+                      "ms_per_step": r["ms_total"] / args.steps,
+                      "krylov_iterations_per_stage": r["stats"]["krylov_iterations"] / max(1, 2 * r["stats"]["steps"]),
+                      "kernel_breakdown_ms": {c: {"ms": round(v[0], 3), "groups": v[1]} for c, v in r["ktimes"].items()},
+                      "roofline": _roofline(N, k, r["ktimes"], p, fp64_tflops, hbm),
+                      "e2e": f["e2e"], "gpu_launches": r["launches"]}
+    hr = forms[head]["r"]
+    per_step = hr["per_step"]
+    p50 = statistics.median(per_step)
+    p99 = sorted(per_step)[min(len(per_step) - 1, math.ceil(0.99 * len(per_step)) - 1)]
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -358,22 +409,21 @@ def main():
         except Exception as ex:   # reported, never silently replaced
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"[:300]}
 
-    per_step_sorted = sorted(per_step)
-    p50 = statistics.median(per_step)
-    p99 = per_step_sorted[min(len(per_step) - 1, math.ceil(0.99 * len(per_step)) - 1)]
-    breakdown = {c: {"ms": round(v[0], 3), "groups": v[1]} for c, v in ktimes.items()}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+    line = {"metric": METRIC, "value": summary[head]["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": summary[head]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if head == "fp64" else "f64+f32 (FP32 Krylov cycles, FP64 refinement and local ops)",
+            "data": "synthetic",
             "config": {"workload": f"{args.workload}: periodic {N}x{N} quads, k={k}, ARS2, "
-                                   f"dt={dt:.6g} (advective CFL 0.5), FP64",
+                                   f"dt={dt:.6g} (advective CFL 0.5)", "form": head,
                        "dof": dof, "parallelism": "replicas" if world > 1 else "single",
-                       "gmres_restart": args.restart or 20, "krylov_rtol": 1e-15,
+                       "gmres_restart": args.restart or 20,
                        "l2": "inputs larger than L2 (A^-1 and trace matrix are GBs)"},
             "latency_ms": {"p50": p50, "p99": p99},
-            "krylov_iterations_per_stage": st["krylov_iterations"] / max(1, 2 * st["steps"]),
-            "gpu_launches": launches, "roofline": roof, "kernel_breakdown_ms": breakdown,
-            "fp64_fma_tflops_measured": fp64_tflops, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+            "rel_l2_mixed_vs_fp64": err,
+            "gpu_launches": summary[head]["gpu_launches"], "roofline": summary[head]["roofline"],
+            "e2e": summary[head]["e2e"], "clocks": forms[head]["clocks"],
+            "fp64_fma_tflops_measured": fp64_tflops, "forms": summary, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -50,7 +50,14 @@ typedef enum {
 } hdgdg_status;
 
 enum { HDGDG_ARS2 = 0, HDGDG_ARS3 = 1 };          /* IMEX schemes named in Sec. 6 */
-enum { HDGDG_FP64 = 0 };                          /* arithmetic of the path */
+/* Arithmetic of the path.
+ * HDGDG_FP64:  every kernel in FP64.
+ * HDGDG_MIXED: the trace Krylov solve runs as FP32 GMRES(m) cycles on an FP32 copy of the
+ *              preconditioned trace matrix, each cycle restarted from the true residual
+ *              g - S qhat computed in FP64 with the solution accumulated in FP64 (iterative
+ *              refinement); residual norms, the local condensation and recovery, the DG
+ *              residual, the stage combinations and mass sums stay in FP64. */
+enum { HDGDG_FP64 = 0, HDGDG_MIXED = 1 };
 
 typedef struct {
     int n_side;          /* N >= 2: elements per side of the periodic unit square */
@@ -59,8 +66,9 @@ typedef struct {
     double H0;           /* reference depth: B = H0 - b */
     int scheme;          /* HDGDG_ARS2 (ARS(2,3,2)) or HDGDG_ARS3 (ARS(4,4,3)) */
     double dt;           /* time step (> 0) */
-    int precision;       /* HDGDG_FP64 */
-    double krylov_rtol;  /* GMRES stop: ||g - S qhat|| <= rtol ||g||; <= 0 selects 1e-15.
+    int precision;       /* HDGDG_FP64 or HDGDG_MIXED */
+    double krylov_rtol;  /* GMRES stop: ||g - S qhat|| <= rtol ||g||; <= 0 selects 1e-15
+                            (FP64) or 1e-10 (MIXED, FP64 residual of the refinement loop).
                             A restart cycle that fails to halve a true residual already below
                             1e-12 ||g|| ends the solve as converged (FP64 rounding floor). */
     int krylov_restart;  /* GMRES(m) restart length m <= 31; <= 0 selects 20 */

@@ -40,7 +40,8 @@ bool valid(const hdgdg_config* c) {
     return c && c->n_side >= 2 && c->n_side <= 32768 && c->degree_k >= 1 && c->degree_k <= kMaxP - 1 &&
            std::isfinite(c->g) && c->g > 0.0 && std::isfinite(c->H0) && std::isfinite(c->dt) &&
            c->dt > 0.0 && (c->scheme == HDGDG_ARS2 || c->scheme == HDGDG_ARS3) &&
-           c->precision == HDGDG_FP64 && (c->linear_only == 0 || c->linear_only == 1) &&
+           (c->precision == HDGDG_FP64 || c->precision == HDGDG_MIXED) &&
+           (c->linear_only == 0 || c->linear_only == 1) &&
            c->krylov_restart <= kMaxRestart;
 }
 
@@ -65,7 +66,13 @@ Plan make_plan(const hdgdg_config* c) {
     b += n_edges * 6 * sizeof(int);                           // columns
     b += 2 * n_edges * (size_t)p.NF * p.NF * d;               // M^{-1}, S_rr
     b += (5 + 2 * (size_t)p.s) * 3 * p.n * d;                 // q, q_new, R1, Z, Q, NL_i, L_i
-    b += (4 + (size_t)p.m + 1) * p.nt * d;                    // g, x~, qhat, w, Krylov basis
+    b += 4 * p.nt * d;                                        // g, x~, qhat, w
+    if (c->precision == HDGDG_MIXED) {                        // FP32 S~, FP32 basis and work vector
+        b += n_edges * 6 * (size_t)p.NF * p.NF * sizeof(float);
+        b += ((size_t)p.m + 2) * p.nt * sizeof(float);
+    } else {
+        b += ((size_t)p.m + 1) * p.nt * d;                    // FP64 Krylov basis
+    }
     b += (dot_scratch_doubles(p.m + 2) + mass_scratch_doubles() + 4 * (size_t)(p.m + 2) + 16) * d;
     b += 64;                                                  // flags
     p.persistent = b;
@@ -197,6 +204,7 @@ struct hdgdg_sim {
     double *q = nullptr, *q_new = nullptr, *R1 = nullptr, *Z = nullptr, *Qs = nullptr;
     double *NLs[kMaxStages] = {}, *Ls[kMaxStages] = {};
     double *gvec = nullptr, *xt = nullptr, *lam = nullptr, *w = nullptr, *V = nullptr;
+    float *Stil32 = nullptr, *V32 = nullptr, *w32 = nullptr;   // mixed precision only
     double *red = nullptr, *mred = nullptr, *dvals = nullptr;
     unsigned* flags = nullptr;
     double* hbuf = nullptr;   // pinned host scratch
@@ -425,6 +433,118 @@ hdgdg_status gmres(hdgdg_sim* sim, const double* g, double* qhat, int* iters, do
     return HDGDG_OK;
 }
 
+// Mixed precision: FP32 GMRES(m) cycles on S~32, each started from the FP64 true residual
+// r = g - S~ x~ (iterative refinement); x~ accumulated in FP64; qhat = M^{-1} x~.
+hdgdg_status gmres_mixed(hdgdg_sim* sim, const double* g, double* qhat, int* iters, double* relres) {
+    const size_t n = sim->plan.nt;
+    const int m = sim->plan.m;
+    const double rtol = sim->cfg.krylov_rtol > 0.0 ? sim->cfg.krylov_rtol : 1e-10;
+    const int maxit = sim->cfg.krylov_maxit > 0 ? sim->cfg.krylov_maxit : 2000;
+    constexpr double kInner = 1e-6;        // FP32 cycle stop, relative to the cycle's residual
+    constexpr double kStagnation = 1e-12;
+    cudaStream_t st = sim->stream;
+    *iters = 0;
+    double bn2;
+    TRY(norm2_to_host(sim, g, &bn2));
+    if (!std::isfinite(bn2)) return fail(sim, HDGDG_ENONFINITE, "non-finite trace right-hand side");
+    if (bn2 == 0.0) {
+        CU(cudaMemsetAsync(qhat, 0, n * sizeof(double), st));
+        *relres = 0.0;
+        return HDGDG_OK;
+    }
+    const double bnorm = std::sqrt(bn2), tol = rtol * bnorm;
+    CU(cudaMemsetAsync(sim->xt, 0, n * sizeof(double), st));
+    CU(cudaMemcpyAsync(sim->w, g, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CU(launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st));
+    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), sv(m + 1), y(m);
+    auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+    double rnorm = bnorm;
+    int total = 0;
+    while (true) {
+        CU(launch_scale_by_rnorm(sim->w, dv_nrm(sim), sim->V32, n, st));
+        std::fill(sv.begin(), sv.end(), 0.0);
+        sv[0] = 1.0;
+        int jend = 0;
+        for (int j = 0; j < m; ++j) {
+            float* Vj = sim->V32 + (size_t)j * n;
+            {
+                TimedGroup tg(sim, HDGDG_KT_SPMV);
+                CU(launch_spmv_pre(sim->g, sim->Stil32, sim->Scol, Vj, sim->w32, st));
+            }
+            {
+                TimedGroup tg(sim, HDGDG_KT_ORTHO);
+                CU(launch_multidot(sim->V32, n, j + 1, sim->w32, n, sim->red, dv_h1(sim), st));
+                CU(launch_cgs2_tail(sim->V32, n, j + 1, dv_h1(sim), sim->w32, n, sim->red, dv_h2(sim),
+                                    dv_nrm(sim) + 2, dv_nrm(sim) + 1, sim->V32 + (size_t)(j + 1) * n, st));
+            }
+            CU(cudaMemcpyAsync(sim->hbuf, sim->dvals, (2 * (m + 2) + 2) * sizeof(double),
+                               cudaMemcpyDeviceToHost, st));
+            TRY(sync(sim));
+            const double* h1 = sim->hbuf;
+            const double* h2 = sim->hbuf + (m + 2);
+            for (int i = 0; i <= j; ++i) Hij(i, j) = h1[i] + h2[i];
+            Hij(j + 1, j) = sim->hbuf[2 * (m + 2) + 1];
+            for (int i = 0; i < j; ++i) {
+                const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+                Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
+                Hij(i, j) = t;
+            }
+            const double den = std::hypot(Hij(j, j), Hij(j + 1, j));
+            cs[j] = den > 0.0 ? Hij(j, j) / den : 1.0;
+            sn[j] = den > 0.0 ? Hij(j + 1, j) / den : 0.0;
+            const double hsub = Hij(j + 1, j);
+            Hij(j, j) = den;
+            Hij(j + 1, j) = 0.0;
+            sv[j + 1] = -sn[j] * sv[j];
+            sv[j] = cs[j] * sv[j];
+            ++total;
+            jend = j + 1;
+            if (!std::isfinite(sv[j + 1]))
+                return fail(sim, HDGDG_ENONFINITE, "non-finite GMRES residual at iteration %d", total);
+            if (std::fabs(sv[j + 1]) <= kInner || std::fabs(sv[j + 1]) * rnorm <= tol || total >= maxit ||
+                hsub == 0.0)
+                break;
+        }
+        for (int i = jend - 1; i >= 0; --i) {
+            double acc = sv[i];
+            for (int k = i + 1; k < jend; ++k) acc -= Hij(i, k) * y[k];
+            y[i] = acc / Hij(i, i);
+        }
+        for (int i = 0; i < jend; ++i) y[i] *= rnorm;
+        CU(cudaMemcpyAsync(dv_coef(sim), y.data(), jend * sizeof(double), cudaMemcpyHostToDevice, st));
+        CU(launch_axpy_f32_into_f64(sim->V32, n, jend, dv_coef(sim), sim->xt, n, st));
+        // FP64 true residual r = g - S~ x~
+        CU(launch_spmv_pre(sim->g, sim->Stil, sim->Scol, sim->xt, sim->w, st));
+        CombineTerms t{};
+        t.n = 1;
+        t.X[0] = sim->w;
+        t.c[0] = -1.0;
+        CU(launch_combine(n, g, t, sim->w, nullptr, st));
+        double rn2;
+        TRY(norm2_to_host(sim, sim->w, &rn2));   // leaves ||r||^2 in dv_nrm for the next cycle
+        const double prev = rnorm;
+        rnorm = std::sqrt(rn2);
+        if (rnorm <= tol) break;
+        if (rnorm <= kStagnation * bnorm && rnorm > 0.5 * prev) break;
+        if (total >= maxit) {
+            *iters = total;
+            *relres = rnorm / bnorm;
+            sim->stats.last_krylov_iterations = total;
+            sim->stats.last_rel_residual = *relres;
+            return fail(sim, HDGDG_ENOTCONVERGED,
+                        "mixed GMRES: relative residual %.3e > %.3e after %d iterations", rnorm / bnorm,
+                        rtol, total);
+        }
+    }
+    CU(launch_block_diag(sim->g, sim->Minv, sim->xt, qhat, st));
+    *iters = total;
+    *relres = rnorm / bnorm;
+    sim->stats.last_krylov_iterations = total;
+    sim->stats.last_rel_residual = *relres;
+    sim->stats.krylov_iterations += total;
+    return HDGDG_OK;
+}
+
 double beta_of(const hdgdg_sim* sim) { return sim->cfg.dt * sim->a_ii * sim->g.two_over_h * sim->g.inv_w0; }
 
 // One implicit stage: R1 (device) -> Q, Lst = dt M^{-1} L (device); qhat left in sim->lam.
@@ -434,7 +554,8 @@ hdgdg_status stage_solve_dev(hdgdg_sim* sim, const double* R1, double* Q, double
         TimedGroup tg(sim, HDGDG_KT_CONDENSE);
         CU(launch_condense(sim->g, sim->Ainv, R1, sim->phiB, sim->tau, sim->Z, sim->gvec, sim->stream));
     }
-    TRY(gmres(sim, sim->gvec, sim->lam, its, &rr));
+    if (sim->cfg.precision == HDGDG_MIXED) TRY(gmres_mixed(sim, sim->gvec, sim->lam, its, &rr));
+    else TRY(gmres(sim, sim->gvec, sim->lam, its, &rr));
     {
         TimedGroup tg(sim, HDGDG_KT_RECOVER);
         CU(launch_recover(sim->g, sim->Ainv, sim->Z, R1, sim->tau, sim->lam, beta_of(sim), 1.0 / sim->a_ii,
@@ -523,7 +644,13 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
         TRY(dalloc(sim, &sim->Ls[i], 3 * p.n));
     }
     for (double** v : {&sim->gvec, &sim->xt, &sim->lam, &sim->w}) TRY(dalloc(sim, v, p.nt));
-    TRY(dalloc(sim, &sim->V, (size_t)(p.m + 1) * p.nt));
+    if (c->precision == HDGDG_MIXED) {
+        TRY(dalloc(sim, &sim->Stil32, (size_t)g.n_edges * 6 * p.NF * p.NF));
+        TRY(dalloc(sim, &sim->V32, (size_t)(p.m + 1) * p.nt));
+        TRY(dalloc(sim, &sim->w32, p.nt));
+    } else {
+        TRY(dalloc(sim, &sim->V, (size_t)(p.m + 1) * p.nt));
+    }
     TRY(dalloc(sim, &sim->red, dot_scratch_doubles(p.m + 2)));
     TRY(dalloc(sim, &sim->mred, mass_scratch_doubles()));
     TRY(dalloc(sim, &sim->dvals, 4 * (size_t)(p.m + 2) + 16));
@@ -549,6 +676,8 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
     cudaError_t e = launch_build_local(g, sim->phiB, sim->tau, c->dt * sim->a_ii, sim->Ainv, Se, dsing, sim->stream);
     if (e == cudaSuccess)
         e = launch_assemble_trace(g, Se, S7, sim->Srr, sim->Minv, sim->Stil, sim->Scol, dsing, sim->stream);
+    if (e == cudaSuccess && c->precision == HDGDG_MIXED)
+        e = launch_to_f32(sim->Stil, sim->Stil32, (size_t)g.n_edges * 6 * p.NF * p.NF, sim->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
     cudaFree(Se);
     cudaFree(S7);

@@ -100,11 +100,14 @@ cudaError_t launch_recover(const Geom& g, const double* Ainv, const double* Z, c
                            const double* tau_edge, const double* qhat, double beta, double inv_aii,
                            double* Q, double* Lst, cudaStream_t s);
 
-// Krylov set on trace vectors of n = n_edges * nf doubles.
+// Krylov set on trace vectors of n = n_edges * nf values.  Overloads on the storage type:
+// double for the FP64 path, float for the inner solves of the mixed-precision path.
 // y = x + sum_slots S~ x[col]   (S~ with identity diagonal blocks)
 cudaError_t launch_spmv_pre(const Geom& g, const double* Stil, const int* Scol, const double* x,
                             double* y, cudaStream_t s);
-// y = B x for a block-diagonal matrix B given as [edge][col][row] blocks
+cudaError_t launch_spmv_pre(const Geom& g, const float* Stil, const int* Scol, const float* x,
+                            float* y, cudaStream_t s);
+// y = B x for a block-diagonal matrix B given as [edge][col][row] blocks (FP64)
 cudaError_t launch_block_diag(const Geom& g, const double* Bd, const double* x, double* y,
                               cudaStream_t s);
 // out[j] = <V_j, w>, j < nv, V_j = V + j * ldv; uses partial-sum scratch of
@@ -112,9 +115,14 @@ cudaError_t launch_block_diag(const Geom& g, const double* Bd, const double* x, 
 size_t dot_scratch_doubles(int nv);
 cudaError_t launch_multidot(const double* V, size_t ldv, int nv, const double* w, size_t n,
                             double* scratch, double* out, cudaStream_t s);
-// w = w - sum_j coef[j] V_j   (coef on the device)
+cudaError_t launch_multidot(const float* V, size_t ldv, int nv, const float* w, size_t n,
+                            double* scratch, double* out, cudaStream_t s);
+// w = w - sign * sum_j coef[j] V_j   (coef on the device)
 cudaError_t launch_multiaxpy(const double* V, size_t ldv, int nv, const double* coef, double sign,
                              double* w, size_t n, cudaStream_t s);
+// x = x + sum_j coef[j] V_j with FP32 V and FP64 x (coef on the device)
+cudaError_t launch_axpy_f32_into_f64(const float* V, size_t ldv, int nv, const double* coef, double* x,
+                                     size_t n, cudaStream_t s);
 // Fused tail of classical Gram-Schmidt applied twice, given h1 = V^T w on the device:
 // w1 = w - V h1 (in place), h2 = V^T w1, ||w1||^2 -> *nw1, hn = sqrt(||w1||^2 - ||h2||^2),
 // vout = (w1 - V h2) / hn.  nv <= cgs2_max_vectors(); scratch of dot_scratch_doubles(nv + 1).
@@ -122,9 +130,15 @@ int cgs2_max_vectors();
 cudaError_t launch_cgs2_tail(const double* V, size_t ldv, int nv, const double* h1, double* w, size_t n,
                              double* scratch, double* h2, double* nw1, double* hn, double* vout,
                              cudaStream_t s);
-// v = w / sqrt(*nrm2)
+cudaError_t launch_cgs2_tail(const float* V, size_t ldv, int nv, const double* h1, float* w, size_t n,
+                             double* scratch, double* h2, double* nw1, double* hn, float* vout,
+                             cudaStream_t s);
+// v = w / sqrt(*nrm2), w in FP64
 cudaError_t launch_scale_by_rnorm(const double* w, const double* nrm2, double* v, size_t n,
                                   cudaStream_t s);
+cudaError_t launch_scale_by_rnorm(const double* w, const double* nrm2, float* v, size_t n,
+                                  cudaStream_t s);
+cudaError_t launch_to_f32(const double* a, float* b, size_t n, cudaStream_t s);
 
 // User-state conversion and diagnostics.
 cudaError_t launch_user_to_state(const Geom& g, const double* h, const double* hu, const double* hv,

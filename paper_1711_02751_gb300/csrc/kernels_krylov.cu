@@ -6,6 +6,10 @@
 // into the stored matrix once at setup, S~ = S M^{-1}, so the diagonal blocks of S~ are the
 // identity and are not stored.  All reductions use a fixed grid and a fixed summation
 // order, so results are bitwise reproducible run to run.
+//
+// Every kernel is a template on the storage type T: double for the FP64 path, float for the
+// inner solves of the mixed-precision path.  Products and per-thread partial sums are in T;
+// warp, block and grid reductions are in double.
 #include "internal.h"
 
 namespace hdgdg {
@@ -16,27 +20,27 @@ constexpr int kDotThreads = 256;
 constexpr int kDotChunk = 8;       // vectors reduced per pass over w
 
 // y[r][ii] = x[r][ii] + sum_{slot, jj} S~[r][slot][jj][ii] x[col(r,slot)][jj]
-template <int NF>
+template <int NF, typename T>
 __global__ void __launch_bounds__(256)
-spmv_pre_kernel(int n_edges, const double* __restrict__ Stil, const int* __restrict__ Scol,
-                const double* __restrict__ x, double* __restrict__ y) {
+spmv_pre_kernel(int n_edges, const T* __restrict__ Stil, const int* __restrict__ Scol,
+                const T* __restrict__ x, T* __restrict__ y) {
     constexpr int EPB = 256 / NF;
     const int le = threadIdx.x / NF, ii = threadIdx.x % NF;
     const int r = blockIdx.x * EPB + le;
     if (le >= EPB || r >= n_edges) return;
-    const double* S = Stil + (size_t)r * 6 * NF * NF;
-    double acc = x[(size_t)r * NF + ii];
+    const T* S = Stil + (size_t)r * 6 * NF * NF;
+    T acc = x[(size_t)r * NF + ii];
 #pragma unroll
     for (int sl = 0; sl < 6; ++sl) {
-        const double* xc = x + (size_t)__ldg(Scol + (size_t)r * 6 + sl) * NF;
-        const double* Sb = S + sl * NF * NF;
+        const T* xc = x + (size_t)__ldg(Scol + (size_t)r * 6 + sl) * NF;
+        const T* Sb = S + sl * NF * NF;
 #pragma unroll
         for (int jj = 0; jj < NF; ++jj) acc += Sb[jj * NF + ii] * xc[jj];
     }
     y[(size_t)r * NF + ii] = acc;
 }
 
-// y[r] = B_r x[r] for column-major NF x NF blocks
+// y[r] = B_r x[r] for column-major NF x NF blocks (FP64)
 template <int NF>
 __global__ void __launch_bounds__(256)
 block_diag_kernel(int n_edges, const double* __restrict__ Bd, const double* __restrict__ x,
@@ -59,19 +63,18 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// partial[blk][j] = sum over this block's slice of V_j . w, for j in [j0, j0 + nj)
-template <int CH>
+// partial[blk][j0 + c] = this block's slice of V_{j0+c} . w, c < nj
+template <int CH, typename T>
 __global__ void __launch_bounds__(kDotThreads)
-multidot_partial_kernel(const double* __restrict__ V, size_t ldv, int j0, int nj,
-                        const double* __restrict__ w, size_t n, double* __restrict__ partial,
-                        int ldp) {
+multidot_partial_kernel(const T* __restrict__ V, size_t ldv, int j0, int nj, const T* __restrict__ w,
+                        size_t n, double* __restrict__ partial, int ldp) {
     __shared__ double sh[CH][kDotThreads / 32];
-    double acc[CH];
+    T acc[CH];
 #pragma unroll
-    for (int c = 0; c < CH; ++c) acc[c] = 0.0;
+    for (int c = 0; c < CH; ++c) acc[c] = T(0);
     for (size_t idx = blockIdx.x * (size_t)kDotThreads + threadIdx.x; idx < n;
          idx += (size_t)gridDim.x * kDotThreads) {
-        const double wv = w[idx];
+        const T wv = w[idx];
 #pragma unroll
         for (int c = 0; c < CH; ++c)
             if (c < nj) acc[c] += V[(size_t)(j0 + c) * ldv + idx] * wv;
@@ -79,7 +82,7 @@ multidot_partial_kernel(const double* __restrict__ V, size_t ldv, int j0, int nj
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
-        const double s = warp_sum(acc[c]);
+        const double s = warp_sum((double)acc[c]);
         if (lane == 0) sh[c][wid] = s;
     }
     __syncthreads();
@@ -102,40 +105,60 @@ __global__ void multidot_final_kernel(const double* __restrict__ partial, int nb
     if (lane == 0) out[j] = s;
 }
 
-__global__ void multiaxpy_kernel(const double* __restrict__ V, size_t ldv, int nv,
-                                 const double* __restrict__ coef, double sign, double* __restrict__ w,
-                                 size_t n) {
+// w -= sign * sum_j coef_j V_j
+template <typename T>
+__global__ void multiaxpy_kernel(const T* __restrict__ V, size_t ldv, int nv, const double* __restrict__ coef,
+                                 double sign, T* __restrict__ w, size_t n) {
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
          idx += (size_t)gridDim.x * blockDim.x) {
-        double acc = w[idx];
-        for (int j = 0; j < nv; ++j) acc -= sign * coef[j] * V[(size_t)j * ldv + idx];
+        T acc = w[idx];
+        for (int j = 0; j < nv; ++j) acc -= T(sign * coef[j]) * V[(size_t)j * ldv + idx];
         w[idx] = acc;
     }
 }
 
+// x += sum_j coef_j V_j with FP32 basis vectors and an FP64 accumulator
+__global__ void axpy_f32_into_f64_kernel(const float* __restrict__ V, size_t ldv, int nv,
+                                         const double* __restrict__ coef, double* __restrict__ x, size_t n) {
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        double acc = x[idx];
+        for (int j = 0; j < nv; ++j) acc += coef[j] * (double)V[(size_t)j * ldv + idx];
+        x[idx] = acc;
+    }
+}
+
+// v = w / sqrt(*nrm2) (w in FP64, v in T)
+template <typename T>
 __global__ void scale_kernel(const double* __restrict__ w, const double* __restrict__ nrm2,
-                             double* __restrict__ v, size_t n) {
+                             T* __restrict__ v, size_t n) {
     const double s = 1.0 / sqrt(*nrm2);
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
          idx += (size_t)gridDim.x * blockDim.x)
-        v[idx] = w[idx] * s;
+        v[idx] = T(w[idx] * s);
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, size_t n) {
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (size_t)gridDim.x * blockDim.x)
+        b[idx] = (float)a[idx];
 }
 
 // Second Gram-Schmidt pass fused with the update of the first: w1 = w - sum_j h1_j V_j (w
 // overwritten), and partial sums of V_j . w1 (j < NJ) and w1 . w1, the V_j kept in registers.
-template <int NJ>
+template <int NJ, typename T>
 __global__ void __launch_bounds__(kDotThreads)
-axpy_dot_kernel(const double* __restrict__ V, size_t ldv, const double* __restrict__ h1,
-                double* __restrict__ w, size_t n, double* __restrict__ partial, int ldp) {
+axpy_dot_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict__ h1, T* __restrict__ w,
+                size_t n, double* __restrict__ partial, int ldp) {
     __shared__ double sh[NJ + 1][kDotThreads / 32];
-    double hc[NJ], acc[NJ + 1];
+    T hc[NJ], acc[NJ + 1];
 #pragma unroll
-    for (int j = 0; j < NJ; ++j) { hc[j] = __ldg(h1 + j); acc[j] = 0.0; }
-    acc[NJ] = 0.0;
+    for (int j = 0; j < NJ; ++j) { hc[j] = T(__ldg(h1 + j)); acc[j] = T(0); }
+    acc[NJ] = T(0);
     for (size_t idx = blockIdx.x * (size_t)kDotThreads + threadIdx.x; idx < n;
          idx += (size_t)gridDim.x * kDotThreads) {
-        double v[NJ];
-        double x = w[idx];
+        T v[NJ];
+        T x = w[idx];
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
             v[j] = V[(size_t)j * ldv + idx];
@@ -149,7 +172,7 @@ axpy_dot_kernel(const double* __restrict__ V, size_t ldv, const double* __restri
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int c = 0; c <= NJ; ++c) {
-        const double s = warp_sum(acc[c]);
+        const double s = warp_sum((double)acc[c]);
         if (lane == 0) sh[c][wid] = s;
     }
     __syncthreads();
@@ -169,28 +192,22 @@ __global__ void finish_norm_kernel(const double* __restrict__ h2, int nj, const 
 }
 
 // V_{j+1} = (w1 - sum_j h2_j V_j) / hn
-template <int NJ>
+template <int NJ, typename T>
 __global__ void __launch_bounds__(256)
-axpy_scale_kernel(const double* __restrict__ V, size_t ldv, const double* __restrict__ h2,
-                  const double* __restrict__ hn, const double* __restrict__ w, double* __restrict__ vout,
-                  size_t n) {
-    double hc[NJ];
+axpy_scale_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict__ h2,
+                  const double* __restrict__ hn, const T* __restrict__ w, T* __restrict__ vout, size_t n) {
+    T hc[NJ];
 #pragma unroll
-    for (int j = 0; j < NJ; ++j) hc[j] = __ldg(h2 + j);
-    const double inv = 1.0 / *hn;
+    for (int j = 0; j < NJ; ++j) hc[j] = T(__ldg(h2 + j));
+    const T inv = T(1.0 / *hn);
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
          idx += (size_t)gridDim.x * blockDim.x) {
-        double x = w[idx];
+        T x = w[idx];
 #pragma unroll
         for (int j = 0; j < NJ; ++j) x -= hc[j] * V[(size_t)j * ldv + idx];
         vout[idx] = x * inv;
     }
 }
-
-template <int NJ>
-cudaError_t cgs2_tail_launch(const double* V, size_t ldv, const double* h1, double* w, size_t n,
-                             double* scratch, double* h2, double* nw1, double* hn, double* vout,
-                             cudaStream_t s);
 
 int stream_grid(size_t n) {
     size_t b = (n + 255) / 256;
@@ -198,11 +215,10 @@ int stream_grid(size_t n) {
     return b > 0 ? (int)b : 1;
 }
 
-template <int NF>
-cudaError_t spmv_launch(int n_edges, const double* Stil, const int* Scol, const double* x, double* y,
-                        cudaStream_t s) {
+template <int NF, typename T>
+cudaError_t spmv_launch(int n_edges, const T* Stil, const int* Scol, const T* x, T* y, cudaStream_t s) {
     constexpr int EPB = 256 / NF;
-    spmv_pre_kernel<NF><<<(n_edges + EPB - 1) / EPB, EPB * NF, 0, s>>>(n_edges, Stil, Scol, x, y);
+    spmv_pre_kernel<NF, T><<<(n_edges + EPB - 1) / EPB, EPB * NF, 0, s>>>(n_edges, Stil, Scol, x, y);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -215,11 +231,10 @@ cudaError_t block_diag_launch(int n_edges, const double* Bd, const double* x, do
     return cudaGetLastError();
 }
 
-template <int NJ>
-cudaError_t cgs2_tail_launch(const double* V, size_t ldv, const double* h1, double* w, size_t n,
-                             double* scratch, double* h2, double* nw1, double* hn, double* vout,
-                             cudaStream_t s) {
-    axpy_dot_kernel<NJ><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, h1, w, n, scratch, NJ + 1);
+template <int NJ, typename T>
+cudaError_t cgs2_tail_launch(const T* V, size_t ldv, const double* h1, T* w, size_t n, double* scratch,
+                             double* h2, double* nw1, double* hn, T* vout, cudaStream_t s) {
+    axpy_dot_kernel<NJ, T><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, h1, w, n, scratch, NJ + 1);
     count_launches(1);
     // scratch holds [blk][NJ + 1]: the first NJ columns reduce to h2, the last to ||w1||^2
     multidot_final_kernel<<<(NJ + 1 + 7) / 8, 256, 0, s>>>(scratch, kDotBlocks, NJ + 1, NJ, h2);
@@ -228,7 +243,48 @@ cudaError_t cgs2_tail_launch(const double* V, size_t ldv, const double* h1, doub
     count_launches(1);
     finish_norm_kernel<<<1, 1, 0, s>>>(h2, NJ, nw1, hn);
     count_launches(1);
-    axpy_scale_kernel<NJ><<<stream_grid(n), 256, 0, s>>>(V, ldv, h2, hn, w, vout, n);
+    axpy_scale_kernel<NJ, T><<<stream_grid(n), 256, 0, s>>>(V, ldv, h2, hn, w, vout, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t cgs2_tail_dispatch(const T* V, size_t ldv, int nv, const double* h1, T* w, size_t n,
+                               double* scratch, double* h2, double* nw1, double* hn, T* vout,
+                               cudaStream_t s) {
+    switch (nv) {
+#define CASE(J) case J: return cgs2_tail_launch<J, T>(V, ldv, h1, w, n, scratch, h2, nw1, hn, vout, s);
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
+        CASE(12) CASE(13) CASE(14) CASE(15) CASE(16) CASE(17) CASE(18) CASE(19) CASE(20) CASE(21)
+        CASE(22) CASE(23) CASE(24) CASE(25) CASE(26) CASE(27) CASE(28) CASE(29) CASE(30) CASE(31)
+        CASE(32)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+cudaError_t spmv_dispatch(const Geom& g, const T* Stil, const int* Scol, const T* x, T* y, cudaStream_t s) {
+    switch (g.P) {
+        case 2: return spmv_launch<6, T>(g.n_edges, Stil, Scol, x, y, s);
+        case 3: return spmv_launch<9, T>(g.n_edges, Stil, Scol, x, y, s);
+        case 4: return spmv_launch<12, T>(g.n_edges, Stil, Scol, x, y, s);
+        case 5: return spmv_launch<15, T>(g.n_edges, Stil, Scol, x, y, s);
+        case 6: return spmv_launch<18, T>(g.n_edges, Stil, Scol, x, y, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+cudaError_t multidot_impl(const T* V, size_t ldv, int nv, const T* w, size_t n, double* scratch, double* out,
+                          cudaStream_t s) {
+    for (int j0 = 0; j0 < nv; j0 += kDotChunk) {
+        const int nj = nv - j0 < kDotChunk ? nv - j0 : kDotChunk;
+        multidot_partial_kernel<kDotChunk, T><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, j0, nj, w, n,
+                                                                                  scratch, nv);
+        count_launches(1);
+    }
+    multidot_final_kernel<<<(nv + 7) / 8, 256, 0, s>>>(scratch, kDotBlocks, nv, nv, out);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -240,27 +296,23 @@ int cgs2_max_vectors() { return 32; }
 cudaError_t launch_cgs2_tail(const double* V, size_t ldv, int nv, const double* h1, double* w, size_t n,
                              double* scratch, double* h2, double* nw1, double* hn, double* vout,
                              cudaStream_t s) {
-    switch (nv) {
-#define CASE(J) case J: return cgs2_tail_launch<J>(V, ldv, h1, w, n, scratch, h2, nw1, hn, vout, s);
-        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
-        CASE(12) CASE(13) CASE(14) CASE(15) CASE(16) CASE(17) CASE(18) CASE(19) CASE(20) CASE(21)
-        CASE(22) CASE(23) CASE(24) CASE(25) CASE(26) CASE(27) CASE(28) CASE(29) CASE(30) CASE(31)
-        CASE(32)
-#undef CASE
-        default: return cudaErrorInvalidValue;
-    }
+    return cgs2_tail_dispatch<double>(V, ldv, nv, h1, w, n, scratch, h2, nw1, hn, vout, s);
+}
+
+cudaError_t launch_cgs2_tail(const float* V, size_t ldv, int nv, const double* h1, float* w, size_t n,
+                             double* scratch, double* h2, double* nw1, double* hn, float* vout,
+                             cudaStream_t s) {
+    return cgs2_tail_dispatch<float>(V, ldv, nv, h1, w, n, scratch, h2, nw1, hn, vout, s);
 }
 
 cudaError_t launch_spmv_pre(const Geom& g, const double* Stil, const int* Scol, const double* x,
                             double* y, cudaStream_t s) {
-    switch (g.P) {
-        case 2: return spmv_launch<6>(g.n_edges, Stil, Scol, x, y, s);
-        case 3: return spmv_launch<9>(g.n_edges, Stil, Scol, x, y, s);
-        case 4: return spmv_launch<12>(g.n_edges, Stil, Scol, x, y, s);
-        case 5: return spmv_launch<15>(g.n_edges, Stil, Scol, x, y, s);
-        case 6: return spmv_launch<18>(g.n_edges, Stil, Scol, x, y, s);
-        default: return cudaErrorInvalidValue;
-    }
+    return spmv_dispatch<double>(g, Stil, Scol, x, y, s);
+}
+
+cudaError_t launch_spmv_pre(const Geom& g, const float* Stil, const int* Scol, const float* x,
+                            float* y, cudaStream_t s) {
+    return spmv_dispatch<float>(g, Stil, Scol, x, y, s);
 }
 
 cudaError_t launch_block_diag(const Geom& g, const double* Bd, const double* x, double* y,
@@ -279,27 +331,44 @@ size_t dot_scratch_doubles(int nv) { return (size_t)kDotBlocks * (size_t)nv; }
 
 cudaError_t launch_multidot(const double* V, size_t ldv, int nv, const double* w, size_t n,
                             double* scratch, double* out, cudaStream_t s) {
-    for (int j0 = 0; j0 < nv; j0 += kDotChunk) {
-        const int nj = nv - j0 < kDotChunk ? nv - j0 : kDotChunk;
-        multidot_partial_kernel<kDotChunk><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, j0, nj, w, n,
-                                                                               scratch, nv);
-        count_launches(1);
-    }
-    multidot_final_kernel<<<(nv + 7) / 8, 256, 0, s>>>(scratch, kDotBlocks, nv, nv, out);
-    count_launches(1);
-    return cudaGetLastError();
+    return multidot_impl<double>(V, ldv, nv, w, n, scratch, out, s);
+}
+
+cudaError_t launch_multidot(const float* V, size_t ldv, int nv, const float* w, size_t n,
+                            double* scratch, double* out, cudaStream_t s) {
+    return multidot_impl<float>(V, ldv, nv, w, n, scratch, out, s);
 }
 
 cudaError_t launch_multiaxpy(const double* V, size_t ldv, int nv, const double* coef, double sign,
                              double* w, size_t n, cudaStream_t s) {
-    multiaxpy_kernel<<<stream_grid(n), 256, 0, s>>>(V, ldv, nv, coef, sign, w, n);
+    multiaxpy_kernel<double><<<stream_grid(n), 256, 0, s>>>(V, ldv, nv, coef, sign, w, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_f32_into_f64(const float* V, size_t ldv, int nv, const double* coef, double* x,
+                                     size_t n, cudaStream_t s) {
+    axpy_f32_into_f64_kernel<<<stream_grid(n), 256, 0, s>>>(V, ldv, nv, coef, x, n);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scale_by_rnorm(const double* w, const double* nrm2, double* v, size_t n,
                                   cudaStream_t s) {
-    scale_kernel<<<stream_grid(n), 256, 0, s>>>(w, nrm2, v, n);
+    scale_kernel<double><<<stream_grid(n), 256, 0, s>>>(w, nrm2, v, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_by_rnorm(const double* w, const double* nrm2, float* v, size_t n,
+                                  cudaStream_t s) {
+    scale_kernel<float><<<stream_grid(n), 256, 0, s>>>(w, nrm2, v, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const double* a, float* b, size_t n, cudaStream_t s) {
+    to_f32_kernel<<<stream_grid(n), 256, 0, s>>>(a, b, n);
     count_launches(1);
     return cudaGetLastError();
 }

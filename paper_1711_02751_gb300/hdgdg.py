@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(_HERE, "libhdgdg.so")
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ENONFINITE, ESTATE = range(7)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTCONVERGED", "ENONFINITE", "ESTATE"]
 SCHEMES = {"ars2": 0, "ars3": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1}
 
 EXPORTS = ["hdgdg_bytes_required", "hdgdg_node_coords", "hdgdg_create", "hdgdg_set_state",
            "hdgdg_step", "hdgdg_get_state", "hdgdg_get_stats", "hdgdg_last_error", "hdgdg_destroy",
@@ -91,8 +92,8 @@ def _f64(a, shape=None):
 
 
 def make_config(N, k, dt, g=1.0, H0=1.0, scheme="ars2", krylov_rtol=0.0, krylov_restart=0,
-                krylov_maxit=0, linear_only=False):
-    return Config(int(N), int(k), float(g), float(H0), SCHEMES[scheme], float(dt), 0,
+                krylov_maxit=0, linear_only=False, precision="fp64"):
+    return Config(int(N), int(k), float(g), float(H0), SCHEMES[scheme], float(dt), PRECISIONS[precision],
                   float(krylov_rtol), int(krylov_restart), int(krylov_maxit), int(bool(linear_only)))
 
 
@@ -123,12 +124,12 @@ class Sim:
     """One simulation handle (hdgdg_create ... hdgdg_destroy)."""
 
     def __init__(self, N, k, dt, bottom=None, g=1.0, H0=1.0, scheme="ars2", stream=None,
-                 krylov_rtol=0.0, krylov_restart=0, krylov_maxit=0, linear_only=False):
+                 krylov_rtol=0.0, krylov_restart=0, krylov_maxit=0, linear_only=False, precision="fp64"):
         self.N, self.k, self.P = int(N), int(k), int(k) + 1
         self.n_el, self.Np = self.N * self.N, self.P * self.P
         self.n_edges = 2 * self.n_el
         self.cfg = make_config(N, k, dt, g, H0, scheme, krylov_rtol, krylov_restart, krylov_maxit,
-                               linear_only)
+                               linear_only, precision)
         self._h = ctypes.c_void_p(None)
         b = None if bottom is None else _f64(bottom, (self.n_el, self.Np))
         st = lib().hdgdg_create(ctypes.byref(self.cfg), None if b is None else _ptr(b),
