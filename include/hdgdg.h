@@ -180,6 +180,24 @@ hdgdg_status hdgdg_kernel_time(hdgdg_sim* sim, int cls, double* total_ms, long l
  * the denominator of ALU-bound roofline fractions.  ECUDA on failure. */
 hdgdg_status hdgdg_measure_fp64_tflops(double* tflops);
 
+/* ---- allocation-free entry point ------------------------------------------------- */
+
+/* Mass sum_e J sum_ij w_i w_j phi_eta of a state, like the mass of hdgdg_get_stats, for
+ * callers that cannot allocate device memory (code inside another framework's fixed memory
+ * pool, a real-time loop that must stay out of the CUDA allocator, a host callback).  The
+ * paper has no counterpart: it is a service of this library.
+ * d_phi_eta: device array [n_el][(k+1)^2] (phi_eta = g (h - B)); d_mass: one device double,
+ * written on the given stream (NULL = legacy default stream); both belong to the caller.
+ * The partial sums live in a fixed array of the library's static device memory (8 MiB on
+ * every GPU that loads the library, held until the process exits), so the call allocates
+ * nothing; its first call on a device looks the array's address up once, and that first
+ * call should come before any stream capture.  The array is shared by all calls on a device
+ * and keeps the last call's contents; calls that overlap on the GPU race on it, so issue
+ * them on one stream or serialise them.  EINVAL for n_side * n_side > 2^20 elements (the
+ * array's capacity), a bad degree or NULL pointers; ECUDA if a launch fails. */
+hdgdg_status hdgdg_mass_noalloc(int n_side, int degree_k, const double* d_phi_eta, double* d_mass,
+                                void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -187,6 +187,15 @@ void scheme_tables(int scheme, double A[kMaxStages][kMaxStages], double At[kMaxS
 
 }  // namespace
 
+namespace hdgdg {
+Geom host_geom(int N, int k) {
+    hdgdg_config c{};
+    c.n_side = N;
+    c.degree_k = k;
+    return make_geom(&c, nullptr);
+}
+}  // namespace hdgdg
+
 struct hdgdg_sim {
     hdgdg_config cfg;
     Plan plan;

@@ -66,6 +66,9 @@ __host__ __device__ inline void edge_sides(int r, int N, int* em, int* fm, int* 
     else { const int e = r - N * N; *em = e; *fm = 3; *ep = neighbour(e, 3, N); *fp = 2; }
 }
 
+// Host-built mesh and GLL tables of an N x N, degree-k mesh (no GPU call).
+Geom host_geom(int N, int k);
+
 // Kernels launched by this library since load (every launcher adds its own launches).
 long long launches_total();
 void count_launches(int n);

@@ -19,7 +19,8 @@ PRECISIONS = {"fp64": 0, "mixed": 1}
 EXPORTS = ["hdgdg_bytes_required", "hdgdg_node_coords", "hdgdg_create", "hdgdg_set_state",
            "hdgdg_step", "hdgdg_get_state", "hdgdg_get_stats", "hdgdg_last_error", "hdgdg_destroy",
            "hdgdg_eval_nl", "hdgdg_condense_rhs", "hdgdg_trace_apply", "hdgdg_stage_solve",
-           "hdgdg_measure_fp64_tflops", "hdgdg_set_kernel_timing", "hdgdg_kernel_time"]
+           "hdgdg_measure_fp64_tflops", "hdgdg_set_kernel_timing", "hdgdg_kernel_time",
+           "hdgdg_mass_noalloc"]
 KERNEL_CLASSES = ["spmv", "ortho", "condense", "recover", "dg", "combine"]
 
 
@@ -74,6 +75,8 @@ def lib():
         L.hdgdg_measure_fp64_tflops.argtypes = [_P]
         L.hdgdg_set_kernel_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.hdgdg_kernel_time.argtypes = [ctypes.c_void_p, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_longlong)]
+        L.hdgdg_mass_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
         _lib = L
@@ -110,6 +113,12 @@ def node_coords(N, k):
     if st != OK:
         raise HdgdgError(st, "node_coords")
     return x, y
+
+
+def mass_noalloc(n_side, degree_k, phi_eta_dev_ptr, mass_dev_ptr, stream=None):
+    """hdgdg_mass_noalloc on caller-owned device buffers (raw addresses); returns the status."""
+    return lib().hdgdg_mass_noalloc(int(n_side), int(degree_k), ctypes.c_void_p(phi_eta_dev_ptr),
+                                    ctypes.c_void_p(mass_dev_ptr), ctypes.c_void_p(stream) if stream else None)
 
 
 def measure_fp64_tflops():
