@@ -62,17 +62,15 @@ def _workload_state(name, x, y, rank):
 
 # ---- oracle timing (the CPU baseline and the reference arm) ----------------------------------
 def _oracle_sample(n_steps, warmup):
-    """Time the FP64 oracle on a bounded sample: the large512 recipe on 64 x 64, k = 3, with dt
-    scaled to keep the same gravity Courant number (dt * 512 / 64), scipy GMRES trace solve."""
+    """Time the FP64 oracle on a bounded sample: the large512 recipe on 64 x 64, k = 3, with its
+    own advective dt (8x the 512x512 one: the same Courant numbers), scipy GMRES trace solve."""
     from oracle import imex, swe
     from paper_1711_02751_gb300 import workloads as W
     N, k = CPU_SAMPLE
     m = swe.Mesh(N, k)
     x, y = m.x.reshape(m.n_el, -1), m.y.reshape(m.n_el, -1)
     h, hu, hv, b = W.large_state(x, y)
-    xl, _ = _library_free_coords(512, 3)
-    dt_full = W.advective_dt(xl, np.ones((1, 16)), np.zeros((1, 16)), np.zeros((1, 16)), 512)
-    dt = dt_full * 512 / N
+    dt = W.advective_dt(x, h, hu, hv, N)      # = the 512x512 dt * 512 / 64: same Courant numbers
     q, phiB = swe.to_state(h, hu, hv, b, W.G, W.H0)
     st = imex.Stepper(m, phiB, dt, solver="gmres", rtol=1e-13)
     for _ in range(warmup):
@@ -84,14 +82,6 @@ def _oracle_sample(n_steps, warmup):
         times.append(time.perf_counter() - t0)
     dof = 3 * m.n_el * m.P ** 2
     return dof, times
-
-
-def _library_free_coords(N, k):
-    """x coordinates of one element row from the oracle's GLL tables (oracle-side only)."""
-    from oracle.gll import gll_nodes_weights
-    xi, _ = gll_nodes_weights(k)
-    x = np.broadcast_to(((1.0 + xi) / 2.0) / N, (k + 1, k + 1)).reshape(1, -1)
-    return x, None
 
 
 def _cpu_baseline_child(args):
@@ -114,8 +104,8 @@ def cpu_baseline(sample_steps=5):
     dof, times = _run_cpu_child(sample_steps)
     value = dof * len(times) / sum(times)
     return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 numpy oracle, large512 recipe on 64x64 k=3 (DOF {dof}), dt*512/64 "
-                      f"(same gravity Courant), scipy GMRES rtol 1e-13, {len(times)} steps timed "
+            "sample": f"FP64 numpy oracle, large512 recipe on 64x64 k=3 (DOF {dof}), its own advective dt "
+                      f"(same Courant numbers), scipy GMRES rtol 1e-13, {len(times)} steps timed "
                       f"after 1 warm-up, setup excluded, 1 thread"}
 
 
@@ -133,7 +123,7 @@ def reference_arm(args, rank, world):
             "data": "synthetic",
             "config": {"workload": f"{args.workload} (oracle sample: 64x64 k=3)", "sample": "bounded"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "large512 recipe on 64x64 k=3, dt*512/64, one oracle step per step"},
+                             "sample": "large512 recipe on 64x64 k=3, own advective dt (same Courant numbers), one oracle step per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -415,7 +405,7 @@ def main():
             "dtype": "f64" if head == "fp64" else "f64+f32 (FP32 Krylov cycles, FP64 refinement and local ops)",
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: periodic {N}x{N} quads, k={k}, ARS2, "
-                                   f"dt={dt:.6g} (advective CFL 0.5)", "form": head,
+                                   f"dt={dt:.6g} (advective CFL 0.5: 0.5 h/((2k+1) 2max|u|))", "form": head,
                        "dof": dof, "parallelism": "replicas" if world > 1 else "single",
                        "gmres_restart": args.restart or 20,
                        "l2": "inputs larger than L2 (A^-1 and trace matrix are GBs)"},

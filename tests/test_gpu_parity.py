@@ -148,7 +148,7 @@ def test_nonlinear_standing_wave_hundred_steps():
     assert max(_rel(m, qa, qo)) <= 1e-9
 
 
-@pytest.mark.parametrize("N,k,steps", [(16, 3, 1), (16, 3, 10), (9, 4, 3), (12, 2, 5)])
+@pytest.mark.parametrize("N,k,steps", [(16, 3, 1), (16, 3, 10), (9, 4, 3), (12, 2, 5), (32, 3, 2)])
 def test_variable_bottom_steps(N, k, steps):
     m, qa, qo, _ = _run_pair(N, k, "large", steps)
     assert max(_rel(m, qa, qo)) <= (1e-11 if steps == 1 else 1e-10)

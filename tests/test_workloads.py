@@ -40,14 +40,24 @@ def test_courant_definition_reproduces_printed_pairs():
 
 
 def test_advective_dt_of_the_two_workloads():
-    for N, k, expect in [(8, 2, 0.625), (512, 3, 0.5 * (1 / 1024) * (1 - 1 / math.sqrt(5)) / 0.05)]:
-        x, _ = gll_nodes_weights(k)
-        ex = np.arange(N * N) % N
-        xs = (ex[:, None, None] + (1 + x[None, None, :]) / 2) / N
-        xs = np.broadcast_to(xs, (N * N, k + 1, k + 1)).reshape(N * N, -1)
-        h = np.ones_like(xs)
-        z = np.zeros_like(xs)
-        assert abs(W.advective_dt(xs, h, z, z, N) - expect) < 1e-12 * expect
+    """dt = 0.5 h / ((2k+1) * 2 max|u|), floored speed 0.05 at rest: bump8 0.25, large512 with
+    its 0.05 peak speed 0.5 / (512 * 7 * 0.1)."""
+    for N, k, umax, expect in [(8, 2, 0.0, 0.5 / (8 * 5 * 0.05)), (512, 3, 0.05, 0.5 / (512 * 7 * 0.1))]:
+        shape = (4, (k + 1) ** 2)
+        h = np.ones(shape)
+        hu = np.full(shape, umax)
+        z = np.zeros(shape)
+        assert abs(W.advective_dt(z, h, hu, z, N) - expect) < 1e-12 * expect
+
+
+def test_explicit_step_stays_below_the_papers_explicit_limit():
+    """In the paper's Courant definition (smallest GLL gap), the explicit part's speed 2|u| and
+    this dt give 0.26 on large512: below the Cr ~ 0.28 at which the paper reports its explicit
+    RK2 DG blowing up (Sec. 7.1)."""
+    k, N = 3, 512
+    dx_min = _dx_min(1.0, N, k)
+    dt = W.advective_dt(np.zeros((1, 16)), np.ones((1, 16)), np.full((1, 16), 0.05), np.zeros((1, 16)), N)
+    assert W.courant(dx_min, dt, 0.1) < 0.28
 
 
 def test_large_state_is_seeded_and_bounded():
