@@ -71,7 +71,7 @@ typedef struct {
                             (FP64) or 1e-10 (MIXED, FP64 residual of the refinement loop).
                             A restart cycle that fails to halve a true residual already below
                             1e-12 ||g|| ends the solve as converged (FP64 rounding floor). */
-    int krylov_restart;  /* GMRES(m) restart length m <= 31; <= 0 selects 20 */
+    int krylov_restart;  /* GMRES(m) restart length m <= 31; <= 0 selects 8 */
     int krylov_maxit;    /* cap on GMRES iterations per stage solve; <= 0 selects 2000 */
     int linear_only;     /* 1: drop NL (linear gravity-wave runs); 0: full method */
 } hdgdg_config;

@@ -45,7 +45,7 @@ bool valid(const hdgdg_config* c) {
            c->krylov_restart <= kMaxRestart;
 }
 
-int restart_of(const hdgdg_config* c) { return c->krylov_restart > 0 ? c->krylov_restart : 20; }
+int restart_of(const hdgdg_config* c) { return c->krylov_restart > 0 ? c->krylov_restart : 8; }
 
 Plan make_plan(const hdgdg_config* c) {
     Plan p;
@@ -74,7 +74,7 @@ Plan make_plan(const hdgdg_config* c) {
         b += ((size_t)p.m + 1) * p.nt * d;                    // FP64 Krylov basis
     }
     b += (dot_scratch_doubles(p.m + 2) + mass_scratch_doubles() + 4 * (size_t)(p.m + 2) + 16) * d;
-    b += 64;                                                  // flags
+    b += 64 + sizeof(GmresCtl);                               // flags, GMRES control block
     p.persistent = b;
     p.setup_temp = n_el * (size_t)p.NT * p.NT * d + n_edges * 7 * (size_t)p.NF * p.NF * d;
     return p;
@@ -215,6 +215,7 @@ struct hdgdg_sim {
     double *gvec = nullptr, *xt = nullptr, *lam = nullptr, *w = nullptr, *V = nullptr;
     float *Stil32 = nullptr, *V32 = nullptr, *w32 = nullptr;   // mixed precision only
     double *red = nullptr, *mred = nullptr, *dvals = nullptr;
+    GmresCtl* ctl = nullptr;
     unsigned* flags = nullptr;
     double* hbuf = nullptr;   // pinned host scratch
     // run state
@@ -223,7 +224,7 @@ struct hdgdg_sim {
     // per-kernel-class timers
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
-    struct Pending { cudaEvent_t a, b; int cls; };
+    struct Pending { cudaEvent_t a, b; int cls, slot; };
     std::vector<Pending> pending;
     double kt_ms[HDGDG_KT_COUNT] = {};
     long long kt_n[HDGDG_KT_COUNT] = {};
@@ -286,12 +287,14 @@ cudaEvent_t take_event(hdgdg_sim* sim) {
     return e;
 }
 
-// Bracket a launch group of class cls with events (no-op unless timing is on).
+// Bracket a launch group of class cls with events (no-op unless timing is on).  slot >= 0
+// tags groups enqueued speculatively in a GMRES cycle: the ones at or after the cycle's
+// actual length returned at once and are dropped when the timers are read.
 struct TimedGroup {
     hdgdg_sim* sim;
-    int cls;
+    int cls, slot;
     cudaEvent_t a = nullptr;
-    TimedGroup(hdgdg_sim* s, int c) : sim(s), cls(c) {
+    TimedGroup(hdgdg_sim* s, int c, int sl = -1) : sim(s), cls(c), slot(sl) {
         if (sim->timing && (a = take_event(sim))) cudaEventRecord(a, sim->stream);
     }
     ~TimedGroup() {
@@ -299,14 +302,14 @@ struct TimedGroup {
         cudaEvent_t b = take_event(sim);
         if (!b) { sim->ev_pool.push_back(a); return; }
         cudaEventRecord(b, sim->stream);
-        sim->pending.push_back({a, b, cls});
+        sim->pending.push_back({a, b, cls, slot});
     }
 };
 
-void flush_timers(hdgdg_sim* sim) {
+void flush_timers(hdgdg_sim* sim, int slot_limit = 1 << 30) {
     for (auto& p : sim->pending) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+        if (p.slot < slot_limit && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
             sim->kt_ms[p.cls] += ms;
             sim->kt_n[p.cls] += 1;
         }
@@ -316,9 +319,9 @@ void flush_timers(hdgdg_sim* sim) {
     sim->pending.clear();
 }
 
-hdgdg_status sync(hdgdg_sim* sim) {
+hdgdg_status sync(hdgdg_sim* sim, int slot_limit = 1 << 30) {
     CU(cudaStreamSynchronize(sim->stream));
-    flush_timers(sim);
+    flush_timers(sim, slot_limit);
     return HDGDG_OK;
 }
 
@@ -331,127 +334,33 @@ hdgdg_status norm2_to_host(hdgdg_sim* sim, const double* v, double* out) {
     return HDGDG_OK;
 }
 
-// Right-preconditioned GMRES(m) with CGS2 on S~ x~ = g, then qhat = M^{-1} x~.
-hdgdg_status gmres(hdgdg_sim* sim, const double* g, double* qhat, int* iters, double* relres) {
+// Right-preconditioned GMRES(m) on S~ x~ = g with classical Gram-Schmidt applied twice, then
+// qhat = M^{-1} x~.  The Givens rotations, the residual estimate and the stop test run on the
+// device (GmresCtl), so a whole restart cycle is queued at once and the host waits once per
+// cycle: the loop kernels after the cycle's last useful iteration return immediately.
+// T = double: the FP64 form.  T = float (mixed form): the cycle runs on the FP32 copy of S~
+// and FP32 basis vectors; every cycle starts from the true residual r = g - S~ x~ computed in
+// FP64 and adds its correction to the FP64 x~ (iterative refinement).
+template <typename T>
+hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* iters, double* relres) {
+    constexpr bool kMixed = sizeof(T) == sizeof(float);
     const size_t n = sim->plan.nt;
     const int m = sim->plan.m;
-    const double rtol = sim->cfg.krylov_rtol > 0.0 ? sim->cfg.krylov_rtol : 1e-15;
-    // A restart cycle that cannot halve the true residual once it is already below
-    // kStagnation * ||g|| has reached the rounding floor of the FP64 residual: accept it.
-    constexpr double kStagnation = 1e-12;
+    const double rtol = sim->cfg.krylov_rtol > 0.0 ? sim->cfg.krylov_rtol : (kMixed ? 1e-10 : 1e-15);
     const int maxit = sim->cfg.krylov_maxit > 0 ? sim->cfg.krylov_maxit : 2000;
-    cudaStream_t st = sim->stream;
-    *iters = 0;
-    double bn2;
-    TRY(norm2_to_host(sim, g, &bn2));
-    if (!std::isfinite(bn2)) return fail(sim, HDGDG_ENONFINITE, "non-finite trace right-hand side");
-    if (bn2 == 0.0) {
-        CU(cudaMemsetAsync(qhat, 0, n * sizeof(double), st));
-        *relres = 0.0;
-        return HDGDG_OK;
-    }
-    const double bnorm = std::sqrt(bn2), tol = rtol * bnorm;
-    CU(cudaMemsetAsync(sim->xt, 0, n * sizeof(double), st));
-    CU(cudaMemcpyAsync(sim->w, g, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), sv(m + 1), y(m);
-    auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
-    double rnorm = bnorm;
-    CU(launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st));
-    int total = 0;
-    while (true) {
-        CU(launch_scale_by_rnorm(sim->w, dv_nrm(sim), sim->V, n, st));
-        std::fill(sv.begin(), sv.end(), 0.0);
-        sv[0] = rnorm;
-        int jend = 0;
-        for (int j = 0; j < m; ++j) {
-            double* Vj = sim->V + (size_t)j * n;
-            {
-                TimedGroup tg(sim, HDGDG_KT_SPMV);
-                CU(launch_spmv_pre(sim->g, sim->Stil, sim->Scol, Vj, sim->w, st));
-            }
-            {
-                // classical Gram-Schmidt, twice: h1 = V^T w, w1 = w - V h1, h2 = V^T w1,
-                // V_{j+1} = (w1 - V h2) / ||w1 - V h2||; the column of H is h1 + h2
-                TimedGroup tg(sim, HDGDG_KT_ORTHO);
-                CU(launch_multidot(sim->V, n, j + 1, sim->w, n, sim->red, dv_h1(sim), st));
-                CU(launch_cgs2_tail(sim->V, n, j + 1, dv_h1(sim), sim->w, n, sim->red, dv_h2(sim),
-                                    dv_nrm(sim), dv_nrm(sim) + 1, sim->V + (size_t)(j + 1) * n, st));
-            }
-            CU(cudaMemcpyAsync(sim->hbuf, sim->dvals, (2 * (m + 2) + 2) * sizeof(double),
-                               cudaMemcpyDeviceToHost, st));
-            TRY(sync(sim));
-            const double* h1 = sim->hbuf;
-            const double* h2 = sim->hbuf + (m + 2);
-            for (int i = 0; i <= j; ++i) Hij(i, j) = h1[i] + h2[i];
-            Hij(j + 1, j) = sim->hbuf[2 * (m + 2) + 1];
-            for (int i = 0; i < j; ++i) {
-                const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
-                Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
-                Hij(i, j) = t;
-            }
-            const double den = std::hypot(Hij(j, j), Hij(j + 1, j));
-            cs[j] = den > 0.0 ? Hij(j, j) / den : 1.0;
-            sn[j] = den > 0.0 ? Hij(j + 1, j) / den : 0.0;
-            const double hsub = Hij(j + 1, j);
-            Hij(j, j) = den;
-            Hij(j + 1, j) = 0.0;
-            sv[j + 1] = -sn[j] * sv[j];
-            sv[j] = cs[j] * sv[j];
-            ++total;
-            jend = j + 1;
-            if (!std::isfinite(sv[j + 1]))
-                return fail(sim, HDGDG_ENONFINITE, "non-finite GMRES residual at iteration %d", total);
-            if (std::fabs(sv[j + 1]) <= tol || total >= maxit || hsub == 0.0) break;
-        }
-        for (int i = jend - 1; i >= 0; --i) {
-            double acc = sv[i];
-            for (int k = i + 1; k < jend; ++k) acc -= Hij(i, k) * y[k];
-            y[i] = acc / Hij(i, i);
-        }
-        CU(cudaMemcpyAsync(dv_coef(sim), y.data(), jend * sizeof(double), cudaMemcpyHostToDevice, st));
-        CU(launch_multiaxpy(sim->V, n, jend, dv_coef(sim), -1.0, sim->xt, n, st));
-        // true residual r = g - S~ x~
-        CU(launch_spmv_pre(sim->g, sim->Stil, sim->Scol, sim->xt, sim->w, st));
-        CombineTerms t{};
-        t.n = 1;
-        t.X[0] = sim->w;
-        t.c[0] = -1.0;
-        CU(launch_combine(n, g, t, sim->w, nullptr, st));
-        double rn2;
-        TRY(norm2_to_host(sim, sim->w, &rn2));   // also leaves ||r||^2 in dv_nrm for the restart
-        const double prev = rnorm;
-        rnorm = std::sqrt(rn2);
-        if (rnorm <= tol) break;
-        if (rnorm <= kStagnation * bnorm && rnorm > 0.5 * prev) break;
-        if (total >= maxit) {
-            *iters = total;
-            *relres = rnorm / bnorm;
-            sim->stats.last_krylov_iterations = total;
-            sim->stats.last_rel_residual = *relres;
-            return fail(sim, HDGDG_ENOTCONVERGED,
-                        "GMRES: relative residual %.3e > %.3e after %d iterations", rnorm / bnorm,
-                        rtol, total);
-        }
-    }
-    CU(launch_block_diag(sim->g, sim->Minv, sim->xt, qhat, st));
-    *iters = total;
-    *relres = rnorm / bnorm;
-    sim->stats.last_krylov_iterations = total;
-    sim->stats.last_rel_residual = *relres;
-    sim->stats.krylov_iterations += total;
-    return HDGDG_OK;
-}
-
-// Mixed precision: FP32 GMRES(m) cycles on S~32, each started from the FP64 true residual
-// r = g - S~ x~ (iterative refinement); x~ accumulated in FP64; qhat = M^{-1} x~.
-hdgdg_status gmres_mixed(hdgdg_sim* sim, const double* g, double* qhat, int* iters, double* relres) {
-    const size_t n = sim->plan.nt;
-    const int m = sim->plan.m;
-    const double rtol = sim->cfg.krylov_rtol > 0.0 ? sim->cfg.krylov_rtol : 1e-10;
-    const int maxit = sim->cfg.krylov_maxit > 0 ? sim->cfg.krylov_maxit : 2000;
-    constexpr double kInner = 1e-6;        // FP32 cycle stop, relative to the cycle's residual
+    // Mixed form: an FP32 cycle stops once it has reduced its starting residual 1e6 times.
+    const double inner_rel = kMixed ? 1e-6 : 0.0;
+    // A restart cycle that cannot halve a true residual already below kStagnation * ||g|| has
+    // reached the rounding floor of the FP64 residual: accept it.
     constexpr double kStagnation = 1e-12;
     cudaStream_t st = sim->stream;
+    T* V = nullptr;
+    T* w = nullptr;
+    const T* St = nullptr;
+    if constexpr (kMixed) { V = sim->V32; w = sim->w32; St = sim->Stil32; }
+    else { V = sim->V; w = sim->w; St = sim->Stil; }
+    GmresCtl* ctl = sim->ctl;
+    const int* done = &ctl->done;
     *iters = 0;
     double bn2;
     TRY(norm2_to_host(sim, g, &bn2));
@@ -465,72 +374,46 @@ hdgdg_status gmres_mixed(hdgdg_sim* sim, const double* g, double* qhat, int* ite
     CU(cudaMemsetAsync(sim->xt, 0, n * sizeof(double), st));
     CU(cudaMemcpyAsync(sim->w, g, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     CU(launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st));
-    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), sv(m + 1), y(m);
-    auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+    CU(launch_gmres_solve_init(ctl, tol, inner_rel, maxit, st));
     double rnorm = bnorm;
     int total = 0;
     while (true) {
-        CU(launch_scale_by_rnorm(sim->w, dv_nrm(sim), sim->V32, n, st));
-        std::fill(sv.begin(), sv.end(), 0.0);
-        sv[0] = 1.0;
-        int jend = 0;
+        CU(launch_gmres_cycle_init(ctl, dv_nrm(sim), st));
+        CU(launch_scale_by_rnorm(sim->w, dv_nrm(sim), V, n, st));
         for (int j = 0; j < m; ++j) {
-            float* Vj = sim->V32 + (size_t)j * n;
+            const T* Vj = V + (size_t)j * n;
             {
-                TimedGroup tg(sim, HDGDG_KT_SPMV);
-                CU(launch_spmv_pre(sim->g, sim->Stil32, sim->Scol, Vj, sim->w32, st));
+                TimedGroup tg(sim, HDGDG_KT_SPMV, j);
+                CU(launch_spmv_pre(sim->g, St, sim->Scol, Vj, w, st, done));
             }
             {
-                TimedGroup tg(sim, HDGDG_KT_ORTHO);
-                CU(launch_multidot(sim->V32, n, j + 1, sim->w32, n, sim->red, dv_h1(sim), st));
-                CU(launch_cgs2_tail(sim->V32, n, j + 1, dv_h1(sim), sim->w32, n, sim->red, dv_h2(sim),
-                                    dv_nrm(sim) + 2, dv_nrm(sim) + 1, sim->V32 + (size_t)(j + 1) * n, st));
+                TimedGroup tg(sim, HDGDG_KT_ORTHO, j);
+                CU(launch_multidot(V, n, j + 1, w, n, sim->red, dv_h1(sim), st, done));
+                CU(launch_cgs2_tail(V, n, j + 1, dv_h1(sim), w, n, sim->red, dv_h2(sim), dv_nrm(sim) + 2,
+                                    dv_nrm(sim) + 1, V + (size_t)(j + 1) * n, st, done));
+                CU(launch_gmres_arnoldi(ctl, j, m, dv_h1(sim), dv_h2(sim), dv_nrm(sim) + 1, st));
             }
-            CU(cudaMemcpyAsync(sim->hbuf, sim->dvals, (2 * (m + 2) + 2) * sizeof(double),
-                               cudaMemcpyDeviceToHost, st));
-            TRY(sync(sim));
-            const double* h1 = sim->hbuf;
-            const double* h2 = sim->hbuf + (m + 2);
-            for (int i = 0; i <= j; ++i) Hij(i, j) = h1[i] + h2[i];
-            Hij(j + 1, j) = sim->hbuf[2 * (m + 2) + 1];
-            for (int i = 0; i < j; ++i) {
-                const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
-                Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
-                Hij(i, j) = t;
-            }
-            const double den = std::hypot(Hij(j, j), Hij(j + 1, j));
-            cs[j] = den > 0.0 ? Hij(j, j) / den : 1.0;
-            sn[j] = den > 0.0 ? Hij(j + 1, j) / den : 0.0;
-            const double hsub = Hij(j + 1, j);
-            Hij(j, j) = den;
-            Hij(j + 1, j) = 0.0;
-            sv[j + 1] = -sn[j] * sv[j];
-            sv[j] = cs[j] * sv[j];
-            ++total;
-            jend = j + 1;
-            if (!std::isfinite(sv[j + 1]))
-                return fail(sim, HDGDG_ENONFINITE, "non-finite GMRES residual at iteration %d", total);
-            if (std::fabs(sv[j + 1]) <= kInner || std::fabs(sv[j + 1]) * rnorm <= tol || total >= maxit ||
-                hsub == 0.0)
-                break;
         }
-        for (int i = jend - 1; i >= 0; --i) {
-            double acc = sv[i];
-            for (int k = i + 1; k < jend; ++k) acc -= Hij(i, k) * y[k];
-            y[i] = acc / Hij(i, i);
-        }
-        for (int i = 0; i < jend; ++i) y[i] *= rnorm;
-        CU(cudaMemcpyAsync(dv_coef(sim), y.data(), jend * sizeof(double), cudaMemcpyHostToDevice, st));
-        CU(launch_axpy_f32_into_f64(sim->V32, n, jend, dv_coef(sim), sim->xt, n, st));
-        // FP64 true residual r = g - S~ x~
+        CU(launch_gmres_update(V, n, ctl, sim->xt, n, st));
+        // true residual r = g - S~ x~ in FP64
         CU(launch_spmv_pre(sim->g, sim->Stil, sim->Scol, sim->xt, sim->w, st));
         CombineTerms t{};
         t.n = 1;
         t.X[0] = sim->w;
         t.c[0] = -1.0;
         CU(launch_combine(n, g, t, sim->w, nullptr, st));
-        double rn2;
-        TRY(norm2_to_host(sim, sim->w, &rn2));   // leaves ||r||^2 in dv_nrm for the next cycle
+        CU(launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st));
+        CU(cudaMemcpyAsync(sim->hbuf, dv_nrm(sim), sizeof(double), cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(sim->hbuf + 1, &ctl->done, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        int cf[5];   // done, jend, total, maxit, status
+        std::memcpy(cf, sim->hbuf + 1, sizeof(cf));
+        flush_timers(sim, cf[1]);
+        total = cf[2];
+        if (cf[4] != 0)
+            return fail(sim, HDGDG_ENONFINITE, "non-finite GMRES residual estimate at iteration %d", total);
+        const double rn2 = sim->hbuf[0];
+        if (!std::isfinite(rn2)) return fail(sim, HDGDG_ENONFINITE, "non-finite GMRES residual");
         const double prev = rnorm;
         rnorm = std::sqrt(rn2);
         if (rnorm <= tol) break;
@@ -540,9 +423,8 @@ hdgdg_status gmres_mixed(hdgdg_sim* sim, const double* g, double* qhat, int* ite
             *relres = rnorm / bnorm;
             sim->stats.last_krylov_iterations = total;
             sim->stats.last_rel_residual = *relres;
-            return fail(sim, HDGDG_ENOTCONVERGED,
-                        "mixed GMRES: relative residual %.3e > %.3e after %d iterations", rnorm / bnorm,
-                        rtol, total);
+            return fail(sim, HDGDG_ENOTCONVERGED, "GMRES: relative residual %.3e > %.3e after %d iterations",
+                        rnorm / bnorm, rtol, total);
         }
     }
     CU(launch_block_diag(sim->g, sim->Minv, sim->xt, qhat, st));
@@ -563,8 +445,8 @@ hdgdg_status stage_solve_dev(hdgdg_sim* sim, const double* R1, double* Q, double
         TimedGroup tg(sim, HDGDG_KT_CONDENSE);
         CU(launch_condense(sim->g, sim->Ainv, R1, sim->phiB, sim->tau, sim->Z, sim->gvec, sim->stream));
     }
-    if (sim->cfg.precision == HDGDG_MIXED) TRY(gmres_mixed(sim, sim->gvec, sim->lam, its, &rr));
-    else TRY(gmres(sim, sim->gvec, sim->lam, its, &rr));
+    if (sim->cfg.precision == HDGDG_MIXED) TRY(gmres_solve<float>(sim, sim->gvec, sim->lam, its, &rr));
+    else TRY(gmres_solve<double>(sim, sim->gvec, sim->lam, its, &rr));
     {
         TimedGroup tg(sim, HDGDG_KT_RECOVER);
         CU(launch_recover(sim->g, sim->Ainv, sim->Z, R1, sim->tau, sim->lam, beta_of(sim), 1.0 / sim->a_ii,
@@ -664,6 +546,7 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
     TRY(dalloc(sim, &sim->mred, mass_scratch_doubles()));
     TRY(dalloc(sim, &sim->dvals, 4 * (size_t)(p.m + 2) + 16));
     TRY(dalloc(sim, &sim->flags, 16));
+    TRY(dalloc(sim, &sim->ctl, 1));
     CU(cudaMallocHost(&sim->hbuf, (4 * (size_t)(p.m + 2) + 16) * sizeof(double)));
     for (int i = 0; i < p.s; ++i) {
         CU(cudaMemsetAsync(sim->NLs[i], 0, 3 * p.n * sizeof(double), sim->stream));

@@ -106,10 +106,11 @@ cudaError_t launch_recover(const Geom& g, const double* Ainv, const double* Z, c
 // Krylov set on trace vectors of n = n_edges * nf values.  Overloads on the storage type:
 // double for the FP64 path, float for the inner solves of the mixed-precision path.
 // y = x + sum_slots S~ x[col]   (S~ with identity diagonal blocks)
+// done (may be NULL): device flag; the Krylov-loop kernels return at once when it is set.
 cudaError_t launch_spmv_pre(const Geom& g, const double* Stil, const int* Scol, const double* x,
-                            double* y, cudaStream_t s);
+                            double* y, cudaStream_t s, const int* done = nullptr);
 cudaError_t launch_spmv_pre(const Geom& g, const float* Stil, const int* Scol, const float* x,
-                            float* y, cudaStream_t s);
+                            float* y, cudaStream_t s, const int* done = nullptr);
 // y = B x for a block-diagonal matrix B given as [edge][col][row] blocks (FP64)
 cudaError_t launch_block_diag(const Geom& g, const double* Bd, const double* x, double* y,
                               cudaStream_t s);
@@ -117,9 +118,9 @@ cudaError_t launch_block_diag(const Geom& g, const double* Bd, const double* x, 
 // dot_scratch_doubles(nv) doubles.  Deterministic (fixed grid, fixed order).
 size_t dot_scratch_doubles(int nv);
 cudaError_t launch_multidot(const double* V, size_t ldv, int nv, const double* w, size_t n,
-                            double* scratch, double* out, cudaStream_t s);
+                            double* scratch, double* out, cudaStream_t s, const int* done = nullptr);
 cudaError_t launch_multidot(const float* V, size_t ldv, int nv, const float* w, size_t n,
-                            double* scratch, double* out, cudaStream_t s);
+                            double* scratch, double* out, cudaStream_t s, const int* done = nullptr);
 // w = w - sign * sum_j coef[j] V_j   (coef on the device)
 cudaError_t launch_multiaxpy(const double* V, size_t ldv, int nv, const double* coef, double sign,
                              double* w, size_t n, cudaStream_t s);
@@ -132,10 +133,30 @@ cudaError_t launch_axpy_f32_into_f64(const float* V, size_t ldv, int nv, const d
 int cgs2_max_vectors();
 cudaError_t launch_cgs2_tail(const double* V, size_t ldv, int nv, const double* h1, double* w, size_t n,
                              double* scratch, double* h2, double* nw1, double* hn, double* vout,
-                             cudaStream_t s);
+                             cudaStream_t s, const int* done = nullptr);
 cudaError_t launch_cgs2_tail(const float* V, size_t ldv, int nv, const double* h1, float* w, size_t n,
                              double* scratch, double* h2, double* nw1, double* hn, float* vout,
-                             cudaStream_t s);
+                             cudaStream_t s, const int* done = nullptr);
+
+// Device-resident control block of one GMRES(m) solve (m <= kM): Hessenberg matrix, Givens
+// rotations, residual estimates and the stop flags the loop kernels test.
+struct GmresCtl {
+    static constexpr int kM = 32;
+    double H[kM + 1][kM];
+    double cs[kM], sn[kM], s[kM + 1], y[kM];
+    double tol_abs;     // the solve stops when the residual estimate is <= tol_abs
+    double inner_rel;   // a cycle also stops at inner_rel * (its starting residual); 0 = off
+    double tol_cycle;
+    double rnorm;       // residual norm at the start of the current cycle
+    int done, jend, total, maxit, status;
+};
+cudaError_t launch_gmres_solve_init(GmresCtl* c, double tol_abs, double inner_rel, int maxit, cudaStream_t s);
+cudaError_t launch_gmres_cycle_init(GmresCtl* c, const double* nrm2, cudaStream_t s);
+cudaError_t launch_gmres_arnoldi(GmresCtl* c, int j, int m, const double* h1, const double* h2,
+                                 const double* hn, cudaStream_t s);
+// y = H^{-1} s, then x += V y (FP64 x; V of either type)
+cudaError_t launch_gmres_update(const double* V, size_t ldv, GmresCtl* c, double* x, size_t n, cudaStream_t s);
+cudaError_t launch_gmres_update(const float* V, size_t ldv, GmresCtl* c, double* x, size_t n, cudaStream_t s);
 // v = w / sqrt(*nrm2), w in FP64
 cudaError_t launch_scale_by_rnorm(const double* w, const double* nrm2, double* v, size_t n,
                                   cudaStream_t s);

@@ -23,7 +23,8 @@ constexpr int kDotChunk = 8;       // vectors reduced per pass over w
 template <int NF, typename T>
 __global__ void __launch_bounds__(256)
 spmv_pre_kernel(int n_edges, const T* __restrict__ Stil, const int* __restrict__ Scol,
-                const T* __restrict__ x, T* __restrict__ y) {
+                const T* __restrict__ x, T* __restrict__ y, const int* __restrict__ done) {
+    if (done && *done) return;
     constexpr int EPB = 256 / NF;
     const int le = threadIdx.x / NF, ii = threadIdx.x % NF;
     const int r = blockIdx.x * EPB + le;
@@ -67,7 +68,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <int CH, typename T>
 __global__ void __launch_bounds__(kDotThreads)
 multidot_partial_kernel(const T* __restrict__ V, size_t ldv, int j0, int nj, const T* __restrict__ w,
-                        size_t n, double* __restrict__ partial, int ldp) {
+                        size_t n, double* __restrict__ partial, int ldp, const int* __restrict__ done) {
+    if (done && *done) return;
     __shared__ double sh[CH][kDotThreads / 32];
     T acc[CH];
 #pragma unroll
@@ -95,7 +97,8 @@ multidot_partial_kernel(const T* __restrict__ V, size_t ldv, int j0, int nj, con
 
 // out[j] = sum_blk partial[blk][j]: one warp per j, fixed order
 __global__ void multidot_final_kernel(const double* __restrict__ partial, int nblk, int ldp, int nj,
-                                      double* __restrict__ out) {
+                                      double* __restrict__ out, const int* __restrict__ done) {
+    if (done && *done) return;
     const int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (j >= nj) return;
@@ -149,7 +152,8 @@ __global__ void to_f32_kernel(const double* __restrict__ a, float* __restrict__ 
 template <int NJ, typename T>
 __global__ void __launch_bounds__(kDotThreads)
 axpy_dot_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict__ h1, T* __restrict__ w,
-                size_t n, double* __restrict__ partial, int ldp) {
+                size_t n, double* __restrict__ partial, int ldp, const int* __restrict__ done) {
+    if (done && *done) return;
     __shared__ double sh[NJ + 1][kDotThreads / 32];
     T hc[NJ], acc[NJ + 1];
 #pragma unroll
@@ -185,7 +189,8 @@ axpy_dot_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict__ 
 
 // hn = sqrt(||w1||^2 - ||h2||^2), the norm of w2 = w1 - V h2 for an orthonormal V (one thread).
 __global__ void finish_norm_kernel(const double* __restrict__ h2, int nj, const double* __restrict__ nw1,
-                                   double* __restrict__ hn) {
+                                   double* __restrict__ hn, const int* __restrict__ done) {
+    if (done && *done) return;
     double s = *nw1;
     for (int j = 0; j < nj; ++j) s -= h2[j] * h2[j];
     *hn = s > 0.0 ? sqrt(s) : 0.0;
@@ -195,7 +200,9 @@ __global__ void finish_norm_kernel(const double* __restrict__ h2, int nj, const 
 template <int NJ, typename T>
 __global__ void __launch_bounds__(256)
 axpy_scale_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict__ h2,
-                  const double* __restrict__ hn, const T* __restrict__ w, T* __restrict__ vout, size_t n) {
+                  const double* __restrict__ hn, const T* __restrict__ w, T* __restrict__ vout, size_t n,
+                  const int* __restrict__ done) {
+    if (done && *done) return;
     T hc[NJ];
 #pragma unroll
     for (int j = 0; j < NJ; ++j) hc[j] = T(__ldg(h2 + j));
@@ -209,6 +216,76 @@ axpy_scale_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict_
     }
 }
 
+// ---- device-side GMRES control: one thread each -----------------------------------------
+__global__ void gmres_solve_init_kernel(GmresCtl* c, double tol_abs, double inner_rel, int maxit) {
+    c->tol_abs = tol_abs;
+    c->inner_rel = inner_rel;
+    c->maxit = maxit;
+    c->total = 0;
+    c->status = 0;
+}
+
+// Start a restart cycle from the residual whose squared norm is *nrm2.
+__global__ void gmres_cycle_init_kernel(GmresCtl* c, const double* nrm2) {
+    const double rn = sqrt(*nrm2);
+    c->rnorm = rn;
+    for (int i = 0; i <= GmresCtl::kM; ++i) c->s[i] = 0.0;
+    c->s[0] = rn;
+    c->jend = 0;
+    c->done = c->total >= c->maxit ? 1 : 0;
+    c->tol_cycle = fmax(c->tol_abs, c->inner_rel * rn);
+}
+
+// Column j of the Hessenberg matrix from the two Gram-Schmidt passes, Givens rotations, the
+// residual estimate |s_{j+1}| and the cycle's stop test.
+__global__ void gmres_arnoldi_kernel(GmresCtl* c, int j, int m, const double* __restrict__ h1,
+                                     const double* __restrict__ h2, const double* __restrict__ hn) {
+    if (c->done) return;
+    for (int i = 0; i <= j; ++i) c->H[i][j] = h1[i] + h2[i];
+    c->H[j + 1][j] = *hn;
+    for (int i = 0; i < j; ++i) {
+        const double t = c->cs[i] * c->H[i][j] + c->sn[i] * c->H[i + 1][j];
+        c->H[i + 1][j] = -c->sn[i] * c->H[i][j] + c->cs[i] * c->H[i + 1][j];
+        c->H[i][j] = t;
+    }
+    const double a = c->H[j][j], b = c->H[j + 1][j];
+    const double den = hypot(a, b);
+    const double cs = den > 0.0 ? a / den : 1.0, sn = den > 0.0 ? b / den : 0.0;
+    c->cs[j] = cs;
+    c->sn[j] = sn;
+    c->H[j][j] = den;
+    c->H[j + 1][j] = 0.0;
+    c->s[j + 1] = -sn * c->s[j];
+    c->s[j] = cs * c->s[j];
+    c->total += 1;
+    c->jend = j + 1;
+    const double est = fabs(c->s[j + 1]);
+    if (!isfinite(est)) { c->status = 1; c->done = 1; return; }
+    if (est <= c->tol_cycle || b == 0.0 || c->total >= c->maxit || j == m - 1) c->done = 1;
+}
+
+// y = H(0:jend, 0:jend)^{-1} s by back substitution.
+__global__ void gmres_solve_y_kernel(GmresCtl* c) {
+    for (int i = c->jend - 1; i >= 0; --i) {
+        double acc = c->s[i];
+        for (int k = i + 1; k < c->jend; ++k) acc -= c->H[i][k] * c->y[k];
+        c->y[i] = acc / c->H[i][i];
+    }
+}
+
+// x += sum_{j < jend} y_j V_j (FP64 accumulator for either basis type)
+template <typename T>
+__global__ void gmres_update_x_kernel(const T* __restrict__ V, size_t ldv, const GmresCtl* __restrict__ c,
+                                      double* __restrict__ x, size_t n) {
+    const int nv = c->jend;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        double acc = x[idx];
+        for (int j = 0; j < nv; ++j) acc += c->y[j] * (double)V[(size_t)j * ldv + idx];
+        x[idx] = acc;
+    }
+}
+
 int stream_grid(size_t n) {
     size_t b = (n + 255) / 256;
     if (b > 152 * 8) b = 152 * 8;
@@ -216,9 +293,10 @@ int stream_grid(size_t n) {
 }
 
 template <int NF, typename T>
-cudaError_t spmv_launch(int n_edges, const T* Stil, const int* Scol, const T* x, T* y, cudaStream_t s) {
+cudaError_t spmv_launch(int n_edges, const T* Stil, const int* Scol, const T* x, T* y, cudaStream_t s,
+                        const int* done) {
     constexpr int EPB = 256 / NF;
-    spmv_pre_kernel<NF, T><<<(n_edges + EPB - 1) / EPB, EPB * NF, 0, s>>>(n_edges, Stil, Scol, x, y);
+    spmv_pre_kernel<NF, T><<<(n_edges + EPB - 1) / EPB, EPB * NF, 0, s>>>(n_edges, Stil, Scol, x, y, done);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -233,17 +311,17 @@ cudaError_t block_diag_launch(int n_edges, const double* Bd, const double* x, do
 
 template <int NJ, typename T>
 cudaError_t cgs2_tail_launch(const T* V, size_t ldv, const double* h1, T* w, size_t n, double* scratch,
-                             double* h2, double* nw1, double* hn, T* vout, cudaStream_t s) {
-    axpy_dot_kernel<NJ, T><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, h1, w, n, scratch, NJ + 1);
+                             double* h2, double* nw1, double* hn, T* vout, cudaStream_t s, const int* done) {
+    axpy_dot_kernel<NJ, T><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, h1, w, n, scratch, NJ + 1, done);
     count_launches(1);
     // scratch holds [blk][NJ + 1]: the first NJ columns reduce to h2, the last to ||w1||^2
-    multidot_final_kernel<<<(NJ + 1 + 7) / 8, 256, 0, s>>>(scratch, kDotBlocks, NJ + 1, NJ, h2);
+    multidot_final_kernel<<<(NJ + 1 + 7) / 8, 256, 0, s>>>(scratch, kDotBlocks, NJ + 1, NJ, h2, done);
     count_launches(1);
-    multidot_final_kernel<<<1, 32, 0, s>>>(scratch + NJ, kDotBlocks, NJ + 1, 1, nw1);
+    multidot_final_kernel<<<1, 32, 0, s>>>(scratch + NJ, kDotBlocks, NJ + 1, 1, nw1, done);
     count_launches(1);
-    finish_norm_kernel<<<1, 1, 0, s>>>(h2, NJ, nw1, hn);
+    finish_norm_kernel<<<1, 1, 0, s>>>(h2, NJ, nw1, hn, done);
     count_launches(1);
-    axpy_scale_kernel<NJ, T><<<stream_grid(n), 256, 0, s>>>(V, ldv, h2, hn, w, vout, n);
+    axpy_scale_kernel<NJ, T><<<stream_grid(n), 256, 0, s>>>(V, ldv, h2, hn, w, vout, n, done);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -251,9 +329,9 @@ cudaError_t cgs2_tail_launch(const T* V, size_t ldv, const double* h1, T* w, siz
 template <typename T>
 cudaError_t cgs2_tail_dispatch(const T* V, size_t ldv, int nv, const double* h1, T* w, size_t n,
                                double* scratch, double* h2, double* nw1, double* hn, T* vout,
-                               cudaStream_t s) {
+                               cudaStream_t s, const int* done) {
     switch (nv) {
-#define CASE(J) case J: return cgs2_tail_launch<J, T>(V, ldv, h1, w, n, scratch, h2, nw1, hn, vout, s);
+#define CASE(J) case J: return cgs2_tail_launch<J, T>(V, ldv, h1, w, n, scratch, h2, nw1, hn, vout, s, done);
         CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
         CASE(12) CASE(13) CASE(14) CASE(15) CASE(16) CASE(17) CASE(18) CASE(19) CASE(20) CASE(21)
         CASE(22) CASE(23) CASE(24) CASE(25) CASE(26) CASE(27) CASE(28) CASE(29) CASE(30) CASE(31)
@@ -264,27 +342,28 @@ cudaError_t cgs2_tail_dispatch(const T* V, size_t ldv, int nv, const double* h1,
 }
 
 template <typename T>
-cudaError_t spmv_dispatch(const Geom& g, const T* Stil, const int* Scol, const T* x, T* y, cudaStream_t s) {
+cudaError_t spmv_dispatch(const Geom& g, const T* Stil, const int* Scol, const T* x, T* y, cudaStream_t s,
+                          const int* done) {
     switch (g.P) {
-        case 2: return spmv_launch<6, T>(g.n_edges, Stil, Scol, x, y, s);
-        case 3: return spmv_launch<9, T>(g.n_edges, Stil, Scol, x, y, s);
-        case 4: return spmv_launch<12, T>(g.n_edges, Stil, Scol, x, y, s);
-        case 5: return spmv_launch<15, T>(g.n_edges, Stil, Scol, x, y, s);
-        case 6: return spmv_launch<18, T>(g.n_edges, Stil, Scol, x, y, s);
+        case 2: return spmv_launch<6, T>(g.n_edges, Stil, Scol, x, y, s, done);
+        case 3: return spmv_launch<9, T>(g.n_edges, Stil, Scol, x, y, s, done);
+        case 4: return spmv_launch<12, T>(g.n_edges, Stil, Scol, x, y, s, done);
+        case 5: return spmv_launch<15, T>(g.n_edges, Stil, Scol, x, y, s, done);
+        case 6: return spmv_launch<18, T>(g.n_edges, Stil, Scol, x, y, s, done);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <typename T>
 cudaError_t multidot_impl(const T* V, size_t ldv, int nv, const T* w, size_t n, double* scratch, double* out,
-                          cudaStream_t s) {
+                          cudaStream_t s, const int* done) {
     for (int j0 = 0; j0 < nv; j0 += kDotChunk) {
         const int nj = nv - j0 < kDotChunk ? nv - j0 : kDotChunk;
         multidot_partial_kernel<kDotChunk, T><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, j0, nj, w, n,
-                                                                                  scratch, nv);
+                                                                                  scratch, nv, done);
         count_launches(1);
     }
-    multidot_final_kernel<<<(nv + 7) / 8, 256, 0, s>>>(scratch, kDotBlocks, nv, nv, out);
+    multidot_final_kernel<<<(nv + 7) / 8, 256, 0, s>>>(scratch, kDotBlocks, nv, nv, out, done);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -295,24 +374,24 @@ int cgs2_max_vectors() { return 32; }
 
 cudaError_t launch_cgs2_tail(const double* V, size_t ldv, int nv, const double* h1, double* w, size_t n,
                              double* scratch, double* h2, double* nw1, double* hn, double* vout,
-                             cudaStream_t s) {
-    return cgs2_tail_dispatch<double>(V, ldv, nv, h1, w, n, scratch, h2, nw1, hn, vout, s);
+                             cudaStream_t s, const int* done) {
+    return cgs2_tail_dispatch<double>(V, ldv, nv, h1, w, n, scratch, h2, nw1, hn, vout, s, done);
 }
 
 cudaError_t launch_cgs2_tail(const float* V, size_t ldv, int nv, const double* h1, float* w, size_t n,
                              double* scratch, double* h2, double* nw1, double* hn, float* vout,
-                             cudaStream_t s) {
-    return cgs2_tail_dispatch<float>(V, ldv, nv, h1, w, n, scratch, h2, nw1, hn, vout, s);
+                             cudaStream_t s, const int* done) {
+    return cgs2_tail_dispatch<float>(V, ldv, nv, h1, w, n, scratch, h2, nw1, hn, vout, s, done);
 }
 
 cudaError_t launch_spmv_pre(const Geom& g, const double* Stil, const int* Scol, const double* x,
-                            double* y, cudaStream_t s) {
-    return spmv_dispatch<double>(g, Stil, Scol, x, y, s);
+                            double* y, cudaStream_t s, const int* done) {
+    return spmv_dispatch<double>(g, Stil, Scol, x, y, s, done);
 }
 
 cudaError_t launch_spmv_pre(const Geom& g, const float* Stil, const int* Scol, const float* x,
-                            float* y, cudaStream_t s) {
-    return spmv_dispatch<float>(g, Stil, Scol, x, y, s);
+                            float* y, cudaStream_t s, const int* done) {
+    return spmv_dispatch<float>(g, Stil, Scol, x, y, s, done);
 }
 
 cudaError_t launch_block_diag(const Geom& g, const double* Bd, const double* x, double* y,
@@ -330,13 +409,13 @@ cudaError_t launch_block_diag(const Geom& g, const double* Bd, const double* x, 
 size_t dot_scratch_doubles(int nv) { return (size_t)kDotBlocks * (size_t)nv; }
 
 cudaError_t launch_multidot(const double* V, size_t ldv, int nv, const double* w, size_t n,
-                            double* scratch, double* out, cudaStream_t s) {
-    return multidot_impl<double>(V, ldv, nv, w, n, scratch, out, s);
+                            double* scratch, double* out, cudaStream_t s, const int* done) {
+    return multidot_impl<double>(V, ldv, nv, w, n, scratch, out, s, done);
 }
 
 cudaError_t launch_multidot(const float* V, size_t ldv, int nv, const float* w, size_t n,
-                            double* scratch, double* out, cudaStream_t s) {
-    return multidot_impl<float>(V, ldv, nv, w, n, scratch, out, s);
+                            double* scratch, double* out, cudaStream_t s, const int* done) {
+    return multidot_impl<float>(V, ldv, nv, w, n, scratch, out, s, done);
 }
 
 cudaError_t launch_multiaxpy(const double* V, size_t ldv, int nv, const double* coef, double sign,
@@ -364,6 +443,39 @@ cudaError_t launch_scale_by_rnorm(const double* w, const double* nrm2, float* v,
                                   cudaStream_t s) {
     scale_kernel<float><<<stream_grid(n), 256, 0, s>>>(w, nrm2, v, n);
     count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_solve_init(GmresCtl* c, double tol_abs, double inner_rel, int maxit, cudaStream_t s) {
+    gmres_solve_init_kernel<<<1, 1, 0, s>>>(c, tol_abs, inner_rel, maxit);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_cycle_init(GmresCtl* c, const double* nrm2, cudaStream_t s) {
+    gmres_cycle_init_kernel<<<1, 1, 0, s>>>(c, nrm2);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_arnoldi(GmresCtl* c, int j, int m, const double* h1, const double* h2, const double* hn,
+                                 cudaStream_t s) {
+    gmres_arnoldi_kernel<<<1, 1, 0, s>>>(c, j, m, h1, h2, hn);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_update(const double* V, size_t ldv, GmresCtl* c, double* x, size_t n, cudaStream_t s) {
+    gmres_solve_y_kernel<<<1, 1, 0, s>>>(c);
+    gmres_update_x_kernel<double><<<stream_grid(n), 256, 0, s>>>(V, ldv, c, x, n);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_update(const float* V, size_t ldv, GmresCtl* c, double* x, size_t n, cudaStream_t s) {
+    gmres_solve_y_kernel<<<1, 1, 0, s>>>(c);
+    gmres_update_x_kernel<float><<<stream_grid(n), 256, 0, s>>>(V, ldv, c, x, n);
+    count_launches(2);
     return cudaGetLastError();
 }
 

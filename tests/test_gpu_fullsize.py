@@ -36,18 +36,26 @@ def test_fullsize_dg_residual_matches_oracle(work):
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
-def test_fullsize_two_hundred_steps_conserve_mass(work):
-    """The workload's 200 steps (mixed form): finite, mass drift within the Krylov bound."""
+def test_fullsize_two_hundred_steps(work):
+    """The workload's 200 steps in both forms: finite; mass conserved to the trace solve's
+    tolerance (the conservation condition, eq. HDGcont, holds to the Krylov residual: FP64 form
+    rtol 1e-15 -> 1e-11 here, mixed form rtol 1e-10 per stage solve over 400 solves -> 1e-7);
+    and the mixed form within 1e-6 of the FP64 form at the end."""
     m, h, hu, hv, b, dt = work
-    with hd.Sim(N, K, dt, bottom=b, precision="mixed") as s:
-        s.set_state(h, hu, hv)
-        m0 = s.stats()["mass"]
-        s.step(200)
-        st = s.stats()
-        out = s.get_state()
-    assert st["steps"] == 200
-    assert all(np.isfinite(a).all() for a in out)
-    assert abs(st["mass"] - m0) <= 1e-9 * abs(m0)
+    res = {}
+    for p, bound in (("fp64", 1e-11), ("mixed", 1e-7)):
+        with hd.Sim(N, K, dt, bottom=b, precision=p) as s:
+            s.set_state(h, hu, hv)
+            m0 = s.stats()["mass"]
+            s.step(200)
+            st = s.stats()
+            out = s.get_state()
+        assert st["steps"] == 200
+        assert all(np.isfinite(a).all() for a in out)
+        assert abs(st["mass"] - m0) <= bound * abs(m0), (p, st["mass"], m0)
+        res[p] = swe.to_state(*out, b, W.G, W.H0)[0]
+    for c in range(3):
+        assert imex.rel_l2(m, res["mixed"][c], res["fp64"][c]) <= 1e-6
 
 
 def test_fullsize_fp64_reproducible_and_conservative(work):
