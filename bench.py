@@ -48,6 +48,10 @@ def _args():
                     help="forms to time; the headline is mixed when within 1e-6 of fp64")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", action="store_true",
+                    help="run the continuous-batching request loop instead and print its line")
+    ap.add_argument("--serving-requests", type=int, default=40)
+    ap.add_argument("--serving-rate", type=float, default=4.0, help="Poisson arrivals per second")
     ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--sample-steps", type=int, default=5, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -308,6 +312,32 @@ def _rel_l2_nodal(a, b, B):
     return out
 
 
+def serving_line(args):
+    """Serving workload: Poisson arrivals, N log-uniform in [32, 256], k in {2, 3, 4}, steps
+    uniform in [50, 500], mixed form, admitted by device-memory budget into 8 slots."""
+    import torch
+    from paper_1711_02751_gb300 import hdgdg as hd
+    from paper_1711_02751_gb300 import serving
+    free, total = torch.cuda.mem_get_info()
+    reqs = serving.poisson_requests(args.serving_requests, args.serving_rate)
+    budget = int(0.5 * free)
+    srv = serving.Server(hbm_budget=budget, max_slots=8, chunk=10)
+    summ = srv.serve(reqs)
+    busy = [e for e in srv.log if e["running"] > 0]
+    line = {"metric": "serving: DOF-steps/s and time to solution (p50/p99) under Poisson arrivals",
+            "value": summ["throughput_dof_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f64+f32 (mixed form)", "data": "synthetic",
+            "config": {"workload": "serving: N log-uniform [32,256], k in {2,3,4}, steps U[50,500], "
+                                   "seeded bump + streamfunction states",
+                       "requests": args.serving_requests, "arrival_rate_per_s": args.serving_rate,
+                       "slots": 8, "hbm_budget_bytes": budget},
+            "tts_p50_s": summ["tts_p50_s"], "tts_p99_s": summ["tts_p99_s"], "wall_s": summ["wall_s"],
+            "completed": summ["completed"], "max_running": summ["max_running"],
+            "max_queued": summ["max_queued"], "errors": summ["errors"][:3],
+            "occupancy": len(busy) / max(1, len(srv.log))}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     if args.cpu_baseline_child:
@@ -317,6 +347,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         reference_arm(args, rank, world)
+        return
+    if args.serving:
+        serving_line(args)
         return
 
     import torch

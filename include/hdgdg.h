@@ -49,7 +49,12 @@ typedef enum {
     HDGDG_ESTATE = 6           /* call made in the wrong order (e.g. step before set_state) */
 } hdgdg_status;
 
-enum { HDGDG_ARS2 = 0, HDGDG_ARS3 = 1 };          /* IMEX schemes named in Sec. 6 */
+/* Time integrators.  ARS2 / ARS3: the IMEX HDG-DG schemes of Sec. 6 (ARS(2,3,2), ARS(4,4,3)).
+ * RK2 / RK3: the explicit RK DG schemes the paper compares against (Sec. 7.1, 7.2) -- the whole
+ * flux with the Rusanov flux of eq. Full_russanov, advanced by Heun's method (RK2) or the
+ * three-stage SSP method of Shu and Osher (RK3); no trace system is built for them, and the
+ * implicit-stage row entry points return EINVAL. */
+enum { HDGDG_ARS2 = 0, HDGDG_ARS3 = 1, HDGDG_RK2 = 2, HDGDG_RK3 = 3 };
 /* Arithmetic of the path.
  * HDGDG_FP64:  every kernel in FP64.
  * HDGDG_MIXED: the trace Krylov solve runs as FP32 GMRES(m) cycles on an FP32 copy of the
@@ -64,7 +69,7 @@ typedef struct {
     int degree_k;        /* polynomial degree k, 1 <= k <= 5 */
     double g;            /* gravitational acceleration (> 0) */
     double H0;           /* reference depth: B = H0 - b */
-    int scheme;          /* HDGDG_ARS2 (ARS(2,3,2)) or HDGDG_ARS3 (ARS(4,4,3)) */
+    int scheme;          /* HDGDG_ARS2, HDGDG_ARS3, HDGDG_RK2 or HDGDG_RK3 */
     double dt;           /* time step (> 0) */
     int precision;       /* HDGDG_FP64 or HDGDG_MIXED */
     double krylov_rtol;  /* GMRES stop: ||g - S qhat|| <= rtol ||g||; <= 0 selects 1e-15

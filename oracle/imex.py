@@ -119,6 +119,35 @@ class Stepper:
         return q
 
 
+# -- explicit RK DG (the comparison scheme of Sec. 7) ------------------------------------------
+class ExplicitRK:
+    """Explicit strong-stability-preserving Runge-Kutta on the full DG residual: 'rk2' is Heun's
+    two-stage method, 'rk3' the three-stage method of Shu and Osher -- the RK2 DG / RK3 DG the
+    paper compares IMEX HDG-DG against (Sec. 7.1, 7.2)."""
+
+    def __init__(self, mesh, phiB, dt, scheme="rk2"):
+        self.mesh, self.phiB, self.dt, self.scheme = mesh, phiB, dt, scheme
+
+    def rhs(self, q):
+        return swe.minv(self.mesh, swe.DG_full(self.mesh, q, self.phiB))
+
+    def step(self, q):
+        dt = self.dt
+        if self.scheme == "rk2":
+            q1 = q + dt * self.rhs(q)
+            return 0.5 * q + 0.5 * (q1 + dt * self.rhs(q1))
+        if self.scheme == "rk3":
+            q1 = q + dt * self.rhs(q)
+            q2 = 0.75 * q + 0.25 * (q1 + dt * self.rhs(q1))
+            return q / 3.0 + 2.0 / 3.0 * (q2 + dt * self.rhs(q2))
+        raise ValueError(self.scheme)
+
+    def run(self, q, n_steps):
+        for _ in range(n_steps):
+            q = self.step(q)
+        return q
+
+
 # -- diagnostics ------------------------------------------------------------------------------
 def mass(mesh, q):
     """Total mass integral of phi_eta (GLL quadrature): sum_e J sum_ij w_i w_j phi_eta."""

@@ -193,6 +193,37 @@ def NL(mesh, q, phiB):
     return r
 
 
+# -- explicit DG residual of the full system (the RK-DG comparison of Sec. 7) ---------------
+def rusanov_full_normal_flux(mesh, q, phiB, f):
+    """F* . n of eq. Full_russanov on face f of every element: {F} . n + tau*/2 (q^- - q^+)."""
+    n = FACE_NORMALS[f]
+    qm = mesh.face_values(q, f)
+    qp = mesh.neighbour_face_values(q, f)
+    bm = mesh.face_values(phiB, f)
+    bp = mesh.neighbour_face_values(phiB, f)
+    Fxm, Fym = flux_full(qm, bm)
+    Fxp, Fyp = flux_full(qp, bp)
+    jump_n = qm * (n @ n) + qp * ((-n) @ n)
+    phim, phip = qm[0] + bm, qp[0] + bp
+    un_m = (qm[1] * n[0] + qm[2] * n[1]) / phim
+    un_p = (qp[1] * n[0] + qp[2] * n[1]) / phip
+    tau_star = np.maximum(np.abs(un_m) + np.sqrt(phim), np.abs(un_p) + np.sqrt(phip))
+    return 0.5 * ((Fxm + Fxp) * n[0] + (Fym + Fyp) * n[1]) + 0.5 * tau_star * jump_n
+
+
+def DG_full(mesh, q, phiB):
+    """(F(q), grad v) + (s(q), v) - <F*(q^+-) . n, v> of eq. WeakForm_DG for the whole flux;
+    a nodal weak-form vector [3, e, j, i] (the explicit RK DG scheme the paper compares with)."""
+    Fx, Fy = flux_full(q, phiB)
+    r = volume_flux_term(mesh, Fx, Fy)
+    dBx, dBy = nodal_gradient(mesh, phiB)
+    s = np.stack([np.zeros_like(q[0]), q[0] * dBx, q[0] * dBy])
+    r = r + mesh.mass[None, None, :, :] * s
+    for f in range(4):
+        face_integral_to_nodes(mesh, r, f, rusanov_full_normal_flux(mesh, q, phiB, f))
+    return r
+
+
 # -- HDG residual of the linear part and the conservation condition ------------------------
 def hdg_normal_flux(q_face, lam_face, phiB_face, tau_face, n):
     """n . Fhat_L(q, qhat) of eq. linear_hdgflux3 at face nodes; all [3 or 1, e, b]."""

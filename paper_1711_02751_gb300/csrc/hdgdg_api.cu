@@ -16,6 +16,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -39,11 +41,13 @@ constexpr int kMaxRestart = 31;   // the fused Gram-Schmidt kernels keep up to 3
 bool valid(const hdgdg_config* c) {
     return c && c->n_side >= 2 && c->n_side <= 32768 && c->degree_k >= 1 && c->degree_k <= kMaxP - 1 &&
            std::isfinite(c->g) && c->g > 0.0 && std::isfinite(c->H0) && std::isfinite(c->dt) &&
-           c->dt > 0.0 && (c->scheme == HDGDG_ARS2 || c->scheme == HDGDG_ARS3) &&
+           c->dt > 0.0 && c->scheme >= HDGDG_ARS2 && c->scheme <= HDGDG_RK3 &&
            (c->precision == HDGDG_FP64 || c->precision == HDGDG_MIXED) &&
            (c->linear_only == 0 || c->linear_only == 1) &&
            c->krylov_restart <= kMaxRestart;
 }
+
+bool explicit_scheme(const hdgdg_config* c) { return c->scheme == HDGDG_RK2 || c->scheme == HDGDG_RK3; }
 
 int restart_of(const hdgdg_config* c) { return c->krylov_restart > 0 ? c->krylov_restart : 8; }
 
@@ -57,16 +61,24 @@ Plan make_plan(const hdgdg_config* c) {
     p.NT = (int)(12 * P);
     p.nt = n_edges * p.NF;
     p.m = restart_of(c);
-    p.s = c->scheme == HDGDG_ARS2 ? 3 : 5;
+    p.s = c->scheme == HDGDG_ARS2 ? 3 : c->scheme == HDGDG_ARS3 ? 5 : 3;
     const size_t d = sizeof(double);
     size_t b = 0;
+    if (explicit_scheme(c)) {   // state, three stage increments, two stage states, face fluxes
+        b += p.n * d + n_edges * P * d;
+        b += 7 * 3 * p.n * d + p.nt * d;
+        b += (dot_scratch_doubles(p.m + 2) + mass_scratch_doubles() + 4 * (size_t)(p.m + 2) + 16) * d + 64;
+        p.persistent = b;
+        p.setup_temp = 0;
+        return p;
+    }
     b += p.n * d + n_edges * P * d;                           // phiB, tau
     b += n_el * (size_t)p.NV * p.NV * d;                      // A^{-1}
     b += n_edges * 6 * (size_t)p.NF * p.NF * d;               // S~
     b += n_edges * 6 * sizeof(int);                           // columns
     b += 2 * n_edges * (size_t)p.NF * p.NF * d;               // M^{-1}, S_rr
     b += (5 + 2 * (size_t)p.s) * 3 * p.n * d;                 // q, q_new, R1, Z, Q, NL_i, L_i
-    b += 4 * p.nt * d;                                        // g, x~, qhat, w
+    b += 5 * p.nt * d;                                        // g, x~, qhat, w, DG face fluxes
     if (c->precision == HDGDG_MIXED) {                        // FP32 S~, FP32 basis and work vector
         b += n_edges * 6 * (size_t)p.NF * p.NF * sizeof(float);
         b += ((size_t)p.m + 2) * p.nt * sizeof(float);
@@ -212,7 +224,7 @@ struct hdgdg_sim {
     int* Scol = nullptr;
     double *q = nullptr, *q_new = nullptr, *R1 = nullptr, *Z = nullptr, *Qs = nullptr;
     double *NLs[kMaxStages] = {}, *Ls[kMaxStages] = {};
-    double *gvec = nullptr, *xt = nullptr, *lam = nullptr, *w = nullptr, *V = nullptr;
+    double *gvec = nullptr, *xt = nullptr, *lam = nullptr, *w = nullptr, *V = nullptr, *fface = nullptr;
     float *Stil32 = nullptr, *V32 = nullptr, *w32 = nullptr;   // mixed precision only
     double *red = nullptr, *mred = nullptr, *dvals = nullptr;
     GmresCtl* ctl = nullptr;
@@ -455,7 +467,50 @@ hdgdg_status stage_solve_dev(hdgdg_sim* sim, const double* R1, double* Q, double
     return HDGDG_OK;
 }
 
+// Explicit SSP Runge-Kutta on the whole DG residual (the paper's RK2 DG / RK3 DG), with the
+// stage increments K_i = dt M^{-1} R(q_i):
+//   RK2 (Heun):        q1 = q + K1;                 q' = q + K1/2 + K2/2
+//   RK3 (Shu-Osher):   q1 = q + K1;  q2 = q + K1/4 + K2/4;  q' = q + K1/6 + K2/6 + 2 K3/3
+hdgdg_status explicit_step(hdgdg_sim* sim) {
+    const size_t n3 = 3 * sim->plan.n;
+    cudaStream_t st = sim->stream;
+    const double dt = sim->cfg.dt;
+    auto rhs = [&](const double* qi, double* K) -> hdgdg_status {
+        TimedGroup tg(sim, HDGDG_KT_DG);
+        CU(launch_dg_full(sim->g, qi, sim->phiB, dt, sim->fface, K, st));
+        return HDGDG_OK;
+    };
+    auto comb = [&](double* out, std::initializer_list<std::pair<double*, double>> terms, unsigned* flag) -> hdgdg_status {
+        CombineTerms t{};
+        for (auto& pr : terms) { t.X[t.n] = pr.first; t.c[t.n++] = pr.second; }
+        TimedGroup tg(sim, HDGDG_KT_COMBINE);
+        CU(launch_combine(n3, sim->q, t, out, flag, st));
+        return HDGDG_OK;
+    };
+    double *K1 = sim->NLs[0], *K2 = sim->NLs[1], *K3 = sim->NLs[2];
+    TRY(rhs(sim->q, K1));
+    TRY(comb(sim->Qs, {{K1, 1.0}}, nullptr));
+    TRY(rhs(sim->Qs, K2));
+    CU(cudaMemsetAsync(sim->flags, 0, sizeof(unsigned), st));
+    if (sim->cfg.scheme == HDGDG_RK2) {
+        TRY(comb(sim->q_new, {{K1, 0.5}, {K2, 0.5}}, sim->flags));
+    } else {
+        TRY(comb(sim->R1, {{K1, 0.25}, {K2, 0.25}}, nullptr));
+        TRY(rhs(sim->R1, K3));
+        TRY(comb(sim->q_new, {{K1, 1.0 / 6.0}, {K2, 1.0 / 6.0}, {K3, 2.0 / 3.0}}, sim->flags));
+    }
+    unsigned flag = 0;
+    CU(cudaMemcpyAsync(&sim->hbuf[0], sim->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    TRY(sync(sim));
+    std::memcpy(&flag, &sim->hbuf[0], sizeof(unsigned));
+    if (flag) return fail(sim, HDGDG_ENONFINITE, "step %lld produced a non-finite state", sim->stats.steps + 1);
+    std::swap(sim->q, sim->q_new);
+    sim->stats.steps += 1;
+    return HDGDG_OK;
+}
+
 hdgdg_status one_step(hdgdg_sim* sim) {
+    if (explicit_scheme(&sim->cfg)) return explicit_step(sim);
     const size_t n3 = 3 * sim->plan.n;
     cudaStream_t st = sim->stream;
     for (int i = 0; i < sim->s; ++i) {
@@ -476,7 +531,7 @@ hdgdg_status one_step(hdgdg_sim* sim) {
         }
         if (!sim->cfg.linear_only) {
             TimedGroup tg(sim, HDGDG_KT_DG);
-            CU(launch_dg_nl(sim->g, Qi, sim->phiB, sim->cfg.dt, sim->NLs[i], st));
+            CU(launch_dg_nl(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st));
         }
     }
     CombineTerms t{};
@@ -524,6 +579,20 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
     }
     TRY(dalloc(sim, &sim->phiB, p.n));
     TRY(dalloc(sim, &sim->tau, tau.size()));
+    if (explicit_scheme(c)) {
+        for (double** v : {&sim->q, &sim->q_new, &sim->R1, &sim->Qs}) TRY(dalloc(sim, v, 3 * p.n));
+        for (int i = 0; i < 3; ++i) TRY(dalloc(sim, &sim->NLs[i], 3 * p.n));
+        TRY(dalloc(sim, &sim->fface, p.nt));
+        TRY(dalloc(sim, &sim->red, dot_scratch_doubles(p.m + 2)));
+        TRY(dalloc(sim, &sim->mred, mass_scratch_doubles()));
+        TRY(dalloc(sim, &sim->dvals, 4 * (size_t)(p.m + 2) + 16));
+        TRY(dalloc(sim, &sim->flags, 16));
+        CU(cudaMallocHost(&sim->hbuf, (4 * (size_t)(p.m + 2) + 16) * sizeof(double)));
+        CU(cudaMemcpyAsync(sim->phiB, phiB.data(), p.n * sizeof(double), cudaMemcpyHostToDevice, sim->stream));
+        CU(cudaMemcpyAsync(sim->tau, tau.data(), tau.size() * sizeof(double), cudaMemcpyHostToDevice, sim->stream));
+        CU(cudaStreamSynchronize(sim->stream));
+        return HDGDG_OK;
+    }
     TRY(dalloc(sim, &sim->Ainv, (size_t)g.n_el * p.NV * p.NV));
     TRY(dalloc(sim, &sim->Stil, (size_t)g.n_edges * 6 * p.NF * p.NF));
     TRY(dalloc(sim, &sim->Scol, (size_t)g.n_edges * 6));
@@ -534,7 +603,7 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
         TRY(dalloc(sim, &sim->NLs[i], 3 * p.n));
         TRY(dalloc(sim, &sim->Ls[i], 3 * p.n));
     }
-    for (double** v : {&sim->gvec, &sim->xt, &sim->lam, &sim->w}) TRY(dalloc(sim, v, p.nt));
+    for (double** v : {&sim->gvec, &sim->xt, &sim->lam, &sim->w, &sim->fface}) TRY(dalloc(sim, v, p.nt));
     if (c->precision == HDGDG_MIXED) {
         TRY(dalloc(sim, &sim->Stil32, (size_t)g.n_edges * 6 * p.NF * p.NF));
         TRY(dalloc(sim, &sim->V32, (size_t)(p.m + 1) * p.nt));
@@ -641,7 +710,13 @@ hdgdg_status hdgdg_create(const hdgdg_config* cfg, const double* bottom_b, void*
     sim->cfg = *cfg;
     sim->plan = make_plan(cfg);
     sim->g = make_geom(cfg, nullptr);
-    scheme_tables(cfg->scheme, sim->A, sim->At, sim->b, sim->bt, &sim->s);
+    if (explicit_scheme(cfg)) {
+        sim->s = 3;
+        std::memset(sim->A, 0, sizeof(sim->A));
+        std::memset(sim->At, 0, sizeof(sim->At));
+    } else {
+        scheme_tables(cfg->scheme, sim->A, sim->At, sim->b, sim->bt, &sim->s);
+    }
     sim->a_ii = sim->At[1][1];
     for (int i = 0; i < sim->s; ++i) {
         if (sim->At[i][i] != 0.0 && sim->At[i][i] != sim->a_ii) {
@@ -733,11 +808,12 @@ hdgdg_status hdgdg_eval_nl(hdgdg_sim* sim, const double* q, double* out) {
     if (!sim || !q || !out) return fail(sim, HDGDG_EINVAL, "NULL argument to eval_nl");
     const size_t n3 = 3 * sim->plan.n;
     TRY(upload3(sim, sim->R1, q, n3));
-    CU(launch_dg_nl(sim->g, sim->R1, sim->phiB, 1.0, sim->Qs, sim->stream));
+    CU(launch_dg_nl(sim->g, sim->R1, sim->phiB, sim->tau, 1.0, sim->fface, sim->Qs, sim->stream));
     return download(sim, out, sim->Qs, n3);
 }
 
 hdgdg_status hdgdg_condense_rhs(hdgdg_sim* sim, const double* R1, double* out) {
+    if (sim && explicit_scheme(&sim->cfg)) return fail(sim, HDGDG_EINVAL, "explicit scheme: no implicit stage");
     if (!sim || !R1 || !out) return fail(sim, HDGDG_EINVAL, "NULL argument to condense_rhs");
     TRY(upload3(sim, sim->R1, R1, 3 * sim->plan.n));
     CU(launch_condense(sim->g, sim->Ainv, sim->R1, sim->phiB, sim->tau, sim->Z, sim->gvec, sim->stream));
@@ -745,6 +821,7 @@ hdgdg_status hdgdg_condense_rhs(hdgdg_sim* sim, const double* R1, double* out) {
 }
 
 hdgdg_status hdgdg_trace_apply(hdgdg_sim* sim, const double* x, double* y) {
+    if (sim && explicit_scheme(&sim->cfg)) return fail(sim, HDGDG_EINVAL, "explicit scheme: no implicit stage");
     if (!sim || !x || !y) return fail(sim, HDGDG_EINVAL, "NULL argument to trace_apply");
     TRY(upload3(sim, sim->lam, x, sim->plan.nt));
     CU(launch_block_diag(sim->g, sim->Srr, sim->lam, sim->xt, sim->stream));          // u = S_rr x
@@ -753,6 +830,7 @@ hdgdg_status hdgdg_trace_apply(hdgdg_sim* sim, const double* x, double* y) {
 }
 
 hdgdg_status hdgdg_stage_solve(hdgdg_sim* sim, const double* R1, double* Q, double* qhat, int* iterations) {
+    if (sim && explicit_scheme(&sim->cfg)) return fail(sim, HDGDG_EINVAL, "explicit scheme: no implicit stage");
     if (!sim || !R1 || !Q) return fail(sim, HDGDG_EINVAL, "NULL argument to stage_solve");
     const size_t n3 = 3 * sim->plan.n;
     TRY(upload3(sim, sim->R1, R1, n3));

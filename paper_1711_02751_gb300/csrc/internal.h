@@ -74,9 +74,12 @@ long long launches_total();
 void count_launches(int n);
 
 // ---- kernel launchers (each returns the launch error) -------------------------------
-// out = scale * M^{-1} NL(q)
-cudaError_t launch_dg_nl(const Geom& g, const double* q, const double* phiB, double scale,
-                         double* out, cudaStream_t s);
+// out = scale * M^{-1} NL(q); fface: scratch of n_edges * 3P doubles for the face fluxes
+cudaError_t launch_dg_nl(const Geom& g, const double* q, const double* phiB, const double* tau_edge,
+                         double scale, double* fface, double* out, cudaStream_t s);
+// out = scale * M^{-1} (the explicit DG residual of the whole flux with the source term)
+cudaError_t launch_dg_full(const Geom& g, const double* q, const double* phiB, double scale,
+                           double* fface, double* out, cudaStream_t s);
 
 struct CombineTerms {
     const double* X[10];

@@ -8,6 +8,7 @@
 // Collocated GLL quadrature makes M diagonal, so M^{-1} NL at node (i, j) is
 //   (2/h) [sum_a (w_a/w_i) D_ai Fx(a,j) + sum_b (w_b/w_j) D_bj Fy(i,b)]
 //   - (2/h) / w_0 * (F*_NL . n) on each face through the node.
+// tau_L* = max_pm sqrt(phi_B) is the per-edge-node tau_hat the library precomputes.
 #include <atomic>
 
 #include "internal.h"
@@ -33,77 +34,123 @@ __device__ __forceinline__ void nl_flux(double ph, double U, double V, double ph
     *fyV = V * V * inv + half;
 }
 
-template <int P>
+// Face pass: the Rusanov flux difference F*_NL . n through every edge node, computed once per
+// node (so the two elements see exactly opposite values) and stored as the flux along the
+// edge's +x / +y normal: fface[edge][c][b].  One thread per (edge, b).
+//   FULL = true: the Rusanov flux F* . n of the whole flux F = F_NL + F_L (eq. Full_russanov),
+//   the residual of the explicit RK DG scheme the paper compares with.
+template <int P, bool FULL>
+__global__ void __launch_bounds__(256)
+dg_face_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ phiB,
+               const double* __restrict__ tau_edge, double* __restrict__ fface) {
+    constexpr int Np = P * P;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.n_edges * P) return;
+    const int r = t / P, b = t % P;
+    int em, fm, ep, fp;
+    edge_sides(r, g.N, &em, &fm, &ep, &fp);
+    const size_t fs = (size_t)g.n_el * Np;
+    const size_t om = (size_t)em * Np + face_node(fm, b, P);
+    const size_t op = (size_t)ep * Np + face_node(fp, b, P);
+    const double phm = q[om], Um = q[fs + om], Vm = q[2 * fs + om], pbm = phiB[om];
+    const double php = q[op], Up = q[fs + op], Vp = q[2 * fs + op], pbp = phiB[op];
+    const double Phm = phm + pbm, Php = php + pbp;
+    const double im = 1.0 / Phm, ip = 1.0 / Php;
+    const bool xedge = fm == 1;
+    // normal (n) and tangential (t) momentum components along this edge's +axis
+    const double Unm = xedge ? Um : Vm, Utm = xedge ? Vm : Um;
+    const double Unp = xedge ? Up : Vp, Utp = xedge ? Vp : Up;
+    // F_NL . n: (0, Un Un / phi + phi_eta^2 / 2, Un Ut / phi) in (normal, tangential) order
+    double Fnm = Unm * Unm * im + 0.5 * phm * phm, Ftm = Unm * Utm * im;
+    double Fnp = Unp * Unp * ip + 0.5 * php * php, Ftp = Unp * Utp * ip;
+    const double tau_star = fmax(fabs(Unm) * im + sqrt(Phm), fabs(Unp) * ip + sqrt(Php));
+    double hd, fph;
+    if (FULL) {   // add F_L . n = (U_n, phi_eta phi_B, 0)
+        Fnm += phm * pbm;
+        Fnp += php * pbp;
+        hd = 0.5 * tau_star;
+        fph = 0.5 * (Unm + Unp) + hd * (phm - php);
+    } else {
+        hd = 0.5 * (tau_star - tau_edge[(size_t)r * P + b]);
+        fph = hd * (phm - php);
+    }
+    const double fn = 0.5 * (Fnm + Fnp) + hd * (Unm - Unp);
+    const double ft = 0.5 * (Ftm + Ftp) + hd * (Utm - Utp);
+    double* out = fface + (size_t)r * 3 * P;
+    out[b] = fph;
+    out[(xedge ? 1 : 2) * P + b] = fn;
+    out[(xedge ? 2 : 1) * P + b] = ft;
+}
+
+// Element pass: volume term from the nodal F_NL (shared memory), minus the lifted face fluxes.
+// FULL = true: the whole flux F and the source s = (0, phi_eta d_x phi_B, phi_eta d_y phi_B).
+template <int P, bool FULL>
 __global__ void __launch_bounds__(DgTile<P>::EPB * P * P)
-dg_nl_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ phiB, double scale,
-             double* __restrict__ out) {
+dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ phiB,
+                 const double* __restrict__ fface, double scale, double* __restrict__ out) {
     constexpr int Np = P * P;
     constexpr int EPB = DgTile<P>::EPB;
     __shared__ double sF[EPB][4][Np];   // fxU, fxV, fyU, fyV
+    __shared__ double sM[FULL ? EPB : 1][3][Np];   // FULL: U, V and phi_B for the mass flux and source
 
     const int le = threadIdx.x / Np;
     const int n = threadIdx.x % Np;
     const int e = blockIdx.x * EPB + le;
     const bool live = e < g.n_el;
-    const size_t fs = (size_t)g.n_el * Np;   // field stride
+    const size_t fs = (size_t)g.n_el * Np;
     const int i = n % P, j = n / P;
 
-    double ph = 0.0, U = 0.0, V = 0.0, pb = 1.0;
+    double ph_own = 0.0;
     if (live) {
         const size_t o = (size_t)e * Np + n;
-        ph = q[o]; U = q[fs + o]; V = q[2 * fs + o]; pb = phiB[o];
+        const double ph = q[o], U = q[fs + o], V = q[2 * fs + o], pb = phiB[o];
         nl_flux(ph, U, V, pb, &sF[le][0][n], &sF[le][1][n], &sF[le][2][n], &sF[le][3][n]);
+        if (FULL) {
+            sF[le][0][n] += ph * pb;
+            sF[le][3][n] += ph * pb;
+            sM[FULL ? le : 0][0][n] = U;
+            sM[FULL ? le : 0][1][n] = V;
+            sM[FULL ? le : 0][2][n] = pb;
+            ph_own = ph;
+        }
     }
     __syncthreads();
     if (!live) return;
 
-    // volume term
-    double rU = 0.0, rV = 0.0;
+    double rU = 0.0, rV = 0.0, rph = 0.0;
 #pragma unroll
     for (int a = 0; a < P; ++a) {
         const double cx = g.Dhat[i * P + a];
         const double cy = g.Dhat[j * P + a];
         rU += cx * sF[le][0][j * P + a] + cy * sF[le][2][a * P + i];
         rV += cx * sF[le][1][j * P + a] + cy * sF[le][3][a * P + i];
+        if (FULL) rph += cx * sM[le][0][j * P + a] + cy * sM[le][1][a * P + i];
     }
     rU *= g.two_over_h;
     rV *= g.two_over_h;
-    double rph = 0.0;
-
-    // face terms: every face through this node
+    rph *= g.two_over_h;
+    if (FULL) {   // source phi_eta grad phi_B with the nodal derivative of phi_B
+        double dBx = 0.0, dBy = 0.0;
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+            dBx += g.D[i * P + a] * sM[le][2][j * P + a];
+            dBy += g.D[j * P + a] * sM[le][2][a * P + i];
+        }
+        rU += ph_own * g.two_over_h * dBx;
+        rV += ph_own * g.two_over_h * dBy;
+    }
     const double lift = g.two_over_h * g.inv_w0;
-    const double c_own = sqrt(ph + pb);
-    const double sb_own = sqrt(pb);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const bool on = (f == 0 && i == 0) || (f == 1 && i == P - 1) || (f == 2 && j == 0) ||
                         (f == 3 && j == P - 1);
         if (!on) continue;
         const int b = (f < 2) ? j : i;
-        const int nb = neighbour(e, f, g.N);
-        const int fo = f ^ 1;                       // opposite face of the neighbour
-        const size_t o2 = (size_t)nb * Np + face_node(fo, b, P);
-        const double ph2 = q[o2], U2 = q[fs + o2], V2 = q[2 * fs + o2], pb2 = phiB[o2];
-        double fxU2, fxV2, fyU2, fyV2;
-        nl_flux(ph2, U2, V2, pb2, &fxU2, &fxV2, &fyU2, &fyV2);
-        const double sgn = (f & 1) ? 1.0 : -1.0;   // outward normal component along the face axis
-        double Fo_U, Fo_V, Fn_U, Fn_V, un_o, un_n;
-        if (f < 2) {
-            Fo_U = sF[le][0][n]; Fo_V = sF[le][1][n]; Fn_U = fxU2; Fn_V = fxV2;
-            un_o = fabs(U) / (ph + pb); un_n = fabs(U2) / (ph2 + pb2);
-        } else {
-            Fo_U = sF[le][2][n]; Fo_V = sF[le][3][n]; Fn_U = fyU2; Fn_V = fyV2;
-            un_o = fabs(V) / (ph + pb); un_n = fabs(V2) / (ph2 + pb2);
-        }
-        const double tau_star = fmax(un_o + c_own, un_n + sqrt(ph2 + pb2));
-        const double tau_L = fmax(sb_own, sqrt(pb2));
-        const double hd = 0.5 * (tau_star - tau_L);
-        const double fph = hd * (ph - ph2);
-        const double fU = 0.5 * (Fo_U + Fn_U) * sgn + hd * (U - U2);
-        const double fV = 0.5 * (Fo_V + Fn_V) * sgn + hd * (V - V2);
-        rph -= lift * fph;
-        rU -= lift * fU;
-        rV -= lift * fV;
+        const double* fl = fface + (size_t)edge_of_face(e, f, g.N) * 3 * P;
+        const double sgn = (f & 1) ? lift : -lift;   // outward normal is + on faces 1, 3
+        rph -= sgn * fl[b];
+        rU -= sgn * fl[P + b];
+        rV -= sgn * fl[2 * P + b];
     }
     const size_t o = (size_t)e * Np + n;
     out[o] = scale * rph;
@@ -189,12 +236,14 @@ __global__ void mass_final_kernel(const double* partial, int nb, double J, doubl
     if (threadIdx.x == 0) *out = J * acc;
 }
 
-template <int P>
-cudaError_t dg_nl_launch(const Geom& g, const double* q, const double* phiB, double scale,
-                         double* out, cudaStream_t s) {
+template <int P, bool FULL>
+cudaError_t dg_launch(const Geom& g, const double* q, const double* phiB, const double* tau_edge,
+                      double scale, double* fface, double* out, cudaStream_t s) {
     constexpr int EPB = DgTile<P>::EPB;
-    const int blocks = (g.n_el + EPB - 1) / EPB;
-    dg_nl_kernel<P><<<blocks, EPB * P * P, 0, s>>>(g, q, phiB, scale, out);
+    const int nf = g.n_edges * P;
+    dg_face_kernel<P, FULL><<<(nf + 255) / 256, 256, 0, s>>>(g, q, phiB, tau_edge, fface);
+    count_launches(1);
+    dg_volume_kernel<P, FULL><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(g, q, phiB, fface, scale, out);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -214,14 +263,26 @@ std::atomic<long long> g_launches{0};
 long long launches_total() { return g_launches.load(); }
 void count_launches(int n) { g_launches.fetch_add(n); }
 
-cudaError_t launch_dg_nl(const Geom& g, const double* q, const double* phiB, double scale,
-                         double* out, cudaStream_t s) {
+cudaError_t launch_dg_nl(const Geom& g, const double* q, const double* phiB, const double* tau_edge,
+                         double scale, double* fface, double* out, cudaStream_t s) {
     switch (g.P) {
-        case 2: return dg_nl_launch<2>(g, q, phiB, scale, out, s);
-        case 3: return dg_nl_launch<3>(g, q, phiB, scale, out, s);
-        case 4: return dg_nl_launch<4>(g, q, phiB, scale, out, s);
-        case 5: return dg_nl_launch<5>(g, q, phiB, scale, out, s);
-        case 6: return dg_nl_launch<6>(g, q, phiB, scale, out, s);
+        case 2: return dg_launch<2, false>(g, q, phiB, tau_edge, scale, fface, out, s);
+        case 3: return dg_launch<3, false>(g, q, phiB, tau_edge, scale, fface, out, s);
+        case 4: return dg_launch<4, false>(g, q, phiB, tau_edge, scale, fface, out, s);
+        case 5: return dg_launch<5, false>(g, q, phiB, tau_edge, scale, fface, out, s);
+        case 6: return dg_launch<6, false>(g, q, phiB, tau_edge, scale, fface, out, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_dg_full(const Geom& g, const double* q, const double* phiB, double scale,
+                           double* fface, double* out, cudaStream_t s) {
+    switch (g.P) {
+        case 2: return dg_launch<2, true>(g, q, phiB, nullptr, scale, fface, out, s);
+        case 3: return dg_launch<3, true>(g, q, phiB, nullptr, scale, fface, out, s);
+        case 4: return dg_launch<4, true>(g, q, phiB, nullptr, scale, fface, out, s);
+        case 5: return dg_launch<5, true>(g, q, phiB, nullptr, scale, fface, out, s);
+        case 6: return dg_launch<6, true>(g, q, phiB, nullptr, scale, fface, out, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(_HERE, "libhdgdg.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ENONFINITE, ESTATE = range(7)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTCONVERGED", "ENONFINITE", "ESTATE"]
-SCHEMES = {"ars2": 0, "ars3": 1}
+SCHEMES = {"ars2": 0, "ars3": 1, "rk2": 2, "rk3": 3}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 
 EXPORTS = ["hdgdg_bytes_required", "hdgdg_node_coords", "hdgdg_create", "hdgdg_set_state",

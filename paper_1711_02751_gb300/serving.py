@@ -1,0 +1,146 @@
+"""Continuous-batching request loop for shallow-water runs on one GPU.
+
+Requests (a mesh size, a degree, a number of steps, a seed, an arrival time) are admitted
+while both a slot and device memory are free -- the memory each needs is the library's own
+``hdgdg_bytes_required`` -- and stay resident until done.  Every admitted simulation is
+stepped by its own host thread on its own CUDA stream (the library creates one per handle;
+ctypes releases the GIL during each call), so the device work of all admitted requests
+overlaps, and requests that arrive while others run join as soon as a slot and memory free
+up.  Each step's arithmetic is the same as when the simulation runs alone, so results do not
+depend on the mix (the reductions have a fixed order).
+
+Reported: throughput in DOF-steps/s over the whole run, and the time to solution of each
+request (arrival to result copied back), summarised as p50 / p99.
+"""
+import math
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import hdgdg as hd
+from . import workloads as W
+
+
+@dataclass
+class Request:
+    rid: int
+    N: int
+    k: int
+    steps: int
+    seed: int
+    arrival: float                      # seconds after the loop starts
+    precision: str = "mixed"
+    result: tuple = None
+    admitted: float = None
+    finished: float = None
+    bytes: int = 0
+    error: str = None
+
+
+def poisson_requests(n, rate_per_s, seed=5000, n_range=(32, 256), degrees=(2, 3, 4),
+                     steps_range=(50, 500), precision="mixed"):
+    """Seeded Poisson arrivals; N log-uniform in n_range, k uniform in degrees, steps uniform."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate_per_s)
+        N = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))))
+        k = int(rng.choice(degrees))
+        steps = int(rng.integers(steps_range[0], steps_range[1] + 1))
+        out.append(Request(i, N, k, steps, seed + 1 + i, t, precision))
+    return out
+
+
+def initial_state(req):
+    """The request's seeded state: the bump recipe of the large workload (one bump per request
+    domain scale, smooth velocity), on the library's own nodes."""
+    x, y = hd.node_coords(req.N, req.k)
+    h, hu, hv, b = W.large_state(x, y, seed=req.seed, n_bumps=1, umax=0.05)
+    dt = W.advective_dt(x, h, hu, hv, req.N)
+    return h, hu, hv, b, dt
+
+
+def run_one(req, chunk=10):
+    """Run one request to completion on a fresh handle; returns the final (h, hu, hv)."""
+    h, hu, hv, b, dt = initial_state(req)
+    with hd.Sim(req.N, req.k, dt, bottom=b, precision=req.precision) as s:
+        s.set_state(h, hu, hv)
+        done = 0
+        while done < req.steps:
+            n = min(chunk, req.steps - done)
+            s.step(n)
+            done += n
+        return s.get_state()
+
+
+@dataclass
+class Server:
+    hbm_budget: int                      # bytes the loop may hand out
+    max_slots: int = 8
+    chunk: int = 10
+    log: list = field(default_factory=list)
+
+    def serve(self, requests, time_scale=1.0):
+        """Serve requests arriving at time_scale * arrival seconds; returns a summary dict."""
+        pending = sorted(requests, key=lambda r: r.arrival)
+        queue, running = [], {}
+        used = 0
+        lock = threading.Lock()
+        t0 = time.perf_counter()
+
+        def now():
+            return time.perf_counter() - t0
+
+        def worker(req):
+            try:
+                req.result = run_one(req, self.chunk)
+            except Exception as ex:           # the request fails, the server carries on
+                req.error = str(ex)
+            req.finished = now()
+
+        finished = []
+        while pending or queue or running:
+            t = now()
+            while pending and pending[0].arrival * time_scale <= t:
+                r = pending.pop(0)
+                r.bytes = hd.bytes_required(hd.make_config(r.N, r.k, 1.0, precision=r.precision))
+                queue.append(r)
+            with lock:
+                for rid in [rid for rid, (r, th) in running.items() if not th.is_alive()]:
+                    r, th = running.pop(rid)
+                    th.join()
+                    used -= r.bytes
+                    finished.append(r)
+                # admit in arrival order while a slot and memory are free (no overtaking)
+                while queue and len(running) < self.max_slots and used + queue[0].bytes <= self.hbm_budget:
+                    r = queue.pop(0)
+                    r.admitted = now()
+                    used += r.bytes
+                    th = threading.Thread(target=worker, args=(r,), daemon=True)
+                    running[r.rid] = (r, th)
+                    th.start()
+                if queue and not running and queue[0].bytes > self.hbm_budget:
+                    r = queue.pop(0)
+                    r.error = "exceeds the memory budget"
+                    r.finished = now()
+                    finished.append(r)
+            self.log.append({"t": round(now(), 4), "queued": len(queue), "running": len(running),
+                             "hbm_used": used})
+            time.sleep(0.002)
+        wall = now()
+        ok = [r for r in finished if r.error is None]
+        tts = sorted((r.finished - r.arrival * time_scale) for r in ok)
+        dof_steps = sum(3 * r.N * r.N * (r.k + 1) ** 2 * r.steps for r in ok)
+
+        def pct(p):
+            return tts[min(len(tts) - 1, max(0, math.ceil(p * len(tts)) - 1))] if tts else None
+
+        return {"requests": len(finished), "completed": len(ok), "wall_s": wall,
+                "throughput_dof_steps_per_s": dof_steps / wall if wall > 0 else None,
+                "tts_p50_s": pct(0.5), "tts_p99_s": pct(0.99),
+                "max_running": max((e["running"] for e in self.log), default=0),
+                "max_queued": max((e["queued"] for e in self.log), default=0),
+                "errors": [r.error for r in finished if r.error]}

@@ -285,3 +285,42 @@ def test_mixed_bump8_two_hundred_steps():
 def test_mixed_standing_wave_hundred_steps():
     m, qa, qo, _ = _run_pair(8, 3, "standing", 100, dt=0.01, precision="mixed")
     assert max(_rel(m, qa, qo)) <= 1e-6
+
+
+# ---- explicit RK DG (the paper's comparison scheme) ---------------------------------------------
+@pytest.mark.parametrize("scheme,N,k,steps", [("rk2", 8, 3, 5), ("rk3", 8, 3, 5), ("rk2", 13, 2, 3),
+                                              ("rk3", 6, 4, 4)])
+def test_explicit_rk_matches_oracle(scheme, N, k, steps):
+    m, h, hu, hv, b = user_state(N, k, "large")
+    q, phiB = oracle_state(m, h, hu, hv, b)
+    dx_min = m.h / 2 * np.diff(m.xi).min()
+    dt = 0.2 * dx_min / 1.2                    # gravity Courant 0.2: inside the explicit limit
+    qo = imex.ExplicitRK(m, phiB, dt, scheme).run(q, steps)
+    with _sim(m, b, dt, scheme=scheme) as s:
+        s.set_state(h, hu, hv)
+        s.step(steps)
+        qa = _q_of(m, *s.get_state(), b)
+        with pytest.raises(hd.HdgdgError) as ei:
+            s.stage_solve(flat(q))
+        assert ei.value.status == hd.EINVAL
+    assert max(_rel(m, qa, qo)) <= 1e-11
+
+
+def test_explicit_blows_up_where_imex_does_not():
+    """Sec. 7: at a gravity Courant number of 4 the explicit RK2 DG fails (non-finite state or a
+    state far outside the data) while ARS2 HDG-DG stays bounded, on the 8 x 8 bump."""
+    m, h, hu, hv, b = user_state(8, 2, "bump8")
+    dt = 4.0 * (m.h / 2 * np.diff(m.xi).min())
+    with _sim(m, b, dt, scheme="rk2") as s:
+        s.set_state(h, hu, hv)
+        blew = False
+        try:
+            s.step(40)
+            blew = np.abs(s.get_state()[0] - 1.0).max() > 1.0
+        except hd.HdgdgError as ex:
+            blew = ex.status == hd.ENONFINITE
+    assert blew
+    with _sim(m, b, dt) as s:
+        s.set_state(h, hu, hv)
+        s.step(40)
+        assert np.abs(s.get_state()[0] - 1.0).max() < 0.011
