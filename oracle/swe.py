@@ -19,7 +19,8 @@ Readings where the paper is silent (all listed in the design notes):
 * grad phi_B: nodal derivative of the nodal phi_B;
 * trace space: nodal P^k on each edge at the GLL points, i.e. the element face nodes.
 
-Mesh conventions: unit square, N x N elements, element e = ey*N + ex, node (i, j) with
+Mesh conventions (periodic unit square by default; see ``Mesh`` for walls): N x N
+elements, element e = ey*N + ex, node (i, j) with
 i along x fastest at GLL points xi_i: x = (ex + (1 + xi_i)/2)/N.  Local faces
 0 = x-minus (left), 1 = x-plus (right), 2 = y-minus (bottom), 3 = y-plus (top).  Edge r < N^2
 is the right face of element r; edge N^2 + r is the top face of element r.  Arrays of
@@ -34,15 +35,24 @@ OPPOSITE_FACE = np.array([1, 0, 3, 2])
 
 
 class Mesh:
-    """Periodic N x N uniform quadrilateral mesh of [0,1]^2 with degree-k GLL nodes."""
+    """Uniform N x N quadrilateral mesh of [x0, x0+L]^2 with degree-k GLL nodes.
 
-    def __init__(self, N, k):
-        if N < 2:
+    boundary='periodic' (default): the unit-square torus; edge r < N^2 is the right face of
+    element r and edge N^2 + r its top face.  boundary='wall': reflecting walls on the four
+    sides (Sec. 4.3, eq. reflection); x-edges are numbered ey*(N+1) + ix (ix = 0..N) and
+    y-edges N(N+1) + iy*N + ex (iy = 0..N); a face on the wall has no neighbour (-1) and sees
+    the mirror state of its own element instead.
+    """
+
+    def __init__(self, N, k, boundary="periodic", x0=0.0, length=1.0):
+        if boundary == "periodic" and N < 2:
             raise ValueError("periodic mesh needs N >= 2")
+        if boundary not in ("periodic", "wall"):
+            raise ValueError(boundary)
         self.N, self.k, self.P = N, k, k + 1
+        self.boundary = boundary
         self.n_el = N * N
-        self.n_edges = 2 * N * N
-        self.h = 1.0 / N
+        self.h = length / N
         self.xi, self.w = gll_nodes_weights(k)
         self.D = lagrange_derivative_matrix(self.xi)
         self.J = (self.h / 2.0) ** 2          # area Jacobian of the reference map
@@ -50,16 +60,28 @@ class Mesh:
         self.face_jac = self.h / 2.0          # length Jacobian of every face
         e = np.arange(self.n_el)
         ex, ey = e % N, e // N
-        self.x = np.broadcast_to((ex[:, None, None] + (1.0 + self.xi[None, None, :]) / 2.0) / N,
+        self.x = np.broadcast_to(x0 + (ex[:, None, None] + (1.0 + self.xi[None, None, :]) / 2.0) * self.h,
                                  (self.n_el, self.P, self.P)).copy()
-        self.y = np.broadcast_to((ey[:, None, None] + (1.0 + self.xi[None, :, None]) / 2.0) / N,
+        self.y = np.broadcast_to(x0 + (ey[:, None, None] + (1.0 + self.xi[None, :, None]) / 2.0) * self.h,
                                  (self.n_el, self.P, self.P)).copy()
-        left = ey * N + (ex - 1) % N
-        right = ey * N + (ex + 1) % N
-        bottom = ((ey - 1) % N) * N + ex
-        top = ((ey + 1) % N) * N + ex
-        self.nbr = np.stack([left, right, bottom, top], axis=1)            # [e, f]
-        self.edge_of_face = np.stack([left, e, N * N + bottom, N * N + e], axis=1)
+        if boundary == "periodic":
+            left = ey * N + (ex - 1) % N
+            right = ey * N + (ex + 1) % N
+            bottom = ((ey - 1) % N) * N + ex
+            top = ((ey + 1) % N) * N + ex
+            self.nbr = np.stack([left, right, bottom, top], axis=1)            # [e, f]
+            self.edge_of_face = np.stack([left, e, N * N + bottom, N * N + e], axis=1)
+            self.n_edges = 2 * N * N
+        else:
+            left = np.where(ex > 0, ey * N + ex - 1, -1)
+            right = np.where(ex < N - 1, ey * N + ex + 1, -1)
+            bottom = np.where(ey > 0, (ey - 1) * N + ex, -1)
+            top = np.where(ey < N - 1, (ey + 1) * N + ex, -1)
+            self.nbr = np.stack([left, right, bottom, top], axis=1)
+            nx = N * (N + 1)
+            self.edge_of_face = np.stack([ey * (N + 1) + ex, ey * (N + 1) + ex + 1,
+                                          nx + ey * N + ex, nx + (ey + 1) * N + ex], axis=1)
+            self.n_edges = 2 * N * (N + 1)
         # mass-matrix diagonal per node (tensor-product GLL): J w_i w_j, shape [j, i]
         self.mass = self.J * np.outer(self.w, self.w)
 
@@ -81,9 +103,23 @@ class Mesh:
         else:
             r[..., :, P - 1, :] += val
 
+    def wall(self, f):
+        """Boolean [e]: face f of the element lies on a wall."""
+        return self.nbr[:, f] < 0
+
     def neighbour_face_values(self, u, f):
-        """Values of u seen from the other side of face f (the neighbour's opposite face)."""
-        return self.face_values(u[..., self.nbr[:, f], :, :], OPPOSITE_FACE[f])
+        """Scalar field u seen from the other side of face f (the neighbour's opposite face; on a
+        wall, the element's own value)."""
+        nb = np.where(self.nbr[:, f] < 0, np.arange(self.n_el), self.nbr[:, f])
+        other = self.face_values(u[..., nb, :, :], OPPOSITE_FACE[f])
+        own = self.face_values(u, f)
+        return np.where(self.wall(f)[:, None], own, other)
+
+    def neighbour_state(self, q, f):
+        """State q = (phi_eta, U, V) across face f; on a wall the mirror state of eq. reflection:
+        phi^+ = phi^-, U^+ = U^- - 2 (U^- . n) n."""
+        qp = np.stack([self.neighbour_face_values(q[c], f) for c in range(3)])
+        return np.where(self.wall(f)[None, :, None], reflect(self.face_values(q, f), FACE_NORMALS[f]), qp)
 
     # -- trace vectors ---------------------------------------------------------------
     def element_traces(self, lam_g):
@@ -103,6 +139,13 @@ class Mesh:
             t[:, f, :] = np.maximum(np.sqrt(self.face_values(phiB, f)),
                                     np.sqrt(self.neighbour_face_values(phiB, f)))
         return t
+
+
+def reflect(q_face, n):
+    """Mirror state across a wall with unit normal n (eq. reflection)."""
+    ph, U, V = q_face
+    un = U * n[0] + V * n[1]
+    return np.stack([ph, U - 2.0 * un * n[0], V - 2.0 * un * n[1]])
 
 
 # -- fluxes (Sec. 3.1) ------------------------------------------------------------------
@@ -165,7 +208,7 @@ def rusanov_nl_normal_flux(mesh, q, phiB, f):
     """
     n = FACE_NORMALS[f]
     qm = mesh.face_values(q, f)
-    qp = mesh.neighbour_face_values(q, f)
+    qp = mesh.neighbour_state(q, f)
     bm = mesh.face_values(phiB, f)
     bp = mesh.neighbour_face_values(phiB, f)
     Fxm, Fym = flux_full(qm, bm)
@@ -198,7 +241,7 @@ def rusanov_full_normal_flux(mesh, q, phiB, f):
     """F* . n of eq. Full_russanov on face f of every element: {F} . n + tau*/2 (q^- - q^+)."""
     n = FACE_NORMALS[f]
     qm = mesh.face_values(q, f)
-    qp = mesh.neighbour_face_values(q, f)
+    qp = mesh.neighbour_state(q, f)
     bm = mesh.face_values(phiB, f)
     bp = mesh.neighbour_face_values(phiB, f)
     Fxm, Fym = flux_full(qm, bm)
@@ -255,12 +298,17 @@ def flux_contributions(mesh, Q, lam_e, phiB, tau_e):
     """Each element's share of Flx: <Fhat_L . n_K, mu> on its four faces, [3, e, f, b].
 
     Summing the two shares that meet on an edge (``Mesh.assemble_edges``) gives
-    <[[Fhat_L . n]], mu>_e of eq. HDGcont at every trace node.
+    <[[Fhat_L . n]], mu>_e of eq. HDGcont at every trace node.  On a wall the second share is
+    the mirror element's (eq. reflection with eq. HDGcont, which yields eq. reflectionBC).
     """
     out = np.zeros((3, mesh.n_el, 4, mesh.P))
     for f in range(4):
-        fn = hdg_normal_flux(mesh.face_values(Q, f), lam_e[:, :, f, :], mesh.face_values(phiB, f),
-                             tau_e[:, f, :], FACE_NORMALS[f])
+        n = FACE_NORMALS[f]
+        qf, bf = mesh.face_values(Q, f), mesh.face_values(phiB, f)
+        fn = hdg_normal_flux(qf, lam_e[:, :, f, :], bf, tau_e[:, f, :], n)
+        # on a wall the mirror element (eq. reflection) contributes its share with normal -n
+        ghost = hdg_normal_flux(reflect(qf, n), lam_e[:, :, f, :], bf, tau_e[:, f, :], -n)
+        fn = fn + np.where(mesh.wall(f)[None, :, None], ghost, 0.0)
         out[:, :, f, :] = mesh.face_jac * mesh.w * fn
     return out
 

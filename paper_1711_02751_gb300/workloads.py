@@ -107,6 +107,28 @@ def standing_wave_state(x, y, eps=1e-3, t=0.0):
     return H0 + eta / G, U / G, V / G, np.zeros_like(x)
 
 
+def standing_wave_walls_state(x, y, eps=1e-3, t=0.0):
+    """Linear standing gravity wave in the walled unit square (flat bottom, g = H0 = 1):
+    phi_eta = eps cos(pi x) cos(pi y) cos(w t), U = eps/sqrt2 sin(pi x) cos(pi y) sin(w t),
+    V = eps/sqrt2 cos(pi x) sin(pi y) sin(w t), w = pi sqrt(2); U.n = 0 on the walls."""
+    w = math.pi * math.sqrt(2.0)
+    cx, sx = np.cos(math.pi * x), np.sin(math.pi * x)
+    cy, sy = np.cos(math.pi * y), np.sin(math.pi * y)
+    eta = eps * cx * cy * math.cos(w * t)
+    U = eps / math.sqrt(2.0) * sx * cy * math.sin(w * t)
+    V = eps / math.sqrt(2.0) * cx * sy * math.sin(w * t)
+    return H0 + eta / G, U / G, V / G, np.zeros_like(x)
+
+
+def perturbation_state(x, y, H_inf=100.0, sigma=0.1):
+    """The paper's water-height perturbation (Sec. 7.2) on [-1, 1]^2: H = H_inf +
+    exp(-(x^2 + y^2) / (2 sigma^2)), u = v = 0, flat bottom (b = H0 - H_inf with H0 = 1 so
+    that B = H_inf).  The paper does not print sigma; 0.1 is this library's reading."""
+    b = np.full_like(x, H0 - H_inf)
+    h = H_inf + np.exp(-(x * x + y * y) / (2.0 * sigma * sigma))
+    return h, np.zeros_like(x), np.zeros_like(x), b
+
+
 def advective_dt(x, h, hu, hv, n_side, cfl=0.5, g=G, H0_=H0):
     """Explicit-part time step dt = cfl * h_e / ((2k+1) * lambda_NL) for states [n_el, (k+1)^2].
 
@@ -143,4 +165,6 @@ def make_state(name, x, y, seed=None):
         return lake_at_rest_state(x, y)
     if kind == "standing":
         return standing_wave_state(x, y)
+    if kind == "standing_walls":
+        return standing_wave_walls_state(x, y)
     raise KeyError(name)
