@@ -15,10 +15,11 @@
  * Conventions shared by every entry point
  * -----------------------------------------
  * Mesh: element e = ey * N + ex; node n = j * (k+1) + i of an element, i along x, at GLL
- *   point xi_i: x = (ex + (1 + xi_i) / 2) / N, y = (ey + (1 + xi_j) / 2) / N.
- * Edges: edge r < N^2 is the right face of element r (normal +x); edge N^2 + r is the top
- *   face of element r (normal +y).  Trace vectors are [edge][field c][node b], b along the
- *   edge (y for right faces, x for top faces), fields (phi_hat, U_hat, V_hat).
+ *   point xi_i: x = x0 + (ex + (1 + xi_i) / 2) h, y = x0 + (ey + (1 + xi_j) / 2) h, h = length/N.
+ * Edges, periodic: edge r < N^2 is the right face of element r (normal +x); edge N^2 + r is
+ *   the top face of element r (normal +y).  Walls: vertical edge ey*(N+1) + ix (ix = 0..N,
+ *   normal +x) and horizontal edge N(N+1) + iy*N + ex (iy = 0..N, normal +y).  Trace vectors
+ *   are [edge][field c][node b], b along the edge, fields (phi_hat, U_hat, V_hat).
  * User state: h (total depth), hu, hv as host arrays [n_el][(k+1)^2], double.
  * Internal state q = (phi_eta, U, V) = (g (h - B), g hu, g hv), B = H0 - b, phi_B = g B
  *   (Sec. 3, "phi = g H, U = phi u"); the row-level entry points take q as host arrays
@@ -66,7 +67,7 @@ enum { HDGDG_FP64 = 0, HDGDG_MIXED = 1 };
 
 typedef struct {
     int n_side;          /* N >= 2: elements per side of the periodic unit square */
-    int degree_k;        /* polynomial degree k, 1 <= k <= 5 */
+    int degree_k;        /* polynomial degree k, 1 <= k <= 8 */
     double g;            /* gravitational acceleration (> 0) */
     double H0;           /* reference depth: B = H0 - b */
     int scheme;          /* HDGDG_ARS2, HDGDG_ARS3, HDGDG_RK2 or HDGDG_RK3 */
@@ -79,7 +80,14 @@ typedef struct {
     int krylov_restart;  /* GMRES(m) restart length m <= 31; <= 0 selects 8 */
     int krylov_maxit;    /* cap on GMRES iterations per stage solve; <= 0 selects 2000 */
     int linear_only;     /* 1: drop NL (linear gravity-wave runs); 0: full method */
+    int boundary;        /* HDGDG_PERIODIC (0) or HDGDG_WALLS (1): reflecting walls on the four
+                            sides (Sec. 4.3, eq. reflection; the trace condition becomes eq.
+                            reflectionBC) */
+    double x0;           /* domain [x0, x0 + length]^2 (node coordinates follow) */
+    double length;       /* side of the square domain; <= 0 selects 1 */
 } hdgdg_config;
+
+enum { HDGDG_PERIODIC = 0, HDGDG_WALLS = 1 };
 
 typedef struct {
     long long steps;              /* time steps completed since set_state */

@@ -39,11 +39,13 @@ struct Plan {
 constexpr int kMaxRestart = 31;   // the fused Gram-Schmidt kernels keep up to 32 basis vectors in registers
 
 bool valid(const hdgdg_config* c) {
-    return c && c->n_side >= 2 && c->n_side <= 32768 && c->degree_k >= 1 && c->degree_k <= kMaxP - 1 &&
+    return c && c->n_side >= (c->boundary == HDGDG_WALLS ? 1 : 2) && c->n_side <= 32768 && c->degree_k >= 1 && c->degree_k <= kMaxP - 1 &&
            std::isfinite(c->g) && c->g > 0.0 && std::isfinite(c->H0) && std::isfinite(c->dt) &&
            c->dt > 0.0 && c->scheme >= HDGDG_ARS2 && c->scheme <= HDGDG_RK3 &&
            (c->precision == HDGDG_FP64 || c->precision == HDGDG_MIXED) &&
            (c->linear_only == 0 || c->linear_only == 1) &&
+           (c->boundary == HDGDG_PERIODIC || c->boundary == HDGDG_WALLS) && std::isfinite(c->x0) &&
+           std::isfinite(c->length) &&
            c->krylov_restart <= kMaxRestart;
 }
 
@@ -54,7 +56,8 @@ int restart_of(const hdgdg_config* c) { return c->krylov_restart > 0 ? c->krylov
 Plan make_plan(const hdgdg_config* c) {
     Plan p;
     const size_t N = (size_t)c->n_side, P = (size_t)c->degree_k + 1;
-    const size_t n_el = N * N, n_edges = 2 * N * N, Np = P * P;
+    const size_t n_el = N * N, Np = P * P;
+    const size_t n_edges = c->boundary == HDGDG_WALLS ? 2 * N * (N + 1) : 2 * N * N;
     p.n = n_el * Np;
     p.NV = (int)(3 * Np);
     p.NF = (int)(3 * P);
@@ -89,6 +92,8 @@ Plan make_plan(const hdgdg_config* c) {
     b += 64 + sizeof(GmresCtl);                               // flags, GMRES control block
     p.persistent = b;
     p.setup_temp = n_el * (size_t)p.NT * p.NT * d + n_edges * 7 * (size_t)p.NF * p.NF * d;
+    if ((size_t)p.NV * 2 * p.NV * d > 200 * 1024)   // k >= 6: the local inverses' global workspace
+        p.setup_temp += (n_el < 512 ? n_el : 512) * (size_t)p.NV * 2 * p.NV * d;
     return p;
 }
 
@@ -148,9 +153,12 @@ Geom make_geom(const hdgdg_config* c, double* xi_out) {
     g.P = c->degree_k + 1;
     g.Np = g.P * g.P;
     g.n_el = g.N * g.N;
-    g.n_edges = 2 * g.n_el;
-    g.h = 1.0 / g.N;
-    g.two_over_h = 2.0 * g.N;
+    g.walls = c->boundary == HDGDG_WALLS ? 1 : 0;
+    g.n_edges = g.walls ? 2 * g.N * (g.N + 1) : 2 * g.n_el;
+    const double L = c->length > 0.0 ? c->length : 1.0;
+    g.x0 = c->x0;
+    g.h = L / g.N;
+    g.two_over_h = 2.0 / g.h;
     g.J = 0.25 * g.h * g.h;
     double xi[kMaxP];
     gll_tables(c->degree_k, xi, g.w, g.D);
@@ -570,10 +578,11 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
     }
     for (int r = 0; r < g.n_edges; ++r) {
         int em, fm, ep, fp;
-        edge_sides(r, g.N, &em, &fm, &ep, &fp);
+        edge_sides(r, g, &em, &fm, &ep, &fp);
         for (int b = 0; b < P; ++b) {
-            const double a1 = std::sqrt(phiB[(size_t)em * Np + face_node(fm, b, P)]);
-            const double a2 = std::sqrt(phiB[(size_t)ep * Np + face_node(fp, b, P)]);
+            // a wall edge has one side: tau = sqrt(phi_B) of that side
+            const double a1 = em >= 0 ? std::sqrt(phiB[(size_t)em * Np + face_node(fm, b, P)]) : 0.0;
+            const double a2 = ep >= 0 ? std::sqrt(phiB[(size_t)ep * Np + face_node(fp, b, P)]) : 0.0;
             tau[(size_t)r * P + b] = a1 > a2 ? a1 : a2;
         }
     }
@@ -677,8 +686,8 @@ hdgdg_status hdgdg_node_coords(const hdgdg_config* cfg, double* x, double* y) {
         const int ex = e % g.N, ey = e / g.N;
         for (int j = 0; j < g.P; ++j)
             for (int i = 0; i < g.P; ++i) {
-                x[(size_t)e * g.Np + j * g.P + i] = (ex + (1.0 + xi[i]) / 2.0) / g.N;
-                y[(size_t)e * g.Np + j * g.P + i] = (ey + (1.0 + xi[j]) / 2.0) / g.N;
+                x[(size_t)e * g.Np + j * g.P + i] = g.x0 + (ex + (1.0 + xi[i]) / 2.0) * g.h;
+                y[(size_t)e * g.Np + j * g.P + i] = g.x0 + (ey + (1.0 + xi[j]) / 2.0) * g.h;
             }
     }
     return HDGDG_OK;

@@ -22,12 +22,14 @@
 
 namespace hdgdg {
 
-constexpr int kMaxP = 6;   // degree k <= 5
+constexpr int kMaxP = 9;   // degree k <= 8
 
 // Mesh and GLL tables, passed by value to kernels.
 struct Geom {
     int N, P, Np, n_el, n_edges;
-    double h;                   // element size 1/N
+    int walls;                  // 0: periodic unit square; 1: reflecting walls (eq. reflection)
+    double x0;                  // domain [x0, x0 + N h]^2
+    double h;                   // element size (domain length / N)
     double two_over_h;          // d(xi)/dx
     double inv_w0;              // 1 / w_0 (= 1 / w_k): face lift of the collocated mass matrix
     double J;                   // area Jacobian (h/2)^2
@@ -40,8 +42,20 @@ __host__ __device__ inline int face_node(int f, int b, int P) {
     return f == 0 ? b * P : f == 1 ? b * P + P - 1 : f == 2 ? b : (P - 1) * P + b;
 }
 
-__host__ __device__ inline int edge_of_face(int e, int f, int N) {
-    const int ex = e % N, ey = e / N;
+// Connectivity of the N x N mesh.  Periodic: edge r < N^2 is face 1 of element r and edge
+// N^2 + r face 3 of element r.  Walls: x-edges ey*(N+1) + ix (ix = 0..N), y-edges
+// N(N+1) + iy*N + ex (iy = 0..N); a face on a wall has no neighbour (-1).
+__host__ __device__ inline int edge_of_face(int e, int f, const Geom& g) {
+    const int N = g.N, ex = e % N, ey = e / N;
+    if (g.walls) {
+        const int nx = N * (N + 1);
+        switch (f) {
+            case 0: return ey * (N + 1) + ex;
+            case 1: return ey * (N + 1) + ex + 1;
+            case 2: return nx + ey * N + ex;
+            default: return nx + (ey + 1) * N + ex;
+        }
+    }
     switch (f) {
         case 0: return ey * N + (ex + N - 1) % N;
         case 1: return e;
@@ -50,8 +64,16 @@ __host__ __device__ inline int edge_of_face(int e, int f, int N) {
     }
 }
 
-__host__ __device__ inline int neighbour(int e, int f, int N) {
-    const int ex = e % N, ey = e / N;
+__host__ __device__ inline int neighbour(int e, int f, const Geom& g) {
+    const int N = g.N, ex = e % N, ey = e / N;
+    if (g.walls) {
+        switch (f) {
+            case 0: return ex > 0 ? e - 1 : -1;
+            case 1: return ex < N - 1 ? e + 1 : -1;
+            case 2: return ey > 0 ? e - N : -1;
+            default: return ey < N - 1 ? e + N : -1;
+        }
+    }
     switch (f) {
         case 0: return ey * N + (ex + N - 1) % N;
         case 1: return ey * N + (ex + 1) % N;
@@ -60,13 +82,32 @@ __host__ __device__ inline int neighbour(int e, int f, int N) {
     }
 }
 
-// Minus / plus element and their faces for edge r.
-__host__ __device__ inline void edge_sides(int r, int N, int* em, int* fm, int* ep, int* fp) {
-    if (r < N * N) { *em = r; *fm = 1; *ep = neighbour(r, 1, N); *fp = 0; }
-    else { const int e = r - N * N; *em = e; *fm = 3; *ep = neighbour(e, 3, N); *fp = 2; }
+// Minus side (face 1 or 3: normal +x / +y) and plus side (face 0 or 2) of edge r; an absent
+// side (wall) is -1 with the face it would have had.
+__host__ __device__ inline void edge_sides(int r, const Geom& g, int* em, int* fm, int* ep, int* fp) {
+    const int N = g.N;
+    if (g.walls) {
+        const int nx = N * (N + 1);
+        if (r < nx) {
+            const int ey = r / (N + 1), ix = r % (N + 1);
+            *em = ix >= 1 ? ey * N + ix - 1 : -1;
+            *ep = ix < N ? ey * N + ix : -1;
+            *fm = 1;
+            *fp = 0;
+        } else {
+            const int rr = r - nx, iy = rr / N, ex = rr % N;
+            *em = iy >= 1 ? (iy - 1) * N + ex : -1;
+            *ep = iy < N ? iy * N + ex : -1;
+            *fm = 3;
+            *fp = 2;
+        }
+        return;
+    }
+    if (r < N * N) { *em = r; *fm = 1; *ep = neighbour(r, 1, g); *fp = 0; }
+    else { const int e = r - N * N; *em = e; *fm = 3; *ep = neighbour(e, 3, g); *fp = 2; }
 }
 
-// Host-built mesh and GLL tables of an N x N, degree-k mesh (no GPU call).
+// Host-built periodic unit-square mesh and GLL tables of an N x N, degree-k mesh (no GPU call).
 Geom host_geom(int N, int k);
 
 // Kernels launched by this library since load (every launcher adds its own launches).

@@ -48,15 +48,24 @@ dg_face_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ 
     if (t >= g.n_edges * P) return;
     const int r = t / P, b = t % P;
     int em, fm, ep, fp;
-    edge_sides(r, g.N, &em, &fm, &ep, &fp);
+    edge_sides(r, g, &em, &fm, &ep, &fp);
     const size_t fs = (size_t)g.n_el * Np;
-    const size_t om = (size_t)em * Np + face_node(fm, b, P);
-    const size_t op = (size_t)ep * Np + face_node(fp, b, P);
-    const double phm = q[om], Um = q[fs + om], Vm = q[2 * fs + om], pbm = phiB[om];
-    const double php = q[op], Up = q[fs + op], Vp = q[2 * fs + op], pbp = phiB[op];
+    const bool xedge = fm == 1;
+    double phm, Um, Vm, pbm, php, Up, Vp, pbp;
+    if (em >= 0) {
+        const size_t om = (size_t)em * Np + face_node(fm, b, P);
+        phm = q[om]; Um = q[fs + om]; Vm = q[2 * fs + om]; pbm = phiB[om];
+    }
+    if (ep >= 0) {
+        const size_t op = (size_t)ep * Np + face_node(fp, b, P);
+        php = q[op]; Up = q[fs + op]; Vp = q[2 * fs + op]; pbp = phiB[op];
+    }
+    // a wall edge sees the mirror state of its one element (eq. reflection): same phi and
+    // tangential momentum, opposite normal momentum
+    if (em < 0) { phm = php; pbm = pbp; Um = xedge ? -Up : Up; Vm = xedge ? Vp : -Vp; }
+    if (ep < 0) { php = phm; pbp = pbm; Up = xedge ? -Um : Um; Vp = xedge ? Vm : -Vm; }
     const double Phm = phm + pbm, Php = php + pbp;
     const double im = 1.0 / Phm, ip = 1.0 / Php;
-    const bool xedge = fm == 1;
     // normal (n) and tangential (t) momentum components along this edge's +axis
     const double Unm = xedge ? Um : Vm, Utm = xedge ? Vm : Um;
     const double Unp = xedge ? Up : Vp, Utp = xedge ? Vp : Up;
@@ -146,7 +155,7 @@ dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict_
                         (f == 3 && j == P - 1);
         if (!on) continue;
         const int b = (f < 2) ? j : i;
-        const double* fl = fface + (size_t)edge_of_face(e, f, g.N) * 3 * P;
+        const double* fl = fface + (size_t)edge_of_face(e, f, g) * 3 * P;
         const double sgn = (f & 1) ? lift : -lift;   // outward normal is + on faces 1, 3
         rph -= sgn * fl[b];
         rU -= sgn * fl[P + b];
@@ -271,6 +280,9 @@ cudaError_t launch_dg_nl(const Geom& g, const double* q, const double* phiB, con
         case 4: return dg_launch<4, false>(g, q, phiB, tau_edge, scale, fface, out, s);
         case 5: return dg_launch<5, false>(g, q, phiB, tau_edge, scale, fface, out, s);
         case 6: return dg_launch<6, false>(g, q, phiB, tau_edge, scale, fface, out, s);
+        case 7: return dg_launch<7, false>(g, q, phiB, tau_edge, scale, fface, out, s);
+        case 8: return dg_launch<8, false>(g, q, phiB, tau_edge, scale, fface, out, s);
+        case 9: return dg_launch<9, false>(g, q, phiB, tau_edge, scale, fface, out, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -283,6 +295,9 @@ cudaError_t launch_dg_full(const Geom& g, const double* q, const double* phiB, d
         case 4: return dg_launch<4, true>(g, q, phiB, nullptr, scale, fface, out, s);
         case 5: return dg_launch<5, true>(g, q, phiB, nullptr, scale, fface, out, s);
         case 6: return dg_launch<6, true>(g, q, phiB, nullptr, scale, fface, out, s);
+        case 7: return dg_launch<7, true>(g, q, phiB, nullptr, scale, fface, out, s);
+        case 8: return dg_launch<8, true>(g, q, phiB, nullptr, scale, fface, out, s);
+        case 9: return dg_launch<9, true>(g, q, phiB, nullptr, scale, fface, out, s);
         default: return cudaErrorInvalidValue;
     }
 }

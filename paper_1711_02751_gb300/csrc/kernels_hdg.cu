@@ -64,23 +64,25 @@ __device__ void gauss_jordan(double* M, int n, int* singular, int* s_piv) {
 
 // One CTA per element.  Builds A_e, inverts it, writes A^{-1} (column major) and the
 // element Schur block S_e = D_e - C_e A^{-1} B_e in local trace order (f, c, b).
-template <int P>
+// The augmented matrix lives in shared memory when it fits (k <= 5); above that it lives in
+// a global workspace of one [NV][2 NV] slab per CTA (gwork, elements e0 .. e0 + gridDim.x).
+template <int P, bool GMEM>
 __global__ void build_local_kernel(Geom g, const double* __restrict__ phiB,
                                    const double* __restrict__ tau_edge, double dta,
                                    double* __restrict__ Ainv, double* __restrict__ Se,
-                                   int* singular) {
+                                   int* singular, int e0, double* __restrict__ gwork) {
     constexpr int Np = P * P, NV = 3 * Np, NT = 12 * P;
     extern __shared__ double sm[];
-    double* M = sm;                       // [NV][2 NV]
-    double* pb = M + NV * 2 * NV;         // [Np]
-    double* tau = pb + Np;                // [4][P]
+    double* M = GMEM ? gwork + (size_t)blockIdx.x * NV * 2 * NV : sm;   // [NV][2 NV]
+    double* pb = GMEM ? sm : M + NV * 2 * NV;                              // [Np]
+    double* tau = pb + Np;                                                 // [4][P]
     __shared__ int s_piv;
-    const int e = blockIdx.x;
+    const int e = e0 + blockIdx.x;
     const int ld = 2 * NV;
 
     for (int n = threadIdx.x; n < Np; n += blockDim.x) pb[n] = phiB[(size_t)e * Np + n];
     for (int t = threadIdx.x; t < 4 * P; t += blockDim.x)
-        tau[t] = tau_edge[(size_t)edge_of_face(e, t / P, g.N) * P + t % P];
+        tau[t] = tau_edge[(size_t)edge_of_face(e, t / P, g) * P + t % P];
     for (int t = threadIdx.x; t < NV * ld; t += blockDim.x) {
         const int r = t / ld, c = t % ld;
         M[t] = (c == r || c == r + NV) ? 1.0 : 0.0;
@@ -162,12 +164,22 @@ __global__ void build_local_kernel(Geom g, const double* __restrict__ phiB,
         const double aph = M[(0 * Np + n1) * ld + col];
         const double aU = M[(1 * Np + n1) * ld + col];
         const double aV = M[(2 * Np + n1) * ld + col];
-        double cz;
-        if (c1 == 0) cz = nx * aU + ny * aV + t1 * aph;
-        else if (c1 == 1) cz = nx * pb[n1] * aph + t1 * aU;
-        else cz = ny * pb[n1] * aph + t1 * aV;
+        double cz, d = t1;
+        if (neighbour(e, f1, g) >= 0) {
+            if (c1 == 0) cz = nx * aU + ny * aV + t1 * aph;
+            else if (c1 == 1) cz = nx * pb[n1] * aph + t1 * aU;
+            else cz = ny * pb[n1] * aph + t1 * aV;
+        } else {
+            // wall face: the element's share plus its mirror's (state R q, normal -n), i.e.
+            // 2 (n.U + tau phi) for phi_hat, 2 tau U_tangential for the momentum rows, D = -2 tau
+            const double un = nx * aU + ny * aV;
+            if (c1 == 0) cz = 2.0 * (un + t1 * aph);
+            else if (c1 == 1) cz = 2.0 * t1 * (aU - un * nx);
+            else cz = 2.0 * t1 * (aV - un * ny);
+            d = 2.0 * t1;
+        }
         double v = beta * t2 * cz;
-        if (rr == cc) v -= t1;
+        if (rr == cc) v -= d;
         S[t] = v;
     }
 }
@@ -180,21 +192,24 @@ __global__ void gather_rows_kernel(Geom g, const double* __restrict__ Se, double
     constexpr int NF = 3 * P, NT = 12 * P;
     const int r = blockIdx.x;
     int em, fm, ep, fp;
-    edge_sides(r, g.N, &em, &fm, &ep, &fp);
-    const double* Sm = Se + (size_t)em * NT * NT;
-    const double* Sp = Se + (size_t)ep * NT * NT;
+    edge_sides(r, g, &em, &fm, &ep, &fp);
+    // a wall edge has one element: its slots carry that element's blocks, the absent side's
+    // three slots are zero blocks pointing at the edge itself
+    const double* Sm = em >= 0 ? Se + (size_t)em * NT * NT : nullptr;
+    const double* Sp = ep >= 0 ? Se + (size_t)ep * NT * NT : nullptr;
     double* row = S7 + (size_t)r * 7 * NF * NF;
     for (int t = threadIdx.x; t < 7 * NF * NF; t += blockDim.x) {
         const int slot = t / (NF * NF), ii = (t / NF) % NF, jj = t % NF;
-        double v;
+        double v = 0.0;
         if (slot == 0) {
-            v = Sm[(fm * NF + ii) * NT + fm * NF + jj] + Sp[(fp * NF + ii) * NT + fp * NF + jj];
+            if (Sm) v += Sm[(fm * NF + ii) * NT + fm * NF + jj];
+            if (Sp) v += Sp[(fp * NF + ii) * NT + fp * NF + jj];
         } else {
             const int side = (slot - 1) / 3, k = (slot - 1) % 3;
             const int fs = side == 0 ? fm : fp;
             const int fo = k < fs ? k : k + 1;        // k-th face other than fs, ascending
             const double* Sx = side == 0 ? Sm : Sp;
-            v = Sx[(fs * NF + ii) * NT + fo * NF + jj];
+            if (Sx) v = Sx[(fs * NF + ii) * NT + fo * NF + jj];
         }
         row[t] = v;
         if (slot == 0) Srr[(size_t)r * NF * NF + jj * NF + ii] = v;   // column major copy
@@ -204,7 +219,8 @@ __global__ void gather_rows_kernel(Geom g, const double* __restrict__ Se, double
         const int side = (slot - 1) / 3, k = (slot - 1) % 3;
         const int fs = side == 0 ? fm : fp;
         const int fo = k < fs ? k : k + 1;
-        Scol[(size_t)r * 6 + threadIdx.x] = edge_of_face(side == 0 ? em : ep, fo, g.N);
+        const int el = side == 0 ? em : ep;
+        Scol[(size_t)r * 6 + threadIdx.x] = el >= 0 ? edge_of_face(el, fo, g) : r;
     }
 }
 
@@ -276,16 +292,21 @@ __global__ void edge_rhs_kernel(Geom g, const double* __restrict__ Z, const doub
     if (t >= g.n_edges * P) return;
     const int r = t / P, b = t % P;
     int em, fm, ep, fp;
-    edge_sides(r, g.N, &em, &fm, &ep, &fp);
+    edge_sides(r, g, &em, &fm, &ep, &fp);
     const size_t fs = (size_t)g.n_el * Np;
     const double tau = tau_edge[(size_t)r * P + b];
     const bool xedge = fm == 1;
     double acc[3] = {0.0, 0.0, 0.0};
+    const int e_in = em >= 0 ? em : ep, f_in = em >= 0 ? fm : fp;   // an element that exists
     for (int side = 0; side < 2; ++side) {
-        const int e = side == 0 ? em : ep;
+        int e = side == 0 ? em : ep;
         const int f = side == 0 ? fm : fp;
-        const size_t o = (size_t)e * Np + face_node(f, b, P);
-        const double zph = Z[o], zU = Z[fs + o], zV = Z[2 * fs + o], pb = phiB[o];
+        const bool mirror = e < 0;                 // wall: the mirror of the other element
+        if (mirror) e = e_in;
+        const size_t o = (size_t)e * Np + face_node(mirror ? f_in : f, b, P);
+        double zph = Z[o], zU = Z[fs + o], zV = Z[2 * fs + o];
+        const double pb = phiB[o];
+        if (mirror) { if (xedge) zU = -zU; else zV = -zV; }
         const double sgn = side == 0 ? 1.0 : -1.0;
         const double nx = xedge ? sgn : 0.0, ny = xedge ? 0.0 : sgn;
         acc[0] += nx * zU + ny * zV + tau * zph;
@@ -319,7 +340,7 @@ __global__ void recover_kernel(Geom g, const double* __restrict__ Ainv, const do
                             (f == 3 && j == P - 1);
             if (!on) continue;
             const int b = (f < 2) ? j : i;
-            const int ed = edge_of_face(e, f, g.N);
+            const int ed = edge_of_face(e, f, g);
             u += tau_edge[(size_t)ed * P + b] * qhat[(size_t)ed * NF + c * P + b];
         }
         su[le][r] = u;
@@ -346,13 +367,31 @@ template <int P>
 cudaError_t build_local_launch(const Geom& g, const double* phiB, const double* tau_edge, double dta,
                                double* Ainv, double* Se, int* singular, cudaStream_t s) {
     constexpr int NV = 3 * P * P;
-    const size_t smem = (size_t)(NV * 2 * NV + P * P + 4 * P) * sizeof(double);
-    cudaError_t err = cudaFuncSetAttribute(build_local_kernel<P>,
+    constexpr bool kGmem = (size_t)NV * 2 * NV * sizeof(double) > 200 * 1024;
+    const size_t small = (size_t)(P * P + 4 * P) * sizeof(double);
+    const size_t smem = kGmem ? small : (size_t)NV * 2 * NV * sizeof(double) + small;
+    cudaError_t err = cudaFuncSetAttribute(build_local_kernel<P, kGmem>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    build_local_kernel<P><<<g.n_el, 128, smem, s>>>(g, phiB, tau_edge, dta, Ainv, Se, singular);
-    count_launches(1);
-    return cudaGetLastError();
+    if (!kGmem) {
+        build_local_kernel<P, false><<<g.n_el, 128, smem, s>>>(g, phiB, tau_edge, dta, Ainv, Se, singular, 0,
+                                                               nullptr);
+        count_launches(1);
+        return cudaGetLastError();
+    }
+    // global workspace: chunks of at most 512 elements (NV = 243 at k = 8: 0.9 MB per element)
+    const int chunk = g.n_el < 512 ? g.n_el : 512;
+    double* work = nullptr;
+    err = cudaMallocAsync(&work, (size_t)chunk * NV * 2 * NV * sizeof(double), s);
+    if (err != cudaSuccess) return err;
+    for (int e0 = 0; e0 < g.n_el; e0 += chunk) {
+        const int n = g.n_el - e0 < chunk ? g.n_el - e0 : chunk;
+        build_local_kernel<P, true><<<n, 256, smem, s>>>(g, phiB, tau_edge, dta, Ainv, Se, singular, e0, work);
+        count_launches(1);
+    }
+    err = cudaGetLastError();
+    cudaError_t e2 = cudaFreeAsync(work, s);
+    return err != cudaSuccess ? err : e2;
 }
 
 template <int P>
@@ -394,16 +433,6 @@ cudaError_t recover_launch(const Geom& g, const double* Ainv, const double* Z, c
 
 }  // namespace
 
-#define HDGDG_DISPATCH_P(CALL)                 \
-    switch (g.P) {                             \
-        case 2: return CALL<2>;                \
-        case 3: return CALL<3>;                \
-        case 4: return CALL<4>;                \
-        case 5: return CALL<5>;                \
-        case 6: return CALL<6>;                \
-        default: return cudaErrorInvalidValue; \
-    }
-
 cudaError_t launch_build_local(const Geom& g, const double* phiB, const double* tau_edge, double dta,
                                double* Ainv, double* Se, int* singular, cudaStream_t s) {
 #define CALL(P) build_local_launch<P>(g, phiB, tau_edge, dta, Ainv, Se, singular, s)
@@ -413,6 +442,9 @@ cudaError_t launch_build_local(const Geom& g, const double* phiB, const double* 
         case 4: return CALL(4);
         case 5: return CALL(5);
         case 6: return CALL(6);
+        case 7: return CALL(7);
+        case 8: return CALL(8);
+        case 9: return CALL(9);
         default: return cudaErrorInvalidValue;
     }
 #undef CALL
@@ -428,6 +460,9 @@ cudaError_t launch_assemble_trace(const Geom& g, const double* Se, double* S7, d
         case 4: return CALL(4);
         case 5: return CALL(5);
         case 6: return CALL(6);
+        case 7: return CALL(7);
+        case 8: return CALL(8);
+        case 9: return CALL(9);
         default: return cudaErrorInvalidValue;
     }
 #undef CALL
@@ -442,6 +477,9 @@ cudaError_t launch_condense(const Geom& g, const double* Ainv, const double* R1,
         case 4: return CALL(4);
         case 5: return CALL(5);
         case 6: return CALL(6);
+        case 7: return CALL(7);
+        case 8: return CALL(8);
+        case 9: return CALL(9);
         default: return cudaErrorInvalidValue;
     }
 #undef CALL
@@ -457,6 +495,9 @@ cudaError_t launch_recover(const Geom& g, const double* Ainv, const double* Z, c
         case 4: return CALL(4);
         case 5: return CALL(5);
         case 6: return CALL(6);
+        case 7: return CALL(7);
+        case 8: return CALL(8);
+        case 9: return CALL(9);
         default: return cudaErrorInvalidValue;
     }
 #undef CALL

@@ -350,6 +350,9 @@ cudaError_t spmv_dispatch(const Geom& g, const T* Stil, const int* Scol, const T
         case 4: return spmv_launch<12, T>(g.n_edges, Stil, Scol, x, y, s, done);
         case 5: return spmv_launch<15, T>(g.n_edges, Stil, Scol, x, y, s, done);
         case 6: return spmv_launch<18, T>(g.n_edges, Stil, Scol, x, y, s, done);
+        case 7: return spmv_launch<21, T>(g.n_edges, Stil, Scol, x, y, s, done);
+        case 8: return spmv_launch<24, T>(g.n_edges, Stil, Scol, x, y, s, done);
+        case 9: return spmv_launch<27, T>(g.n_edges, Stil, Scol, x, y, s, done);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -402,6 +405,9 @@ cudaError_t launch_block_diag(const Geom& g, const double* Bd, const double* x, 
         case 4: return block_diag_launch<12>(g.n_edges, Bd, x, y, s);
         case 5: return block_diag_launch<15>(g.n_edges, Bd, x, y, s);
         case 6: return block_diag_launch<18>(g.n_edges, Bd, x, y, s);
+        case 7: return block_diag_launch<21>(g.n_edges, Bd, x, y, s);
+        case 8: return block_diag_launch<24>(g.n_edges, Bd, x, y, s);
+        case 9: return block_diag_launch<27>(g.n_edges, Bd, x, y, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -15,6 +15,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ENONFINITE, ESTATE = range(7)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTCONVERGED", "ENONFINITE", "ESTATE"]
 SCHEMES = {"ars2": 0, "ars3": 1, "rk2": 2, "rk3": 3}
 PRECISIONS = {"fp64": 0, "mixed": 1}
+BOUNDARIES = {"periodic": 0, "wall": 1}
 
 EXPORTS = ["hdgdg_bytes_required", "hdgdg_node_coords", "hdgdg_create", "hdgdg_set_state",
            "hdgdg_step", "hdgdg_get_state", "hdgdg_get_stats", "hdgdg_last_error", "hdgdg_destroy",
@@ -36,7 +37,8 @@ class Config(ctypes.Structure):
                 ("H0", ctypes.c_double), ("scheme", ctypes.c_int), ("dt", ctypes.c_double),
                 ("precision", ctypes.c_int), ("krylov_rtol", ctypes.c_double),
                 ("krylov_restart", ctypes.c_int), ("krylov_maxit", ctypes.c_int),
-                ("linear_only", ctypes.c_int)]
+                ("linear_only", ctypes.c_int), ("boundary", ctypes.c_int), ("x0", ctypes.c_double),
+                ("length", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -95,18 +97,20 @@ def _f64(a, shape=None):
 
 
 def make_config(N, k, dt, g=1.0, H0=1.0, scheme="ars2", krylov_rtol=0.0, krylov_restart=0,
-                krylov_maxit=0, linear_only=False, precision="fp64"):
+                krylov_maxit=0, linear_only=False, precision="fp64", boundary="periodic", x0=0.0,
+                length=1.0):
     return Config(int(N), int(k), float(g), float(H0), SCHEMES[scheme], float(dt), PRECISIONS[precision],
-                  float(krylov_rtol), int(krylov_restart), int(krylov_maxit), int(bool(linear_only)))
+                  float(krylov_rtol), int(krylov_restart), int(krylov_maxit), int(bool(linear_only)),
+                  BOUNDARIES[boundary], float(x0), float(length))
 
 
 def bytes_required(cfg):
     return int(lib().hdgdg_bytes_required(ctypes.byref(cfg)))
 
 
-def node_coords(N, k):
+def node_coords(N, k, boundary="periodic", x0=0.0, length=1.0):
     """GLL node coordinates (x, y), each [N*N, (k+1)^2], from the library's own tables."""
-    cfg = make_config(N, k, 1.0)
+    cfg = make_config(N, k, 1.0, boundary=boundary, x0=x0, length=length)
     x = np.empty((N * N, (k + 1) ** 2))
     y = np.empty_like(x)
     st = lib().hdgdg_node_coords(ctypes.byref(cfg), _ptr(x), _ptr(y))
@@ -133,12 +137,13 @@ class Sim:
     """One simulation handle (hdgdg_create ... hdgdg_destroy)."""
 
     def __init__(self, N, k, dt, bottom=None, g=1.0, H0=1.0, scheme="ars2", stream=None,
-                 krylov_rtol=0.0, krylov_restart=0, krylov_maxit=0, linear_only=False, precision="fp64"):
+                 krylov_rtol=0.0, krylov_restart=0, krylov_maxit=0, linear_only=False, precision="fp64",
+                 boundary="periodic", x0=0.0, length=1.0):
         self.N, self.k, self.P = int(N), int(k), int(k) + 1
         self.n_el, self.Np = self.N * self.N, self.P * self.P
-        self.n_edges = 2 * self.n_el
+        self.n_edges = 2 * self.N * (self.N + 1) if boundary == "wall" else 2 * self.n_el
         self.cfg = make_config(N, k, dt, g, H0, scheme, krylov_rtol, krylov_restart, krylov_maxit,
-                               linear_only, precision)
+                               linear_only, precision, boundary, x0, length)
         self._h = ctypes.c_void_p(None)
         b = None if bottom is None else _f64(bottom, (self.n_el, self.Np))
         st = lib().hdgdg_create(ctypes.byref(self.cfg), None if b is None else _ptr(b),

@@ -41,7 +41,7 @@ def test_host_only_entry_points(libmod):
     cfg = libmod.make_config(8, 2, 0.625)
     assert libmod.bytes_required(cfg) > 0
     assert libmod.bytes_required(libmod.make_config(1, 2, 0.1)) == 0      # N < 2 rejected
-    assert libmod.bytes_required(libmod.make_config(4, 9, 0.1)) == 0      # k > 5 rejected
+    assert libmod.bytes_required(libmod.make_config(4, 9, 0.1)) == 0      # k > 8 rejected
     x, y = libmod.node_coords(4, 3)
     from oracle import swe
     m = swe.Mesh(4, 3)
