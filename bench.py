@@ -44,6 +44,8 @@ def _args():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="large512", choices=sorted(WORKLOADS))
     ap.add_argument("--restart", type=int, default=0, help="GMRES restart length (0: library default)")
+    ap.add_argument("--mixed-rtol", type=float, default=0.0,
+                    help="refinement tolerance of the mixed form (0: library default 1e-10)")
     ap.add_argument("--precisions", default="fp64,mixed",
                     help="forms to time; the headline is mixed when within 1e-6 of fp64")
     ap.add_argument("--no-e2e", action="store_true")
@@ -52,6 +54,11 @@ def _args():
                     help="run the continuous-batching request loop instead and print its line")
     ap.add_argument("--serving-requests", type=int, default=40)
     ap.add_argument("--serving-rate", type=float, default=4.0, help="Poisson arrivals per second")
+    ap.add_argument("--ensemble", action="store_true",
+                    help="run the batched ensemble (256 uneven instances at once) and print its line")
+    ap.add_argument("--ensemble-slots", type=int, default=16)
+    ap.add_argument("--paper-table", action="store_true",
+                    help="time the paper's water-height perturbation runs (Sec. 7.2) and print their line")
     ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--sample-steps", type=int, default=5, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -338,6 +345,71 @@ def serving_line(args):
     print(json.dumps(line), flush=True)
 
 
+PAPER_TABLE = [  # the paper's Table tab:waterdrop_wallclock (Sec. 7.2): scheme, dt, Cr, wall clock
+    ("rk2", 0.0001, 0.2, "18m 20s", 1100.0),
+    ("ars2", 0.0020, 4.0, "20m 41s", 1241.0),
+    ("ars2", 0.0200, 40.0, "2m 28s", 148.0),
+]
+
+
+def ensemble_line(args):
+    """Batched ensemble: 256 instances submitted at once, N in {16, 32, 64, 128}, k in {2, 3, 4},
+    own seeded bump and bottom amplitude U[0, 0.1], 100 steps each, mixed form; run as
+    independent handles overlapping on the device (no single persistent launch)."""
+    import torch
+    from paper_1711_02751_gb300 import serving
+    free, _ = torch.cuda.mem_get_info()
+    reqs = serving.ensemble_requests()
+    srv = serving.Server(hbm_budget=int(0.6 * free), max_slots=args.ensemble_slots, chunk=20)
+    summ = srv.serve(reqs)
+    line = {"metric": "batched ensemble: DOF-steps/s over 256 uneven instances", "unit": UNIT,
+            "value": summ["throughput_dof_steps_per_s"], "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f64+f32 (mixed form)", "data": "synthetic",
+            "config": {"workload": "256 instances, N in {16,32,64,128}, k in {2,3,4}, bottom amp U[0,0.1], "
+                                   "100 steps each, all submitted at t=0", "slots": args.ensemble_slots},
+            "wall_s": summ["wall_s"], "completed": summ["completed"], "errors": summ["errors"][:3],
+            "tts_p50_s": summ["tts_p50_s"], "tts_p99_s": summ["tts_p99_s"]}
+    print(json.dumps(line), flush=True)
+
+
+def paper_table_line():
+    """The paper's water-height perturbation on [-1,1]^2 (20 x 20 elements, p = 8, H_inf = 100,
+    g = 1, T = 0.16; walls and sigma = 0.1 are this library's readings), run to T with the
+    paper's three (scheme, dt) choices; time to solution on the GPU beside the paper's wall clock
+    (its hardware is not stated)."""
+    import torch
+    from paper_1711_02751_gb300 import hdgdg as hd
+    from paper_1711_02751_gb300 import workloads as W
+    N, k, T = 20, 8, 0.16
+    x, y = hd.node_coords(N, k, boundary="wall", x0=-1.0, length=2.0)
+    h, hu, hv, b = W.perturbation_state(x, y, H_inf=100.0, sigma=0.1)
+    rows = []
+    for scheme, dt, cr, paper_clock, paper_s in PAPER_TABLE:
+        steps = int(round(T / dt))
+        t0 = time.perf_counter()
+        sim = hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, scheme=scheme, boundary="wall", x0=-1.0,
+                     length=2.0, precision="fp64")
+        t_setup = time.perf_counter() - t0
+        sim.set_state(h, hu, hv)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        sim.step(steps)
+        out = sim.get_state()
+        t_run = time.perf_counter() - t1
+        st = sim.stats()
+        sim.close()
+        eta = out[0] - (W.H0 - b)
+        rows.append({"scheme": scheme, "dt": dt, "paper_Cr": cr, "steps": steps, "setup_s": t_setup,
+                     "run_s": t_run, "time_to_solution_s": t_setup + t_run, "paper_wall_clock": paper_clock,
+                     "paper_s": paper_s, "krylov_iterations": st["krylov_iterations"],
+                     "eta_max": float(eta.max()), "eta_min": float(eta.min())})
+    line = {"metric": "time to solution of the paper's water-height perturbation runs (Sec. 7.2)",
+            "unit": "s", "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "[-1,1]^2, 20x20 quads, p=8, H_inf=100, g=1, T=0.16, walls, sigma=0.1"},
+            "runs": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     if args.cpu_baseline_child:
@@ -350,6 +422,12 @@ def main():
         return
     if args.serving:
         serving_line(args)
+        return
+    if args.paper_table:
+        paper_table_line()
+        return
+    if args.ensemble:
+        ensemble_line(args)
         return
 
     import torch
@@ -378,7 +456,8 @@ def main():
     clk = None
     for precision in args.precisions.split(","):
         sim = hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, stream=stream.cuda_stream,
-                     krylov_restart=args.restart, precision=precision)
+                     krylov_restart=args.restart, precision=precision,
+                     krylov_rtol=args.mixed_rtol if precision == "mixed" else 0.0)
         sim.set_state(h, hu, hv)
         for _ in range(args.warmup):
             sim.step(1)

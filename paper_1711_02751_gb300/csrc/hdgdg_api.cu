@@ -216,6 +216,12 @@ Geom host_geom(int N, int k) {
 }
 }  // namespace hdgdg
 
+struct CycleGraph {
+    cudaGraphExec_t exec = nullptr;
+    const double* g = nullptr;     // right-hand side the graph was captured for
+    long long launches = 0;        // kernels per replay
+};
+
 struct hdgdg_sim {
     hdgdg_config cfg;
     Plan plan;
@@ -236,6 +242,7 @@ struct hdgdg_sim {
     float *Stil32 = nullptr, *V32 = nullptr, *w32 = nullptr;   // mixed precision only
     double *red = nullptr, *mred = nullptr, *dvals = nullptr;
     GmresCtl* ctl = nullptr;
+    CycleGraph cycle_graph[2];   // [FP64 form, mixed form]
     unsigned* flags = nullptr;
     double* hbuf = nullptr;   // pinned host scratch
     // run state
@@ -397,34 +404,67 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
     CU(launch_gmres_solve_init(ctl, tol, inner_rel, maxit, st));
     double rnorm = bnorm;
     int total = 0;
-    while (true) {
-        CU(launch_gmres_cycle_init(ctl, dv_nrm(sim), st));
-        CU(launch_scale_by_rnorm(sim->w, dv_nrm(sim), V, n, st));
-        for (int j = 0; j < m; ++j) {
+    // One restart cycle: m Arnoldi steps (the ones after the cycle's stop return at once), the
+    // correction, the FP64 true residual and its read-back.  Without kernel timing the cycle is
+    // captured once per handle and form as a CUDA graph and replayed.
+    auto enqueue_cycle = [&]() -> cudaError_t {
+        cudaError_t e = launch_gmres_cycle_init(ctl, dv_nrm(sim), st);
+        if (e == cudaSuccess) e = launch_scale_by_rnorm(sim->w, dv_nrm(sim), V, n, st);
+        for (int j = 0; j < m && e == cudaSuccess; ++j) {
             const T* Vj = V + (size_t)j * n;
             {
                 TimedGroup tg(sim, HDGDG_KT_SPMV, j);
-                CU(launch_spmv_pre(sim->g, St, sim->Scol, Vj, w, st, done));
+                e = launch_spmv_pre(sim->g, St, sim->Scol, Vj, w, st, done);
             }
-            {
-                TimedGroup tg(sim, HDGDG_KT_ORTHO, j);
-                CU(launch_multidot(V, n, j + 1, w, n, sim->red, dv_h1(sim), st, done));
-                CU(launch_cgs2_tail(V, n, j + 1, dv_h1(sim), w, n, sim->red, dv_h2(sim), dv_nrm(sim) + 2,
-                                    dv_nrm(sim) + 1, V + (size_t)(j + 1) * n, st, done));
-                CU(launch_gmres_arnoldi(ctl, j, m, dv_h1(sim), dv_h2(sim), dv_nrm(sim) + 1, st));
-            }
+            TimedGroup tg(sim, HDGDG_KT_ORTHO, j);
+            if (e == cudaSuccess) e = launch_multidot(V, n, j + 1, w, n, sim->red, dv_h1(sim), st, done);
+            if (e == cudaSuccess)
+                e = launch_cgs2_tail(V, n, j + 1, dv_h1(sim), w, n, sim->red, dv_h2(sim), dv_nrm(sim) + 2,
+                                     dv_nrm(sim) + 1, V + (size_t)(j + 1) * n, st, done);
+            if (e == cudaSuccess) e = launch_gmres_arnoldi(ctl, j, m, dv_h1(sim), dv_h2(sim), dv_nrm(sim) + 1, st);
         }
-        CU(launch_gmres_update(V, n, ctl, sim->xt, n, st));
-        // true residual r = g - S~ x~ in FP64
-        CU(launch_spmv_pre(sim->g, sim->Stil, sim->Scol, sim->xt, sim->w, st));
+        if (e == cudaSuccess) e = launch_gmres_update(V, n, ctl, sim->xt, n, st);
+        if (e == cudaSuccess) e = launch_spmv_pre(sim->g, sim->Stil, sim->Scol, sim->xt, sim->w, st);
         CombineTerms t{};
         t.n = 1;
         t.X[0] = sim->w;
         t.c[0] = -1.0;
-        CU(launch_combine(n, g, t, sim->w, nullptr, st));
-        CU(launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st));
-        CU(cudaMemcpyAsync(sim->hbuf, dv_nrm(sim), sizeof(double), cudaMemcpyDeviceToHost, st));
-        CU(cudaMemcpyAsync(sim->hbuf + 1, &ctl->done, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (e == cudaSuccess) e = launch_combine(n, g, t, sim->w, nullptr, st);
+        if (e == cudaSuccess) e = launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sim->hbuf, dv_nrm(sim), sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sim->hbuf + 1, &ctl->done, 5 * sizeof(int), cudaMemcpyDeviceToHost, st);
+        return e;
+    };
+    CycleGraph& cg = sim->cycle_graph[kMixed ? 1 : 0];
+    while (true) {
+        if (sim->timing) {
+            CU(enqueue_cycle());
+        } else {
+            if (cg.exec && cg.g != g) {
+                cudaGraphExecDestroy(cg.exec);
+                cg.exec = nullptr;
+            }
+            if (!cg.exec) {
+                const long long l0 = launches_total();
+                CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                const cudaError_t e = enqueue_cycle();
+                cudaGraph_t graph = nullptr;
+                const cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+                if (e != cudaSuccess || e2 != cudaSuccess)
+                    return fail(sim, HDGDG_ECUDA, "capturing the GMRES cycle failed: %s",
+                                cudaGetErrorString(e != cudaSuccess ? e : e2));
+                const cudaError_t e3 = cudaGraphInstantiate(&cg.exec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (e3 != cudaSuccess) return fail(sim, HDGDG_ECUDA, "GMRES cycle graph: %s", cudaGetErrorString(e3));
+                cg.g = g;
+                cg.launches = launches_total() - l0;
+                count_launches((int)-cg.launches);   // counted again at every replay below
+            }
+            CU(cudaGraphLaunch(cg.exec, st));
+            count_launches((int)cg.launches);
+        }
         CU(cudaStreamSynchronize(st));
         int cf[5];   // done, jend, total, maxit, status
         std::memcpy(cf, sim->hbuf + 1, sizeof(cf));
@@ -703,6 +743,8 @@ void hdgdg_destroy(hdgdg_sim* sim) {
     if (sim->stream) cudaStreamSynchronize(sim->stream);
     flush_timers(sim);
     for (cudaEvent_t e : sim->ev_pool) cudaEventDestroy(e);
+    for (auto& cg : sim->cycle_graph)
+        if (cg.exec) cudaGraphExecDestroy(cg.exec);
     for (void* p : sim->allocs) cudaFree(p);
     if (sim->hbuf) cudaFreeHost(sim->hbuf);
     if (sim->own_stream && sim->stream) cudaStreamDestroy(sim->stream);

@@ -32,6 +32,7 @@ class Request:
     seed: int
     arrival: float                      # seconds after the loop starts
     precision: str = "mixed"
+    bottom_amp: float = 0.1
     result: tuple = None
     admitted: float = None
     finished: float = None
@@ -54,11 +55,26 @@ def poisson_requests(n, rate_per_s, seed=5000, n_range=(32, 256), degrees=(2, 3,
     return out
 
 
+def ensemble_requests(n=256, seed=4000, sides=(16, 32, 64, 128), degrees=(2, 3, 4), steps=100,
+                      precision="mixed"):
+    """The batched-ensemble workload: n instances, all submitted at once, mesh side uniform in
+    sides, k uniform in degrees, each with its own seeded bump and bottom amplitude U[0, 0.1]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [Request(i, int(rng.choice(sides)), int(rng.choice(degrees)), steps, seed + 1 + i, 0.0,
+                    precision, float(rng.uniform(0.0, 0.1))) for i in range(n)]
+
+
 def initial_state(req):
-    """The request's seeded state: the bump recipe of the large workload (one bump per request
-    domain scale, smooth velocity), on the library's own nodes."""
+    """The request's seeded state: one seeded Gaussian bump over a sinusoidal bottom of the
+    request's amplitude, smooth streamfunction velocity, on the library's own nodes."""
     x, y = hd.node_coords(req.N, req.k)
     h, hu, hv, b = W.large_state(x, y, seed=req.seed, n_bumps=1, umax=0.05)
+    if req.bottom_amp != 0.1:                  # rescale the bottom, keep the bump and the velocity
+        bump = h - (W.H0 - b)
+        u, v = hu / h, hv / h
+        b = b * (req.bottom_amp / 0.1)
+        h = W.H0 - b + bump
+        hu, hv = h * u, h * v
     dt = W.advective_dt(x, h, hu, hv, req.N)
     return h, hu, hv, b, dt
 

@@ -108,3 +108,27 @@ def test_perturbation_in_the_box_is_symmetric():
     gx = g[:, :, ::-1, :, ::-1]
     scale = np.abs(g[0]).max()
     assert np.abs(g[0] - gx[0]).max() <= 1e-10 * scale
+
+
+@pytest.mark.parametrize("k", [6, 8])
+def test_high_degree_walls_match_oracle(k):
+    """k = 6 and 8 (the local inverses built in a global workspace): DG residual, one implicit
+    stage and two whole steps against the oracle on a 3 x 3 walled box."""
+    m, (h, hu, hv, b), q, phiB = _walled(3, k, kind="perturbation", x0=-1.0, length=2.0, H_inf=1.0,
+                                         sigma=0.4)
+    dt = 0.01
+    st = imex.Stepper(m, phiB, dt, solver="dense")
+    R1 = q + 0.001 * rng.standard_normal(q.shape)
+    Qo, _ = st.cond.solve(R1)
+    qo = st.run(q, 2)
+    ref_nl = _flat(swe.minv(m, swe.NL(m, R1, phiB)))
+    with _sim(m, b, dt) as s:
+        nl = s.eval_nl(_flat(R1))
+        Q, _, _ = s.stage_solve(_flat(R1))
+        s.set_state(h, hu, hv)
+        s.step(2)
+        qa, _ = swe.to_state(*s.get_state(), b, W.G, W.H0)
+    assert np.abs(nl - ref_nl).max() <= 1e-11 * np.abs(ref_nl).max()
+    for c in range(3):
+        assert imex.rel_l2(m, Q[c].reshape(m.x.shape), Qo[c]) <= 1e-10
+        assert imex.rel_l2(m, qa[c], qo[c]) <= 1e-10
