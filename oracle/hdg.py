@@ -49,10 +49,12 @@ def unreduced_matrix(mesh, phiB, tau_e, dta):
     return K, nv, nt
 
 
-def solve_unreduced(mesh, phiB, tau_e, dta, R1):
-    """Direct dense solve of the coupled (Q, Qhat) system; returns (Q [3,e,j,i], Qhat [edge,c,b])."""
+def solve_unreduced(mesh, phiB, tau_e, dta, R1, R2=None):
+    """Direct dense solve of the coupled (Q, Qhat) system; returns (Q [3,e,j,i], Qhat [edge,c,b]).
+    R2 [edge, c, b] is the right side of the trace rows (0 except prescribed boundary values)."""
     K, nv, nt = unreduced_matrix(mesh, phiB, tau_e, dta)
-    sol = np.linalg.solve(K, np.concatenate([R1.ravel(), np.zeros(nt)]))
+    r2 = np.zeros(nt) if R2 is None else R2.ravel()
+    sol = np.linalg.solve(K, np.concatenate([R1.ravel(), r2]))
     return sol[:nv].reshape(R1.shape), sol[nv:].reshape(mesh.n_edges, 3, mesh.P)
 
 
@@ -156,11 +158,12 @@ class Condensed:
         inv = np.linalg.inv(diag)
         return sp.block_diag([sp.coo_matrix(b) for b in inv], format="csr")
 
-    def rhs(self, R1):
-        """-C A^{-1} R1 assembled on the skeleton (R2 = 0)."""
+    def rhs(self, R1, R2=None):
+        """R2 - C A^{-1} R1 assembled on the skeleton (R2 = 0 except prescribed boundary values)."""
         R1e = _elem_major(R1)
         loc = -np.einsum('etv,ev->et', self.C, np.einsum('evw,ew->ev', self.Ainv, R1e))
-        return np.bincount(self.gi.ravel(), weights=loc.ravel(), minlength=self.n)
+        g = np.bincount(self.gi.ravel(), weights=loc.ravel(), minlength=self.n)
+        return g if R2 is None else g + R2.ravel()
 
     def solve_trace(self, g):
         if self.solver == "dense":
@@ -185,8 +188,8 @@ class Condensed:
         Qe = np.einsum('evw,ew->ev', self.Ainv, R1e - np.einsum('evt,et->ev', self.B, lam_loc))
         return _field_major(Qe, R1.shape[2:])
 
-    def solve(self, R1):
-        g = self.rhs(R1)
+    def solve(self, R1, R2=None):
+        g = self.rhs(R1, R2)
         lam = self.solve_trace(g)
         Q = self.recover(R1, lam)
         return Q, lam.reshape(self.mesh.n_edges, 3, self.mesh.P)

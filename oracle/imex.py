@@ -51,8 +51,12 @@ class Stepper:
     (the linear-wave tests).
     """
 
-    def __init__(self, mesh, phiB, dt, scheme="ars2", solver="lu", linear_only=False, rtol=1e-14):
+    def __init__(self, mesh, phiB, dt, scheme="ars2", solver="lu", linear_only=False, rtol=1e-14,
+                 bc=None):
+        """bc(t) -> prescribed boundary states [3, e, 4, P] at time t (Dirichlet meshes only)."""
         self.mesh, self.phiB, self.dt = mesh, phiB, dt
+        self.bc = bc
+        self.t = 0.0
         self.A, self.At, self.b, self.bt = SCHEMES[scheme]()
         self.s = len(self.b)
         self.tau_e = mesh.face_tau_hat(phiB)
@@ -74,21 +78,30 @@ class Stepper:
     def lin(self, Q, lam_g):
         return swe.L(self.mesh, Q, self.mesh.element_traces(lam_g), self.phiB, self.tau_e)
 
-    def stage_solve(self, R1):
+    def stage_solve(self, R1, R2=None):
         if self.cond is None:
-            return solve_unreduced(self.mesh, self.phiB, self.tau_e, self.dt * self.a_ii, R1)
-        return self.cond.solve(R1)
+            return solve_unreduced(self.mesh, self.phiB, self.tau_e, self.dt * self.a_ii, R1, R2)
+        return self.cond.solve(R1, R2)
+
+    def _boundary_at(self, t):
+        """Set the prescribed boundary states for stage time t; returns the trace rows' R2."""
+        if self.bc is None:
+            return None
+        self.mesh.bc_q = self.bc(t)
+        return swe.dirichlet_R2(self.mesh, self.mesh.bc_q)
 
     def step(self, q):
-        """One step q^n -> q^{n+1} of Algorithm 1."""
+        """One step q^n -> q^{n+1} of Algorithm 1 (stage i at time t + c_i dt, c = A 1)."""
         m, dt = self.mesh, self.dt
+        c = self.A.sum(axis=1)
         NLs, Ls, Qs, R1s, lams = [None] * self.s, [None] * self.s, [None] * self.s, [None] * self.s, [None] * self.s
         for i in range(self.s):
+            R2 = self._boundary_at(self.t + c[i] * dt)
             if self.At[i, i] == 0.0:
                 Q = q
                 # L(Q^(i)) is needed only if some later coefficient multiplies it.
                 if np.any(self.At[i + 1:, i] != 0.0) or self.bt[i] != 0.0:
-                    lam = swe.trace_from_conservation(m, Q, self.phiB, self.tau_e)
+                    lam = swe.trace_from_conservation(m, Q, self.phiB, self.tau_e, R2)
                     Ls[i] = self.lin(Q, lam)
                     lams[i] = lam
             else:
@@ -99,7 +112,7 @@ class Stepper:
                     if self.At[i, j] != 0.0:
                         acc = acc + self.At[i, j] * Ls[j]
                 R1 = q + dt * swe.minv(m, acc)
-                Q, lam = self.stage_solve(R1)
+                Q, lam = self.stage_solve(R1, R2)
                 Ls[i] = self.lin(Q, lam)
                 R1s[i], lams[i] = R1, lam
             Qs[i] = Q
@@ -111,6 +124,7 @@ class Stepper:
             if self.bt[i] != 0.0:
                 acc = acc + self.bt[i] * Ls[i]
         self.last = {"Q": Qs, "R1": R1s, "L": Ls, "NL": NLs, "lam": lams}
+        self.t += dt
         return q + dt * swe.minv(m, acc)
 
     def run(self, q, n_steps):
@@ -125,21 +139,26 @@ class ExplicitRK:
     two-stage method, 'rk3' the three-stage method of Shu and Osher -- the RK2 DG / RK3 DG the
     paper compares IMEX HDG-DG against (Sec. 7.1, 7.2)."""
 
-    def __init__(self, mesh, phiB, dt, scheme="rk2"):
+    def __init__(self, mesh, phiB, dt, scheme="rk2", bc=None):
         self.mesh, self.phiB, self.dt, self.scheme = mesh, phiB, dt, scheme
+        self.bc = bc
+        self.t = 0.0
 
-    def rhs(self, q):
+    def rhs(self, q, t):
+        if self.bc is not None:
+            self.mesh.bc_q = self.bc(t)
         return swe.minv(self.mesh, swe.DG_full(self.mesh, q, self.phiB))
 
     def step(self, q):
-        dt = self.dt
+        dt, t = self.dt, self.t
+        self.t += dt
         if self.scheme == "rk2":
-            q1 = q + dt * self.rhs(q)
-            return 0.5 * q + 0.5 * (q1 + dt * self.rhs(q1))
+            q1 = q + dt * self.rhs(q, t)
+            return 0.5 * q + 0.5 * (q1 + dt * self.rhs(q1, t + dt))
         if self.scheme == "rk3":
-            q1 = q + dt * self.rhs(q)
-            q2 = 0.75 * q + 0.25 * (q1 + dt * self.rhs(q1))
-            return q / 3.0 + 2.0 / 3.0 * (q2 + dt * self.rhs(q2))
+            q1 = q + dt * self.rhs(q, t)
+            q2 = 0.75 * q + 0.25 * (q1 + dt * self.rhs(q1, t + dt))
+            return q / 3.0 + 2.0 / 3.0 * (q2 + dt * self.rhs(q2, t + 0.5 * dt))
         raise ValueError(self.scheme)
 
     def run(self, q, n_steps):

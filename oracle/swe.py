@@ -41,14 +41,18 @@ class Mesh:
     element r and edge N^2 + r its top face.  boundary='wall': reflecting walls on the four
     sides (Sec. 4.3, eq. reflection); x-edges are numbered ey*(N+1) + ix (ix = 0..N) and
     y-edges N(N+1) + iy*N + ex (iy = 0..N); a face on the wall has no neighbour (-1) and sees
-    the mirror state of its own element instead.
+    the mirror state of its own element instead.  boundary='dirichlet': the same numbering,
+    and a boundary face sees a prescribed state (``bc_q``, set by the caller for the current
+    time) while its trace equals that state (the exact-solution boundary conditions of the
+    paper's moving-vortex test, Sec. 7.1).
     """
 
     def __init__(self, N, k, boundary="periodic", x0=0.0, length=1.0):
         if boundary == "periodic" and N < 2:
             raise ValueError("periodic mesh needs N >= 2")
-        if boundary not in ("periodic", "wall"):
+        if boundary not in ("periodic", "wall", "dirichlet"):
             raise ValueError(boundary)
+        self.bc_q = None
         self.N, self.k, self.P = N, k, k + 1
         self.boundary = boundary
         self.n_el = N * N
@@ -117,8 +121,10 @@ class Mesh:
 
     def neighbour_state(self, q, f):
         """State q = (phi_eta, U, V) across face f; on a wall the mirror state of eq. reflection:
-        phi^+ = phi^-, U^+ = U^- - 2 (U^- . n) n."""
+        phi^+ = phi^-, U^+ = U^- - 2 (U^- . n) n; on a Dirichlet boundary the prescribed state."""
         qp = np.stack([self.neighbour_face_values(q[c], f) for c in range(3)])
+        if self.boundary == "dirichlet":
+            return np.where(self.wall(f)[None, :, None], self.bc_q[:, :, f, :], qp)
         return np.where(self.wall(f)[None, :, None], reflect(self.face_values(q, f), FACE_NORMALS[f]), qp)
 
     # -- trace vectors ---------------------------------------------------------------
@@ -306,6 +312,11 @@ def flux_contributions(mesh, Q, lam_e, phiB, tau_e):
         n = FACE_NORMALS[f]
         qf, bf = mesh.face_values(Q, f), mesh.face_values(phiB, f)
         fn = hdg_normal_flux(qf, lam_e[:, :, f, :], bf, tau_e[:, f, :], n)
+        if mesh.boundary == "dirichlet":
+            # a Dirichlet trace row is qhat = q_bc: its left side is qhat (q_bc goes to R2)
+            out[:, :, f, :] = np.where(mesh.wall(f)[None, :, None], lam_e[:, :, f, :],
+                                       mesh.face_jac * mesh.w * fn)
+            continue
         # on a wall the mirror element (eq. reflection) contributes its share with normal -n
         ghost = hdg_normal_flux(reflect(qf, n), lam_e[:, :, f, :], bf, tau_e[:, f, :], -n)
         fn = fn + np.where(mesh.wall(f)[None, :, None], ghost, 0.0)
@@ -323,17 +334,24 @@ def minv(mesh, r):
     return r / mesh.mass[None, None, :, :]
 
 
-def trace_from_conservation(mesh, Q, phiB, tau_e):
-    """The trace that makes Flx(Q, qhat) = 0 for a given volume state Q.
+def trace_from_conservation(mesh, Q, phiB, tau_e, R2=None):
+    """The trace that makes Flx(Q, qhat) = R2 (0 by default) for a given volume state Q.
 
     With collocated face quadrature the conservation rows are node-local and diagonal in
-    qhat, so qhat = -Flx(Q, 0) / Flx(0, 1) node by node.  Used where Algorithm 1 asks for
-    L(Q^(i)) with no trace (an explicit first stage).
+    qhat, so qhat = (R2 - Flx(Q, 0)) / Flx(0, 1) node by node.  Used where Algorithm 1 asks
+    for L(Q^(i)) with no trace (an explicit first stage).
     """
     z = np.zeros((mesh.n_edges, 3, mesh.P))
     num = Flx(mesh, Q, z, phiB, tau_e)
     den = Flx(mesh, np.zeros_like(Q), np.ones_like(z), phiB, tau_e)
-    return -num / den
+    return ((0.0 if R2 is None else R2) - num) / den
+
+
+def dirichlet_R2(mesh, bc_face):
+    """Right side of the trace rows for prescribed boundary states bc_face [3, e, f, b]: the
+    boundary value on Dirichlet edges, 0 on every conservation row; global [edge, c, b]."""
+    val = np.where(np.stack([mesh.wall(f) for f in range(4)], axis=1)[None, :, :, None], bc_face, 0.0)
+    return mesh.assemble_edges(val)
 
 
 # -- boundary conversions ------------------------------------------------------------------

@@ -129,6 +129,24 @@ def perturbation_state(x, y, H_inf=100.0, sigma=0.1):
     return h, np.zeros_like(x), np.zeros_like(x), b
 
 
+VORTEX = {"H_inf": 1.0, "u_inf": 1.0, "v_inf": 0.0, "beta": 5.0, "g": 2.0, "xc": 0.0, "yc": 0.0}
+
+
+def vortex_state(x, y, t, H_inf=1.0, u_inf=1.0, v_inf=0.0, beta=5.0, g=2.0, xc=0.0, yc=0.0):
+    """The moving vortex of the paper's Sec. 7.1 (eq. tc_vortex_ic) at time t, as (h, hu, hv, b)
+    with a flat bottom b = 0 and H0 = H_inf.  The depth is H_inf - beta^2/(16 pi^2 g)
+    e^{-2(r^2-1)}, which is the cyclostrophic balance of the printed swirl and equals the printed
+    beta^2/(32 pi^2) at the paper's g = 2."""
+    xt = x - xc - u_inf * t
+    yt = y - yc - v_inf * t
+    r2 = xt * xt + yt * yt
+    e = np.exp(-(r2 - 1.0))
+    H = H_inf - beta * beta / (16.0 * math.pi ** 2 * g) * e * e
+    u = u_inf - beta / (2.0 * math.pi) * e * yt
+    v = v_inf + beta / (2.0 * math.pi) * e * xt
+    return H, H * u, H * v, np.zeros_like(x)
+
+
 def advective_dt(x, h, hu, hv, n_side, cfl=0.5, g=G, H0_=H0):
     """Explicit-part time step dt = cfl * h_e / ((2k+1) * lambda_NL) for states [n_el, (k+1)^2].
 
