@@ -74,20 +74,27 @@ typedef struct {
     double dt;           /* time step (> 0) */
     int precision;       /* HDGDG_FP64 or HDGDG_MIXED */
     double krylov_rtol;  /* GMRES stop: ||g - S qhat|| <= rtol ||g||; <= 0 selects 1e-15
-                            (FP64) or 1e-10 (MIXED, FP64 residual of the refinement loop).
+                            (FP64) or 1e-9 (MIXED, FP64 residual of the refinement loop).
                             A restart cycle that fails to halve a true residual already below
                             1e-12 ||g|| ends the solve as converged (FP64 rounding floor). */
     int krylov_restart;  /* GMRES(m) restart length m <= 31; <= 0 selects 8 */
     int krylov_maxit;    /* cap on GMRES iterations per stage solve; <= 0 selects 2000 */
     int linear_only;     /* 1: drop NL (linear gravity-wave runs); 0: full method */
-    int boundary;        /* HDGDG_PERIODIC (0) or HDGDG_WALLS (1): reflecting walls on the four
+    int boundary;        /* HDGDG_PERIODIC (0), HDGDG_WALLS (1): reflecting walls on the four
                             sides (Sec. 4.3, eq. reflection; the trace condition becomes eq.
-                            reflectionBC) */
+                            reflectionBC), or HDGDG_VORTEX (2): prescribed exact-solution
+                            traces (below) */
     double x0;           /* domain [x0, x0 + length]^2 (node coordinates follow) */
     double length;       /* side of the square domain; <= 0 selects 1 */
+    double bc_params[5]; /* HDGDG_VORTEX: beta, u_inf, v_inf, x_c, y_c of eq. tc_vortex_ic */
 } hdgdg_config;
 
-enum { HDGDG_PERIODIC = 0, HDGDG_WALLS = 1 };
+/* HDGDG_VORTEX: the exact-solution boundary conditions of the paper's moving-vortex test
+ * (Sec. 7.1): every boundary trace is prescribed, qhat = q_exact(t) at the stage time, and the
+ * DG flux sees q_exact(t) across the boundary; q_exact is eq. tc_vortex_ic with H_inf = H0 over
+ * a flat bottom (b = 0), depth H_inf - beta^2/(16 pi^2 g) e^{-2(r^2-1)} (the printed
+ * beta^2/(32 pi^2) at the paper's g = 2). */
+enum { HDGDG_PERIODIC = 0, HDGDG_WALLS = 1, HDGDG_VORTEX = 2 };
 
 typedef struct {
     long long steps;              /* time steps completed since set_state */
@@ -96,6 +103,7 @@ typedef struct {
     double last_rel_residual;     /* ||g - S qhat|| / ||g|| of the most recent stage solve */
     double mass;                  /* sum_e J sum_ij w_i w_j phi_eta of the current state */
     long long kernel_launches;    /* CUDA kernels this handle launched in hdgdg_step since set_state */
+    double time;                  /* simulated time since set_state (steps x dt) */
 } hdgdg_stats;
 
 /* Kernel classes of the per-kernel timers (hdgdg_kernel_time). */
@@ -118,6 +126,10 @@ size_t hdgdg_bytes_required(const hdgdg_config* cfg);
 /* GLL node coordinates x, y (host, [n_el][(k+1)^2] each) of the mesh of cfg, in the
  * node order above.  No GPU call is made.  EINVAL on a bad configuration or NULL. */
 hdgdg_status hdgdg_node_coords(const hdgdg_config* cfg, double* x, double* y);
+
+/* The library's degree-k Gauss-Lobatto-Legendre nodes and weights on [-1, 1] (host arrays of
+ * k+1 doubles each), the collocation points of every element.  EINVAL if k is out of range. */
+hdgdg_status hdgdg_gll(int degree_k, double* nodes, double* weights);
 
 /* Build a simulation: mesh, GLL tables, the bottom phi_B = g (H0 - b), and the
  * time-invariant implicit-stage operators of Sec. 6 -- per-element A^{-1} and the
@@ -154,7 +166,9 @@ const char* hdgdg_last_error(const hdgdg_sim* sim);
 /* Release every device and host resource of the handle (NULL is a no-op). */
 void hdgdg_destroy(hdgdg_sim* sim);
 
-/* ---- row-level entry points (one step of the hot path each; host buffers) ---------- */
+/* ---- row-level entry points (one step of the hot path each; host buffers) ----------
+ * Prescribed boundary data (HDGDG_VORTEX) are taken at the handle's current time (0 after
+ * create or set_state, then steps x dt). */
 
 /* M^{-1} NL(q) of Sec. 4.3 (DG volume term plus Rusanov face terms of the nonlinear
  * flux F_NL = F - F_L) for the internal state q [3][n_el][(k+1)^2]; out has the same

@@ -39,12 +39,12 @@ struct Plan {
 constexpr int kMaxRestart = 31;   // the fused Gram-Schmidt kernels keep up to 32 basis vectors in registers
 
 bool valid(const hdgdg_config* c) {
-    return c && c->n_side >= (c->boundary == HDGDG_WALLS ? 1 : 2) && c->n_side <= 32768 && c->degree_k >= 1 && c->degree_k <= kMaxP - 1 &&
+    return c && c->n_side >= (c->boundary != HDGDG_PERIODIC ? 1 : 2) && c->n_side <= 32768 && c->degree_k >= 1 && c->degree_k <= kMaxP - 1 &&
            std::isfinite(c->g) && c->g > 0.0 && std::isfinite(c->H0) && std::isfinite(c->dt) &&
            c->dt > 0.0 && c->scheme >= HDGDG_ARS2 && c->scheme <= HDGDG_RK3 &&
            (c->precision == HDGDG_FP64 || c->precision == HDGDG_MIXED) &&
            (c->linear_only == 0 || c->linear_only == 1) &&
-           (c->boundary == HDGDG_PERIODIC || c->boundary == HDGDG_WALLS) && std::isfinite(c->x0) &&
+           c->boundary >= HDGDG_PERIODIC && c->boundary <= HDGDG_VORTEX && std::isfinite(c->x0) &&
            std::isfinite(c->length) &&
            c->krylov_restart <= kMaxRestart;
 }
@@ -57,7 +57,7 @@ Plan make_plan(const hdgdg_config* c) {
     Plan p;
     const size_t N = (size_t)c->n_side, P = (size_t)c->degree_k + 1;
     const size_t n_el = N * N, Np = P * P;
-    const size_t n_edges = c->boundary == HDGDG_WALLS ? 2 * N * (N + 1) : 2 * N * N;
+    const size_t n_edges = c->boundary != HDGDG_PERIODIC ? 2 * N * (N + 1) : 2 * N * N;
     p.n = n_el * Np;
     p.NV = (int)(3 * Np);
     p.NF = (int)(3 * P);
@@ -153,7 +153,11 @@ Geom make_geom(const hdgdg_config* c, double* xi_out) {
     g.P = c->degree_k + 1;
     g.Np = g.P * g.P;
     g.n_el = g.N * g.N;
-    g.walls = c->boundary == HDGDG_WALLS ? 1 : 0;
+    g.walls = c->boundary != HDGDG_PERIODIC ? 1 : 0;
+    g.dirichlet = c->boundary == HDGDG_VORTEX ? 1 : 0;
+    g.gacc = c->g;
+    g.H0 = c->H0;
+    for (int i = 0; i < 5; ++i) g.vortex[i] = c->bc_params[i];
     g.n_edges = g.walls ? 2 * g.N * (g.N + 1) : 2 * g.n_el;
     const double L = c->length > 0.0 ? c->length : 1.0;
     g.x0 = c->x0;
@@ -162,6 +166,7 @@ Geom make_geom(const hdgdg_config* c, double* xi_out) {
     g.J = 0.25 * g.h * g.h;
     double xi[kMaxP];
     gll_tables(c->degree_k, xi, g.w, g.D);
+    for (int i = 0; i < g.P; ++i) g.xi[i] = xi[i];
     g.inv_w0 = 1.0 / g.w[0];
     for (int i = 0; i < g.P; ++i)
         for (int a = 0; a < g.P; ++a) g.Dhat[i * g.P + a] = (g.w[a] / g.w[i]) * g.D[a * g.P + i];
@@ -247,6 +252,7 @@ struct hdgdg_sim {
     double* hbuf = nullptr;   // pinned host scratch
     // run state
     bool have_state = false;
+    double t = 0.0;
     hdgdg_stats stats{};
     // per-kernel-class timers
     bool timing = false;
@@ -373,7 +379,7 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
     constexpr bool kMixed = sizeof(T) == sizeof(float);
     const size_t n = sim->plan.nt;
     const int m = sim->plan.m;
-    const double rtol = sim->cfg.krylov_rtol > 0.0 ? sim->cfg.krylov_rtol : (kMixed ? 1e-10 : 1e-15);
+    const double rtol = sim->cfg.krylov_rtol > 0.0 ? sim->cfg.krylov_rtol : (kMixed ? 1e-9 : 1e-15);
     const int maxit = sim->cfg.krylov_maxit > 0 ? sim->cfg.krylov_maxit : 2000;
     // Mixed form: an FP32 cycle stops once it has reduced its starting residual 1e6 times.
     const double inner_rel = kMixed ? 1e-6 : 0.0;
@@ -499,11 +505,12 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
 double beta_of(const hdgdg_sim* sim) { return sim->cfg.dt * sim->a_ii * sim->g.two_over_h * sim->g.inv_w0; }
 
 // One implicit stage: R1 (device) -> Q, Lst = dt M^{-1} L (device); qhat left in sim->lam.
-hdgdg_status stage_solve_dev(hdgdg_sim* sim, const double* R1, double* Q, double* Lst, int* its) {
+hdgdg_status stage_solve_dev(hdgdg_sim* sim, const double* R1, double* Q, double* Lst, int* its,
+                             double t_stage = 0.0) {
     double rr;
     {
         TimedGroup tg(sim, HDGDG_KT_CONDENSE);
-        CU(launch_condense(sim->g, sim->Ainv, R1, sim->phiB, sim->tau, sim->Z, sim->gvec, sim->stream));
+        CU(launch_condense(sim->g, sim->Ainv, R1, sim->phiB, sim->tau, sim->Z, sim->gvec, sim->stream, t_stage));
     }
     if (sim->cfg.precision == HDGDG_MIXED) TRY(gmres_solve<float>(sim, sim->gvec, sim->lam, its, &rr));
     else TRY(gmres_solve<double>(sim, sim->gvec, sim->lam, its, &rr));
@@ -523,11 +530,12 @@ hdgdg_status explicit_step(hdgdg_sim* sim) {
     const size_t n3 = 3 * sim->plan.n;
     cudaStream_t st = sim->stream;
     const double dt = sim->cfg.dt;
-    auto rhs = [&](const double* qi, double* K) -> hdgdg_status {
+    auto rhs = [&](const double* qi, double* K, double ti) -> hdgdg_status {
         TimedGroup tg(sim, HDGDG_KT_DG);
-        CU(launch_dg_full(sim->g, qi, sim->phiB, dt, sim->fface, K, st));
+        CU(launch_dg_full(sim->g, qi, sim->phiB, dt, sim->fface, K, st, ti));
         return HDGDG_OK;
     };
+    const double t0 = sim->t;
     auto comb = [&](double* out, std::initializer_list<std::pair<double*, double>> terms, unsigned* flag) -> hdgdg_status {
         CombineTerms t{};
         for (auto& pr : terms) { t.X[t.n] = pr.first; t.c[t.n++] = pr.second; }
@@ -536,15 +544,15 @@ hdgdg_status explicit_step(hdgdg_sim* sim) {
         return HDGDG_OK;
     };
     double *K1 = sim->NLs[0], *K2 = sim->NLs[1], *K3 = sim->NLs[2];
-    TRY(rhs(sim->q, K1));
+    TRY(rhs(sim->q, K1, t0));
     TRY(comb(sim->Qs, {{K1, 1.0}}, nullptr));
-    TRY(rhs(sim->Qs, K2));
+    TRY(rhs(sim->Qs, K2, t0 + dt));
     CU(cudaMemsetAsync(sim->flags, 0, sizeof(unsigned), st));
     if (sim->cfg.scheme == HDGDG_RK2) {
         TRY(comb(sim->q_new, {{K1, 0.5}, {K2, 0.5}}, sim->flags));
     } else {
         TRY(comb(sim->R1, {{K1, 0.25}, {K2, 0.25}}, nullptr));
-        TRY(rhs(sim->R1, K3));
+        TRY(rhs(sim->R1, K3, t0 + 0.5 * dt));
         TRY(comb(sim->q_new, {{K1, 1.0 / 6.0}, {K2, 1.0 / 6.0}, {K3, 2.0 / 3.0}}, sim->flags));
     }
     unsigned flag = 0;
@@ -554,6 +562,7 @@ hdgdg_status explicit_step(hdgdg_sim* sim) {
     if (flag) return fail(sim, HDGDG_ENONFINITE, "step %lld produced a non-finite state", sim->stats.steps + 1);
     std::swap(sim->q, sim->q_new);
     sim->stats.steps += 1;
+    sim->t += dt;
     return HDGDG_OK;
 }
 
@@ -563,6 +572,9 @@ hdgdg_status one_step(hdgdg_sim* sim) {
     cudaStream_t st = sim->stream;
     for (int i = 0; i < sim->s; ++i) {
         const double* Qi = sim->q;
+        double ci = 0.0;   // stage abscissa c_i = sum_j a_ij (equal for both tableaux of ARS)
+        for (int j = 0; j < i; ++j) ci += sim->A[i][j];
+        const double ti = sim->t + ci * sim->cfg.dt;
         if (sim->At[i][i] != 0.0) {
             CombineTerms t{};
             for (int j = 0; j < i; ++j) {
@@ -574,12 +586,12 @@ hdgdg_status one_step(hdgdg_sim* sim) {
                 CU(launch_combine(n3, sim->q, t, sim->R1, nullptr, st));
             }
             int its = 0;
-            TRY(stage_solve_dev(sim, sim->R1, sim->Qs, sim->Ls[i], &its));
+            TRY(stage_solve_dev(sim, sim->R1, sim->Qs, sim->Ls[i], &its, ti));
             Qi = sim->Qs;
         }
         if (!sim->cfg.linear_only) {
             TimedGroup tg(sim, HDGDG_KT_DG);
-            CU(launch_dg_nl(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st));
+            CU(launch_dg_nl(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st, ti));
         }
     }
     CombineTerms t{};
@@ -599,6 +611,7 @@ hdgdg_status one_step(hdgdg_sim* sim) {
     if (flag) return fail(sim, HDGDG_ENONFINITE, "step %lld produced a non-finite state", sim->stats.steps + 1);
     std::swap(sim->q, sim->q_new);
     sim->stats.steps += 1;
+    sim->t += sim->cfg.dt;
     return HDGDG_OK;
 }
 
@@ -733,6 +746,13 @@ hdgdg_status hdgdg_node_coords(const hdgdg_config* cfg, double* x, double* y) {
     return HDGDG_OK;
 }
 
+hdgdg_status hdgdg_gll(int degree_k, double* nodes, double* weights) {
+    if (degree_k < 1 || degree_k > kMaxP - 1 || !nodes || !weights) return HDGDG_EINVAL;
+    double D[kMaxP * kMaxP];
+    gll_tables(degree_k, nodes, weights, D);
+    return HDGDG_OK;
+}
+
 const char* hdgdg_last_error(const hdgdg_sim* sim) {
     if (!sim) return "no handle";
     return sim->err.c_str();
@@ -815,6 +835,7 @@ hdgdg_status hdgdg_set_state(hdgdg_sim* sim, const double* h, const double* hu, 
     }
     sim->have_state = true;
     sim->stats = hdgdg_stats{};
+    sim->t = 0.0;
     return HDGDG_OK;
 }
 
@@ -852,6 +873,7 @@ hdgdg_status hdgdg_get_stats(hdgdg_sim* sim, hdgdg_stats* out) {
         sim->stats.mass = sim->hbuf[0];
     }
     *out = sim->stats;
+    out->time = sim->t;
     return HDGDG_OK;
 }
 
@@ -859,7 +881,7 @@ hdgdg_status hdgdg_eval_nl(hdgdg_sim* sim, const double* q, double* out) {
     if (!sim || !q || !out) return fail(sim, HDGDG_EINVAL, "NULL argument to eval_nl");
     const size_t n3 = 3 * sim->plan.n;
     TRY(upload3(sim, sim->R1, q, n3));
-    CU(launch_dg_nl(sim->g, sim->R1, sim->phiB, sim->tau, 1.0, sim->fface, sim->Qs, sim->stream));
+    CU(launch_dg_nl(sim->g, sim->R1, sim->phiB, sim->tau, 1.0, sim->fface, sim->Qs, sim->stream, sim->t));
     return download(sim, out, sim->Qs, n3);
 }
 
@@ -867,7 +889,7 @@ hdgdg_status hdgdg_condense_rhs(hdgdg_sim* sim, const double* R1, double* out) {
     if (sim && explicit_scheme(&sim->cfg)) return fail(sim, HDGDG_EINVAL, "explicit scheme: no implicit stage");
     if (!sim || !R1 || !out) return fail(sim, HDGDG_EINVAL, "NULL argument to condense_rhs");
     TRY(upload3(sim, sim->R1, R1, 3 * sim->plan.n));
-    CU(launch_condense(sim->g, sim->Ainv, sim->R1, sim->phiB, sim->tau, sim->Z, sim->gvec, sim->stream));
+    CU(launch_condense(sim->g, sim->Ainv, sim->R1, sim->phiB, sim->tau, sim->Z, sim->gvec, sim->stream, sim->t));
     return download(sim, out, sim->gvec, sim->plan.nt);
 }
 
@@ -886,7 +908,7 @@ hdgdg_status hdgdg_stage_solve(hdgdg_sim* sim, const double* R1, double* Q, doub
     const size_t n3 = 3 * sim->plan.n;
     TRY(upload3(sim, sim->R1, R1, n3));
     int its = 0;
-    TRY(stage_solve_dev(sim, sim->R1, sim->Qs, sim->Ls[0], &its));
+    TRY(stage_solve_dev(sim, sim->R1, sim->Qs, sim->Ls[0], &its, sim->t));
     if (iterations) *iterations = its;
     TRY(download(sim, Q, sim->Qs, n3));
     if (qhat) TRY(download(sim, qhat, sim->lam, sim->plan.nt));

@@ -27,8 +27,12 @@ constexpr int kMaxP = 9;   // degree k <= 8
 // Mesh and GLL tables, passed by value to kernels.
 struct Geom {
     int N, P, Np, n_el, n_edges;
-    int walls;                  // 0: periodic unit square; 1: reflecting walls (eq. reflection)
+    int walls;                  // 0: periodic unit square; 1: a bounded square (walls or Dirichlet)
+    int dirichlet;              // 1: boundary faces take the moving-vortex exact solution (Sec. 7.1)
     double x0;                  // domain [x0, x0 + N h]^2
+    double gacc, H0;            // gravity and reference depth (flat bottom for the vortex)
+    double vortex[5];           // beta, u_inf, v_inf, x_c, y_c of eq. tc_vortex_ic
+    double xi[kMaxP];           // GLL nodes
     double h;                   // element size (domain length / N)
     double two_over_h;          // d(xi)/dx
     double inv_w0;              // 1 / w_0 (= 1 / w_k): face lift of the collocated mass matrix
@@ -107,6 +111,31 @@ __host__ __device__ inline void edge_sides(int r, const Geom& g, int* em, int* f
     else { const int e = r - N * N; *em = e; *fm = 3; *ep = neighbour(e, 3, g); *fp = 2; }
 }
 
+// The moving vortex of Sec. 7.1 (eq. tc_vortex_ic) at (x, y, t) as (phi_eta, U, V) over the
+// flat bottom B = H0: H = H0 - beta^2/(16 pi^2 g) e^{-2(r^2-1)} (the printed beta^2/(32 pi^2) at
+// g = 2), u = u_inf - beta/(2 pi) e^{-(r^2-1)} y_t, v = v_inf + beta/(2 pi) e^{-(r^2-1)} x_t.
+__host__ __device__ inline void vortex_state(const Geom& g, double x, double y, double t, double* ph,
+                                             double* U, double* V) {
+    const double pi = 3.14159265358979323846;
+    const double beta = g.vortex[0];
+    const double xt = x - g.vortex[3] - g.vortex[1] * t;
+    const double yt = y - g.vortex[4] - g.vortex[2] * t;
+    const double e = exp(-(xt * xt + yt * yt - 1.0));
+    const double H = g.H0 - beta * beta / (16.0 * pi * pi * g.gacc) * e * e;
+    const double u = g.vortex[1] - beta / (2.0 * pi) * e * yt;
+    const double v = g.vortex[2] + beta / (2.0 * pi) * e * xt;
+    *ph = g.gacc * (H - g.H0);
+    *U = g.gacc * H * u;
+    *V = g.gacc * H * v;
+}
+
+// Physical coordinates of face node b of face f of element e.
+__host__ __device__ inline void face_node_xy(const Geom& g, int e, int f, int b, double* x, double* y) {
+    const int n = face_node(f, b, g.P), i = n % g.P, j = n / g.P;
+    *x = g.x0 + (e % g.N + 0.5 * (1.0 + g.xi[i])) * g.h;
+    *y = g.x0 + (e / g.N + 0.5 * (1.0 + g.xi[j])) * g.h;
+}
+
 // Host-built periodic unit-square mesh and GLL tables of an N x N, degree-k mesh (no GPU call).
 Geom host_geom(int N, int k);
 
@@ -116,11 +145,12 @@ void count_launches(int n);
 
 // ---- kernel launchers (each returns the launch error) -------------------------------
 // out = scale * M^{-1} NL(q); fface: scratch of n_edges * 3P doubles for the face fluxes
+// t: time of the boundary data (Dirichlet boundaries only)
 cudaError_t launch_dg_nl(const Geom& g, const double* q, const double* phiB, const double* tau_edge,
-                         double scale, double* fface, double* out, cudaStream_t s);
+                         double scale, double* fface, double* out, cudaStream_t s, double t = 0.0);
 // out = scale * M^{-1} (the explicit DG residual of the whole flux with the source term)
 cudaError_t launch_dg_full(const Geom& g, const double* q, const double* phiB, double scale,
-                           double* fface, double* out, cudaStream_t s);
+                           double* fface, double* out, cudaStream_t s, double t = 0.0);
 
 struct CombineTerms {
     const double* X[10];
@@ -140,8 +170,9 @@ cudaError_t launch_assemble_trace(const Geom& g, const double* Se, double* S7, d
                                   cudaStream_t s);
 
 // Condensation: Z = A^{-1} R1 per element, then g = -C Z edge by edge (pointwise rows).
+// t: time of the prescribed boundary traces (Dirichlet boundaries only)
 cudaError_t launch_condense(const Geom& g, const double* Ainv, const double* R1, const double* phiB,
-                            const double* tau_edge, double* Z, double* gvec, cudaStream_t s);
+                            const double* tau_edge, double* Z, double* gvec, cudaStream_t s, double t = 0.0);
 // Recovery: Q = Z + beta A^{-1} (tau qhat) on boundary nodes; Lst = (Q - R1) / a_ii.
 cudaError_t launch_recover(const Geom& g, const double* Ainv, const double* Z, const double* R1,
                            const double* tau_edge, const double* qhat, double beta, double inv_aii,

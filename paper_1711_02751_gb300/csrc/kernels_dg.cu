@@ -42,7 +42,7 @@ __device__ __forceinline__ void nl_flux(double ph, double U, double V, double ph
 template <int P, bool FULL>
 __global__ void __launch_bounds__(256)
 dg_face_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ phiB,
-               const double* __restrict__ tau_edge, double* __restrict__ fface) {
+               const double* __restrict__ tau_edge, double* __restrict__ fface, double t_bc) {
     constexpr int Np = P * P;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.n_edges * P) return;
@@ -60,10 +60,20 @@ dg_face_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ 
         const size_t op = (size_t)ep * Np + face_node(fp, b, P);
         php = q[op]; Up = q[fs + op]; Vp = q[2 * fs + op]; pbp = phiB[op];
     }
-    // a wall edge sees the mirror state of its one element (eq. reflection): same phi and
-    // tangential momentum, opposite normal momentum
-    if (em < 0) { phm = php; pbm = pbp; Um = xedge ? -Up : Up; Vm = xedge ? Vp : -Vp; }
-    if (ep < 0) { php = phm; pbp = pbm; Up = xedge ? -Um : Um; Vp = xedge ? Vm : -Vm; }
+    if (g.dirichlet && (em < 0 || ep < 0)) {
+        // Dirichlet boundary: the other side is the prescribed exact state at the node
+        double x, y;
+        face_node_xy(g, em >= 0 ? em : ep, em >= 0 ? fm : fp, b, &x, &y);
+        double ph, U, V;
+        vortex_state(g, x, y, t_bc, &ph, &U, &V);
+        if (em < 0) { phm = ph; Um = U; Vm = V; pbm = pbp; }
+        else { php = ph; Up = U; Vp = V; pbp = pbm; }
+    } else {
+        // a wall edge sees the mirror state of its one element (eq. reflection): same phi and
+        // tangential momentum, opposite normal momentum
+        if (em < 0) { phm = php; pbm = pbp; Um = xedge ? -Up : Up; Vm = xedge ? Vp : -Vp; }
+        if (ep < 0) { php = phm; pbp = pbm; Up = xedge ? -Um : Um; Vp = xedge ? Vm : -Vm; }
+    }
     const double Phm = phm + pbm, Php = php + pbp;
     const double im = 1.0 / Phm, ip = 1.0 / Php;
     // normal (n) and tangential (t) momentum components along this edge's +axis
@@ -247,10 +257,10 @@ __global__ void mass_final_kernel(const double* partial, int nb, double J, doubl
 
 template <int P, bool FULL>
 cudaError_t dg_launch(const Geom& g, const double* q, const double* phiB, const double* tau_edge,
-                      double scale, double* fface, double* out, cudaStream_t s) {
+                      double scale, double* fface, double* out, cudaStream_t s, double t) {
     constexpr int EPB = DgTile<P>::EPB;
     const int nf = g.n_edges * P;
-    dg_face_kernel<P, FULL><<<(nf + 255) / 256, 256, 0, s>>>(g, q, phiB, tau_edge, fface);
+    dg_face_kernel<P, FULL><<<(nf + 255) / 256, 256, 0, s>>>(g, q, phiB, tau_edge, fface, t);
     count_launches(1);
     dg_volume_kernel<P, FULL><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(g, q, phiB, fface, scale, out);
     count_launches(1);
@@ -273,31 +283,31 @@ long long launches_total() { return g_launches.load(); }
 void count_launches(int n) { g_launches.fetch_add(n); }
 
 cudaError_t launch_dg_nl(const Geom& g, const double* q, const double* phiB, const double* tau_edge,
-                         double scale, double* fface, double* out, cudaStream_t s) {
+                         double scale, double* fface, double* out, cudaStream_t s, double t) {
     switch (g.P) {
-        case 2: return dg_launch<2, false>(g, q, phiB, tau_edge, scale, fface, out, s);
-        case 3: return dg_launch<3, false>(g, q, phiB, tau_edge, scale, fface, out, s);
-        case 4: return dg_launch<4, false>(g, q, phiB, tau_edge, scale, fface, out, s);
-        case 5: return dg_launch<5, false>(g, q, phiB, tau_edge, scale, fface, out, s);
-        case 6: return dg_launch<6, false>(g, q, phiB, tau_edge, scale, fface, out, s);
-        case 7: return dg_launch<7, false>(g, q, phiB, tau_edge, scale, fface, out, s);
-        case 8: return dg_launch<8, false>(g, q, phiB, tau_edge, scale, fface, out, s);
-        case 9: return dg_launch<9, false>(g, q, phiB, tau_edge, scale, fface, out, s);
+        case 2: return dg_launch<2, false>(g, q, phiB, tau_edge, scale, fface, out, s, t);
+        case 3: return dg_launch<3, false>(g, q, phiB, tau_edge, scale, fface, out, s, t);
+        case 4: return dg_launch<4, false>(g, q, phiB, tau_edge, scale, fface, out, s, t);
+        case 5: return dg_launch<5, false>(g, q, phiB, tau_edge, scale, fface, out, s, t);
+        case 6: return dg_launch<6, false>(g, q, phiB, tau_edge, scale, fface, out, s, t);
+        case 7: return dg_launch<7, false>(g, q, phiB, tau_edge, scale, fface, out, s, t);
+        case 8: return dg_launch<8, false>(g, q, phiB, tau_edge, scale, fface, out, s, t);
+        case 9: return dg_launch<9, false>(g, q, phiB, tau_edge, scale, fface, out, s, t);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_dg_full(const Geom& g, const double* q, const double* phiB, double scale,
-                           double* fface, double* out, cudaStream_t s) {
+                           double* fface, double* out, cudaStream_t s, double t) {
     switch (g.P) {
-        case 2: return dg_launch<2, true>(g, q, phiB, nullptr, scale, fface, out, s);
-        case 3: return dg_launch<3, true>(g, q, phiB, nullptr, scale, fface, out, s);
-        case 4: return dg_launch<4, true>(g, q, phiB, nullptr, scale, fface, out, s);
-        case 5: return dg_launch<5, true>(g, q, phiB, nullptr, scale, fface, out, s);
-        case 6: return dg_launch<6, true>(g, q, phiB, nullptr, scale, fface, out, s);
-        case 7: return dg_launch<7, true>(g, q, phiB, nullptr, scale, fface, out, s);
-        case 8: return dg_launch<8, true>(g, q, phiB, nullptr, scale, fface, out, s);
-        case 9: return dg_launch<9, true>(g, q, phiB, nullptr, scale, fface, out, s);
+        case 2: return dg_launch<2, true>(g, q, phiB, nullptr, scale, fface, out, s, t);
+        case 3: return dg_launch<3, true>(g, q, phiB, nullptr, scale, fface, out, s, t);
+        case 4: return dg_launch<4, true>(g, q, phiB, nullptr, scale, fface, out, s, t);
+        case 5: return dg_launch<5, true>(g, q, phiB, nullptr, scale, fface, out, s, t);
+        case 6: return dg_launch<6, true>(g, q, phiB, nullptr, scale, fface, out, s, t);
+        case 7: return dg_launch<7, true>(g, q, phiB, nullptr, scale, fface, out, s, t);
+        case 8: return dg_launch<8, true>(g, q, phiB, nullptr, scale, fface, out, s, t);
+        case 9: return dg_launch<9, true>(g, q, phiB, nullptr, scale, fface, out, s, t);
         default: return cudaErrorInvalidValue;
     }
 }

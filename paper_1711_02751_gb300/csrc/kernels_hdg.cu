@@ -165,7 +165,7 @@ __global__ void build_local_kernel(Geom g, const double* __restrict__ phiB,
         const double aU = M[(1 * Np + n1) * ld + col];
         const double aV = M[(2 * Np + n1) * ld + col];
         double cz, d = t1;
-        if (neighbour(e, f1, g) >= 0) {
+        if (neighbour(e, f1, g) >= 0 || g.dirichlet) {   // (Dirichlet rows are replaced at assembly)
             if (c1 == 0) cz = nx * aU + ny * aV + t1 * aph;
             else if (c1 == 1) cz = nx * pb[n1] * aph + t1 * aU;
             else cz = ny * pb[n1] * aph + t1 * aV;
@@ -201,7 +201,9 @@ __global__ void gather_rows_kernel(Geom g, const double* __restrict__ Se, double
     for (int t = threadIdx.x; t < 7 * NF * NF; t += blockDim.x) {
         const int slot = t / (NF * NF), ii = (t / NF) % NF, jj = t % NF;
         double v = 0.0;
-        if (slot == 0) {
+        if (g.dirichlet && (!Sm || !Sp)) {
+            v = (slot == 0 && ii == jj) ? 1.0 : 0.0;   // prescribed trace: qhat = q_bc
+        } else if (slot == 0) {
             if (Sm) v += Sm[(fm * NF + ii) * NT + fm * NF + jj];
             if (Sp) v += Sp[(fp * NF + ii) * NT + fp * NF + jj];
         } else {
@@ -220,7 +222,8 @@ __global__ void gather_rows_kernel(Geom g, const double* __restrict__ Se, double
         const int fs = side == 0 ? fm : fp;
         const int fo = k < fs ? k : k + 1;
         const int el = side == 0 ? em : ep;
-        Scol[(size_t)r * 6 + threadIdx.x] = el >= 0 ? edge_of_face(el, fo, g) : r;
+        const bool prescribed = g.dirichlet && (em < 0 || ep < 0);
+        Scol[(size_t)r * 6 + threadIdx.x] = (el >= 0 && !prescribed) ? edge_of_face(el, fo, g) : r;
     }
 }
 
@@ -286,7 +289,7 @@ __global__ void apply_ainv_kernel(Geom g, const double* __restrict__ Ainv, const
 // g = -C Z at every trace node: one thread per (edge, b).
 template <int P>
 __global__ void edge_rhs_kernel(Geom g, const double* __restrict__ Z, const double* __restrict__ phiB,
-                                const double* __restrict__ tau_edge, double* __restrict__ gvec) {
+                                const double* __restrict__ tau_edge, double* __restrict__ gvec, double t_bc) {
     constexpr int Np = P * P, NF = 3 * P;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.n_edges * P) return;
@@ -296,8 +299,18 @@ __global__ void edge_rhs_kernel(Geom g, const double* __restrict__ Z, const doub
     const size_t fs = (size_t)g.n_el * Np;
     const double tau = tau_edge[(size_t)r * P + b];
     const bool xedge = fm == 1;
-    double acc[3] = {0.0, 0.0, 0.0};
+    double* out = gvec + (size_t)r * NF;
     const int e_in = em >= 0 ? em : ep, f_in = em >= 0 ? fm : fp;   // an element that exists
+    if (g.dirichlet && (em < 0 || ep < 0)) {   // prescribed trace row: qhat = q_bc(t)
+        double x, y, ph, U, V;
+        face_node_xy(g, e_in, f_in, b, &x, &y);
+        vortex_state(g, x, y, t_bc, &ph, &U, &V);
+        out[b] = ph;
+        out[P + b] = U;
+        out[2 * P + b] = V;
+        return;
+    }
+    double acc[3] = {0.0, 0.0, 0.0};
     for (int side = 0; side < 2; ++side) {
         int e = side == 0 ? em : ep;
         const int f = side == 0 ? fm : fp;
@@ -313,7 +326,6 @@ __global__ void edge_rhs_kernel(Geom g, const double* __restrict__ Z, const doub
         acc[1] += nx * pb * zph + tau * zU;
         acc[2] += ny * pb * zph + tau * zV;
     }
-    double* out = gvec + (size_t)r * NF;
     out[0 * P + b] = -acc[0];
     out[1 * P + b] = -acc[1];
     out[2 * P + b] = -acc[2];
@@ -408,13 +420,13 @@ cudaError_t assemble_launch(const Geom& g, const double* Se, double* S7, double*
 
 template <int P>
 cudaError_t condense_launch(const Geom& g, const double* Ainv, const double* R1, const double* phiB,
-                            const double* tau_edge, double* Z, double* gvec, cudaStream_t s) {
+                            const double* tau_edge, double* Z, double* gvec, cudaStream_t s, double t) {
     constexpr int NV = 3 * P * P;
     constexpr int EPB = (256 / NV) > 0 ? 256 / NV : 1;
     apply_ainv_kernel<P><<<(g.n_el + EPB - 1) / EPB, EPB * NV, 0, s>>>(g, Ainv, R1, Z);
     count_launches(1);
     const int n = g.n_edges * P;
-    edge_rhs_kernel<P><<<(n + 255) / 256, 256, 0, s>>>(g, Z, phiB, tau_edge, gvec);
+    edge_rhs_kernel<P><<<(n + 255) / 256, 256, 0, s>>>(g, Z, phiB, tau_edge, gvec, t);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -469,8 +481,8 @@ cudaError_t launch_assemble_trace(const Geom& g, const double* Se, double* S7, d
 }
 
 cudaError_t launch_condense(const Geom& g, const double* Ainv, const double* R1, const double* phiB,
-                            const double* tau_edge, double* Z, double* gvec, cudaStream_t s) {
-#define CALL(P) condense_launch<P>(g, Ainv, R1, phiB, tau_edge, Z, gvec, s)
+                            const double* tau_edge, double* Z, double* gvec, cudaStream_t s, double t) {
+#define CALL(P) condense_launch<P>(g, Ainv, R1, phiB, tau_edge, Z, gvec, s, t)
     switch (g.P) {
         case 2: return CALL(2);
         case 3: return CALL(3);

@@ -15,13 +15,13 @@ OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ENONFINITE, ESTATE = range(7)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTCONVERGED", "ENONFINITE", "ESTATE"]
 SCHEMES = {"ars2": 0, "ars3": 1, "rk2": 2, "rk3": 3}
 PRECISIONS = {"fp64": 0, "mixed": 1}
-BOUNDARIES = {"periodic": 0, "wall": 1}
+BOUNDARIES = {"periodic": 0, "wall": 1, "vortex": 2}
 
 EXPORTS = ["hdgdg_bytes_required", "hdgdg_node_coords", "hdgdg_create", "hdgdg_set_state",
            "hdgdg_step", "hdgdg_get_state", "hdgdg_get_stats", "hdgdg_last_error", "hdgdg_destroy",
            "hdgdg_eval_nl", "hdgdg_condense_rhs", "hdgdg_trace_apply", "hdgdg_stage_solve",
            "hdgdg_measure_fp64_tflops", "hdgdg_set_kernel_timing", "hdgdg_kernel_time",
-           "hdgdg_mass_noalloc"]
+           "hdgdg_mass_noalloc", "hdgdg_gll"]
 KERNEL_CLASSES = ["spmv", "ortho", "condense", "recover", "dg", "combine"]
 
 
@@ -38,13 +38,13 @@ class Config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("krylov_rtol", ctypes.c_double),
                 ("krylov_restart", ctypes.c_int), ("krylov_maxit", ctypes.c_int),
                 ("linear_only", ctypes.c_int), ("boundary", ctypes.c_int), ("x0", ctypes.c_double),
-                ("length", ctypes.c_double)]
+                ("length", ctypes.c_double), ("bc_params", ctypes.c_double * 5)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_longlong), ("krylov_iterations", ctypes.c_longlong),
                 ("last_krylov_iterations", ctypes.c_int), ("last_rel_residual", ctypes.c_double),
-                ("mass", ctypes.c_double), ("kernel_launches", ctypes.c_longlong)]
+                ("mass", ctypes.c_double), ("kernel_launches", ctypes.c_longlong), ("time", ctypes.c_double)]
 
 
 _lib = None
@@ -61,6 +61,7 @@ def lib():
         L.hdgdg_bytes_required.restype = ctypes.c_size_t
         L.hdgdg_bytes_required.argtypes = [ctypes.POINTER(Config)]
         L.hdgdg_node_coords.argtypes = [ctypes.POINTER(Config), _P, _P]
+        L.hdgdg_gll.argtypes = [ctypes.c_int, _P, _P]
         L.hdgdg_create.argtypes = [ctypes.POINTER(Config), _P, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
         L.hdgdg_set_state.argtypes = [ctypes.c_void_p, _P, _P, _P]
         L.hdgdg_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
@@ -98,10 +99,11 @@ def _f64(a, shape=None):
 
 def make_config(N, k, dt, g=1.0, H0=1.0, scheme="ars2", krylov_rtol=0.0, krylov_restart=0,
                 krylov_maxit=0, linear_only=False, precision="fp64", boundary="periodic", x0=0.0,
-                length=1.0):
+                length=1.0, bc_params=(0.0, 0.0, 0.0, 0.0, 0.0)):
+    """bc_params (boundary='vortex'): beta, u_inf, v_inf, x_c, y_c of the moving vortex."""
     return Config(int(N), int(k), float(g), float(H0), SCHEMES[scheme], float(dt), PRECISIONS[precision],
                   float(krylov_rtol), int(krylov_restart), int(krylov_maxit), int(bool(linear_only)),
-                  BOUNDARIES[boundary], float(x0), float(length))
+                  BOUNDARIES[boundary], float(x0), float(length), (ctypes.c_double * 5)(*bc_params))
 
 
 def bytes_required(cfg):
@@ -125,6 +127,16 @@ def mass_noalloc(n_side, degree_k, phi_eta_dev_ptr, mass_dev_ptr, stream=None):
                                     ctypes.c_void_p(mass_dev_ptr), ctypes.c_void_p(stream) if stream else None)
 
 
+def gll(k):
+    """The library's GLL nodes and weights of degree k."""
+    x = np.empty(k + 1)
+    w = np.empty(k + 1)
+    st = lib().hdgdg_gll(int(k), _ptr(x), _ptr(w))
+    if st != OK:
+        raise HdgdgError(st, "gll")
+    return x, w
+
+
 def measure_fp64_tflops():
     out = ctypes.c_double(0.0)
     st = lib().hdgdg_measure_fp64_tflops(ctypes.byref(out))
@@ -138,12 +150,12 @@ class Sim:
 
     def __init__(self, N, k, dt, bottom=None, g=1.0, H0=1.0, scheme="ars2", stream=None,
                  krylov_rtol=0.0, krylov_restart=0, krylov_maxit=0, linear_only=False, precision="fp64",
-                 boundary="periodic", x0=0.0, length=1.0):
+                 boundary="periodic", x0=0.0, length=1.0, bc_params=(0.0, 0.0, 0.0, 0.0, 0.0)):
         self.N, self.k, self.P = int(N), int(k), int(k) + 1
         self.n_el, self.Np = self.N * self.N, self.P * self.P
-        self.n_edges = 2 * self.N * (self.N + 1) if boundary == "wall" else 2 * self.n_el
+        self.n_edges = 2 * self.N * (self.N + 1) if boundary != "periodic" else 2 * self.n_el
         self.cfg = make_config(N, k, dt, g, H0, scheme, krylov_rtol, krylov_restart, krylov_maxit,
-                               linear_only, precision, boundary, x0, length)
+                               linear_only, precision, boundary, x0, length, bc_params)
         self._h = ctypes.c_void_p(None)
         b = None if bottom is None else _f64(bottom, (self.n_el, self.Np))
         st = lib().hdgdg_create(ctypes.byref(self.cfg), None if b is None else _ptr(b),

@@ -39,11 +39,11 @@ def test_fullsize_dg_residual_matches_oracle(work):
 def test_fullsize_two_hundred_steps(work):
     """The workload's 200 steps in both forms: finite; mass conserved to the trace solve's
     tolerance (the conservation condition, eq. HDGcont, holds to the Krylov residual: FP64 form
-    rtol 1e-15 -> 1e-11 here, mixed form rtol 1e-10 per stage solve over 400 solves -> 1e-7);
+    rtol 1e-15 -> 1e-11 here, mixed form rtol 1e-9 per stage solve over 400 solves -> 1e-6);
     and the mixed form within 1e-6 of the FP64 form at the end."""
     m, h, hu, hv, b, dt = work
     res = {}
-    for p, bound in (("fp64", 1e-11), ("mixed", 1e-7)):
+    for p, bound in (("fp64", 1e-11), ("mixed", 1e-6)):
         with hd.Sim(N, K, dt, bottom=b, precision=p) as s:
             s.set_state(h, hu, hv)
             m0 = s.stats()["mass"]

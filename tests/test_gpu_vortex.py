@@ -1,0 +1,77 @@
+"""The moving vortex with exact-solution traces (Sec. 7.1) on the GPU, against the oracle."""
+import numpy as np
+import pytest
+
+from oracle import imex, swe
+from paper_1711_02751_gb300 import workloads as W
+
+from test_oracle_vortex import eta_errors, vortex_problem
+
+pytestmark = pytest.mark.gpu
+hd = pytest.importorskip("paper_1711_02751_gb300.hdgdg")
+V = W.VORTEX
+BC = (V["beta"], V["u_inf"], V["v_inf"], V["xc"], V["yc"])
+
+
+def _sim(m, dt, **kw):
+    return hd.Sim(m.N, m.k, dt, bottom=np.zeros((m.n_el, m.P ** 2)), g=V["g"], H0=V["H_inf"],
+                  boundary="vortex", x0=-2.0, length=4.0, bc_params=BC, **kw)
+
+
+def _user(m, q):
+    return swe.from_state(q, np.full(m.x.shape, V["g"] * V["H_inf"]), V["g"])
+
+
+@pytest.mark.parametrize("N,k", [(3, 2), (4, 3), (2, 4)])
+def test_vortex_rows_match_oracle(N, k):
+    m, q, phiB, bc = vortex_problem(N, k)
+    m.bc_q = bc(0.0)
+    R2 = swe.dirichlet_R2(m, m.bc_q)
+    qq = q + 1e-3 * np.random.default_rng(N).standard_normal(q.shape)
+    ref_nl = swe.minv(m, swe.NL(m, qq, phiB)).reshape(3, m.n_el, -1)
+    st = imex.Stepper(m, phiB, 0.01, scheme="ars3", solver="dense", bc=bc)
+    Qo, lo = st.cond.solve(qq, R2)
+    with _sim(m, 0.01, scheme="ars3") as s:
+        nl = s.eval_nl(qq.reshape(3, m.n_el, -1))
+        Q, lam, _ = s.stage_solve(qq.reshape(3, m.n_el, -1))
+    assert np.abs(nl - ref_nl).max() <= 1e-12 * np.abs(ref_nl).max()
+    for c in range(3):
+        assert imex.rel_l2(m, Q[c].reshape(m.x.shape), Qo[c]) <= 1e-11
+    assert np.abs(lam - lo.reshape(lam.shape)).max() <= 1e-11 * np.abs(lo).max()
+
+
+@pytest.mark.parametrize("scheme,precision", [("ars3", "fp64"), ("ars2", "fp64"), ("ars3", "mixed"),
+                                              ("rk3", "fp64")])
+def test_vortex_steps_match_oracle(scheme, precision):
+    m, q, phiB, bc = vortex_problem(4, 3)
+    dt = 0.005 if scheme != "rk3" else 0.002
+    n = 10
+    if scheme == "rk3":
+        qo = imex.ExplicitRK(m, phiB, dt, "rk3", bc=bc).run(q, n)
+    else:
+        qo = imex.Stepper(m, phiB, dt, scheme=scheme, solver="lu", bc=bc).run(q, n)
+    with _sim(m, dt, scheme=scheme, precision=precision) as s:
+        s.set_state(*_user(m, q))
+        s.step(n)
+        assert abs(s.stats()["time"] - n * dt) < 1e-12
+        qa, _ = swe.to_state(*s.get_state(), np.zeros((m.n_el, m.P ** 2)), V["g"], V["H_inf"])
+    tol = 1e-11 if precision == "fp64" else 1e-7
+    for c in range(3):
+        assert imex.rel_l2(m, qa[c], qo[c]) <= tol
+
+
+def test_vortex_errors_on_gpu_match_papers_table():
+    """p = 2 and 3 on 8x8 at T = 2 (Table tab:tc_mv_hconv_hdg3): L1 and L2 of eta within 15%."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "vortex_errors.json")))
+    for k, dt in ((2, 0.005), (3, 0.0025)):
+        m, q, phiB, bc = vortex_problem(8, k)
+        with _sim(m, dt, scheme="ars3") as s:
+            s.set_state(*_user(m, q))
+            s.step(int(round(2.0 / dt)))
+            qa, _ = swe.to_state(*s.get_state(), np.zeros((m.n_el, m.P ** 2)), V["g"], V["H_inf"])
+        l1, l2, _ = eta_errors(m, qa, 2.0)
+        ref = gold["eta"][str(k)]["8"]
+        assert abs(l1 - ref[0]) <= 0.15 * ref[0], (k, l1, ref)
+        assert abs(l2 - ref[1]) <= 0.15 * ref[1], (k, l2, ref)

@@ -69,7 +69,7 @@ def test_wall_trace_system_matches_oracle(N, k):
 
 
 @pytest.mark.parametrize("scheme,precision,tol", [("ars2", "fp64", 1e-11), ("ars3", "fp64", 1e-11),
-                                                  ("ars2", "mixed", 1e-8), ("rk2", "fp64", 1e-11)])
+                                                  ("ars2", "mixed", 1e-7), ("rk2", "fp64", 1e-11)])
 def test_wall_steps_match_oracle(scheme, precision, tol):
     m, (h, hu, hv, b), q, phiB = _walled(6, 3)
     dt = W.advective_dt(m.x.reshape(m.n_el, -1), h, hu, hv, 6)
