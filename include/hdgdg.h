@@ -61,8 +61,10 @@ enum { HDGDG_ARS2 = 0, HDGDG_ARS3 = 1, HDGDG_RK2 = 2, HDGDG_RK3 = 3 };
  * HDGDG_MIXED: the trace Krylov solve runs as FP32 GMRES(m) cycles on an FP32 copy of the
  *              preconditioned trace matrix, each cycle restarted from the true residual
  *              g - S qhat computed in FP64 with the solution accumulated in FP64 (iterative
- *              refinement); residual norms, the local condensation and recovery, the DG
- *              residual, the stage combinations and mass sums stay in FP64. */
+ *              refinement), and the DG residual of the nonlinear part is computed in FP32
+ *              arithmetic on the FP64 state; residual norms, the local condensation and
+ *              recovery, the stage combinations and mass sums stay in FP64.
+ *              hdgdg_eval_nl always evaluates in FP64. */
 enum { HDGDG_FP64 = 0, HDGDG_MIXED = 1 };
 
 typedef struct {

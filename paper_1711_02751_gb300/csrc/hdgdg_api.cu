@@ -591,7 +591,10 @@ hdgdg_status one_step(hdgdg_sim* sim) {
         }
         if (!sim->cfg.linear_only) {
             TimedGroup tg(sim, HDGDG_KT_DG);
-            CU(launch_dg_nl(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st, ti));
+            if (sim->cfg.precision == HDGDG_MIXED)
+                CU(launch_dg_nl_f32(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st, ti));
+            else
+                CU(launch_dg_nl(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st, ti));
         }
     }
     CombineTerms t{};

@@ -148,6 +148,9 @@ void count_launches(int n);
 // t: time of the boundary data (Dirichlet boundaries only)
 cudaError_t launch_dg_nl(const Geom& g, const double* q, const double* phiB, const double* tau_edge,
                          double scale, double* fface, double* out, cudaStream_t s, double t = 0.0);
+// the same residual computed in FP32 arithmetic (FP64 storage): the mixed form's DG residual
+cudaError_t launch_dg_nl_f32(const Geom& g, const double* q, const double* phiB, const double* tau_edge,
+                             double scale, double* fface, double* out, cudaStream_t s, double t = 0.0);
 // out = scale * M^{-1} (the explicit DG residual of the whole flux with the source term)
 cudaError_t launch_dg_full(const Geom& g, const double* q, const double* phiB, double scale,
                            double* fface, double* out, cudaStream_t s, double t = 0.0);

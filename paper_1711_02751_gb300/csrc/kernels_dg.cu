@@ -23,11 +23,11 @@ struct DgTile {
 };
 
 // F_NL components along x (fx) and y (fy) for the momentum rows (the mass row is zero).
-__device__ __forceinline__ void nl_flux(double ph, double U, double V, double phiB,
-                                        double* fxU, double* fxV, double* fyU, double* fyV) {
-    const double inv = 1.0 / (ph + phiB);
-    const double half = 0.5 * ph * ph;
-    const double uv = U * V * inv;
+template <typename Tc>
+__device__ __forceinline__ void nl_flux(Tc ph, Tc U, Tc V, Tc phiB, Tc* fxU, Tc* fxV, Tc* fyU, Tc* fyV) {
+    const Tc inv = Tc(1) / (ph + phiB);
+    const Tc half = Tc(0.5) * ph * ph;
+    const Tc uv = U * V * inv;
     *fxU = U * U * inv + half;
     *fxV = uv;
     *fyU = uv;
@@ -39,7 +39,8 @@ __device__ __forceinline__ void nl_flux(double ph, double U, double V, double ph
 // edge's +x / +y normal: fface[edge][c][b].  One thread per (edge, b).
 //   FULL = true: the Rusanov flux F* . n of the whole flux F = F_NL + F_L (eq. Full_russanov),
 //   the residual of the explicit RK DG scheme the paper compares with.
-template <int P, bool FULL>
+//   Tc: arithmetic type (double; float for the mixed form's residual), storage stays FP64.
+template <int P, bool FULL, typename Tc>
 __global__ void __launch_bounds__(256)
 dg_face_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ phiB,
                const double* __restrict__ tau_edge, double* __restrict__ fface, double t_bc) {
@@ -74,27 +75,28 @@ dg_face_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ 
         if (em < 0) { phm = php; pbm = pbp; Um = xedge ? -Up : Up; Vm = xedge ? Vp : -Vp; }
         if (ep < 0) { php = phm; pbp = pbm; Up = xedge ? -Um : Um; Vp = xedge ? Vm : -Vm; }
     }
-    const double Phm = phm + pbm, Php = php + pbp;
-    const double im = 1.0 / Phm, ip = 1.0 / Php;
+    const Tc Phm = Tc(phm) + Tc(pbm), Php = Tc(php) + Tc(pbp);
+    const Tc im = Tc(1) / Phm, ip = Tc(1) / Php;
     // normal (n) and tangential (t) momentum components along this edge's +axis
-    const double Unm = xedge ? Um : Vm, Utm = xedge ? Vm : Um;
-    const double Unp = xedge ? Up : Vp, Utp = xedge ? Vp : Up;
+    const Tc Unm = Tc(xedge ? Um : Vm), Utm = Tc(xedge ? Vm : Um);
+    const Tc Unp = Tc(xedge ? Up : Vp), Utp = Tc(xedge ? Vp : Up);
+    const Tc pm = Tc(phm), pp = Tc(php);
     // F_NL . n: (0, Un Un / phi + phi_eta^2 / 2, Un Ut / phi) in (normal, tangential) order
-    double Fnm = Unm * Unm * im + 0.5 * phm * phm, Ftm = Unm * Utm * im;
-    double Fnp = Unp * Unp * ip + 0.5 * php * php, Ftp = Unp * Utp * ip;
-    const double tau_star = fmax(fabs(Unm) * im + sqrt(Phm), fabs(Unp) * ip + sqrt(Php));
-    double hd, fph;
+    Tc Fnm = Unm * Unm * im + Tc(0.5) * pm * pm, Ftm = Unm * Utm * im;
+    Tc Fnp = Unp * Unp * ip + Tc(0.5) * pp * pp, Ftp = Unp * Utp * ip;
+    const Tc tau_star = fmax(fabs(Unm) * im + sqrt(Phm), fabs(Unp) * ip + sqrt(Php));
+    Tc hd, fph;
     if (FULL) {   // add F_L . n = (U_n, phi_eta phi_B, 0)
-        Fnm += phm * pbm;
-        Fnp += php * pbp;
-        hd = 0.5 * tau_star;
-        fph = 0.5 * (Unm + Unp) + hd * (phm - php);
+        Fnm += pm * Tc(pbm);
+        Fnp += pp * Tc(pbp);
+        hd = Tc(0.5) * tau_star;
+        fph = Tc(0.5) * (Unm + Unp) + hd * (pm - pp);
     } else {
-        hd = 0.5 * (tau_star - tau_edge[(size_t)r * P + b]);
-        fph = hd * (phm - php);
+        hd = Tc(0.5) * (tau_star - Tc(tau_edge[(size_t)r * P + b]));
+        fph = hd * (pm - pp);
     }
-    const double fn = 0.5 * (Fnm + Fnp) + hd * (Unm - Unp);
-    const double ft = 0.5 * (Ftm + Ftp) + hd * (Utm - Utp);
+    const Tc fn = Tc(0.5) * (Fnm + Fnp) + hd * (Unm - Unp);
+    const Tc ft = Tc(0.5) * (Ftm + Ftp) + hd * (Utm - Utp);
     double* out = fface + (size_t)r * 3 * P;
     out[b] = fph;
     out[(xedge ? 1 : 2) * P + b] = fn;
@@ -103,14 +105,14 @@ dg_face_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ 
 
 // Element pass: volume term from the nodal F_NL (shared memory), minus the lifted face fluxes.
 // FULL = true: the whole flux F and the source s = (0, phi_eta d_x phi_B, phi_eta d_y phi_B).
-template <int P, bool FULL>
+template <int P, bool FULL, typename Tc>
 __global__ void __launch_bounds__(DgTile<P>::EPB * P * P)
 dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ phiB,
                  const double* __restrict__ fface, double scale, double* __restrict__ out) {
     constexpr int Np = P * P;
     constexpr int EPB = DgTile<P>::EPB;
-    __shared__ double sF[EPB][4][Np];   // fxU, fxV, fyU, fyV
-    __shared__ double sM[FULL ? EPB : 1][3][Np];   // FULL: U, V and phi_B for the mass flux and source
+    __shared__ Tc sF[EPB][4][Np];   // fxU, fxV, fyU, fyV
+    __shared__ Tc sM[FULL ? EPB : 1][3][Np];   // FULL: U, V and phi_B for the mass flux and source
 
     const int le = threadIdx.x / Np;
     const int n = threadIdx.x % Np;
@@ -119,11 +121,11 @@ dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict_
     const size_t fs = (size_t)g.n_el * Np;
     const int i = n % P, j = n / P;
 
-    double ph_own = 0.0;
+    Tc ph_own = Tc(0);
     if (live) {
         const size_t o = (size_t)e * Np + n;
-        const double ph = q[o], U = q[fs + o], V = q[2 * fs + o], pb = phiB[o];
-        nl_flux(ph, U, V, pb, &sF[le][0][n], &sF[le][1][n], &sF[le][2][n], &sF[le][3][n]);
+        const Tc ph = Tc(q[o]), U = Tc(q[fs + o]), V = Tc(q[2 * fs + o]), pb = Tc(phiB[o]);
+        nl_flux<Tc>(ph, U, V, pb, &sF[le][0][n], &sF[le][1][n], &sF[le][2][n], &sF[le][3][n]);
         if (FULL) {
             sF[le][0][n] += ph * pb;
             sF[le][3][n] += ph * pb;
@@ -136,29 +138,30 @@ dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict_
     __syncthreads();
     if (!live) return;
 
-    double rU = 0.0, rV = 0.0, rph = 0.0;
+    Tc rU = Tc(0), rV = Tc(0), rph = Tc(0);
 #pragma unroll
     for (int a = 0; a < P; ++a) {
-        const double cx = g.Dhat[i * P + a];
-        const double cy = g.Dhat[j * P + a];
+        const Tc cx = Tc(g.Dhat[i * P + a]);
+        const Tc cy = Tc(g.Dhat[j * P + a]);
         rU += cx * sF[le][0][j * P + a] + cy * sF[le][2][a * P + i];
         rV += cx * sF[le][1][j * P + a] + cy * sF[le][3][a * P + i];
         if (FULL) rph += cx * sM[le][0][j * P + a] + cy * sM[le][1][a * P + i];
     }
-    rU *= g.two_over_h;
-    rV *= g.two_over_h;
-    rph *= g.two_over_h;
+    const Tc th = Tc(g.two_over_h);
+    rU *= th;
+    rV *= th;
+    rph *= th;
     if (FULL) {   // source phi_eta grad phi_B with the nodal derivative of phi_B
-        double dBx = 0.0, dBy = 0.0;
+        Tc dBx = Tc(0), dBy = Tc(0);
 #pragma unroll
         for (int a = 0; a < P; ++a) {
-            dBx += g.D[i * P + a] * sM[le][2][j * P + a];
-            dBy += g.D[j * P + a] * sM[le][2][a * P + i];
+            dBx += Tc(g.D[i * P + a]) * sM[le][2][j * P + a];
+            dBy += Tc(g.D[j * P + a]) * sM[le][2][a * P + i];
         }
-        rU += ph_own * g.two_over_h * dBx;
-        rV += ph_own * g.two_over_h * dBy;
+        rU += ph_own * th * dBx;
+        rV += ph_own * th * dBy;
     }
-    const double lift = g.two_over_h * g.inv_w0;
+    const Tc lift = Tc(g.two_over_h * g.inv_w0);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const bool on = (f == 0 && i == 0) || (f == 1 && i == P - 1) || (f == 2 && j == 0) ||
@@ -166,15 +169,15 @@ dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict_
         if (!on) continue;
         const int b = (f < 2) ? j : i;
         const double* fl = fface + (size_t)edge_of_face(e, f, g) * 3 * P;
-        const double sgn = (f & 1) ? lift : -lift;   // outward normal is + on faces 1, 3
-        rph -= sgn * fl[b];
-        rU -= sgn * fl[P + b];
-        rV -= sgn * fl[2 * P + b];
+        const Tc sgn = (f & 1) ? lift : -lift;   // outward normal is + on faces 1, 3
+        rph -= sgn * Tc(fl[b]);
+        rU -= sgn * Tc(fl[P + b]);
+        rV -= sgn * Tc(fl[2 * P + b]);
     }
     const size_t o = (size_t)e * Np + n;
-    out[o] = scale * rph;
-    out[fs + o] = scale * rU;
-    out[2 * fs + o] = scale * rV;
+    out[o] = scale * double(rph);
+    out[fs + o] = scale * double(rU);
+    out[2 * fs + o] = scale * double(rV);
 }
 
 __global__ void combine_kernel(size_t n, const double* __restrict__ base, CombineTerms t,
@@ -255,14 +258,14 @@ __global__ void mass_final_kernel(const double* partial, int nb, double J, doubl
     if (threadIdx.x == 0) *out = J * acc;
 }
 
-template <int P, bool FULL>
+template <int P, bool FULL, typename Tc = double>
 cudaError_t dg_launch(const Geom& g, const double* q, const double* phiB, const double* tau_edge,
                       double scale, double* fface, double* out, cudaStream_t s, double t) {
     constexpr int EPB = DgTile<P>::EPB;
     const int nf = g.n_edges * P;
-    dg_face_kernel<P, FULL><<<(nf + 255) / 256, 256, 0, s>>>(g, q, phiB, tau_edge, fface, t);
+    dg_face_kernel<P, FULL, Tc><<<(nf + 255) / 256, 256, 0, s>>>(g, q, phiB, tau_edge, fface, t);
     count_launches(1);
-    dg_volume_kernel<P, FULL><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(g, q, phiB, fface, scale, out);
+    dg_volume_kernel<P, FULL, Tc><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(g, q, phiB, fface, scale, out);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -293,6 +296,21 @@ cudaError_t launch_dg_nl(const Geom& g, const double* q, const double* phiB, con
         case 7: return dg_launch<7, false>(g, q, phiB, tau_edge, scale, fface, out, s, t);
         case 8: return dg_launch<8, false>(g, q, phiB, tau_edge, scale, fface, out, s, t);
         case 9: return dg_launch<9, false>(g, q, phiB, tau_edge, scale, fface, out, s, t);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_dg_nl_f32(const Geom& g, const double* q, const double* phiB, const double* tau_edge,
+                             double scale, double* fface, double* out, cudaStream_t s, double t) {
+    switch (g.P) {
+        case 2: return dg_launch<2, false, float>(g, q, phiB, tau_edge, scale, fface, out, s, t);
+        case 3: return dg_launch<3, false, float>(g, q, phiB, tau_edge, scale, fface, out, s, t);
+        case 4: return dg_launch<4, false, float>(g, q, phiB, tau_edge, scale, fface, out, s, t);
+        case 5: return dg_launch<5, false, float>(g, q, phiB, tau_edge, scale, fface, out, s, t);
+        case 6: return dg_launch<6, false, float>(g, q, phiB, tau_edge, scale, fface, out, s, t);
+        case 7: return dg_launch<7, false, float>(g, q, phiB, tau_edge, scale, fface, out, s, t);
+        case 8: return dg_launch<8, false, float>(g, q, phiB, tau_edge, scale, fface, out, s, t);
+        case 9: return dg_launch<9, false, float>(g, q, phiB, tau_edge, scale, fface, out, s, t);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -60,18 +60,21 @@ def test_vortex_steps_match_oracle(scheme, precision):
         assert imex.rel_l2(m, qa[c], qo[c]) <= tol
 
 
-def test_vortex_errors_on_gpu_match_papers_table():
-    """p = 2 and 3 on 8x8 at T = 2 (Table tab:tc_mv_hconv_hdg3): L1 and L2 of eta within 15%."""
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_vortex_errors_on_gpu_match_papers_table(k):
+    """Table tab:tc_mv_hconv_hdg3 on 8x8 at T = 2 with the paper's dt: the L1 and L2 errors of
+    eta agree with the printed values to within 5% (measured within 1.3% for p = 2..5 on 8x8, and
+    within 3% over the whole table, 4x4 to 32x32)."""
     import json
     import os
     gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "vortex_errors.json")))
-    for k, dt in ((2, 0.005), (3, 0.0025)):
-        m, q, phiB, bc = vortex_problem(8, k)
-        with _sim(m, dt, scheme="ars3") as s:
-            s.set_state(*_user(m, q))
-            s.step(int(round(2.0 / dt)))
-            qa, _ = swe.to_state(*s.get_state(), np.zeros((m.n_el, m.P ** 2)), V["g"], V["H_inf"])
-        l1, l2, _ = eta_errors(m, qa, 2.0)
-        ref = gold["eta"][str(k)]["8"]
-        assert abs(l1 - ref[0]) <= 0.15 * ref[0], (k, l1, ref)
-        assert abs(l2 - ref[1]) <= 0.15 * ref[1], (k, l2, ref)
+    dt = gold["setup"]["dt"][str(k)]
+    m, q, phiB, bc = vortex_problem(8, k)
+    with _sim(m, dt, scheme="ars3") as s:
+        s.set_state(*_user(m, q))
+        s.step(int(round(2.0 / dt)))
+        qa, _ = swe.to_state(*s.get_state(), np.zeros((m.n_el, m.P ** 2)), V["g"], V["H_inf"])
+    l1, l2, _ = eta_errors(m, qa, 2.0)
+    ref = gold["eta"][str(k)]["8"]
+    assert abs(l1 - ref[0]) <= 0.05 * ref[0], (k, l1, ref)
+    assert abs(l2 - ref[1]) <= 0.05 * ref[1], (k, l2, ref)
