@@ -89,6 +89,11 @@ typedef struct {
     double x0;           /* domain [x0, x0 + length]^2 (node coordinates follow) */
     double length;       /* side of the square domain; <= 0 selects 1 */
     double bc_params[5]; /* HDGDG_VORTEX: beta, u_inf, v_inf, x_c, y_c of eq. tc_vortex_ic */
+    int batch;           /* >= 1 (0 = 1): independent instances of this mesh advanced together;
+                            every kernel covers all instances in one launch per stage and the
+                            trace systems are solved as one block-diagonal system.  Arrays of
+                            create / set_state / get_state are then [batch][n_el][(k+1)^2]. */
+    const double* dt_per_instance; /* host [batch] time steps (read at create); NULL = dt for all */
 } hdgdg_config;
 
 /* HDGDG_VORTEX: the exact-solution boundary conditions of the paper's moving-vortex test
@@ -125,8 +130,8 @@ typedef struct hdgdg_sim hdgdg_sim;
  * memory budget).  Returns 0 for an invalid configuration.  No GPU call is made. */
 size_t hdgdg_bytes_required(const hdgdg_config* cfg);
 
-/* GLL node coordinates x, y (host, [n_el][(k+1)^2] each) of the mesh of cfg, in the
- * node order above.  No GPU call is made.  EINVAL on a bad configuration or NULL. */
+/* GLL node coordinates x, y (host, [n_el][(k+1)^2] each) of one instance of the mesh of cfg,
+ * in the node order above.  No GPU call is made.  EINVAL on a bad configuration or NULL. */
 hdgdg_status hdgdg_node_coords(const hdgdg_config* cfg, double* x, double* y);
 
 /* The library's degree-k Gauss-Lobatto-Legendre nodes and weights on [-1, 1] (host arrays of

@@ -45,7 +45,7 @@ bool valid(const hdgdg_config* c) {
            (c->precision == HDGDG_FP64 || c->precision == HDGDG_MIXED) &&
            (c->linear_only == 0 || c->linear_only == 1) &&
            c->boundary >= HDGDG_PERIODIC && c->boundary <= HDGDG_VORTEX && std::isfinite(c->x0) &&
-           std::isfinite(c->length) &&
+           std::isfinite(c->length) && c->batch >= 0 && c->batch <= (1 << 20) &&
            c->krylov_restart <= kMaxRestart;
 }
 
@@ -56,8 +56,9 @@ int restart_of(const hdgdg_config* c) { return c->krylov_restart > 0 ? c->krylov
 Plan make_plan(const hdgdg_config* c) {
     Plan p;
     const size_t N = (size_t)c->n_side, P = (size_t)c->degree_k + 1;
-    const size_t n_el = N * N, Np = P * P;
-    const size_t n_edges = c->boundary != HDGDG_PERIODIC ? 2 * N * (N + 1) : 2 * N * N;
+    const size_t B = c->batch > 0 ? (size_t)c->batch : 1;
+    const size_t n_el = B * N * N, Np = P * P;
+    const size_t n_edges = B * (c->boundary != HDGDG_PERIODIC ? 2 * N * (N + 1) : 2 * N * N);
     p.n = n_el * Np;
     p.NV = (int)(3 * Np);
     p.NF = (int)(3 * P);
@@ -75,7 +76,7 @@ Plan make_plan(const hdgdg_config* c) {
         p.setup_temp = 0;
         return p;
     }
-    b += p.n * d + n_edges * P * d;                           // phiB, tau
+    b += p.n * d + n_edges * P * d + B * d;                   // phiB, tau, time-step factors
     b += n_el * (size_t)p.NV * p.NV * d;                      // A^{-1}
     b += n_edges * 6 * (size_t)p.NF * p.NF * d;               // S~
     b += n_edges * 6 * sizeof(int);                           // columns
@@ -152,13 +153,17 @@ Geom make_geom(const hdgdg_config* c, double* xi_out) {
     g.N = c->n_side;
     g.P = c->degree_k + 1;
     g.Np = g.P * g.P;
-    g.n_el = g.N * g.N;
+    g.batch = c->batch > 0 ? c->batch : 1;
+    g.n_el_inst = g.N * g.N;
+    g.n_el = g.batch * g.n_el_inst;
     g.walls = c->boundary != HDGDG_PERIODIC ? 1 : 0;
     g.dirichlet = c->boundary == HDGDG_VORTEX ? 1 : 0;
     g.gacc = c->g;
     g.H0 = c->H0;
     for (int i = 0; i < 5; ++i) g.vortex[i] = c->bc_params[i];
-    g.n_edges = g.walls ? 2 * g.N * (g.N + 1) : 2 * g.n_el;
+    g.n_edges_inst = g.walls ? 2 * g.N * (g.N + 1) : 2 * g.n_el_inst;
+    g.n_edges = g.batch * g.n_edges_inst;
+    g.dt_scale = nullptr;
     const double L = c->length > 0.0 ? c->length : 1.0;
     g.x0 = c->x0;
     g.h = L / g.N;
@@ -644,6 +649,18 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
     }
     TRY(dalloc(sim, &sim->phiB, p.n));
     TRY(dalloc(sim, &sim->tau, tau.size()));
+    if (c->dt_per_instance) {   // per-instance time steps as factors of cfg.dt
+        std::vector<double> f(g.batch);
+        for (int i = 0; i < g.batch; ++i) {
+            f[i] = c->dt_per_instance[i] / c->dt;
+            if (!std::isfinite(f[i]) || !(f[i] > 0.0))
+                return fail(sim, HDGDG_EINVAL, "time step of instance %d is not positive", i);
+        }
+        double* d = nullptr;
+        TRY(dalloc(sim, &d, g.batch));
+        CU(cudaMemcpy(d, f.data(), g.batch * sizeof(double), cudaMemcpyHostToDevice));
+        sim->g.dt_scale = d;
+    }
     if (explicit_scheme(c)) {
         for (double** v : {&sim->q, &sim->q_new, &sim->R1, &sim->Qs}) TRY(dalloc(sim, v, 3 * p.n));
         for (int i = 0; i < 3; ++i) TRY(dalloc(sim, &sim->NLs[i], 3 * p.n));
@@ -738,7 +755,7 @@ hdgdg_status hdgdg_node_coords(const hdgdg_config* cfg, double* x, double* y) {
     if (!valid(cfg) || !x || !y) return HDGDG_EINVAL;
     double xi[kMaxP];
     Geom g = make_geom(cfg, xi);
-    for (int e = 0; e < g.n_el; ++e) {
+    for (int e = 0; e < g.n_el_inst; ++e) {
         const int ex = e % g.N, ey = e / g.N;
         for (int j = 0; j < g.P; ++j)
             for (int i = 0; i < g.P; ++i) {

@@ -26,7 +26,10 @@ constexpr int kMaxP = 9;   // degree k <= 8
 
 // Mesh and GLL tables, passed by value to kernels.
 struct Geom {
-    int N, P, Np, n_el, n_edges;
+    int N, P, Np, n_el, n_edges;   // n_el, n_edges: totals over all instances of the batch
+    int batch;                     // instances of the same N x N mesh advanced together
+    int n_el_inst, n_edges_inst;   // per instance
+    const double* dt_scale;        // device [batch]: instance time step / config time step, or NULL
     int walls;                  // 0: periodic unit square; 1: a bounded square (walls or Dirichlet)
     int dirichlet;              // 1: boundary faces take the moving-vortex exact solution (Sec. 7.1)
     double x0;                  // domain [x0, x0 + N h]^2
@@ -49,7 +52,7 @@ __host__ __device__ inline int face_node(int f, int b, int P) {
 // Connectivity of the N x N mesh.  Periodic: edge r < N^2 is face 1 of element r and edge
 // N^2 + r face 3 of element r.  Walls: x-edges ey*(N+1) + ix (ix = 0..N), y-edges
 // N(N+1) + iy*N + ex (iy = 0..N); a face on a wall has no neighbour (-1).
-__host__ __device__ inline int edge_of_face(int e, int f, const Geom& g) {
+__host__ __device__ inline int local_edge_of_face(int e, int f, const Geom& g) {
     const int N = g.N, ex = e % N, ey = e / N;
     if (g.walls) {
         const int nx = N * (N + 1);
@@ -68,7 +71,7 @@ __host__ __device__ inline int edge_of_face(int e, int f, const Geom& g) {
     }
 }
 
-__host__ __device__ inline int neighbour(int e, int f, const Geom& g) {
+__host__ __device__ inline int local_neighbour(int e, int f, const Geom& g) {
     const int N = g.N, ex = e % N, ey = e / N;
     if (g.walls) {
         switch (f) {
@@ -88,7 +91,7 @@ __host__ __device__ inline int neighbour(int e, int f, const Geom& g) {
 
 // Minus side (face 1 or 3: normal +x / +y) and plus side (face 0 or 2) of edge r; an absent
 // side (wall) is -1 with the face it would have had.
-__host__ __device__ inline void edge_sides(int r, const Geom& g, int* em, int* fm, int* ep, int* fp) {
+__host__ __device__ inline void local_edge_sides(int r, const Geom& g, int* em, int* fm, int* ep, int* fp) {
     const int N = g.N;
     if (g.walls) {
         const int nx = N * (N + 1);
@@ -107,8 +110,33 @@ __host__ __device__ inline void edge_sides(int r, const Geom& g, int* em, int* f
         }
         return;
     }
-    if (r < N * N) { *em = r; *fm = 1; *ep = neighbour(r, 1, g); *fp = 0; }
-    else { const int e = r - N * N; *em = e; *fm = 3; *ep = neighbour(e, 3, g); *fp = 2; }
+    if (r < N * N) { *em = r; *fm = 1; *ep = local_neighbour(r, 1, g); *fp = 0; }
+    else { const int e = r - N * N; *em = e; *fm = 3; *ep = local_neighbour(e, 3, g); *fp = 2; }
+}
+
+// Batched indices: instance i owns elements [i n_el_inst, (i+1) n_el_inst) and edges
+// [i n_edges_inst, (i+1) n_edges_inst); connectivity never crosses instances.
+__host__ __device__ inline int edge_of_face(int e, int f, const Geom& g) {
+    const int inst = e / g.n_el_inst;
+    return inst * g.n_edges_inst + local_edge_of_face(e - inst * g.n_el_inst, f, g);
+}
+
+__host__ __device__ inline int neighbour(int e, int f, const Geom& g) {
+    const int inst = e / g.n_el_inst;
+    const int nb = local_neighbour(e - inst * g.n_el_inst, f, g);
+    return nb < 0 ? -1 : inst * g.n_el_inst + nb;
+}
+
+__host__ __device__ inline void edge_sides(int r, const Geom& g, int* em, int* fm, int* ep, int* fp) {
+    const int inst = r / g.n_edges_inst;
+    local_edge_sides(r - inst * g.n_edges_inst, g, em, fm, ep, fp);
+    if (*em >= 0) *em += inst * g.n_el_inst;
+    if (*ep >= 0) *ep += inst * g.n_el_inst;
+}
+
+// Time-step factor of the instance that owns element e (1 without a batch table).
+__host__ __device__ inline double dt_factor(const Geom& g, int e) {
+    return g.dt_scale ? g.dt_scale[e / g.n_el_inst] : 1.0;
 }
 
 // The moving vortex of Sec. 7.1 (eq. tc_vortex_ic) at (x, y, t) as (phi_eta, U, V) over the
@@ -132,8 +160,9 @@ __host__ __device__ inline void vortex_state(const Geom& g, double x, double y, 
 // Physical coordinates of face node b of face f of element e.
 __host__ __device__ inline void face_node_xy(const Geom& g, int e, int f, int b, double* x, double* y) {
     const int n = face_node(f, b, g.P), i = n % g.P, j = n / g.P;
-    *x = g.x0 + (e % g.N + 0.5 * (1.0 + g.xi[i])) * g.h;
-    *y = g.x0 + (e / g.N + 0.5 * (1.0 + g.xi[j])) * g.h;
+    const int el = e % g.n_el_inst;
+    *x = g.x0 + (el % g.N + 0.5 * (1.0 + g.xi[i])) * g.h;
+    *y = g.x0 + (el / g.N + 0.5 * (1.0 + g.xi[j])) * g.h;
 }
 
 // Host-built periodic unit-square mesh and GLL tables of an N x N, degree-k mesh (no GPU call).

@@ -66,7 +66,7 @@ dg_face_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ 
         double x, y;
         face_node_xy(g, em >= 0 ? em : ep, em >= 0 ? fm : fp, b, &x, &y);
         double ph, U, V;
-        vortex_state(g, x, y, t_bc, &ph, &U, &V);
+        vortex_state(g, x, y, t_bc * dt_factor(g, em >= 0 ? em : ep), &ph, &U, &V);
         if (em < 0) { phm = ph; Um = U; Vm = V; pbm = pbp; }
         else { php = ph; Up = U; Vp = V; pbp = pbm; }
     } else {
@@ -175,9 +175,10 @@ dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict_
         rV -= sgn * Tc(fl[2 * P + b]);
     }
     const size_t o = (size_t)e * Np + n;
-    out[o] = scale * double(rph);
-    out[fs + o] = scale * double(rU);
-    out[2 * fs + o] = scale * double(rV);
+    const double sc = scale * dt_factor(g, e);   // this instance's time step
+    out[o] = sc * double(rph);
+    out[fs + o] = sc * double(rU);
+    out[2 * fs + o] = sc * double(rV);
 }
 
 __global__ void combine_kernel(size_t n, const double* __restrict__ base, CombineTerms t,

@@ -79,6 +79,7 @@ __global__ void build_local_kernel(Geom g, const double* __restrict__ phiB,
     __shared__ int s_piv;
     const int e = e0 + blockIdx.x;
     const int ld = 2 * NV;
+    dta *= dt_factor(g, e);   // this instance's time step
 
     for (int n = threadIdx.x; n < Np; n += blockDim.x) pb[n] = phiB[(size_t)e * Np + n];
     for (int t = threadIdx.x; t < 4 * P; t += blockDim.x)
@@ -304,7 +305,7 @@ __global__ void edge_rhs_kernel(Geom g, const double* __restrict__ Z, const doub
     if (g.dirichlet && (em < 0 || ep < 0)) {   // prescribed trace row: qhat = q_bc(t)
         double x, y, ph, U, V;
         face_node_xy(g, e_in, f_in, b, &x, &y);
-        vortex_state(g, x, y, t_bc, &ph, &U, &V);
+        vortex_state(g, x, y, t_bc * dt_factor(g, e_in), &ph, &U, &V);
         out[b] = ph;
         out[P + b] = U;
         out[2 * P + b] = V;
@@ -370,7 +371,7 @@ __global__ void recover_kernel(Geom g, const double* __restrict__ Ainv, const do
         }
     }
     const size_t o = (r / Np) * fs + (size_t)e * Np + r % Np;
-    const double q = Z[o] + beta * acc;
+    const double q = Z[o] + beta * dt_factor(g, e) * acc;
     Q[o] = q;
     Lst[o] = (q - R1[o]) * inv_aii;
 }

@@ -9,6 +9,12 @@ overlaps, and requests that arrive while others run join as soon as a slot and m
 up.  Each step's arithmetic is the same as when the simulation runs alone, so results do not
 depend on the mix (the reductions have a fixed order).
 
+Requests that share a mesh size, degree, step count and arithmetic can instead be grouped
+(``batch_requests``) and served as one batched handle each: one launch per kernel per stage
+then covers the whole group.  A batch's trace systems are solved together, so its Krylov
+iteration count is that of its hardest member and its results agree with the members' lone
+runs to the solver tolerance, not bit for bit.
+
 Reported: throughput in DOF-steps/s over the whole run, and the time to solution of each
 request (arrival to result copied back), summarised as p50 / p99.
 """
@@ -79,6 +85,76 @@ def initial_state(req):
     return h, hu, hv, b, dt
 
 
+@dataclass
+class Batch:
+    """Requests of one mesh size, degree, step count and arithmetic served as ONE batched handle:
+    every kernel then covers all of them in one launch per stage, each keeping its own bottom,
+    state and time step."""
+    rid: int
+    members: list
+    arrival: float
+    result: tuple = None
+    admitted: float = None
+    finished: float = None
+    bytes: int = 0
+    error: str = None
+
+    @property
+    def N(self):
+        return self.members[0].N
+
+    @property
+    def k(self):
+        return self.members[0].k
+
+    @property
+    def steps(self):
+        return self.members[0].steps
+
+    @property
+    def precision(self):
+        return self.members[0].precision
+
+
+def batch_requests(requests, max_batch=64):
+    """Group requests by (N, k, steps, precision) in arrival order, at most max_batch per group."""
+    groups = {}
+    for r in sorted(requests, key=lambda r: r.arrival):
+        groups.setdefault((r.N, r.k, r.steps, r.precision), []).append(r)
+    out = []
+    for members in groups.values():
+        for i in range(0, len(members), max_batch):
+            part = members[i:i + max_batch]
+            out.append(Batch(len(out), part, max(m.arrival for m in part)))
+    return sorted(out, key=lambda b: b.arrival)
+
+
+def bytes_of(req):
+    """Device bytes one request (or batch) needs, from the library's own plan."""
+    B = len(req.members) if isinstance(req, Batch) else 1
+    return hd.bytes_required(hd.make_config(req.N, req.k, 1.0, precision=req.precision, batch=B))
+
+
+def run_batch(batch, chunk=10):
+    """Run every member of a batch in one handle; sets each member's result."""
+    states = [initial_state(r) for r in batch.members]
+    cat = lambda j: np.concatenate([s[j] for s in states])  # noqa: E731
+    dts = np.array([s[4] for s in states])
+    n = batch.N * batch.N
+    with hd.Sim(batch.N, batch.k, float(dts.max()), bottom=cat(3), precision=batch.precision,
+                batch=len(states), dt_per_instance=dts) as s:
+        s.set_state(cat(0), cat(1), cat(2))
+        done = 0
+        while done < batch.steps:
+            m = min(chunk, batch.steps - done)
+            s.step(m)
+            done += m
+        out = s.get_state()
+    for i, r in enumerate(batch.members):
+        r.result = tuple(a[i * n:(i + 1) * n] for a in out)
+    return out
+
+
 def run_one(req, chunk=10):
     """Run one request to completion on a fresh handle; returns the final (h, hu, hv)."""
     h, hu, hv, b, dt = initial_state(req)
@@ -100,7 +176,8 @@ class Server:
     log: list = field(default_factory=list)
 
     def serve(self, requests, time_scale=1.0):
-        """Serve requests arriving at time_scale * arrival seconds; returns a summary dict."""
+        """Serve requests (or batches of them) arriving at time_scale * arrival seconds; returns a
+        summary dict over the individual requests."""
         pending = sorted(requests, key=lambda r: r.arrival)
         queue, running = [], {}
         used = 0
@@ -112,17 +189,22 @@ class Server:
 
         def worker(req):
             try:
-                req.result = run_one(req, self.chunk)
+                if isinstance(req, Batch):
+                    run_batch(req, self.chunk)
+                else:
+                    req.result = run_one(req, self.chunk)
             except Exception as ex:           # the request fails, the server carries on
                 req.error = str(ex)
             req.finished = now()
+            for m in getattr(req, "members", ()):
+                m.admitted, m.finished, m.error = req.admitted, req.finished, req.error
 
         finished = []
         while pending or queue or running:
             t = now()
             while pending and pending[0].arrival * time_scale <= t:
                 r = pending.pop(0)
-                r.bytes = hd.bytes_required(hd.make_config(r.N, r.k, 1.0, precision=r.precision))
+                r.bytes = bytes_of(r)
                 queue.append(r)
             with lock:
                 for rid in [rid for rid, (r, th) in running.items() if not th.is_alive()]:
@@ -147,6 +229,7 @@ class Server:
                              "hbm_used": used})
             time.sleep(0.002)
         wall = now()
+        finished = [m for r in finished for m in (r.members if isinstance(r, Batch) else [r])]
         ok = [r for r in finished if r.error is None]
         tts = sorted((r.finished - r.arrival * time_scale) for r in ok)
         dof_steps = sum(3 * r.N * r.N * (r.k + 1) ** 2 * r.steps for r in ok)

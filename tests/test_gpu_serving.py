@@ -40,3 +40,19 @@ def test_admission_respects_the_memory_budget():
     srv2 = serving.Server(hbm_budget=1000, max_slots=2)
     s2 = srv2.serve([too_big])
     assert s2["completed"] == 0 and s2["errors"] == ["exceeds the memory budget"]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-6)])
+def test_batched_units_match_lone_runs(precision, tol):
+    """Requests grouped into batched handles give each member its lone result (to the solver
+    tolerance: a batch's trace systems are solved together)."""
+    reqs = serving.ensemble_requests(n=10, sides=(8, 12), degrees=(2, 3), steps=12, precision=precision)
+    units = serving.batch_requests(reqs, max_batch=3)
+    assert any(len(u.members) > 1 for u in units)
+    budget = sum(serving.bytes_of(u) for u in units)
+    summary = serving.Server(hbm_budget=budget, max_slots=4, chunk=5).serve(units)
+    assert summary["completed"] == len(reqs) and not summary["errors"]
+    for r in reqs:
+        alone = serving.run_one(r, chunk=12)
+        for a, b in zip(r.result, alone):
+            assert np.linalg.norm(a - b) <= tol * np.linalg.norm(b)
