@@ -66,6 +66,17 @@ enum { HDGDG_ARS2 = 0, HDGDG_ARS3 = 1, HDGDG_RK2 = 2, HDGDG_RK3 = 3 };
  *              recovery, the stage combinations and mass sums stay in FP64.
  *              hdgdg_eval_nl always evaluates in FP64. */
 enum { HDGDG_FP64 = 0, HDGDG_MIXED = 1 };
+/* Arithmetic of the local condensation Z = A^{-1} R1 and recovery A^{-1} (tau qhat) (eq.
+ * linearizedHDGsystem_schur, recover_volume_unknowns); implicit schemes only.
+ * HDGDG_LOCAL_FP64: per-element FP64 A^{-1} (default).
+ * HDGDG_LOCAL_FP32: a per-element FP32 copy of A^{-1}, FP32 products and sums (CUDA cores).
+ * HDGDG_LOCAL_BF16: ONE operator shared by all elements -- a flat bottom (phi_B constant) and
+ *                   one time step for all instances, else create fails with EINVAL -- applied
+ *                   to all elements as one dense contraction on the tensor cores (tcgen05, BF16
+ *                   inputs, FP32 accumulation in tensor memory).
+ * Vectors stay FP64 in every case; the precision variants of the paper's workloads report
+ * their error against the FP64 form. */
+enum { HDGDG_LOCAL_FP64 = 0, HDGDG_LOCAL_FP32 = 1, HDGDG_LOCAL_BF16 = 2 };
 
 typedef struct {
     int n_side;          /* N >= 2: elements per side of the periodic unit square */
@@ -94,6 +105,7 @@ typedef struct {
                             trace systems are solved as one block-diagonal system.  Arrays of
                             create / set_state / get_state are then [batch][n_el][(k+1)^2]. */
     const double* dt_per_instance; /* host [batch] time steps (read at create); NULL = dt for all */
+    int local_precision; /* HDGDG_LOCAL_FP64 (0), HDGDG_LOCAL_FP32 or HDGDG_LOCAL_BF16 */
 } hdgdg_config;
 
 /* HDGDG_VORTEX: the exact-solution boundary conditions of the paper's moving-vortex test

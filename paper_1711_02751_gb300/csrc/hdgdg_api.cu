@@ -46,7 +46,9 @@ bool valid(const hdgdg_config* c) {
            (c->linear_only == 0 || c->linear_only == 1) &&
            c->boundary >= HDGDG_PERIODIC && c->boundary <= HDGDG_VORTEX && std::isfinite(c->x0) &&
            std::isfinite(c->length) && c->batch >= 0 && c->batch <= (1 << 20) &&
-           c->krylov_restart <= kMaxRestart;
+           c->krylov_restart <= kMaxRestart && c->local_precision >= HDGDG_LOCAL_FP64 &&
+           c->local_precision <= HDGDG_LOCAL_BF16 &&
+           (c->local_precision != HDGDG_LOCAL_BF16 || c->degree_k <= 4);   // tensor-core tiles: k <= 4
 }
 
 bool explicit_scheme(const hdgdg_config* c) { return c->scheme == HDGDG_RK2 || c->scheme == HDGDG_RK3; }
@@ -91,6 +93,8 @@ Plan make_plan(const hdgdg_config* c) {
     }
     b += (dot_scratch_doubles(p.m + 2) + mass_scratch_doubles() + 4 * (size_t)(p.m + 2) + 16) * d;
     b += 64 + sizeof(GmresCtl);                               // flags, GMRES control block
+    if (c->local_precision == HDGDG_LOCAL_FP32) b += n_el * (size_t)p.NV * p.NV * sizeof(float);
+    if (c->local_precision == HDGDG_LOCAL_BF16) b += tc_image_bytes((int)P);
     p.persistent = b;
     p.setup_temp = n_el * (size_t)p.NT * p.NT * d + n_edges * 7 * (size_t)p.NF * p.NF * d;
     if ((size_t)p.NV * 2 * p.NV * d > 200 * 1024)   // k >= 6: the local inverses' global workspace
@@ -245,6 +249,9 @@ struct hdgdg_sim {
     // device memory
     std::vector<void*> allocs;
     double *phiB = nullptr, *tau = nullptr, *Ainv = nullptr, *Stil = nullptr, *Minv = nullptr, *Srr = nullptr;
+    float* Ainv32 = nullptr;      // HDGDG_LOCAL_FP32
+    void* tc_image = nullptr;     // HDGDG_LOCAL_BF16: the shared operator's tensor-core tile
+    LocalOps ops;
     int* Scol = nullptr;
     double *q = nullptr, *q_new = nullptr, *R1 = nullptr, *Z = nullptr, *Qs = nullptr;
     double *NLs[kMaxStages] = {}, *Ls[kMaxStages] = {};
@@ -515,13 +522,13 @@ hdgdg_status stage_solve_dev(hdgdg_sim* sim, const double* R1, double* Q, double
     double rr;
     {
         TimedGroup tg(sim, HDGDG_KT_CONDENSE);
-        CU(launch_condense(sim->g, sim->Ainv, R1, sim->phiB, sim->tau, sim->Z, sim->gvec, sim->stream, t_stage));
+        CU(launch_condense(sim->g, sim->ops, R1, sim->phiB, sim->tau, sim->Z, sim->gvec, sim->stream, t_stage));
     }
     if (sim->cfg.precision == HDGDG_MIXED) TRY(gmres_solve<float>(sim, sim->gvec, sim->lam, its, &rr));
     else TRY(gmres_solve<double>(sim, sim->gvec, sim->lam, its, &rr));
     {
         TimedGroup tg(sim, HDGDG_KT_RECOVER);
-        CU(launch_recover(sim->g, sim->Ainv, sim->Z, R1, sim->tau, sim->lam, beta_of(sim), 1.0 / sim->a_ii,
+        CU(launch_recover(sim->g, sim->ops, sim->Z, R1, sim->tau, sim->lam, beta_of(sim), 1.0 / sim->a_ii,
                           Q, Lst, sim->stream));
     }
     return HDGDG_OK;
@@ -612,11 +619,12 @@ hdgdg_status one_step(hdgdg_sim* sim) {
         TimedGroup tg(sim, HDGDG_KT_COMBINE);
         CU(launch_combine(n3, sim->q, t, sim->q_new, sim->flags, st));
     }
-    unsigned flag = 0;
-    CU(cudaMemcpyAsync(&sim->hbuf[0], sim->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    unsigned flag[3] = {0, 0, 0};   // non-finite, (setup), tensor-core wait ran out
+    CU(cudaMemcpyAsync(&sim->hbuf[0], sim->flags, sizeof(flag), cudaMemcpyDeviceToHost, st));
     TRY(sync(sim));
-    std::memcpy(&flag, &sim->hbuf[0], sizeof(unsigned));
-    if (flag) return fail(sim, HDGDG_ENONFINITE, "step %lld produced a non-finite state", sim->stats.steps + 1);
+    std::memcpy(flag, &sim->hbuf[0], sizeof(flag));
+    if (flag[2]) return fail(sim, HDGDG_ECUDA, "a bounded wait of the tensor-core local kernel ran out (%u)", flag[2]);
+    if (flag[0]) return fail(sim, HDGDG_ENONFINITE, "step %lld produced a non-finite state", sim->stats.steps + 1);
     std::swap(sim->q, sim->q_new);
     sim->stats.steps += 1;
     sim->t += sim->cfg.dt;
@@ -728,6 +736,33 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
     int sing = 0;
     CU(cudaMemcpy(&sing, dsing, sizeof(int), cudaMemcpyDeviceToHost));
     if (sing) return fail(sim, HDGDG_EINVAL, "a local operator block is singular");
+    sim->ops.kind = 0;
+    sim->ops.Ainv = sim->Ainv;
+    if (c->local_precision == HDGDG_LOCAL_FP32) {
+        const size_t n = (size_t)g.n_el * p.NV * p.NV;
+        TRY(dalloc(sim, &sim->Ainv32, n));
+        CU(launch_to_f32(sim->Ainv, sim->Ainv32, n, sim->stream));
+        sim->ops.kind = 1;
+        sim->ops.Ainv32 = sim->Ainv32;
+    } else if (c->local_precision == HDGDG_LOCAL_BF16) {
+        // one operator for every element: phi_B constant and one time step
+        for (size_t k = 1; k < p.n; ++k)
+            if (phiB[k] != phiB[0])
+                return fail(sim, HDGDG_EINVAL, "BF16 tensor-core local contractions need a flat bottom");
+        if (c->dt_per_instance)
+            for (int i = 0; i < g.batch; ++i)
+                if (c->dt_per_instance[i] != c->dt)
+                    return fail(sim, HDGDG_EINVAL, "BF16 tensor-core local contractions need one time step");
+        uint8_t* img = nullptr;
+        TRY(dalloc(sim, &img, tc_image_bytes(P)));
+        sim->tc_image = img;
+        CU(launch_tc_image(g, sim->Ainv, img, sim->stream));
+        sim->ops.kind = 2;
+        sim->ops.image = img;
+        sim->ops.error = reinterpret_cast<int*>(sim->flags) + 2;
+    }
+    CU(cudaMemsetAsync(sim->flags, 0, 16, sim->stream));
+    CU(cudaStreamSynchronize(sim->stream));
     return HDGDG_OK;
 }
 
@@ -909,7 +944,7 @@ hdgdg_status hdgdg_condense_rhs(hdgdg_sim* sim, const double* R1, double* out) {
     if (sim && explicit_scheme(&sim->cfg)) return fail(sim, HDGDG_EINVAL, "explicit scheme: no implicit stage");
     if (!sim || !R1 || !out) return fail(sim, HDGDG_EINVAL, "NULL argument to condense_rhs");
     TRY(upload3(sim, sim->R1, R1, 3 * sim->plan.n));
-    CU(launch_condense(sim->g, sim->Ainv, sim->R1, sim->phiB, sim->tau, sim->Z, sim->gvec, sim->stream, sim->t));
+    CU(launch_condense(sim->g, sim->ops, sim->R1, sim->phiB, sim->tau, sim->Z, sim->gvec, sim->stream, sim->t));
     return download(sim, out, sim->gvec, sim->plan.nt);
 }
 

@@ -201,14 +201,31 @@ cudaError_t launch_assemble_trace(const Geom& g, const double* Se, double* S7, d
                                   double* Minv, double* Stil, int* Scol, int* singular,
                                   cudaStream_t s);
 
+// The local operators as the condensation and recovery kernels apply them.
+struct LocalOps {
+    int kind = 0;                   // 0: per-element FP64; 1: per-element FP32; 2: shared, tensor cores
+    const double* Ainv = nullptr;   // kind 0: [n_el][col s][row r] = (A^{-1})_{rs}
+    const float* Ainv32 = nullptr;  // kind 1: same layout in FP32
+    const void* image = nullptr;    // kind 2: the shared A^{-1} as a BF16 tensor-core operand tile
+    int* error = nullptr;           // kind 2: set when a bounded wait of the tensor-core kernel ran out
+};
 // Condensation: Z = A^{-1} R1 per element, then g = -C Z edge by edge (pointwise rows).
 // t: time of the prescribed boundary traces (Dirichlet boundaries only)
-cudaError_t launch_condense(const Geom& g, const double* Ainv, const double* R1, const double* phiB,
+cudaError_t launch_condense(const Geom& g, const LocalOps& ops, const double* R1, const double* phiB,
                             const double* tau_edge, double* Z, double* gvec, cudaStream_t s, double t = 0.0);
 // Recovery: Q = Z + beta A^{-1} (tau qhat) on boundary nodes; Lst = (Q - R1) / a_ii.
-cudaError_t launch_recover(const Geom& g, const double* Ainv, const double* Z, const double* R1,
+cudaError_t launch_recover(const Geom& g, const LocalOps& ops, const double* Z, const double* R1,
                            const double* tau_edge, const double* qhat, double beta, double inv_aii,
                            double* Q, double* Lst, cudaStream_t s);
+// Tensor-core tile of one shared operator: bytes of the BF16 image, and its build from the
+// FP64 A^{-1} of element 0 (setup).
+size_t tc_image_bytes(int P);
+cudaError_t launch_tc_image(const Geom& g, const double* Ainv, void* image, cudaStream_t s);
+// Z = A^{-1} R1 (mode 0) or Q = Z + beta A^{-1}(tau qhat), Lst = (Q - R1)/a_ii (mode 1) on the
+// tensor cores with the shared operator image.
+cudaError_t launch_local_tc(const Geom& g, int mode, const void* image, const double* R1,
+                            const double* Z, const double* tau_edge, const double* qhat, double beta,
+                            double inv_aii, double* out0, double* out1, int* error, cudaStream_t s);
 
 // Krylov set on trace vectors of n = n_edges * nf values.  Overloads on the storage type:
 // double for the FP64 path, float for the inner solves of the mixed-precision path.

@@ -266,25 +266,26 @@ __global__ void precondition_kernel(int n_edges, const double* __restrict__ S7,
     }
 }
 
-// Z = A^{-1} R1: one thread per (element, row); R1 staged in shared memory.
-template <int P>
-__global__ void apply_ainv_kernel(Geom g, const double* __restrict__ Ainv, const double* __restrict__ R1,
+// Z = A^{-1} R1: one thread per (element, row); R1 staged in shared memory.  T is the type of
+// the stored operator and of the products and sums (double, or float for the FP32 variant).
+template <int P, typename T>
+__global__ void apply_ainv_kernel(Geom g, const T* __restrict__ Ainv, const double* __restrict__ R1,
                                   double* __restrict__ Z) {
     constexpr int Np = P * P, NV = 3 * Np;
     constexpr int EPB = (256 / NV) > 0 ? 256 / NV : 1;
-    __shared__ double sx[EPB][NV];
+    __shared__ T sx[EPB][NV];
     const int le = threadIdx.x / NV, r = threadIdx.x % NV;
     const int e = blockIdx.x * EPB + le;
     const size_t fs = (size_t)g.n_el * Np;
     const bool live = e < g.n_el && le < EPB;
-    if (live) sx[le][r] = R1[(r / Np) * fs + (size_t)e * Np + r % Np];
+    if (live) sx[le][r] = (T)R1[(r / Np) * fs + (size_t)e * Np + r % Np];
     __syncthreads();
     if (!live) return;
-    const double* A = Ainv + (size_t)e * NV * NV;
-    double acc = 0.0;
+    const T* A = Ainv + (size_t)e * NV * NV;
+    T acc = 0;
 #pragma unroll 8
     for (int s = 0; s < NV; ++s) acc += A[s * NV + r] * sx[le][s];
-    Z[(r / Np) * fs + (size_t)e * Np + r % Np] = acc;
+    Z[(r / Np) * fs + (size_t)e * Np + r % Np] = (double)acc;
 }
 
 // g = -C Z at every trace node: one thread per (edge, b).
@@ -332,15 +333,15 @@ __global__ void edge_rhs_kernel(Geom g, const double* __restrict__ Z, const doub
     out[2 * P + b] = -acc[2];
 }
 
-// Q = Z + beta A^{-1}_{:, boundary} (tau qhat);  Lst = (Q - R1) * inv_aii.
-template <int P>
-__global__ void recover_kernel(Geom g, const double* __restrict__ Ainv, const double* __restrict__ Z,
+// Q = Z + beta A^{-1}_{:, boundary} (tau qhat);  Lst = (Q - R1) * inv_aii.  T as above.
+template <int P, typename T>
+__global__ void recover_kernel(Geom g, const T* __restrict__ Ainv, const double* __restrict__ Z,
                                const double* __restrict__ R1, const double* __restrict__ tau_edge,
                                const double* __restrict__ qhat, double beta, double inv_aii,
                                double* __restrict__ Q, double* __restrict__ Lst) {
     constexpr int Np = P * P, NV = 3 * Np, NF = 3 * P;
     constexpr int EPB = (256 / NV) > 0 ? 256 / NV : 1;
-    __shared__ double su[EPB][NV];
+    __shared__ T su[EPB][NV];
     const int le = threadIdx.x / NV, r = threadIdx.x % NV;
     const int e = blockIdx.x * EPB + le;
     const size_t fs = (size_t)g.n_el * Np;
@@ -356,12 +357,12 @@ __global__ void recover_kernel(Geom g, const double* __restrict__ Ainv, const do
             const int ed = edge_of_face(e, f, g);
             u += tau_edge[(size_t)ed * P + b] * qhat[(size_t)ed * NF + c * P + b];
         }
-        su[le][r] = u;
+        su[le][r] = (T)u;
     }
     __syncthreads();
     if (!live) return;
-    const double* A = Ainv + (size_t)e * NV * NV;
-    double acc = 0.0;
+    const T* A = Ainv + (size_t)e * NV * NV;
+    T acc = 0;
     for (int c = 0; c < 3; ++c) {
         for (int n = 0; n < Np; ++n) {
             const int i = n % P, j = n / P;
@@ -371,7 +372,7 @@ __global__ void recover_kernel(Geom g, const double* __restrict__ Ainv, const do
         }
     }
     const size_t o = (r / Np) * fs + (size_t)e * Np + r % Np;
-    const double q = Z[o] + beta * dt_factor(g, e) * acc;
+    const double q = Z[o] + beta * dt_factor(g, e) * (double)acc;
     Q[o] = q;
     Lst[o] = (q - R1[o]) * inv_aii;
 }
@@ -420,12 +421,22 @@ cudaError_t assemble_launch(const Geom& g, const double* Se, double* S7, double*
 }
 
 template <int P>
-cudaError_t condense_launch(const Geom& g, const double* Ainv, const double* R1, const double* phiB,
+cudaError_t condense_launch(const Geom& g, const LocalOps& ops, const double* R1, const double* phiB,
                             const double* tau_edge, double* Z, double* gvec, cudaStream_t s, double t) {
     constexpr int NV = 3 * P * P;
     constexpr int EPB = (256 / NV) > 0 ? 256 / NV : 1;
-    apply_ainv_kernel<P><<<(g.n_el + EPB - 1) / EPB, EPB * NV, 0, s>>>(g, Ainv, R1, Z);
-    count_launches(1);
+    const int blocks = (g.n_el + EPB - 1) / EPB;
+    if (ops.kind == 2) {
+        cudaError_t e = launch_local_tc(g, 0, ops.image, R1, nullptr, nullptr, nullptr, 0.0, 0.0, Z, nullptr,
+                                        ops.error, s);
+        if (e != cudaSuccess) return e;
+    } else if (ops.kind == 1) {
+        apply_ainv_kernel<P, float><<<blocks, EPB * NV, 0, s>>>(g, ops.Ainv32, R1, Z);
+        count_launches(1);
+    } else {
+        apply_ainv_kernel<P, double><<<blocks, EPB * NV, 0, s>>>(g, ops.Ainv, R1, Z);
+        count_launches(1);
+    }
     const int n = g.n_edges * P;
     edge_rhs_kernel<P><<<(n + 255) / 256, 256, 0, s>>>(g, Z, phiB, tau_edge, gvec, t);
     count_launches(1);
@@ -433,13 +444,20 @@ cudaError_t condense_launch(const Geom& g, const double* Ainv, const double* R1,
 }
 
 template <int P>
-cudaError_t recover_launch(const Geom& g, const double* Ainv, const double* Z, const double* R1,
+cudaError_t recover_launch(const Geom& g, const LocalOps& ops, const double* Z, const double* R1,
                            const double* tau_edge, const double* qhat, double beta, double inv_aii,
                            double* Q, double* Lst, cudaStream_t s) {
     constexpr int NV = 3 * P * P;
     constexpr int EPB = (256 / NV) > 0 ? 256 / NV : 1;
-    recover_kernel<P><<<(g.n_el + EPB - 1) / EPB, EPB * NV, 0, s>>>(g, Ainv, Z, R1, tau_edge, qhat,
-                                                                    beta, inv_aii, Q, Lst);
+    const int blocks = (g.n_el + EPB - 1) / EPB;
+    if (ops.kind == 2)
+        return launch_local_tc(g, 1, ops.image, R1, Z, tau_edge, qhat, beta, inv_aii, Q, Lst, ops.error, s);
+    if (ops.kind == 1)
+        recover_kernel<P, float><<<blocks, EPB * NV, 0, s>>>(g, ops.Ainv32, Z, R1, tau_edge, qhat, beta,
+                                                             inv_aii, Q, Lst);
+    else
+        recover_kernel<P, double><<<blocks, EPB * NV, 0, s>>>(g, ops.Ainv, Z, R1, tau_edge, qhat, beta,
+                                                              inv_aii, Q, Lst);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -481,9 +499,9 @@ cudaError_t launch_assemble_trace(const Geom& g, const double* Se, double* S7, d
 #undef CALL
 }
 
-cudaError_t launch_condense(const Geom& g, const double* Ainv, const double* R1, const double* phiB,
+cudaError_t launch_condense(const Geom& g, const LocalOps& ops, const double* R1, const double* phiB,
                             const double* tau_edge, double* Z, double* gvec, cudaStream_t s, double t) {
-#define CALL(P) condense_launch<P>(g, Ainv, R1, phiB, tau_edge, Z, gvec, s, t)
+#define CALL(P) condense_launch<P>(g, ops, R1, phiB, tau_edge, Z, gvec, s, t)
     switch (g.P) {
         case 2: return CALL(2);
         case 3: return CALL(3);
@@ -498,10 +516,10 @@ cudaError_t launch_condense(const Geom& g, const double* Ainv, const double* R1,
 #undef CALL
 }
 
-cudaError_t launch_recover(const Geom& g, const double* Ainv, const double* Z, const double* R1,
+cudaError_t launch_recover(const Geom& g, const LocalOps& ops, const double* Z, const double* R1,
                            const double* tau_edge, const double* qhat, double beta, double inv_aii,
                            double* Q, double* Lst, cudaStream_t s) {
-#define CALL(P) recover_launch<P>(g, Ainv, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s)
+#define CALL(P) recover_launch<P>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s)
     switch (g.P) {
         case 2: return CALL(2);
         case 3: return CALL(3);

@@ -1,0 +1,384 @@
+// Shared-operator local contractions on the 5th-generation tensor cores (tcgen05).
+//
+// With a flat bottom and one time step, every element has the same local operator A (eq.
+// linearizedHDGsystem: A = I - dt a_ii M^{-1} dL/dQ depends only on phi_B, tau and the
+// reference element), so the condensation Z = A^{-1} R1 and the recovery A^{-1}(tau qhat) of all
+// elements are ONE dense product
+//
+//     D [elements x NV] = X [elements x NV] * (A^{-1})^T,      NV = 3 (k+1)^2,
+//
+// with X the rows R1_e (condensation) or the boundary values tau qhat gathered per element
+// (recovery, zero at interior nodes).  One CTA of 128 threads takes 128 elements:
+//   * warp 0 allocates tensor memory for the 128 x NPAD FP32 accumulator;
+//   * thread 0 starts a bulk copy (TMA) of the operator tile (BF16, prepared once at setup in
+//     the tensor core's shared-memory layout) into shared memory;
+//   * all threads write X's 128 rows as BF16 into shared memory in the same layout;
+//   * thread 0 issues KP/16 tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulate, M = 128,
+//     N = NPAD) and commits them to an mbarrier;
+//   * every warp reads its 32 accumulator rows back with tcgen05.ld and writes the FP64 result
+//     (plus, in recovery, Q = Z + beta D and L_i = (Q - R1)/a_ii).
+// Every wait is bounded: when one runs out the kernel sets *error, skips the dependent work,
+// frees its tensor memory and returns.
+//
+// Shared-memory operand layout (no swizzle, K-major): the matrix is cut into core matrices of
+// 8 rows x 16 bytes (8 BF16 values along K) stored as 128 contiguous bytes; core matrices
+// adjacent along K are 128 bytes apart (leading byte offset) and 8-row groups are KP*16 bytes
+// apart (stride byte offset).  Rows beyond the valid elements and columns beyond NV are zero.
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace hdgdg {
+namespace {
+
+constexpr int kTileM = 128;          // elements per CTA = accumulator lanes
+constexpr int kThreads = 128;
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz: the bound on every wait
+
+__host__ __device__ constexpr int pad16(int n) { return (n + 15) / 16 * 16; }
+__host__ __device__ constexpr int tmem_cols(int n) { return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : 256; }
+
+template <int P>
+struct TcShape {
+    static constexpr int Np = P * P, NV = 3 * Np;
+    static constexpr int KP = pad16(NV);       // K padded to the BF16 MMA step (16)
+    static constexpr int NPAD = pad16(NV);     // N: a multiple of 16 for M = 128
+    static constexpr int COLS = tmem_cols(NPAD);
+    static constexpr int A_BYTES = kTileM * KP * 2;
+    static constexpr int B_BYTES = NPAD * KP * 2;
+    static constexpr int SBO = KP * 16;        // bytes between 8-row groups
+};
+
+// byte offset of (row, k) in the canonical K-major layout above
+__host__ __device__ inline int tile_offset(int row, int k, int sbo) {
+    return (row >> 3) * sbo + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait for phase `parity` of an mbarrier for at most kWaitCycles; false when the bound ran out.
+__device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+
+// Bulk (non-tensor) TMA copy global -> shared, completing on an mbarrier.  Both addresses
+// 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Make this thread's generic-proxy shared-memory writes visible to the tensor core (async proxy).
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// warp-wide: allocate `cols` tensor-memory columns, base address written to *holder
+__device__ __forceinline__ void tmem_alloc(uint32_t* holder, uint32_t cols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(holder)),
+                 "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t base, uint32_t cols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(cols) : "memory");
+}
+
+// Shared-memory matrix descriptor: start >> 4 (bits 0-13), leading byte offset >> 4 (16-29),
+// stride byte offset >> 4 (32-45), descriptor version 1 (46-47), base offset 0, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint32_t sbo) {
+    const uint64_t a = (smem_addr(p) >> 4) & 0x3FFF;
+    return a | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) | ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1),
+// both K-major (bits 15, 16 = 0), N >> 3 (bits 17-22), M >> 4 (bits 24-28).
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_addr(bar))
+                 : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's accumulator row (warp-collective).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void store_bf16(uint8_t* tile, int row, int k, int sbo, double v) {
+    *reinterpret_cast<__nv_bfloat16*>(tile + tile_offset(row, k, sbo)) = __double2bfloat16(v);
+}
+
+// Setup: the shared operator's tile from element 0's FP64 A^{-1} (column major).
+template <int P>
+__global__ void tc_image_kernel(const double* __restrict__ Ainv, uint8_t* __restrict__ image) {
+    using S = TcShape<P>;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= S::NPAD * S::KP) return;
+    const int r = t / S::KP, k = t % S::KP;   // B row = output index r, column = input index k
+    const double v = (r < S::NV && k < S::NV) ? Ainv[(size_t)k * S::NV + r] : 0.0;
+    *reinterpret_cast<__nv_bfloat16*>(image + tile_offset(r, k, S::SBO)) = __double2bfloat16(v);
+}
+
+template <int P, int MODE>
+__global__ void __launch_bounds__(kThreads) local_tc_kernel(
+    Geom g, const uint8_t* __restrict__ image, const double* __restrict__ R1, const double* __restrict__ Z,
+    const double* __restrict__ tau_edge, const double* __restrict__ qhat, double beta, double inv_aii,
+    double* __restrict__ out0, double* __restrict__ out1, int* __restrict__ error) {
+    using S = TcShape<P>;
+    constexpr int Np = S::Np, NV = S::NV, NF = 3 * P;
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint8_t* sA = smem;                  // 128 x KP BF16 rows of X
+    uint8_t* sB = smem + S::A_BYTES;     // NPAD x KP BF16 operator tile
+    __shared__ __align__(8) uint64_t bar_tma, bar_mma;
+    __shared__ uint32_t tmem_holder;
+    __shared__ int s_issued;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int e0 = blockIdx.x * kTileM;
+    const int cnt = min(kTileM, g.n_el - e0);
+    const size_t fs = (size_t)g.n_el * Np;
+
+    if (warp == 0) tmem_alloc(&tmem_holder, S::COLS);
+    if (tid == 0) {
+        mbar_init(&bar_tma, 1);
+        mbar_init(&bar_mma, 1);
+        mbar_init_fence();
+    }
+    for (int i = tid; i < S::A_BYTES / 16; i += kThreads) reinterpret_cast<uint4*>(sA)[i] = make_uint4(0, 0, 0, 0);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_holder;
+
+    if (tid == 0) {
+        mbar_expect_tx(&bar_tma, S::B_BYTES);
+        bulk_copy_g2s(sB, image, S::B_BYTES, &bar_tma);
+    }
+
+    // X rows (BF16).  Condensation: R1, read coalesced field by field.
+    if (MODE == 0) {
+        for (int c = 0; c < 3; ++c) {
+            const double* src = R1 + c * fs + (size_t)e0 * Np;
+            for (int i = tid; i < cnt * Np; i += kThreads) store_bf16(sA, i / Np, c * Np + i % Np, S::SBO, src[i]);
+        }
+    } else if (tid < cnt) {
+        // Recovery: tau qhat summed onto the boundary nodes of element e (corners get two faces).
+        const int e = e0 + tid;
+        double u[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) u[i] = 0.0;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const int ed = edge_of_face(e, f, g);
+#pragma unroll
+            for (int b = 0; b < P; ++b) {
+                const int n = face_node(f, b, P);
+                const double tau = tau_edge[(size_t)ed * P + b];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) u[c * Np + n] += tau * qhat[(size_t)ed * NF + c * P + b];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NV; ++i) store_bf16(sA, tid, i, S::SBO, u[i]);
+    }
+    fence_proxy_async();
+    __syncthreads();
+
+    if (tid == 0) {
+        tc_fence_after();
+        int issued = 0;
+        if (mbar_wait_bounded(&bar_tma, 0)) {
+            constexpr uint32_t idesc = idesc_bf16(kTileM, S::NPAD);
+#pragma unroll
+            for (int kc = 0; kc < S::KP / 16; ++kc) {
+                const uint64_t da = smem_desc(sA + kc * 256, 128, S::SBO);
+                const uint64_t db = smem_desc(sB + kc * 256, 128, S::SBO);
+                mma_bf16(tmem, da, db, idesc, kc > 0 ? 1u : 0u);
+            }
+            mma_commit(&bar_mma);
+            issued = 1;
+        } else {
+            atomicExch(error, 1);
+        }
+        s_issued = issued;
+    }
+    __syncthreads();
+    bool ok = s_issued != 0;
+    if (ok) ok = mbar_wait_bounded(&bar_mma, 0);
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok && tid == 0 && s_issued) atomicExch(error, 2);
+    tc_fence_after();
+
+    if (ok) {
+        const int e = e0 + tid;
+        const bool live = tid < cnt;
+        const double bet = live ? beta * dt_factor(g, e) : 0.0;
+#pragma unroll
+        for (int c0 = 0; c0 < S::NPAD; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (live) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = c0 + j;
+                    if (col >= NV) continue;
+                    const size_t o = (col / Np) * fs + (size_t)e * Np + col % Np;
+                    if (MODE == 0) {
+                        out0[o] = (double)v[j];
+                    } else {
+                        const double q = Z[o] + bet * (double)v[j];
+                        out0[o] = q;
+                        out1[o] = (q - R1[o]) * inv_aii;
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, S::COLS);
+    }
+}
+
+template <int P>
+size_t smem_bytes() {
+    using S = TcShape<P>;
+    // at most 512 / COLS CTAs per SM may hold tensor memory at once: ask for enough shared memory
+    // that no more than that many are resident
+    const int max_ctas = 512 / S::COLS;
+    const int need = S::A_BYTES + S::B_BYTES;
+    const int floor_bytes = 232448 / max_ctas - 2048;   // 227 KB usable per SM, 1 KB reserved per CTA
+    return (size_t)(need > floor_bytes ? need : floor_bytes);
+}
+
+template <int P>
+cudaError_t local_tc_launch(const Geom& g, int mode, const void* image, const double* R1, const double* Z,
+                            const double* tau_edge, const double* qhat, double beta, double inv_aii, double* out0,
+                            double* out1, int* error, cudaStream_t s) {
+    const size_t smem = smem_bytes<P>();
+    const int blocks = (g.n_el + kTileM - 1) / kTileM;
+    if (mode == 0) {
+        cudaError_t e = cudaFuncSetAttribute(local_tc_kernel<P, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        local_tc_kernel<P, 0><<<blocks, kThreads, smem, s>>>(g, static_cast<const uint8_t*>(image), R1, Z,
+                                                             tau_edge, qhat, beta, inv_aii, out0, out1, error);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(local_tc_kernel<P, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        local_tc_kernel<P, 1><<<blocks, kThreads, smem, s>>>(g, static_cast<const uint8_t*>(image), R1, Z,
+                                                             tau_edge, qhat, beta, inv_aii, out0, out1, error);
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t tc_image_bytes(int P) {
+    const int NV = 3 * P * P;
+    return (size_t)pad16(NV) * pad16(NV) * 2;
+}
+
+cudaError_t launch_tc_image(const Geom& g, const double* Ainv, void* image, cudaStream_t s) {
+#define CALL(P)                                                                                         \
+    do {                                                                                                \
+        const int n = TcShape<P>::NPAD * TcShape<P>::KP;                                              \
+        tc_image_kernel<P><<<(n + 255) / 256, 256, 0, s>>>(Ainv, static_cast<uint8_t*>(image));      \
+        count_launches(1);                                                                              \
+        return cudaGetLastError();                                                                      \
+    } while (0)
+    switch (g.P) {
+        case 2: CALL(2);
+        case 3: CALL(3);
+        case 4: CALL(4);
+        case 5: CALL(5);
+        default: return cudaErrorInvalidValue;
+    }
+#undef CALL
+}
+
+cudaError_t launch_local_tc(const Geom& g, int mode, const void* image, const double* R1, const double* Z,
+                            const double* tau_edge, const double* qhat, double beta, double inv_aii, double* out0,
+                            double* out1, int* error, cudaStream_t s) {
+#define CALL(P) return local_tc_launch<P>(g, mode, image, R1, Z, tau_edge, qhat, beta, inv_aii, out0, out1, error, s)
+    switch (g.P) {
+        case 2: CALL(2);
+        case 3: CALL(3);
+        case 4: CALL(4);
+        case 5: CALL(5);
+        default: return cudaErrorInvalidValue;
+    }
+#undef CALL
+}
+
+}  // namespace hdgdg

@@ -56,7 +56,7 @@ def test_batched_fp64_equals_alone(scheme):
     N, k, B, steps = 12, 3, 4, 10
     insts = _instances(N, k, B)
     if scheme == "rk2":                            # explicit: a stable step for every instance
-        insts = [x[:4] + (0.5 * x[4],) for x in insts]
+        insts = [x[:4] + (0.05 * x[4],) for x in insts]   # gravity Courant ~0.13
     res, _ = _run_batched(N, k, insts, steps, scheme=scheme)
     for inst, got in zip(insts, res):
         ref = _run_alone(N, k, inst, steps, scheme=scheme)
@@ -77,10 +77,10 @@ def test_batched_time_steps_really_differ():
 
 def test_batched_walls_equal_alone():
     N, k, B = 8, 3, 3
-    insts = _instances(N, k, B, boundary="walls")
-    res, _ = _run_batched(N, k, insts, 8, boundary="walls")
+    insts = _instances(N, k, B, boundary="wall")
+    res, _ = _run_batched(N, k, insts, 8, boundary="wall")
     for inst, got in zip(insts, res):
-        ref = _run_alone(N, k, inst, 8, boundary="walls")
+        ref = _run_alone(N, k, inst, 8, boundary="wall")
         for a, b in zip(got, ref):
             assert _rel(a, b) <= 1e-12 or np.abs(a - b).max() <= 1e-14
 
