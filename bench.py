@@ -59,6 +59,8 @@ def _args():
     ap.add_argument("--ensemble-slots", type=int, default=16)
     ap.add_argument("--vortex-table", action="store_true",
                     help="the paper's moving-vortex spatial convergence (Sec. 7.1) against its tables")
+    ap.add_argument("--precision-table", action="store_true",
+                    help="precision variants of the local contractions (FP32, BF16 tensor cores)")
     ap.add_argument("--paper-table", action="store_true",
                     help="time the paper's water-height perturbation runs (Sec. 7.2) and print their line")
     ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
@@ -457,6 +459,76 @@ def paper_table_line():
     print(json.dumps(line), flush=True)
 
 
+def precision_table_line(args):
+    """Precision variants (the 8x8 bump recipe, flat bottom, 200 ARS2 steps): FP64 form, mixed form
+    with FP64 / FP32 / BF16 (tensor-core) local contractions -- relative L2 of eta, hu, hv and the
+    energy-norm error against the FP64 form (itself within 1e-9 of the oracle); and the time of
+    the local contractions per implicit stage on a 512x512, k = 3 flat-bottom case (the large
+    recipe with b = 0) for each local arithmetic."""
+    import torch
+    from paper_1711_02751_gb300 import hdgdg as hd
+    from paper_1711_02751_gb300 import workloads as W
+    rows = []
+    x, y = hd.node_coords(8, 2)
+    h, hu, hv, b = W.bump8_state(x, y)
+    dt = W.advective_dt(x, h, hu, hv, 8)
+    wq = np.tile(np.outer(*(2 * [hd.gll(2)[1]])).ravel(), (64, 1))
+
+    def run(precision, local):
+        with hd.Sim(8, 2, dt, bottom=b, g=W.G, H0=W.H0, precision=precision, local_precision=local) as s:
+            s.set_state(h, hu, hv)
+            t0 = time.perf_counter()
+            s.step(200)
+            out = s.get_state()
+            return out, time.perf_counter() - t0
+
+    ref, t_ref = run("fp64", "fp64")
+    B = W.H0 - b
+    eref = (ref[0] - B, ref[1], ref[2])
+
+    def rel(a, r):
+        return float(np.sqrt(np.sum(wq * (a - r) ** 2) / np.sum(wq * r ** 2)))
+
+    rows.append({"form": "fp64", "local": "fp64", "wall_s_200_steps": t_ref})
+    for local in ("fp64", "fp32", "bf16"):
+        out, t = run("mixed", local)
+        e = (out[0] - B, out[1], out[2])
+        num = np.sum(wq * ((e[0] - eref[0]) ** 2 + ((e[1] - eref[1]) ** 2 + (e[2] - eref[2]) ** 2) / (W.G * B)))
+        den = np.sum(wq * (eref[0] ** 2 + (eref[1] ** 2 + eref[2] ** 2) / (W.G * B)))
+        rows.append({"form": "mixed", "local": local, "wall_s_200_steps": t,
+                     "rel_l2_vs_fp64": {"eta": rel(e[0], eref[0]), "hu": rel(e[1], eref[1]), "hv": rel(e[2], eref[2])},
+                     "energy_rel_vs_fp64": float(np.sqrt(num / den))})
+    # the local contractions' time on a large flat-bottom case
+    N, k = 512, 3
+    x, y = hd.node_coords(N, k)
+    h, hu, hv, b = W.large_state(x, y, seed=2000)
+    h = h + b
+    b = np.zeros_like(b)
+    dtl = W.advective_dt(x, h, hu, hv, N)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    timing = []
+    for local in ("fp64", "fp32", "bf16"):
+        with hd.Sim(N, k, dtl, bottom=b, g=W.G, H0=W.H0, precision="mixed", local_precision=local,
+                    stream=stream.cuda_stream) as s:
+            s.set_state(h, hu, hv)
+            s.step(3)
+            s.set_kernel_timing(True)
+            s.step(10)
+            kt = s.kernel_times()
+            st = s.stats()
+        n_stage = 20.0
+        timing.append({"local": local, "condense_ms_per_stage": kt["condense"][0] / n_stage,
+                       "recover_ms_per_stage": kt["recover"][0] / n_stage,
+                       "mass_after_13_steps": st["mass"]})
+    line = {"metric": "precision variants: error vs the FP64 form after 200 steps; local-contraction time",
+            "unit": "-", "n_gpus": 1, "dtype": "f64 / f32 / bf16 (tensor cores, f32 accumulation)",
+            "data": "synthetic",
+            "config": {"workload": "8x8 bump, k=2, flat bottom, ARS2, 200 steps; timing on 512x512, k=3, flat bottom"},
+            "runs": rows, "local_timing_512": timing}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     if args.cpu_baseline_child:
@@ -478,6 +550,9 @@ def main():
         return
     if args.vortex_table:
         vortex_table_line()
+        return
+    if args.precision_table:
+        precision_table_line(args)
         return
 
     import torch

@@ -1,0 +1,148 @@
+"""Precision variants of the local contractions -- condensation Z = A^{-1} R1 and recovery
+A^{-1}(tau qhat) (eq. linearizedHDGsystem_schur, recover_volume_unknowns):
+
+* local_precision='fp32': per-element FP32 copies of A^{-1}, FP32 products and sums;
+* local_precision='bf16': one operator shared by all elements (flat bottom), applied to all
+  elements as one product on the tensor cores with BF16 inputs and FP32 accumulation.
+
+The tensor-core product is checked sharply against a host emulation of the same arithmetic:
+the oracle's A^{-1} and the inputs rounded to BF16 (round to nearest even, 8 significant bits),
+exact products and sums (the device's FP32 accumulation adds ~1e-7 relative).  A wrong tile
+layout, a transposed operator or a misplaced row would be O(1) off; the BF16 rounding itself is
+~1e-3, so each test also checks that it really differs from the FP64 path by that much.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+hd = pytest.importorskip("paper_1711_02751_gb300.hdgdg")
+from paper_1711_02751_gb300 import workloads as W  # noqa: E402
+
+from _common import dt_of, flat, oracle_state, user_state  # noqa: E402
+from oracle import imex, swe  # noqa: E402
+
+rng = np.random.Generator(np.random.PCG64(77))
+
+
+def bf16(x):
+    """Round FP64 values to BF16 (8 significant bits, nearest even)."""
+    m, e = np.frexp(np.asarray(x, dtype=np.float64))
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+
+
+def _flat_case(N, k):
+    """The 8x8 bump recipe (flat bottom) on an N x N mesh, with a small seeded velocity."""
+    m = swe.Mesh(N, k)
+    x, y = m.x.reshape(m.n_el, -1), m.y.reshape(m.n_el, -1)
+    h, hu, hv, b = W.make_state("bump8", x, y)
+    hu = hu + 0.01 * np.sin(2 * np.pi * y)
+    hv = hv + 0.01 * np.cos(2 * np.pi * x)
+    return m, h, hu, hv, b
+
+
+def _elem(u):
+    """[3, e, ...] -> [e, 3 * ...]"""
+    return np.moveaxis(np.asarray(u), 1, 0).reshape(np.shape(u)[1], -1)
+
+
+@pytest.mark.parametrize("N,k", [(6, 3), (12, 2), (5, 1), (4, 4), (17, 3)])
+def test_tensor_core_condensation_matches_bf16_emulation(N, k):
+    m, h, hu, hv, b = _flat_case(N, k)
+    q, phiB = oracle_state(m, h, hu, hv, b)
+    dt = 0.4 / N
+    st = imex.Stepper(m, phiB, dt, solver="dense")
+    R1 = q + 0.01 * rng.standard_normal(q.shape)
+    Ainv, C = st.cond.Ainv, st.cond.C
+    Zb = np.einsum("evw,ew->ev", bf16(Ainv), bf16(_elem(R1)))          # emulated tensor-core product
+    loc = -np.einsum("etv,ev->et", C, Zb)
+    ref = np.bincount(st.cond.gi.ravel(), weights=loc.ravel(), minlength=st.cond.n)
+    ref = ref.reshape(m.n_edges, 3, m.P) / (m.face_jac * m.w)[None, None, :]
+    with hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, local_precision="bf16") as s:
+        got = s.condense_rhs(flat(R1))
+    with hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0) as s:
+        g64 = s.condense_rhs(flat(R1))
+    scale = np.abs(ref).max()
+    err = np.abs(got - ref).max()
+    assert err <= 2e-6 * scale
+    assert np.abs(g64 - ref).max() >= 20 * max(err, 1e-300)   # the BF16 rounding is really there
+
+
+@pytest.mark.parametrize("N,k", [(6, 3), (12, 2), (4, 4)])
+def test_tensor_core_recovery_matches_bf16_emulation(N, k):
+    """Q = Z + beta A^{-1}(tau qhat) from the library's own stage solve (its qhat), emulated on
+    the host from the oracle's A^{-1} and B (B qhat = -beta tau qhat on the boundary nodes,
+    beta = dt a_ii (2/h)/w_0)."""
+    m, h, hu, hv, b = _flat_case(N, k)
+    q, phiB = oracle_state(m, h, hu, hv, b)
+    dt = 0.4 / N
+    st = imex.Stepper(m, phiB, dt, solver="dense")
+    R1 = q + 0.01 * rng.standard_normal(q.shape)
+    with hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, local_precision="bf16") as s:
+        Q, lam, _ = s.stage_solve(flat(R1))
+    Ainv, B = st.cond.Ainv, st.cond.B
+    lam_loc = lam.ravel()[st.cond.gi]
+    v = -np.einsum("evt,et->ev", B, lam_loc)                          # = beta * tau qhat (gathered)
+    w0 = 2.0 / (k * (k + 1))
+    beta = dt * st.a_ii * (2.0 * N) / w0
+    Zb = np.einsum("evw,ew->ev", bf16(Ainv), bf16(_elem(R1)))
+    Qb = Zb + beta * np.einsum("evw,ew->ev", bf16(Ainv), bf16(v / beta))
+    Q64 = np.einsum("evw,ew->ev", Ainv, _elem(R1) + v)
+    got = _elem(Q)
+    scale = np.abs(Qb).max()
+    err = np.abs(got - Qb).max()
+    assert err <= 2e-6 * scale
+    assert np.abs(Q64 - Qb).max() >= 20 * max(err, 1e-300)
+
+
+@pytest.mark.parametrize("N,k", [(6, 3), (9, 2)])
+def test_fp32_local_operators_match_fp64_to_fp32_rounding(N, k):
+    m, h, hu, hv, b = user_state(N, k, "large")      # variable bottom: per-element operators
+    q, phiB = oracle_state(m, h, hu, hv, b)
+    dt = 0.4 / N
+    R1 = q + 0.01 * rng.standard_normal(q.shape)
+    with hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, local_precision="fp32") as s:
+        g32 = s.condense_rhs(flat(R1))
+        Q32, lam32, _ = s.stage_solve(flat(R1))
+    with hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0) as s:
+        g64 = s.condense_rhs(flat(R1))
+        Q64, lam64, _ = s.stage_solve(flat(R1))
+    d = np.abs(g32 - g64).max() / np.abs(g64).max()
+    assert 1e-10 < d <= 1e-5
+    assert np.abs(Q32 - Q64).max() <= 1e-5 * np.abs(Q64).max()
+
+
+def test_bf16_needs_a_shared_operator():
+    m, h, hu, hv, b = user_state(4, 2, "large")          # variable bottom
+    with pytest.raises(hd.HdgdgError):
+        hd.Sim(4, 2, 0.01, bottom=b, local_precision="bf16")
+    with pytest.raises(hd.HdgdgError):
+        hd.Sim(4, 5, 0.01, local_precision="bf16")        # tensor-core tiles cover k <= 4
+    with pytest.raises(hd.HdgdgError):
+        hd.Sim(4, 2, 0.01, batch=2, dt_per_instance=[0.01, 0.02], local_precision="bf16")
+
+
+def _energy_rel(m, qa, qo, phiB):
+    w = m.mass[None]
+    num = np.sum(w * ((qa[0] - qo[0]) ** 2 + ((qa[1] - qo[1]) ** 2 + (qa[2] - qo[2]) ** 2) / phiB))
+    den = np.sum(w * (qo[0] ** 2 + (qo[1] ** 2 + qo[2] ** 2) / phiB))
+    return float(np.sqrt(num / den))
+
+
+@pytest.mark.parametrize("local,bound", [("fp32", 1e-5), ("bf16", 5e-2)])
+def test_precision_variant_of_the_8x8_bump_200_steps(local, bound):
+    """The 8x8, k = 2 bump (flat bottom), 200 ARS2 steps in the mixed form with the local
+    contractions in FP32 or BF16 (tensor cores): error against the FP64 oracle in the energy
+    norm and in eta (hu, hv have decayed ~1e4 times below eta by then and are not gated)."""
+    m, h, hu, hv, b = user_state(8, 2, "bump8")
+    q, phiB = oracle_state(m, h, hu, hv, b)
+    dt = dt_of(m, h, hu, hv)
+    qo = imex.Stepper(m, phiB, dt, solver="lu").run(q, 200)
+    with hd.Sim(8, 2, dt, bottom=b, g=W.G, H0=W.H0, precision="mixed", local_precision=local) as s:
+        s.set_state(h, hu, hv)
+        s.step(200)
+        out = s.get_state()
+    qa, _ = swe.to_state(*out, b, W.G, W.H0)
+    e = _energy_rel(m, qa, qo, phiB)
+    r_eta = imex.rel_l2(m, qa[0], qo[0])
+    print(f"local {local}: energy-norm rel {e:.3e}, eta rel {r_eta:.3e}")
+    assert e <= bound and r_eta <= bound
