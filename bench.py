@@ -48,6 +48,8 @@ def _args():
                     help="refinement tolerance of the mixed form (0: library default 1e-9)")
     ap.add_argument("--precisions", default="fp64,mixed",
                     help="forms to time; the headline is mixed when within 1e-6 of fp64")
+    ap.add_argument("--local", default="fp64", choices=["fp64", "fp32"],
+                    help="arithmetic of the local condensation / recovery in the mixed form")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true",
@@ -582,7 +584,8 @@ def main():
     for precision in args.precisions.split(","):
         sim = hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, stream=stream.cuda_stream,
                      krylov_restart=args.restart, precision=precision,
-                     krylov_rtol=args.mixed_rtol if precision == "mixed" else 0.0)
+                     krylov_rtol=args.mixed_rtol if precision == "mixed" else 0.0,
+                     local_precision=args.local if precision == "mixed" else "fp64")
         sim.set_state(h, hu, hv)
         for _ in range(args.warmup):
             sim.step(1)
@@ -639,7 +642,8 @@ def main():
     line = {"metric": METRIC, "value": summary[head]["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": summary[head]["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if head == "fp64" else "f64+f32 (FP32 Krylov cycles, FP64 refinement and local ops)",
+            "dtype": "f64" if head == "fp64" else
+                     (f"f64+f32 (FP32 Krylov cycles and DG residual, FP64 refinement, {args.local.upper()} local ops)"),
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: periodic {N}x{N} quads, k={k}, ARS2, "
                                    f"dt={dt:.6g} (advective CFL 0.5: 0.5 h/((2k+1) 2max|u|))", "form": head,
