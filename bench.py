@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DOF-steps/s of IMEX HDG-DG at rel L2≤1e-6 vs FP64 form; p50/p99 latency"
 UNIT = "DOF-steps/s"
-WORKLOADS = {"large512": (512, 3), "bump8": (8, 2), "mid128": (128, 3)}
+WORKLOADS = {"large512": (512, 3), "bump8": (8, 2), "mid128": (128, 3), "flat512": (512, 3), "flat256": (256, 3)}
 CPU_SAMPLE = (64, 3)       # oracle sample: the large512 recipe on 64 x 64, k = 3
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -48,7 +48,7 @@ def _args():
                     help="refinement tolerance of the mixed form (0: library default 1e-9)")
     ap.add_argument("--precisions", default="fp64,mixed",
                     help="forms to time; the headline is mixed when within 1e-6 of fp64")
-    ap.add_argument("--local", default="fp64", choices=["fp64", "fp32"],
+    ap.add_argument("--local", default="fp64", choices=["fp64", "fp32", "bf16"],
                     help="arithmetic of the local condensation / recovery in the mixed form")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -74,7 +74,10 @@ def _workload_state(name, x, y, rank):
     from paper_1711_02751_gb300 import workloads as W
     if name == "bump8":
         return W.bump8_state(x, y)
-    return W.large_state(x, y, seed=2000 + rank)
+    h, hu, hv, b = W.large_state(x, y, seed=2000 + rank)
+    if name.startswith("flat"):          # the large recipe over a flat bottom: one shared local operator
+        h, b = h + b, np.zeros_like(b)
+    return h, hu, hv, b
 
 
 # ---- oracle timing (the CPU baseline and the reference arm) ----------------------------------
