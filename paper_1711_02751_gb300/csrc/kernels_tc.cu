@@ -15,8 +15,10 @@
 //   * all threads write X's 128 rows as BF16 into shared memory in the same layout;
 //   * thread 0 issues KP/16 tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulate, M = 128,
 //     N = NPAD) and commits them to an mbarrier;
-//   * every warp reads its 32 accumulator rows back with tcgen05.ld and writes the FP64 result
-//     (plus, in recovery, Q = Z + beta D and L_i = (Q - R1)/a_ii).
+//   * every warp reads its 32 accumulator rows back with tcgen05.ld into a shared-memory tile,
+//     and the CTA writes the FP64 result field plane by field plane with consecutive threads
+//     on consecutive addresses (in recovery also reading Z and R1 that way: Q = Z + beta D,
+//     L_i = (Q - R1)/a_ii).
 // Every wait is bounded: when one runs out the kernel sets *error, skips the dependent work,
 // frees its tensor memory and returns.
 //
@@ -48,6 +50,8 @@ struct TcShape {
     static constexpr int A_BYTES = kTileM * KP * 2;
     static constexpr int B_BYTES = NPAD * KP * 2;
     static constexpr int SBO = KP * 16;        // bytes between 8-row groups
+    static constexpr int DS = NV | 1;          // row stride (floats) of the staged result: odd, no bank conflicts
+    static constexpr int D_BYTES = kTileM * DS * 4;
 };
 
 // byte offset of (row, k) in the canonical K-major layout above
@@ -195,6 +199,7 @@ __global__ void __launch_bounds__(kThreads) local_tc_kernel(
     extern __shared__ __align__(128) uint8_t smem[];
     uint8_t* sA = smem;                  // 128 x KP BF16 rows of X
     uint8_t* sB = smem + S::A_BYTES;     // NPAD x KP BF16 operator tile
+    float* sD = reinterpret_cast<float*>(smem + S::A_BYTES + S::B_BYTES);   // 128 x DS FP32 result
     __shared__ __align__(8) uint64_t bar_tma, bar_mma;
     __shared__ uint32_t tmem_holder;
     __shared__ int s_issued;
@@ -276,26 +281,28 @@ __global__ void __launch_bounds__(kThreads) local_tc_kernel(
     tc_fence_after();
 
     if (ok) {
-        const int e = e0 + tid;
-        const bool live = tid < cnt;
-        const double bet = live ? beta * dt_factor(g, e) : 0.0;
 #pragma unroll
         for (int c0 = 0; c0 < S::NPAD; c0 += 16) {
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (live) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = c0 + j;
-                    if (col >= NV) continue;
-                    const size_t o = (col / Np) * fs + (size_t)e * Np + col % Np;
-                    if (MODE == 0) {
-                        out0[o] = (double)v[j];
-                    } else {
-                        const double q = Z[o] + bet * (double)v[j];
-                        out0[o] = q;
-                        out1[o] = (q - R1[o]) * inv_aii;
-                    }
+            for (int j = 0; j < 16; ++j)
+                if (c0 + j < NV) sD[tid * S::DS + c0 + j] = v[j];
+        }
+    }
+    __syncthreads();
+    if (ok) {
+        for (int c = 0; c < 3; ++c) {
+            const size_t base = c * fs + (size_t)e0 * Np;
+            for (int i = tid; i < cnt * Np; i += kThreads) {
+                const int m = i / Np, n = i % Np;
+                const double d = (double)sD[m * S::DS + c * Np + n];
+                if (MODE == 0) {
+                    out0[base + i] = d;
+                } else {
+                    const double q = Z[base + i] + beta * dt_factor(g, e0 + m) * d;
+                    out0[base + i] = q;
+                    out1[base + i] = (q - R1[base + i]) * inv_aii;
                 }
             }
         }
@@ -314,7 +321,7 @@ size_t smem_bytes() {
     // at most 512 / COLS CTAs per SM may hold tensor memory at once: ask for enough shared memory
     // that no more than that many are resident
     const int max_ctas = 512 / S::COLS;
-    const int need = S::A_BYTES + S::B_BYTES;
+    const int need = S::A_BYTES + S::B_BYTES + S::D_BYTES;
     const int floor_bytes = 232448 / max_ctas - 2048;   // 227 KB usable per SM, 1 KB reserved per CTA
     return (size_t)(need > floor_bytes ? need : floor_bytes);
 }
