@@ -50,6 +50,8 @@ def _args():
                     help="forms to time; the headline is mixed when within 1e-6 of fp64")
     ap.add_argument("--local", default="fp64", choices=["fp64", "fp32", "bf16"],
                     help="arithmetic of the local condensation / recovery in the mixed form")
+    ap.add_argument("--guess", type=int, default=0, choices=[0, 1, 2],
+                    help="trace-solve initial guess: 0 zero, 1 previous step, 2 linear extrapolation")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true",
@@ -588,7 +590,8 @@ def main():
         sim = hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, stream=stream.cuda_stream,
                      krylov_restart=args.restart, precision=precision,
                      krylov_rtol=args.mixed_rtol if precision == "mixed" else 0.0,
-                     local_precision=args.local if precision == "mixed" else "fp64")
+                     local_precision=args.local if precision == "mixed" else "fp64",
+                     krylov_guess=args.guess)
         sim.set_state(h, hu, hv)
         for _ in range(args.warmup):
             sim.step(1)

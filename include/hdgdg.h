@@ -106,6 +106,10 @@ typedef struct {
                             create / set_state / get_state are then [batch][n_el][(k+1)^2]. */
     const double* dt_per_instance; /* host [batch] time steps (read at create); NULL = dt for all */
     int local_precision; /* HDGDG_LOCAL_FP64 (0), HDGDG_LOCAL_FP32 or HDGDG_LOCAL_BF16 */
+    int krylov_guess;    /* start of each implicit stage's trace solve: 0 = zero; 1 = the previous
+                            step's solution of the same stage; 2 = linear extrapolation from the
+                            two previous steps (2 x_{n-1} - x_{n-2}).  The stop test stays
+                            ||g - S qhat|| <= rtol ||g||; a guess costs one FP64 residual. */
 } hdgdg_config;
 
 /* HDGDG_VORTEX: the exact-solution boundary conditions of the paper's moving-vortex test

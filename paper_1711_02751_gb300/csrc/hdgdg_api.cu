@@ -48,7 +48,8 @@ bool valid(const hdgdg_config* c) {
            std::isfinite(c->length) && c->batch >= 0 && c->batch <= (1 << 20) &&
            c->krylov_restart <= kMaxRestart && c->local_precision >= HDGDG_LOCAL_FP64 &&
            c->local_precision <= HDGDG_LOCAL_BF16 &&
-           (c->local_precision != HDGDG_LOCAL_BF16 || c->degree_k <= 4);   // tensor-core tiles: k <= 4
+           (c->local_precision != HDGDG_LOCAL_BF16 || c->degree_k <= 4) &&   // tensor-core tiles: k <= 4
+           c->krylov_guess >= 0 && c->krylov_guess <= 2;
 }
 
 bool explicit_scheme(const hdgdg_config* c) { return c->scheme == HDGDG_RK2 || c->scheme == HDGDG_RK3; }
@@ -95,6 +96,7 @@ Plan make_plan(const hdgdg_config* c) {
     b += 64 + sizeof(GmresCtl);                               // flags, GMRES control block
     if (c->local_precision == HDGDG_LOCAL_FP32) b += n_el * (size_t)p.NV * p.NV * sizeof(float);
     if (c->local_precision == HDGDG_LOCAL_BF16) b += tc_image_bytes((int)P);
+    if (c->krylov_guess > 0) b += 2 * (size_t)p.s * p.nt * d;   // previous stage solutions
     p.persistent = b;
     p.setup_temp = n_el * (size_t)p.NT * p.NT * d + n_edges * 7 * (size_t)p.NF * p.NF * d;
     if ((size_t)p.NV * 2 * p.NV * d > 200 * 1024)   // k >= 6: the local inverses' global workspace
@@ -249,6 +251,8 @@ struct hdgdg_sim {
     // device memory
     std::vector<void*> allocs;
     double *phiB = nullptr, *tau = nullptr, *Ainv = nullptr, *Stil = nullptr, *Minv = nullptr, *Srr = nullptr;
+    double* xhist[kMaxStages][2] = {};   // krylov_guess: preconditioned trace solutions of the
+    int n_hist[kMaxStages] = {};         // last two steps, per stage ([0] newest), and their count
     float* Ainv32 = nullptr;      // HDGDG_LOCAL_FP32
     void* tc_image = nullptr;     // HDGDG_LOCAL_BF16: the shared operator's tensor-core tile
     LocalOps ops;
@@ -387,7 +391,8 @@ hdgdg_status norm2_to_host(hdgdg_sim* sim, const double* v, double* out) {
 // and FP32 basis vectors; every cycle starts from the true residual r = g - S~ x~ computed in
 // FP64 and adds its correction to the FP64 x~ (iterative refinement).
 template <typename T>
-hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* iters, double* relres) {
+hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* iters, double* relres,
+                         int stage) {
     constexpr bool kMixed = sizeof(T) == sizeof(float);
     const size_t n = sim->plan.nt;
     const int m = sim->plan.m;
@@ -416,11 +421,29 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
         return HDGDG_OK;
     }
     const double bnorm = std::sqrt(bn2), tol = rtol * bnorm;
-    CU(cudaMemsetAsync(sim->xt, 0, n * sizeof(double), st));
-    CU(cudaMemcpyAsync(sim->w, g, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    CU(launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st));
-    CU(launch_gmres_solve_init(ctl, tol, inner_rel, maxit, st));
+    // initial guess: zero, or from the stage's solutions of the previous steps
+    const int guess = stage >= 0 ? std::min(sim->cfg.krylov_guess, sim->n_hist[stage]) : 0;
     double rnorm = bnorm;
+    if (guess == 0) {
+        CU(cudaMemsetAsync(sim->xt, 0, n * sizeof(double), st));
+        CU(cudaMemcpyAsync(sim->w, g, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CU(launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st));
+    } else {
+        CombineTerms t{};
+        if (guess == 2) { t.n = 2; t.X[0] = sim->xhist[stage][0]; t.c[0] = 1.0; t.X[1] = sim->xhist[stage][1]; t.c[1] = -1.0; }
+        CU(launch_combine(n, sim->xhist[stage][0], t, sim->xt, nullptr, st));
+        CU(launch_spmv_pre(sim->g, sim->Stil, sim->Scol, sim->xt, sim->w, st));
+        CombineTerms r{};
+        r.n = 1;
+        r.X[0] = sim->w;
+        r.c[0] = -1.0;
+        CU(launch_combine(n, g, r, sim->w, nullptr, st));
+        double r2;
+        TRY(norm2_to_host(sim, sim->w, &r2));   // leaves ||r0||^2 in the norm slot for the cycle
+        if (!std::isfinite(r2)) return fail(sim, HDGDG_ENONFINITE, "non-finite initial trace residual");
+        rnorm = std::sqrt(r2);
+    }
+    CU(launch_gmres_solve_init(ctl, tol, inner_rel, maxit, st));
     int total = 0;
     // One restart cycle: m Arnoldi steps (the ones after the cycle's stop return at once), the
     // correction, the FP64 true residual and its read-back.  Without kernel timing the cycle is
@@ -456,7 +479,7 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
         return e;
     };
     CycleGraph& cg = sim->cycle_graph[kMixed ? 1 : 0];
-    while (true) {
+    while (rnorm > tol) {
         if (sim->timing) {
             CU(enqueue_cycle());
         } else {
@@ -506,6 +529,11 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
         }
     }
     CU(launch_block_diag(sim->g, sim->Minv, sim->xt, qhat, st));
+    if (stage >= 0 && sim->cfg.krylov_guess > 0) {   // keep x~ for the next step's guess
+        std::swap(sim->xhist[stage][0], sim->xhist[stage][1]);
+        CU(cudaMemcpyAsync(sim->xhist[stage][0], sim->xt, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        sim->n_hist[stage] = std::min(sim->n_hist[stage] + 1, 2);
+    }
     *iters = total;
     *relres = rnorm / bnorm;
     sim->stats.last_krylov_iterations = total;
@@ -518,14 +546,14 @@ double beta_of(const hdgdg_sim* sim) { return sim->cfg.dt * sim->a_ii * sim->g.t
 
 // One implicit stage: R1 (device) -> Q, Lst = dt M^{-1} L (device); qhat left in sim->lam.
 hdgdg_status stage_solve_dev(hdgdg_sim* sim, const double* R1, double* Q, double* Lst, int* its,
-                             double t_stage = 0.0) {
+                             double t_stage = 0.0, int stage = -1) {
     double rr;
     {
         TimedGroup tg(sim, HDGDG_KT_CONDENSE);
         CU(launch_condense(sim->g, sim->ops, R1, sim->phiB, sim->tau, sim->Z, sim->gvec, sim->stream, t_stage));
     }
-    if (sim->cfg.precision == HDGDG_MIXED) TRY(gmres_solve<float>(sim, sim->gvec, sim->lam, its, &rr));
-    else TRY(gmres_solve<double>(sim, sim->gvec, sim->lam, its, &rr));
+    if (sim->cfg.precision == HDGDG_MIXED) TRY(gmres_solve<float>(sim, sim->gvec, sim->lam, its, &rr, stage));
+    else TRY(gmres_solve<double>(sim, sim->gvec, sim->lam, its, &rr, stage));
     {
         TimedGroup tg(sim, HDGDG_KT_RECOVER);
         CU(launch_recover(sim->g, sim->ops, sim->Z, R1, sim->tau, sim->lam, beta_of(sim), 1.0 / sim->a_ii,
@@ -598,7 +626,7 @@ hdgdg_status one_step(hdgdg_sim* sim) {
                 CU(launch_combine(n3, sim->q, t, sim->R1, nullptr, st));
             }
             int its = 0;
-            TRY(stage_solve_dev(sim, sim->R1, sim->Qs, sim->Ls[i], &its, ti));
+            TRY(stage_solve_dev(sim, sim->R1, sim->Qs, sim->Ls[i], &its, ti, i));
             Qi = sim->Qs;
         }
         if (!sim->cfg.linear_only) {
@@ -694,6 +722,9 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
         TRY(dalloc(sim, &sim->Ls[i], 3 * p.n));
     }
     for (double** v : {&sim->gvec, &sim->xt, &sim->lam, &sim->w, &sim->fface}) TRY(dalloc(sim, v, p.nt));
+    if (c->krylov_guess > 0)
+        for (int i = 0; i < p.s; ++i)
+            for (int h = 0; h < 2; ++h) TRY(dalloc(sim, &sim->xhist[i][h], p.nt));
     if (c->precision == HDGDG_MIXED) {
         TRY(dalloc(sim, &sim->Stil32, (size_t)g.n_edges * 6 * p.NF * p.NF));
         TRY(dalloc(sim, &sim->V32, (size_t)(p.m + 1) * p.nt));
@@ -891,6 +922,7 @@ hdgdg_status hdgdg_set_state(hdgdg_sim* sim, const double* h, const double* hu, 
     sim->have_state = true;
     sim->stats = hdgdg_stats{};
     sim->t = 0.0;
+    for (int i = 0; i < kMaxStages; ++i) sim->n_hist[i] = 0;   // a new trajectory: no guess history
     return HDGDG_OK;
 }
 

@@ -1,0 +1,54 @@
+"""Initial guesses of the trace solve (krylov_guess: the previous step's solution of the same
+stage, or the linear extrapolation of the last two): the stop test is unchanged, so a run
+matches the oracle as closely as one started from zero, in fewer Krylov iterations."""
+import pytest
+
+pytestmark = pytest.mark.gpu
+hd = pytest.importorskip("paper_1711_02751_gb300.hdgdg")
+from paper_1711_02751_gb300 import workloads as W  # noqa: E402
+
+from _common import dt_of, oracle_state, user_state  # noqa: E402
+from oracle import imex, swe  # noqa: E402
+
+
+def _run(N, k, kind, steps, guess, precision="fp64", scheme="ars2"):
+    m, h, hu, hv, b = user_state(N, k, kind)
+    dt = dt_of(m, h, hu, hv)
+    with hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, krylov_guess=guess, precision=precision, scheme=scheme) as s:
+        s.set_state(h, hu, hv)
+        s.step(steps)
+        out = s.get_state()
+        st = s.stats()
+    return m, h, hu, hv, b, dt, swe.to_state(*out, b, W.G, W.H0)[0], st
+
+
+@pytest.mark.parametrize("guess,scheme", [(1, "ars2"), (2, "ars2"), (2, "ars3")])
+def test_guess_matches_oracle(guess, scheme):
+    m, h, hu, hv, b, dt, qa, st = _run(12, 3, "large", 8, guess, scheme=scheme)
+    q, phiB = oracle_state(m, h, hu, hv, b)
+    qo = imex.Stepper(m, phiB, dt, scheme=scheme, solver="lu").run(q, 8)
+    assert max(imex.rel_l2(m, qa[c], qo[c]) for c in range(3)) <= 1e-10
+    _, _, _, _, _, _, _, st0 = _run(12, 3, "large", 8, 0, scheme=scheme)
+    assert st["krylov_iterations"] < st0["krylov_iterations"]
+
+
+def test_guess_restarts_with_set_state():
+    """set_state starts a new trajectory: the guess history is dropped, so a second run from the
+    same state repeats the first exactly."""
+    m, h, hu, hv, b = user_state(8, 2, "large")
+    dt = dt_of(m, h, hu, hv)
+    with hd.Sim(8, 2, dt, bottom=b, krylov_guess=2) as s:
+        s.set_state(h, hu, hv)
+        s.step(4)
+        a = s.get_state()
+        s.set_state(h, hu, hv)
+        s.step(4)
+        c = s.get_state()
+    for x, y in zip(a, c):
+        assert (x == y).all()
+
+
+def test_guess_mixed_within_1e6():
+    _, _, _, _, _, _, q1, st1 = _run(16, 3, "large", 20, 2, precision="mixed")
+    m, _, _, _, _, _, q0, _ = _run(16, 3, "large", 20, 0, precision="fp64")
+    assert max(imex.rel_l2(m, q1[c], q0[c]) for c in range(3)) <= 1e-6
