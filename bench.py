@@ -50,8 +50,8 @@ def _args():
                     help="forms to time; the headline is mixed when within 1e-6 of fp64")
     ap.add_argument("--local", default="fp64", choices=["fp64", "fp32", "bf16"],
                     help="arithmetic of the local condensation / recovery in the mixed form")
-    ap.add_argument("--guess", type=int, default=0, choices=[0, 1, 2],
-                    help="trace-solve initial guess: 0 zero, 1 previous step, 2 linear extrapolation")
+    ap.add_argument("--guess", type=int, default=0, choices=[-1, 0, 1, 2, 3],
+                    help="trace-solve initial guess: extrapolation order 1-3, -1 zero, 0 library default")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true",
@@ -654,7 +654,9 @@ def main():
             "config": {"workload": f"{args.workload}: periodic {N}x{N} quads, k={k}, ARS2, "
                                    f"dt={dt:.6g} (advective CFL 0.5: 0.5 h/((2k+1) 2max|u|))", "form": head,
                        "dof": dof, "parallelism": "replicas" if world > 1 else "single",
-                       "gmres_restart": args.restart or 20,
+                       "gmres_restart": args.restart or 10,
+                       "krylov_guess": {-1: "zero", 0: "linear extrapolation (default)", 1: "previous step",
+                                        2: "linear extrapolation", 3: "quadratic extrapolation"}[args.guess],
                        "l2": "inputs larger than L2 (A^-1 and trace matrix are GBs)"},
             "latency_ms": {"p50": p50, "p99": p99},
             "rel_l2_mixed_vs_fp64": err,

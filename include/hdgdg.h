@@ -90,7 +90,7 @@ typedef struct {
                             (FP64) or 1e-9 (MIXED, FP64 residual of the refinement loop).
                             A restart cycle that fails to halve a true residual already below
                             1e-12 ||g|| ends the solve as converged (FP64 rounding floor). */
-    int krylov_restart;  /* GMRES(m) restart length m <= 31; <= 0 selects 8 */
+    int krylov_restart;  /* GMRES(m) restart length m <= 31; <= 0 selects 10 */
     int krylov_maxit;    /* cap on GMRES iterations per stage solve; <= 0 selects 2000 */
     int linear_only;     /* 1: drop NL (linear gravity-wave runs); 0: full method */
     int boundary;        /* HDGDG_PERIODIC (0), HDGDG_WALLS (1): reflecting walls on the four
@@ -106,10 +106,13 @@ typedef struct {
                             create / set_state / get_state are then [batch][n_el][(k+1)^2]. */
     const double* dt_per_instance; /* host [batch] time steps (read at create); NULL = dt for all */
     int local_precision; /* HDGDG_LOCAL_FP64 (0), HDGDG_LOCAL_FP32 or HDGDG_LOCAL_BF16 */
-    int krylov_guess;    /* start of each implicit stage's trace solve: 0 = zero; 1 = the previous
-                            step's solution of the same stage; 2 = linear extrapolation from the
-                            two previous steps (2 x_{n-1} - x_{n-2}).  The stop test stays
-                            ||g - S qhat|| <= rtol ||g||; a guess costs one FP64 residual. */
+    int krylov_guess;    /* start of each implicit stage's trace solve: the polynomial extrapolation
+                            in time of the same stage's solutions of the previous steps --
+                            1 = previous step (x_{n-1}), 2 = linear (2 x_{n-1} - x_{n-2}),
+                            3 = quadratic (3 x_{n-1} - 3 x_{n-2} + x_{n-3}); -1 = start from zero;
+                            0 selects 2.  Fewer steps than the order since set_state lower it.
+                            The stop test stays ||g - S qhat|| <= rtol ||g||; a guess costs one
+                            FP64 residual. */
 } hdgdg_config;
 
 /* HDGDG_VORTEX: the exact-solution boundary conditions of the paper's moving-vortex test

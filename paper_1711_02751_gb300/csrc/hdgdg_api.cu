@@ -49,12 +49,15 @@ bool valid(const hdgdg_config* c) {
            c->krylov_restart <= kMaxRestart && c->local_precision >= HDGDG_LOCAL_FP64 &&
            c->local_precision <= HDGDG_LOCAL_BF16 &&
            (c->local_precision != HDGDG_LOCAL_BF16 || c->degree_k <= 4) &&   // tensor-core tiles: k <= 4
-           c->krylov_guess >= 0 && c->krylov_guess <= 2;
+           c->krylov_guess >= -1 && c->krylov_guess <= 3;
 }
 
 bool explicit_scheme(const hdgdg_config* c) { return c->scheme == HDGDG_RK2 || c->scheme == HDGDG_RK3; }
 
-int restart_of(const hdgdg_config* c) { return c->krylov_restart > 0 ? c->krylov_restart : 8; }
+int restart_of(const hdgdg_config* c) { return c->krylov_restart > 0 ? c->krylov_restart : 10; }
+
+// order of the trace-solve initial guess (0: start from zero)
+int guess_order(const hdgdg_config* c) { return c->krylov_guess < 0 ? 0 : c->krylov_guess == 0 ? 2 : c->krylov_guess; }
 
 Plan make_plan(const hdgdg_config* c) {
     Plan p;
@@ -96,7 +99,7 @@ Plan make_plan(const hdgdg_config* c) {
     b += 64 + sizeof(GmresCtl);                               // flags, GMRES control block
     if (c->local_precision == HDGDG_LOCAL_FP32) b += n_el * (size_t)p.NV * p.NV * sizeof(float);
     if (c->local_precision == HDGDG_LOCAL_BF16) b += tc_image_bytes((int)P);
-    if (c->krylov_guess > 0) b += 2 * (size_t)p.s * p.nt * d;   // previous stage solutions
+    b += (size_t)guess_order(c) * p.s * p.nt * d;             // previous stage solutions (guess)
     p.persistent = b;
     p.setup_temp = n_el * (size_t)p.NT * p.NT * d + n_edges * 7 * (size_t)p.NF * p.NF * d;
     if ((size_t)p.NV * 2 * p.NV * d > 200 * 1024)   // k >= 6: the local inverses' global workspace
@@ -251,8 +254,8 @@ struct hdgdg_sim {
     // device memory
     std::vector<void*> allocs;
     double *phiB = nullptr, *tau = nullptr, *Ainv = nullptr, *Stil = nullptr, *Minv = nullptr, *Srr = nullptr;
-    double* xhist[kMaxStages][2] = {};   // krylov_guess: preconditioned trace solutions of the
-    int n_hist[kMaxStages] = {};         // last two steps, per stage ([0] newest), and their count
+    double* xhist[kMaxStages][3] = {};   // trace-solve guess: preconditioned solutions of the last
+    int n_hist[kMaxStages] = {};         // steps, per stage ([0] newest), and their count
     float* Ainv32 = nullptr;      // HDGDG_LOCAL_FP32
     void* tc_image = nullptr;     // HDGDG_LOCAL_BF16: the shared operator's tensor-core tile
     LocalOps ops;
@@ -422,15 +425,20 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
     }
     const double bnorm = std::sqrt(bn2), tol = rtol * bnorm;
     // initial guess: zero, or from the stage's solutions of the previous steps
-    const int guess = stage >= 0 ? std::min(sim->cfg.krylov_guess, sim->n_hist[stage]) : 0;
+    const int guess = stage >= 0 ? std::min(guess_order(&sim->cfg), sim->n_hist[stage]) : 0;
     double rnorm = bnorm;
     if (guess == 0) {
         CU(cudaMemsetAsync(sim->xt, 0, n * sizeof(double), st));
         CU(cudaMemcpyAsync(sim->w, g, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
         CU(launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st));
     } else {
+        // x0 = sum_j c_j x_{n-j}: the extrapolation polynomial through the last `guess` solutions
+        static const double coef[4][3] = {{0, 0, 0}, {1, 0, 0}, {2, -1, 0}, {3, -3, 1}};
         CombineTerms t{};
-        if (guess == 2) { t.n = 2; t.X[0] = sim->xhist[stage][0]; t.c[0] = 1.0; t.X[1] = sim->xhist[stage][1]; t.c[1] = -1.0; }
+        for (int j = 0; j < guess; ++j) {
+            t.X[t.n] = sim->xhist[stage][j];
+            t.c[t.n++] = coef[guess][j] - (j == 0 ? 1.0 : 0.0);   // base x_{n-1} counted once
+        }
         CU(launch_combine(n, sim->xhist[stage][0], t, sim->xt, nullptr, st));
         CU(launch_spmv_pre(sim->g, sim->Stil, sim->Scol, sim->xt, sim->w, st));
         CombineTerms r{};
@@ -529,10 +537,13 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
         }
     }
     CU(launch_block_diag(sim->g, sim->Minv, sim->xt, qhat, st));
-    if (stage >= 0 && sim->cfg.krylov_guess > 0) {   // keep x~ for the next step's guess
-        std::swap(sim->xhist[stage][0], sim->xhist[stage][1]);
-        CU(cudaMemcpyAsync(sim->xhist[stage][0], sim->xt, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        sim->n_hist[stage] = std::min(sim->n_hist[stage] + 1, 2);
+    const int order = guess_order(&sim->cfg);
+    if (stage >= 0 && order > 0) {   // keep x~ for the next steps' guesses (oldest slot reused)
+        double* oldest = sim->xhist[stage][order - 1];
+        for (int j = order - 1; j > 0; --j) sim->xhist[stage][j] = sim->xhist[stage][j - 1];
+        sim->xhist[stage][0] = oldest;
+        CU(cudaMemcpyAsync(oldest, sim->xt, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        sim->n_hist[stage] = std::min(sim->n_hist[stage] + 1, order);
     }
     *iters = total;
     *relres = rnorm / bnorm;
@@ -722,9 +733,8 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
         TRY(dalloc(sim, &sim->Ls[i], 3 * p.n));
     }
     for (double** v : {&sim->gvec, &sim->xt, &sim->lam, &sim->w, &sim->fface}) TRY(dalloc(sim, v, p.nt));
-    if (c->krylov_guess > 0)
-        for (int i = 0; i < p.s; ++i)
-            for (int h = 0; h < 2; ++h) TRY(dalloc(sim, &sim->xhist[i][h], p.nt));
+    for (int i = 0; i < p.s; ++i)
+        for (int h = 0; h < guess_order(c); ++h) TRY(dalloc(sim, &sim->xhist[i][h], p.nt));
     if (c->precision == HDGDG_MIXED) {
         TRY(dalloc(sim, &sim->Stil32, (size_t)g.n_edges * 6 * p.NF * p.NF));
         TRY(dalloc(sim, &sim->V32, (size_t)(p.m + 1) * p.nt));

@@ -1,6 +1,7 @@
-"""Initial guesses of the trace solve (krylov_guess: the previous step's solution of the same
-stage, or the linear extrapolation of the last two): the stop test is unchanged, so a run
-matches the oracle as closely as one started from zero, in fewer Krylov iterations."""
+"""Initial guesses of the trace solve (krylov_guess: the same stage's solutions of the previous
+steps extrapolated in time -- constant, linear or quadratic -- or -1, zero): the stop test is
+unchanged, so a run matches the oracle as closely as one started from zero, in fewer Krylov
+iterations."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -22,13 +23,13 @@ def _run(N, k, kind, steps, guess, precision="fp64", scheme="ars2"):
     return m, h, hu, hv, b, dt, swe.to_state(*out, b, W.G, W.H0)[0], st
 
 
-@pytest.mark.parametrize("guess,scheme", [(1, "ars2"), (2, "ars2"), (2, "ars3")])
+@pytest.mark.parametrize("guess,scheme", [(1, "ars2"), (2, "ars2"), (3, "ars2"), (2, "ars3"), (0, "ars2")])
 def test_guess_matches_oracle(guess, scheme):
     m, h, hu, hv, b, dt, qa, st = _run(12, 3, "large", 8, guess, scheme=scheme)
     q, phiB = oracle_state(m, h, hu, hv, b)
     qo = imex.Stepper(m, phiB, dt, scheme=scheme, solver="lu").run(q, 8)
     assert max(imex.rel_l2(m, qa[c], qo[c]) for c in range(3)) <= 1e-10
-    _, _, _, _, _, _, _, st0 = _run(12, 3, "large", 8, 0, scheme=scheme)
+    _, _, _, _, _, _, _, st0 = _run(12, 3, "large", 8, -1, scheme=scheme)
     assert st["krylov_iterations"] < st0["krylov_iterations"]
 
 
@@ -50,5 +51,5 @@ def test_guess_restarts_with_set_state():
 
 def test_guess_mixed_within_1e6():
     _, _, _, _, _, _, q1, st1 = _run(16, 3, "large", 20, 2, precision="mixed")
-    m, _, _, _, _, _, q0, _ = _run(16, 3, "large", 20, 0, precision="fp64")
+    m, _, _, _, _, _, q0, _ = _run(16, 3, "large", 20, -1, precision="fp64")
     assert max(imex.rel_l2(m, q1[c], q0[c]) for c in range(3)) <= 1e-6
