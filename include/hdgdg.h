@@ -110,9 +110,10 @@ typedef struct {
                             in time of the same stage's solutions of the previous steps --
                             1 = previous step (x_{n-1}), 2 = linear (2 x_{n-1} - x_{n-2}),
                             3 = quadratic (3 x_{n-1} - 3 x_{n-2} + x_{n-3}); -1 = start from zero;
-                            0 selects 2.  Fewer steps than the order since set_state lower it.
-                            The stop test stays ||g - S qhat|| <= rtol ||g||; a guess costs one
-                            FP64 residual. */
+                            0 selects 3.  Fewer steps than the order since set_state lower it.
+                            The stop test stays ||g - S qhat|| <= rtol ||g||.  The guess's residual
+                            needs no matrix product: the same extrapolation of the stored
+                            products S x_{n-j} (g - r at the end of each solve) gives S x_0. */
 } hdgdg_config;
 
 /* HDGDG_VORTEX: the exact-solution boundary conditions of the paper's moving-vortex test

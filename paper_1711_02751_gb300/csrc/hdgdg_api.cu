@@ -57,7 +57,7 @@ bool explicit_scheme(const hdgdg_config* c) { return c->scheme == HDGDG_RK2 || c
 int restart_of(const hdgdg_config* c) { return c->krylov_restart > 0 ? c->krylov_restart : 10; }
 
 // order of the trace-solve initial guess (0: start from zero)
-int guess_order(const hdgdg_config* c) { return c->krylov_guess < 0 ? 0 : c->krylov_guess == 0 ? 2 : c->krylov_guess; }
+int guess_order(const hdgdg_config* c) { return c->krylov_guess < 0 ? 0 : c->krylov_guess == 0 ? 3 : c->krylov_guess; }
 
 Plan make_plan(const hdgdg_config* c) {
     Plan p;
@@ -99,7 +99,7 @@ Plan make_plan(const hdgdg_config* c) {
     b += 64 + sizeof(GmresCtl);                               // flags, GMRES control block
     if (c->local_precision == HDGDG_LOCAL_FP32) b += n_el * (size_t)p.NV * p.NV * sizeof(float);
     if (c->local_precision == HDGDG_LOCAL_BF16) b += tc_image_bytes((int)P);
-    b += (size_t)guess_order(c) * p.s * p.nt * d;             // previous stage solutions (guess)
+    b += 2 * (size_t)guess_order(c) * p.s * p.nt * d;         // previous stage solutions and products
     p.persistent = b;
     p.setup_temp = n_el * (size_t)p.NT * p.NT * d + n_edges * 7 * (size_t)p.NF * p.NF * d;
     if ((size_t)p.NV * 2 * p.NV * d > 200 * 1024)   // k >= 6: the local inverses' global workspace
@@ -255,7 +255,8 @@ struct hdgdg_sim {
     std::vector<void*> allocs;
     double *phiB = nullptr, *tau = nullptr, *Ainv = nullptr, *Stil = nullptr, *Minv = nullptr, *Srr = nullptr;
     double* xhist[kMaxStages][3] = {};   // trace-solve guess: preconditioned solutions of the last
-    int n_hist[kMaxStages] = {};         // steps, per stage ([0] newest), and their count
+    double* yhist[kMaxStages][3] = {};   // steps per stage ([0] newest), their products S~ x~ (from
+    int n_hist[kMaxStages] = {};         // the final true residual: g - r), and their count
     float* Ainv32 = nullptr;      // HDGDG_LOCAL_FP32
     void* tc_image = nullptr;     // HDGDG_LOCAL_BF16: the shared operator's tensor-core tile
     LocalOps ops;
@@ -440,11 +441,13 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
             t.c[t.n++] = coef[guess][j] - (j == 0 ? 1.0 : 0.0);   // base x_{n-1} counted once
         }
         CU(launch_combine(n, sim->xhist[stage][0], t, sim->xt, nullptr, st));
-        CU(launch_spmv_pre(sim->g, sim->Stil, sim->Scol, sim->xt, sim->w, st));
+        // r0 = g - S~ x0 = g - sum_j c_j (S~ x~_{n-j}): S~ is linear, and each S~ x~_{n-j} is
+        // known from the true residual that ended that step's solve -- no product needed
         CombineTerms r{};
-        r.n = 1;
-        r.X[0] = sim->w;
-        r.c[0] = -1.0;
+        for (int j = 0; j < guess; ++j) {
+            r.X[r.n] = sim->yhist[stage][j];
+            r.c[r.n++] = -coef[guess][j];
+        }
         CU(launch_combine(n, g, r, sim->w, nullptr, st));
         double r2;
         TRY(norm2_to_host(sim, sim->w, &r2));   // leaves ||r0||^2 in the norm slot for the cycle
@@ -538,11 +541,21 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
     }
     CU(launch_block_diag(sim->g, sim->Minv, sim->xt, qhat, st));
     const int order = guess_order(&sim->cfg);
-    if (stage >= 0 && order > 0) {   // keep x~ for the next steps' guesses (oldest slot reused)
-        double* oldest = sim->xhist[stage][order - 1];
-        for (int j = order - 1; j > 0; --j) sim->xhist[stage][j] = sim->xhist[stage][j - 1];
-        sim->xhist[stage][0] = oldest;
-        CU(cudaMemcpyAsync(oldest, sim->xt, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (stage >= 0 && order > 0) {   // keep x~ and S~ x~ = g - r for the next steps' guesses
+        double* ox = sim->xhist[stage][order - 1];
+        double* oy = sim->yhist[stage][order - 1];
+        for (int j = order - 1; j > 0; --j) {
+            sim->xhist[stage][j] = sim->xhist[stage][j - 1];
+            sim->yhist[stage][j] = sim->yhist[stage][j - 1];
+        }
+        sim->xhist[stage][0] = ox;
+        sim->yhist[stage][0] = oy;
+        CU(cudaMemcpyAsync(ox, sim->xt, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CombineTerms r{};   // sim->w holds the final true residual g - S~ x~
+        r.n = 1;
+        r.X[0] = sim->w;
+        r.c[0] = -1.0;
+        CU(launch_combine(n, g, r, oy, nullptr, st));
         sim->n_hist[stage] = std::min(sim->n_hist[stage] + 1, order);
     }
     *iters = total;
@@ -734,7 +747,10 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
     }
     for (double** v : {&sim->gvec, &sim->xt, &sim->lam, &sim->w, &sim->fface}) TRY(dalloc(sim, v, p.nt));
     for (int i = 0; i < p.s; ++i)
-        for (int h = 0; h < guess_order(c); ++h) TRY(dalloc(sim, &sim->xhist[i][h], p.nt));
+        for (int h = 0; h < guess_order(c); ++h) {
+            TRY(dalloc(sim, &sim->xhist[i][h], p.nt));
+            TRY(dalloc(sim, &sim->yhist[i][h], p.nt));
+        }
     if (c->precision == HDGDG_MIXED) {
         TRY(dalloc(sim, &sim->Stil32, (size_t)g.n_edges * 6 * p.NF * p.NF));
         TRY(dalloc(sim, &sim->V32, (size_t)(p.m + 1) * p.nt));
