@@ -235,10 +235,18 @@ Geom host_geom(int N, int k) {
 }
 }  // namespace hdgdg
 
+// Two events bracketing a launch group of kernel class cls; slot >= 0 tags the groups of
+// Arnoldi step `slot` of a GMRES cycle.
+struct TimerPair {
+    cudaEvent_t a, b;
+    int cls, slot;
+};
+
 struct CycleGraph {
     cudaGraphExec_t exec = nullptr;
     const double* g = nullptr;     // right-hand side the graph was captured for
     long long launches = 0;        // kernels per replay
+    std::vector<TimerPair> timers; // event-record nodes of a graph captured with kernel timing on
 };
 
 struct hdgdg_sim {
@@ -267,7 +275,8 @@ struct hdgdg_sim {
     float *Stil32 = nullptr, *V32 = nullptr, *w32 = nullptr;   // mixed precision only
     double *red = nullptr, *mred = nullptr, *dvals = nullptr;
     GmresCtl* ctl = nullptr;
-    CycleGraph cycle_graph[2];   // [FP64 form, mixed form]
+    CycleGraph cycle_graph[4];   // [FP64 form, mixed form] x [timers off, on]
+    std::vector<TimerPair>* capture_sink = nullptr;   // timers of the graph being captured
     unsigned* flags = nullptr;
     double* hbuf = nullptr;   // pinned host scratch
     // run state
@@ -277,8 +286,7 @@ struct hdgdg_sim {
     // per-kernel-class timers
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
-    struct Pending { cudaEvent_t a, b; int cls, slot; };
-    std::vector<Pending> pending;
+    std::vector<TimerPair> pending;
     double kt_ms[HDGDG_KT_COUNT] = {};
     long long kt_n[HDGDG_KT_COUNT] = {};
 };
@@ -355,7 +363,9 @@ struct TimedGroup {
         cudaEvent_t b = take_event(sim);
         if (!b) { sim->ev_pool.push_back(a); return; }
         cudaEventRecord(b, sim->stream);
-        sim->pending.push_back({a, b, cls, slot});
+        // groups recorded while a GMRES cycle is captured belong to that graph and are read
+        // after each of its replays
+        (sim->capture_sink ? sim->capture_sink : &sim->pending)->push_back({a, b, cls, slot});
     }
 };
 
@@ -370,6 +380,27 @@ void flush_timers(hdgdg_sim* sim, int slot_limit = 1 << 30) {
         sim->ev_pool.push_back(p.b);
     }
     sim->pending.clear();
+}
+
+// Add a replayed graph's timers (groups of Arnoldi steps at or after slot_limit returned at once).
+void read_graph_timers(hdgdg_sim* sim, const CycleGraph& cg, int slot_limit) {
+    for (const auto& p : cg.timers) {
+        float ms = 0.f;
+        if (p.slot < slot_limit && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            sim->kt_ms[p.cls] += ms;
+            sim->kt_n[p.cls] += 1;
+        }
+    }
+}
+
+void drop_graph(hdgdg_sim* sim, CycleGraph& cg) {
+    if (cg.exec) cudaGraphExecDestroy(cg.exec);
+    cg.exec = nullptr;
+    for (const auto& p : cg.timers) {
+        sim->ev_pool.push_back(p.a);
+        sim->ev_pool.push_back(p.b);
+    }
+    cg.timers.clear();
 }
 
 hdgdg_status sync(hdgdg_sim* sim, int slot_limit = 1 << 30) {
@@ -470,10 +501,9 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
             }
             TimedGroup tg(sim, HDGDG_KT_ORTHO, j);
             if (e == cudaSuccess) e = launch_multidot(V, n, j + 1, w, n, sim->red, dv_h1(sim), st, done);
-            if (e == cudaSuccess)
+            if (e == cudaSuccess)   // second pass, norm, Hessenberg column j and stop test
                 e = launch_cgs2_tail(V, n, j + 1, dv_h1(sim), w, n, sim->red, dv_h2(sim), dv_nrm(sim) + 2,
-                                     dv_nrm(sim) + 1, V + (size_t)(j + 1) * n, st, done);
-            if (e == cudaSuccess) e = launch_gmres_arnoldi(ctl, j, m, dv_h1(sim), dv_h2(sim), dv_nrm(sim) + 1, st);
+                                     dv_nrm(sim) + 1, V + (size_t)(j + 1) * n, ctl, j, m, st, done);
         }
         if (e == cudaSuccess) e = launch_gmres_update(V, n, ctl, sim->xt, n, st);
         if (e == cudaSuccess) e = launch_spmv_pre(sim->g, sim->Stil, sim->Scol, sim->xt, sim->w, st);
@@ -489,38 +519,42 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
             e = cudaMemcpyAsync(sim->hbuf + 1, &ctl->done, 5 * sizeof(int), cudaMemcpyDeviceToHost, st);
         return e;
     };
-    CycleGraph& cg = sim->cycle_graph[kMixed ? 1 : 0];
+    // one graph per form, captured with or without the kernel-class timers (event-record nodes)
+    CycleGraph& cg = sim->cycle_graph[(kMixed ? 1 : 0) + (sim->timing ? 2 : 0)];
     while (rnorm > tol) {
-        if (sim->timing) {
-            CU(enqueue_cycle());
-        } else {
-            if (cg.exec && cg.g != g) {
-                cudaGraphExecDestroy(cg.exec);
+        if (cg.exec && cg.g != g) drop_graph(sim, cg);
+        if (!cg.exec) {
+            const long long l0 = launches_total();
+            if (sim->timing) sim->capture_sink = &cg.timers;
+            CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            const cudaError_t e = enqueue_cycle();
+            cudaGraph_t graph = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+            sim->capture_sink = nullptr;
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                drop_graph(sim, cg);
+                return fail(sim, HDGDG_ECUDA, "capturing the GMRES cycle failed: %s",
+                            cudaGetErrorString(e != cudaSuccess ? e : e2));
+            }
+            const cudaError_t e3 = cudaGraphInstantiate(&cg.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e3 != cudaSuccess) {
                 cg.exec = nullptr;
+                drop_graph(sim, cg);
+                return fail(sim, HDGDG_ECUDA, "GMRES cycle graph: %s", cudaGetErrorString(e3));
             }
-            if (!cg.exec) {
-                const long long l0 = launches_total();
-                CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-                const cudaError_t e = enqueue_cycle();
-                cudaGraph_t graph = nullptr;
-                const cudaError_t e2 = cudaStreamEndCapture(st, &graph);
-                if (e != cudaSuccess || e2 != cudaSuccess)
-                    return fail(sim, HDGDG_ECUDA, "capturing the GMRES cycle failed: %s",
-                                cudaGetErrorString(e != cudaSuccess ? e : e2));
-                const cudaError_t e3 = cudaGraphInstantiate(&cg.exec, graph, 0);
-                cudaGraphDestroy(graph);
-                if (e3 != cudaSuccess) return fail(sim, HDGDG_ECUDA, "GMRES cycle graph: %s", cudaGetErrorString(e3));
-                cg.g = g;
-                cg.launches = launches_total() - l0;
-                count_launches((int)-cg.launches);   // counted again at every replay below
-            }
-            CU(cudaGraphLaunch(cg.exec, st));
-            count_launches((int)cg.launches);
+            cg.g = g;
+            cg.launches = launches_total() - l0;
+            count_launches((int)-cg.launches);   // counted again at every replay below
         }
+        CU(cudaGraphLaunch(cg.exec, st));
+        count_launches((int)cg.launches);
         CU(cudaStreamSynchronize(st));
         int cf[5];   // done, jend, total, maxit, status
         std::memcpy(cf, sim->hbuf + 1, sizeof(cf));
         flush_timers(sim, cf[1]);
+        if (sim->timing) read_graph_timers(sim, cg, cf[1]);
         total = cf[2];
         if (cf[4] != 0)
             return fail(sim, HDGDG_ENONFINITE, "non-finite GMRES residual estimate at iteration %d", total);
@@ -726,6 +760,7 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
         for (int i = 0; i < 3; ++i) TRY(dalloc(sim, &sim->NLs[i], 3 * p.n));
         TRY(dalloc(sim, &sim->fface, p.nt));
         TRY(dalloc(sim, &sim->red, dot_scratch_doubles(p.m + 2)));
+    CU(cudaMemset(sim->red, 0, sizeof(double)));   // the reductions' ticket counter starts at zero
         TRY(dalloc(sim, &sim->mred, mass_scratch_doubles()));
         TRY(dalloc(sim, &sim->dvals, 4 * (size_t)(p.m + 2) + 16));
         TRY(dalloc(sim, &sim->flags, 16));
@@ -759,6 +794,7 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
         TRY(dalloc(sim, &sim->V, (size_t)(p.m + 1) * p.nt));
     }
     TRY(dalloc(sim, &sim->red, dot_scratch_doubles(p.m + 2)));
+    CU(cudaMemset(sim->red, 0, sizeof(double)));   // the reductions' ticket counter starts at zero
     TRY(dalloc(sim, &sim->mred, mass_scratch_doubles()));
     TRY(dalloc(sim, &sim->dvals, 4 * (size_t)(p.m + 2) + 16));
     TRY(dalloc(sim, &sim->flags, 16));
@@ -874,9 +910,8 @@ void hdgdg_destroy(hdgdg_sim* sim) {
     if (!sim) return;
     if (sim->stream) cudaStreamSynchronize(sim->stream);
     flush_timers(sim);
+    for (auto& cg : sim->cycle_graph) drop_graph(sim, cg);
     for (cudaEvent_t e : sim->ev_pool) cudaEventDestroy(e);
-    for (auto& cg : sim->cycle_graph)
-        if (cg.exec) cudaGraphExecDestroy(cg.exec);
     for (void* p : sim->allocs) cudaFree(p);
     if (sim->hbuf) cudaFreeHost(sim->hbuf);
     if (sim->own_stream && sim->stream) cudaStreamDestroy(sim->stream);

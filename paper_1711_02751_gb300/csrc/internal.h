@@ -238,8 +238,22 @@ cudaError_t launch_spmv_pre(const Geom& g, const float* Stil, const int* Scol, c
 // y = B x for a block-diagonal matrix B given as [edge][col][row] blocks (FP64)
 cudaError_t launch_block_diag(const Geom& g, const double* Bd, const double* x, double* y,
                               cudaStream_t s);
-// out[j] = <V_j, w>, j < nv, V_j = V + j * ldv; uses partial-sum scratch of
-// dot_scratch_doubles(nv) doubles.  Deterministic (fixed grid, fixed order).
+// Device-resident control block of one GMRES(m) solve (m <= kM): Hessenberg matrix, Givens
+// rotations, residual estimates and the stop flags the loop kernels test.
+struct GmresCtl {
+    static constexpr int kM = 32;
+    double H[kM + 1][kM];
+    double cs[kM], sn[kM], s[kM + 1], y[kM];
+    double tol_abs;     // the solve stops when the residual estimate is <= tol_abs
+    double inner_rel;   // a cycle also stops at inner_rel * (its starting residual); 0 = off
+    double tol_cycle;
+    double rnorm;       // residual norm at the start of the current cycle
+    int done, jend, total, maxit, status;
+};
+
+// out[j] = <V_j, w>, j < nv, V_j = V + j * ldv; uses a scratch of dot_scratch_doubles(nv)
+// doubles (a ticket counter, zero between calls, then the block partial sums) that every call
+// on one stream may share.  Deterministic (fixed grid, fixed order).
 size_t dot_scratch_doubles(int nv);
 cudaError_t launch_multidot(const double* V, size_t ldv, int nv, const double* w, size_t n,
                             double* scratch, double* out, cudaStream_t s, const int* done = nullptr);
@@ -254,30 +268,20 @@ cudaError_t launch_axpy_f32_into_f64(const float* V, size_t ldv, int nv, const d
 // Fused tail of classical Gram-Schmidt applied twice, given h1 = V^T w on the device:
 // w1 = w - V h1 (in place), h2 = V^T w1, ||w1||^2 -> *nw1, hn = sqrt(||w1||^2 - ||h2||^2),
 // vout = (w1 - V h2) / hn.  nv <= cgs2_max_vectors(); scratch of dot_scratch_doubles(nv + 1).
+// With a GMRES control block, column j of the Hessenberg matrix, its Givens rotation and the
+// cycle's stop test are done in the same launch (restart length m).
 int cgs2_max_vectors();
 cudaError_t launch_cgs2_tail(const double* V, size_t ldv, int nv, const double* h1, double* w, size_t n,
                              double* scratch, double* h2, double* nw1, double* hn, double* vout,
-                             cudaStream_t s, const int* done = nullptr);
+                             GmresCtl* ctl, int j, int m, cudaStream_t s, const int* done = nullptr);
 cudaError_t launch_cgs2_tail(const float* V, size_t ldv, int nv, const double* h1, float* w, size_t n,
                              double* scratch, double* h2, double* nw1, double* hn, float* vout,
-                             cudaStream_t s, const int* done = nullptr);
+                             GmresCtl* ctl, int j, int m, cudaStream_t s, const int* done = nullptr);
 
-// Device-resident control block of one GMRES(m) solve (m <= kM): Hessenberg matrix, Givens
-// rotations, residual estimates and the stop flags the loop kernels test.
-struct GmresCtl {
-    static constexpr int kM = 32;
-    double H[kM + 1][kM];
-    double cs[kM], sn[kM], s[kM + 1], y[kM];
-    double tol_abs;     // the solve stops when the residual estimate is <= tol_abs
-    double inner_rel;   // a cycle also stops at inner_rel * (its starting residual); 0 = off
-    double tol_cycle;
-    double rnorm;       // residual norm at the start of the current cycle
-    int done, jend, total, maxit, status;
-};
+
 cudaError_t launch_gmres_solve_init(GmresCtl* c, double tol_abs, double inner_rel, int maxit, cudaStream_t s);
 cudaError_t launch_gmres_cycle_init(GmresCtl* c, const double* nrm2, cudaStream_t s);
-cudaError_t launch_gmres_arnoldi(GmresCtl* c, int j, int m, const double* h1, const double* h2,
-                                 const double* hn, cudaStream_t s);
+
 // y = H^{-1} s, then x += V y (FP64 x; V of either type)
 cudaError_t launch_gmres_update(const double* V, size_t ldv, GmresCtl* c, double* x, size_t n, cudaStream_t s);
 cudaError_t launch_gmres_update(const float* V, size_t ldv, GmresCtl* c, double* x, size_t n, cudaStream_t s);

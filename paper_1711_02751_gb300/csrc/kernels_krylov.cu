@@ -64,12 +64,42 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// partial[blk][j0 + c] = this block's slice of V_{j0+c} . w, c < nj
+// Grid reductions finish in the block that arrives last: every block writes its partial sums,
+// takes a ticket, and the block holding the last ticket sums the partials in block order -- the
+// same order whichever block arrives last, so results are reproducible bit for bit.  The ticket
+// counter is the first word of the scratch buffer (partials follow) and is reset by that block.
+__device__ bool last_block_arrives(unsigned* counter) {
+    __shared__ unsigned s_ticket;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_ticket = atomicAdd(counter, 1u);
+    __syncthreads();
+    return s_ticket == gridDim.x - 1;
+}
+
+// out[c] = sum over blocks of partial[blk * ldp + c0 + c], c < nc: one warp per column, fixed order
+__device__ void reduce_partials(const double* partial, int nblk, int ldp, int c0, int nc, double* out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = wid; c < nc; c += nw) {
+        double s = 0.0;
+        for (int k = lane; k < nblk; k += 32) s += __ldcg(partial + (size_t)k * ldp + c0 + c);
+        s = warp_sum(s);
+        if (lane == 0) out[c] = s;
+    }
+}
+
+__device__ void gmres_arnoldi_update(GmresCtl* c, int j, int m, const double* h1, const double* h2,
+                                     const double* hn);
+
+// out[j0 + c] = V_{j0+c} . w, c < nj: block partials in scratch, summed by the last block
 template <int CH, typename T>
 __global__ void __launch_bounds__(kDotThreads)
-multidot_partial_kernel(const T* __restrict__ V, size_t ldv, int j0, int nj, const T* __restrict__ w,
-                        size_t n, double* __restrict__ partial, int ldp, const int* __restrict__ done) {
+multidot_kernel(const T* __restrict__ V, size_t ldv, int j0, int nj, const T* __restrict__ w,
+                size_t n, double* __restrict__ scratch, int ldp, double* __restrict__ out,
+                const int* __restrict__ done) {
     if (done && *done) return;
+    unsigned* counter = reinterpret_cast<unsigned*>(scratch);
+    double* partial = scratch + 1;
     __shared__ double sh[CH][kDotThreads / 32];
     T acc[CH];
 #pragma unroll
@@ -93,19 +123,10 @@ multidot_partial_kernel(const T* __restrict__ V, size_t ldv, int j0, int nj, con
         for (int k = 0; k < kDotThreads / 32; ++k) s += sh[threadIdx.x][k];
         partial[(size_t)blockIdx.x * ldp + j0 + threadIdx.x] = s;
     }
-}
-
-// out[j] = sum_blk partial[blk][j]: one warp per j, fixed order
-__global__ void multidot_final_kernel(const double* __restrict__ partial, int nblk, int ldp, int nj,
-                                      double* __restrict__ out, const int* __restrict__ done) {
-    if (done && *done) return;
-    const int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    const int lane = threadIdx.x & 31;
-    if (j >= nj) return;
-    double s = 0.0;
-    for (int k = lane; k < nblk; k += 32) s += partial[(size_t)k * ldp + j];
-    s = warp_sum(s);
-    if (lane == 0) out[j] = s;
+    if (last_block_arrives(counter)) {
+        reduce_partials(partial, gridDim.x, ldp, j0, nj, out + j0);
+        if (threadIdx.x == 0) *counter = 0u;
+    }
 }
 
 // w -= sign * sum_j coef_j V_j
@@ -148,12 +169,19 @@ __global__ void to_f32_kernel(const double* __restrict__ a, float* __restrict__ 
 }
 
 // Second Gram-Schmidt pass fused with the update of the first: w1 = w - sum_j h1_j V_j (w
-// overwritten), and partial sums of V_j . w1 (j < NJ) and w1 . w1, the V_j kept in registers.
+// overwritten), and V_j . w1 (j < NJ) -> h2 and w1 . w1 -> nw1, the V_j kept in registers.  The
+// last block also forms hn = sqrt(||w1||^2 - ||h2||^2), the norm of w2 = w1 - V h2 for an
+// orthonormal V, and, given a GMRES control block, the Hessenberg column j with its Givens
+// rotation and stop test.
 template <int NJ, typename T>
 __global__ void __launch_bounds__(kDotThreads)
 axpy_dot_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict__ h1, T* __restrict__ w,
-                size_t n, double* __restrict__ partial, int ldp, const int* __restrict__ done) {
+                size_t n, double* __restrict__ scratch, double* __restrict__ h2, double* __restrict__ nw1,
+                double* __restrict__ hn, GmresCtl* ctl, int jcol, int m, const int* __restrict__ done) {
     if (done && *done) return;
+    constexpr int ldp = NJ + 1;
+    unsigned* counter = reinterpret_cast<unsigned*>(scratch);
+    double* partial = scratch + 1;
     __shared__ double sh[NJ + 1][kDotThreads / 32];
     T hc[NJ], acc[NJ + 1];
 #pragma unroll
@@ -185,15 +213,18 @@ axpy_dot_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict__ 
         for (int k = 0; k < kDotThreads / 32; ++k) s += sh[threadIdx.x][k];
         partial[(size_t)blockIdx.x * ldp + threadIdx.x] = s;
     }
-}
-
-// hn = sqrt(||w1||^2 - ||h2||^2), the norm of w2 = w1 - V h2 for an orthonormal V (one thread).
-__global__ void finish_norm_kernel(const double* __restrict__ h2, int nj, const double* __restrict__ nw1,
-                                   double* __restrict__ hn, const int* __restrict__ done) {
-    if (done && *done) return;
-    double s = *nw1;
-    for (int j = 0; j < nj; ++j) s -= h2[j] * h2[j];
-    *hn = s > 0.0 ? sqrt(s) : 0.0;
+    if (last_block_arrives(counter)) {
+        reduce_partials(partial, gridDim.x, ldp, 0, NJ, h2);
+        reduce_partials(partial, gridDim.x, ldp, NJ, 1, nw1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s2 = *nw1;
+            for (int j = 0; j < NJ; ++j) s2 -= h2[j] * h2[j];
+            *hn = s2 > 0.0 ? sqrt(s2) : 0.0;
+            if (ctl) gmres_arnoldi_update(ctl, jcol, m, h1, h2, hn);
+            *counter = 0u;
+        }
+    }
 }
 
 // V_{j+1} = (w1 - sum_j h2_j V_j) / hn
@@ -237,9 +268,9 @@ __global__ void gmres_cycle_init_kernel(GmresCtl* c, const double* nrm2) {
 }
 
 // Column j of the Hessenberg matrix from the two Gram-Schmidt passes, Givens rotations, the
-// residual estimate |s_{j+1}| and the cycle's stop test.
-__global__ void gmres_arnoldi_kernel(GmresCtl* c, int j, int m, const double* __restrict__ h1,
-                                     const double* __restrict__ h2, const double* __restrict__ hn) {
+// residual estimate |s_{j+1}| and the cycle's stop test (one thread).
+__device__ void gmres_arnoldi_update(GmresCtl* c, int j, int m, const double* h1, const double* h2,
+                                     const double* hn) {
     if (c->done) return;
     for (int i = 0; i <= j; ++i) c->H[i][j] = h1[i] + h2[i];
     c->H[j + 1][j] = *hn;
@@ -311,15 +342,10 @@ cudaError_t block_diag_launch(int n_edges, const double* Bd, const double* x, do
 
 template <int NJ, typename T>
 cudaError_t cgs2_tail_launch(const T* V, size_t ldv, const double* h1, T* w, size_t n, double* scratch,
-                             double* h2, double* nw1, double* hn, T* vout, cudaStream_t s, const int* done) {
-    axpy_dot_kernel<NJ, T><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, h1, w, n, scratch, NJ + 1, done);
-    count_launches(1);
-    // scratch holds [blk][NJ + 1]: the first NJ columns reduce to h2, the last to ||w1||^2
-    multidot_final_kernel<<<(NJ + 1 + 7) / 8, 256, 0, s>>>(scratch, kDotBlocks, NJ + 1, NJ, h2, done);
-    count_launches(1);
-    multidot_final_kernel<<<1, 32, 0, s>>>(scratch + NJ, kDotBlocks, NJ + 1, 1, nw1, done);
-    count_launches(1);
-    finish_norm_kernel<<<1, 1, 0, s>>>(h2, NJ, nw1, hn, done);
+                             double* h2, double* nw1, double* hn, T* vout, GmresCtl* ctl, int j, int m,
+                             cudaStream_t s, const int* done) {
+    axpy_dot_kernel<NJ, T><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, h1, w, n, scratch, h2, nw1, hn, ctl, j, m,
+                                                              done);
     count_launches(1);
     axpy_scale_kernel<NJ, T><<<stream_grid(n), 256, 0, s>>>(V, ldv, h2, hn, w, vout, n, done);
     count_launches(1);
@@ -329,9 +355,9 @@ cudaError_t cgs2_tail_launch(const T* V, size_t ldv, const double* h1, T* w, siz
 template <typename T>
 cudaError_t cgs2_tail_dispatch(const T* V, size_t ldv, int nv, const double* h1, T* w, size_t n,
                                double* scratch, double* h2, double* nw1, double* hn, T* vout,
-                               cudaStream_t s, const int* done) {
+                               GmresCtl* ctl, int j, int m, cudaStream_t s, const int* done) {
     switch (nv) {
-#define CASE(J) case J: return cgs2_tail_launch<J, T>(V, ldv, h1, w, n, scratch, h2, nw1, hn, vout, s, done);
+#define CASE(J) case J: return cgs2_tail_launch<J, T>(V, ldv, h1, w, n, scratch, h2, nw1, hn, vout, ctl, j, m, s, done);
         CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
         CASE(12) CASE(13) CASE(14) CASE(15) CASE(16) CASE(17) CASE(18) CASE(19) CASE(20) CASE(21)
         CASE(22) CASE(23) CASE(24) CASE(25) CASE(26) CASE(27) CASE(28) CASE(29) CASE(30) CASE(31)
@@ -362,12 +388,10 @@ cudaError_t multidot_impl(const T* V, size_t ldv, int nv, const T* w, size_t n, 
                           cudaStream_t s, const int* done) {
     for (int j0 = 0; j0 < nv; j0 += kDotChunk) {
         const int nj = nv - j0 < kDotChunk ? nv - j0 : kDotChunk;
-        multidot_partial_kernel<kDotChunk, T><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, j0, nj, w, n,
-                                                                                  scratch, nv, done);
+        multidot_kernel<kDotChunk, T><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, j0, nj, w, n, scratch, nv, out,
+                                                                          done);
         count_launches(1);
     }
-    multidot_final_kernel<<<(nv + 7) / 8, 256, 0, s>>>(scratch, kDotBlocks, nv, nv, out, done);
-    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -377,14 +401,14 @@ int cgs2_max_vectors() { return 32; }
 
 cudaError_t launch_cgs2_tail(const double* V, size_t ldv, int nv, const double* h1, double* w, size_t n,
                              double* scratch, double* h2, double* nw1, double* hn, double* vout,
-                             cudaStream_t s, const int* done) {
-    return cgs2_tail_dispatch<double>(V, ldv, nv, h1, w, n, scratch, h2, nw1, hn, vout, s, done);
+                             GmresCtl* ctl, int j, int m, cudaStream_t s, const int* done) {
+    return cgs2_tail_dispatch<double>(V, ldv, nv, h1, w, n, scratch, h2, nw1, hn, vout, ctl, j, m, s, done);
 }
 
 cudaError_t launch_cgs2_tail(const float* V, size_t ldv, int nv, const double* h1, float* w, size_t n,
                              double* scratch, double* h2, double* nw1, double* hn, float* vout,
-                             cudaStream_t s, const int* done) {
-    return cgs2_tail_dispatch<float>(V, ldv, nv, h1, w, n, scratch, h2, nw1, hn, vout, s, done);
+                             GmresCtl* ctl, int j, int m, cudaStream_t s, const int* done) {
+    return cgs2_tail_dispatch<float>(V, ldv, nv, h1, w, n, scratch, h2, nw1, hn, vout, ctl, j, m, s, done);
 }
 
 cudaError_t launch_spmv_pre(const Geom& g, const double* Stil, const int* Scol, const double* x,
@@ -412,7 +436,7 @@ cudaError_t launch_block_diag(const Geom& g, const double* Bd, const double* x, 
     }
 }
 
-size_t dot_scratch_doubles(int nv) { return (size_t)kDotBlocks * (size_t)nv; }
+size_t dot_scratch_doubles(int nv) { return 1 + (size_t)kDotBlocks * (size_t)nv; }   // ticket + partials
 
 cudaError_t launch_multidot(const double* V, size_t ldv, int nv, const double* w, size_t n,
                             double* scratch, double* out, cudaStream_t s, const int* done) {
@@ -464,12 +488,6 @@ cudaError_t launch_gmres_cycle_init(GmresCtl* c, const double* nrm2, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t launch_gmres_arnoldi(GmresCtl* c, int j, int m, const double* h1, const double* h2, const double* hn,
-                                 cudaStream_t s) {
-    gmres_arnoldi_kernel<<<1, 1, 0, s>>>(c, j, m, h1, h2, hn);
-    count_launches(1);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_gmres_update(const double* V, size_t ldv, GmresCtl* c, double* x, size_t n, cudaStream_t s) {
     gmres_solve_y_kernel<<<1, 1, 0, s>>>(c);
