@@ -240,6 +240,21 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
+def max_over_ranks(value, dist, device="cuda"):
+    """The largest value over all ranks (the job's time is its slowest rank's)."""
+    if not dist:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, dof, steps, ms):
+    """Whole-job DOF-steps/s: every rank advances its own replica of dof unknowns by steps."""
+    return world * dof * steps / (ms / 1e3)
+
+
 def _timed_steps(sim, stream, steps, dist):
     """K steps of a resident instance, CUDA events on the library's stream around each."""
     import torch
@@ -257,44 +272,40 @@ def _timed_steps(sim, stream, steps, dist):
     if dist:
         dist.barrier()
     per_step = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
-    ms_total = evs[0].elapsed_time(evs[-1])
-    if dist:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(evs[0].elapsed_time(evs[-1]), dist)
     st = sim.stats()
     return {"ms_total": ms_total, "per_step": per_step, "ktimes": sim.kernel_times(), "stats": st,
             "launches": st["kernel_launches"] - l0}
 
 
 def _e2e(sim, stream, steps, dist, h, hu, hv):
-    """The same steps through host buffers: pinned H2D of the state, step, D2H of the result."""
+    """The same steps through host buffers, host in the loop: every step uploads its input state
+    from pinned host memory (the previous step's result; hdgdg_update_state continues the
+    trajectory), steps, and reads its result back into pinned host memory."""
     import torch
     n = h.size
     bufs = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(6)]
     for bsrc, a in zip(bufs[:3], (h, hu, hv)):
         bsrc.numpy()[:] = a.ravel()
-    ptrs_in = [bb.data_ptr() for bb in bufs[:3]]
-    ptrs_out = [bb.data_ptr() for bb in bufs[3:]]
-    sim.set_state_ptrs(*ptrs_in)
+    ping = [bb.data_ptr() for bb in bufs[:3]]
+    pong = [bb.data_ptr() for bb in bufs[3:]]
+    sim.set_state_ptrs(*ping)
     sim.step(1)
-    sim.get_state_ptrs(*ptrs_out)
+    sim.get_state_ptrs(*pong)
+    ping, pong = pong, ping
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(steps):
-        sim.set_state_ptrs(*ptrs_in)
+        sim.update_state_ptrs(*ping)
         sim.step(1)
-        sim.get_state_ptrs(*ptrs_out)
+        sim.get_state_ptrs(*pong)
+        ping, pong = pong, ping
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
     return ms, 3 * n * 8
 
 
@@ -606,7 +617,7 @@ def main():
         e2e = None
         if not args.no_e2e:
             ms_e2e, nbytes = _e2e(sim, stream, args.steps, dist, h, hu, hv)
-            e2e = {"value": world * dof * args.steps / (ms_e2e / 1e3), "unit": UNIT,
+            e2e = {"value": job_value(world, dof, args.steps, ms_e2e), "unit": UNIT,
                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
         sim.close()
         forms[precision] = {"r": r, "clocks": c, "e2e": e2e}
@@ -627,7 +638,7 @@ def main():
     summary = {}
     for p, f in forms.items():
         r = f["r"]
-        summary[p] = {"value": world * dof * args.steps / (r["ms_total"] / 1e3),
+        summary[p] = {"value": job_value(world, dof, args.steps, r["ms_total"]),
                       "ms_per_step": r["ms_total"] / args.steps,
                       "krylov_iterations_per_stage": r["stats"]["krylov_iterations"] / max(1, 2 * r["stats"]["steps"]),
                       "kernel_breakdown_ms": {c: {"ms": round(v[0], 3), "groups": v[1]} for c, v in r["ktimes"].items()},

@@ -171,9 +171,16 @@ hdgdg_status hdgdg_gll(int degree_k, double* nodes, double* weights);
 hdgdg_status hdgdg_create(const hdgdg_config* cfg, const double* bottom_b, void* cuda_stream,
                           hdgdg_sim** out);
 
-/* Copy a user state (host arrays h, hu, hv [n_el][(k+1)^2]) in and reset the step
- * counters.  ENONFINITE if any value is not finite or h - B leaves phi = g h <= 0. */
+/* Copy a user state (host arrays h, hu, hv [n_el][(k+1)^2]) in and start a new trajectory:
+ * step counters, simulated time and the trace solve's initial-guess history are reset.
+ * ENONFINITE if any value is not finite or h - B leaves phi = g h <= 0. */
 hdgdg_status hdgdg_set_state(hdgdg_sim* sim, const double* h, const double* hu, const double* hv);
+
+/* Replace the state of a running trajectory (e.g. a host that corrects the state between
+ * steps): like hdgdg_set_state, but the step counters, the simulated time and the
+ * initial-guess history are kept.  ESTATE before the first hdgdg_set_state; ENONFINITE as
+ * hdgdg_set_state (the previous state is then kept). */
+hdgdg_status hdgdg_update_state(hdgdg_sim* sim, const double* h, const double* hu, const double* hv);
 
 /* Advance n_steps >= 0 time steps of Algorithm 1.  Synchronises the stream on return.
  * ENOTCONVERGED if a trace solve misses krylov_rtol within krylov_maxit (the state is

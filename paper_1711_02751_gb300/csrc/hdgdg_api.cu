@@ -864,6 +864,26 @@ hdgdg_status upload3(hdgdg_sim* sim, double* dst, const double* src, size_t coun
     return HDGDG_OK;
 }
 
+// User (h, hu, hv) on the host -> state q = (phi_eta, U, V) in dst; *ok false when a value is
+// not finite or the depth is not positive.
+hdgdg_status load_user_state(hdgdg_sim* sim, const double* h, const double* hu, const double* hv, double* dst,
+                             bool* ok) {
+    const size_t n = sim->plan.n;
+    double* stg = sim->NLs[0];
+    TRY(upload3(sim, stg, h, n));
+    TRY(upload3(sim, stg + n, hu, n));
+    TRY(upload3(sim, stg + 2 * n, hv, n));
+    CU(cudaMemsetAsync(sim->flags, 0, sizeof(unsigned), sim->stream));
+    CU(launch_user_to_state(sim->g, stg, stg + n, stg + 2 * n, sim->phiB, sim->cfg.g, dst, sim->flags,
+                            sim->stream));
+    CU(cudaMemcpyAsync(sim->hbuf, sim->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, sim->stream));
+    TRY(sync(sim));
+    unsigned bad = 0;
+    std::memcpy(&bad, sim->hbuf, sizeof(unsigned));
+    *ok = bad == 0;
+    return HDGDG_OK;
+}
+
 hdgdg_status download(hdgdg_sim* sim, double* dst, const double* src, size_t count) {
     CU(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDeviceToHost, sim->stream));
     return sync(sim);
@@ -964,19 +984,9 @@ hdgdg_status hdgdg_create(const hdgdg_config* cfg, const double* bottom_b, void*
 
 hdgdg_status hdgdg_set_state(hdgdg_sim* sim, const double* h, const double* hu, const double* hv) {
     if (!sim || !h || !hu || !hv) return fail(sim, HDGDG_EINVAL, "NULL argument to set_state");
-    const size_t n = sim->plan.n;
-    double* stg = sim->NLs[0];
-    TRY(upload3(sim, stg, h, n));
-    TRY(upload3(sim, stg + n, hu, n));
-    TRY(upload3(sim, stg + 2 * n, hv, n));
-    CU(cudaMemsetAsync(sim->flags, 0, sizeof(unsigned), sim->stream));
-    CU(launch_user_to_state(sim->g, stg, stg + n, stg + 2 * n, sim->phiB, sim->cfg.g, sim->q, sim->flags,
-                            sim->stream));
-    CU(cudaMemcpyAsync(sim->hbuf, sim->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, sim->stream));
-    TRY(sync(sim));
-    unsigned bad = 0;
-    std::memcpy(&bad, sim->hbuf, sizeof(unsigned));
-    if (bad) {
+    bool ok = false;
+    TRY(load_user_state(sim, h, hu, hv, sim->q, &ok));
+    if (!ok) {
         sim->have_state = false;
         return fail(sim, HDGDG_ENONFINITE, "state has a non-finite value or non-positive depth");
     }
@@ -984,6 +994,16 @@ hdgdg_status hdgdg_set_state(hdgdg_sim* sim, const double* h, const double* hu, 
     sim->stats = hdgdg_stats{};
     sim->t = 0.0;
     for (int i = 0; i < kMaxStages; ++i) sim->n_hist[i] = 0;   // a new trajectory: no guess history
+    return HDGDG_OK;
+}
+
+hdgdg_status hdgdg_update_state(hdgdg_sim* sim, const double* h, const double* hu, const double* hv) {
+    if (!sim || !h || !hu || !hv) return fail(sim, HDGDG_EINVAL, "NULL argument to update_state");
+    if (!sim->have_state) return fail(sim, HDGDG_ESTATE, "update_state before set_state");
+    bool ok = false;
+    TRY(load_user_state(sim, h, hu, hv, sim->q_new, &ok));   // q_new is free between steps
+    if (!ok) return fail(sim, HDGDG_ENONFINITE, "state has a non-finite value or non-positive depth");
+    std::swap(sim->q, sim->q_new);
     return HDGDG_OK;
 }
 

@@ -20,7 +20,7 @@ BOUNDARIES = {"periodic": 0, "wall": 1, "vortex": 2}
 
 EXPORTS = ["hdgdg_bytes_required", "hdgdg_node_coords", "hdgdg_create", "hdgdg_set_state",
            "hdgdg_step", "hdgdg_get_state", "hdgdg_get_stats", "hdgdg_last_error", "hdgdg_destroy",
-           "hdgdg_eval_nl", "hdgdg_condense_rhs", "hdgdg_trace_apply", "hdgdg_stage_solve",
+           "hdgdg_update_state", "hdgdg_eval_nl", "hdgdg_condense_rhs", "hdgdg_trace_apply", "hdgdg_stage_solve",
            "hdgdg_measure_fp64_tflops", "hdgdg_set_kernel_timing", "hdgdg_kernel_time",
            "hdgdg_mass_noalloc", "hdgdg_gll"]
 KERNEL_CLASSES = ["spmv", "ortho", "condense", "recover", "dg", "combine"]
@@ -67,6 +67,7 @@ def lib():
         L.hdgdg_gll.argtypes = [ctypes.c_int, _P, _P]
         L.hdgdg_create.argtypes = [ctypes.POINTER(Config), _P, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
         L.hdgdg_set_state.argtypes = [ctypes.c_void_p, _P, _P, _P]
+        L.hdgdg_update_state.argtypes = [ctypes.c_void_p, _P, _P, _P]
         L.hdgdg_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.hdgdg_get_state.argtypes = [ctypes.c_void_p, _P, _P, _P]
         L.hdgdg_get_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(Stats)]
@@ -221,6 +222,17 @@ class Sim:
         """set_state from raw host addresses (e.g. pinned buffers); sizes as in set_state."""
         self._check(lib().hdgdg_set_state(self._h, ctypes.cast(h_ptr, _P), ctypes.cast(hu_ptr, _P),
                                           ctypes.cast(hv_ptr, _P)))
+
+    def update_state(self, h, hu, hv):
+        """Replace the state of the running trajectory (time, counters and solver history kept)."""
+        sh = (self.n_el, self.Np)
+        h, hu, hv = _f64(h, sh), _f64(hu, sh), _f64(hv, sh)
+        self._check(lib().hdgdg_update_state(self._h, _ptr(h), _ptr(hu), _ptr(hv)))
+
+    def update_state_ptrs(self, h_ptr, hu_ptr, hv_ptr):
+        """update_state from raw host addresses (e.g. pinned buffers)."""
+        self._check(lib().hdgdg_update_state(self._h, ctypes.cast(h_ptr, _P), ctypes.cast(hu_ptr, _P),
+                                             ctypes.cast(hv_ptr, _P)))
 
     def step(self, n_steps=1):
         self._check(lib().hdgdg_step(self._h, int(n_steps)))

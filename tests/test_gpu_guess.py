@@ -53,3 +53,27 @@ def test_guess_mixed_within_1e6():
     _, _, _, _, _, _, q1, st1 = _run(16, 3, "large", 20, 2, precision="mixed")
     m, _, _, _, _, _, q0, _ = _run(16, 3, "large", 20, -1, precision="fp64")
     assert max(imex.rel_l2(m, q1[c], q0[c]) for c in range(3)) <= 1e-6
+
+
+def test_update_state_continues_the_trajectory():
+    """update_state replaces the state but keeps time, counters and the guess history: a run
+    that is read back and re-entered half-way matches the uninterrupted run to round-off."""
+    import numpy as np
+    m, h, hu, hv, b = user_state(8, 3, "large")
+    dt = dt_of(m, h, hu, hv)
+    with hd.Sim(8, 3, dt, bottom=b) as s:
+        with pytest.raises(hd.HdgdgError):
+            s.update_state(h, hu, hv)              # no trajectory yet
+        s.set_state(h, hu, hv)
+        s.step(6)
+        ref = s.get_state()
+        s.set_state(h, hu, hv)
+        s.step(3)
+        mid = s.get_state()
+        s.update_state(*mid)
+        s.step(3)
+        got = s.get_state()
+        st = s.stats()
+    assert st["steps"] == 6 and abs(st["time"] - 6 * dt) <= 1e-15
+    for a, r in zip(got, ref):
+        assert np.abs(a - r).max() <= 1e-12 * max(np.abs(r).max(), 1.0)
