@@ -356,13 +356,19 @@ struct TimedGroup {
     int cls, slot;
     cudaEvent_t a = nullptr;
     TimedGroup(hdgdg_sim* s, int c, int sl = -1) : sim(s), cls(c), slot(sl) {
-        if (sim->timing && (a = take_event(sim))) cudaEventRecord(a, sim->stream);
+        if (sim->timing && (a = take_event(sim))) record(a);
+    }
+    // Inside a stream capture a plain event record only orders the capture; an external record
+    // becomes a graph node that records the event at every replay.
+    void record(cudaEvent_t e) const {
+        if (sim->capture_sink) cudaEventRecordWithFlags(e, sim->stream, cudaEventRecordExternal);
+        else cudaEventRecord(e, sim->stream);
     }
     ~TimedGroup() {
         if (!a) return;
         cudaEvent_t b = take_event(sim);
         if (!b) { sim->ev_pool.push_back(a); return; }
-        cudaEventRecord(b, sim->stream);
+        record(b);
         // groups recorded while a GMRES cycle is captured belong to that graph and are read
         // after each of its replays
         (sim->capture_sink ? sim->capture_sink : &sim->pending)->push_back({a, b, cls, slot});
@@ -372,9 +378,13 @@ struct TimedGroup {
 void flush_timers(hdgdg_sim* sim, int slot_limit = 1 << 30) {
     for (auto& p : sim->pending) {
         float ms = 0.f;
-        if (p.slot < slot_limit && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-            sim->kt_ms[p.cls] += ms;
-            sim->kt_n[p.cls] += 1;
+        if (p.slot < slot_limit) {
+            if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+                sim->kt_ms[p.cls] += ms;
+                sim->kt_n[p.cls] += 1;
+            } else {
+                cudaGetLastError();   // a timer that could not be read is skipped, not an error
+            }
         }
         sim->ev_pool.push_back(p.a);
         sim->ev_pool.push_back(p.b);
@@ -386,9 +396,12 @@ void flush_timers(hdgdg_sim* sim, int slot_limit = 1 << 30) {
 void read_graph_timers(hdgdg_sim* sim, const CycleGraph& cg, int slot_limit) {
     for (const auto& p : cg.timers) {
         float ms = 0.f;
-        if (p.slot < slot_limit && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+        if (p.slot >= slot_limit) continue;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
             sim->kt_ms[p.cls] += ms;
             sim->kt_n[p.cls] += 1;
+        } else {
+            cudaGetLastError();
         }
     }
 }
