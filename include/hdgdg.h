@@ -177,9 +177,10 @@ hdgdg_status hdgdg_create(const hdgdg_config* cfg, const double* bottom_b, void*
 hdgdg_status hdgdg_set_state(hdgdg_sim* sim, const double* h, const double* hu, const double* hv);
 
 /* Replace the state of a running trajectory (e.g. a host that corrects the state between
- * steps): like hdgdg_set_state, but the step counters, the simulated time and the
- * initial-guess history are kept.  ESTATE before the first hdgdg_set_state; ENONFINITE as
- * hdgdg_set_state (the previous state is then kept). */
+ * steps; the paper has no counterpart): like hdgdg_set_state, but the step counters, the
+ * simulated time and the initial-guess history are kept.  Arrays as hdgdg_set_state, copied
+ * in.  ESTATE before the first hdgdg_set_state; ENONFINITE as hdgdg_set_state (the previous
+ * state is then kept). */
 hdgdg_status hdgdg_update_state(hdgdg_sim* sim, const double* h, const double* hu, const double* hv);
 
 /* Advance n_steps >= 0 time steps of Algorithm 1.  Synchronises the stream on return.
