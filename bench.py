@@ -52,6 +52,10 @@ def _args():
                     help="arithmetic of the local condensation / recovery in the mixed form")
     ap.add_argument("--guess", type=int, default=0, choices=[-1, 0, 1, 2, 3],
                     help="trace-solve initial guess: extrapolation order 1-3, -1 zero, 0 library default")
+    ap.add_argument("--spmv-kernel", type=int, default=0, choices=[0, 1],
+                    help="FP32 inner SpMV: 0 plain (x gathered through shared memory), 1 pipelined bulk copies")
+    ap.add_argument("--ortho", type=int, default=0, choices=[0, 1],
+                    help="Gram-Schmidt of the mixed form's inner cycles: 0 twice (CGS2), 1 once")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true",
@@ -602,7 +606,7 @@ def main():
                      krylov_restart=args.restart, precision=precision,
                      krylov_rtol=args.mixed_rtol if precision == "mixed" else 0.0,
                      local_precision=args.local if precision == "mixed" else "fp64",
-                     krylov_guess=args.guess)
+                     krylov_guess=args.guess, spmv_kernel=args.spmv_kernel, krylov_ortho=args.ortho)
         sim.set_state(h, hu, hv)
         for _ in range(args.warmup):
             sim.step(1)

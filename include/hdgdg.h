@@ -114,6 +114,14 @@ typedef struct {
                             The stop test stays ||g - S qhat|| <= rtol ||g||.  The guess's residual
                             needs no matrix product: the same extrapolation of the stored
                             products S x_{n-j} (g - r at the end of each solve) gives S x_0. */
+    int spmv_kernel;     /* FP32 trace-matrix product of the mixed form's inner cycles: 0 = one
+                            thread per row component, neighbour vectors gathered through shared
+                            memory; 1 = a persistent kernel that also streams the matrix through
+                            shared memory with bulk (TMA) copies, two stages deep.  Identical
+                            results (same summation order). */
+    int krylov_ortho;    /* Gram-Schmidt of the mixed form's FP32 inner cycles: 0 = classical,
+                            applied twice (CGS2); 1 = classical, once.  The FP64 form and the
+                            FP64 refinement residuals are not affected. */
 } hdgdg_config;
 
 /* HDGDG_VORTEX: the exact-solution boundary conditions of the paper's moving-vortex test

@@ -49,7 +49,8 @@ bool valid(const hdgdg_config* c) {
            c->krylov_restart <= kMaxRestart && c->local_precision >= HDGDG_LOCAL_FP64 &&
            c->local_precision <= HDGDG_LOCAL_BF16 &&
            (c->local_precision != HDGDG_LOCAL_BF16 || c->degree_k <= 4) &&   // tensor-core tiles: k <= 4
-           c->krylov_guess >= -1 && c->krylov_guess <= 3;
+           c->krylov_guess >= -1 && c->krylov_guess <= 3 && (c->spmv_kernel == 0 || c->spmv_kernel == 1) &&
+           (c->krylov_ortho == 0 || c->krylov_ortho == 1);
 }
 
 bool explicit_scheme(const hdgdg_config* c) { return c->scheme == HDGDG_RK2 || c->scheme == HDGDG_RK3; }
@@ -334,6 +335,8 @@ hdgdg_status dalloc(hdgdg_sim* sim, T** p, size_t count) {
 // Slots of the small device array dvals
 inline double* dv_h1(hdgdg_sim* s) { return s->dvals; }
 inline double* dv_h2(hdgdg_sim* s) { return s->dvals + (s->plan.m + 2); }
+// device error word of the pipelined SpMV (a bounded wait ran out)
+inline int* spmv_error(hdgdg_sim* s) { return reinterpret_cast<int*>(s->flags) + 3; }
 inline double* dv_nrm(hdgdg_sim* s) { return s->dvals + 2 * (s->plan.m + 2); }
 inline double* dv_coef(hdgdg_sim* s) { return s->dvals + 2 * (s->plan.m + 2) + 8; }
 
@@ -510,13 +513,18 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
             const T* Vj = V + (size_t)j * n;
             {
                 TimedGroup tg(sim, HDGDG_KT_SPMV, j);
-                e = launch_spmv_pre(sim->g, St, sim->Scol, Vj, w, st, done);
+                if constexpr (kMixed)
+                    e = launch_spmv_pre(sim->g, St, sim->Scol, Vj, w, st, done,
+                                        sim->cfg.spmv_kernel == 1 ? spmv_error(sim) : nullptr);
+                else
+                    e = launch_spmv_pre(sim->g, St, sim->Scol, Vj, w, st, done);
             }
             TimedGroup tg(sim, HDGDG_KT_ORTHO, j);
             if (e == cudaSuccess) e = launch_multidot(V, n, j + 1, w, n, sim->red, dv_h1(sim), st, done);
             if (e == cudaSuccess)   // second pass, norm, Hessenberg column j and stop test
                 e = launch_cgs2_tail(V, n, j + 1, dv_h1(sim), w, n, sim->red, dv_h2(sim), dv_nrm(sim) + 2,
-                                     dv_nrm(sim) + 1, V + (size_t)(j + 1) * n, ctl, j, m, st, done);
+                                     dv_nrm(sim) + 1, V + (size_t)(j + 1) * n, ctl, j, m,
+                                     !(kMixed && sim->cfg.krylov_ortho == 1), st, done);
         }
         if (e == cudaSuccess) e = launch_gmres_update(V, n, ctl, sim->xt, n, st);
         if (e == cudaSuccess) e = launch_spmv_pre(sim->g, sim->Stil, sim->Scol, sim->xt, sim->w, st);
@@ -718,11 +726,12 @@ hdgdg_status one_step(hdgdg_sim* sim) {
         TimedGroup tg(sim, HDGDG_KT_COMBINE);
         CU(launch_combine(n3, sim->q, t, sim->q_new, sim->flags, st));
     }
-    unsigned flag[3] = {0, 0, 0};   // non-finite, (setup), tensor-core wait ran out
+    unsigned flag[4] = {0, 0, 0, 0};   // non-finite, (setup), tensor-core wait, SpMV wait ran out
     CU(cudaMemcpyAsync(&sim->hbuf[0], sim->flags, sizeof(flag), cudaMemcpyDeviceToHost, st));
     TRY(sync(sim));
     std::memcpy(flag, &sim->hbuf[0], sizeof(flag));
     if (flag[2]) return fail(sim, HDGDG_ECUDA, "a bounded wait of the tensor-core local kernel ran out (%u)", flag[2]);
+    if (flag[3]) return fail(sim, HDGDG_ECUDA, "a bounded wait of the pipelined SpMV ran out (%u)", flag[3]);
     if (flag[0]) return fail(sim, HDGDG_ENONFINITE, "step %lld produced a non-finite state", sim->stats.steps + 1);
     std::swap(sim->q, sim->q_new);
     sim->stats.steps += 1;

@@ -233,8 +233,10 @@ cudaError_t launch_local_tc(const Geom& g, int mode, const void* image, const do
 // done (may be NULL): device flag; the Krylov-loop kernels return at once when it is set.
 cudaError_t launch_spmv_pre(const Geom& g, const double* Stil, const int* Scol, const double* x,
                             double* y, cudaStream_t s, const int* done = nullptr);
+// FP32: given stream_error (a device int set when a bounded wait runs out), the matrix is
+// streamed through shared memory by bulk copies in a persistent pipelined kernel instead.
 cudaError_t launch_spmv_pre(const Geom& g, const float* Stil, const int* Scol, const float* x,
-                            float* y, cudaStream_t s, const int* done = nullptr);
+                            float* y, cudaStream_t s, const int* done = nullptr, int* stream_error = nullptr);
 // y = B x for a block-diagonal matrix B given as [edge][col][row] blocks (FP64)
 cudaError_t launch_block_diag(const Geom& g, const double* Bd, const double* x, double* y,
                               cudaStream_t s);
@@ -269,14 +271,15 @@ cudaError_t launch_axpy_f32_into_f64(const float* V, size_t ldv, int nv, const d
 // w1 = w - V h1 (in place), h2 = V^T w1, ||w1||^2 -> *nw1, hn = sqrt(||w1||^2 - ||h2||^2),
 // vout = (w1 - V h2) / hn.  nv <= cgs2_max_vectors(); scratch of dot_scratch_doubles(nv + 1).
 // With a GMRES control block, column j of the Hessenberg matrix, its Givens rotation and the
-// cycle's stop test are done in the same launch (restart length m).
+// cycle's stop test are done in the same launch (restart length m).  twice = false: classical
+// Gram-Schmidt once (h2 = 0, hn = ||w1||, vout = w1 / hn).
 int cgs2_max_vectors();
 cudaError_t launch_cgs2_tail(const double* V, size_t ldv, int nv, const double* h1, double* w, size_t n,
                              double* scratch, double* h2, double* nw1, double* hn, double* vout,
-                             GmresCtl* ctl, int j, int m, cudaStream_t s, const int* done = nullptr);
+                             GmresCtl* ctl, int j, int m, bool twice, cudaStream_t s, const int* done = nullptr);
 cudaError_t launch_cgs2_tail(const float* V, size_t ldv, int nv, const double* h1, float* w, size_t n,
                              double* scratch, double* h2, double* nw1, double* hn, float* vout,
-                             GmresCtl* ctl, int j, int m, cudaStream_t s, const int* done = nullptr);
+                             GmresCtl* ctl, int j, int m, bool twice, cudaStream_t s, const int* done = nullptr);
 
 
 cudaError_t launch_gmres_solve_init(GmresCtl* c, double tol_abs, double inner_rel, int maxit, cudaStream_t s);

@@ -10,6 +10,9 @@
 // Every kernel is a template on the storage type T: double for the FP64 path, float for the
 // inner solves of the mixed-precision path.  Products and per-thread partial sums are in T;
 // warp, block and grid reductions are in double.
+#include <algorithm>
+
+#include "async_copy.h"
 #include "internal.h"
 
 namespace hdgdg {
@@ -26,19 +29,113 @@ spmv_pre_kernel(int n_edges, const T* __restrict__ Stil, const int* __restrict__
                 const T* __restrict__ x, T* __restrict__ y, const int* __restrict__ done) {
     if (done && *done) return;
     constexpr int EPB = 256 / NF;
+    __shared__ T sx[EPB][6][NF];   // the six gathered neighbour trace vectors of each edge row
     const int le = threadIdx.x / NF, ii = threadIdx.x % NF;
     const int r = blockIdx.x * EPB + le;
-    if (le >= EPB || r >= n_edges) return;
+    const bool live = le < EPB && r < n_edges;
+    if (live) {   // each thread loads one value per slot: six independent loads
+#pragma unroll
+        for (int sl = 0; sl < 6; ++sl) sx[le][sl][ii] = x[(size_t)__ldg(Scol + (size_t)r * 6 + sl) * NF + ii];
+    }
+    __syncthreads();
+    if (!live) return;
     const T* S = Stil + (size_t)r * 6 * NF * NF;
     T acc = x[(size_t)r * NF + ii];
 #pragma unroll
     for (int sl = 0; sl < 6; ++sl) {
-        const T* xc = x + (size_t)__ldg(Scol + (size_t)r * 6 + sl) * NF;
         const T* Sb = S + sl * NF * NF;
 #pragma unroll
-        for (int jj = 0; jj < NF; ++jj) acc += Sb[jj * NF + ii] * xc[jj];
+        for (int jj = 0; jj < NF; ++jj) acc += Sb[jj * NF + ii] * sx[le][sl][jj];
     }
     y[(size_t)r * NF + ii] = acc;
+}
+
+// The same product with the matrix streamed through shared memory: a persistent CTA takes
+// tiles of ET consecutive edge rows; their 6 NF x NF blocks are contiguous in S~, so one bulk
+// (TMA) copy per tile brings them in, two stages deep on mbarriers, while the threads (one per
+// row component, as above) multiply the previous tile.  Same summation order as
+// spmv_pre_kernel, so the results are identical bit for bit.  n_edges * NF must be even (every
+// tile a multiple of 16 bytes); a wait that runs out sets *error and ends the CTA.
+template <int NF>
+struct SpmvTile {
+    static constexpr int BLK = 6 * NF * NF;   // floats of one edge row
+    static constexpr int ET0 = 55296 / (BLK * 4);
+    static constexpr int ET = ET0 > 32 ? 32 : (ET0 < 2 ? 2 : (ET0 & ~1));   // even
+    static constexpr int TILE = ET * BLK;
+    static constexpr int THREADS = ET * NF;
+};
+
+template <int NF>
+__global__ void __launch_bounds__(SpmvTile<NF>::THREADS)
+spmv_stream_kernel(int n_edges, const float* __restrict__ Stil, const int* __restrict__ Scol,
+                   const float* __restrict__ x, float* __restrict__ y, const int* __restrict__ done,
+                   int* __restrict__ error) {
+    if (done && *done) return;
+    using Tl = SpmvTile<NF>;
+    extern __shared__ __align__(128) float stile[];     // [2][TILE]
+    __shared__ __align__(8) uint64_t full[2], empty[2];
+    __shared__ float sx[Tl::ET][6][NF];
+    const int tid = threadIdx.x;
+    const int n_tiles = (n_edges + Tl::ET - 1) / Tl::ET;
+    if (tid == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&empty[0], blockDim.x);
+        mbar_init(&empty[1], blockDim.x);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    auto issue = [&](int i) {   // thread 0: the i-th tile of this CTA into stage i % 2
+        const int t = blockIdx.x + i * gridDim.x;
+        if (t >= n_tiles) return;
+        const int e0 = t * Tl::ET;
+        const int ne = min(Tl::ET, n_edges - e0);
+        const uint32_t bytes = (uint32_t)ne * Tl::BLK * 4u;
+        mbar_expect_tx(&full[i & 1], bytes);
+        bulk_copy_g2s(stile + (i & 1) * Tl::TILE, Stil + (size_t)e0 * Tl::BLK, bytes, &full[i & 1]);
+    };
+    if (tid == 0) {
+        issue(0);
+        issue(1);
+    }
+    const int le = tid / NF, ii = tid % NF;
+    for (int i = 0;; ++i) {
+        const int t = blockIdx.x + i * gridDim.x;
+        if (t >= n_tiles) break;
+        const int st = i & 1;
+        const uint32_t parity = (uint32_t)(i >> 1) & 1u;
+        if (!mbar_wait_bounded(&full[st], parity)) {
+            atomicExch(error, 1);
+            return;
+        }
+        const int r = t * Tl::ET + le;
+        if (r < n_edges) {   // gather the neighbour trace vectors: six independent loads
+#pragma unroll
+            for (int sl = 0; sl < 6; ++sl) sx[le][sl][ii] = x[(size_t)__ldg(Scol + (size_t)r * 6 + sl) * NF + ii];
+        }
+        __syncthreads();
+        if (r < n_edges) {
+            const float* S = stile + st * Tl::TILE + le * Tl::BLK;
+            float acc = x[(size_t)r * NF + ii];
+#pragma unroll
+            for (int sl = 0; sl < 6; ++sl) {
+                const float* Sb = S + sl * NF * NF;
+#pragma unroll
+                for (int jj = 0; jj < NF; ++jj) acc += Sb[jj * NF + ii] * sx[le][sl][jj];
+            }
+            y[(size_t)r * NF + ii] = acc;
+        }
+        __syncthreads();   // sx is rewritten for the next tile
+        mbar_arrive(&empty[st]);
+        if (tid == 0 && blockIdx.x + (i + 2) * gridDim.x < n_tiles) {
+            // the stage is reused for tile i + 2 once every thread has read tile i
+            if (!mbar_wait_bounded(&empty[st], parity)) {
+                atomicExch(error, 2);
+                return;
+            }
+            issue(i + 2);
+        }
+    }
 }
 
 // y[r] = B_r x[r] for column-major NF x NF blocks (FP64)
@@ -173,7 +270,8 @@ __global__ void to_f32_kernel(const double* __restrict__ a, float* __restrict__ 
 // last block also forms hn = sqrt(||w1||^2 - ||h2||^2), the norm of w2 = w1 - V h2 for an
 // orthonormal V, and, given a GMRES control block, the Hessenberg column j with its Givens
 // rotation and stop test.
-template <int NJ, typename T>
+// TWICE = false (classical Gram-Schmidt once): only the update and ||w1||; h2 = 0, hn = ||w1||.
+template <int NJ, typename T, bool TWICE>
 __global__ void __launch_bounds__(kDotThreads)
 axpy_dot_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict__ h1, T* __restrict__ w,
                 size_t n, double* __restrict__ scratch, double* __restrict__ h2, double* __restrict__ nw1,
@@ -197,8 +295,10 @@ axpy_dot_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict__ 
             x -= hc[j] * v[j];
         }
         w[idx] = x;
+        if (TWICE) {
 #pragma unroll
-        for (int j = 0; j < NJ; ++j) acc[j] += v[j] * x;
+            for (int j = 0; j < NJ; ++j) acc[j] += v[j] * x;
+        }
         acc[NJ] += x * x;
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -225,6 +325,18 @@ axpy_dot_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict__ 
             *counter = 0u;
         }
     }
+}
+
+// V_{j+1} = w1 / hn (classical Gram-Schmidt once)
+template <typename T>
+__global__ void __launch_bounds__(256)
+scale_out_kernel(const double* __restrict__ hn, const T* __restrict__ w, T* __restrict__ vout, size_t n,
+                 const int* __restrict__ done) {
+    if (done && *done) return;
+    const T inv = T(1.0 / *hn);
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (size_t)gridDim.x * blockDim.x)
+        vout[idx] = w[idx] * inv;
 }
 
 // V_{j+1} = (w1 - sum_j h2_j V_j) / hn
@@ -332,6 +444,31 @@ cudaError_t spmv_launch(int n_edges, const T* Stil, const int* Scol, const T* x,
     return cudaGetLastError();
 }
 
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        n = (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) ? v : 1;
+    }
+    return n;
+}
+
+template <int NF>
+cudaError_t spmv_stream_launch(int n_edges, const float* Stil, const int* Scol, const float* x, float* y,
+                               cudaStream_t s, const int* done, int* error) {
+    using Tl = SpmvTile<NF>;
+    const size_t smem = 2 * (size_t)Tl::TILE * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(spmv_stream_kernel<NF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int n_tiles = (n_edges + Tl::ET - 1) / Tl::ET;
+    const int grid = std::min(n_tiles, 2 * sm_count());   // persistent: two CTAs per SM
+    spmv_stream_kernel<NF><<<grid, Tl::THREADS, smem, s>>>(n_edges, Stil, Scol, x, y, done, error);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 template <int NF>
 cudaError_t block_diag_launch(int n_edges, const double* Bd, const double* x, double* y, cudaStream_t s) {
     constexpr int EPB = 256 / NF;
@@ -343,11 +480,18 @@ cudaError_t block_diag_launch(int n_edges, const double* Bd, const double* x, do
 template <int NJ, typename T>
 cudaError_t cgs2_tail_launch(const T* V, size_t ldv, const double* h1, T* w, size_t n, double* scratch,
                              double* h2, double* nw1, double* hn, T* vout, GmresCtl* ctl, int j, int m,
-                             cudaStream_t s, const int* done) {
-    axpy_dot_kernel<NJ, T><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, h1, w, n, scratch, h2, nw1, hn, ctl, j, m,
-                                                              done);
-    count_launches(1);
-    axpy_scale_kernel<NJ, T><<<stream_grid(n), 256, 0, s>>>(V, ldv, h2, hn, w, vout, n, done);
+                             bool twice, cudaStream_t s, const int* done) {
+    if (twice) {
+        axpy_dot_kernel<NJ, T, true><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, h1, w, n, scratch, h2, nw1, hn,
+                                                                        ctl, j, m, done);
+        count_launches(1);
+        axpy_scale_kernel<NJ, T><<<stream_grid(n), 256, 0, s>>>(V, ldv, h2, hn, w, vout, n, done);
+    } else {
+        axpy_dot_kernel<NJ, T, false><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, h1, w, n, scratch, h2, nw1, hn,
+                                                                         ctl, j, m, done);
+        count_launches(1);
+        scale_out_kernel<T><<<stream_grid(n), 256, 0, s>>>(hn, w, vout, n, done);
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -355,9 +499,9 @@ cudaError_t cgs2_tail_launch(const T* V, size_t ldv, const double* h1, T* w, siz
 template <typename T>
 cudaError_t cgs2_tail_dispatch(const T* V, size_t ldv, int nv, const double* h1, T* w, size_t n,
                                double* scratch, double* h2, double* nw1, double* hn, T* vout,
-                               GmresCtl* ctl, int j, int m, cudaStream_t s, const int* done) {
+                               GmresCtl* ctl, int j, int m, bool twice, cudaStream_t s, const int* done) {
     switch (nv) {
-#define CASE(J) case J: return cgs2_tail_launch<J, T>(V, ldv, h1, w, n, scratch, h2, nw1, hn, vout, ctl, j, m, s, done);
+#define CASE(J) case J: return cgs2_tail_launch<J, T>(V, ldv, h1, w, n, scratch, h2, nw1, hn, vout, ctl, j, m, twice, s, done);
         CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
         CASE(12) CASE(13) CASE(14) CASE(15) CASE(16) CASE(17) CASE(18) CASE(19) CASE(20) CASE(21)
         CASE(22) CASE(23) CASE(24) CASE(25) CASE(26) CASE(27) CASE(28) CASE(29) CASE(30) CASE(31)
@@ -401,14 +545,14 @@ int cgs2_max_vectors() { return 32; }
 
 cudaError_t launch_cgs2_tail(const double* V, size_t ldv, int nv, const double* h1, double* w, size_t n,
                              double* scratch, double* h2, double* nw1, double* hn, double* vout,
-                             GmresCtl* ctl, int j, int m, cudaStream_t s, const int* done) {
-    return cgs2_tail_dispatch<double>(V, ldv, nv, h1, w, n, scratch, h2, nw1, hn, vout, ctl, j, m, s, done);
+                             GmresCtl* ctl, int j, int m, bool twice, cudaStream_t s, const int* done) {
+    return cgs2_tail_dispatch<double>(V, ldv, nv, h1, w, n, scratch, h2, nw1, hn, vout, ctl, j, m, twice, s, done);
 }
 
 cudaError_t launch_cgs2_tail(const float* V, size_t ldv, int nv, const double* h1, float* w, size_t n,
                              double* scratch, double* h2, double* nw1, double* hn, float* vout,
-                             GmresCtl* ctl, int j, int m, cudaStream_t s, const int* done) {
-    return cgs2_tail_dispatch<float>(V, ldv, nv, h1, w, n, scratch, h2, nw1, hn, vout, ctl, j, m, s, done);
+                             GmresCtl* ctl, int j, int m, bool twice, cudaStream_t s, const int* done) {
+    return cgs2_tail_dispatch<float>(V, ldv, nv, h1, w, n, scratch, h2, nw1, hn, vout, ctl, j, m, twice, s, done);
 }
 
 cudaError_t launch_spmv_pre(const Geom& g, const double* Stil, const int* Scol, const double* x,
@@ -417,9 +561,22 @@ cudaError_t launch_spmv_pre(const Geom& g, const double* Stil, const int* Scol, 
 }
 
 cudaError_t launch_spmv_pre(const Geom& g, const float* Stil, const int* Scol, const float* x,
-                            float* y, cudaStream_t s, const int* done) {
-    return spmv_dispatch<float>(g, Stil, Scol, x, y, s, done);
+                            float* y, cudaStream_t s, const int* done, int* stream_error) {
+    if (!stream_error || ((long long)g.n_edges * 3 * g.P) % 2 != 0)
+        return spmv_dispatch<float>(g, Stil, Scol, x, y, s, done);
+    switch (g.P) {   // the bulk-copy pipelined kernel
+        case 2: return spmv_stream_launch<6>(g.n_edges, Stil, Scol, x, y, s, done, stream_error);
+        case 3: return spmv_stream_launch<9>(g.n_edges, Stil, Scol, x, y, s, done, stream_error);
+        case 4: return spmv_stream_launch<12>(g.n_edges, Stil, Scol, x, y, s, done, stream_error);
+        case 5: return spmv_stream_launch<15>(g.n_edges, Stil, Scol, x, y, s, done, stream_error);
+        case 6: return spmv_stream_launch<18>(g.n_edges, Stil, Scol, x, y, s, done, stream_error);
+        case 7: return spmv_stream_launch<21>(g.n_edges, Stil, Scol, x, y, s, done, stream_error);
+        case 8: return spmv_stream_launch<24>(g.n_edges, Stil, Scol, x, y, s, done, stream_error);
+        case 9: return spmv_stream_launch<27>(g.n_edges, Stil, Scol, x, y, s, done, stream_error);
+        default: return cudaErrorInvalidValue;
+    }
 }
+
 
 cudaError_t launch_block_diag(const Geom& g, const double* Bd, const double* x, double* y,
                               cudaStream_t s) {

@@ -77,3 +77,18 @@ def test_update_state_continues_the_trajectory():
     assert st["steps"] == 6 and abs(st["time"] - 6 * dt) <= 1e-15
     for a, r in zip(got, ref):
         assert np.abs(a - r).max() <= 1e-12 * max(np.abs(r).max(), 1.0)
+
+
+def test_single_pass_gram_schmidt_in_the_inner_cycles():
+    """krylov_ortho = 1 (classical Gram-Schmidt once in the mixed form's FP32 cycles): the FP64
+    refinement keeps the result within 1e-6 of the FP64 form."""
+    import numpy as np  # noqa: F401
+    m, h, hu, hv, b = user_state(16, 3, "large")
+    dt = dt_of(m, h, hu, hv)
+    outs = []
+    for kw in ({"precision": "mixed", "krylov_ortho": 1}, {"precision": "fp64"}):
+        with hd.Sim(16, 3, dt, bottom=b, **kw) as s:
+            s.set_state(h, hu, hv)
+            s.step(20)
+            outs.append(swe.to_state(*s.get_state(), b, W.G, W.H0)[0])
+    assert max(imex.rel_l2(m, outs[0][c], outs[1][c]) for c in range(3)) <= 1e-6
