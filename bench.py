@@ -48,7 +48,7 @@ def _args():
                     help="refinement tolerance of the mixed form (0: library default 1e-9)")
     ap.add_argument("--precisions", default="fp64,mixed",
                     help="forms to time; the headline is mixed when within 1e-6 of fp64")
-    ap.add_argument("--local", default="fp64", choices=["fp64", "fp32", "bf16"],
+    ap.add_argument("--local", default="fp64", choices=["fp64", "fp32", "bf16", "f32x2"],
                     help="arithmetic of the local condensation / recovery in the mixed form")
     ap.add_argument("--guess", type=int, default=0, choices=[-1, 0, 1, 2, 3],
                     help="trace-solve initial guess: extrapolation order 1-3, -1 zero, 0 library default")

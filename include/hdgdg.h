@@ -74,9 +74,13 @@ enum { HDGDG_FP64 = 0, HDGDG_MIXED = 1 };
  *                   one time step for all instances, else create fails with EINVAL -- applied
  *                   to all elements as one dense contraction on the tensor cores (tcgen05, BF16
  *                   inputs, FP32 accumulation in tensor memory).
+ * HDGDG_LOCAL_F32X2: FP64-class on the FP32 pipes: A^{-1} held as an FP32 pair (hi + lo, 8
+ *                   bytes per entry like FP64) and every row's dot product computed with the
+ *                   compensated Dot2 scheme (exact products by FMA, TwoSum accumulation; Ogita,
+ *                   Rump and Oishi 2005), about 1e-13 relative, at the HBM bound.
  * Vectors stay FP64 in every case; the precision variants of the paper's workloads report
  * their error against the FP64 form. */
-enum { HDGDG_LOCAL_FP64 = 0, HDGDG_LOCAL_FP32 = 1, HDGDG_LOCAL_BF16 = 2 };
+enum { HDGDG_LOCAL_FP64 = 0, HDGDG_LOCAL_FP32 = 1, HDGDG_LOCAL_BF16 = 2, HDGDG_LOCAL_F32X2 = 3 };
 
 typedef struct {
     int n_side;          /* N >= 2: elements per side of the periodic unit square */
@@ -105,7 +109,8 @@ typedef struct {
                             trace systems are solved as one block-diagonal system.  Arrays of
                             create / set_state / get_state are then [batch][n_el][(k+1)^2]. */
     const double* dt_per_instance; /* host [batch] time steps (read at create); NULL = dt for all */
-    int local_precision; /* HDGDG_LOCAL_FP64 (0), HDGDG_LOCAL_FP32 or HDGDG_LOCAL_BF16 */
+    int local_precision; /* HDGDG_LOCAL_FP64 (0), HDGDG_LOCAL_FP32, HDGDG_LOCAL_BF16 or
+                            HDGDG_LOCAL_F32X2 */
     int krylov_guess;    /* start of each implicit stage's trace solve: the polynomial extrapolation
                             in time of the same stage's solutions of the previous steps --
                             1 = previous step (x_{n-1}), 2 = linear (2 x_{n-1} - x_{n-2}),

@@ -47,7 +47,7 @@ bool valid(const hdgdg_config* c) {
            c->boundary >= HDGDG_PERIODIC && c->boundary <= HDGDG_VORTEX && std::isfinite(c->x0) &&
            std::isfinite(c->length) && c->batch >= 0 && c->batch <= (1 << 20) &&
            c->krylov_restart <= kMaxRestart && c->local_precision >= HDGDG_LOCAL_FP64 &&
-           c->local_precision <= HDGDG_LOCAL_BF16 &&
+           c->local_precision <= HDGDG_LOCAL_F32X2 &&
            (c->local_precision != HDGDG_LOCAL_BF16 || c->degree_k <= 4) &&   // tensor-core tiles: k <= 4
            c->krylov_guess >= -1 && c->krylov_guess <= 3 && (c->spmv_kernel == 0 || c->spmv_kernel == 1) &&
            (c->krylov_ortho == 0 || c->krylov_ortho == 1);
@@ -100,6 +100,7 @@ Plan make_plan(const hdgdg_config* c) {
     b += 64 + sizeof(GmresCtl);                               // flags, GMRES control block
     if (c->local_precision == HDGDG_LOCAL_FP32) b += n_el * (size_t)p.NV * p.NV * sizeof(float);
     if (c->local_precision == HDGDG_LOCAL_BF16) b += tc_image_bytes((int)P);
+    if (c->local_precision == HDGDG_LOCAL_F32X2) b += 2 * n_el * (size_t)p.NV * p.NV * sizeof(float);
     b += 2 * (size_t)guess_order(c) * p.s * p.nt * d;         // previous stage solutions and products
     p.persistent = b;
     p.setup_temp = n_el * (size_t)p.NT * p.NT * d + n_edges * 7 * (size_t)p.NF * p.NF * d;
@@ -267,6 +268,7 @@ struct hdgdg_sim {
     double* yhist[kMaxStages][3] = {};   // steps per stage ([0] newest), their products S~ x~ (from
     int n_hist[kMaxStages] = {};         // the final true residual: g - r), and their count
     float* Ainv32 = nullptr;      // HDGDG_LOCAL_FP32
+    float *Ahi = nullptr, *Alo = nullptr;   // HDGDG_LOCAL_F32X2
     void* tc_image = nullptr;     // HDGDG_LOCAL_BF16: the shared operator's tensor-core tile
     LocalOps ops;
     int* Scol = nullptr;
@@ -859,6 +861,14 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
         CU(launch_to_f32(sim->Ainv, sim->Ainv32, n, sim->stream));
         sim->ops.kind = 1;
         sim->ops.Ainv32 = sim->Ainv32;
+    } else if (c->local_precision == HDGDG_LOCAL_F32X2) {
+        const size_t n = (size_t)g.n_el * p.NV * p.NV;
+        TRY(dalloc(sim, &sim->Ahi, n));
+        TRY(dalloc(sim, &sim->Alo, n));
+        CU(launch_split_f32x2(sim->Ainv, sim->Ahi, sim->Alo, n, sim->stream));
+        sim->ops.kind = 3;
+        sim->ops.Ahi = sim->Ahi;
+        sim->ops.Alo = sim->Alo;
     } else if (c->local_precision == HDGDG_LOCAL_BF16) {
         // one operator for every element: phi_B constant and one time step
         for (size_t k = 1; k < p.n; ++k)

@@ -203,9 +203,12 @@ cudaError_t launch_assemble_trace(const Geom& g, const double* Se, double* S7, d
 
 // The local operators as the condensation and recovery kernels apply them.
 struct LocalOps {
-    int kind = 0;                   // 0: per-element FP64; 1: per-element FP32; 2: shared, tensor cores
+    int kind = 0;                   // 0: per-element FP64; 1: per-element FP32; 2: shared, tensor cores;
+                                    // 3: per-element FP32 pairs (FP64-class, compensated dot products)
     const double* Ainv = nullptr;   // kind 0: [n_el][col s][row r] = (A^{-1})_{rs}
     const float* Ainv32 = nullptr;  // kind 1: same layout in FP32
+    const float* Ahi = nullptr;     // kind 3: A^{-1} = Ahi + Alo, same layout
+    const float* Alo = nullptr;
     const void* image = nullptr;    // kind 2: the shared A^{-1} as a BF16 tensor-core operand tile
     int* error = nullptr;           // kind 2: set when a bounded wait of the tensor-core kernel ran out
 };
@@ -217,6 +220,8 @@ cudaError_t launch_condense(const Geom& g, const LocalOps& ops, const double* R1
 cudaError_t launch_recover(const Geom& g, const LocalOps& ops, const double* Z, const double* R1,
                            const double* tau_edge, const double* qhat, double beta, double inv_aii,
                            double* Q, double* Lst, cudaStream_t s);
+// hi = (float)a, lo = (float)(a - hi): the FP32-pair copy of an FP64 array.
+cudaError_t launch_split_f32x2(const double* a, float* hi, float* lo, size_t n, cudaStream_t s);
 // Tensor-core tile of one shared operator: bytes of the BF16 image, and its build from the
 // FP64 A^{-1} of element 0 (setup).
 size_t tc_image_bytes(int P);

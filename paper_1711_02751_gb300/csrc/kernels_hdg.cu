@@ -288,6 +288,114 @@ __global__ void apply_ainv_kernel(Geom g, const T* __restrict__ Ainv, const doub
     Z[(r / Np) * fs + (size_t)e * Np + r % Np] = (double)acc;
 }
 
+// ---- FP64-class local contractions on the FP32 pipes -------------------------------------------
+// GB300 issues FP32 FMAs at 64x the FP64 rate, so A^{-1} is held as an unevaluated pair of FP32
+// arrays (a = a_hi + a_lo, the same 8 bytes per entry as FP64) and each row's dot product runs as
+// the compensated Dot2 of Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26, 2005): the products
+// a_hi x_hi are split exactly with Dekker's TwoProduct (via FMA) and summed with Knuth's TwoSum,
+// the cross terms a_hi x_lo + a_lo x_hi are added in FP32.  The result carries about 48 bits --
+// ~1e-13 relative, against 1e-16 for FP64 arithmetic -- at the HBM bound instead of the FP64
+// bound.  The explicit _rn intrinsics keep the compiler from fusing the steps.
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+struct Dot2 {
+    float p = 0.f, c = 0.f;   // running sum and its accumulated correction
+    __device__ __forceinline__ void add(float ah, float al, float xh, float xl) {
+        float h, r, q;
+        two_prod(ah, xh, h, r);
+        two_sum(p, h, p, q);
+        c = __fadd_rn(c, __fadd_rn(q, r));
+        c = __fmaf_rn(ah, xl, c);
+        c = __fmaf_rn(al, xh, c);
+    }
+    __device__ __forceinline__ double value() const { return (double)p + (double)c; }
+};
+
+__device__ __forceinline__ void split(double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+__global__ void split_kernel(const double* __restrict__ a, float* __restrict__ hi, float* __restrict__ lo,
+                             size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        split(a[i], hi[i], lo[i]);
+}
+
+// Z = A^{-1} R1 with the FP32-pair operator: one thread per (element, row), as apply_ainv_kernel.
+template <int P>
+__global__ void apply_ainv_x2_kernel(Geom g, const float* __restrict__ Ahi, const float* __restrict__ Alo,
+                                     const double* __restrict__ R1, double* __restrict__ Z) {
+    constexpr int Np = P * P, NV = 3 * Np;
+    constexpr int EPB = (256 / NV) > 0 ? 256 / NV : 1;
+    __shared__ float sxh[EPB][NV], sxl[EPB][NV];
+    const int le = threadIdx.x / NV, r = threadIdx.x % NV;
+    const int e = blockIdx.x * EPB + le;
+    const size_t fs = (size_t)g.n_el * Np;
+    const bool live = e < g.n_el && le < EPB;
+    if (live) split(R1[(r / Np) * fs + (size_t)e * Np + r % Np], sxh[le][r], sxl[le][r]);
+    __syncthreads();
+    if (!live) return;
+    const size_t base = (size_t)e * NV * NV;
+    Dot2 acc;
+#pragma unroll 4
+    for (int s = 0; s < NV; ++s) acc.add(Ahi[base + s * NV + r], Alo[base + s * NV + r], sxh[le][s], sxl[le][s]);
+    Z[(r / Np) * fs + (size_t)e * Np + r % Np] = acc.value();
+}
+
+// Q = Z + beta A^{-1}_{:, boundary} (tau qhat), Lst = (Q - R1) / a_ii with the FP32-pair operator.
+template <int P>
+__global__ void recover_x2_kernel(Geom g, const float* __restrict__ Ahi, const float* __restrict__ Alo,
+                                  const double* __restrict__ Z, const double* __restrict__ R1,
+                                  const double* __restrict__ tau_edge, const double* __restrict__ qhat, double beta,
+                                  double inv_aii, double* __restrict__ Q, double* __restrict__ Lst) {
+    constexpr int Np = P * P, NV = 3 * Np, NF = 3 * P;
+    constexpr int EPB = (256 / NV) > 0 ? 256 / NV : 1;
+    __shared__ float suh[EPB][NV], sul[EPB][NV];
+    const int le = threadIdx.x / NV, r = threadIdx.x % NV;
+    const int e = blockIdx.x * EPB + le;
+    const size_t fs = (size_t)g.n_el * Np;
+    const bool live = e < g.n_el && le < EPB;
+    if (live) {
+        const int c = r / Np, n = r % Np, i = n % P, j = n / P;
+        double u = 0.0;
+        for (int f = 0; f < 4; ++f) {
+            const bool on = (f == 0 && i == 0) || (f == 1 && i == P - 1) || (f == 2 && j == 0) ||
+                            (f == 3 && j == P - 1);
+            if (!on) continue;
+            const int b = (f < 2) ? j : i;
+            const int ed = edge_of_face(e, f, g);
+            u += tau_edge[(size_t)ed * P + b] * qhat[(size_t)ed * NF + c * P + b];
+        }
+        split(u, suh[le][r], sul[le][r]);
+    }
+    __syncthreads();
+    if (!live) return;
+    const size_t base = (size_t)e * NV * NV;
+    Dot2 acc;
+    for (int c = 0; c < 3; ++c) {
+        for (int n = 0; n < Np; ++n) {
+            const int i = n % P, j = n / P;
+            if (i != 0 && i != P - 1 && j != 0 && j != P - 1) continue;
+            const int s = c * Np + n;
+            acc.add(Ahi[base + s * NV + r], Alo[base + s * NV + r], suh[le][s], sul[le][s]);
+        }
+    }
+    const size_t o = (r / Np) * fs + (size_t)e * Np + r % Np;
+    const double q = Z[o] + beta * dt_factor(g, e) * acc.value();
+    Q[o] = q;
+    Lst[o] = (q - R1[o]) * inv_aii;
+}
+
 // g = -C Z at every trace node: one thread per (edge, b).
 template <int P>
 __global__ void edge_rhs_kernel(Geom g, const double* __restrict__ Z, const double* __restrict__ phiB,
@@ -430,6 +538,9 @@ cudaError_t condense_launch(const Geom& g, const LocalOps& ops, const double* R1
         cudaError_t e = launch_local_tc(g, 0, ops.image, R1, nullptr, nullptr, nullptr, 0.0, 0.0, Z, nullptr,
                                         ops.error, s);
         if (e != cudaSuccess) return e;
+    } else if (ops.kind == 3) {
+        apply_ainv_x2_kernel<P><<<blocks, EPB * NV, 0, s>>>(g, ops.Ahi, ops.Alo, R1, Z);
+        count_launches(1);
     } else if (ops.kind == 1) {
         apply_ainv_kernel<P, float><<<blocks, EPB * NV, 0, s>>>(g, ops.Ainv32, R1, Z);
         count_launches(1);
@@ -452,7 +563,10 @@ cudaError_t recover_launch(const Geom& g, const LocalOps& ops, const double* Z, 
     const int blocks = (g.n_el + EPB - 1) / EPB;
     if (ops.kind == 2)
         return launch_local_tc(g, 1, ops.image, R1, Z, tau_edge, qhat, beta, inv_aii, Q, Lst, ops.error, s);
-    if (ops.kind == 1)
+    if (ops.kind == 3)
+        recover_x2_kernel<P><<<blocks, EPB * NV, 0, s>>>(g, ops.Ahi, ops.Alo, Z, R1, tau_edge, qhat, beta,
+                                                         inv_aii, Q, Lst);
+    else if (ops.kind == 1)
         recover_kernel<P, float><<<blocks, EPB * NV, 0, s>>>(g, ops.Ainv32, Z, R1, tau_edge, qhat, beta,
                                                              inv_aii, Q, Lst);
     else
@@ -463,6 +577,14 @@ cudaError_t recover_launch(const Geom& g, const LocalOps& ops, const double* Z, 
 }
 
 }  // namespace
+
+cudaError_t launch_split_f32x2(const double* a, float* hi, float* lo, size_t n, cudaStream_t s) {
+    size_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    split_kernel<<<(int)(blocks > 0 ? blocks : 1), 256, 0, s>>>(a, hi, lo, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_build_local(const Geom& g, const double* phiB, const double* tau_edge, double dta,
                                double* Ainv, double* Se, int* singular, cudaStream_t s) {

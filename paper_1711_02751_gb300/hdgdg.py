@@ -15,7 +15,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ENONFINITE, ESTATE = range(7)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTCONVERGED", "ENONFINITE", "ESTATE"]
 SCHEMES = {"ars2": 0, "ars3": 1, "rk2": 2, "rk3": 3}
 PRECISIONS = {"fp64": 0, "mixed": 1}
-LOCAL_PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
+LOCAL_PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2, "f32x2": 3}
 BOUNDARIES = {"periodic": 0, "wall": 1, "vortex": 2}
 
 EXPORTS = ["hdgdg_bytes_required", "hdgdg_node_coords", "hdgdg_create", "hdgdg_set_state",

@@ -162,3 +162,30 @@ def test_fp32_variant_of_the_8x8_bump_200_steps():
     e, r_eta = _bump8_run("fp32", 200)
     print(f"local fp32, 200 steps: energy-norm rel {e:.3e}, eta rel {r_eta:.3e}")
     assert e <= 1e-4 and r_eta <= 1e-4
+
+
+@pytest.mark.parametrize("N,k", [(6, 3), (9, 2), (5, 4)])
+def test_f32x2_local_operators_are_fp64_class(N, k):
+    """HDGDG_LOCAL_F32X2 (FP32-pair operator, compensated Dot2 sums): condensation and a whole
+    stage solve agree with the FP64 local operators to ~1e-13, far below FP32's ~1e-7."""
+    m, h, hu, hv, b = user_state(N, k, "large")
+    q, phiB = oracle_state(m, h, hu, hv, b)
+    dt = 0.4 / N
+    R1 = q + 0.01 * rng.standard_normal(q.shape)
+    with hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, local_precision="f32x2") as s:
+        gx = s.condense_rhs(flat(R1))
+        Qx, _, _ = s.stage_solve(flat(R1))
+    with hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0) as s:
+        g64 = s.condense_rhs(flat(R1))
+        Q64, _, _ = s.stage_solve(flat(R1))
+    assert np.abs(gx - g64).max() <= 1e-12 * np.abs(g64).max()
+    assert np.abs(Qx - Q64).max() <= 1e-12 * np.abs(Q64).max()
+
+
+def test_f32x2_mixed_bump8_200_steps_against_the_oracle():
+    """The mixed form with FP32-pair local contractions over the 8x8 bump's 200 steps stays as
+    close to the FP64 oracle as the mixed form with FP64 local contractions (energy norm and
+    eta <= 1e-6; FP32 local contractions end at 2.7e-5)."""
+    e, r_eta = _bump8_run("f32x2", 200)
+    print(f"local f32x2, 200 steps: energy-norm rel {e:.3e}, eta rel {r_eta:.3e}")
+    assert e <= 1e-6 and r_eta <= 1e-6
