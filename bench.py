@@ -56,6 +56,8 @@ def _args():
                     help="FP32 inner SpMV: 0 plain (x gathered through shared memory), 1 pipelined bulk copies")
     ap.add_argument("--ortho", type=int, default=0, choices=[0, 1],
                     help="Gram-Schmidt of the mixed form's inner cycles: 0 twice (CGS2), 1 once")
+    ap.add_argument("--residual-f32x2", type=int, default=0, choices=[0, 1],
+                    help="mixed form: refinement residual in FP32-pair (FP64-class) arithmetic")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true",
@@ -606,7 +608,8 @@ def main():
                      krylov_restart=args.restart, precision=precision,
                      krylov_rtol=args.mixed_rtol if precision == "mixed" else 0.0,
                      local_precision=args.local if precision == "mixed" else "fp64",
-                     krylov_guess=args.guess, spmv_kernel=args.spmv_kernel, krylov_ortho=args.ortho)
+                     krylov_guess=args.guess, spmv_kernel=args.spmv_kernel, krylov_ortho=args.ortho,
+                     residual_f32x2=bool(args.residual_f32x2) and precision == "mixed")
         sim.set_state(h, hu, hv)
         for _ in range(args.warmup):
             sim.step(1)

@@ -127,6 +127,9 @@ typedef struct {
     int krylov_ortho;    /* Gram-Schmidt of the mixed form's FP32 inner cycles: 0 = classical,
                             applied twice (CGS2); 1 = classical, once.  The FP64 form and the
                             FP64 refinement residuals are not affected. */
+    int residual_f32x2;  /* mixed form: 1 = the refinement's true residual g - S qhat in FP64-class
+                            arithmetic on the FP32 pipes (S as an FP32 pair, compensated Dot2
+                            sums, ~1e-13 relative; see HDGDG_LOCAL_F32X2); 0 = FP64. */
 } hdgdg_config;
 
 /* HDGDG_VORTEX: the exact-solution boundary conditions of the paper's moving-vortex test

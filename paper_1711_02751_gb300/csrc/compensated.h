@@ -1,0 +1,42 @@
+// FP64-class sums on the FP32 pipes.  GB300 issues FP32 FMAs at 64x its FP64 rate, so FP64-bound
+// contractions keep their operand as an unevaluated pair of FP32 arrays (a = a_hi + a_lo, the
+// same 8 bytes per entry as FP64) and form each dot product with the compensated Dot2 of Ogita,
+// Rump and Oishi (SIAM J. Sci. Comput. 26, 2005): the products a_hi x_hi are split exactly with
+// Dekker's TwoProduct (via FMA) and summed with Knuth's TwoSum, and the cross terms
+// a_hi x_lo + a_lo x_hi are added in FP32.  The result carries about 48 bits (~1e-13 relative,
+// against 1e-16 for FP64 arithmetic) at the memory bound instead of the FP64 bound.  The
+// explicit _rn intrinsics keep the compiler from fusing the steps.
+#pragma once
+
+namespace hdgdg {
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+struct Dot2 {
+    float p = 0.f, c = 0.f;   // running sum and its accumulated correction
+    __device__ __forceinline__ void add(float ah, float al, float xh, float xl) {
+        float h, r, q;
+        two_prod(ah, xh, h, r);
+        two_sum(p, h, p, q);
+        c = __fadd_rn(c, __fadd_rn(q, r));
+        c = __fmaf_rn(ah, xl, c);
+        c = __fmaf_rn(al, xh, c);
+    }
+    __device__ __forceinline__ double value() const { return (double)p + (double)c; }
+};
+
+__device__ __forceinline__ void split(double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+}  // namespace hdgdg

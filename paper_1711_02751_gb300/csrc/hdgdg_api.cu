@@ -50,7 +50,7 @@ bool valid(const hdgdg_config* c) {
            c->local_precision <= HDGDG_LOCAL_F32X2 &&
            (c->local_precision != HDGDG_LOCAL_BF16 || c->degree_k <= 4) &&   // tensor-core tiles: k <= 4
            c->krylov_guess >= -1 && c->krylov_guess <= 3 && (c->spmv_kernel == 0 || c->spmv_kernel == 1) &&
-           (c->krylov_ortho == 0 || c->krylov_ortho == 1);
+           (c->krylov_ortho == 0 || c->krylov_ortho == 1) && (c->residual_f32x2 == 0 || c->residual_f32x2 == 1);
 }
 
 bool explicit_scheme(const hdgdg_config* c) { return c->scheme == HDGDG_RK2 || c->scheme == HDGDG_RK3; }
@@ -101,6 +101,7 @@ Plan make_plan(const hdgdg_config* c) {
     if (c->local_precision == HDGDG_LOCAL_FP32) b += n_el * (size_t)p.NV * p.NV * sizeof(float);
     if (c->local_precision == HDGDG_LOCAL_BF16) b += tc_image_bytes((int)P);
     if (c->local_precision == HDGDG_LOCAL_F32X2) b += 2 * n_el * (size_t)p.NV * p.NV * sizeof(float);
+    if (c->precision == HDGDG_MIXED && c->residual_f32x2) b += n_edges * 6 * (size_t)p.NF * p.NF * sizeof(float);
     b += 2 * (size_t)guess_order(c) * p.s * p.nt * d;         // previous stage solutions and products
     p.persistent = b;
     p.setup_temp = n_el * (size_t)p.NT * p.NT * d + n_edges * 7 * (size_t)p.NF * p.NF * d;
@@ -276,6 +277,7 @@ struct hdgdg_sim {
     double *NLs[kMaxStages] = {}, *Ls[kMaxStages] = {};
     double *gvec = nullptr, *xt = nullptr, *lam = nullptr, *w = nullptr, *V = nullptr, *fface = nullptr;
     float *Stil32 = nullptr, *V32 = nullptr, *w32 = nullptr;   // mixed precision only
+    float* Stil_lo = nullptr;   // residual_f32x2: S~ = Stil32 + Stil_lo
     double *red = nullptr, *mred = nullptr, *dvals = nullptr;
     GmresCtl* ctl = nullptr;
     CycleGraph cycle_graph[4];   // [FP64 form, mixed form] x [timers off, on]
@@ -529,7 +531,9 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
                                      !(kMixed && sim->cfg.krylov_ortho == 1), st, done);
         }
         if (e == cudaSuccess) e = launch_gmres_update(V, n, ctl, sim->xt, n, st);
-        if (e == cudaSuccess) e = launch_spmv_pre(sim->g, sim->Stil, sim->Scol, sim->xt, sim->w, st);
+        if (e == cudaSuccess)   // the true residual that ends the cycle
+            e = (kMixed && sim->Stil_lo) ? launch_spmv_x2(sim->g, sim->Stil32, sim->Stil_lo, sim->Scol, sim->xt, sim->w, st)
+                                         : launch_spmv_pre(sim->g, sim->Stil, sim->Scol, sim->xt, sim->w, st);
         CombineTerms t{};
         t.n = 1;
         t.X[0] = sim->w;
@@ -812,6 +816,7 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
         }
     if (c->precision == HDGDG_MIXED) {
         TRY(dalloc(sim, &sim->Stil32, (size_t)g.n_edges * 6 * p.NF * p.NF));
+        if (c->residual_f32x2) TRY(dalloc(sim, &sim->Stil_lo, (size_t)g.n_edges * 6 * p.NF * p.NF));
         TRY(dalloc(sim, &sim->V32, (size_t)(p.m + 1) * p.nt));
         TRY(dalloc(sim, &sim->w32, p.nt));
     } else {
@@ -844,8 +849,13 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
     cudaError_t e = launch_build_local(g, sim->phiB, sim->tau, c->dt * sim->a_ii, sim->Ainv, Se, dsing, sim->stream);
     if (e == cudaSuccess)
         e = launch_assemble_trace(g, Se, S7, sim->Srr, sim->Minv, sim->Stil, sim->Scol, dsing, sim->stream);
-    if (e == cudaSuccess && c->precision == HDGDG_MIXED)
-        e = launch_to_f32(sim->Stil, sim->Stil32, (size_t)g.n_edges * 6 * p.NF * p.NF, sim->stream);
+    if (e == cudaSuccess && c->precision == HDGDG_MIXED) {
+        if (sim->Stil_lo)   // hi part = the FP32 copy of the inner cycles, lo part = the rest
+            e = launch_split_f32x2(sim->Stil, sim->Stil32, sim->Stil_lo, (size_t)g.n_edges * 6 * p.NF * p.NF,
+                                   sim->stream);
+        else
+            e = launch_to_f32(sim->Stil, sim->Stil32, (size_t)g.n_edges * 6 * p.NF * p.NF, sim->stream);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
     cudaFree(Se);
     cudaFree(S7);

@@ -14,6 +14,7 @@
 // B acts only on boundary volume nodes: B = -beta tau with beta = dt a (2/h) / w_0.
 // Schur complement (eq. linearizedHDGsystem_schur): S = D - C A^{-1} B, rhs -C A^{-1} R1;
 // recovery (eq. recover_volume_unknowns): Q = A^{-1}(R1 - B Qhat).
+#include "compensated.h"
 #include "internal.h"
 
 namespace hdgdg {
@@ -288,43 +289,7 @@ __global__ void apply_ainv_kernel(Geom g, const T* __restrict__ Ainv, const doub
     Z[(r / Np) * fs + (size_t)e * Np + r % Np] = (double)acc;
 }
 
-// ---- FP64-class local contractions on the FP32 pipes -------------------------------------------
-// GB300 issues FP32 FMAs at 64x the FP64 rate, so A^{-1} is held as an unevaluated pair of FP32
-// arrays (a = a_hi + a_lo, the same 8 bytes per entry as FP64) and each row's dot product runs as
-// the compensated Dot2 of Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26, 2005): the products
-// a_hi x_hi are split exactly with Dekker's TwoProduct (via FMA) and summed with Knuth's TwoSum,
-// the cross terms a_hi x_lo + a_lo x_hi are added in FP32.  The result carries about 48 bits --
-// ~1e-13 relative, against 1e-16 for FP64 arithmetic -- at the HBM bound instead of the FP64
-// bound.  The explicit _rn intrinsics keep the compiler from fusing the steps.
-__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
-    p = __fmul_rn(a, b);
-    e = __fmaf_rn(a, b, -p);
-}
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = __fadd_rn(a, b);
-    const float z = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
-}
-
-struct Dot2 {
-    float p = 0.f, c = 0.f;   // running sum and its accumulated correction
-    __device__ __forceinline__ void add(float ah, float al, float xh, float xl) {
-        float h, r, q;
-        two_prod(ah, xh, h, r);
-        two_sum(p, h, p, q);
-        c = __fadd_rn(c, __fadd_rn(q, r));
-        c = __fmaf_rn(ah, xl, c);
-        c = __fmaf_rn(al, xh, c);
-    }
-    __device__ __forceinline__ double value() const { return (double)p + (double)c; }
-};
-
-__device__ __forceinline__ void split(double v, float& hi, float& lo) {
-    hi = (float)v;
-    lo = (float)(v - (double)hi);
-}
-
+// ---- FP64-class local contractions on the FP32 pipes (compensated.h) ---------------------------
 __global__ void split_kernel(const double* __restrict__ a, float* __restrict__ hi, float* __restrict__ lo,
                              size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)

@@ -13,6 +13,7 @@
 #include <algorithm>
 
 #include "async_copy.h"
+#include "compensated.h"
 #include "internal.h"
 
 namespace hdgdg {
@@ -48,6 +49,37 @@ spmv_pre_kernel(int n_edges, const T* __restrict__ Stil, const int* __restrict__
         for (int jj = 0; jj < NF; ++jj) acc += Sb[jj * NF + ii] * sx[le][sl][jj];
     }
     y[(size_t)r * NF + ii] = acc;
+}
+
+// The same product in FP64-class arithmetic on the FP32 pipes (compensated.h): S~ as an FP32
+// pair, x split into a pair while it is gathered, each component a Dot2 sum; y = x + that sum.
+template <int NF>
+__global__ void __launch_bounds__(256)
+spmv_x2_kernel(int n_edges, const float* __restrict__ Shi, const float* __restrict__ Slo,
+               const int* __restrict__ Scol, const double* __restrict__ x, double* __restrict__ y) {
+    constexpr int EPB = 256 / NF;
+    __shared__ float sxh[EPB][6][NF], sxl[EPB][6][NF];
+    const int le = threadIdx.x / NF, ii = threadIdx.x % NF;
+    const int r = blockIdx.x * EPB + le;
+    const bool live = le < EPB && r < n_edges;
+    if (live) {
+#pragma unroll
+        for (int sl = 0; sl < 6; ++sl)
+            split(x[(size_t)__ldg(Scol + (size_t)r * 6 + sl) * NF + ii], sxh[le][sl][ii], sxl[le][sl][ii]);
+    }
+    __syncthreads();
+    if (!live) return;
+    const size_t base = (size_t)r * 6 * NF * NF;
+    Dot2 acc;
+#pragma unroll
+    for (int sl = 0; sl < 6; ++sl) {
+#pragma unroll
+        for (int jj = 0; jj < NF; ++jj) {
+            const size_t o = base + (size_t)sl * NF * NF + jj * NF + ii;
+            acc.add(Shi[o], Slo[o], sxh[le][sl][jj], sxl[le][sl][jj]);
+        }
+    }
+    y[(size_t)r * NF + ii] = x[(size_t)r * NF + ii] + acc.value();
 }
 
 // The same product with the matrix streamed through shared memory: a persistent CTA takes
@@ -577,6 +609,22 @@ cudaError_t launch_spmv_pre(const Geom& g, const float* Stil, const int* Scol, c
     }
 }
 
+
+cudaError_t launch_spmv_x2(const Geom& g, const float* Shi, const float* Slo, const int* Scol, const double* x,
+                           double* y, cudaStream_t s) {
+#define CASE(P, NF)                                                                                     \
+    case P: {                                                                                           \
+        constexpr int EPB = 256 / NF;                                                                   \
+        spmv_x2_kernel<NF><<<(g.n_edges + EPB - 1) / EPB, EPB * NF, 0, s>>>(g.n_edges, Shi, Slo, Scol, x, y); \
+        count_launches(1);                                                                              \
+        return cudaGetLastError();                                                                      \
+    }
+    switch (g.P) {
+        CASE(2, 6) CASE(3, 9) CASE(4, 12) CASE(5, 15) CASE(6, 18) CASE(7, 21) CASE(8, 24) CASE(9, 27)
+        default: return cudaErrorInvalidValue;
+    }
+#undef CASE
+}
 
 cudaError_t launch_block_diag(const Geom& g, const double* Bd, const double* x, double* y,
                               cudaStream_t s) {

@@ -92,3 +92,22 @@ def test_single_pass_gram_schmidt_in_the_inner_cycles():
             s.step(20)
             outs.append(swe.to_state(*s.get_state(), b, W.G, W.H0)[0])
     assert max(imex.rel_l2(m, outs[0][c], outs[1][c]) for c in range(3)) <= 1e-6
+
+
+def test_fp32_pair_refinement_residual():
+    """residual_f32x2: the mixed form's refinement residual in FP64-class arithmetic on the FP32
+    pipes (~1e-13 relative) gives the same iteration counts and stays within 1e-6 of the FP64
+    form and within 1e-8 of the mixed form with an FP64 residual."""
+    m, h, hu, hv, b = user_state(16, 3, "large")
+    dt = dt_of(m, h, hu, hv)
+    outs, its = [], []
+    for kw in ({"precision": "mixed", "residual_f32x2": True, "local_precision": "f32x2"},
+               {"precision": "mixed"}, {"precision": "fp64"}):
+        with hd.Sim(16, 3, dt, bottom=b, **kw) as s:
+            s.set_state(h, hu, hv)
+            s.step(20)
+            outs.append(swe.to_state(*s.get_state(), b, W.G, W.H0)[0])
+            its.append(s.stats()["krylov_iterations"])
+    assert its[0] == its[1]
+    assert max(imex.rel_l2(m, outs[0][c], outs[2][c]) for c in range(3)) <= 1e-6
+    assert max(imex.rel_l2(m, outs[0][c], outs[1][c]) for c in range(3)) <= 1e-8
