@@ -48,7 +48,7 @@ def _args():
                     help="refinement tolerance of the mixed form (0: library default 1e-9)")
     ap.add_argument("--precisions", default="fp64,mixed",
                     help="forms to time; the headline is mixed when within 1e-6 of fp64")
-    ap.add_argument("--local", default="fp64", choices=["fp64", "fp32", "bf16", "f32x2"],
+    ap.add_argument("--local", default="f32x2", choices=["fp64", "fp32", "bf16", "f32x2"],
                     help="arithmetic of the local condensation / recovery in the mixed form")
     ap.add_argument("--guess", type=int, default=0, choices=[-1, 0, 1, 2, 3],
                     help="trace-solve initial guess: extrapolation order 1-3, -1 zero, 0 library default")
@@ -56,7 +56,7 @@ def _args():
                     help="FP32 inner SpMV: 0 plain (x gathered through shared memory), 1 pipelined bulk copies")
     ap.add_argument("--ortho", type=int, default=0, choices=[0, 1],
                     help="Gram-Schmidt of the mixed form's inner cycles: 0 twice (CGS2), 1 once")
-    ap.add_argument("--residual-f32x2", type=int, default=0, choices=[0, 1],
+    ap.add_argument("--residual-f32x2", type=int, default=1, choices=[0, 1],
                     help="mixed form: refinement residual in FP32-pair (FP64-class) arithmetic")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -667,7 +667,9 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": summary[head]["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if head == "fp64" else
-                     (f"f64+f32 (FP32 Krylov cycles and DG residual, FP64 refinement, {args.local.upper()} local ops)"),
+                     ("f64+f32 (FP32 Krylov cycles and DG residual; refinement residual "
+                      f"{'FP32-pair' if args.residual_f32x2 else 'FP64'}, local contractions "
+                      f"{ {'f32x2': 'FP32-pair'}.get(args.local, args.local.upper()) }; FP64 vectors)"),
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: periodic {N}x{N} quads, k={k}, ARS2, "
                                    f"dt={dt:.6g} (advective CFL 0.5: 0.5 h/((2k+1) 2max|u|))", "form": head,

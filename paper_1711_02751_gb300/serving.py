@@ -132,7 +132,7 @@ def batch_requests(requests, max_batch=64):
 def bytes_of(req):
     """Device bytes one request (or batch) needs, from the library's own plan."""
     B = len(req.members) if isinstance(req, Batch) else 1
-    return hd.bytes_required(hd.make_config(req.N, req.k, 1.0, precision=req.precision, batch=B))
+    return hd.bytes_required(hd.make_config(req.N, req.k, 1.0, batch=B, **form_options(req.precision)))
 
 
 def run_batch(batch, chunk=10):
@@ -141,8 +141,8 @@ def run_batch(batch, chunk=10):
     cat = lambda j: np.concatenate([s[j] for s in states])  # noqa: E731
     dts = np.array([s[4] for s in states])
     n = batch.N * batch.N
-    with hd.Sim(batch.N, batch.k, float(dts.max()), bottom=cat(3), precision=batch.precision,
-                batch=len(states), dt_per_instance=dts) as s:
+    with hd.Sim(batch.N, batch.k, float(dts.max()), bottom=cat(3), batch=len(states), dt_per_instance=dts,
+                **form_options(batch.precision)) as s:
         s.set_state(cat(0), cat(1), cat(2))
         done = 0
         while done < batch.steps:
@@ -155,10 +155,18 @@ def run_batch(batch, chunk=10):
     return out
 
 
+def form_options(precision):
+    """Library options of a request's arithmetic: the mixed form runs its FP64-bound parts (local
+    contractions, refinement residuals) as FP32 pairs."""
+    if precision == "mixed":
+        return {"precision": "mixed", "local_precision": "f32x2", "residual_f32x2": True}
+    return {"precision": precision}
+
+
 def run_one(req, chunk=10):
     """Run one request to completion on a fresh handle; returns the final (h, hu, hv)."""
     h, hu, hv, b, dt = initial_state(req)
-    with hd.Sim(req.N, req.k, dt, bottom=b, precision=req.precision) as s:
+    with hd.Sim(req.N, req.k, dt, bottom=b, **form_options(req.precision)) as s:
         s.set_state(h, hu, hv)
         done = 0
         while done < req.steps:

@@ -97,7 +97,9 @@ def test_single_pass_gram_schmidt_in_the_inner_cycles():
 def test_fp32_pair_refinement_residual():
     """residual_f32x2: the mixed form's refinement residual in FP64-class arithmetic on the FP32
     pipes (~1e-13 relative) gives the same iteration counts and stays within 1e-6 of the FP64
-    form and within 1e-8 of the mixed form with an FP64 residual."""
+    form.  Against the mixed form with an FP64 residual the bound is 1e-7: both stop at the
+    refinement tolerance 1e-9 per solve, so they differ by that tolerance accumulated over the
+    40 stage solves (2.2e-8 measured)."""
     m, h, hu, hv, b = user_state(16, 3, "large")
     dt = dt_of(m, h, hu, hv)
     outs, its = [], []
@@ -110,4 +112,4 @@ def test_fp32_pair_refinement_residual():
             its.append(s.stats()["krylov_iterations"])
     assert its[0] == its[1]
     assert max(imex.rel_l2(m, outs[0][c], outs[2][c]) for c in range(3)) <= 1e-6
-    assert max(imex.rel_l2(m, outs[0][c], outs[1][c]) for c in range(3)) <= 1e-8
+    assert max(imex.rel_l2(m, outs[0][c], outs[1][c]) for c in range(3)) <= 1e-7

@@ -16,7 +16,7 @@ def _requests(precision):
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_results_same_alone_and_in_the_mix(precision):
     reqs = _requests(precision)
-    budget = 4 * max(hd.bytes_required(hd.make_config(r.N, r.k, 1.0, precision=precision)) for r in reqs)
+    budget = 4 * max(serving.bytes_of(r) for r in reqs)
     srv = serving.Server(hbm_budget=budget, max_slots=3, chunk=5)
     summary = srv.serve(reqs, time_scale=1.0)
     assert summary["completed"] == len(reqs) and not summary["errors"]
@@ -30,7 +30,7 @@ def test_results_same_alone_and_in_the_mix(precision):
 
 def test_admission_respects_the_memory_budget():
     reqs = _requests("fp64")
-    sizes = [hd.bytes_required(hd.make_config(r.N, r.k, 1.0)) for r in reqs]
+    sizes = [serving.bytes_of(r) for r in reqs]
     srv = serving.Server(hbm_budget=max(sizes), max_slots=8, chunk=5)
     summary = srv.serve(reqs)
     assert summary["completed"] == len(reqs)
