@@ -113,6 +113,13 @@ dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict_
     constexpr int EPB = DgTile<P>::EPB;
     __shared__ Tc sF[EPB][4][Np];   // fxU, fxV, fyU, fyV
     __shared__ Tc sM[FULL ? EPB : 1][3][Np];   // FULL: U, V and phi_B for the mass flux and source
+    // the derivative matrices, read below with a thread-dependent row: from shared memory, since
+    // the kernel-parameter (constant) bank serialises a warp's loads of different addresses
+    __shared__ Tc sDh[Np], sD[Np];
+    if (threadIdx.x < Np) {
+        sDh[threadIdx.x] = Tc(g.Dhat[threadIdx.x]);
+        sD[threadIdx.x] = Tc(g.D[threadIdx.x]);
+    }
 
     const int le = threadIdx.x / Np;
     const int n = threadIdx.x % Np;
@@ -141,8 +148,8 @@ dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict_
     Tc rU = Tc(0), rV = Tc(0), rph = Tc(0);
 #pragma unroll
     for (int a = 0; a < P; ++a) {
-        const Tc cx = Tc(g.Dhat[i * P + a]);
-        const Tc cy = Tc(g.Dhat[j * P + a]);
+        const Tc cx = sDh[i * P + a];
+        const Tc cy = sDh[j * P + a];
         rU += cx * sF[le][0][j * P + a] + cy * sF[le][2][a * P + i];
         rV += cx * sF[le][1][j * P + a] + cy * sF[le][3][a * P + i];
         if (FULL) rph += cx * sM[le][0][j * P + a] + cy * sM[le][1][a * P + i];
@@ -155,8 +162,8 @@ dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict_
         Tc dBx = Tc(0), dBy = Tc(0);
 #pragma unroll
         for (int a = 0; a < P; ++a) {
-            dBx += Tc(g.D[i * P + a]) * sM[le][2][j * P + a];
-            dBy += Tc(g.D[j * P + a]) * sM[le][2][a * P + i];
+            dBx += sD[i * P + a] * sM[le][2][j * P + a];
+            dBy += sD[j * P + a] * sM[le][2][a * P + i];
         }
         rU += ph_own * th * dBx;
         rV += ph_own * th * dBy;
