@@ -113,3 +113,46 @@ def test_fp32_pair_refinement_residual():
     assert its[0] == its[1]
     assert max(imex.rel_l2(m, outs[0][c], outs[2][c]) for c in range(3)) <= 1e-6
     assert max(imex.rel_l2(m, outs[0][c], outs[1][c]) for c in range(3)) <= 1e-7
+
+
+@pytest.mark.parametrize("case", ["walls", "vortex", "batch", "k1", "k7"])
+def test_bench_mixed_form_across_configurations(case):
+    """The mixed form as bench.py and the serving loop run it (FP32 Krylov cycles and DG residual,
+    FP32-pair local contractions and refinement residual) against the FP64 form: <= 1e-6 after
+    10 steps on walls, prescribed vortex traces, a batch with unequal time steps, k = 1 and k = 7."""
+    import numpy as np
+    fast = {"precision": "mixed", "local_precision": "f32x2", "residual_f32x2": True}
+    kw, N, k, B = {}, 8, 3, 1
+    if case == "k1":
+        N, k = 16, 1
+    if case == "k7":
+        N, k = 4, 7
+    if case == "vortex":
+        V = W.VORTEX
+        kw = dict(boundary="vortex", x0=-2.0, length=4.0, g=V["g"], H0=V["H_inf"],
+                  bc_params=(V["beta"], V["u_inf"], V["v_inf"], V["xc"], V["yc"]))
+        x, y = hd.node_coords(N, k, boundary="vortex", x0=-2.0, length=4.0)
+        h, hu, hv, b = W.vortex_state(x, y, 0.0, **V)
+        dt = 0.02
+    else:
+        bnd = "wall" if case == "walls" else "periodic"
+        kw = dict(boundary=bnd)
+        x, y = hd.node_coords(N, k, boundary=bnd)
+        h, hu, hv, b = W.large_state(x, y, seed=21)
+        if case == "walls":
+            hu, hv = 0.0 * hu, 0.0 * hv
+        dt = W.advective_dt(x, h, hu, hv, N)
+    if case == "batch":
+        B = 3
+        kw["batch"], kw["dt_per_instance"] = B, [dt, 0.7 * dt, 0.4 * dt]
+        h, hu, hv, b = (np.concatenate([a] * B) for a in (h, hu, hv, b))
+    outs = []
+    for form in (fast, {"precision": "fp64"}):
+        with hd.Sim(N, k, dt, bottom=b, **form, **kw) as s:
+            s.set_state(h, hu, hv)
+            s.step(10)
+            outs.append(s.get_state())
+    B0 = (kw.get("H0", W.H0)) - b
+    for a, r, base in zip(outs[0], outs[1], (B0, 0.0, 0.0)):
+        ra, rr = a - base, r - base
+        assert np.linalg.norm(ra - rr) <= 1e-6 * np.linalg.norm(rr)
