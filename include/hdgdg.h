@@ -211,6 +211,21 @@ hdgdg_status hdgdg_get_state(hdgdg_sim* sim, double* h, double* hu, double* hv);
 /* Counters of the run so far; computes the mass of the current state on the device. */
 hdgdg_status hdgdg_get_stats(hdgdg_sim* sim, hdgdg_stats* out);
 
+/* Checkpoint / resume (the paper has no counterpart; long runs and preempted serving
+ * requests).  A checkpoint holds the state, the simulated time, the counters and the trace
+ * solve's initial-guess history, so that a handle created with the same configuration and
+ * bottom, loaded from it, continues bit for bit as the uninterrupted run.  The layout is this
+ * library version's, host byte order.  hdgdg_checkpoint_bytes: the size a checkpoint of the
+ * current state needs (0 before set_state).  hdgdg_save_checkpoint copies it into the caller's
+ * host buffer buf of `bytes` (EINVAL if too small, ESTATE before set_state).
+ * hdgdg_load_checkpoint replaces the handle's state and history from buf; EINVAL if buf is not a
+ * checkpoint, is truncated, or was taken with another mesh, degree, scheme, arithmetic,
+ * boundary, batch, time step, g, H0 or domain.  The bottom is not recorded: pass the same bottom
+ * to hdgdg_create. */
+size_t hdgdg_checkpoint_bytes(hdgdg_sim* sim);
+hdgdg_status hdgdg_save_checkpoint(hdgdg_sim* sim, void* buf, size_t bytes);
+hdgdg_status hdgdg_load_checkpoint(hdgdg_sim* sim, const void* buf, size_t bytes);
+
 /* Message of the last failure on this handle ("" if none; a static message if sim is NULL). */
 const char* hdgdg_last_error(const hdgdg_sim* sim);
 

@@ -21,6 +21,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hdgdg.h"
 #include "internal.h"
 
@@ -243,6 +245,15 @@ Geom host_geom(int N, int k) {
 struct TimerPair {
     cudaEvent_t a, b;
     int cls, slot;
+};
+
+// NVTX range for profilers (a no-op unless one is attached): time steps, stage solves and
+// GMRES restart cycles show up on their timelines.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 struct CycleGraph {
@@ -575,6 +586,7 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
             cg.launches = launches_total() - l0;
             count_launches((int)-cg.launches);   // counted again at every replay below
         }
+        NvtxRange nv_cycle("gmres_cycle");
         CU(cudaGraphLaunch(cg.exec, st));
         count_launches((int)cg.launches);
         CU(cudaStreamSynchronize(st));
@@ -632,6 +644,7 @@ double beta_of(const hdgdg_sim* sim) { return sim->cfg.dt * sim->a_ii * sim->g.t
 // One implicit stage: R1 (device) -> Q, Lst = dt M^{-1} L (device); qhat left in sim->lam.
 hdgdg_status stage_solve_dev(hdgdg_sim* sim, const double* R1, double* Q, double* Lst, int* its,
                              double t_stage = 0.0, int stage = -1) {
+    NvtxRange nv("stage_solve");
     double rr;
     {
         TimedGroup tg(sim, HDGDG_KT_CONDENSE);
@@ -652,6 +665,7 @@ hdgdg_status stage_solve_dev(hdgdg_sim* sim, const double* R1, double* Q, double
 //   RK2 (Heun):        q1 = q + K1;                 q' = q + K1/2 + K2/2
 //   RK3 (Shu-Osher):   q1 = q + K1;  q2 = q + K1/4 + K2/4;  q' = q + K1/6 + K2/6 + 2 K3/3
 hdgdg_status explicit_step(hdgdg_sim* sim) {
+    NvtxRange nv("time_step");
     const size_t n3 = 3 * sim->plan.n;
     cudaStream_t st = sim->stream;
     const double dt = sim->cfg.dt;
@@ -692,6 +706,7 @@ hdgdg_status explicit_step(hdgdg_sim* sim) {
 }
 
 hdgdg_status one_step(hdgdg_sim* sim) {
+    NvtxRange nv("time_step");
     if (explicit_scheme(&sim->cfg)) return explicit_step(sim);
     const size_t n3 = 3 * sim->plan.n;
     cudaStream_t st = sim->stream;
@@ -1072,6 +1087,118 @@ hdgdg_status hdgdg_get_state(hdgdg_sim* sim, double* h, double* hu, double* hv) 
     CU(cudaMemcpyAsync(hu, stg + n, n * sizeof(double), cudaMemcpyDeviceToHost, sim->stream));
     CU(cudaMemcpyAsync(hv, stg + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost, sim->stream));
     return sync(sim);
+}
+
+}  // extern "C"
+
+// ---- checkpoint / resume -------------------------------------------------------------------
+namespace {
+struct CheckpointHeader {
+    char magic[8];                 // "HDGDGCK1"
+    int n_side, degree_k, scheme, precision, boundary, batch, local_precision, guess, stages;
+    long long n_state, n_trace;    // doubles in the state, in one trace vector
+    double dt, g, H0, x0, length;
+    double t;
+    hdgdg_stats stats;
+    int n_hist[kMaxStages];        // guess history kept per stage (newest first)
+};
+
+int history_slots(const hdgdg_sim* sim) { return explicit_scheme(&sim->cfg) ? 0 : guess_order(&sim->cfg); }
+
+size_t checkpoint_size(const hdgdg_sim* sim) {
+    size_t b = sizeof(CheckpointHeader) + 3 * sim->plan.n * sizeof(double);
+    for (int i = 0; i < sim->s; ++i) b += 2 * (size_t)sim->n_hist[i] * sim->plan.nt * sizeof(double);
+    return b;
+}
+
+void fill_header(const hdgdg_sim* sim, CheckpointHeader* h) {
+    std::memset(h, 0, sizeof(*h));
+    std::memcpy(h->magic, "HDGDGCK1", 8);
+    const hdgdg_config& c = sim->cfg;
+    h->n_side = c.n_side;
+    h->degree_k = c.degree_k;
+    h->scheme = c.scheme;
+    h->precision = c.precision;
+    h->boundary = c.boundary;
+    h->batch = sim->g.batch;
+    h->local_precision = c.local_precision;
+    h->guess = history_slots(sim);
+    h->stages = sim->s;
+    h->n_state = (long long)(3 * sim->plan.n);
+    h->n_trace = (long long)sim->plan.nt;
+    h->dt = c.dt;
+    h->g = c.g;
+    h->H0 = c.H0;
+    h->x0 = c.x0;
+    h->length = c.length;
+}
+}  // namespace
+
+extern "C" {
+
+size_t hdgdg_checkpoint_bytes(hdgdg_sim* sim) {
+    if (!sim || !sim->have_state) return 0;
+    return checkpoint_size(sim);
+}
+
+hdgdg_status hdgdg_save_checkpoint(hdgdg_sim* sim, void* buf, size_t bytes) {
+    if (!sim || !buf) return fail(sim, HDGDG_EINVAL, "NULL argument to save_checkpoint");
+    if (!sim->have_state) return fail(sim, HDGDG_ESTATE, "save_checkpoint before set_state");
+    if (bytes < checkpoint_size(sim))
+        return fail(sim, HDGDG_EINVAL, "checkpoint buffer of %zu bytes, %zu needed", bytes, checkpoint_size(sim));
+    auto* h = static_cast<CheckpointHeader*>(buf);
+    fill_header(sim, h);
+    h->t = sim->t;
+    h->stats = sim->stats;
+    for (int i = 0; i < kMaxStages; ++i) h->n_hist[i] = i < sim->s ? sim->n_hist[i] : 0;
+    char* p = static_cast<char*>(buf) + sizeof(CheckpointHeader);
+    const size_t nq = 3 * sim->plan.n * sizeof(double), nt = sim->plan.nt * sizeof(double);
+    CU(cudaMemcpyAsync(p, sim->q, nq, cudaMemcpyDeviceToHost, sim->stream));
+    p += nq;
+    for (int i = 0; i < sim->s; ++i)
+        for (int j = 0; j < sim->n_hist[i]; ++j) {
+            CU(cudaMemcpyAsync(p, sim->xhist[i][j], nt, cudaMemcpyDeviceToHost, sim->stream));
+            CU(cudaMemcpyAsync(p + nt, sim->yhist[i][j], nt, cudaMemcpyDeviceToHost, sim->stream));
+            p += 2 * nt;
+        }
+    return sync(sim);
+}
+
+hdgdg_status hdgdg_load_checkpoint(hdgdg_sim* sim, const void* buf, size_t bytes) {
+    if (!sim || !buf) return fail(sim, HDGDG_EINVAL, "NULL argument to load_checkpoint");
+    if (bytes < sizeof(CheckpointHeader)) return fail(sim, HDGDG_EINVAL, "checkpoint shorter than its header");
+    const auto* h = static_cast<const CheckpointHeader*>(buf);
+    CheckpointHeader mine;
+    fill_header(sim, &mine);
+    if (std::memcmp(h->magic, mine.magic, 8) != 0) return fail(sim, HDGDG_EINVAL, "not a checkpoint of this library");
+    if (h->n_side != mine.n_side || h->degree_k != mine.degree_k || h->scheme != mine.scheme ||
+        h->precision != mine.precision || h->boundary != mine.boundary || h->batch != mine.batch ||
+        h->local_precision != mine.local_precision || h->guess != mine.guess || h->stages != mine.stages ||
+        h->n_state != mine.n_state || h->n_trace != mine.n_trace || h->dt != mine.dt || h->g != mine.g ||
+        h->H0 != mine.H0 || h->x0 != mine.x0 || h->length != mine.length)
+        return fail(sim, HDGDG_EINVAL, "checkpoint of a different configuration");
+    size_t need = sizeof(CheckpointHeader) + 3 * sim->plan.n * sizeof(double);
+    for (int i = 0; i < sim->s; ++i) {
+        if (h->n_hist[i] < 0 || h->n_hist[i] > mine.guess) return fail(sim, HDGDG_EINVAL, "corrupt checkpoint history");
+        need += 2 * (size_t)h->n_hist[i] * sim->plan.nt * sizeof(double);
+    }
+    if (bytes < need) return fail(sim, HDGDG_EINVAL, "checkpoint of %zu bytes, %zu expected", bytes, need);
+    const char* p = static_cast<const char*>(buf) + sizeof(CheckpointHeader);
+    const size_t nq = 3 * sim->plan.n * sizeof(double), nt = sim->plan.nt * sizeof(double);
+    CU(cudaMemcpyAsync(sim->q, p, nq, cudaMemcpyHostToDevice, sim->stream));
+    p += nq;
+    for (int i = 0; i < sim->s; ++i)
+        for (int j = 0; j < h->n_hist[i]; ++j) {
+            CU(cudaMemcpyAsync(sim->xhist[i][j], p, nt, cudaMemcpyHostToDevice, sim->stream));
+            CU(cudaMemcpyAsync(sim->yhist[i][j], p + nt, nt, cudaMemcpyHostToDevice, sim->stream));
+            p += 2 * nt;
+        }
+    TRY(sync(sim));
+    for (int i = 0; i < kMaxStages; ++i) sim->n_hist[i] = i < sim->s ? h->n_hist[i] : 0;
+    sim->t = h->t;
+    sim->stats = h->stats;
+    sim->have_state = true;
+    return HDGDG_OK;
 }
 
 hdgdg_status hdgdg_get_stats(hdgdg_sim* sim, hdgdg_stats* out) {

@@ -22,7 +22,8 @@ EXPORTS = ["hdgdg_bytes_required", "hdgdg_node_coords", "hdgdg_create", "hdgdg_s
            "hdgdg_step", "hdgdg_get_state", "hdgdg_get_stats", "hdgdg_last_error", "hdgdg_destroy",
            "hdgdg_update_state", "hdgdg_eval_nl", "hdgdg_condense_rhs", "hdgdg_trace_apply", "hdgdg_stage_solve",
            "hdgdg_measure_fp64_tflops", "hdgdg_set_kernel_timing", "hdgdg_kernel_time",
-           "hdgdg_mass_noalloc", "hdgdg_gll"]
+           "hdgdg_mass_noalloc", "hdgdg_gll", "hdgdg_checkpoint_bytes", "hdgdg_save_checkpoint",
+           "hdgdg_load_checkpoint"]
 KERNEL_CLASSES = ["spmv", "ortho", "condense", "recover", "dg", "combine"]
 
 
@@ -69,6 +70,10 @@ def lib():
         L.hdgdg_create.argtypes = [ctypes.POINTER(Config), _P, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
         L.hdgdg_set_state.argtypes = [ctypes.c_void_p, _P, _P, _P]
         L.hdgdg_update_state.argtypes = [ctypes.c_void_p, _P, _P, _P]
+        L.hdgdg_checkpoint_bytes.restype = ctypes.c_size_t
+        L.hdgdg_checkpoint_bytes.argtypes = [ctypes.c_void_p]
+        L.hdgdg_save_checkpoint.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
+        L.hdgdg_load_checkpoint.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
         L.hdgdg_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.hdgdg_get_state.argtypes = [ctypes.c_void_p, _P, _P, _P]
         L.hdgdg_get_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(Stats)]
@@ -236,6 +241,20 @@ class Sim:
         """update_state from raw host addresses (e.g. pinned buffers)."""
         self._check(lib().hdgdg_update_state(self._h, ctypes.cast(h_ptr, _P), ctypes.cast(hu_ptr, _P),
                                              ctypes.cast(hv_ptr, _P)))
+
+    def save_checkpoint(self):
+        """The state, time, counters and solver history as bytes (see hdgdg_save_checkpoint)."""
+        n = int(lib().hdgdg_checkpoint_bytes(self._h))
+        if n == 0:
+            raise HdgdgError(ESTATE, "save_checkpoint before set_state")
+        buf = ctypes.create_string_buffer(n)
+        self._check(lib().hdgdg_save_checkpoint(self._h, buf, n))
+        return buf.raw
+
+    def load_checkpoint(self, data):
+        """Continue from bytes written by save_checkpoint (same configuration and bottom)."""
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        self._check(lib().hdgdg_load_checkpoint(self._h, buf, len(data)))
 
     def step(self, n_steps=1):
         self._check(lib().hdgdg_step(self._h, int(n_steps)))
