@@ -51,7 +51,7 @@ bool valid(const hdgdg_config* c) {
            c->krylov_restart <= kMaxRestart && c->local_precision >= HDGDG_LOCAL_FP64 &&
            c->local_precision <= HDGDG_LOCAL_F32X2 &&
            (c->local_precision != HDGDG_LOCAL_BF16 || c->degree_k <= 4) &&   // tensor-core tiles: k <= 4
-           c->krylov_guess >= -1 && c->krylov_guess <= 3 && (c->spmv_kernel == 0 || c->spmv_kernel == 1) &&
+           c->krylov_guess >= -1 && c->krylov_guess <= 4 && (c->spmv_kernel == 0 || c->spmv_kernel == 1) &&
            (c->krylov_ortho == 0 || c->krylov_ortho == 1) && (c->residual_f32x2 == 0 || c->residual_f32x2 == 1);
 }
 
@@ -276,8 +276,8 @@ struct hdgdg_sim {
     // device memory
     std::vector<void*> allocs;
     double *phiB = nullptr, *tau = nullptr, *Ainv = nullptr, *Stil = nullptr, *Minv = nullptr, *Srr = nullptr;
-    double* xhist[kMaxStages][3] = {};   // trace-solve guess: preconditioned solutions of the last
-    double* yhist[kMaxStages][3] = {};   // steps per stage ([0] newest), their products S~ x~ (from
+    double* xhist[kMaxStages][4] = {};   // trace-solve guess: preconditioned solutions of the last
+    double* yhist[kMaxStages][4] = {};   // steps per stage ([0] newest), their products S~ x~ (from
     int n_hist[kMaxStages] = {};         // the final true residual: g - r), and their count
     float* Ainv32 = nullptr;      // HDGDG_LOCAL_FP32
     float *Ahi = nullptr, *Alo = nullptr;   // HDGDG_LOCAL_F32X2
@@ -496,7 +496,7 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
         CU(launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st));
     } else {
         // x0 = sum_j c_j x_{n-j}: the extrapolation polynomial through the last `guess` solutions
-        static const double coef[4][3] = {{0, 0, 0}, {1, 0, 0}, {2, -1, 0}, {3, -3, 1}};
+        static const double coef[5][4] = {{0, 0, 0, 0}, {1, 0, 0, 0}, {2, -1, 0, 0}, {3, -3, 1, 0}, {4, -6, 4, -1}};
         CombineTerms t{};
         for (int j = 0; j < guess; ++j) {
             t.X[t.n] = sim->xhist[stage][j];
@@ -542,15 +542,20 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
                                      !(kMixed && sim->cfg.krylov_ortho == 1), st, done);
         }
         if (e == cudaSuccess) e = launch_gmres_update(V, n, ctl, sim->xt, n, st);
-        if (e == cudaSuccess)   // the true residual that ends the cycle
-            e = (kMixed && sim->Stil_lo) ? launch_spmv_x2(sim->g, sim->Stil32, sim->Stil_lo, sim->Scol, sim->xt, sim->w, st)
-                                         : launch_spmv_pre(sim->g, sim->Stil, sim->Scol, sim->xt, sim->w, st);
-        CombineTerms t{};
-        t.n = 1;
-        t.X[0] = sim->w;
-        t.c[0] = -1.0;
-        if (e == cudaSuccess) e = launch_combine(n, g, t, sim->w, nullptr, st);
-        if (e == cudaSuccess) e = launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st);
+        // the true residual w = g - S~ x~ that ends the cycle, and ||w||^2
+        if (kMixed && sim->Stil_lo) {   // one fused FP32-pair pass
+            if (e == cudaSuccess)
+                e = launch_residual_norm_x2(sim->g, sim->Stil32, sim->Stil_lo, sim->Scol, sim->xt, g, sim->w,
+                                            sim->red, dv_nrm(sim), st);
+        } else {
+            if (e == cudaSuccess) e = launch_spmv_pre(sim->g, sim->Stil, sim->Scol, sim->xt, sim->w, st);
+            CombineTerms t{};
+            t.n = 1;
+            t.X[0] = sim->w;
+            t.c[0] = -1.0;
+            if (e == cudaSuccess) e = launch_combine(n, g, t, sim->w, nullptr, st);
+            if (e == cudaSuccess) e = launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st);
+        }
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(sim->hbuf, dv_nrm(sim), sizeof(double), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess)

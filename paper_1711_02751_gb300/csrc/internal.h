@@ -242,10 +242,11 @@ cudaError_t launch_spmv_pre(const Geom& g, const double* Stil, const int* Scol, 
 // streamed through shared memory by bulk copies in a persistent pipelined kernel instead.
 cudaError_t launch_spmv_pre(const Geom& g, const float* Stil, const int* Scol, const float* x,
                             float* y, cudaStream_t s, const int* done = nullptr, int* stream_error = nullptr);
-// y = x + sum_slots S~ x[col] in FP64-class arithmetic on the FP32 pipes: S~ = Shi + Slo
-// (an FP32 pair), compensated Dot2 sums (compensated.h).
-cudaError_t launch_spmv_x2(const Geom& g, const float* Shi, const float* Slo, const int* Scol, const double* x,
-                           double* y, cudaStream_t s);
+// w = rhs - (x + S~ x) with S~ = Shi + Slo (FP32 pair, compensated sums) and ||w||^2 -> *nrm2 in
+// one pass; scratch as for launch_multidot (a ticket counter and at least 608 partial sums).
+cudaError_t launch_residual_norm_x2(const Geom& g, const float* Shi, const float* Slo, const int* Scol,
+                                    const double* x, const double* rhs, double* w, double* scratch, double* nrm2,
+                                    cudaStream_t s);
 // y = B x for a block-diagonal matrix B given as [edge][col][row] blocks (FP64)
 cudaError_t launch_block_diag(const Geom& g, const double* Bd, const double* x, double* y,
                               cudaStream_t s);

@@ -12,6 +12,7 @@
 // warp, block and grid reductions are in double.  The trace-matrix products are in
 // kernels_spmv.cu.
 #include "internal.h"
+#include "reduce.h"
 
 namespace hdgdg {
 namespace {
@@ -35,36 +36,6 @@ block_diag_kernel(int n_edges, const double* __restrict__ Bd, const double* __re
 #pragma unroll
     for (int jj = 0; jj < NF; ++jj) acc += B[jj * NF + ii] * xr[jj];
     y[(size_t)r * NF + ii] = acc;
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Grid reductions finish in the block that arrives last: every block writes its partial sums,
-// takes a ticket, and the block holding the last ticket sums the partials in block order -- the
-// same order whichever block arrives last, so results are reproducible bit for bit.  The ticket
-// counter is the first word of the scratch buffer (partials follow) and is reset by that block.
-__device__ bool last_block_arrives(unsigned* counter) {
-    __shared__ unsigned s_ticket;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_ticket = atomicAdd(counter, 1u);
-    __syncthreads();
-    return s_ticket == gridDim.x - 1;
-}
-
-// out[c] = sum over blocks of partial[blk * ldp + c0 + c], c < nc: one warp per column, fixed order
-__device__ void reduce_partials(const double* partial, int nblk, int ldp, int c0, int nc, double* out) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int c = wid; c < nc; c += nw) {
-        double s = 0.0;
-        for (int k = lane; k < nblk; k += 32) s += __ldcg(partial + (size_t)k * ldp + c0 + c);
-        s = warp_sum(s);
-        if (lane == 0) out[c] = s;
-    }
 }
 
 __device__ void gmres_arnoldi_update(GmresCtl* c, int j, int m, const double* h1, const double* h2,

@@ -4,16 +4,20 @@
 //   spmv_pre_kernel<NF, T>  one thread per row component; the row's six neighbour trace vectors
 //                           are gathered into shared memory first (six independent loads per
 //                           thread), then the products read them from there;
-//   spmv_x2_kernel<NF>      the same in FP64-class arithmetic on the FP32 pipes (compensated.h);
+//   residual_norm_x2_kernel<NF>  w = g - (x + S~ x) and ||w||^2 in FP64-class arithmetic on the
+//                           FP32 pipes (compensated.h): the refinement's true residual;
 //   spmv_stream_kernel<NF>  FP32, the matrix also streamed through shared memory by bulk copies.
 #include <algorithm>
 
 #include "async_copy.h"
 #include "compensated.h"
 #include "internal.h"
+#include "reduce.h"
 
 namespace hdgdg {
 namespace {
+
+constexpr int kGrid = 608;   // fixed grid of the fused residual pass (its norm partials)
 
 // y[r][ii] = x[r][ii] + sum_{slot, jj} S~[r][slot][jj][ii] x[col(r,slot)][jj]
 template <int NF, typename T>
@@ -43,35 +47,61 @@ spmv_pre_kernel(int n_edges, const T* __restrict__ Stil, const int* __restrict__
     y[(size_t)r * NF + ii] = acc;
 }
 
-// The same product in FP64-class arithmetic on the FP32 pipes (compensated.h): S~ as an FP32
-// pair, x split into a pair while it is gathered, each component a Dot2 sum; y = x + that sum.
+// w = g - (x + S~ x) with S~ as an FP32 pair (compensated Dot2 sums, compensated.h), and
+// ||w||^2: the refinement's true residual and its norm in one pass.  A fixed grid walks the edge
+// rows in groups of EPB; the norm's block partials are summed by the last block (fixed order).
 template <int NF>
 __global__ void __launch_bounds__(256)
-spmv_x2_kernel(int n_edges, const float* __restrict__ Shi, const float* __restrict__ Slo,
-               const int* __restrict__ Scol, const double* __restrict__ x, double* __restrict__ y) {
+residual_norm_x2_kernel(int n_edges, const float* __restrict__ Shi, const float* __restrict__ Slo,
+                        const int* __restrict__ Scol, const double* __restrict__ x, const double* __restrict__ g,
+                        double* __restrict__ w, double* __restrict__ scratch, double* __restrict__ nrm2) {
     constexpr int EPB = 256 / NF;
     __shared__ float sxh[EPB][6][NF], sxl[EPB][6][NF];
+    __shared__ double sh[8];
     const int le = threadIdx.x / NF, ii = threadIdx.x % NF;
-    const int r = blockIdx.x * EPB + le;
-    const bool live = le < EPB && r < n_edges;
-    if (live) {
+    double acc2 = 0.0;
+    for (int r0 = blockIdx.x * EPB; r0 < n_edges; r0 += gridDim.x * EPB) {
+        const int r = r0 + le;
+        const bool live = le < EPB && r < n_edges;
+        if (live) {
 #pragma unroll
-        for (int sl = 0; sl < 6; ++sl)
-            split(x[(size_t)__ldg(Scol + (size_t)r * 6 + sl) * NF + ii], sxh[le][sl][ii], sxl[le][sl][ii]);
-    }
-    __syncthreads();
-    if (!live) return;
-    const size_t base = (size_t)r * 6 * NF * NF;
-    Dot2 acc;
-#pragma unroll
-    for (int sl = 0; sl < 6; ++sl) {
-#pragma unroll
-        for (int jj = 0; jj < NF; ++jj) {
-            const size_t o = base + (size_t)sl * NF * NF + jj * NF + ii;
-            acc.add(Shi[o], Slo[o], sxh[le][sl][jj], sxl[le][sl][jj]);
+            for (int sl = 0; sl < 6; ++sl)
+                split(x[(size_t)__ldg(Scol + (size_t)r * 6 + sl) * NF + ii], sxh[le][sl][ii], sxl[le][sl][ii]);
         }
+        __syncthreads();
+        if (live) {
+            const size_t base = (size_t)r * 6 * NF * NF;
+            Dot2 acc;
+#pragma unroll
+            for (int sl = 0; sl < 6; ++sl) {
+#pragma unroll
+                for (int jj = 0; jj < NF; ++jj) {
+                    const size_t o = base + (size_t)sl * NF * NF + jj * NF + ii;
+                    acc.add(Shi[o], Slo[o], sxh[le][sl][jj], sxl[le][sl][jj]);
+                }
+            }
+            const size_t o = (size_t)r * NF + ii;
+            const double v = g[o] - (x[o] + acc.value());
+            w[o] = v;
+            acc2 += v * v;
+        }
+        __syncthreads();   // sx is rewritten for the next group
     }
-    y[(size_t)r * NF + ii] = x[(size_t)r * NF + ii] + acc.value();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const double s = warp_sum(acc2);
+    if (lane == 0) sh[wid] = s;
+    __syncthreads();
+    unsigned* counter = reinterpret_cast<unsigned*>(scratch);
+    double* partial = scratch + 1;
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int k = 0; k < (int)(blockDim.x + 31) / 32; ++k) b += sh[k];
+        partial[blockIdx.x] = b;
+    }
+    if (last_block_arrives(counter)) {
+        reduce_partials(partial, gridDim.x, 1, 0, 1, nrm2);
+        if (threadIdx.x == 0) *counter = 0u;
+    }
 }
 
 // The same product with the matrix streamed through shared memory: a persistent CTA takes
@@ -237,12 +267,15 @@ cudaError_t launch_spmv_pre(const Geom& g, const float* Stil, const int* Scol, c
 }
 
 
-cudaError_t launch_spmv_x2(const Geom& g, const float* Shi, const float* Slo, const int* Scol, const double* x,
-                           double* y, cudaStream_t s) {
+cudaError_t launch_residual_norm_x2(const Geom& g, const float* Shi, const float* Slo, const int* Scol,
+                                    const double* x, const double* rhs, double* w, double* scratch, double* nrm2,
+                                    cudaStream_t s) {
 #define CASE(P, NF)                                                                                     \
     case P: {                                                                                           \
         constexpr int EPB = 256 / NF;                                                                   \
-        spmv_x2_kernel<NF><<<(g.n_edges + EPB - 1) / EPB, EPB * NF, 0, s>>>(g.n_edges, Shi, Slo, Scol, x, y); \
+        const int groups = (g.n_edges + EPB - 1) / EPB;                                                 \
+        residual_norm_x2_kernel<NF><<<groups < kGrid ? groups : kGrid, 256, 0, s>>>(                 \
+            g.n_edges, Shi, Slo, Scol, x, rhs, w, scratch, nrm2);                                        \
         count_launches(1);                                                                              \
         return cudaGetLastError();                                                                      \
     }
