@@ -50,7 +50,7 @@ def _args():
                     help="forms to time; the headline is mixed when within 1e-6 of fp64")
     ap.add_argument("--local", default="f32x2", choices=["fp64", "fp32", "bf16", "f32x2"],
                     help="arithmetic of the local condensation / recovery in the mixed form")
-    ap.add_argument("--guess", type=int, default=0, choices=[-1, 0, 1, 2, 3, 4],
+    ap.add_argument("--guess", type=int, default=0, choices=[-1, 0, 1, 2, 3, 4, 5, 6],
                     help="trace-solve initial guess: extrapolation order 1-3, -1 zero, 0 library default")
     ap.add_argument("--spmv-kernel", type=int, default=0, choices=[0, 1],
                     help="FP32 inner SpMV: 0 plain (x gathered through shared memory), 1 pipelined bulk copies")
@@ -677,7 +677,8 @@ def main():
                        "gmres_restart": args.restart or 10,
                        "krylov_guess": {-1: "zero", 0: "quadratic extrapolation (default)", 1: "previous step",
                                         2: "linear extrapolation", 3: "quadratic extrapolation",
-                                        4: "cubic extrapolation"}[args.guess],
+                                        4: "cubic extrapolation", 5: "quartic extrapolation",
+                                        6: "quintic extrapolation"}[args.guess],
                        "l2": "inputs larger than L2 (A^-1 and trace matrix are GBs)"},
             "latency_ms": {"p50": p50, "p99": p99},
             "rel_l2_mixed_vs_fp64": err,

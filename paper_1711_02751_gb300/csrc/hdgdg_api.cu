@@ -51,7 +51,7 @@ bool valid(const hdgdg_config* c) {
            c->krylov_restart <= kMaxRestart && c->local_precision >= HDGDG_LOCAL_FP64 &&
            c->local_precision <= HDGDG_LOCAL_F32X2 &&
            (c->local_precision != HDGDG_LOCAL_BF16 || c->degree_k <= 4) &&   // tensor-core tiles: k <= 4
-           c->krylov_guess >= -1 && c->krylov_guess <= 4 && (c->spmv_kernel == 0 || c->spmv_kernel == 1) &&
+           c->krylov_guess >= -1 && c->krylov_guess <= 6 && (c->spmv_kernel == 0 || c->spmv_kernel == 1) &&
            (c->krylov_ortho == 0 || c->krylov_ortho == 1) && (c->residual_f32x2 == 0 || c->residual_f32x2 == 1);
 }
 
@@ -80,7 +80,7 @@ Plan make_plan(const hdgdg_config* c) {
     if (explicit_scheme(c)) {   // state, three stage increments, two stage states, face fluxes
         b += p.n * d + n_edges * P * d;
         b += 7 * 3 * p.n * d + p.nt * d;
-        b += (dot_scratch_doubles(p.m + 2) + mass_scratch_doubles() + 4 * (size_t)(p.m + 2) + 16) * d + 64;
+        b += (reduction_scratch_doubles(p.m) + mass_scratch_doubles() + 4 * (size_t)(p.m + 2) + 16) * d + 64;
         p.persistent = b;
         p.setup_temp = 0;
         return p;
@@ -98,7 +98,7 @@ Plan make_plan(const hdgdg_config* c) {
     } else {
         b += ((size_t)p.m + 1) * p.nt * d;                    // FP64 Krylov basis
     }
-    b += (dot_scratch_doubles(p.m + 2) + mass_scratch_doubles() + 4 * (size_t)(p.m + 2) + 16) * d;
+    b += (reduction_scratch_doubles(p.m) + mass_scratch_doubles() + 4 * (size_t)(p.m + 2) + 16) * d;
     b += 64 + sizeof(GmresCtl);                               // flags, GMRES control block
     if (c->local_precision == HDGDG_LOCAL_FP32) b += n_el * (size_t)p.NV * p.NV * sizeof(float);
     if (c->local_precision == HDGDG_LOCAL_BF16) b += tc_image_bytes((int)P);
@@ -276,8 +276,8 @@ struct hdgdg_sim {
     // device memory
     std::vector<void*> allocs;
     double *phiB = nullptr, *tau = nullptr, *Ainv = nullptr, *Stil = nullptr, *Minv = nullptr, *Srr = nullptr;
-    double* xhist[kMaxStages][4] = {};   // trace-solve guess: preconditioned solutions of the last
-    double* yhist[kMaxStages][4] = {};   // steps per stage ([0] newest), their products S~ x~ (from
+    double* xhist[kMaxStages][6] = {};   // trace-solve guess: preconditioned solutions of the last
+    double* yhist[kMaxStages][6] = {};   // steps per stage ([0] newest), their products S~ x~ (from
     int n_hist[kMaxStages] = {};         // the final true residual: g - r), and their count
     float* Ainv32 = nullptr;      // HDGDG_LOCAL_FP32
     float *Ahi = nullptr, *Alo = nullptr;   // HDGDG_LOCAL_F32X2
@@ -496,7 +496,9 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
         CU(launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st));
     } else {
         // x0 = sum_j c_j x_{n-j}: the extrapolation polynomial through the last `guess` solutions
-        static const double coef[5][4] = {{0, 0, 0, 0}, {1, 0, 0, 0}, {2, -1, 0, 0}, {3, -3, 1, 0}, {4, -6, 4, -1}};
+        static const double coef[7][6] = {{0, 0, 0, 0, 0, 0},     {1, 0, 0, 0, 0, 0},     {2, -1, 0, 0, 0, 0},
+                                          {3, -3, 1, 0, 0, 0},    {4, -6, 4, -1, 0, 0},   {5, -10, 10, -5, 1, 0},
+                                          {6, -15, 20, -15, 6, -1}};
         CombineTerms t{};
         for (int j = 0; j < guess; ++j) {
             t.X[t.n] = sim->xhist[stage][j];
@@ -807,7 +809,7 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
         for (double** v : {&sim->q, &sim->q_new, &sim->R1, &sim->Qs}) TRY(dalloc(sim, v, 3 * p.n));
         for (int i = 0; i < 3; ++i) TRY(dalloc(sim, &sim->NLs[i], 3 * p.n));
         TRY(dalloc(sim, &sim->fface, p.nt));
-        TRY(dalloc(sim, &sim->red, dot_scratch_doubles(p.m + 2)));
+        TRY(dalloc(sim, &sim->red, reduction_scratch_doubles(p.m)));
     CU(cudaMemset(sim->red, 0, sizeof(double)));   // the reductions' ticket counter starts at zero
         TRY(dalloc(sim, &sim->mred, mass_scratch_doubles()));
         TRY(dalloc(sim, &sim->dvals, 4 * (size_t)(p.m + 2) + 16));
@@ -842,7 +844,7 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
     } else {
         TRY(dalloc(sim, &sim->V, (size_t)(p.m + 1) * p.nt));
     }
-    TRY(dalloc(sim, &sim->red, dot_scratch_doubles(p.m + 2)));
+    TRY(dalloc(sim, &sim->red, reduction_scratch_doubles(p.m)));
     CU(cudaMemset(sim->red, 0, sizeof(double)));   // the reductions' ticket counter starts at zero
     TRY(dalloc(sim, &sim->mred, mass_scratch_doubles()));
     TRY(dalloc(sim, &sim->dvals, 4 * (size_t)(p.m + 2) + 16));

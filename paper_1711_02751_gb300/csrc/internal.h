@@ -243,7 +243,7 @@ cudaError_t launch_spmv_pre(const Geom& g, const double* Stil, const int* Scol, 
 cudaError_t launch_spmv_pre(const Geom& g, const float* Stil, const int* Scol, const float* x,
                             float* y, cudaStream_t s, const int* done = nullptr, int* stream_error = nullptr);
 // w = rhs - (x + S~ x) with S~ = Shi + Slo (FP32 pair, compensated sums) and ||w||^2 -> *nrm2 in
-// one pass; scratch as for launch_multidot (a ticket counter and at least 608 partial sums).
+// one pass; scratch as for launch_multidot (a ticket counter and at least 2432 partial sums).
 cudaError_t launch_residual_norm_x2(const Geom& g, const float* Shi, const float* Slo, const int* Scol,
                                     const double* x, const double* rhs, double* w, double* scratch, double* nrm2,
                                     cudaStream_t s);
@@ -267,6 +267,9 @@ struct GmresCtl {
 // doubles (a ticket counter, zero between calls, then the block partial sums) that every call
 // on one stream may share.  Deterministic (fixed grid, fixed order).
 size_t dot_scratch_doubles(int nv);
+// The handle's reduction scratch: the Gram-Schmidt dots of a GMRES(m) cycle and the fused
+// residual pass (launch_residual_norm_x2) share it.
+size_t reduction_scratch_doubles(int m);
 cudaError_t launch_multidot(const double* V, size_t ldv, int nv, const double* w, size_t n,
                             double* scratch, double* out, cudaStream_t s, const int* done = nullptr);
 cudaError_t launch_multidot(const float* V, size_t ldv, int nv, const float* w, size_t n,

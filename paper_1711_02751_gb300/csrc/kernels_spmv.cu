@@ -17,7 +17,7 @@
 namespace hdgdg {
 namespace {
 
-constexpr int kGrid = 608;   // fixed grid of the fused residual pass (its norm partials)
+constexpr int kGrid = 152 * 16;   // fixed grid of the fused residual pass (its norm partials)
 
 // y[r][ii] = x[r][ii] + sum_{slot, jj} S~[r][slot][jj][ii] x[col(r,slot)][jj]
 template <int NF, typename T>
@@ -98,9 +98,19 @@ residual_norm_x2_kernel(int n_edges, const float* __restrict__ Shi, const float*
         for (int k = 0; k < (int)(blockDim.x + 31) / 32; ++k) b += sh[k];
         partial[blockIdx.x] = b;
     }
-    if (last_block_arrives(counter)) {
-        reduce_partials(partial, gridDim.x, 1, 0, 1, nrm2);
-        if (threadIdx.x == 0) *counter = 0u;
+    if (last_block_arrives(counter)) {   // the whole block sums the partials, fixed order
+        double t = 0.0;
+        for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) t += __ldcg(partial + k);
+        t = warp_sum(t);
+        __syncthreads();
+        if (lane == 0) sh[wid] = t;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = 0.0;
+            for (int k = 0; k < (int)(blockDim.x + 31) / 32; ++k) b += sh[k];
+            *nrm2 = b;
+            *counter = 0u;
+        }
     }
 }
 
@@ -284,6 +294,11 @@ cudaError_t launch_residual_norm_x2(const Geom& g, const float* Shi, const float
         default: return cudaErrorInvalidValue;
     }
 #undef CASE
+}
+
+size_t reduction_scratch_doubles(int m) {
+    const size_t dots = dot_scratch_doubles(m + 2), fused = 1 + (size_t)kGrid;
+    return dots > fused ? dots : fused;
 }
 
 }  // namespace hdgdg
