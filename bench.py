@@ -675,7 +675,7 @@ def main():
                                    f"dt={dt:.6g} (advective CFL 0.5: 0.5 h/((2k+1) 2max|u|))", "form": head,
                        "dof": dof, "parallelism": "replicas" if world > 1 else "single",
                        "gmres_restart": args.restart or 10,
-                       "krylov_guess": {-1: "zero", 0: "quadratic extrapolation (default)", 1: "previous step",
+                       "krylov_guess": {-1: "zero", 0: "quartic extrapolation (default)", 1: "previous step",
                                         2: "linear extrapolation", 3: "quadratic extrapolation",
                                         4: "cubic extrapolation", 5: "quartic extrapolation",
                                         6: "quintic extrapolation"}[args.guess],

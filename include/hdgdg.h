@@ -113,10 +113,10 @@ typedef struct {
                             HDGDG_LOCAL_F32X2 */
     int krylov_guess;    /* start of each implicit stage's trace solve: the polynomial extrapolation
                             in time of the same stage's solutions of the previous steps --
-                            1 = previous step (x_{n-1}), 2 = linear (2 x_{n-1} - x_{n-2}),
-                            3 = quadratic (3 x_{n-1} - 3 x_{n-2} + x_{n-3}), 4 = cubic
-                            (4 x_{n-1} - 6 x_{n-2} + 4 x_{n-3} - x_{n-4}); -1 = start from zero;
-                            0 selects 3.  Fewer steps than the order since set_state lower it.
+                            order p = 1..6 uses the last p solutions, x_0 = sum_{j=1..p}
+                            (-1)^(j+1) C(p, j) x_{n-j} (1: x_{n-1}; 2: 2 x_{n-1} - x_{n-2};
+                            3: 3, -3, 1; 4: 4, -6, 4, -1; ...); -1 = start from zero; 0 selects 5.
+                            Fewer steps than the order since set_state lower it.
                             The stop test stays ||g - S qhat|| <= rtol ||g||.  The guess's residual
                             needs no matrix product: the same extrapolation of the stored
                             products S x_{n-j} (g - r at the end of each solve) gives S x_0. */

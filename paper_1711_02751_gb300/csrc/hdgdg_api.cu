@@ -60,7 +60,7 @@ bool explicit_scheme(const hdgdg_config* c) { return c->scheme == HDGDG_RK2 || c
 int restart_of(const hdgdg_config* c) { return c->krylov_restart > 0 ? c->krylov_restart : 10; }
 
 // order of the trace-solve initial guess (0: start from zero)
-int guess_order(const hdgdg_config* c) { return c->krylov_guess < 0 ? 0 : c->krylov_guess == 0 ? 3 : c->krylov_guess; }
+int guess_order(const hdgdg_config* c) { return c->krylov_guess < 0 ? 0 : c->krylov_guess == 0 ? 5 : c->krylov_guess; }
 
 Plan make_plan(const hdgdg_config* c) {
     Plan p;

@@ -23,7 +23,8 @@ def _run(N, k, kind, steps, guess, precision="fp64", scheme="ars2"):
     return m, h, hu, hv, b, dt, swe.to_state(*out, b, W.G, W.H0)[0], st
 
 
-@pytest.mark.parametrize("guess,scheme", [(1, "ars2"), (2, "ars2"), (3, "ars2"), (2, "ars3"), (0, "ars2")])
+@pytest.mark.parametrize("guess,scheme", [(1, "ars2"), (2, "ars2"), (3, "ars2"), (4, "ars2"), (6, "ars2"), (2, "ars3"),
+                                          (4, "ars3"), (0, "ars2")])
 def test_guess_matches_oracle(guess, scheme):
     m, h, hu, hv, b, dt, qa, st = _run(12, 3, "large", 8, guess, scheme=scheme)
     q, phiB = oracle_state(m, h, hu, hv, b)
