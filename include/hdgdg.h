@@ -112,14 +112,15 @@ typedef struct {
     int local_precision; /* HDGDG_LOCAL_FP64 (0), HDGDG_LOCAL_FP32, HDGDG_LOCAL_BF16 or
                             HDGDG_LOCAL_F32X2 */
     int krylov_guess;    /* start of each implicit stage's trace solve: the polynomial extrapolation
-                            in time of the same stage's solutions of the previous steps --
-                            order p = 1..6 uses the last p solutions, x_0 = sum_{j=1..p}
-                            (-1)^(j+1) C(p, j) x_{n-j} (1: x_{n-1}; 2: 2 x_{n-1} - x_{n-2};
-                            3: 3, -3, 1; 4: 4, -6, 4, -1; ...); -1 = start from zero; 0 selects 5.
-                            Fewer steps than the order since set_state lower it.
-                            The stop test stays ||g - S qhat|| <= rtol ||g||.  The guess's residual
-                            needs no matrix product: the same extrapolation of the stored
-                            products S x_{n-j} (g - r at the end of each solve) gives S x_0. */
+                            in time of the same stage's solutions of the previous steps, of
+                            order at most p = 1..6 (the last p solutions, x_0 = sum_{j=1..p}
+                            (-1)^(j+1) C(p, j) x_{n-j}: 1 = x_{n-1}; 2 = 2 x_{n-1} - x_{n-2};
+                            3: 3, -3, 1; ...), -1 = always start from zero, 0 selects 5.  Each
+                            solve starts from the order <= p (or zero) whose residual is
+                            smallest; one pass over g and the stored products S x_{n-j} (g - r
+                            at the end of each solve) gives every candidate's residual, no
+                            matrix product is needed.  The stop test stays
+                            ||g - S qhat|| <= rtol ||g||. */
     int spmv_kernel;     /* FP32 trace-matrix product of the mixed form's inner cycles: 0 = one
                             thread per row component, neighbour vectors gathered through shared
                             memory; 1 = a persistent kernel that also streams the matrix through
@@ -148,6 +149,8 @@ typedef struct {
     double mass;                  /* sum_e J sum_ij w_i w_j phi_eta of the current state */
     long long kernel_launches;    /* CUDA kernels this handle launched in hdgdg_step since set_state */
     double time;                  /* simulated time since set_state (steps x dt) */
+    int last_guess_order;         /* extrapolation order the most recent trace solve started from
+                                     (0: zero start) */
 } hdgdg_stats;
 
 /* Kernel classes of the per-kernel timers (hdgdg_kernel_time). */

@@ -353,7 +353,7 @@ inline double* dv_h2(hdgdg_sim* s) { return s->dvals + (s->plan.m + 2); }
 // device error word of the pipelined SpMV (a bounded wait ran out)
 inline int* spmv_error(hdgdg_sim* s) { return reinterpret_cast<int*>(s->flags) + 3; }
 inline double* dv_nrm(hdgdg_sim* s) { return s->dvals + 2 * (s->plan.m + 2); }
-inline double* dv_coef(hdgdg_sim* s) { return s->dvals + 2 * (s->plan.m + 2) + 8; }
+inline double* dv_guess(hdgdg_sim* s) { return s->dvals + 3 * (s->plan.m + 2) + 8; }   // 7 slots
 
 cudaEvent_t take_event(hdgdg_sim* sim) {
     if (!sim->ev_pool.empty()) {
@@ -478,8 +478,27 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
     GmresCtl* ctl = sim->ctl;
     const int* done = &ctl->done;
     *iters = 0;
-    double bn2;
-    TRY(norm2_to_host(sim, g, &bn2));
+    // Initial guess: the extrapolation in time of the stage's previous solutions, at the order
+    // (or zero) whose residual is smallest.  One pass over g and the stored products S~ x~_{n-j}
+    // gives ||g||^2 and every candidate's residual norm; no matrix product is needed.
+    static const double coef[7][6] = {{0, 0, 0, 0, 0, 0},     {1, 0, 0, 0, 0, 0},     {2, -1, 0, 0, 0, 0},
+                                      {3, -3, 1, 0, 0, 0},    {4, -6, 4, -1, 0, 0},   {5, -10, 10, -5, 1, 0},
+                                      {6, -15, 20, -15, 6, -1}};
+    const int avail = stage >= 0 ? std::min(guess_order(&sim->cfg), sim->n_hist[stage]) : 0;
+    double cand[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (avail > 0) {
+        GuessTerms gt{};
+        gt.nq = avail;
+        for (int j = 0; j < avail; ++j) gt.y[j] = sim->yhist[stage][j];
+        std::memcpy(gt.c, coef, sizeof(coef));
+        CU(launch_guess_norms(n, g, gt, sim->red, dv_guess(sim), st));
+        CU(cudaMemcpyAsync(sim->hbuf, dv_guess(sim), (avail + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+        TRY(sync(sim));
+        std::memcpy(cand, sim->hbuf, (avail + 1) * sizeof(double));
+    } else {
+        TRY(norm2_to_host(sim, g, &cand[0]));
+    }
+    const double bn2 = cand[0];
     if (!std::isfinite(bn2)) return fail(sim, HDGDG_ENONFINITE, "non-finite trace right-hand side");
     if (bn2 == 0.0) {
         CU(cudaMemsetAsync(qhat, 0, n * sizeof(double), st));
@@ -487,18 +506,19 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
         return HDGDG_OK;
     }
     const double bnorm = std::sqrt(bn2), tol = rtol * bnorm;
-    // initial guess: zero, or from the stage's solutions of the previous steps
-    const int guess = stage >= 0 ? std::min(guess_order(&sim->cfg), sim->n_hist[stage]) : 0;
-    double rnorm = bnorm;
+    int guess = 0;
+    for (int q = 1; q <= avail; ++q)
+        if (std::isfinite(cand[q]) && cand[q] < cand[guess]) guess = q;
+    sim->stats.last_guess_order = guess;
+    const double rnorm0 = std::sqrt(cand[guess]);
+    double rnorm = rnorm0;
     if (guess == 0) {
         CU(cudaMemsetAsync(sim->xt, 0, n * sizeof(double), st));
         CU(cudaMemcpyAsync(sim->w, g, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        CU(launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st));
+        if (avail > 0)   // ||g||^2 for the cycle's first basis vector (norm2_to_host left it otherwise)
+            CU(cudaMemcpyAsync(dv_nrm(sim), dv_guess(sim), sizeof(double), cudaMemcpyDeviceToDevice, st));
     } else {
         // x0 = sum_j c_j x_{n-j}: the extrapolation polynomial through the last `guess` solutions
-        static const double coef[7][6] = {{0, 0, 0, 0, 0, 0},     {1, 0, 0, 0, 0, 0},     {2, -1, 0, 0, 0, 0},
-                                          {3, -3, 1, 0, 0, 0},    {4, -6, 4, -1, 0, 0},   {5, -10, 10, -5, 1, 0},
-                                          {6, -15, 20, -15, 6, -1}};
         CombineTerms t{};
         for (int j = 0; j < guess; ++j) {
             t.X[t.n] = sim->xhist[stage][j];
@@ -513,10 +533,7 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
             r.c[r.n++] = -coef[guess][j];
         }
         CU(launch_combine(n, g, r, sim->w, nullptr, st));
-        double r2;
-        TRY(norm2_to_host(sim, sim->w, &r2));   // leaves ||r0||^2 in the norm slot for the cycle
-        if (!std::isfinite(r2)) return fail(sim, HDGDG_ENONFINITE, "non-finite initial trace residual");
-        rnorm = std::sqrt(r2);
+        CU(cudaMemcpyAsync(dv_nrm(sim), dv_guess(sim) + guess, sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
     CU(launch_gmres_solve_init(ctl, tol, inner_rel, maxit, st));
     int total = 0;

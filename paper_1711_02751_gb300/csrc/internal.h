@@ -267,9 +267,19 @@ struct GmresCtl {
 // doubles (a ticket counter, zero between calls, then the block partial sums) that every call
 // on one stream may share.  Deterministic (fixed grid, fixed order).
 size_t dot_scratch_doubles(int nv);
-// The handle's reduction scratch: the Gram-Schmidt dots of a GMRES(m) cycle and the fused
-// residual pass (launch_residual_norm_x2) share it.
+// The handle's reduction scratch: the Gram-Schmidt dots of a GMRES(m) cycle, the fused
+// residual pass (launch_residual_norm_x2) and the guess norms (launch_guess_norms) share it.
 size_t reduction_scratch_doubles(int m);
+// Candidate initial guesses of a trace solve: y[j] = S~ x~_{n-1-j} (j < nq) and the extrapolation
+// coefficients of each order q = 1..nq.  out[0] = ||g||^2, out[q] = ||g - sum_j c[q][j] y[j]||^2.
+struct GuessTerms {
+    const double* y[6];
+    double c[7][6];
+    int nq;
+};
+size_t guess_scratch_doubles();
+cudaError_t launch_guess_norms(size_t n, const double* g, const GuessTerms& t, double* scratch, double* out,
+                               cudaStream_t s);
 cudaError_t launch_multidot(const double* V, size_t ldv, int nv, const double* w, size_t n,
                             double* scratch, double* out, cudaStream_t s, const int* done = nullptr);
 cudaError_t launch_multidot(const float* V, size_t ldv, int nv, const float* w, size_t n,

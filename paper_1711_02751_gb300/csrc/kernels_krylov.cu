@@ -212,6 +212,53 @@ axpy_scale_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict_
     }
 }
 
+// ||g||^2 and the residual norms of every candidate initial guess in one pass over g and the
+// stored products (no matrix product): out[0] = ||g||^2, out[q] = ||g - sum_j c[q][j] y[j]||^2.
+__global__ void __launch_bounds__(kDotThreads)
+guess_norms_kernel(size_t n, const double* __restrict__ g, GuessTerms t, double* __restrict__ scratch,
+                   double* __restrict__ out) {
+    constexpr int NQ = 7;
+    unsigned* counter = reinterpret_cast<unsigned*>(scratch);
+    double* partial = scratch + 1;
+    __shared__ double sh[NQ][kDotThreads / 32];
+    double acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+    for (size_t idx = blockIdx.x * (size_t)kDotThreads + threadIdx.x; idx < n;
+         idx += (size_t)gridDim.x * kDotThreads) {
+        const double gv = g[idx];
+        double yv[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) yv[j] = j < t.nq ? t.y[j][idx] : 0.0;
+        acc[0] += gv * gv;
+#pragma unroll
+        for (int q = 1; q < NQ; ++q) {
+            if (q > t.nq) break;
+            double r = gv;
+#pragma unroll
+            for (int j = 0; j < 6; ++j)
+                if (j < q) r -= t.c[q][j] * yv[j];
+            acc[q] += r * r;
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const double s = warp_sum(acc[q]);
+        if (lane == 0) sh[q][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NQ) {
+        double s = 0.0;
+        for (int k = 0; k < kDotThreads / 32; ++k) s += sh[threadIdx.x][k];
+        partial[(size_t)blockIdx.x * NQ + threadIdx.x] = s;
+    }
+    if (last_block_arrives(counter)) {
+        reduce_partials(partial, gridDim.x, NQ, 0, t.nq + 1, out);
+        if (threadIdx.x == 0) *counter = 0u;
+    }
+}
+
 // ---- device-side GMRES control: one thread each -----------------------------------------
 __global__ void gmres_solve_init_kernel(GmresCtl* c, double tol_abs, double inner_rel, int maxit) {
     c->tol_abs = tol_abs;
@@ -343,6 +390,16 @@ cudaError_t multidot_impl(const T* V, size_t ldv, int nv, const T* w, size_t n, 
 }
 
 }  // namespace
+
+size_t guess_scratch_doubles() { return 1 + (size_t)kDotBlocks * 7; }
+
+cudaError_t launch_guess_norms(size_t n, const double* g, const GuessTerms& t, double* scratch, double* out,
+                               cudaStream_t s) {
+    if (t.nq < 1 || t.nq > 6) return cudaErrorInvalidValue;
+    guess_norms_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(n, g, t, scratch, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 int cgs2_max_vectors() { return 32; }
 

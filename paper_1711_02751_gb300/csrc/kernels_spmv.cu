@@ -297,8 +297,8 @@ cudaError_t launch_residual_norm_x2(const Geom& g, const float* Shi, const float
 }
 
 size_t reduction_scratch_doubles(int m) {
-    const size_t dots = dot_scratch_doubles(m + 2), fused = 1 + (size_t)kGrid;
-    return dots > fused ? dots : fused;
+    const size_t dots = dot_scratch_doubles(m + 2), fused = 1 + (size_t)kGrid, guess = guess_scratch_doubles();
+    return std::max(dots, std::max(fused, guess));
 }
 
 }  // namespace hdgdg

@@ -157,3 +157,23 @@ def test_bench_mixed_form_across_configurations(case):
     for a, r, base in zip(outs[0], outs[1], (B0, 0.0, 0.0)):
         ra, rr = a - base, r - base
         assert np.linalg.norm(ra - rr) <= 1e-6 * np.linalg.norm(rr)
+
+
+def test_adaptive_guess_order():
+    """Each solve starts from the extrapolation order (<= krylov_guess) or zero whose residual is
+    smallest: the order reported stays in range, and on the coarse, under-resolved bump case -- where
+    high fixed orders extrapolate the unresolved oscillation and lose to a zero start -- the run
+    needs no more Krylov iterations than starting from zero."""
+    m, h, hu, hv, b = user_state(12, 3, "large")
+    dt = dt_of(m, h, hu, hv)
+    its = {}
+    for guess in (-1, 6):
+        with hd.Sim(12, 3, dt, bottom=b, krylov_guess=guess) as s:
+            s.set_state(h, hu, hv)
+            orders = []
+            for _ in range(8):
+                s.step(1)
+                orders.append(s.stats()["last_guess_order"])
+            its[guess] = s.stats()["krylov_iterations"]
+        assert all(0 <= o <= max(guess, 0) for o in orders)
+    assert its[6] <= its[-1]
