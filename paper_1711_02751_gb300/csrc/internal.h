@@ -285,19 +285,12 @@ cudaError_t launch_multidot(const double* V, size_t ldv, int nv, const double* w
                             double* scratch, double* out, cudaStream_t s, const int* done = nullptr);
 cudaError_t launch_multidot(const float* V, size_t ldv, int nv, const float* w, size_t n,
                             double* scratch, double* out, cudaStream_t s, const int* done = nullptr);
-// w = w - sign * sum_j coef[j] V_j   (coef on the device)
-cudaError_t launch_multiaxpy(const double* V, size_t ldv, int nv, const double* coef, double sign,
-                             double* w, size_t n, cudaStream_t s);
-// x = x + sum_j coef[j] V_j with FP32 V and FP64 x (coef on the device)
-cudaError_t launch_axpy_f32_into_f64(const float* V, size_t ldv, int nv, const double* coef, double* x,
-                                     size_t n, cudaStream_t s);
 // Fused tail of classical Gram-Schmidt applied twice, given h1 = V^T w on the device:
 // w1 = w - V h1 (in place), h2 = V^T w1, ||w1||^2 -> *nw1, hn = sqrt(||w1||^2 - ||h2||^2),
-// vout = (w1 - V h2) / hn.  nv <= cgs2_max_vectors(); scratch of dot_scratch_doubles(nv + 1).
+// vout = (w1 - V h2) / hn.  nv <= 32; scratch of dot_scratch_doubles(nv + 1).
 // With a GMRES control block, column j of the Hessenberg matrix, its Givens rotation and the
 // cycle's stop test are done in the same launch (restart length m).  twice = false: classical
 // Gram-Schmidt once (h2 = 0, hn = ||w1||, vout = w1 / hn).
-int cgs2_max_vectors();
 cudaError_t launch_cgs2_tail(const double* V, size_t ldv, int nv, const double* h1, double* w, size_t n,
                              double* scratch, double* h2, double* nw1, double* hn, double* vout,
                              GmresCtl* ctl, int j, int m, bool twice, cudaStream_t s, const int* done = nullptr);

@@ -79,29 +79,6 @@ multidot_kernel(const T* __restrict__ V, size_t ldv, int j0, int nj, const T* __
     }
 }
 
-// w -= sign * sum_j coef_j V_j
-template <typename T>
-__global__ void multiaxpy_kernel(const T* __restrict__ V, size_t ldv, int nv, const double* __restrict__ coef,
-                                 double sign, T* __restrict__ w, size_t n) {
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        T acc = w[idx];
-        for (int j = 0; j < nv; ++j) acc -= T(sign * coef[j]) * V[(size_t)j * ldv + idx];
-        w[idx] = acc;
-    }
-}
-
-// x += sum_j coef_j V_j with FP32 basis vectors and an FP64 accumulator
-__global__ void axpy_f32_into_f64_kernel(const float* __restrict__ V, size_t ldv, int nv,
-                                         const double* __restrict__ coef, double* __restrict__ x, size_t n) {
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        double acc = x[idx];
-        for (int j = 0; j < nv; ++j) acc += coef[j] * (double)V[(size_t)j * ldv + idx];
-        x[idx] = acc;
-    }
-}
-
 // v = w / sqrt(*nrm2) (w in FP64, v in T)
 template <typename T>
 __global__ void scale_kernel(const double* __restrict__ w, const double* __restrict__ nrm2,
@@ -413,8 +390,6 @@ cudaError_t launch_guess_norms(size_t n, const double* g, const GuessTerms& t, d
     return cudaGetLastError();
 }
 
-int cgs2_max_vectors() { return 32; }
-
 cudaError_t launch_cgs2_tail(const double* V, size_t ldv, int nv, const double* h1, double* w, size_t n,
                              double* scratch, double* h2, double* nw1, double* hn, double* vout,
                              GmresCtl* ctl, int j, int m, bool twice, cudaStream_t s, const int* done) {
@@ -452,20 +427,6 @@ cudaError_t launch_multidot(const double* V, size_t ldv, int nv, const double* w
 cudaError_t launch_multidot(const float* V, size_t ldv, int nv, const float* w, size_t n,
                             double* scratch, double* out, cudaStream_t s, const int* done) {
     return multidot_impl<float>(V, ldv, nv, w, n, scratch, out, s, done);
-}
-
-cudaError_t launch_multiaxpy(const double* V, size_t ldv, int nv, const double* coef, double sign,
-                             double* w, size_t n, cudaStream_t s) {
-    multiaxpy_kernel<double><<<stream_grid(n), 256, 0, s>>>(V, ldv, nv, coef, sign, w, n);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_axpy_f32_into_f64(const float* V, size_t ldv, int nv, const double* coef, double* x,
-                                     size_t n, cudaStream_t s) {
-    axpy_f32_into_f64_kernel<<<stream_grid(n), 256, 0, s>>>(V, ldv, nv, coef, x, n);
-    count_launches(1);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_scale_by_rnorm(const double* w, const double* nrm2, double* v, size_t n,
