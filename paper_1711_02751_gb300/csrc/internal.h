@@ -185,9 +185,8 @@ cudaError_t launch_dg_full(const Geom& g, const double* q, const double* phiB, d
                            double* fface, double* out, cudaStream_t s, double t = 0.0);
 
 struct CombineTerms {
-    static constexpr int kMax = 10;
-    const double* X[kMax];
-    double c[kMax];
+    const double* X[10];
+    double c[10];
     int n;
 };
 // out = base + sum_t c_t X_t over n doubles (out may alias base)

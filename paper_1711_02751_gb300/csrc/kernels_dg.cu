@@ -192,13 +192,8 @@ __global__ void combine_kernel(size_t n, const double* __restrict__ base, Combin
                                double* out, unsigned* nonfinite) {
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
          idx += (size_t)gridDim.x * blockDim.x) {
-        double v[CombineTerms::kMax];
-#pragma unroll
-        for (int k = 0; k < CombineTerms::kMax; ++k) v[k] = k < t.n ? t.X[k][idx] : 0.0;   // independent loads
         double acc = base[idx];
-#pragma unroll
-        for (int k = 0; k < CombineTerms::kMax; ++k)
-            if (k < t.n) acc += t.c[k] * v[k];   // summed in order
+        for (int k = 0; k < t.n; ++k) acc += t.c[k] * t.X[k][idx];
         out[idx] = acc;
         if (nonfinite && !isfinite(acc)) *nonfinite = 1u;
     }

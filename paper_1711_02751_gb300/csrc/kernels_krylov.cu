@@ -297,23 +297,11 @@ __global__ void gmres_solve_y_kernel(GmresCtl* c) {
 template <typename T>
 __global__ void gmres_update_x_kernel(const T* __restrict__ V, size_t ldv, const GmresCtl* __restrict__ c,
                                       double* __restrict__ x, size_t n) {
-    __shared__ double sy[GmresCtl::kM];   // the cycle's coefficients, read once per block
     const int nv = c->jend;
-    for (int j = threadIdx.x; j < nv; j += blockDim.x) sy[j] = c->y[j];
-    __syncthreads();
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
          idx += (size_t)gridDim.x * blockDim.x) {
         double acc = x[idx];
-        int j = 0;
-        for (; j + 4 <= nv; j += 4) {   // four independent loads in flight, summed in order
-            const T v0 = V[(size_t)j * ldv + idx], v1 = V[(size_t)(j + 1) * ldv + idx];
-            const T v2 = V[(size_t)(j + 2) * ldv + idx], v3 = V[(size_t)(j + 3) * ldv + idx];
-            acc += sy[j] * (double)v0;
-            acc += sy[j + 1] * (double)v1;
-            acc += sy[j + 2] * (double)v2;
-            acc += sy[j + 3] * (double)v3;
-        }
-        for (; j < nv; ++j) acc += sy[j] * (double)V[(size_t)j * ldv + idx];
+        for (int j = 0; j < nv; ++j) acc += c->y[j] * (double)V[(size_t)j * ldv + idx];
         x[idx] = acc;
     }
 }
