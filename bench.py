@@ -222,6 +222,17 @@ def _algorithmic(N, k, cls, precision="fp64"):
     return None, None
 
 
+def kernel_source(text, start):
+    """The source of one kernel: from the line holding `start` to the end of the function that
+    follows it (the first line that is a lone closing brace); the whole text if start is empty."""
+    if not start:
+        return text.encode()
+    i = text.index(start)
+    i = text.rfind("\n", 0, i) + 1
+    j = text.index("\n}\n", i) + 3
+    return text[i:j].encode()
+
+
 def _traffic_for(cls, N, k, precision="fp64"):
     """dram bytes per launch from a committed ncu summary, if it is for the current kernel source."""
     try:
@@ -230,7 +241,7 @@ def _traffic_for(cls, N, k, precision="fp64"):
         return None
     src = os.path.join(ROOT, "paper_1711_02751_gb300", "csrc", d.get("source", ""))
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = hashlib.sha256(kernel_source(open(src).read(), d.get("region", ""))).hexdigest()[:16]
     except Exception:
         return None
     e = d.get("kernels", {}).get(f"{cls}_{precision}")
