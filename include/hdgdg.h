@@ -224,7 +224,7 @@ hdgdg_status hdgdg_get_stats(hdgdg_sim* sim, hdgdg_stats* out);
  * host buffer buf of `bytes` (EINVAL if too small, ESTATE before set_state).
  * hdgdg_load_checkpoint replaces the handle's state and history from buf; EINVAL if buf is not a
  * checkpoint, is truncated, or was taken with another mesh, degree, scheme, arithmetic,
- * boundary, batch, time step, g, H0 or domain.  The bottom is not recorded: pass the same bottom
+ * boundary, batch, time step (per-instance time steps included), g, H0 or domain.  The bottom is not recorded: pass the same bottom
  * to hdgdg_create. */
 size_t hdgdg_checkpoint_bytes(hdgdg_sim* sim);
 hdgdg_status hdgdg_save_checkpoint(hdgdg_sim* sim, void* buf, size_t bytes);

@@ -279,6 +279,7 @@ struct hdgdg_sim {
     double* xhist[kMaxStages][6] = {};   // trace-solve guess: preconditioned solutions of the last
     double* yhist[kMaxStages][6] = {};   // steps per stage ([0] newest), their products S~ x~ (from
     int n_hist[kMaxStages] = {};         // the final true residual: g - r), and their count
+    double dt_fingerprint = 0.0;  // sum_i (i + 1) dt_i of a batch with per-instance time steps
     float* Ainv32 = nullptr;      // HDGDG_LOCAL_FP32
     float *Ahi = nullptr, *Alo = nullptr;   // HDGDG_LOCAL_F32X2
     void* tc_image = nullptr;     // HDGDG_LOCAL_BF16: the shared operator's tensor-core tile
@@ -814,6 +815,7 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
         std::vector<double> f(g.batch);
         for (int i = 0; i < g.batch; ++i) {
             f[i] = c->dt_per_instance[i] / c->dt;
+            sim->dt_fingerprint += (i + 1) * c->dt_per_instance[i];
             if (!std::isfinite(f[i]) || !(f[i] > 0.0))
                 return fail(sim, HDGDG_EINVAL, "time step of instance %d is not positive", i);
         }
@@ -1122,6 +1124,7 @@ struct CheckpointHeader {
     int n_side, degree_k, scheme, precision, boundary, batch, local_precision, guess, stages;
     long long n_state, n_trace;    // doubles in the state, in one trace vector
     double dt, g, H0, x0, length;
+    double dt_fingerprint;         // order-sensitive sum of the batch's per-instance time steps
     double t;
     hdgdg_stats stats;
     int n_hist[kMaxStages];        // guess history kept per stage (newest first)
@@ -1155,6 +1158,7 @@ void fill_header(const hdgdg_sim* sim, CheckpointHeader* h) {
     h->H0 = c.H0;
     h->x0 = c.x0;
     h->length = c.length;
+    h->dt_fingerprint = sim->dt_fingerprint;
 }
 }  // namespace
 
@@ -1199,7 +1203,8 @@ hdgdg_status hdgdg_load_checkpoint(hdgdg_sim* sim, const void* buf, size_t bytes
         h->precision != mine.precision || h->boundary != mine.boundary || h->batch != mine.batch ||
         h->local_precision != mine.local_precision || h->guess != mine.guess || h->stages != mine.stages ||
         h->n_state != mine.n_state || h->n_trace != mine.n_trace || h->dt != mine.dt || h->g != mine.g ||
-        h->H0 != mine.H0 || h->x0 != mine.x0 || h->length != mine.length)
+        h->H0 != mine.H0 || h->x0 != mine.x0 || h->length != mine.length ||
+        h->dt_fingerprint != mine.dt_fingerprint)
         return fail(sim, HDGDG_EINVAL, "checkpoint of a different configuration");
     size_t need = sizeof(CheckpointHeader) + 3 * sim->plan.n * sizeof(double);
     for (int i = 0; i < sim->s; ++i) {

@@ -111,8 +111,10 @@ dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict_
                  const double* __restrict__ fface, double scale, double* __restrict__ out) {
     constexpr int Np = P * P;
     constexpr int EPB = DgTile<P>::EPB;
-    __shared__ Tc sF[EPB][4][Np];   // fxU, fxV, fyU, fyV
-    __shared__ Tc sM[FULL ? EPB : 1][3][Np];   // FULL: U, V and phi_B for the mass flux and source
+    // fxU, fxV, fyU, fyV (and, FULL: U, V, phi_B) per element, each element's row padded by one
+    // word so that the two or more elements a warp covers fall in different banks
+    __shared__ Tc sFr[EPB][4 * Np + 1];
+    __shared__ Tc sMr[FULL ? EPB : 1][3 * Np + 1];
     // the derivative matrices, read below with a thread-dependent row: from shared memory, since
     // the kernel-parameter (constant) bank serialises a warp's loads of different addresses
     __shared__ Tc sDh[Np], sD[Np];
@@ -132,13 +134,13 @@ dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict_
     if (live) {
         const size_t o = (size_t)e * Np + n;
         const Tc ph = Tc(q[o]), U = Tc(q[fs + o]), V = Tc(q[2 * fs + o]), pb = Tc(phiB[o]);
-        nl_flux<Tc>(ph, U, V, pb, &sF[le][0][n], &sF[le][1][n], &sF[le][2][n], &sF[le][3][n]);
+        nl_flux<Tc>(ph, U, V, pb, &sFr[le][0 * Np + n], &sFr[le][1 * Np + n], &sFr[le][2 * Np + n], &sFr[le][3 * Np + n]);
         if (FULL) {
-            sF[le][0][n] += ph * pb;
-            sF[le][3][n] += ph * pb;
-            sM[FULL ? le : 0][0][n] = U;
-            sM[FULL ? le : 0][1][n] = V;
-            sM[FULL ? le : 0][2][n] = pb;
+            sFr[le][0 * Np + n] += ph * pb;
+            sFr[le][3 * Np + n] += ph * pb;
+            sMr[FULL ? le : 0][0 * Np + n] = U;
+            sMr[FULL ? le : 0][1 * Np + n] = V;
+            sMr[FULL ? le : 0][2 * Np + n] = pb;
             ph_own = ph;
         }
     }
@@ -150,9 +152,9 @@ dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict_
     for (int a = 0; a < P; ++a) {
         const Tc cx = sDh[i * P + a];
         const Tc cy = sDh[j * P + a];
-        rU += cx * sF[le][0][j * P + a] + cy * sF[le][2][a * P + i];
-        rV += cx * sF[le][1][j * P + a] + cy * sF[le][3][a * P + i];
-        if (FULL) rph += cx * sM[le][0][j * P + a] + cy * sM[le][1][a * P + i];
+        rU += cx * sFr[le][0 * Np + j * P + a] + cy * sFr[le][2 * Np + a * P + i];
+        rV += cx * sFr[le][1 * Np + j * P + a] + cy * sFr[le][3 * Np + a * P + i];
+        if (FULL) rph += cx * sMr[le][0 * Np + j * P + a] + cy * sMr[le][1 * Np + a * P + i];
     }
     const Tc th = Tc(g.two_over_h);
     rU *= th;
@@ -162,8 +164,8 @@ dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict_
         Tc dBx = Tc(0), dBy = Tc(0);
 #pragma unroll
         for (int a = 0; a < P; ++a) {
-            dBx += sD[i * P + a] * sM[le][2][j * P + a];
-            dBy += sD[j * P + a] * sM[le][2][a * P + i];
+            dBx += sD[i * P + a] * sMr[le][2 * Np + j * P + a];
+            dBy += sD[j * P + a] * sMr[le][2 * Np + a * P + i];
         }
         rU += ph_own * th * dBx;
         rV += ph_own * th * dBy;

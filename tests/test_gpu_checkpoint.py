@@ -65,3 +65,25 @@ def test_checkpoint_rejections():
     with hd.Sim(N, k, dt, bottom=b, precision="mixed") as s:   # another arithmetic
         with pytest.raises(hd.HdgdgError):
             s.load_checkpoint(ck)
+
+
+def test_batch_checkpoint_checks_the_time_steps():
+    x, y = hd.node_coords(8, 2)
+    h, hu, hv, b = W.large_state(x, y, seed=3)
+    dt = W.advective_dt(x, h, hu, hv, 8)
+    cat = lambda a: np.concatenate([a, a])  # noqa: E731
+    with hd.Sim(8, 2, dt, bottom=cat(b), batch=2, dt_per_instance=[dt, 0.5 * dt]) as s:
+        s.set_state(cat(h), cat(hu), cat(hv))
+        s.step(2)
+        ck = s.save_checkpoint()
+        ref = None
+        s.step(2)
+        ref = s.get_state()
+    with hd.Sim(8, 2, dt, bottom=cat(b), batch=2, dt_per_instance=[0.5 * dt, dt]) as s:
+        with pytest.raises(hd.HdgdgError):
+            s.load_checkpoint(ck)
+    with hd.Sim(8, 2, dt, bottom=cat(b), batch=2, dt_per_instance=[dt, 0.5 * dt]) as s:
+        s.load_checkpoint(ck)
+        s.step(2)
+        for a, r in zip(s.get_state(), ref):
+            assert np.array_equal(a, r)
