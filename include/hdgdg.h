@@ -151,6 +151,11 @@ typedef struct {
     double time;                  /* simulated time since set_state (steps x dt) */
     int last_guess_order;         /* extrapolation order the most recent trace solve started from
                                      (0: zero start) */
+    /* HDGDG_LOCAL_F32X2 on meshes of >= 4096 elements: elements per block of the condensation
+     * and recovery kernels, picked at create by timing each candidate tile on the handle's own
+     * operators (0: the default tile, not tuned). */
+    int local_tile_condense;
+    int local_tile_recover;
 } hdgdg_stats;
 
 /* Kernel classes of the per-kernel timers (hdgdg_kernel_time). */

@@ -920,6 +920,13 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
         sim->ops.kind = 3;
         sim->ops.Ahi = sim->Ahi;
         sim->ops.Alo = sim->Alo;
+        if (g.n_el >= 4096) {   // pick the kernels' tile on this handle's operators, then clear the scratch
+            CU(launch_autotune_local(g, sim->ops, sim->R1, sim->Z, sim->tau, sim->lam, sim->Qs, sim->NLs[0],
+                                     sim->stream));
+            for (double* v : {sim->R1, sim->Z, sim->Qs, sim->NLs[0]})
+                CU(cudaMemsetAsync(v, 0, 3 * p.n * sizeof(double), sim->stream));
+            CU(cudaMemsetAsync(sim->lam, 0, p.nt * sizeof(double), sim->stream));
+        }
     } else if (c->local_precision == HDGDG_LOCAL_BF16) {
         // one operator for every element: phi_B constant and one time step
         for (size_t k = 1; k < p.n; ++k)
@@ -1240,6 +1247,8 @@ hdgdg_status hdgdg_get_stats(hdgdg_sim* sim, hdgdg_stats* out) {
     }
     *out = sim->stats;
     out->time = sim->t;
+    out->local_tile_condense = sim->ops.tile_condense;
+    out->local_tile_recover = sim->ops.tile_recover;
     return HDGDG_OK;
 }
 

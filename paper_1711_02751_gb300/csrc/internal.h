@@ -209,6 +209,8 @@ struct LocalOps {
     const float* Ainv32 = nullptr;  // kind 1: same layout in FP32
     const float* Ahi = nullptr;     // kind 3: A^{-1} = Ahi + Alo, same layout
     const float* Alo = nullptr;
+    int tile_condense = 0, tile_recover = 0;              // kind 3: elements per block (0: default)
+    int tile_condense_index = 0, tile_recover_index = 0;  // their index in the candidate list
     const void* image = nullptr;    // kind 2: the shared A^{-1} as a BF16 tensor-core operand tile
     int* error = nullptr;           // kind 2: set when a bounded wait of the tensor-core kernel ran out
 };
@@ -220,6 +222,11 @@ cudaError_t launch_condense(const Geom& g, const LocalOps& ops, const double* R1
 cudaError_t launch_recover(const Geom& g, const LocalOps& ops, const double* Z, const double* R1,
                            const double* tau_edge, const double* qhat, double beta, double inv_aii,
                            double* Q, double* Lst, cudaStream_t s);
+// Autotuner of the FP32-pair local kernels' tile (elements per block): times each candidate on
+// the handle's operators, using R1, Z, Q, Lst as scratch (their contents are overwritten), and
+// records the fastest in ops.  No-op for other local arithmetic.
+cudaError_t launch_autotune_local(const Geom& g, LocalOps& ops, double* R1, double* Z, const double* tau_edge,
+                                  const double* qhat, double* Q, double* Lst, cudaStream_t s);
 // hi = (float)a, lo = (float)(a - hi): the FP32-pair copy of an FP64 array.
 cudaError_t launch_split_f32x2(const double* a, float* hi, float* lo, size_t n, cudaStream_t s);
 // Tensor-core tile of one shared operator: bytes of the BF16 image, and its build from the

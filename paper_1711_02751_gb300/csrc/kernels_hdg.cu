@@ -296,12 +296,12 @@ __global__ void split_kernel(const double* __restrict__ a, float* __restrict__ h
         split(a[i], hi[i], lo[i]);
 }
 
-// Z = A^{-1} R1 with the FP32-pair operator: one thread per (element, row), as apply_ainv_kernel.
-template <int P>
+// Z = A^{-1} R1 with the FP32-pair operator: one thread per (element, row), as apply_ainv_kernel;
+// EPB elements per block (the tile the autotuner picks; results do not depend on it).
+template <int P, int EPB>
 __global__ void apply_ainv_x2_kernel(Geom g, const float* __restrict__ Ahi, const float* __restrict__ Alo,
                                      const double* __restrict__ R1, double* __restrict__ Z) {
     constexpr int Np = P * P, NV = 3 * Np;
-    constexpr int EPB = (256 / NV) > 0 ? 256 / NV : 1;
     __shared__ float sxh[EPB][NV], sxl[EPB][NV];
     const int le = threadIdx.x / NV, r = threadIdx.x % NV;
     const int e = blockIdx.x * EPB + le;
@@ -317,14 +317,14 @@ __global__ void apply_ainv_x2_kernel(Geom g, const float* __restrict__ Ahi, cons
     Z[(r / Np) * fs + (size_t)e * Np + r % Np] = acc.value();
 }
 
-// Q = Z + beta A^{-1}_{:, boundary} (tau qhat), Lst = (Q - R1) / a_ii with the FP32-pair operator.
-template <int P>
+// Q = Z + beta A^{-1}_{:, boundary} (tau qhat), Lst = (Q - R1) / a_ii with the FP32-pair operator;
+// EPB elements per block as above.
+template <int P, int EPB>
 __global__ void recover_x2_kernel(Geom g, const float* __restrict__ Ahi, const float* __restrict__ Alo,
                                   const double* __restrict__ Z, const double* __restrict__ R1,
                                   const double* __restrict__ tau_edge, const double* __restrict__ qhat, double beta,
                                   double inv_aii, double* __restrict__ Q, double* __restrict__ Lst) {
     constexpr int Np = P * P, NV = 3 * Np, NF = 3 * P;
-    constexpr int EPB = (256 / NV) > 0 ? 256 / NV : 1;
     __shared__ float suh[EPB][NV], sul[EPB][NV];
     const int le = threadIdx.x / NV, r = threadIdx.x % NV;
     const int e = blockIdx.x * EPB + le;
@@ -493,6 +493,96 @@ cudaError_t assemble_launch(const Geom& g, const double* Se, double* S7, double*
     return cudaGetLastError();
 }
 
+// Tiles (elements per block) of the FP32-pair local kernels: index 0 is 256 / NV, then 1, 2, 4, 8
+// where the block stays within 1024 threads.
+template <int P>
+constexpr int tile_epb(int t) {
+    constexpr int NV = 3 * P * P;
+    const int e = t == 0 ? (256 / NV > 0 ? 256 / NV : 1) : (1 << (t - 1));
+    return e * NV <= 1024 ? e : 0;
+}
+
+template <int P, int EPB>
+void x2_apply(const Geom& g, const LocalOps& ops, const double* R1, double* Z, cudaStream_t s) {
+    constexpr int NV = 3 * P * P;
+    if constexpr (EPB > 0 && EPB * NV <= 1024) {
+        apply_ainv_x2_kernel<P, EPB><<<(g.n_el + EPB - 1) / EPB, EPB * NV, 0, s>>>(g, ops.Ahi, ops.Alo, R1, Z);
+        count_launches(1);
+    }
+}
+
+template <int P, int EPB>
+void x2_recover(const Geom& g, const LocalOps& ops, const double* Z, const double* R1, const double* tau_edge,
+                const double* qhat, double beta, double inv_aii, double* Q, double* Lst, cudaStream_t s) {
+    constexpr int NV = 3 * P * P;
+    if constexpr (EPB > 0 && EPB * NV <= 1024) {
+        recover_x2_kernel<P, EPB><<<(g.n_el + EPB - 1) / EPB, EPB * NV, 0, s>>>(g, ops.Ahi, ops.Alo, Z, R1, tau_edge,
+                                                                              qhat, beta, inv_aii, Q, Lst);
+        count_launches(1);
+    }
+}
+
+template <int P>
+void x2_apply_tile(int t, const Geom& g, const LocalOps& ops, const double* R1, double* Z, cudaStream_t s) {
+    switch (t) {
+        case 1: return x2_apply<P, tile_epb<P>(1)>(g, ops, R1, Z, s);
+        case 2: return x2_apply<P, tile_epb<P>(2)>(g, ops, R1, Z, s);
+        case 3: return x2_apply<P, tile_epb<P>(3)>(g, ops, R1, Z, s);
+        case 4: return x2_apply<P, tile_epb<P>(4)>(g, ops, R1, Z, s);
+        default: return x2_apply<P, tile_epb<P>(0)>(g, ops, R1, Z, s);
+    }
+}
+
+template <int P>
+void x2_recover_tile(int t, const Geom& g, const LocalOps& ops, const double* Z, const double* R1,
+                     const double* tau_edge, const double* qhat, double beta, double inv_aii, double* Q, double* Lst,
+                     cudaStream_t s) {
+    switch (t) {
+        case 1: return x2_recover<P, tile_epb<P>(1)>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s);
+        case 2: return x2_recover<P, tile_epb<P>(2)>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s);
+        case 3: return x2_recover<P, tile_epb<P>(3)>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s);
+        case 4: return x2_recover<P, tile_epb<P>(4)>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s);
+        default: return x2_recover<P, tile_epb<P>(0)>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s);
+    }
+}
+
+// Time every valid tile of both FP32-pair kernels on the handle's own operators (one warm-up and
+// three timed launches each, CUDA events on the stream) and keep the fastest in ops.
+template <int P>
+cudaError_t autotune_x2(const Geom& g, LocalOps& ops, double* R1, double* Z, const double* tau_edge,
+                        const double* qhat, double* Q, double* Lst, cudaStream_t s) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return cudaGetLastError();
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return cudaGetLastError();
+    }
+    float best_c = 1e30f, best_r = 1e30f;
+    cudaError_t err = cudaSuccess;
+    for (int t = 0; t < 5 && err == cudaSuccess; ++t) {
+        if (tile_epb<P>(t) == 0 || (t > 0 && tile_epb<P>(t) == tile_epb<P>(0))) continue;
+        float ms_c = 0.f, ms_r = 0.f;
+        x2_apply_tile<P>(t, g, ops, R1, Z, s);
+        cudaEventRecord(a, s);
+        for (int k = 0; k < 3; ++k) x2_apply_tile<P>(t, g, ops, R1, Z, s);
+        cudaEventRecord(b, s);
+        err = cudaEventSynchronize(b);
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms_c, a, b);
+        x2_recover_tile<P>(t, g, ops, Z, R1, tau_edge, qhat, 1.0, 1.0, Q, Lst, s);
+        cudaEventRecord(a, s);
+        for (int k = 0; k < 3; ++k) x2_recover_tile<P>(t, g, ops, Z, R1, tau_edge, qhat, 1.0, 1.0, Q, Lst, s);
+        cudaEventRecord(b, s);
+        if (err == cudaSuccess) err = cudaEventSynchronize(b);
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms_r, a, b);
+        if (err == cudaSuccess && ms_c < best_c) { best_c = ms_c; ops.tile_condense = tile_epb<P>(t); ops.tile_condense_index = t; }
+        if (err == cudaSuccess && ms_r < best_r) { best_r = ms_r; ops.tile_recover = tile_epb<P>(t); ops.tile_recover_index = t; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (err == cudaSuccess) err = cudaGetLastError();
+    return err;
+}
+
 template <int P>
 cudaError_t condense_launch(const Geom& g, const LocalOps& ops, const double* R1, const double* phiB,
                             const double* tau_edge, double* Z, double* gvec, cudaStream_t s, double t) {
@@ -504,8 +594,7 @@ cudaError_t condense_launch(const Geom& g, const LocalOps& ops, const double* R1
                                         ops.error, s);
         if (e != cudaSuccess) return e;
     } else if (ops.kind == 3) {
-        apply_ainv_x2_kernel<P><<<blocks, EPB * NV, 0, s>>>(g, ops.Ahi, ops.Alo, R1, Z);
-        count_launches(1);
+        x2_apply_tile<P>(ops.tile_condense_index, g, ops, R1, Z, s);
     } else if (ops.kind == 1) {
         apply_ainv_kernel<P, float><<<blocks, EPB * NV, 0, s>>>(g, ops.Ainv32, R1, Z);
         count_launches(1);
@@ -528,10 +617,11 @@ cudaError_t recover_launch(const Geom& g, const LocalOps& ops, const double* Z, 
     const int blocks = (g.n_el + EPB - 1) / EPB;
     if (ops.kind == 2)
         return launch_local_tc(g, 1, ops.image, R1, Z, tau_edge, qhat, beta, inv_aii, Q, Lst, ops.error, s);
-    if (ops.kind == 3)
-        recover_x2_kernel<P><<<blocks, EPB * NV, 0, s>>>(g, ops.Ahi, ops.Alo, Z, R1, tau_edge, qhat, beta,
-                                                         inv_aii, Q, Lst);
-    else if (ops.kind == 1)
+    if (ops.kind == 3) {
+        x2_recover_tile<P>(ops.tile_recover_index, g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s);
+        return cudaGetLastError();
+    }
+    if (ops.kind == 1)
         recover_kernel<P, float><<<blocks, EPB * NV, 0, s>>>(g, ops.Ainv32, Z, R1, tau_edge, qhat, beta,
                                                              inv_aii, Q, Lst);
     else
@@ -542,6 +632,24 @@ cudaError_t recover_launch(const Geom& g, const LocalOps& ops, const double* Z, 
 }
 
 }  // namespace
+
+cudaError_t launch_autotune_local(const Geom& g, LocalOps& ops, double* R1, double* Z, const double* tau_edge,
+                                  const double* qhat, double* Q, double* Lst, cudaStream_t s) {
+    if (ops.kind != 3) return cudaSuccess;
+#define CALL(P) autotune_x2<P>(g, ops, R1, Z, tau_edge, qhat, Q, Lst, s)
+    switch (g.P) {
+        case 2: return CALL(2);
+        case 3: return CALL(3);
+        case 4: return CALL(4);
+        case 5: return CALL(5);
+        case 6: return CALL(6);
+        case 7: return CALL(7);
+        case 8: return CALL(8);
+        case 9: return CALL(9);
+        default: return cudaErrorInvalidValue;
+    }
+#undef CALL
+}
 
 cudaError_t launch_split_f32x2(const double* a, float* hi, float* lo, size_t n, cudaStream_t s) {
     size_t blocks = (n + 255) / 256;

@@ -50,7 +50,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_longlong), ("krylov_iterations", ctypes.c_longlong),
                 ("last_krylov_iterations", ctypes.c_int), ("last_rel_residual", ctypes.c_double),
                 ("mass", ctypes.c_double), ("kernel_launches", ctypes.c_longlong), ("time", ctypes.c_double),
-                ("last_guess_order", ctypes.c_int)]
+                ("last_guess_order", ctypes.c_int), ("local_tile_condense", ctypes.c_int),
+                ("local_tile_recover", ctypes.c_int)]
 
 
 _lib = None
