@@ -661,7 +661,9 @@ def main():
                       "krylov_iterations_per_stage": r["stats"]["krylov_iterations"] / max(1, 2 * r["stats"]["steps"]),
                       "kernel_breakdown_ms": {c: {"ms": round(v[0], 3), "groups": v[1]} for c, v in r["ktimes"].items()},
                       "roofline": _roofline(N, k, r["ktimes"], p, fp64_tflops, hbm),
-                      "e2e": f["e2e"], "gpu_launches": r["launches"]}
+                      "e2e": f["e2e"], "gpu_launches": r["launches"],
+                      "local_tiles": {"condense": r["stats"].get("local_tile_condense", 0),
+                                      "recover": r["stats"].get("local_tile_recover", 0)}}
     hr = forms[head]["r"]
     per_step = hr["per_step"]
     p50 = statistics.median(per_step)
