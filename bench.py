@@ -58,6 +58,8 @@ def _args():
                     help="Gram-Schmidt of the mixed form's inner cycles: 0 twice (CGS2), 1 once")
     ap.add_argument("--residual-f32x2", type=int, default=1, choices=[0, 1],
                     help="mixed form: refinement residual in FP32-pair (FP64-class) arithmetic")
+    ap.add_argument("--local-dense", type=int, default=0, choices=[0, 1],
+                    help="local solves: 0 Schur complement on phi (library default), 1 dense A^-1")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true",
@@ -203,7 +205,7 @@ class ClockSampler:
 
 
 # ---- roofline --------------------------------------------------------------------------------
-def _algorithmic(N, k, cls, precision="fp64"):
+def _algorithmic(N, k, cls, precision="fp64", dense=False):
     """(bytes, flops) one launch group of a kernel class moves / performs."""
     P = k + 1
     NF, NV, Np = 3 * P, 3 * P * P, P * P
@@ -211,12 +213,17 @@ def _algorithmic(N, k, cls, precision="fp64"):
     if cls == "spmv":   # 6 off-diagonal NF x NF blocks + column ids + x and y once
         w = 4 if precision == "mixed" else 8
         return n_edges * (6 * NF * NF * w + 6 * 4 + 2 * NF * w), n_edges * NF * (12 * NF + 1)
-    if cls == "condense":   # A^{-1} once, R1 in, Z out; then Z face values + phiB in, g out
-        return (n_el * (NV * NV * 8 + 2 * NV * 8) + n_edges * NF * 8 * 3,
-                n_el * 2 * NV * NV)
-    if cls == "recover":    # boundary columns of A^{-1}, Z, R1 in, Q, L out, traces in
+    # local solves: dense A^{-1} ((3 Np)^2 numbers), or the Schur complement on phi: the (phi, phi)
+    # block of A^{-1} (Np^2) and (1/d, cx, cy, phi_B) per node, 2 Np^2 + Np (8P + 26) flops
+    op_b = n_el * NV * NV * 8 if dense else n_el * (Np * Np + 4 * Np) * 8
+    if cls == "condense":   # operator once, R1 in, Z out; then Z face values + phiB in, g out
+        return (op_b + n_el * 2 * NV * 8 + n_edges * NF * 8 * 3,
+                n_el * 2 * NV * NV if dense else n_el * (2 * Np * Np + Np * (8 * P + 26)))
+    if cls == "recover":    # operator (dense: its boundary columns), Z, R1 in, Q, L out, traces in
         nb = 3 * (4 * P - 4)
-        return n_el * (NV * nb * 8 + 4 * NV * 8) + n_edges * NF * 8, n_el * 2 * NV * nb
+        if dense:
+            return n_el * (NV * nb * 8 + 4 * NV * 8) + n_edges * NF * 8, n_el * 2 * NV * nb
+        return op_b + n_el * 4 * NV * 8 + n_edges * NF * 8, n_el * (2 * Np * Np + Np * (8 * P + 32))
     if cls == "dg":
         return n_el * (2 * NV + Np) * 8, n_el * Np * 60
     return None, None
@@ -326,12 +333,12 @@ def _e2e(sim, stream, steps, dist, h, hu, hv):
     return ms, 3 * n * 8
 
 
-def _roofline(N, k, ktimes, precision, fp64_tflops, hbm):
-    dom = max((c for c in ktimes if ktimes[c][1] > 0 and _algorithmic(N, k, c, precision)[0]),
+def _roofline(N, k, ktimes, precision, fp64_tflops, hbm, dense=False):
+    dom = max((c for c in ktimes if ktimes[c][1] > 0 and _algorithmic(N, k, c, precision, dense)[0]),
               key=lambda c: ktimes[c][0])
     tot_ms, n_l = ktimes[dom]
     avg_s = tot_ms / n_l / 1e3
-    byt, flo = _algorithmic(N, k, dom, precision)
+    byt, flo = _algorithmic(N, k, dom, precision, dense)
     alu_peak = fp64_tflops if (precision == "fp64" or dom != "spmv") else FP32_NOMINAL_TFLOPS
     t_hbm, t_alu = byt / (hbm * 1e9), flo / (alu_peak * 1e12)
     if t_hbm >= t_alu:
@@ -620,7 +627,8 @@ def main():
                      krylov_rtol=args.mixed_rtol if precision == "mixed" else 0.0,
                      local_precision=args.local if precision == "mixed" else "fp64",
                      krylov_guess=args.guess, spmv_kernel=args.spmv_kernel, krylov_ortho=args.ortho,
-                     residual_f32x2=bool(args.residual_f32x2) and precision == "mixed")
+                     residual_f32x2=bool(args.residual_f32x2) and precision == "mixed",
+                     local_dense=bool(args.local_dense))
         sim.set_state(h, hu, hv)
         for _ in range(args.warmup):
             sim.step(1)
@@ -660,7 +668,10 @@ def main():
                       "ms_per_step": r["ms_total"] / args.steps,
                       "krylov_iterations_per_stage": r["stats"]["krylov_iterations"] / max(1, 2 * r["stats"]["steps"]),
                       "kernel_breakdown_ms": {c: {"ms": round(v[0], 3), "groups": v[1]} for c, v in r["ktimes"].items()},
-                      "roofline": _roofline(N, k, r["ktimes"], p, fp64_tflops, hbm),
+                      "roofline": _roofline(N, k, r["ktimes"], p, fp64_tflops, hbm, bool(args.local_dense)),
+                      "local_roofline": {c: _roofline(N, k, {c: r["ktimes"][c]}, p, fp64_tflops, hbm,
+                                                      bool(args.local_dense))
+                                         for c in ("condense", "recover") if r["ktimes"].get(c, (0, 0))[1] > 0},
                       "e2e": f["e2e"], "gpu_launches": r["launches"],
                       "local_tiles": {"condense": r["stats"].get("local_tile_condense", 0),
                                       "recover": r["stats"].get("local_tile_recover", 0)}}
@@ -688,11 +699,13 @@ def main():
                                    f"dt={dt:.6g} (advective CFL 0.5: 0.5 h/((2k+1) 2max|u|))", "form": head,
                        "dof": dof, "parallelism": "replicas" if world > 1 else "single",
                        "gmres_restart": args.restart or 10,
-                       "krylov_guess": {-1: "zero", 0: "quartic extrapolation (default)", 1: "previous step",
+                       "local_solve": "dense A^-1" if args.local_dense else "Schur complement on phi",
+                       "krylov_guess": {-1: "zero", 0: "adaptive, up to quartic extrapolation (default)",
+                                        1: "previous step",
                                         2: "linear extrapolation", 3: "quadratic extrapolation",
                                         4: "cubic extrapolation", 5: "quartic extrapolation",
                                         6: "quintic extrapolation"}[args.guess],
-                       "l2": "inputs larger than L2 (A^-1 and trace matrix are GBs)"},
+                       "l2": "inputs larger than L2 (trace matrix GBs, local operators >= 0.5 GB)"},
             "latency_ms": {"p50": p50, "p99": p99},
             "rel_l2_mixed_vs_fp64": err,
             "gpu_launches": summary[head]["gpu_launches"], "roofline": summary[head]["roofline"],

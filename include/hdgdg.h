@@ -132,6 +132,14 @@ typedef struct {
     int residual_f32x2;  /* mixed form: 1 = the refinement's true residual g - S qhat in FP64-class
                             arithmetic on the FP32 pipes (S as an FP32 pair, compensated Dot2
                             sums, ~1e-13 relative; see HDGDG_LOCAL_F32X2); 0 = FP64. */
+    int local_dense;     /* HDGDG_LOCAL_FP64 and HDGDG_LOCAL_F32X2: 0 (default) = A^{-1} applied
+                            through the Schur complement on phi.  With collocated GLL nodes the
+                            velocity blocks of A are diagonal, so U and V are eliminated node by
+                            node and only the (phi, phi) block of A^{-1} ((k+1)^4 numbers per
+                            element) is stored and read; the derivative couplings are rebuilt from
+                            phi_B, tau and the GLL derivative matrix.  1 = the whole per-element
+                            A^{-1} ((3 (k+1)^2)^2 numbers) as one dense product.  Same result up to
+                            rounding.  The other local precisions are always dense. */
 } hdgdg_config;
 
 /* HDGDG_VORTEX: the exact-solution boundary conditions of the paper's moving-vortex test
@@ -151,9 +159,9 @@ typedef struct {
     double time;                  /* simulated time since set_state (steps x dt) */
     int last_guess_order;         /* extrapolation order the most recent trace solve started from
                                      (0: zero start) */
-    /* HDGDG_LOCAL_F32X2 on meshes of >= 4096 elements: elements per block of the condensation
-     * and recovery kernels, picked at create by timing each candidate tile on the handle's own
-     * operators (0: the default tile, not tuned). */
+    /* HDGDG_LOCAL_F32X2 with local_dense = 1 on meshes of >= 4096 elements: elements per block
+     * of the condensation and recovery kernels, picked at create by timing each candidate tile on
+     * the handle's own operators (0: the default tile, not tuned). */
     int local_tile_condense;
     int local_tile_recover;
 } hdgdg_stats;

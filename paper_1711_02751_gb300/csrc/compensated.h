@@ -8,6 +8,8 @@
 // explicit _rn intrinsics keep the compiler from fusing the steps.
 #pragma once
 
+#include "fastcvt.h"
+
 namespace hdgdg {
 
 __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
@@ -31,12 +33,13 @@ struct Dot2 {
         c = __fmaf_rn(ah, xl, c);
         c = __fmaf_rn(al, xh, c);
     }
-    __device__ __forceinline__ double value() const { return (double)p + (double)c; }
+    __device__ __forceinline__ double value() const { return f32_to_f64(p) + f32_to_f64(c); }
 };
 
+// v = hi + lo to ~48 bits; the conversions run on the integer pipes (fastcvt.h), one FP64 subtract
 __device__ __forceinline__ void split(double v, float& hi, float& lo) {
-    hi = (float)v;
-    lo = (float)(v - (double)hi);
+    hi = f64_to_f32(v);
+    lo = f64_to_f32(v - f32_to_f64(hi));
 }
 
 }  // namespace hdgdg

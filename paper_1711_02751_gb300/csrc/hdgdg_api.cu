@@ -52,7 +52,8 @@ bool valid(const hdgdg_config* c) {
            c->local_precision <= HDGDG_LOCAL_F32X2 &&
            (c->local_precision != HDGDG_LOCAL_BF16 || c->degree_k <= 4) &&   // tensor-core tiles: k <= 4
            c->krylov_guess >= -1 && c->krylov_guess <= 6 && (c->spmv_kernel == 0 || c->spmv_kernel == 1) &&
-           (c->krylov_ortho == 0 || c->krylov_ortho == 1) && (c->residual_f32x2 == 0 || c->residual_f32x2 == 1);
+           (c->krylov_ortho == 0 || c->krylov_ortho == 1) && (c->residual_f32x2 == 0 || c->residual_f32x2 == 1) &&
+           (c->local_dense == 0 || c->local_dense == 1);
 }
 
 bool explicit_scheme(const hdgdg_config* c) { return c->scheme == HDGDG_RK2 || c->scheme == HDGDG_RK3; }
@@ -61,6 +62,11 @@ int restart_of(const hdgdg_config* c) { return c->krylov_restart > 0 ? c->krylov
 
 // order of the trace-solve initial guess (0: start from zero)
 int guess_order(const hdgdg_config* c) { return c->krylov_guess < 0 ? 0 : c->krylov_guess == 0 ? 5 : c->krylov_guess; }
+
+// local solves through the Schur complement on phi (FP64 and FP32-pair local arithmetic)
+bool local_schur(const hdgdg_config* c) {
+    return !c->local_dense && (c->local_precision == HDGDG_LOCAL_FP64 || c->local_precision == HDGDG_LOCAL_F32X2);
+}
 
 Plan make_plan(const hdgdg_config* c) {
     Plan p;
@@ -102,7 +108,11 @@ Plan make_plan(const hdgdg_config* c) {
     b += 64 + sizeof(GmresCtl);                               // flags, GMRES control block
     if (c->local_precision == HDGDG_LOCAL_FP32) b += n_el * (size_t)p.NV * p.NV * sizeof(float);
     if (c->local_precision == HDGDG_LOCAL_BF16) b += tc_image_bytes((int)P);
-    if (c->local_precision == HDGDG_LOCAL_F32X2) b += 2 * n_el * (size_t)p.NV * p.NV * sizeof(float);
+    if (local_schur(c)) {   // (phi, phi) block of A^{-1}, 4 numbers per node, 2 P x P per instance
+        b += (n_el * Np * Np + 4 * n_el * Np + 2 * B * Np) * d;   // FP64 or FP32 pairs: 8 bytes each
+    } else if (c->local_precision == HDGDG_LOCAL_F32X2) {
+        b += 2 * n_el * (size_t)p.NV * p.NV * sizeof(float);
+    }
     if (c->precision == HDGDG_MIXED && c->residual_f32x2) b += n_edges * 6 * (size_t)p.NF * p.NF * sizeof(float);
     b += 2 * (size_t)guess_order(c) * p.s * p.nt * d;         // previous stage solutions and products
     p.persistent = b;
@@ -281,7 +291,9 @@ struct hdgdg_sim {
     int n_hist[kMaxStages] = {};         // the final true residual: g - r), and their count
     double dt_fingerprint = 0.0;  // sum_i (i + 1) dt_i of a batch with per-instance time steps
     float* Ainv32 = nullptr;      // HDGDG_LOCAL_FP32
-    float *Ahi = nullptr, *Alo = nullptr;   // HDGDG_LOCAL_F32X2
+    float *Ahi = nullptr, *Alo = nullptr;   // HDGDG_LOCAL_F32X2, dense
+    double *Sphi = nullptr, *Saux = nullptr, *Seg = nullptr;   // Schur-complement local solves (8-byte
+                                                                // values: FP64 or FP32 pairs)
     void* tc_image = nullptr;     // HDGDG_LOCAL_BF16: the shared operator's tensor-core tile
     LocalOps ops;
     int* Scol = nullptr;
@@ -492,7 +504,7 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
         gt.nq = avail;
         for (int j = 0; j < avail; ++j) gt.y[j] = sim->yhist[stage][j];
         std::memcpy(gt.c, coef, sizeof(coef));
-        CU(launch_guess_norms(n, g, gt, sim->red, dv_guess(sim), st));
+        CU(launch_guess_norms(n, g, gt, sim->red, dv_guess(sim), st, kMixed));
         CU(cudaMemcpyAsync(sim->hbuf, dv_guess(sim), (avail + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
         TRY(sync(sim));
         std::memcpy(cand, sim->hbuf, (avail + 1) * sizeof(double));
@@ -534,7 +546,10 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
             r.c[r.n++] = -coef[guess][j];
         }
         CU(launch_combine(n, g, r, sim->w, nullptr, st));
-        CU(cudaMemcpyAsync(dv_nrm(sim), dv_guess(sim) + guess, sizeof(double), cudaMemcpyDeviceToDevice, st));
+        if constexpr (kMixed)   // the candidates were FP32-pair estimates: the cycle's start norm exactly
+            CU(launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st));
+        else
+            CU(cudaMemcpyAsync(dv_nrm(sim), dv_guess(sim) + guess, sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
     CU(launch_gmres_solve_init(ctl, tol, inner_rel, maxit, st));
     int total = 0;
@@ -906,7 +921,19 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
     if (sing) return fail(sim, HDGDG_EINVAL, "a local operator block is singular");
     sim->ops.kind = 0;
     sim->ops.Ainv = sim->Ainv;
-    if (c->local_precision == HDGDG_LOCAL_FP32) {
+    if (local_schur(c)) {
+        const bool x2 = c->local_precision == HDGDG_LOCAL_F32X2;
+        TRY(dalloc(sim, &sim->Sphi, (size_t)g.n_el * Np * Np));
+        TRY(dalloc(sim, &sim->Saux, 4 * (size_t)g.n_el * Np));
+        TRY(dalloc(sim, &sim->Seg, 2 * (size_t)g.batch * Np));
+        CU(launch_schur_setup(g, sim->Ainv, sim->phiB, sim->tau, c->dt * sim->a_ii, x2, sim->Sphi, sim->Saux,
+                              sim->Seg, sim->stream));
+        sim->ops.kind = x2 ? 3 : 0;
+        sim->ops.schur = true;
+        sim->ops.S = sim->Sphi;
+        sim->ops.aux = sim->Saux;
+        sim->ops.EG = sim->Seg;
+    } else if (c->local_precision == HDGDG_LOCAL_FP32) {
         const size_t n = (size_t)g.n_el * p.NV * p.NV;
         TRY(dalloc(sim, &sim->Ainv32, n));
         CU(launch_to_f32(sim->Ainv, sim->Ainv32, n, sim->stream));

@@ -213,7 +213,19 @@ struct LocalOps {
     int tile_condense_index = 0, tile_recover_index = 0;  // their index in the candidate list
     const void* image = nullptr;    // kind 2: the shared A^{-1} as a BF16 tensor-core operand tile
     int* error = nullptr;           // kind 2: set when a bounded wait of the tensor-core kernel ran out
+    // Kinds 0 and 3 with schur set: A^{-1} applied through the Schur complement on phi.  Only the
+    // (phi, phi) block of A^{-1} is kept, S [n_el][col m][row n], with aux [n_el][4][Np] =
+    // (1/d, -cx, -cy, phi_B) per node and EG [batch][2][P][P] = (-E, -G) per instance; the values
+    // are double (kind 0) or FP32 pairs float2 (hi, lo) (kind 3).
+    bool schur = false;
+    const void* S = nullptr;
+    const void* aux = nullptr;
+    const void* EG = nullptr;
 };
+// Setup of the Schur-complement local operators (LocalOps::S, aux, EG) from the FP64 A^{-1}, as
+// double or, with f32x2, as FP32 pairs (float2).  dta = dt a_ii.
+cudaError_t launch_schur_setup(const Geom& g, const double* Ainv, const double* phiB, const double* tau_edge,
+                               double dta, bool f32x2, void* S, void* aux, void* EG, cudaStream_t s);
 // Condensation: Z = A^{-1} R1 per element, then g = -C Z edge by edge (pointwise rows).
 // t: time of the prescribed boundary traces (Dirichlet boundaries only)
 cudaError_t launch_condense(const Geom& g, const LocalOps& ops, const double* R1, const double* phiB,
@@ -285,8 +297,10 @@ struct GuessTerms {
     int nq;
 };
 size_t guess_scratch_doubles();
+// f32x2: the candidates and sums in FP32-pair arithmetic (compensated Dot2; each candidate to
+// ~1e-13 ||g||, against ~1e-15 ||g|| in FP64) -- the mixed form, whose tolerance is 1e-9 ||g||.
 cudaError_t launch_guess_norms(size_t n, const double* g, const GuessTerms& t, double* scratch, double* out,
-                               cudaStream_t s);
+                               cudaStream_t s, bool f32x2 = false);
 cudaError_t launch_multidot(const double* V, size_t ldv, int nv, const double* w, size_t n,
                             double* scratch, double* out, cudaStream_t s, const int* done = nullptr);
 cudaError_t launch_multidot(const float* V, size_t ldv, int nv, const float* w, size_t n,

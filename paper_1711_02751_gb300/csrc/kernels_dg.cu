@@ -11,6 +11,7 @@
 // tau_L* = max_pm sqrt(phi_B) is the per-edge-node tau_hat the library precomputes.
 #include <atomic>
 
+#include "fastcvt.h"
 #include "internal.h"
 
 namespace hdgdg {
@@ -75,32 +76,33 @@ dg_face_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ 
         if (em < 0) { phm = php; pbm = pbp; Um = xedge ? -Up : Up; Vm = xedge ? Vp : -Vp; }
         if (ep < 0) { php = phm; pbp = pbm; Up = xedge ? -Um : Um; Vp = xedge ? Vm : -Vm; }
     }
-    const Tc Phm = Tc(phm) + Tc(pbm), Php = Tc(php) + Tc(pbp);
+    // (conversions to the arithmetic type on the integer pipes, fastcvt.h)
+    const Tc pm = from_f64<Tc>(phm), pp = from_f64<Tc>(php);
+    const Tc Phm = pm + from_f64<Tc>(pbm), Php = pp + from_f64<Tc>(pbp);
     const Tc im = Tc(1) / Phm, ip = Tc(1) / Php;
     // normal (n) and tangential (t) momentum components along this edge's +axis
-    const Tc Unm = Tc(xedge ? Um : Vm), Utm = Tc(xedge ? Vm : Um);
-    const Tc Unp = Tc(xedge ? Up : Vp), Utp = Tc(xedge ? Vp : Up);
-    const Tc pm = Tc(phm), pp = Tc(php);
+    const Tc Unm = from_f64<Tc>(xedge ? Um : Vm), Utm = from_f64<Tc>(xedge ? Vm : Um);
+    const Tc Unp = from_f64<Tc>(xedge ? Up : Vp), Utp = from_f64<Tc>(xedge ? Vp : Up);
     // F_NL . n: (0, Un Un / phi + phi_eta^2 / 2, Un Ut / phi) in (normal, tangential) order
     Tc Fnm = Unm * Unm * im + Tc(0.5) * pm * pm, Ftm = Unm * Utm * im;
     Tc Fnp = Unp * Unp * ip + Tc(0.5) * pp * pp, Ftp = Unp * Utp * ip;
     const Tc tau_star = fmax(fabs(Unm) * im + sqrt(Phm), fabs(Unp) * ip + sqrt(Php));
     Tc hd, fph;
     if (FULL) {   // add F_L . n = (U_n, phi_eta phi_B, 0)
-        Fnm += pm * Tc(pbm);
-        Fnp += pp * Tc(pbp);
+        Fnm += pm * from_f64<Tc>(pbm);
+        Fnp += pp * from_f64<Tc>(pbp);
         hd = Tc(0.5) * tau_star;
         fph = Tc(0.5) * (Unm + Unp) + hd * (pm - pp);
     } else {
-        hd = Tc(0.5) * (tau_star - Tc(tau_edge[(size_t)r * P + b]));
+        hd = Tc(0.5) * (tau_star - from_f64<Tc>(tau_edge[(size_t)r * P + b]));
         fph = hd * (pm - pp);
     }
     const Tc fn = Tc(0.5) * (Fnm + Fnp) + hd * (Unm - Unp);
     const Tc ft = Tc(0.5) * (Ftm + Ftp) + hd * (Utm - Utp);
     double* out = fface + (size_t)r * 3 * P;
-    out[b] = fph;
-    out[(xedge ? 1 : 2) * P + b] = fn;
-    out[(xedge ? 2 : 1) * P + b] = ft;
+    out[b] = to_f64(fph);
+    out[(xedge ? 1 : 2) * P + b] = to_f64(fn);
+    out[(xedge ? 2 : 1) * P + b] = to_f64(ft);
 }
 
 // Element pass: volume term from the nodal F_NL (shared memory), minus the lifted face fluxes.
@@ -119,8 +121,8 @@ dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict_
     // the kernel-parameter (constant) bank serialises a warp's loads of different addresses
     __shared__ Tc sDh[Np], sD[Np];
     if (threadIdx.x < Np) {
-        sDh[threadIdx.x] = Tc(g.Dhat[threadIdx.x]);
-        sD[threadIdx.x] = Tc(g.D[threadIdx.x]);
+        sDh[threadIdx.x] = from_f64<Tc>(g.Dhat[threadIdx.x]);
+        sD[threadIdx.x] = from_f64<Tc>(g.D[threadIdx.x]);
     }
 
     const int le = threadIdx.x / Np;
@@ -133,7 +135,8 @@ dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict_
     Tc ph_own = Tc(0);
     if (live) {
         const size_t o = (size_t)e * Np + n;
-        const Tc ph = Tc(q[o]), U = Tc(q[fs + o]), V = Tc(q[2 * fs + o]), pb = Tc(phiB[o]);
+        const Tc ph = from_f64<Tc>(q[o]), U = from_f64<Tc>(q[fs + o]), V = from_f64<Tc>(q[2 * fs + o]),
+                 pb = from_f64<Tc>(phiB[o]);
         nl_flux<Tc>(ph, U, V, pb, &sFr[le][0 * Np + n], &sFr[le][1 * Np + n], &sFr[le][2 * Np + n], &sFr[le][3 * Np + n]);
         if (FULL) {
             sFr[le][0 * Np + n] += ph * pb;
@@ -156,7 +159,7 @@ dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict_
         rV += cx * sFr[le][1 * Np + j * P + a] + cy * sFr[le][3 * Np + a * P + i];
         if (FULL) rph += cx * sMr[le][0 * Np + j * P + a] + cy * sMr[le][1 * Np + a * P + i];
     }
-    const Tc th = Tc(g.two_over_h);
+    const Tc th = from_f64<Tc>(g.two_over_h);
     rU *= th;
     rV *= th;
     rph *= th;
@@ -170,7 +173,7 @@ dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict_
         rU += ph_own * th * dBx;
         rV += ph_own * th * dBy;
     }
-    const Tc lift = Tc(g.two_over_h * g.inv_w0);
+    const Tc lift = from_f64<Tc>(g.two_over_h * g.inv_w0);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const bool on = (f == 0 && i == 0) || (f == 1 && i == P - 1) || (f == 2 && j == 0) ||
@@ -179,15 +182,15 @@ dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict_
         const int b = (f < 2) ? j : i;
         const double* fl = fface + (size_t)edge_of_face(e, f, g) * 3 * P;
         const Tc sgn = (f & 1) ? lift : -lift;   // outward normal is + on faces 1, 3
-        rph -= sgn * Tc(fl[b]);
-        rU -= sgn * Tc(fl[P + b]);
-        rV -= sgn * Tc(fl[2 * P + b]);
+        rph -= sgn * from_f64<Tc>(fl[b]);
+        rU -= sgn * from_f64<Tc>(fl[P + b]);
+        rV -= sgn * from_f64<Tc>(fl[2 * P + b]);
     }
     const size_t o = (size_t)e * Np + n;
     const double sc = scale * dt_factor(g, e);   // this instance's time step
-    out[o] = sc * double(rph);
-    out[fs + o] = sc * double(rU);
-    out[2 * fs + o] = sc * double(rV);
+    out[o] = sc * to_f64(rph);
+    out[fs + o] = sc * to_f64(rU);
+    out[2 * fs + o] = sc * to_f64(rV);
 }
 
 __global__ void combine_kernel(size_t n, const double* __restrict__ base, CombineTerms t,

@@ -385,25 +385,30 @@ __global__ void edge_rhs_kernel(Geom g, const double* __restrict__ Z, const doub
         out[2 * P + b] = V;
         return;
     }
-    double acc[3] = {0.0, 0.0, 0.0};
+    // face values of the two sides, the momentum as normal (n) and tangential (t) components along
+    // the edge's +axis; a wall's absent side is the mirror of the other (same phi and tangential
+    // momentum, opposite normal momentum)
+    double zph[2], zn[2], zt[2], pb[2];
     for (int side = 0; side < 2; ++side) {
         int e = side == 0 ? em : ep;
         const int f = side == 0 ? fm : fp;
-        const bool mirror = e < 0;                 // wall: the mirror of the other element
+        const bool mirror = e < 0;
         if (mirror) e = e_in;
         const size_t o = (size_t)e * Np + face_node(mirror ? f_in : f, b, P);
-        double zph = Z[o], zU = Z[fs + o], zV = Z[2 * fs + o];
-        const double pb = phiB[o];
-        if (mirror) { if (xedge) zU = -zU; else zV = -zV; }
-        const double sgn = side == 0 ? 1.0 : -1.0;
-        const double nx = xedge ? sgn : 0.0, ny = xedge ? 0.0 : sgn;
-        acc[0] += nx * zU + ny * zV + tau * zph;
-        acc[1] += nx * pb * zph + tau * zU;
-        acc[2] += ny * pb * zph + tau * zV;
+        const double zU = Z[fs + o], zV = Z[2 * fs + o];
+        zph[side] = Z[o];
+        pb[side] = phiB[o];
+        zn[side] = mirror ? -(xedge ? zU : zV) : (xedge ? zU : zV);
+        zt[side] = xedge ? zV : zU;
     }
-    out[0 * P + b] = -acc[0];
-    out[1 * P + b] = -acc[1];
-    out[2 * P + b] = -acc[2];
+    // g = -(C_- Z_- + C_+ Z_+), the normal +1 on the minus side and -1 on the plus side:
+    //   phi_hat row: -(n.U + tau phi) summed;  normal row: -(n phi_B phi + tau U_n);  tangential: -tau U_t
+    const double g0 = (zn[1] - zn[0]) - tau * (zph[0] + zph[1]);
+    const double gn = (pb[1] * zph[1] - pb[0] * zph[0]) - tau * (zn[0] + zn[1]);
+    const double gt = -tau * (zt[0] + zt[1]);
+    out[b] = g0;
+    out[(xedge ? 1 : 2) * P + b] = gn;
+    out[(xedge ? 2 : 1) * P + b] = gt;
 }
 
 // Q = Z + beta A^{-1}_{:, boundary} (tau qhat);  Lst = (Q - R1) * inv_aii.  T as above.
@@ -448,6 +453,299 @@ __global__ void recover_kernel(Geom g, const T* __restrict__ Ainv, const double*
     const double q = Z[o] + beta * dt_factor(g, e) * (double)acc;
     Q[o] = q;
     Lst[o] = (q - R1[o]) * inv_aii;
+}
+
+// ---- Local solves through the Schur complement on phi ---------------------------------------------
+// With collocated GLL nodes the velocity blocks of A are diagonal and equal to the phi block's
+// diagonal d_n = 1 + kk sum_{faces at n} tau:
+//   A = [[diag(d), Bx, By], [Cx, diag(d), 0], [Cy, 0, diag(d)]],
+//   (Bx v)_(i,j) = sum_a E[i][a] v_(a,j),   E = alpha Dhat + kk diag(nv),
+//   (Cx v)_(i,j) = sum_a G[i][a] phi_B v_(a,j) + cx_(i,j) v_(i,j),   G = alpha Dhat,
+//   cx = alpha (d_x phi_B) + kk nv(i) phi_B,
+// alpha = -dta (2/h), kk = dta (2/h) / w_0, nv(i) = [i = P-1] - [i = 0] the outward normal of the
+// element's x-face through the node (By, Cy alike along y with the same E and G, cy with nv(j);
+// these are the rows build_local_kernel fills).  Eliminating U and V:
+//   S phi = x_phi - Bx d^{-1} x_U - By d^{-1} x_V,   S = diag(d) - Bx d^{-1} Cx - By d^{-1} Cy,
+//   U = d^{-1} (x_U - Cx phi),   V = d^{-1} (x_V - Cy phi),
+// and S^{-1} is the (phi, phi) block of A^{-1}.  Per element the kernels read Np^2 + 4 Np numbers
+// of operator data instead of (3 Np)^2; E and G depend only on the instance's time step.  Each
+// output is one dot product: s over 2P + 1 terms, phi over Np, d U and d V over P + 2.
+
+// Arithmetic of these solves.  ArithF64: FP64.  ArithF2: unevaluated FP32 pairs (hi, lo) with
+// the compensated Dot2 sums of compensated.h -- FP64-class results on the FP32 pipes.
+struct ArithF64 {
+    using T = double;
+    struct Acc {
+        double s = 0.0;
+        __device__ __forceinline__ void add(double a, double x) { s = fma(a, x, s); }
+        __device__ __forceinline__ double get() const { return s; }
+    };
+    __device__ __forceinline__ static double from(double v) { return v; }
+    __device__ __forceinline__ static double to(double v) { return v; }
+    __device__ __forceinline__ static double mul(double a, double b) { return a * b; }
+};
+
+struct ArithF2 {
+    using T = float2;
+    struct Acc {
+        Dot2 d;
+        __device__ __forceinline__ void add(float2 a, float2 x) { d.add(a.x, a.y, x.x, x.y); }
+        __device__ __forceinline__ float2 get() const {
+            float2 r;
+            two_sum(d.p, d.c, r.x, r.y);
+            return r;
+        }
+    };
+    __device__ __forceinline__ static float2 from(double v) {
+        float2 r;
+        split(v, r.x, r.y);
+        return r;
+    }
+    __device__ __forceinline__ static double to(float2 v) { return f32_to_f64(v.x) + f32_to_f64(v.y); }
+    // (a_hi + a_lo)(b_hi + b_lo): the exact a_hi b_hi (TwoProduct) plus the cross terms, renormalised
+    __device__ __forceinline__ static float2 mul(float2 a, float2 b) {
+        float p, e;
+        two_prod(a.x, b.x, p, e);
+        e = __fmaf_rn(a.x, b.y, e);
+        e = __fmaf_rn(a.y, b.x, e);
+        float2 r;
+        r.x = __fadd_rn(p, e);
+        r.y = __fsub_rn(e, __fsub_rn(r.x, p));
+        return r;
+    }
+};
+
+template <class A>
+__device__ __forceinline__ void store_from(typename A::T* dst, double v) { *dst = A::from(v); }
+
+// Setup, one thread per (element, node n): row n of the (phi, phi) block of A^{-1} into
+// S [n_el][col m][row n], and aux [n_el][4][Np] = (1/d, -cx, -cy, phi_B) at node n.
+template <int P, class A>
+__global__ void schur_setup_kernel(Geom g, const double* __restrict__ Ainv, const double* __restrict__ phiB,
+                                   const double* __restrict__ tau_edge, double dta, typename A::T* __restrict__ S,
+                                   typename A::T* __restrict__ aux) {
+    constexpr int Np = P * P, NV = 3 * Np;
+    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (t >= (size_t)g.n_el * Np) return;
+    const int e = (int)(t / Np), n = (int)(t % Np), i = n % P, j = n / P;
+    const double* Ae = Ainv + (size_t)e * NV * NV;
+    for (int m = 0; m < Np; ++m)   // (A^{-1})_{n m}; A^{-1} is stored column major
+        store_from<A>(&S[((size_t)e * Np + m) * Np + n], Ae[(size_t)m * NV + n]);
+    const double de = dta * dt_factor(g, e), th = g.two_over_h;
+    const double alpha = -de * th, kk = de * th * g.inv_w0;
+    double tsum = 0.0;
+    for (int f = 0; f < 4; ++f) {
+        const bool on = (f == 0 && i == 0) || (f == 1 && i == P - 1) || (f == 2 && j == 0) ||
+                        (f == 3 && j == P - 1);
+        if (on) tsum += tau_edge[(size_t)edge_of_face(e, f, g) * P + ((f < 2) ? j : i)];
+    }
+    const double* pb = phiB + (size_t)e * Np;
+    double dBx = 0.0, dBy = 0.0;
+    for (int a = 0; a < P; ++a) {
+        dBx += g.D[i * P + a] * pb[j * P + a];
+        dBy += g.D[j * P + a] * pb[a * P + i];
+    }
+    const double nx = (i == P - 1 ? 1.0 : 0.0) - (i == 0 ? 1.0 : 0.0);
+    const double ny = (j == P - 1 ? 1.0 : 0.0) - (j == 0 ? 1.0 : 0.0);
+    typename A::T* ax = aux + (size_t)e * 4 * Np;
+    store_from<A>(&ax[n], 1.0 / (1.0 + kk * tsum));
+    store_from<A>(&ax[Np + n], -(alpha * dBx + kk * nx * pb[n]));
+    store_from<A>(&ax[2 * Np + n], -(alpha * dBy + kk * ny * pb[n]));
+    store_from<A>(&ax[3 * Np + n], pb[n]);
+}
+
+// Setup, one thread per (instance, entry): EG [batch][2][P][P] = (-E, -G) of each instance.
+template <int P, class A>
+__global__ void schur_eg_kernel(Geom g, double dta, typename A::T* __restrict__ EG) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.batch * 2 * P * P) return;
+    const int inst = t / (2 * P * P), w = (t / (P * P)) % 2, r = (t % (P * P)) / P, a = t % P;
+    const double de = dta * dt_factor(g, inst * g.n_el_inst), th = g.two_over_h;
+    const double alpha = -de * th, kk = de * th * g.inv_w0;
+    double v = alpha * g.Dhat[r * P + a];
+    if (w == 0 && a == r) v += kk * ((r == P - 1 ? 1.0 : 0.0) - (r == 0 ? 1.0 : 0.0));
+    store_from<A>(&EG[t], -v);
+}
+
+template <int P, int EPB, class A>
+struct SchurSmem {
+    using T = typename A::T;
+    static constexpr int Np = P * P;
+    T EG[EPB][2][Np];   // the element's -E, -G (P x P each, row major)
+    T t[EPB][2][Np];    // d^{-1} x_U, d^{-1} x_V
+    T s[EPB][Np];       // Schur right-hand side
+    T w[EPB][Np];       // phi_B phi
+};
+
+// A^{-1} x for the element of thread (le, n) with x = (x0, xU, xV) at node n (each thread its
+// own node's values); returns phi, U, V at node n.  Every thread of the block calls it (its
+// barriers are block-wide); live marks threads of real elements.
+template <int P, int EPB, class A>
+__device__ __forceinline__ void schur_solve(SchurSmem<P, EPB, A>& sm, const Geom& g, int e, int le, int n,
+                                            bool live, const typename A::T* __restrict__ S,
+                                            const typename A::T* __restrict__ aux,
+                                            const typename A::T* __restrict__ EG, typename A::T x0,
+                                            typename A::T xU, typename A::T xV, typename A::T& phi,
+                                            typename A::T& U, typename A::T& V) {
+    using T = typename A::T;
+    constexpr int Np = P * P;
+    const int i = n % P, j = n / P;
+    const T one = A::from(1.0);
+    T rd{}, ncx{}, ncy{}, pb{};
+    if (live) {
+        const T* ax = aux + (size_t)e * 4 * Np;
+        rd = ax[n];
+        ncx = ax[Np + n];
+        ncy = ax[2 * Np + n];
+        pb = ax[3 * Np + n];
+        const T* eg = EG + (size_t)(e / g.n_el_inst) * 2 * Np;
+        sm.EG[le][0][n] = eg[n];
+        sm.EG[le][1][n] = eg[Np + n];
+        sm.t[le][0][n] = A::mul(xU, rd);
+        sm.t[le][1][n] = A::mul(xV, rd);
+    }
+    __syncthreads();
+    if (live) {   // s = x_phi - Bx d^{-1} x_U - By d^{-1} x_V
+        typename A::Acc acc;
+        acc.add(one, x0);
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+            acc.add(sm.EG[le][0][i * P + a], sm.t[le][0][j * P + a]);
+            acc.add(sm.EG[le][0][j * P + a], sm.t[le][1][a * P + i]);
+        }
+        sm.s[le][n] = acc.get();
+    }
+    __syncthreads();
+    if (live) {   // phi = S^{-1} s
+        const T* Sn = S + (size_t)e * Np * Np + n;
+        typename A::Acc acc;
+#pragma unroll 4
+        for (int m = 0; m < Np; ++m) acc.add(Sn[(size_t)m * Np], sm.s[le][m]);
+        phi = acc.get();
+        sm.w[le][n] = A::mul(pb, phi);
+    }
+    __syncthreads();
+    if (live) {   // d U = x_U - Cx phi,  d V = x_V - Cy phi
+        typename A::Acc au, av;
+        au.add(one, xU);
+        au.add(ncx, phi);
+        av.add(one, xV);
+        av.add(ncy, phi);
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+            au.add(sm.EG[le][1][i * P + a], sm.w[le][j * P + a]);
+            av.add(sm.EG[le][1][j * P + a], sm.w[le][a * P + i]);
+        }
+        U = A::mul(au.get(), rd);
+        V = A::mul(av.get(), rd);
+    }
+}
+
+// Z = A^{-1} R1 through the Schur complement: one thread per (element, node), EPB elements per block.
+template <int P, int EPB, class A>
+__global__ void __launch_bounds__(EPB * P * P)
+    schur_condense_kernel(Geom g, const typename A::T* __restrict__ S, const typename A::T* __restrict__ aux,
+                          const typename A::T* __restrict__ EG, const double* __restrict__ R1,
+                          double* __restrict__ Z) {
+    using T = typename A::T;
+    constexpr int Np = P * P;
+    __shared__ SchurSmem<P, EPB, A> sm;
+    const int le = threadIdx.x / Np, n = threadIdx.x % Np;
+    const int e = blockIdx.x * EPB + le;
+    const bool live = e < g.n_el;
+    const size_t fs = (size_t)g.n_el * Np, o = (size_t)e * Np + n;
+    T x0{}, xU{}, xV{};
+    if (live) {
+        x0 = A::from(R1[o]);
+        xU = A::from(R1[fs + o]);
+        xV = A::from(R1[2 * fs + o]);
+    }
+    T phi{}, U{}, V{};
+    schur_solve<P, EPB, A>(sm, g, e, le, n, live, S, aux, EG, x0, xU, xV, phi, U, V);
+    if (live) {
+        Z[o] = A::to(phi);
+        Z[fs + o] = A::to(U);
+        Z[2 * fs + o] = A::to(V);
+    }
+}
+
+// Q = Z + beta A^{-1} (tau qhat), Lst = (Q - R1) / a_ii through the Schur complement.
+template <int P, int EPB, class A>
+__global__ void __launch_bounds__(EPB * P * P)
+    schur_recover_kernel(Geom g, const typename A::T* __restrict__ S, const typename A::T* __restrict__ aux,
+                         const typename A::T* __restrict__ EG, const double* __restrict__ Z,
+                         const double* __restrict__ R1, const double* __restrict__ tau_edge,
+                         const double* __restrict__ qhat, double beta, double inv_aii, double* __restrict__ Q,
+                         double* __restrict__ Lst) {
+    using T = typename A::T;
+    constexpr int Np = P * P, NF = 3 * P;
+    __shared__ SchurSmem<P, EPB, A> sm;
+    const int le = threadIdx.x / Np, n = threadIdx.x % Np, i = n % P, j = n / P;
+    const int e = blockIdx.x * EPB + le;
+    const bool live = e < g.n_el;
+    const size_t fs = (size_t)g.n_el * Np, o = (size_t)e * Np + n;
+    double u[3] = {0.0, 0.0, 0.0};
+    if (live) {
+        for (int f = 0; f < 4; ++f) {
+            const bool on = (f == 0 && i == 0) || (f == 1 && i == P - 1) || (f == 2 && j == 0) ||
+                            (f == 3 && j == P - 1);
+            if (!on) continue;
+            const int b = (f < 2) ? j : i;
+            const int ed = edge_of_face(e, f, g);
+            const double tau = tau_edge[(size_t)ed * P + b];
+            for (int c = 0; c < 3; ++c) u[c] += tau * qhat[(size_t)ed * NF + c * P + b];
+        }
+    }
+    T y[3];
+    schur_solve<P, EPB, A>(sm, g, e, le, n, live, S, aux, EG, A::from(u[0]), A::from(u[1]), A::from(u[2]), y[0],
+                           y[1], y[2]);
+    if (live) {
+        const double kk = beta * dt_factor(g, e);
+        for (int c = 0; c < 3; ++c) {
+            const size_t oc = c * fs + o;
+            const double q = Z[oc] + kk * A::to(y[c]);
+            Q[oc] = q;
+            Lst[oc] = (q - R1[oc]) * inv_aii;
+        }
+    }
+}
+
+template <int P>
+constexpr int schur_epb() {
+    return 256 / (P * P) > 0 ? 256 / (P * P) : 1;
+}
+
+template <int P, class A>
+void schur_condense(const Geom& g, const LocalOps& ops, const double* R1, double* Z, cudaStream_t s) {
+    using T = typename A::T;
+    constexpr int EPB = schur_epb<P>();
+    schur_condense_kernel<P, EPB, A><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(
+        g, static_cast<const T*>(ops.S), static_cast<const T*>(ops.aux), static_cast<const T*>(ops.EG), R1, Z);
+    count_launches(1);
+}
+
+template <int P, class A>
+void schur_recover(const Geom& g, const LocalOps& ops, const double* Z, const double* R1, const double* tau_edge,
+                   const double* qhat, double beta, double inv_aii, double* Q, double* Lst, cudaStream_t s) {
+    using T = typename A::T;
+    constexpr int EPB = schur_epb<P>();
+    schur_recover_kernel<P, EPB, A><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(
+        g, static_cast<const T*>(ops.S), static_cast<const T*>(ops.aux), static_cast<const T*>(ops.EG), Z, R1,
+        tau_edge, qhat, beta, inv_aii, Q, Lst);
+    count_launches(1);
+}
+
+template <int P, class A>
+cudaError_t schur_setup(const Geom& g, const double* Ainv, const double* phiB, const double* tau_edge, double dta,
+                        void* S, void* aux, void* EG, cudaStream_t s) {
+    using T = typename A::T;
+    const size_t n = (size_t)g.n_el * g.Np;
+    schur_setup_kernel<P, A><<<(int)((n + 255) / 256), 256, 0, s>>>(g, Ainv, phiB, tau_edge, dta,
+                                                                     static_cast<T*>(S), static_cast<T*>(aux));
+    const int ne = g.batch * 2 * P * P;
+    schur_eg_kernel<P, A><<<(ne + 255) / 256, 256, 0, s>>>(g, dta, static_cast<T*>(EG));
+    count_launches(2);
+    return cudaGetLastError();
 }
 
 template <int P>
@@ -589,7 +887,10 @@ cudaError_t condense_launch(const Geom& g, const LocalOps& ops, const double* R1
     constexpr int NV = 3 * P * P;
     constexpr int EPB = (256 / NV) > 0 ? 256 / NV : 1;
     const int blocks = (g.n_el + EPB - 1) / EPB;
-    if (ops.kind == 2) {
+    if (ops.schur) {
+        if (ops.kind == 3) schur_condense<P, ArithF2>(g, ops, R1, Z, s);
+        else schur_condense<P, ArithF64>(g, ops, R1, Z, s);
+    } else if (ops.kind == 2) {
         cudaError_t e = launch_local_tc(g, 0, ops.image, R1, nullptr, nullptr, nullptr, 0.0, 0.0, Z, nullptr,
                                         ops.error, s);
         if (e != cudaSuccess) return e;
@@ -615,6 +916,11 @@ cudaError_t recover_launch(const Geom& g, const LocalOps& ops, const double* Z, 
     constexpr int NV = 3 * P * P;
     constexpr int EPB = (256 / NV) > 0 ? 256 / NV : 1;
     const int blocks = (g.n_el + EPB - 1) / EPB;
+    if (ops.schur) {
+        if (ops.kind == 3) schur_recover<P, ArithF2>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s);
+        else schur_recover<P, ArithF64>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s);
+        return cudaGetLastError();
+    }
     if (ops.kind == 2)
         return launch_local_tc(g, 1, ops.image, R1, Z, tau_edge, qhat, beta, inv_aii, Q, Lst, ops.error, s);
     if (ops.kind == 3) {
@@ -635,7 +941,7 @@ cudaError_t recover_launch(const Geom& g, const LocalOps& ops, const double* Z, 
 
 cudaError_t launch_autotune_local(const Geom& g, LocalOps& ops, double* R1, double* Z, const double* tau_edge,
                                   const double* qhat, double* Q, double* Lst, cudaStream_t s) {
-    if (ops.kind != 3) return cudaSuccess;
+    if (ops.kind != 3 || ops.schur) return cudaSuccess;
 #define CALL(P) autotune_x2<P>(g, ops, R1, Z, tau_edge, qhat, Q, Lst, s)
     switch (g.P) {
         case 2: return CALL(2);
@@ -646,6 +952,25 @@ cudaError_t launch_autotune_local(const Geom& g, LocalOps& ops, double* R1, doub
         case 7: return CALL(7);
         case 8: return CALL(8);
         case 9: return CALL(9);
+        default: return cudaErrorInvalidValue;
+    }
+#undef CALL
+}
+
+cudaError_t launch_schur_setup(const Geom& g, const double* Ainv, const double* phiB, const double* tau_edge,
+                               double dta, bool f32x2, void* S, void* aux, void* EG, cudaStream_t s) {
+#define CALL(P)                                                                                      \
+    return f32x2 ? schur_setup<P, ArithF2>(g, Ainv, phiB, tau_edge, dta, S, aux, EG, s)              \
+                 : schur_setup<P, ArithF64>(g, Ainv, phiB, tau_edge, dta, S, aux, EG, s)
+    switch (g.P) {
+        case 2: CALL(2);
+        case 3: CALL(3);
+        case 4: CALL(4);
+        case 5: CALL(5);
+        case 6: CALL(6);
+        case 7: CALL(7);
+        case 8: CALL(8);
+        case 9: CALL(9);
         default: return cudaErrorInvalidValue;
     }
 #undef CALL

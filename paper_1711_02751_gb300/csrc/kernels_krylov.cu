@@ -11,6 +11,7 @@
 // inner solves of the mixed-precision path.  Products and per-thread partial sums are in T;
 // warp, block and grid reductions are in double.  The trace-matrix products are in
 // kernels_spmv.cu.
+#include "compensated.h"
 #include "internal.h"
 #include "reduce.h"
 
@@ -86,7 +87,7 @@ __global__ void scale_kernel(const double* __restrict__ w, const double* __restr
     const double s = 1.0 / sqrt(*nrm2);
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
          idx += (size_t)gridDim.x * blockDim.x)
-        v[idx] = T(w[idx] * s);
+        v[idx] = from_f64<T>(w[idx] * s);
 }
 
 __global__ void to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, size_t n) {
@@ -236,6 +237,63 @@ guess_norms_kernel(size_t n, const double* __restrict__ g, GuessTerms t, double*
     }
 }
 
+// The same norms in FP32-pair arithmetic: g and the y_j split into FP32 pairs as they are loaded
+// (integer-pipe conversions), each candidate g - sum_j c[q][j] y_j formed as one compensated Dot2
+// sum (the binomial coefficients are exact in FP32) and its square summed the same way.  GB300's
+// FP64 rate would otherwise bound this pass (about 21 FP64 operations per trace entry at order 5).
+__global__ void __launch_bounds__(kDotThreads)
+guess_norms_x2_kernel(size_t n, const double* __restrict__ g, GuessTerms t, double* __restrict__ scratch,
+                      double* __restrict__ out) {
+    constexpr int NQ = 7;
+    unsigned* counter = reinterpret_cast<unsigned*>(scratch);
+    double* partial = scratch + 1;
+    __shared__ double sh[NQ][kDotThreads / 32];
+    __shared__ float nc[NQ][6];   // -c[q][j]
+    if (threadIdx.x < NQ * 6) nc[threadIdx.x / 6][threadIdx.x % 6] = -f64_to_f32(t.c[threadIdx.x / 6][threadIdx.x % 6]);
+    __syncthreads();
+    Dot2 acc[NQ];
+    for (size_t idx = blockIdx.x * (size_t)kDotThreads + threadIdx.x; idx < n;
+         idx += (size_t)gridDim.x * kDotThreads) {
+        float gh, gl, yh[6], yl[6];
+        split(g[idx], gh, gl);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            yh[j] = 0.f;
+            yl[j] = 0.f;
+            if (j < t.nq) split(t.y[j][idx], yh[j], yl[j]);
+        }
+        acc[0].add(gh, gl, gh, gl);
+#pragma unroll
+        for (int q = 1; q < NQ; ++q) {
+            if (q > t.nq) break;
+            Dot2 r;
+            r.add(1.f, 0.f, gh, gl);
+#pragma unroll
+            for (int j = 0; j < 6; ++j)
+                if (j < q) r.add(nc[q][j], 0.f, yh[j], yl[j]);
+            float rh, rl;
+            two_sum(r.p, r.c, rh, rl);
+            acc[q].add(rh, rl, rh, rl);
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const double s = warp_sum(acc[q].value());
+        if (lane == 0) sh[q][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NQ) {
+        double s = 0.0;
+        for (int k = 0; k < kDotThreads / 32; ++k) s += sh[threadIdx.x][k];
+        partial[(size_t)blockIdx.x * NQ + threadIdx.x] = s;
+    }
+    if (last_block_arrives(counter)) {
+        reduce_partials(partial, gridDim.x, NQ, 0, t.nq + 1, out);
+        if (threadIdx.x == 0) *counter = 0u;
+    }
+}
+
 // ---- device-side GMRES control: one thread each -----------------------------------------
 __global__ void gmres_solve_init_kernel(GmresCtl* c, double tol_abs, double inner_rel, int maxit) {
     c->tol_abs = tol_abs;
@@ -293,16 +351,21 @@ __global__ void gmres_solve_y_kernel(GmresCtl* c) {
     }
 }
 
-// x += sum_{j < jend} y_j V_j (FP64 accumulator for either basis type)
+// x += sum_{j < jend} y_j V_j.  FP64 basis: FP64 sums.  FP32 basis (the mixed form's inner
+// cycles): the correction is summed in FP32 -- the cycle that produced it is FP32 throughout --
+// and added to the FP64 iterate once, one conversion (fastcvt.h) and one FP64 add per entry.
 template <typename T>
 __global__ void gmres_update_x_kernel(const T* __restrict__ V, size_t ldv, const GmresCtl* __restrict__ c,
                                       double* __restrict__ x, size_t n) {
     const int nv = c->jend;
+    __shared__ T sy[GmresCtl::kM];
+    for (int j = threadIdx.x; j < nv; j += blockDim.x) sy[j] = T(c->y[j]);
+    __syncthreads();
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
          idx += (size_t)gridDim.x * blockDim.x) {
-        double acc = x[idx];
-        for (int j = 0; j < nv; ++j) acc += c->y[j] * (double)V[(size_t)j * ldv + idx];
-        x[idx] = acc;
+        T acc = T(0);
+        for (int j = 0; j < nv; ++j) acc += sy[j] * V[(size_t)j * ldv + idx];
+        x[idx] += to_f64(acc);
     }
 }
 
@@ -371,9 +434,10 @@ cudaError_t multidot_impl(const T* V, size_t ldv, int nv, const T* w, size_t n, 
 size_t guess_scratch_doubles() { return 1 + (size_t)kDotBlocks * 7; }
 
 cudaError_t launch_guess_norms(size_t n, const double* g, const GuessTerms& t, double* scratch, double* out,
-                               cudaStream_t s) {
+                               cudaStream_t s, bool f32x2) {
     if (t.nq < 1 || t.nq > 6) return cudaErrorInvalidValue;
-    guess_norms_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(n, g, t, scratch, out);
+    if (f32x2) guess_norms_x2_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(n, g, t, scratch, out);
+    else guess_norms_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(n, g, t, scratch, out);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -43,7 +43,8 @@ class Config(ctypes.Structure):
                 ("length", ctypes.c_double), ("bc_params", ctypes.c_double * 5),
                 ("batch", ctypes.c_int), ("dt_per_instance", ctypes.POINTER(ctypes.c_double)),
                 ("local_precision", ctypes.c_int), ("krylov_guess", ctypes.c_int), ("spmv_kernel", ctypes.c_int),
-                ("krylov_ortho", ctypes.c_int), ("residual_f32x2", ctypes.c_int)]
+                ("krylov_ortho", ctypes.c_int), ("residual_f32x2", ctypes.c_int),
+                ("local_dense", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -112,7 +113,8 @@ def _f64(a, shape=None):
 def make_config(N, k, dt, g=1.0, H0=1.0, scheme="ars2", krylov_rtol=0.0, krylov_restart=0,
                 krylov_maxit=0, linear_only=False, precision="fp64", boundary="periodic", x0=0.0,
                 length=1.0, bc_params=(0.0, 0.0, 0.0, 0.0, 0.0), batch=1, dt_per_instance=None,
-                local_precision="fp64", krylov_guess=0, spmv_kernel=0, krylov_ortho=0, residual_f32x2=False):
+                local_precision="fp64", krylov_guess=0, spmv_kernel=0, krylov_ortho=0, residual_f32x2=False,
+                local_dense=False):
     """bc_params (boundary='vortex'): beta, u_inf, v_inf, x_c, y_c of the moving vortex.
     batch > 1: that many instances in one handle; dt_per_instance (length batch) overrides dt
     instance by instance (dt then only sets the scale the factors are taken against)."""
@@ -125,7 +127,8 @@ def make_config(N, k, dt, g=1.0, H0=1.0, scheme="ars2", krylov_rtol=0.0, krylov_
                  float(krylov_rtol), int(krylov_restart), int(krylov_maxit), int(bool(linear_only)),
                  BOUNDARIES[boundary], float(x0), float(length), (ctypes.c_double * 5)(*bc_params),
                  int(batch), _ptr(dts) if dts is not None else None, LOCAL_PRECISIONS[local_precision],
-                 int(krylov_guess), int(spmv_kernel), int(krylov_ortho), int(bool(residual_f32x2)))
+                 int(krylov_guess), int(spmv_kernel), int(krylov_ortho), int(bool(residual_f32x2)),
+                 int(bool(local_dense)))
     cfg._dts = dts                     # keeps the array alive as long as the config
     return cfg
 
@@ -176,7 +179,7 @@ class Sim:
                  krylov_rtol=0.0, krylov_restart=0, krylov_maxit=0, linear_only=False, precision="fp64",
                  boundary="periodic", x0=0.0, length=1.0, bc_params=(0.0, 0.0, 0.0, 0.0, 0.0),
                  batch=1, dt_per_instance=None, local_precision="fp64", krylov_guess=0, spmv_kernel=0,
-                 krylov_ortho=0, residual_f32x2=False):
+                 krylov_ortho=0, residual_f32x2=False, local_dense=False):
         """batch > 1 holds that many independent instances of the mesh (one launch per kernel
         per stage covers all of them); arrays are then [batch * N * N, (k+1)^2], instance-major,
         and the bottom and the time step (dt_per_instance) may differ from instance to instance."""
@@ -187,7 +190,7 @@ class Sim:
         self.cfg = make_config(N, k, dt, g, H0, scheme, krylov_rtol, krylov_restart, krylov_maxit,
                                linear_only, precision, boundary, x0, length, bc_params, batch,
                                dt_per_instance, local_precision, krylov_guess, spmv_kernel, krylov_ortho,
-                               residual_f32x2)
+                               residual_f32x2, local_dense)
         self._h = ctypes.c_void_p(None)
         b = None if bottom is None else _f64(bottom, (self.n_el, self.Np))
         st = lib().hdgdg_create(ctypes.byref(self.cfg), None if b is None else _ptr(b),

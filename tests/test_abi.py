@@ -52,3 +52,16 @@ def test_host_only_entry_points(libmod):
 def test_large_workload_fits_one_gpu(libmod):
     cfg = libmod.make_config(512, 3, 5.4e-3)
     assert libmod.bytes_required(cfg) < 60e9
+
+
+def test_schur_local_operators_need_less_memory(libmod):
+    """The Schur-complement local solves keep the (phi, phi) block of A^{-1} instead of an FP32
+    pair of the whole A^{-1}: (k+1)^4 + 4 (k+1)^2 eight-byte numbers per element (and two
+    (k+1) x (k+1) matrices per instance) instead of 9 (k+1)^4 FP32 pairs."""
+    s = libmod.bytes_required(libmod.make_config(64, 3, 5e-3, local_precision="f32x2"))
+    d = libmod.bytes_required(libmod.make_config(64, 3, 5e-3, local_precision="f32x2", local_dense=True))
+    n_el, Np = 64 * 64, 16
+    assert d - s == n_el * 8 * (3 * Np) ** 2 - (n_el * (Np * Np + 4 * Np) + 2 * Np) * 8
+    bad = libmod.make_config(8, 2, 0.1)
+    bad.local_dense = 2
+    assert libmod.bytes_required(bad) == 0

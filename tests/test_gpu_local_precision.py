@@ -192,9 +192,10 @@ def test_f32x2_mixed_bump8_200_steps_against_the_oracle():
 
 
 def test_f32x2_autotuned_tile():
-    """On a mesh of >= 4096 elements the FP32-pair local kernels' tile (elements per block) is
-    picked at create by timing the candidates; whichever wins, the condensation and stage solve
-    stay within 1e-12 of the FP64 local operators (the tile does not change any row's sums)."""
+    """On a mesh of >= 4096 elements the dense FP32-pair local kernels' tile (elements per block)
+    is picked at create by timing the candidates; whichever wins, the condensation and stage solve
+    stay within 1e-12 of the FP64 local operators (the tile does not change any row's sums).  The
+    Schur-complement kernels (the default) have one tile and report 0."""
     N, k = 64, 3
     x, y = hd.node_coords(N, k)
     h, hu, hv, b = W.large_state(x, y, seed=9)
@@ -203,10 +204,13 @@ def test_f32x2_autotuned_tile():
     dt = 0.4 / N
     with hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, local_precision="f32x2") as s:
         st = s.stats()
+        assert st["local_tile_condense"] == 0 and st["local_tile_recover"] == 0
+    with hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, local_precision="f32x2", local_dense=True) as s:
+        st = s.stats()
         assert st["local_tile_condense"] in (1, 2, 4, 5, 8) and st["local_tile_recover"] in (1, 2, 4, 5, 8)
         gx = s.condense_rhs(R1)
         Qx, _, _ = s.stage_solve(R1)
-    with hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0) as s:
+    with hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, local_dense=True) as s:
         g64 = s.condense_rhs(R1)
         Q64, _, _ = s.stage_solve(R1)
     assert np.abs(gx - g64).max() <= 1e-12 * np.abs(g64).max()
