@@ -174,7 +174,12 @@ enum {
     HDGDG_KT_RECOVER = 3,   /* local recovery of Q and L_i */
     HDGDG_KT_DG = 4,        /* DG residual of the nonlinear part */
     HDGDG_KT_COMBINE = 5,   /* stage combinations and the final update */
-    HDGDG_KT_COUNT = 6
+    HDGDG_KT_RESIDUAL = 6,  /* end of each restart cycle: the correction x += V y, the true residual
+                               g - S x and its norm */
+    HDGDG_KT_GUESS = 7,     /* initial guess of each trace solve: candidate residual norms, the
+                               chosen extrapolation and residual, and the history update */
+    HDGDG_KT_PRECOND = 8,   /* qhat = M^{-1} x~ after each trace solve (block-Jacobi blocks) */
+    HDGDG_KT_COUNT = 9
 };
 
 typedef struct hdgdg_sim hdgdg_sim;

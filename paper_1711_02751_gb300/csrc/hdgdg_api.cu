@@ -86,7 +86,7 @@ Plan make_plan(const hdgdg_config* c) {
     if (explicit_scheme(c)) {   // state, three stage increments, two stage states, face fluxes
         b += p.n * d + n_edges * P * d;
         b += 7 * 3 * p.n * d + p.nt * d;
-        b += (reduction_scratch_doubles(p.m) + mass_scratch_doubles() + 4 * (size_t)(p.m + 2) + 16) * d + 64;
+        b += (reduction_scratch_doubles(p.m, (int)n_edges, (int)P) + mass_scratch_doubles() + 4 * (size_t)(p.m + 2) + 16) * d + 64;
         p.persistent = b;
         p.setup_temp = 0;
         return p;
@@ -104,7 +104,7 @@ Plan make_plan(const hdgdg_config* c) {
     } else {
         b += ((size_t)p.m + 1) * p.nt * d;                    // FP64 Krylov basis
     }
-    b += (reduction_scratch_doubles(p.m) + mass_scratch_doubles() + 4 * (size_t)(p.m + 2) + 16) * d;
+    b += (reduction_scratch_doubles(p.m, (int)n_edges, (int)P) + mass_scratch_doubles() + 4 * (size_t)(p.m + 2) + 16) * d;
     b += 64 + sizeof(GmresCtl);                               // flags, GMRES control block
     if (c->local_precision == HDGDG_LOCAL_FP32) b += n_el * (size_t)p.NV * p.NV * sizeof(float);
     if (c->local_precision == HDGDG_LOCAL_BF16) b += tc_image_bytes((int)P);
@@ -504,6 +504,7 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
         gt.nq = avail;
         for (int j = 0; j < avail; ++j) gt.y[j] = sim->yhist[stage][j];
         std::memcpy(gt.c, coef, sizeof(coef));
+        TimedGroup tg(sim, HDGDG_KT_GUESS);
         CU(launch_guess_norms(n, g, gt, sim->red, dv_guess(sim), st, kMixed));
         CU(cudaMemcpyAsync(sim->hbuf, dv_guess(sim), (avail + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
         TRY(sync(sim));
@@ -525,31 +526,34 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
     sim->stats.last_guess_order = guess;
     const double rnorm0 = std::sqrt(cand[guess]);
     double rnorm = rnorm0;
-    if (guess == 0) {
-        CU(cudaMemsetAsync(sim->xt, 0, n * sizeof(double), st));
-        CU(cudaMemcpyAsync(sim->w, g, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        if (avail > 0)   // ||g||^2 for the cycle's first basis vector (norm2_to_host left it otherwise)
-            CU(cudaMemcpyAsync(dv_nrm(sim), dv_guess(sim), sizeof(double), cudaMemcpyDeviceToDevice, st));
-    } else {
-        // x0 = sum_j c_j x_{n-j}: the extrapolation polynomial through the last `guess` solutions
-        CombineTerms t{};
-        for (int j = 0; j < guess; ++j) {
-            t.X[t.n] = sim->xhist[stage][j];
-            t.c[t.n++] = coef[guess][j] - (j == 0 ? 1.0 : 0.0);   // base x_{n-1} counted once
+    {
+        TimedGroup tg_guess(sim, HDGDG_KT_GUESS);
+        if (guess == 0) {
+            CU(cudaMemsetAsync(sim->xt, 0, n * sizeof(double), st));
+            CU(cudaMemcpyAsync(sim->w, g, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            if (avail > 0)   // ||g||^2 for the cycle's first basis vector (norm2_to_host left it otherwise)
+                CU(cudaMemcpyAsync(dv_nrm(sim), dv_guess(sim), sizeof(double), cudaMemcpyDeviceToDevice, st));
+        } else {
+            // x0 = sum_j c_j x_{n-j}: the extrapolation polynomial through the last `guess` solutions
+            CombineTerms t{};
+            for (int j = 0; j < guess; ++j) {
+                t.X[t.n] = sim->xhist[stage][j];
+                t.c[t.n++] = coef[guess][j] - (j == 0 ? 1.0 : 0.0);   // base x_{n-1} counted once
+            }
+            CU(launch_combine(n, sim->xhist[stage][0], t, sim->xt, nullptr, st));
+            // r0 = g - S~ x0 = g - sum_j c_j (S~ x~_{n-j}): S~ is linear, and each S~ x~_{n-j} is
+            // known from the true residual that ended that step's solve -- no product needed
+            CombineTerms r{};
+            for (int j = 0; j < guess; ++j) {
+                r.X[r.n] = sim->yhist[stage][j];
+                r.c[r.n++] = -coef[guess][j];
+            }
+            CU(launch_combine(n, g, r, sim->w, nullptr, st));
+            if constexpr (kMixed)   // the candidates were FP32-pair estimates: the cycle's start norm exactly
+                CU(launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st));
+            else
+                CU(cudaMemcpyAsync(dv_nrm(sim), dv_guess(sim) + guess, sizeof(double), cudaMemcpyDeviceToDevice, st));
         }
-        CU(launch_combine(n, sim->xhist[stage][0], t, sim->xt, nullptr, st));
-        // r0 = g - S~ x0 = g - sum_j c_j (S~ x~_{n-j}): S~ is linear, and each S~ x~_{n-j} is
-        // known from the true residual that ended that step's solve -- no product needed
-        CombineTerms r{};
-        for (int j = 0; j < guess; ++j) {
-            r.X[r.n] = sim->yhist[stage][j];
-            r.c[r.n++] = -coef[guess][j];
-        }
-        CU(launch_combine(n, g, r, sim->w, nullptr, st));
-        if constexpr (kMixed)   // the candidates were FP32-pair estimates: the cycle's start norm exactly
-            CU(launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st));
-        else
-            CU(cudaMemcpyAsync(dv_nrm(sim), dv_guess(sim) + guess, sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
     CU(launch_gmres_solve_init(ctl, tol, inner_rel, maxit, st));
     int total = 0;
@@ -576,6 +580,7 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
                                      dv_nrm(sim) + 1, V + (size_t)(j + 1) * n, ctl, j, m,
                                      !(kMixed && sim->cfg.krylov_ortho == 1), st, done);
         }
+        TimedGroup tg_end(sim, HDGDG_KT_RESIDUAL);
         if (e == cudaSuccess) e = launch_gmres_update(V, n, ctl, sim->xt, n, st);
         // the true residual w = g - S~ x~ that ends the cycle, and ||w||^2
         if (kMixed && sim->Stil_lo) {   // one fused FP32-pair pass
@@ -652,9 +657,13 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
                         rnorm / bnorm, rtol, total);
         }
     }
-    CU(launch_block_diag(sim->g, sim->Minv, sim->xt, qhat, st));
+    {
+        TimedGroup tg(sim, HDGDG_KT_PRECOND);
+        CU(launch_block_diag(sim->g, sim->Minv, sim->xt, qhat, st));
+    }
     const int order = guess_order(&sim->cfg);
     if (stage >= 0 && order > 0) {   // keep x~ and S~ x~ = g - r for the next steps' guesses
+        TimedGroup tg(sim, HDGDG_KT_GUESS);
         double* ox = sim->xhist[stage][order - 1];
         double* oy = sim->yhist[stage][order - 1];
         for (int j = order - 1; j > 0; --j) {
@@ -843,7 +852,7 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
         for (double** v : {&sim->q, &sim->q_new, &sim->R1, &sim->Qs}) TRY(dalloc(sim, v, 3 * p.n));
         for (int i = 0; i < 3; ++i) TRY(dalloc(sim, &sim->NLs[i], 3 * p.n));
         TRY(dalloc(sim, &sim->fface, p.nt));
-        TRY(dalloc(sim, &sim->red, reduction_scratch_doubles(p.m)));
+        TRY(dalloc(sim, &sim->red, reduction_scratch_doubles(p.m, g.n_edges, g.P)));
     CU(cudaMemset(sim->red, 0, sizeof(double)));   // the reductions' ticket counter starts at zero
         TRY(dalloc(sim, &sim->mred, mass_scratch_doubles()));
         TRY(dalloc(sim, &sim->dvals, 4 * (size_t)(p.m + 2) + 16));
@@ -878,7 +887,7 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
     } else {
         TRY(dalloc(sim, &sim->V, (size_t)(p.m + 1) * p.nt));
     }
-    TRY(dalloc(sim, &sim->red, reduction_scratch_doubles(p.m)));
+    TRY(dalloc(sim, &sim->red, reduction_scratch_doubles(p.m, g.n_edges, g.P)));
     CU(cudaMemset(sim->red, 0, sizeof(double)));   // the reductions' ticket counter starts at zero
     TRY(dalloc(sim, &sim->mred, mass_scratch_doubles()));
     TRY(dalloc(sim, &sim->dvals, 4 * (size_t)(p.m + 2) + 16));

@@ -288,7 +288,7 @@ struct GmresCtl {
 size_t dot_scratch_doubles(int nv);
 // The handle's reduction scratch: the Gram-Schmidt dots of a GMRES(m) cycle, the fused
 // residual pass (launch_residual_norm_x2) and the guess norms (launch_guess_norms) share it.
-size_t reduction_scratch_doubles(int m);
+size_t reduction_scratch_doubles(int m, int n_edges, int P);
 // Candidate initial guesses of a trace solve: y[j] = S~ x~_{n-1-j} (j < nq) and the extrapolation
 // coefficients of each order q = 1..nq.  out[0] = ||g||^2, out[q] = ||g - sum_j c[q][j] y[j]||^2.
 struct GuessTerms {

@@ -11,6 +11,9 @@
 // inner solves of the mixed-precision path.  Products and per-thread partial sums are in T;
 // warp, block and grid reductions are in double.  The trace-matrix products are in
 // kernels_spmv.cu.
+#include <cstdint>
+#include <initializer_list>
+
 #include "compensated.h"
 #include "internal.h"
 #include "reduce.h"
@@ -21,6 +24,35 @@ namespace {
 constexpr int kDotBlocks = 608;    // 4 x 152 SMs
 constexpr int kDotThreads = 256;
 constexpr int kDotChunk = 8;       // vectors reduced per pass over w
+
+// VW consecutive entries of a vector: one 16-byte load or store for VW = 4 (FP32), one entry for
+// VW = 1.  Index i counts groups of VW entries; the launchers use VW = 4 only when every vector
+// involved starts on a 16-byte boundary and n is a multiple of 4.
+template <typename T, int VW>
+struct Lanes {
+    T v[VW];
+};
+
+template <typename T, int VW>
+__device__ __forceinline__ Lanes<T, VW> load_lanes(const T* __restrict__ p, size_t i) {
+    Lanes<T, VW> r;
+    if constexpr (VW == 4) {
+        const float4 q = reinterpret_cast<const float4*>(p)[i];
+        r.v[0] = q.x;
+        r.v[1] = q.y;
+        r.v[2] = q.z;
+        r.v[3] = q.w;
+    } else {
+        r.v[0] = p[i];
+    }
+    return r;
+}
+
+template <typename T, int VW>
+__device__ __forceinline__ void store_lanes(T* __restrict__ p, size_t i, const Lanes<T, VW>& r) {
+    if constexpr (VW == 4) reinterpret_cast<float4*>(p)[i] = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+    else p[i] = r.v[0];
+}
 
 // y[r] = B_r x[r] for column-major NF x NF blocks (FP64)
 template <int NF>
@@ -43,7 +75,7 @@ __device__ void gmres_arnoldi_update(GmresCtl* c, int j, int m, const double* h1
                                      const double* hn);
 
 // out[j0 + c] = V_{j0+c} . w, c < nj: block partials in scratch, summed by the last block
-template <int CH, typename T>
+template <int CH, typename T, int VW = 1>
 __global__ void __launch_bounds__(kDotThreads)
 multidot_kernel(const T* __restrict__ V, size_t ldv, int j0, int nj, const T* __restrict__ w,
                 size_t n, double* __restrict__ scratch, int ldp, double* __restrict__ out,
@@ -55,12 +87,17 @@ multidot_kernel(const T* __restrict__ V, size_t ldv, int j0, int nj, const T* __
     T acc[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) acc[c] = T(0);
-    for (size_t idx = blockIdx.x * (size_t)kDotThreads + threadIdx.x; idx < n;
-         idx += (size_t)gridDim.x * kDotThreads) {
-        const T wv = w[idx];
+    for (size_t iv = blockIdx.x * (size_t)kDotThreads + threadIdx.x; iv < n / VW;
+         iv += (size_t)gridDim.x * kDotThreads) {
+        const Lanes<T, VW> wv = load_lanes<T, VW>(w, iv);
 #pragma unroll
-        for (int c = 0; c < CH; ++c)
-            if (c < nj) acc[c] += V[(size_t)(j0 + c) * ldv + idx] * wv;
+        for (int c = 0; c < CH; ++c) {
+            if (c < nj) {
+                const Lanes<T, VW> v = load_lanes<T, VW>(V + (size_t)(j0 + c) * ldv, iv);
+#pragma unroll
+                for (int k = 0; k < VW; ++k) acc[c] += v.v[k] * wv.v[k];
+            }
+        }
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -102,7 +139,7 @@ __global__ void to_f32_kernel(const double* __restrict__ a, float* __restrict__ 
 // orthonormal V, and, given a GMRES control block, the Hessenberg column j with its Givens
 // rotation and stop test.
 // TWICE = false (classical Gram-Schmidt once): only the update and ||w1||; h2 = 0, hn = ||w1||.
-template <int NJ, typename T, bool TWICE>
+template <int NJ, typename T, bool TWICE, int VW = 1>
 __global__ void __launch_bounds__(kDotThreads)
 axpy_dot_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict__ h1, T* __restrict__ w,
                 size_t n, double* __restrict__ scratch, double* __restrict__ h2, double* __restrict__ nw1,
@@ -116,21 +153,25 @@ axpy_dot_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict__ 
 #pragma unroll
     for (int j = 0; j < NJ; ++j) { hc[j] = T(__ldg(h1 + j)); acc[j] = T(0); }
     acc[NJ] = T(0);
-    for (size_t idx = blockIdx.x * (size_t)kDotThreads + threadIdx.x; idx < n;
-         idx += (size_t)gridDim.x * kDotThreads) {
-        T v[NJ];
-        T x = w[idx];
+    for (size_t iv = blockIdx.x * (size_t)kDotThreads + threadIdx.x; iv < n / VW;
+         iv += (size_t)gridDim.x * kDotThreads) {
+        Lanes<T, VW> v[NJ];
+        Lanes<T, VW> x = load_lanes<T, VW>(w, iv);
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
-            v[j] = V[(size_t)j * ldv + idx];
-            x -= hc[j] * v[j];
+            v[j] = load_lanes<T, VW>(V + (size_t)j * ldv, iv);
+#pragma unroll
+            for (int k = 0; k < VW; ++k) x.v[k] -= hc[j] * v[j].v[k];
         }
-        w[idx] = x;
+        store_lanes<T, VW>(w, iv, x);
         if (TWICE) {
 #pragma unroll
-            for (int j = 0; j < NJ; ++j) acc[j] += v[j] * x;
+            for (int j = 0; j < NJ; ++j)
+#pragma unroll
+                for (int k = 0; k < VW; ++k) acc[j] += v[j].v[k] * x.v[k];
         }
-        acc[NJ] += x * x;
+#pragma unroll
+        for (int k = 0; k < VW; ++k) acc[NJ] += x.v[k] * x.v[k];
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -171,7 +212,7 @@ scale_out_kernel(const double* __restrict__ hn, const T* __restrict__ w, T* __re
 }
 
 // V_{j+1} = (w1 - sum_j h2_j V_j) / hn
-template <int NJ, typename T>
+template <int NJ, typename T, int VW = 1>
 __global__ void __launch_bounds__(256)
 axpy_scale_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict__ h2,
                   const double* __restrict__ hn, const T* __restrict__ w, T* __restrict__ vout, size_t n,
@@ -181,12 +222,18 @@ axpy_scale_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict_
 #pragma unroll
     for (int j = 0; j < NJ; ++j) hc[j] = T(__ldg(h2 + j));
     const T inv = T(1.0 / *hn);
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        T x = w[idx];
+    for (size_t iv = blockIdx.x * (size_t)blockDim.x + threadIdx.x; iv < n / VW;
+         iv += (size_t)gridDim.x * blockDim.x) {
+        Lanes<T, VW> x = load_lanes<T, VW>(w, iv);
 #pragma unroll
-        for (int j = 0; j < NJ; ++j) x -= hc[j] * V[(size_t)j * ldv + idx];
-        vout[idx] = x * inv;
+        for (int j = 0; j < NJ; ++j) {
+            const Lanes<T, VW> v = load_lanes<T, VW>(V + (size_t)j * ldv, iv);
+#pragma unroll
+            for (int k = 0; k < VW; ++k) x.v[k] -= hc[j] * v.v[k];
+        }
+#pragma unroll
+        for (int k = 0; k < VW; ++k) x.v[k] *= inv;
+        store_lanes<T, VW>(vout, iv, x);
     }
 }
 
@@ -383,10 +430,30 @@ cudaError_t block_diag_launch(int n_edges, const double* Bd, const double* x, do
     return cudaGetLastError();
 }
 
+// 16-byte lanes: FP32 vectors that all start on a 16-byte boundary, n and the basis stride
+// multiples of 4
+template <typename T>
+bool lanes4(size_t n, size_t ldv, std::initializer_list<const void*> ptrs) {
+    if (sizeof(T) != 4 || n % 4 != 0 || ldv % 4 != 0) return false;
+    for (const void* p : ptrs)
+        if (reinterpret_cast<uintptr_t>(p) % 16 != 0) return false;
+    return true;
+}
+
 template <int NJ, typename T>
 cudaError_t cgs2_tail_launch(const T* V, size_t ldv, const double* h1, T* w, size_t n, double* scratch,
                              double* h2, double* nw1, double* hn, T* vout, GmresCtl* ctl, int j, int m,
                              bool twice, cudaStream_t s, const int* done) {
+    // the NJ x 4 basis lanes stay in registers (80 at NJ = 10: three blocks per SM, hence the grid)
+    if constexpr (sizeof(T) == 4 && NJ <= 10) {
+        if (twice && lanes4<T>(n, ldv, {V, w, vout})) {
+            axpy_dot_kernel<NJ, T, true, 4><<<152 * 3, kDotThreads, 0, s>>>(V, ldv, h1, w, n, scratch, h2, nw1, hn,
+                                                                             ctl, j, m, done);
+            axpy_scale_kernel<NJ, T, 4><<<stream_grid(n / 4), 256, 0, s>>>(V, ldv, h2, hn, w, vout, n, done);
+            count_launches(2);
+            return cudaGetLastError();
+        }
+    }
     if (twice) {
         axpy_dot_kernel<NJ, T, true><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, h1, w, n, scratch, h2, nw1, hn,
                                                                         ctl, j, m, done);
@@ -420,8 +487,17 @@ cudaError_t cgs2_tail_dispatch(const T* V, size_t ldv, int nv, const double* h1,
 template <typename T>
 cudaError_t multidot_impl(const T* V, size_t ldv, int nv, const T* w, size_t n, double* scratch, double* out,
                           cudaStream_t s, const int* done) {
+    const bool v4 = lanes4<T>(n, ldv, {V, w});
     for (int j0 = 0; j0 < nv; j0 += kDotChunk) {
         const int nj = nv - j0 < kDotChunk ? nv - j0 : kDotChunk;
+        if constexpr (sizeof(T) == 4) {
+            if (v4) {
+                multidot_kernel<kDotChunk, T, 4><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, j0, nj, w, n, scratch, nv,
+                                                                                     out, done);
+                count_launches(1);
+                continue;
+            }
+        }
         multidot_kernel<kDotChunk, T><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, j0, nj, w, n, scratch, nv, out,
                                                                           done);
         count_launches(1);

@@ -17,8 +17,6 @@
 namespace hdgdg {
 namespace {
 
-constexpr int kGrid = 152 * 16;   // fixed grid of the fused residual pass (its norm partials)
-
 // y[r][ii] = x[r][ii] + sum_{slot, jj} S~[r][slot][jj][ii] x[col(r,slot)][jj]
 template <int NF, typename T>
 __global__ void __launch_bounds__(256)
@@ -48,8 +46,9 @@ spmv_pre_kernel(int n_edges, const T* __restrict__ Stil, const int* __restrict__
 }
 
 // w = g - (x + S~ x) with S~ as an FP32 pair (compensated Dot2 sums, compensated.h), and
-// ||w||^2: the refinement's true residual and its norm in one pass.  A fixed grid walks the edge
-// rows in groups of EPB; the norm's block partials are summed by the last block (fixed order).
+// ||w||^2: the refinement's true residual and its norm in one pass.  One block per group of EPB
+// edge rows (as spmv_pre_kernel); each block leaves its partial sum of squares in scratch and the
+// last block to arrive sums them in block order (fixed order, reproducible).
 template <int NF>
 __global__ void __launch_bounds__(256)
 residual_norm_x2_kernel(int n_edges, const float* __restrict__ Shi, const float* __restrict__ Slo,
@@ -59,36 +58,33 @@ residual_norm_x2_kernel(int n_edges, const float* __restrict__ Shi, const float*
     __shared__ float sxh[EPB][6][NF], sxl[EPB][6][NF];
     __shared__ double sh[8];
     const int le = threadIdx.x / NF, ii = threadIdx.x % NF;
-    double acc2 = 0.0;
-    for (int r0 = blockIdx.x * EPB; r0 < n_edges; r0 += gridDim.x * EPB) {
-        const int r = r0 + le;
-        const bool live = le < EPB && r < n_edges;
-        if (live) {
+    const int r = blockIdx.x * EPB + le;
+    const bool live = le < EPB && r < n_edges;
+    if (live) {
 #pragma unroll
-            for (int sl = 0; sl < 6; ++sl)
-                split(x[(size_t)__ldg(Scol + (size_t)r * 6 + sl) * NF + ii], sxh[le][sl][ii], sxl[le][sl][ii]);
-        }
-        __syncthreads();
-        if (live) {
-            const size_t base = (size_t)r * 6 * NF * NF;
-            Dot2 acc;
+        for (int sl = 0; sl < 6; ++sl)
+            split(x[(size_t)__ldg(Scol + (size_t)r * 6 + sl) * NF + ii], sxh[le][sl][ii], sxl[le][sl][ii]);
+    }
+    __syncthreads();
+    double v2 = 0.0;
+    if (live) {
+        const size_t base = (size_t)r * 6 * NF * NF;
+        Dot2 acc;
 #pragma unroll
-            for (int sl = 0; sl < 6; ++sl) {
+        for (int sl = 0; sl < 6; ++sl) {
 #pragma unroll
-                for (int jj = 0; jj < NF; ++jj) {
-                    const size_t o = base + (size_t)sl * NF * NF + jj * NF + ii;
-                    acc.add(Shi[o], Slo[o], sxh[le][sl][jj], sxl[le][sl][jj]);
-                }
+            for (int jj = 0; jj < NF; ++jj) {
+                const size_t o = base + (size_t)sl * NF * NF + jj * NF + ii;
+                acc.add(Shi[o], Slo[o], sxh[le][sl][jj], sxl[le][sl][jj]);
             }
-            const size_t o = (size_t)r * NF + ii;
-            const double v = g[o] - (x[o] + acc.value());
-            w[o] = v;
-            acc2 += v * v;
         }
-        __syncthreads();   // sx is rewritten for the next group
+        const size_t o = (size_t)r * NF + ii;
+        const double v = g[o] - (x[o] + acc.value());
+        w[o] = v;
+        v2 = v * v;
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const double s = warp_sum(acc2);
+    const double s = warp_sum(v2);
     if (lane == 0) sh[wid] = s;
     __syncthreads();
     unsigned* counter = reinterpret_cast<unsigned*>(scratch);
@@ -99,8 +95,7 @@ residual_norm_x2_kernel(int n_edges, const float* __restrict__ Shi, const float*
         partial[blockIdx.x] = b;
     }
     if (last_block_arrives(counter)) {   // the whole block sums the partials, fixed order
-        double t = 0.0;
-        for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) t += __ldcg(partial + k);
+        double t = strided_sum(partial, threadIdx.x, blockDim.x, gridDim.x, 1, 0.0);
         t = warp_sum(t);
         __syncthreads();
         if (lane == 0) sh[wid] = t;
@@ -284,7 +279,7 @@ cudaError_t launch_residual_norm_x2(const Geom& g, const float* Shi, const float
     case P: {                                                                                           \
         constexpr int EPB = 256 / NF;                                                                   \
         const int groups = (g.n_edges + EPB - 1) / EPB;                                                 \
-        residual_norm_x2_kernel<NF><<<groups < kGrid ? groups : kGrid, 256, 0, s>>>(                 \
+        residual_norm_x2_kernel<NF><<<groups, 256, 0, s>>>(                                          \
             g.n_edges, Shi, Slo, Scol, x, rhs, w, scratch, nrm2);                                        \
         count_launches(1);                                                                              \
         return cudaGetLastError();                                                                      \
@@ -296,9 +291,10 @@ cudaError_t launch_residual_norm_x2(const Geom& g, const float* Shi, const float
 #undef CASE
 }
 
-size_t reduction_scratch_doubles(int m) {
-    const size_t dots = dot_scratch_doubles(m + 2), fused = 1 + (size_t)kGrid, guess = guess_scratch_doubles();
-    return std::max(dots, std::max(fused, guess));
+size_t reduction_scratch_doubles(int m, int n_edges, int P) {
+    const int EPB = 256 / (3 * P);
+    const size_t dots = dot_scratch_doubles(m + 2), fused = 1 + (size_t)(n_edges + EPB - 1) / EPB;
+    return std::max(dots, std::max(fused, guess_scratch_doubles()));
 }
 
 }  // namespace hdgdg

@@ -23,12 +23,25 @@ __device__ inline bool last_block_arrives(unsigned* counter) {
     return s_ticket == gridDim.x - 1;
 }
 
+// s += partial[k * ld] for k = k0, k0 + stride, ... < nblk, in that order; the loads are issued
+// eight at a time so that the chain of adds does not serialise them.
+__device__ __forceinline__ double strided_sum(const double* partial, int k0, int stride, int nblk, size_t ld,
+                                              double s) {
+    for (int k = k0; k < nblk; k += 8 * stride) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = k + u * stride < nblk ? __ldcg(partial + (size_t)(k + u * stride) * ld) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    return s;
+}
+
 // out[c] = sum over blocks of partial[blk * ldp + c0 + c], c < nc: one warp per column, fixed order
 __device__ inline void reduce_partials(const double* partial, int nblk, int ldp, int c0, int nc, double* out) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int c = wid; c < nc; c += nw) {
-        double s = 0.0;
-        for (int k = lane; k < nblk; k += 32) s += __ldcg(partial + (size_t)k * ldp + c0 + c);
+        double s = strided_sum(partial + c0 + c, lane, 32, nblk, (size_t)ldp, 0.0);
         s = warp_sum(s);
         if (lane == 0) out[c] = s;
     }

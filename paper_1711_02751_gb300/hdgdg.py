@@ -24,7 +24,7 @@ EXPORTS = ["hdgdg_bytes_required", "hdgdg_node_coords", "hdgdg_create", "hdgdg_s
            "hdgdg_measure_fp64_tflops", "hdgdg_set_kernel_timing", "hdgdg_kernel_time",
            "hdgdg_mass_noalloc", "hdgdg_gll", "hdgdg_checkpoint_bytes", "hdgdg_save_checkpoint",
            "hdgdg_load_checkpoint"]
-KERNEL_CLASSES = ["spmv", "ortho", "condense", "recover", "dg", "combine"]
+KERNEL_CLASSES = ["spmv", "ortho", "condense", "recover", "dg", "combine", "residual", "guess", "precond"]
 
 
 class HdgdgError(RuntimeError):

@@ -23,7 +23,7 @@ def test_timers_on_and_off_give_the_same_steps(precision):
             outs.append(s.get_state())
             kt = s.kernel_times()
         if timing:
-            for cls in ("spmv", "ortho", "condense", "recover", "dg", "combine"):
+            for cls in ("spmv", "ortho", "condense", "recover", "dg", "combine", "residual", "guess", "precond"):
                 assert kt[cls][0] > 0.0 and kt[cls][1] > 0, cls
         else:
             assert all(v[1] == 0 for v in kt.values())
