@@ -286,6 +286,7 @@ struct hdgdg_sim {
     // device memory
     std::vector<void*> allocs;
     double *phiB = nullptr, *tau = nullptr, *Ainv = nullptr, *Stil = nullptr, *Minv = nullptr, *Srr = nullptr;
+    bool minv_pairs = false;   // residual_f32x2: M^{-1} rewritten in place as FP32 pairs after setup
     double* xhist[kMaxStages][6] = {};   // trace-solve guess: preconditioned solutions of the last
     double* yhist[kMaxStages][6] = {};   // steps per stage ([0] newest), their products S~ x~ (from
     int n_hist[kMaxStages] = {};         // the final true residual: g - r), and their count
@@ -659,7 +660,7 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
     }
     {
         TimedGroup tg(sim, HDGDG_KT_PRECOND);
-        CU(launch_block_diag(sim->g, sim->Minv, sim->xt, qhat, st));
+        CU(launch_block_diag(sim->g, sim->Minv, sim->xt, qhat, st, sim->minv_pairs));
     }
     const int order = guess_order(&sim->cfg);
     if (stage >= 0 && order > 0) {   // keep x~ and S~ x~ = g - r for the next steps' guesses
@@ -915,9 +916,13 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
     if (e == cudaSuccess)
         e = launch_assemble_trace(g, Se, S7, sim->Srr, sim->Minv, sim->Stil, sim->Scol, dsing, sim->stream);
     if (e == cudaSuccess && c->precision == HDGDG_MIXED) {
-        if (sim->Stil_lo)   // hi part = the FP32 copy of the inner cycles, lo part = the rest
+        if (sim->Stil_lo) {   // hi part = the FP32 copy of the inner cycles, lo part = the rest
             e = launch_split_f32x2(sim->Stil, sim->Stil32, sim->Stil_lo, (size_t)g.n_edges * 6 * p.NF * p.NF,
                                    sim->stream);
+            // M^{-1} (no longer needed in FP64 once S~ exists) as FP32 pairs for the back-transformation
+            if (e == cudaSuccess) e = launch_split_pairs_inplace(sim->Minv, (size_t)g.n_edges * p.NF * p.NF, sim->stream);
+            sim->minv_pairs = e == cudaSuccess;
+        }
         else
             e = launch_to_f32(sim->Stil, sim->Stil32, (size_t)g.n_edges * 6 * p.NF * p.NF, sim->stream);
     }

@@ -266,9 +266,12 @@ cudaError_t launch_spmv_pre(const Geom& g, const float* Stil, const int* Scol, c
 cudaError_t launch_residual_norm_x2(const Geom& g, const float* Shi, const float* Slo, const int* Scol,
                                     const double* x, const double* rhs, double* w, double* scratch, double* nrm2,
                                     cudaStream_t s);
-// y = B x for a block-diagonal matrix B given as [edge][col][row] blocks (FP64)
+// y = B x for a block-diagonal matrix B given as [edge][col][row] blocks: FP64, or (pairs) FP32
+// pairs stored in the same eight bytes per entry (launch_split_pairs_inplace), compensated sums.
 cudaError_t launch_block_diag(const Geom& g, const double* Bd, const double* x, double* y,
-                              cudaStream_t s);
+                              cudaStream_t s, bool pairs = false);
+// a[i] -> (float hi, float lo) in place, as float2 (split of compensated.h)
+cudaError_t launch_split_pairs_inplace(double* a, size_t n, cudaStream_t s);
 // Device-resident control block of one GMRES(m) solve (m <= kM): Hessenberg matrix, Givens
 // rotations, residual estimates and the stop flags the loop kernels test.
 struct GmresCtl {

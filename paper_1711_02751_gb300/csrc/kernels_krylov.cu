@@ -71,6 +71,39 @@ block_diag_kernel(int n_edges, const double* __restrict__ Bd, const double* __re
     y[(size_t)r * NF + ii] = acc;
 }
 
+// The same product with the blocks held as FP32 pairs (float2 (hi, lo), in place of the FP64
+// blocks) and compensated Dot2 sums (compensated.h); each x entry is split once, into shared memory.
+template <int NF>
+__global__ void __launch_bounds__(256)
+block_diag_x2_kernel(int n_edges, const float2* __restrict__ Bd, const double* __restrict__ x,
+                     double* __restrict__ y) {
+    constexpr int EPB = 256 / NF;
+    __shared__ float sxh[EPB][NF], sxl[EPB][NF];
+    const int le = threadIdx.x / NF, ii = threadIdx.x % NF;
+    const int r = blockIdx.x * EPB + le;
+    const bool live = le < EPB && r < n_edges;
+    if (live) split(x[(size_t)r * NF + ii], sxh[le][ii], sxl[le][ii]);
+    __syncthreads();
+    if (!live) return;
+    const float2* B = Bd + (size_t)r * NF * NF;
+    Dot2 acc;
+#pragma unroll
+    for (int jj = 0; jj < NF; ++jj) {
+        const float2 bv = B[jj * NF + ii];
+        acc.add(bv.x, bv.y, sxh[le][jj], sxl[le][jj]);
+    }
+    y[(size_t)r * NF + ii] = acc.value();
+}
+
+// a[i] (FP64) -> its FP32 pair (hi, lo) stored in the same eight bytes
+__global__ void split_pairs_inplace_kernel(double* a, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float2 pr;
+        split(a[i], pr.x, pr.y);
+        reinterpret_cast<float2*>(a)[i] = pr;
+    }
+}
+
 __device__ void gmres_arnoldi_update(GmresCtl* c, int j, int m, const double* h1, const double* h2,
                                      const double* hn);
 
@@ -423,9 +456,14 @@ int stream_grid(size_t n) {
 }
 
 template <int NF>
-cudaError_t block_diag_launch(int n_edges, const double* Bd, const double* x, double* y, cudaStream_t s) {
+cudaError_t block_diag_launch(int n_edges, const double* Bd, const double* x, double* y, cudaStream_t s,
+                              bool pairs) {
     constexpr int EPB = 256 / NF;
-    block_diag_kernel<NF><<<(n_edges + EPB - 1) / EPB, EPB * NF, 0, s>>>(n_edges, Bd, x, y);
+    if (pairs)
+        block_diag_x2_kernel<NF><<<(n_edges + EPB - 1) / EPB, EPB * NF, 0, s>>>(
+            n_edges, reinterpret_cast<const float2*>(Bd), x, y);
+    else
+        block_diag_kernel<NF><<<(n_edges + EPB - 1) / EPB, EPB * NF, 0, s>>>(n_edges, Bd, x, y);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -487,19 +525,27 @@ cudaError_t cgs2_tail_dispatch(const T* V, size_t ldv, int nv, const double* h1,
 template <typename T>
 cudaError_t multidot_impl(const T* V, size_t ldv, int nv, const T* w, size_t n, double* scratch, double* out,
                           cudaStream_t s, const int* done) {
+    // one instance per column count: a runtime bound on the column loop would leave predicated-off
+    // FMAs in the kernel, and on GB300 those still occupy the slow FP64 pipe
     const bool v4 = lanes4<T>(n, ldv, {V, w});
     for (int j0 = 0; j0 < nv; j0 += kDotChunk) {
         const int nj = nv - j0 < kDotChunk ? nv - j0 : kDotChunk;
-        if constexpr (sizeof(T) == 4) {
-            if (v4) {
-                multidot_kernel<kDotChunk, T, 4><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, j0, nj, w, n, scratch, nv,
-                                                                                     out, done);
-                count_launches(1);
-                continue;
-            }
+        switch (nj) {
+#define CASE(C)                                                                                                   \
+    case C:                                                                                                       \
+        if constexpr (sizeof(T) == 4) {                                                                           \
+            if (v4) {                                                                                             \
+                multidot_kernel<C, T, 4><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, j0, nj, w, n, scratch, nv, out, \
+                                                                           done);                                 \
+                break;                                                                                            \
+            }                                                                                                     \
+        }                                                                                                         \
+        multidot_kernel<C, T><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, j0, nj, w, n, scratch, nv, out, done);   \
+        break;
+            CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+            default: return cudaErrorInvalidValue;
         }
-        multidot_kernel<kDotChunk, T><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, j0, nj, w, n, scratch, nv, out,
-                                                                          done);
         count_launches(1);
     }
     return cudaGetLastError();
@@ -531,18 +577,24 @@ cudaError_t launch_cgs2_tail(const float* V, size_t ldv, int nv, const double* h
 }
 
 cudaError_t launch_block_diag(const Geom& g, const double* Bd, const double* x, double* y,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool pairs) {
     switch (g.P) {
-        case 2: return block_diag_launch<6>(g.n_edges, Bd, x, y, s);
-        case 3: return block_diag_launch<9>(g.n_edges, Bd, x, y, s);
-        case 4: return block_diag_launch<12>(g.n_edges, Bd, x, y, s);
-        case 5: return block_diag_launch<15>(g.n_edges, Bd, x, y, s);
-        case 6: return block_diag_launch<18>(g.n_edges, Bd, x, y, s);
-        case 7: return block_diag_launch<21>(g.n_edges, Bd, x, y, s);
-        case 8: return block_diag_launch<24>(g.n_edges, Bd, x, y, s);
-        case 9: return block_diag_launch<27>(g.n_edges, Bd, x, y, s);
+        case 2: return block_diag_launch<6>(g.n_edges, Bd, x, y, s, pairs);
+        case 3: return block_diag_launch<9>(g.n_edges, Bd, x, y, s, pairs);
+        case 4: return block_diag_launch<12>(g.n_edges, Bd, x, y, s, pairs);
+        case 5: return block_diag_launch<15>(g.n_edges, Bd, x, y, s, pairs);
+        case 6: return block_diag_launch<18>(g.n_edges, Bd, x, y, s, pairs);
+        case 7: return block_diag_launch<21>(g.n_edges, Bd, x, y, s, pairs);
+        case 8: return block_diag_launch<24>(g.n_edges, Bd, x, y, s, pairs);
+        case 9: return block_diag_launch<27>(g.n_edges, Bd, x, y, s, pairs);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_split_pairs_inplace(double* a, size_t n, cudaStream_t s) {
+    split_pairs_inplace_kernel<<<stream_grid(n), 256, 0, s>>>(a, n);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 size_t dot_scratch_doubles(int nv) { return 1 + (size_t)kDotBlocks * (size_t)nv; }   // ticket + partials
