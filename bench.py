@@ -205,7 +205,7 @@ class ClockSampler:
 
 
 # ---- roofline --------------------------------------------------------------------------------
-def _algorithmic(N, k, cls, precision="fp64", dense=False):
+def _algorithmic(N, k, cls, precision="fp64", dense=False, local="fp64"):
     """(bytes, flops) one launch group of a kernel class moves / performs."""
     P = k + 1
     NF, NV, Np = 3 * P, 3 * P * P, P * P
@@ -216,14 +216,16 @@ def _algorithmic(N, k, cls, precision="fp64", dense=False):
     # local solves: dense A^{-1} ((3 Np)^2 numbers), or the Schur complement on phi: the (phi, phi)
     # block of A^{-1} (Np^2) and (1/d, cx, cy, phi_B) per node, 2 Np^2 + Np (8P + 26) flops
     op_b = n_el * NV * NV * 8 if dense else n_el * (Np * Np + 4 * Np) * 8
+    # FP32-pair Schur solves: the FP64 pipe only splits the inputs and forms the outputs
+    pair = local == "f32x2" and not dense
     if cls == "condense":   # operator once, R1 in, Z out; then Z face values + phiB in, g out
         return (op_b + n_el * 2 * NV * 8 + n_edges * NF * 8 * 3,
-                n_el * 2 * NV * NV if dense else n_el * (2 * Np * Np + Np * (8 * P + 26)))
+                n_el * 2 * NV * NV if dense else n_el * Np * (12 if pair else 2 * Np + 8 * P + 26))
     if cls == "recover":    # operator (dense: its boundary columns), Z, R1 in, Q, L out, traces in
         nb = 3 * (4 * P - 4)
         if dense:
             return n_el * (NV * nb * 8 + 4 * NV * 8) + n_edges * NF * 8, n_el * 2 * NV * nb
-        return op_b + n_el * 4 * NV * 8 + n_edges * NF * 8, n_el * (2 * Np * Np + Np * (8 * P + 32))
+        return op_b + n_el * 4 * NV * 8 + n_edges * NF * 8, n_el * Np * (40 if pair else 2 * Np + 8 * P + 32)
     if cls == "dg":
         return n_el * (2 * NV + Np) * 8, n_el * Np * 60
     return None, None
@@ -333,12 +335,12 @@ def _e2e(sim, stream, steps, dist, h, hu, hv):
     return ms, 3 * n * 8
 
 
-def _roofline(N, k, ktimes, precision, fp64_tflops, hbm, dense=False):
-    dom = max((c for c in ktimes if ktimes[c][1] > 0 and _algorithmic(N, k, c, precision, dense)[0]),
+def _roofline(N, k, ktimes, precision, fp64_tflops, hbm, dense=False, local="fp64"):
+    dom = max((c for c in ktimes if ktimes[c][1] > 0 and _algorithmic(N, k, c, precision, dense, local)[0]),
               key=lambda c: ktimes[c][0])
     tot_ms, n_l = ktimes[dom]
     avg_s = tot_ms / n_l / 1e3
-    byt, flo = _algorithmic(N, k, dom, precision, dense)
+    byt, flo = _algorithmic(N, k, dom, precision, dense, local)
     alu_peak = fp64_tflops if (precision == "fp64" or dom != "spmv") else FP32_NOMINAL_TFLOPS
     t_hbm, t_alu = byt / (hbm * 1e9), flo / (alu_peak * 1e12)
     if t_hbm >= t_alu:
@@ -617,6 +619,7 @@ def main():
     torch.cuda.set_stream(stream)
     dof = 3 * N * N * (k + 1) ** 2
     fp64_tflops = hd.measure_fp64_tflops()
+    cvt_hw, cvt_int = hd.measure_conversion_rates()
 
     forms = {}
     finals = {}
@@ -668,9 +671,10 @@ def main():
                       "ms_per_step": r["ms_total"] / args.steps,
                       "krylov_iterations_per_stage": r["stats"]["krylov_iterations"] / max(1, 2 * r["stats"]["steps"]),
                       "kernel_breakdown_ms": {c: {"ms": round(v[0], 3), "groups": v[1]} for c, v in r["ktimes"].items()},
-                      "roofline": _roofline(N, k, r["ktimes"], p, fp64_tflops, hbm, bool(args.local_dense)),
+                      "roofline": _roofline(N, k, r["ktimes"], p, fp64_tflops, hbm, bool(args.local_dense),
+                                            args.local if p == "mixed" else "fp64"),
                       "local_roofline": {c: _roofline(N, k, {c: r["ktimes"][c]}, p, fp64_tflops, hbm,
-                                                      bool(args.local_dense))
+                                                      bool(args.local_dense), args.local if p == "mixed" else "fp64")
                                          for c in ("condense", "recover") if r["ktimes"].get(c, (0, 0))[1] > 0},
                       "e2e": f["e2e"], "gpu_launches": r["launches"],
                       "local_tiles": {"condense": r["stats"].get("local_tile_condense", 0),
@@ -710,7 +714,9 @@ def main():
             "rel_l2_mixed_vs_fp64": err,
             "gpu_launches": summary[head]["gpu_launches"], "roofline": summary[head]["roofline"],
             "e2e": summary[head]["e2e"], "clocks": forms[head]["clocks"],
-            "fp64_fma_tflops_measured": fp64_tflops, "forms": summary, "cpu_baseline": cpu}
+            "fp64_fma_tflops_measured": fp64_tflops,
+            "f64_f32_conversions_per_s_measured": {"hardware": cvt_hw, "integer_pipe": cvt_int},
+            "forms": summary, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -295,6 +295,13 @@ hdgdg_status hdgdg_kernel_time(hdgdg_sim* sim, int cls, double* total_ms, long l
  * the denominator of ALU-bound roofline fractions.  ECUDA on failure. */
 hdgdg_status hdgdg_measure_fp64_tflops(double* tflops);
 
+/* Measured FP64 <-> FP32 conversion throughput of the current device (conversions per second),
+ * from chain kernels timed with CUDA events: *hardware_per_s with the conversion instructions the
+ * compiler emits for casts, *integer_per_s with the library's integer-pipe routines (the mixed
+ * and FP32-pair kernels use the latter; on GB300 the former run at the FP64 rate).  ECUDA on
+ * failure, EINVAL for NULL. */
+hdgdg_status hdgdg_measure_conversion_rates(double* hardware_per_s, double* integer_per_s);
+
 /* ---- allocation-free entry point ------------------------------------------------- */
 
 /* Mass sum_e J sum_ij w_i w_j phi_eta of a state, like the mass of hdgdg_get_stats, for

@@ -1353,4 +1353,9 @@ hdgdg_status hdgdg_measure_fp64_tflops(double* tflops) {
     return measure_fp64_fma(tflops) == cudaSuccess ? HDGDG_OK : HDGDG_ECUDA;
 }
 
+hdgdg_status hdgdg_measure_conversion_rates(double* hardware_per_s, double* integer_per_s) {
+    if (!hardware_per_s || !integer_per_s) return HDGDG_EINVAL;
+    return measure_conversions(hardware_per_s, integer_per_s) == cudaSuccess ? HDGDG_OK : HDGDG_ECUDA;
+}
+
 }  // extern "C"

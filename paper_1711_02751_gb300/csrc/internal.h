@@ -345,5 +345,6 @@ size_t mass_scratch_doubles();
 cudaError_t launch_mass(const Geom& g, const double* q, double* scratch, double* out, cudaStream_t s);
 
 cudaError_t measure_fp64_fma(double* tflops);
+cudaError_t measure_conversions(double* hw_per_s, double* int_per_s);
 
 }  // namespace hdgdg

@@ -21,7 +21,7 @@ BOUNDARIES = {"periodic": 0, "wall": 1, "vortex": 2}
 EXPORTS = ["hdgdg_bytes_required", "hdgdg_node_coords", "hdgdg_create", "hdgdg_set_state",
            "hdgdg_step", "hdgdg_get_state", "hdgdg_get_stats", "hdgdg_last_error", "hdgdg_destroy",
            "hdgdg_update_state", "hdgdg_eval_nl", "hdgdg_condense_rhs", "hdgdg_trace_apply", "hdgdg_stage_solve",
-           "hdgdg_measure_fp64_tflops", "hdgdg_set_kernel_timing", "hdgdg_kernel_time",
+           "hdgdg_measure_fp64_tflops", "hdgdg_measure_conversion_rates", "hdgdg_set_kernel_timing", "hdgdg_kernel_time",
            "hdgdg_mass_noalloc", "hdgdg_gll", "hdgdg_checkpoint_bytes", "hdgdg_save_checkpoint",
            "hdgdg_load_checkpoint"]
 KERNEL_CLASSES = ["spmv", "ortho", "condense", "recover", "dg", "combine", "residual", "guess", "precond"]
@@ -89,6 +89,7 @@ def lib():
         L.hdgdg_trace_apply.argtypes = [ctypes.c_void_p, _P, _P]
         L.hdgdg_stage_solve.argtypes = [ctypes.c_void_p, _P, _P, _P, ctypes.POINTER(ctypes.c_int)]
         L.hdgdg_measure_fp64_tflops.argtypes = [_P]
+        L.hdgdg_measure_conversion_rates.argtypes = [_P, _P]
         L.hdgdg_set_kernel_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.hdgdg_kernel_time.argtypes = [ctypes.c_void_p, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_longlong)]
         L.hdgdg_mass_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
@@ -162,6 +163,15 @@ def gll(k):
     if st != OK:
         raise HdgdgError(st, "gll")
     return x, w
+
+
+def measure_conversion_rates():
+    """(hardware, integer-pipe) FP64<->FP32 conversions per second on the current device."""
+    hw, it = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = lib().hdgdg_measure_conversion_rates(ctypes.byref(hw), ctypes.byref(it))
+    if st != OK:
+        raise HdgdgError(st, "measure_conversion_rates")
+    return hw.value, it.value
 
 
 def measure_fp64_tflops():
