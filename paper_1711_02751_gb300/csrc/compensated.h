@@ -36,10 +36,24 @@ struct Dot2 {
     __device__ __forceinline__ double value() const { return f32_to_f64(p) + f32_to_f64(c); }
 };
 
-// v = hi + lo to ~48 bits; the conversions run on the integer pipes (fastcvt.h), one FP64 subtract
+// v = hi + lo to ~48 bits (relative error <= 2e-15), on the integer pipes alone: hi is v rounded to
+// FP32 (fastcvt.h) and lo the exact remainder -- the 29 mantissa bits below hi's, less 2^29 when
+// hi rounded up, in units of v's last place -- normalised with a count of leading zeros and
+// rounded to 24 bits.  lo is 0 where hi is 0 or infinite (|v| outside [2^-126, 2^128)) and where
+// the remainder falls below 2^-126.
 __device__ __forceinline__ void split(double v, float& hi, float& lo) {
+    const unsigned hw = (unsigned)__double2hiint(v), lw = (unsigned)__double2loint(v);
     hi = f64_to_f32(v);
-    lo = f64_to_f32(v - f32_to_f64(hi));
+    const int e11 = (int)((hw & 0x7FFFFFFFu) >> 20);
+    const int r = (int)(lw & 0x1FFFFFFFu) - (int)((lw >> 28) & 1u) * (1 << 29);
+    const unsigned a = (unsigned)(r < 0 ? -r : r);   // < 2^29
+    const int p = 31 - __clz(a);                      // its top bit
+    const int sh = p - 23;
+    const unsigned mant = sh > 0 ? (((a >> (sh - 1)) + 1u) >> 1) : (a << (-sh));   // in [2^23, 2^24]
+    const int e8 = e11 + p - 948;                     // (e11 - 1075) + p + 127
+    unsigned bits = ((hw & 0x80000000u) ^ (r < 0 ? 0x80000000u : 0u)) | (unsigned)((e8 << 23) + (int)mant - (1 << 23));
+    bits = (a == 0u || e8 <= 0 || e11 <= 896 || e11 >= 1151) ? 0u : bits;
+    lo = __uint_as_float(bits);
 }
 
 }  // namespace hdgdg

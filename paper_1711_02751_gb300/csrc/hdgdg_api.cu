@@ -187,6 +187,10 @@ Geom make_geom(const hdgdg_config* c, double* xi_out) {
     for (int i = 0; i < 5; ++i) g.vortex[i] = c->bc_params[i];
     g.n_edges_inst = g.walls ? 2 * g.N * (g.N + 1) : 2 * g.n_el_inst;
     g.n_edges = g.batch * g.n_edges_inst;
+    g.byN.set((unsigned)g.N);
+    g.byN1.set((unsigned)g.N + 1u);
+    g.by_el.set((unsigned)g.n_el_inst);
+    g.by_edges.set((unsigned)g.n_edges_inst);
     g.dt_scale = nullptr;
     const double L = c->length > 0.0 ? c->length : 1.0;
     g.x0 = c->x0;

@@ -24,6 +24,34 @@ namespace hdgdg {
 
 constexpr int kMaxP = 9;   // degree k <= 8
 
+// Division by a divisor fixed at create.  A general integer division compiles to conversions
+// between integer and floating point, which GB300 executes at its FP64 rate; this is the
+// round-up multiply of Granlund and Montgomery ("Division by invariant integers using
+// multiplication", PLDI 1994): with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// q = (t + ((n - t) >> 1)) >> (l - 1) for t = the high word of n m, exact for every 32-bit n.
+struct FastDiv {
+    unsigned d = 1, m = 0;
+    int l = 0;
+    __host__ void set(unsigned div) {
+        d = div;
+        m = 0;
+        l = 0;
+        if (div <= 1) return;
+        while ((1ull << l) < div) ++l;
+        m = (unsigned)((((1ull << 32) * ((1ull << l) - div)) / div) + 1);
+    }
+    __host__ __device__ __forceinline__ int div(int n) const {   // n >= 0
+        if (d == 1) return n;
+        const unsigned u = (unsigned)n;
+#ifdef __CUDA_ARCH__
+        const unsigned t = __umulhi(u, m);
+#else
+        const unsigned t = (unsigned)(((unsigned long long)u * m) >> 32);
+#endif
+        return (int)((t + ((u - t) >> 1)) >> (l - 1));
+    }
+};
+
 // Mesh and GLL tables, passed by value to kernels.
 struct Geom {
     int N, P, Np, n_el, n_edges;   // n_el, n_edges: totals over all instances of the batch
@@ -43,6 +71,7 @@ struct Geom {
     double w[kMaxP];            // GLL weights
     double D[kMaxP * kMaxP];    // D[r*P + c] = l_c'(xi_r)
     double Dhat[kMaxP * kMaxP]; // Dhat[i*P + a] = (w_a / w_i) D[a*P + i]: weak-form volume lift
+    FastDiv byN, byN1, by_el, by_edges;   // / N, / (N + 1), / n_el_inst, / n_edges_inst
 };
 
 __host__ __device__ inline int face_node(int f, int b, int P) {
@@ -53,7 +82,7 @@ __host__ __device__ inline int face_node(int f, int b, int P) {
 // N^2 + r face 3 of element r.  Walls: x-edges ey*(N+1) + ix (ix = 0..N), y-edges
 // N(N+1) + iy*N + ex (iy = 0..N); a face on a wall has no neighbour (-1).
 __host__ __device__ inline int local_edge_of_face(int e, int f, const Geom& g) {
-    const int N = g.N, ex = e % N, ey = e / N;
+    const int N = g.N, ey = g.byN.div(e), ex = e - ey * N;
     if (g.walls) {
         const int nx = N * (N + 1);
         switch (f) {
@@ -64,15 +93,15 @@ __host__ __device__ inline int local_edge_of_face(int e, int f, const Geom& g) {
         }
     }
     switch (f) {
-        case 0: return ey * N + (ex + N - 1) % N;
+        case 0: return ey * N + (ex == 0 ? N - 1 : ex - 1);
         case 1: return e;
-        case 2: return N * N + ((ey + N - 1) % N) * N + ex;
+        case 2: return N * N + (ey == 0 ? N - 1 : ey - 1) * N + ex;
         default: return N * N + e;
     }
 }
 
 __host__ __device__ inline int local_neighbour(int e, int f, const Geom& g) {
-    const int N = g.N, ex = e % N, ey = e / N;
+    const int N = g.N, ey = g.byN.div(e), ex = e - ey * N;
     if (g.walls) {
         switch (f) {
             case 0: return ex > 0 ? e - 1 : -1;
@@ -82,10 +111,10 @@ __host__ __device__ inline int local_neighbour(int e, int f, const Geom& g) {
         }
     }
     switch (f) {
-        case 0: return ey * N + (ex + N - 1) % N;
-        case 1: return ey * N + (ex + 1) % N;
-        case 2: return ((ey + N - 1) % N) * N + ex;
-        default: return ((ey + 1) % N) * N + ex;
+        case 0: return ey * N + (ex == 0 ? N - 1 : ex - 1);
+        case 1: return ey * N + (ex == N - 1 ? 0 : ex + 1);
+        case 2: return (ey == 0 ? N - 1 : ey - 1) * N + ex;
+        default: return (ey == N - 1 ? 0 : ey + 1) * N + ex;
     }
 }
 
@@ -96,13 +125,13 @@ __host__ __device__ inline void local_edge_sides(int r, const Geom& g, int* em, 
     if (g.walls) {
         const int nx = N * (N + 1);
         if (r < nx) {
-            const int ey = r / (N + 1), ix = r % (N + 1);
+            const int ey = g.byN1.div(r), ix = r - ey * (N + 1);
             *em = ix >= 1 ? ey * N + ix - 1 : -1;
             *ep = ix < N ? ey * N + ix : -1;
             *fm = 1;
             *fp = 0;
         } else {
-            const int rr = r - nx, iy = rr / N, ex = rr % N;
+            const int rr = r - nx, iy = g.byN.div(rr), ex = rr - iy * N;
             *em = iy >= 1 ? (iy - 1) * N + ex : -1;
             *ep = iy < N ? iy * N + ex : -1;
             *fm = 3;
@@ -117,18 +146,18 @@ __host__ __device__ inline void local_edge_sides(int r, const Geom& g, int* em, 
 // Batched indices: instance i owns elements [i n_el_inst, (i+1) n_el_inst) and edges
 // [i n_edges_inst, (i+1) n_edges_inst); connectivity never crosses instances.
 __host__ __device__ inline int edge_of_face(int e, int f, const Geom& g) {
-    const int inst = e / g.n_el_inst;
+    const int inst = g.by_el.div(e);
     return inst * g.n_edges_inst + local_edge_of_face(e - inst * g.n_el_inst, f, g);
 }
 
 __host__ __device__ inline int neighbour(int e, int f, const Geom& g) {
-    const int inst = e / g.n_el_inst;
+    const int inst = g.by_el.div(e);
     const int nb = local_neighbour(e - inst * g.n_el_inst, f, g);
     return nb < 0 ? -1 : inst * g.n_el_inst + nb;
 }
 
 __host__ __device__ inline void edge_sides(int r, const Geom& g, int* em, int* fm, int* ep, int* fp) {
-    const int inst = r / g.n_edges_inst;
+    const int inst = g.by_edges.div(r);
     local_edge_sides(r - inst * g.n_edges_inst, g, em, fm, ep, fp);
     if (*em >= 0) *em += inst * g.n_el_inst;
     if (*ep >= 0) *ep += inst * g.n_el_inst;
@@ -136,7 +165,7 @@ __host__ __device__ inline void edge_sides(int r, const Geom& g, int* em, int* f
 
 // Time-step factor of the instance that owns element e (1 without a batch table).
 __host__ __device__ inline double dt_factor(const Geom& g, int e) {
-    return g.dt_scale ? g.dt_scale[e / g.n_el_inst] : 1.0;
+    return g.dt_scale ? g.dt_scale[g.by_el.div(e)] : 1.0;
 }
 
 // The moving vortex of Sec. 7.1 (eq. tc_vortex_ic) at (x, y, t) as (phi_eta, U, V) over the
@@ -160,9 +189,9 @@ __host__ __device__ inline void vortex_state(const Geom& g, double x, double y, 
 // Physical coordinates of face node b of face f of element e.
 __host__ __device__ inline void face_node_xy(const Geom& g, int e, int f, int b, double* x, double* y) {
     const int n = face_node(f, b, g.P), i = n % g.P, j = n / g.P;
-    const int el = e % g.n_el_inst;
-    *x = g.x0 + (el % g.N + 0.5 * (1.0 + g.xi[i])) * g.h;
-    *y = g.x0 + (el / g.N + 0.5 * (1.0 + g.xi[j])) * g.h;
+    const int el = e - g.by_el.div(e) * g.n_el_inst, ey = g.byN.div(el);
+    *x = g.x0 + (el - ey * g.N + 0.5 * (1.0 + g.xi[i])) * g.h;
+    *y = g.x0 + (ey + 0.5 * (1.0 + g.xi[j])) * g.h;
 }
 
 // Host-built periodic unit-square mesh and GLL tables of an N x N, degree-k mesh (no GPU call).

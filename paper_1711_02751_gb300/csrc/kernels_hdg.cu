@@ -598,7 +598,7 @@ __device__ __forceinline__ void schur_solve(SchurSmem<P, EPB, A>& sm, const Geom
         ncx = ax[Np + n];
         ncy = ax[2 * Np + n];
         pb = ax[3 * Np + n];
-        const T* eg = EG + (size_t)(e / g.n_el_inst) * 2 * Np;
+        const T* eg = EG + (size_t)g.by_el.div(e) * 2 * Np;
         sm.EG[le][0][n] = eg[n];
         sm.EG[le][1][n] = eg[Np + n];
         sm.t[le][0][n] = A::mul(xU, rd);

@@ -34,7 +34,7 @@ __global__ void cvt_chain_kernel(double* out, int iters) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             if (FAST) x[c] = f32_to_f64(f64_to_f32(x[c]) + 1e-7f);
-            else x[c] = (double)((float)x[c] + 1e-7f);
+            else x[c] = (double)(__double2float_rn(x[c]) + 1e-7f);   // the intrinsic: a cast pair would fold
         }
     }
     const double s = x[0] + x[1] + x[2] + x[3];
