@@ -33,7 +33,18 @@ UNIT = "DOF-steps/s"
 WORKLOADS = {"large512": (512, 3), "bump8": (8, 2), "mid128": (128, 3), "flat512": (512, 3), "flat256": (256, 3)}
 CPU_SAMPLE = (64, 3)       # oracle sample: the large512 recipe on 64 x 64, k = 3
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
-FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes of one Blackwell SM (4 partitions x 32)
+
+
+def fp32_nominal_tflops(peaks):
+    """Nominal FP32 FMA rate of the current device: its SM count (queried) x 128 lanes x 2 flops x
+    the maximum SM clock (MEASURED_PEAKS.json's sm_max_mhz, else the device's reported clock)."""
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    mhz = float(peaks.get("sm_max_mhz") or 0.0)
+    if mhz <= 0.0:
+        mhz = float(getattr(props, "clock_rate", 0) or 0) / 1e3
+    return props.multi_processor_count * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, props.multi_processor_count, mhz
 
 
 def _args():
@@ -335,13 +346,14 @@ def _e2e(sim, stream, steps, dist, h, hu, hv):
     return ms, 3 * n * 8
 
 
-def _roofline(N, k, ktimes, precision, fp64_tflops, hbm, dense=False, local="fp64"):
+def _roofline(N, k, ktimes, precision, fp64_tflops, hbm, dense=False, local="fp64", fp32_peak=(None, 0, 0.0)):
     dom = max((c for c in ktimes if ktimes[c][1] > 0 and _algorithmic(N, k, c, precision, dense, local)[0]),
               key=lambda c: ktimes[c][0])
     tot_ms, n_l = ktimes[dom]
     avg_s = tot_ms / n_l / 1e3
     byt, flo = _algorithmic(N, k, dom, precision, dense, local)
-    alu_peak = fp64_tflops if (precision == "fp64" or dom != "spmv") else FP32_NOMINAL_TFLOPS
+    fp32_tflops, n_sm, mhz = fp32_peak
+    alu_peak = fp64_tflops if (precision == "fp64" or dom != "spmv" or not fp32_tflops) else fp32_tflops
     t_hbm, t_alu = byt / (hbm * 1e9), flo / (alu_peak * 1e12)
     if t_hbm >= t_alu:
         roof = {"bound": "hbm", "achieved": byt / avg_s / 1e9, "peak": hbm, "unit": "GB/s"}
@@ -354,7 +366,7 @@ def _roofline(N, k, ktimes, precision, fp64_tflops, hbm, dense=False, local="fp6
                  "peak_source": ("FP64 FMA rate measured in bench.py by the library's probe (of measured)"
                                  if roof["bound"] == "alu" and alu_peak == fp64_tflops else
                                  "MEASURED_PEAKS.json hbm_gbs (of measured)" if roof["bound"] == "hbm"
-                                 else "nominal FP32 rate 152 SMs x 128 lanes x 2 x 2.07 GHz")})
+                                 else f"nominal FP32 rate: {n_sm} SMs (queried) x 128 lanes x 2 x {mhz:.0f} MHz")})
     return roof
 
 
@@ -657,6 +669,7 @@ def main():
 
     peaks = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
+    fp32_peak = fp32_nominal_tflops(peaks)
     err = None
     if "fp64" in finals and "mixed" in finals:
         err = _rel_l2_nodal(finals["mixed"], finals["fp64"], B)
@@ -672,9 +685,10 @@ def main():
                       "krylov_iterations_per_stage": r["stats"]["krylov_iterations"] / max(1, 2 * r["stats"]["steps"]),
                       "kernel_breakdown_ms": {c: {"ms": round(v[0], 3), "groups": v[1]} for c, v in r["ktimes"].items()},
                       "roofline": _roofline(N, k, r["ktimes"], p, fp64_tflops, hbm, bool(args.local_dense),
-                                            args.local if p == "mixed" else "fp64"),
+                                            args.local if p == "mixed" else "fp64", fp32_peak),
                       "local_roofline": {c: _roofline(N, k, {c: r["ktimes"][c]}, p, fp64_tflops, hbm,
-                                                      bool(args.local_dense), args.local if p == "mixed" else "fp64")
+                                                      bool(args.local_dense), args.local if p == "mixed" else "fp64",
+                                                      fp32_peak)
                                          for c in ("condense", "recover") if r["ktimes"].get(c, (0, 0))[1] > 0},
                       "e2e": f["e2e"], "gpu_launches": r["launches"],
                       "local_tiles": {"condense": r["stats"].get("local_tile_condense", 0),

@@ -62,19 +62,24 @@ enum { HDGDG_ARS2 = 0, HDGDG_ARS3 = 1, HDGDG_RK2 = 2, HDGDG_RK3 = 3 };
  *              preconditioned trace matrix, each cycle restarted from the true residual
  *              g - S qhat computed in FP64 with the solution accumulated in FP64 (iterative
  *              refinement), and the DG residual of the nonlinear part is computed in FP32
- *              arithmetic on the FP64 state; residual norms, the local condensation and
- *              recovery, the stage combinations and mass sums stay in FP64.
+ *              arithmetic on the FP64 state; residual norms, the stage combinations and mass
+ *              sums stay in FP64.  The local condensation and recovery follow local_precision
+ *              (FP64 unless another is chosen; HDGDG_LOCAL_F32X2 keeps them FP64-class on the
+ *              FP32 pipes) and the refinement residual follows residual_f32x2.
  *              hdgdg_eval_nl always evaluates in FP64. */
 enum { HDGDG_FP64 = 0, HDGDG_MIXED = 1 };
 /* Arithmetic of the local condensation Z = A^{-1} R1 and recovery A^{-1} (tau qhat) (eq.
  * linearizedHDGsystem_schur, recover_volume_unknowns); implicit schemes only.
- * HDGDG_LOCAL_FP64: per-element FP64 A^{-1} (default).
+ * HDGDG_LOCAL_FP64: FP64 arithmetic (0, the default): A^{-1} applied through the Schur
+ *                   complement on phi (see local_dense), or as the whole per-element FP64
+ *                   A^{-1} with local_dense = 1.
  * HDGDG_LOCAL_FP32: a per-element FP32 copy of A^{-1}, FP32 products and sums (CUDA cores).
  * HDGDG_LOCAL_BF16: ONE operator shared by all elements -- a flat bottom (phi_B constant) and
  *                   one time step for all instances, else create fails with EINVAL -- applied
  *                   to all elements as one dense contraction on the tensor cores (tcgen05, BF16
  *                   inputs, FP32 accumulation in tensor memory).
- * HDGDG_LOCAL_F32X2: FP64-class on the FP32 pipes: A^{-1} held as an FP32 pair (hi + lo, 8
+ * HDGDG_LOCAL_F32X2: FP64-class on the FP32 pipes: the local operator (the Schur-complement
+ *                   operators, or A^{-1} with local_dense = 1) held as FP32 pairs (hi + lo, 8
  *                   bytes per entry like FP64) and every row's dot product computed with the
  *                   compensated Dot2 scheme (exact products by FMA, TwoSum accumulation; Ogita,
  *                   Rump and Oishi 2005), about 1e-13 relative, at the HBM bound.
@@ -304,21 +309,27 @@ hdgdg_status hdgdg_measure_conversion_rates(double* hardware_per_s, double* inte
 
 /* ---- allocation-free entry point ------------------------------------------------- */
 
-/* Mass sum_e J sum_ij w_i w_j phi_eta of a state, like the mass of hdgdg_get_stats, for
- * callers that cannot allocate device memory (code inside another framework's fixed memory
- * pool, a real-time loop that must stay out of the CUDA allocator, a host callback).  The
- * paper has no counterpart: it is a service of this library.
+/* Mass sum_e J sum_ij w_i w_j phi_eta of ONE instance's state -- the mass hdgdg_get_stats
+ * reports for a handle of batch 1 -- for callers that cannot allocate device memory: code that
+ * runs inside another framework's fixed memory pool, a real-time loop that must stay out of the
+ * CUDA allocator, or a host callback, none of which may call cudaMalloc.  The paper has no
+ * counterpart: it is a service of this library.
+ * n_side: elements per side N of the square mesh (n_side * n_side elements, any boundary);
+ * length: side of the square domain, as hdgdg_config.length (<= 0 selects 1), which sets the
+ * element Jacobian J = (length / (2 N))^2.  For a batched handle, call once per instance on that
+ * instance's slice and add the results.
  * d_phi_eta: device array [n_el][(k+1)^2] (phi_eta = g (h - B)); d_mass: one device double,
  * written on the given stream (NULL = legacy default stream); both belong to the caller.
- * The partial sums live in a fixed array of the library's static device memory (8 MiB on
- * every GPU that loads the library, held until the process exits), so the call allocates
- * nothing; its first call on a device looks the array's address up once, and that first
- * call should come before any stream capture.  The array is shared by all calls on a device
- * and keeps the last call's contents; calls that overlap on the GPU race on it, so issue
- * them on one stream or serialise them.  EINVAL for n_side * n_side > 2^20 elements (the
- * array's capacity), a bad degree or NULL pointers; ECUDA if a launch fails. */
-hdgdg_status hdgdg_mass_noalloc(int n_side, int degree_k, const double* d_phi_eta, double* d_mass,
-                                void* cuda_stream);
+ * The per-element partial sums live in a fixed array of the library's static device memory
+ * (8 MiB on every GPU that loads the library, held until the process exits), so the call
+ * allocates nothing.  Each call looks the array's address up in the current context; the first
+ * call on a device may load the library's device code, so it should come before any stream
+ * capture.  The array is shared by all calls on a device and keeps the last call's contents;
+ * calls that overlap on the GPU race on it, so issue them on one stream or serialise them.
+ * EINVAL for n_side * n_side > 2^20 elements (the array's capacity), n_side < 1, a bad degree, a
+ * non-finite length or NULL pointers; ECUDA if the lookup or a launch fails. */
+hdgdg_status hdgdg_mass_noalloc(int n_side, int degree_k, double length, const double* d_phi_eta,
+                                double* d_mass, void* cuda_stream);
 
 #ifdef __cplusplus
 }

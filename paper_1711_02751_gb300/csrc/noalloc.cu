@@ -6,7 +6,7 @@
 // entry point takes the state and the output from the caller and keeps its own partial sums
 // in a fixed-size array in the library's static device memory, which every GPU that loads
 // the library holds until the process exits.
-#include <mutex>
+#include <cmath>
 
 #include "hdgdg.h"
 #include "internal.h"
@@ -14,7 +14,6 @@
 namespace {
 
 constexpr int kNoAllocMaxElements = 1 << 20;   // 8 MiB of per-element partial sums per device
-constexpr int kMaxDevices = 64;
 
 // Per-element partial masses of the current call.  Shared by every call on a device: calls
 // that overlap on the GPU race on it.
@@ -46,41 +45,35 @@ __global__ void sum_partials_kernel(const double* __restrict__ part, int n, doub
     if (threadIdx.x == 0) *out = J * sh[0];
 }
 
-std::mutex g_mu;
-double* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the static scratch on the current device, looked up once per device.
+// Device address of the static scratch in the current context.  Looked up on every call (the
+// lookup allocates nothing and is cheap), so a context that was torn down and created again,
+// which may place the module's static memory elsewhere, never sees a stale address.
 cudaError_t scratch_address(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_elem_mass);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_elem_mass);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = static_cast<double*>(p);
-    }
-    *out = g_scratch_addr[dev];
+    *out = static_cast<double*>(p);
     return cudaSuccess;
 }
 
 }  // namespace
 
-extern "C" hdgdg_status hdgdg_mass_noalloc(int n_side, int degree_k, const double* d_phi_eta,
+extern "C" hdgdg_status hdgdg_mass_noalloc(int n_side, int degree_k, double length, const double* d_phi_eta,
                                            double* d_mass, void* cuda_stream) {
-    if (n_side < 2 || degree_k < 1 || degree_k > hdgdg::kMaxP - 1 || !d_phi_eta || !d_mass)
+    if (n_side < 1 || degree_k < 1 || degree_k > hdgdg::kMaxP - 1 || !d_phi_eta || !d_mass ||
+        !std::isfinite(length))
         return HDGDG_EINVAL;
     const long long n_el = (long long)n_side * n_side;
     if (n_el > kNoAllocMaxElements) return HDGDG_EINVAL;   // beyond the static scratch
     hdgdg::Geom g = hdgdg::host_geom(n_side, degree_k);
+    const double L = length > 0.0 ? length : 1.0;
+    const double J = 0.25 * (L / n_side) * (L / n_side);   // element Jacobian (h/2)^2, h = L/N
     double* part = nullptr;
     if (scratch_address(&part) != cudaSuccess) return HDGDG_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const int threads = 256;
     elem_mass_kernel<<<(int)((n_el + threads - 1) / threads), threads, 0, s>>>((int)n_el, g.P, g, d_phi_eta, part);
-    sum_partials_kernel<<<1, 256, 0, s>>>(part, (int)n_el, g.J, d_mass);
+    sum_partials_kernel<<<1, 256, 0, s>>>(part, (int)n_el, J, d_mass);
     hdgdg::count_launches(2);
     return cudaGetLastError() == cudaSuccess ? HDGDG_OK : HDGDG_ECUDA;
 }

@@ -92,8 +92,8 @@ def lib():
         L.hdgdg_measure_conversion_rates.argtypes = [_P, _P]
         L.hdgdg_set_kernel_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.hdgdg_kernel_time.argtypes = [ctypes.c_void_p, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_longlong)]
-        L.hdgdg_mass_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
-                                         ctypes.c_void_p]
+        L.hdgdg_mass_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
         _lib = L
@@ -149,9 +149,9 @@ def node_coords(N, k, boundary="periodic", x0=0.0, length=1.0):
     return x, y
 
 
-def mass_noalloc(n_side, degree_k, phi_eta_dev_ptr, mass_dev_ptr, stream=None):
+def mass_noalloc(n_side, degree_k, phi_eta_dev_ptr, mass_dev_ptr, stream=None, length=1.0):
     """hdgdg_mass_noalloc on caller-owned device buffers (raw addresses); returns the status."""
-    return lib().hdgdg_mass_noalloc(int(n_side), int(degree_k), ctypes.c_void_p(phi_eta_dev_ptr),
+    return lib().hdgdg_mass_noalloc(int(n_side), int(degree_k), float(length), ctypes.c_void_p(phi_eta_dev_ptr),
                                     ctypes.c_void_p(mass_dev_ptr), ctypes.c_void_p(stream) if stream else None)
 
 

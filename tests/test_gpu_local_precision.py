@@ -138,7 +138,7 @@ def _bump8_run(local, n_steps):
         s.step(n_steps)
         out = s.get_state()
     qa, _ = swe.to_state(*out, b, W.G, W.H0)
-    return _energy_rel(m, qa, qo, phiB), imex.rel_l2(m, qa[0], qo[0])
+    return _energy_rel(m, qa, qo, phiB), max(imex.rel_l2(m, qa[c], qo[c]) for c in range(3))
 
 
 @pytest.mark.parametrize("local,bound", [("fp32", 1e-6), ("bf16", 2e-2)])
@@ -146,22 +146,22 @@ def test_precision_variant_one_step(local, bound):
     """One step of the 8x8, k = 2 bump in the mixed form with FP32 or BF16 (tensor-core) local
     contractions: error against the FP64 oracle at the operands' rounding level (FP32: ~1e-7;
     BF16: ~1e-3) -- and not below it, so the variant really ran."""
-    e, r_eta = _bump8_run(local, 1)
-    print(f"local {local}, 1 step: energy-norm rel {e:.3e}, eta rel {r_eta:.3e}")
-    assert e <= bound and r_eta <= bound
+    e, r_max = _bump8_run(local, 1)
+    print(f"local {local}, 1 step: energy-norm rel {e:.3e}, largest field rel {r_max:.3e}")
+    assert e <= bound and r_max <= bound
     assert e >= bound * 1e-4
 
 
 def test_fp32_variant_of_the_8x8_bump_200_steps():
     """The precision variant of the 8x8 bump over its 200 steps with FP32 local contractions:
-    measured 2.7e-5 against the FP64 oracle (energy norm and eta; hu, hv have decayed ~1e4 times
-    below eta and are not gated).  The error grows while the L-stable implicit part damps the
+    measured 2.7e-5 (eta), 1.2e-5 (hu), 1.4e-5 (hv) against the FP64 oracle; every field and the
+    energy norm are gated at 1e-4.  The error grows while the L-stable implicit part damps the
     bump: every stage rounds R1 -- the state itself -- to FP32, and the damped solution shrinks
     below the injected rounding.  (With BF16 operands the same mechanism leaves no accuracy after
     200 steps: 1.04 measured; bench.py --precision-table reports it.)"""
-    e, r_eta = _bump8_run("fp32", 200)
-    print(f"local fp32, 200 steps: energy-norm rel {e:.3e}, eta rel {r_eta:.3e}")
-    assert e <= 1e-4 and r_eta <= 1e-4
+    e, r_max = _bump8_run("fp32", 200)
+    print(f"local fp32, 200 steps: energy-norm rel {e:.3e}, largest field rel {r_max:.3e}")
+    assert e <= 1e-4 and r_max <= 1e-4
 
 
 @pytest.mark.parametrize("N,k", [(6, 3), (9, 2), (5, 4)])
@@ -185,10 +185,10 @@ def test_f32x2_local_operators_are_fp64_class(N, k):
 def test_f32x2_mixed_bump8_200_steps_against_the_oracle():
     """The mixed form with FP32-pair local contractions over the 8x8 bump's 200 steps stays as
     close to the FP64 oracle as the mixed form with FP64 local contractions (energy norm and
-    eta <= 1e-6; FP32 local contractions end at 2.7e-5)."""
-    e, r_eta = _bump8_run("f32x2", 200)
-    print(f"local f32x2, 200 steps: energy-norm rel {e:.3e}, eta rel {r_eta:.3e}")
-    assert e <= 1e-6 and r_eta <= 1e-6
+    every field <= 1e-6; FP32 local contractions end at 2.7e-5)."""
+    e, r_max = _bump8_run("f32x2", 200)
+    print(f"local f32x2, 200 steps: energy-norm rel {e:.3e}, largest field rel {r_max:.3e}")
+    assert e <= 1e-6 and r_max <= 1e-6
 
 
 def test_f32x2_autotuned_tile():

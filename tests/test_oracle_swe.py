@@ -222,3 +222,80 @@ def test_boundary_conversion_roundtrip():
     out = swe.from_state(q, phiB, 9.81)
     for a, r in zip(out, (h, hu, hv)):
         np.testing.assert_allclose(a, r, rtol=1e-14, atol=1e-16)
+
+
+# -- the Rusanov dissipation coefficients, pinned by the flux Jacobian's spectrum ----------------
+def _spectral_radius(flux, q, phiB, n):
+    """max |lambda| of d(F(q) . n)/dq at every node, F = flux(q, phiB) -> (F_x, F_y) each [3, ...].
+
+    The Jacobian is taken by central differences of the flux function and its eigenvalues by
+    numpy.linalg.eigvals, so nothing here restates the wave-speed formula (|u.n| + sqrt(phi)
+    for the full flux, sqrt(phi_B) for the linear one) that the oracle writes out.
+    """
+    q = np.asarray(q, dtype=float)
+    shape = q.shape[1:]
+    J = np.zeros(shape + (3, 3))
+    for c in range(3):
+        step = 1e-6 * (1.0 + np.abs(q[c]))
+        qp, qm = q.copy(), q.copy()
+        qp[c] += step
+        qm[c] -= step
+        Fxp, Fyp = flux(qp, phiB)
+        Fxm, Fym = flux(qm, phiB)
+        dF = ((Fxp - Fxm) * n[0] + (Fyp - Fym) * n[1]) / (2.0 * step)   # [3, ...]
+        J[..., :, c] = np.moveaxis(dF, 0, -1)
+    return np.abs(np.linalg.eigvals(J)).max(axis=-1)
+
+
+def _discontinuous_state(m, speed):
+    """phi_B in [1.5, 3] (so that phi differs from 1), depth perturbations of 0.2 and velocities of
+    `speed` that jump across every face (independent nodal noise, no continuity)."""
+    r = np.random.Generator(np.random.PCG64(11))
+    shape = (m.n_el, m.P, m.P)
+    phiB = 1.5 + 1.5 * r.random(shape)
+    q = np.stack([0.2 * r.standard_normal(shape),
+                  speed * phiB * r.standard_normal(shape),
+                  speed * phiB * r.standard_normal(shape)])
+    return q, phiB
+
+
+@pytest.mark.parametrize("f", [0, 1, 2, 3])
+def test_rusanov_coefficients_are_the_jacobian_spectral_radii(f):
+    """Eq. Full_russanov / Linear_russanov: tau* is the largest |eigenvalue| of the normal flux
+    Jacobian over the two sides of the face, and tau_L* the same for the linear flux.  The
+    oracle's F*_NL . n minus its central part {F_NL} . n must equal (tau* - tau_L*)/2 (q^- - q^+)
+    with both coefficients taken from the numerically computed spectra.  A dissipation
+    coefficient that drops |u.n|, forgets to divide U.n by phi, or uses phi_B in place of phi
+    moves the result by O(jump) and fails here."""
+    m = swe.Mesh(3, 2)
+    q, phiB = _discontinuous_state(m, 0.4)
+    n = swe.FACE_NORMALS[f]
+    qm, qp = m.face_values(q, f), m.neighbour_state(q, f)
+    bm, bp = m.face_values(phiB, f), m.neighbour_face_values(phiB, f)
+    Fxm, Fym = swe.flux_nonlinear(qm, bm)
+    Fxp, Fyp = swe.flux_nonlinear(qp, bp)
+    central = 0.5 * ((Fxm + Fxp) * n[0] + (Fym + Fyp) * n[1])
+    got = swe.rusanov_nl_normal_flux(m, q, phiB, f) - central
+    tau = np.maximum(_spectral_radius(swe.flux_full, qm, bm, n), _spectral_radius(swe.flux_full, qp, bp, n))
+    tau_L = np.maximum(_spectral_radius(swe.flux_linear, qm, bm, n), _spectral_radius(swe.flux_linear, qp, bp, n))
+    want = 0.5 * (tau - tau_L)[None] * (qm - qp)
+    scale = np.abs(want).max()
+    assert scale > 0.05                      # the dissipation term is not negligible in this state
+    assert np.abs(got - want).max() <= 1e-7 * scale
+    # the full flux of the explicit RK DG comparison uses the same tau*
+    Fxm, Fym = swe.flux_full(qm, bm)
+    Fxp, Fyp = swe.flux_full(qp, bp)
+    got_full = swe.rusanov_full_normal_flux(m, q, phiB, f) - 0.5 * ((Fxm + Fxp) * n[0] + (Fym + Fyp) * n[1])
+    want_full = 0.5 * tau[None] * (qm - qp)
+    assert np.abs(got_full - want_full).max() <= 1e-7 * np.abs(want_full).max()
+
+
+def test_jacobian_spectrum_of_the_shallow_water_flux():
+    """Sanity of the numerical spectrum itself on one state where the textbook answer is known:
+    a resting lake (U = V = 0) has normal-flux eigenvalues 0, +-sqrt(phi)."""
+    phi_eta, phiB = np.array([0.44]), np.array([2.0])
+    q = np.stack([phi_eta, np.zeros(1), np.zeros(1)])
+    rho = _spectral_radius(swe.flux_full, q, phiB, np.array([1.0, 0.0]))
+    assert abs(rho[0] - math.sqrt(2.44)) <= 1e-8
+    rho_L = _spectral_radius(swe.flux_linear, q, phiB, np.array([0.0, 1.0]))
+    assert abs(rho_L[0] - math.sqrt(2.0)) <= 1e-8

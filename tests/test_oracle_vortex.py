@@ -79,3 +79,20 @@ def test_vortex_error_matches_papers_table():
         ref = gold[str(N)]
         assert abs(l1 - ref[0]) <= 0.15 * ref[0], (N, l1, ref[0])
         assert abs(l2 - ref[1]) <= 0.15 * ref[1], (N, l2, ref[1])
+
+
+@pytest.mark.slow_oracle
+@pytest.mark.parametrize("k,dt", [(2, 0.005), (3, 0.0025)])
+def test_vortex_error_on_16x16_matches_papers_table_to_two_percent(k, dt):
+    """p = 2 and 3 at T = 2 on 16 x 16 (Table tab:tc_mv_hconv_hdg3): on a mesh that resolves the
+    vortex, the L1 and L2 errors of eta agree with the printed values to within 2% (measured:
+    0.3% for p = 2, 0.05% for p = 3).  Where the discretisation's error is this close to the
+    paper's, its flux choices are the paper's: the Rusanov coefficient tau* enters every face of
+    the explicit part, and the sharp pin of tau* is the flux Jacobian's spectrum (test_oracle_swe)."""
+    gold = json.load(open(GOLDEN))["eta"][str(k)]["16"]
+    m, q, phiB, bc = vortex_problem(16, k)
+    st = imex.Stepper(m, phiB, dt, scheme="ars3", solver="lu", bc=bc)
+    q = st.run(q, int(round(2.0 / dt)))
+    l1, l2, _ = eta_errors(m, q, 2.0)
+    assert abs(l1 - gold[0]) <= 0.02 * gold[0], (l1, gold[0])
+    assert abs(l2 - gold[1]) <= 0.02 * gold[1], (l2, gold[1])
