@@ -71,6 +71,13 @@ def _args():
                     help="mixed form: refinement residual in FP32-pair (FP64-class) arithmetic")
     ap.add_argument("--local-dense", type=int, default=0, choices=[0, 1],
                     help="local solves: 0 Schur complement on phi (library default), 1 dense A^-1")
+    ap.add_argument("--stiff-steps", type=int, default=10,
+                    help="timed steps of the stiff variant (large512_stiff, gravity Courant ~14) "
+                         "reported beside the headline; 0 skips it")
+    ap.add_argument("--line-serving-requests", type=int, default=12,
+                    help="requests of the short serving run reported in the main line; 0 skips it")
+    ap.add_argument("--line-serving-rate", type=float, default=2.0,
+                    help="Poisson arrival rate (requests/s) of that serving run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true",
@@ -292,10 +299,10 @@ def job_value(world, dof, steps, ms):
     return world * dof * steps / (ms / 1e3)
 
 
-def _timed_steps(sim, stream, steps, dist):
+def _timed_steps(sim, stream, steps, dist, timing=True):
     """K steps of a resident instance, CUDA events on the library's stream around each."""
     import torch
-    sim.set_kernel_timing(True)
+    sim.set_kernel_timing(timing)
     l0 = sim.stats()["kernel_launches"]
     if dist:
         dist.barrier()
@@ -379,29 +386,77 @@ def _rel_l2_nodal(a, b, B):
     return out
 
 
+def stiff_block(args, stream, dist, world):
+    """The stiff variant beside the headline: large512_stiff (the large512 recipe with max |u| =
+    0.01 and the time-step floor at 0.01 sqrt(g H0): gravity Courant number ~14 while the explicit
+    part keeps its Courant number), both forms, --stiff-steps timed steps after --warmup."""
+    import torch
+    from paper_1711_02751_gb300 import hdgdg as hd
+    from paper_1711_02751_gb300 import workloads as W
+    N, k = WORKLOADS["large512"]
+    x, y = hd.node_coords(N, k)
+    rank = int(os.environ.get("RANK", "0"))
+    h, hu, hv, b = W.stiff_state(x, y, seed=2000 + rank)
+    dt = W.advective_dt(x, h, hu, hv, N, floor=W.STIFF_FLOOR)
+    dx_min = (1.0 / N) / 2.0 * float(np.diff(hd.gll(k)[0]).min())
+    cr_gravity = float(np.sqrt(W.G * h).max()) * dt / dx_min
+    speed = float((np.sqrt(hu ** 2 + hv ** 2) / h).max())
+    dof = 3 * N * N * (k + 1) ** 2
+    out = {"workload": f"large512_stiff: the large512 recipe with max|u| = {W.STIFF_UMAX}, "
+                       f"dt = {dt:.6g} (0.5 h/((2k+1) max(2max|u|, {W.STIFF_FLOOR})))",
+           "gravity_courant": cr_gravity, "paper_courant": (speed + float(np.sqrt(W.G * h).max())) * dt / dx_min,
+           "explicit_courant_2u": 2.0 * speed * dt / dx_min, "steps": args.stiff_steps, "forms": {}}
+    finals = {}
+    for precision in args.precisions.split(","):
+        sim = hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, stream=stream.cuda_stream, precision=precision,
+                     local_precision=args.local if precision == "mixed" else "fp64",
+                     residual_f32x2=bool(args.residual_f32x2) and precision == "mixed")
+        sim.set_state(h, hu, hv)
+        for _ in range(args.warmup):
+            sim.step(1)
+        torch.cuda.synchronize()
+        s0 = sim.stats()
+        r = _timed_steps(sim, stream, args.stiff_steps, dist, timing=False)
+        st = r["stats"]
+        finals[precision] = sim.get_state()
+        sim.close()
+        out["forms"][precision] = {
+            "value": job_value(world, dof, args.stiff_steps, r["ms_total"]),
+            "ms_per_step": r["ms_total"] / args.stiff_steps,
+            "krylov_iterations_per_stage": (st["krylov_iterations"] - s0["krylov_iterations"]) / (2 * args.stiff_steps),
+            "gpu_launches": r["launches"]}
+    if "fp64" in finals and "mixed" in finals:
+        out["rel_l2_mixed_vs_fp64"] = _rel_l2_nodal(finals["mixed"], finals["fp64"], W.H0 - b)
+    return out
+
+
+def serving_summary(n_requests, rate, slots=8):
+    """A serving run: Poisson arrivals at `rate`, N log-uniform in [32, 256], k in {2, 3, 4}, steps
+    U[50, 500], one seeded bump at rest on a flat bottom, mixed form, admitted by memory budget."""
+    import torch
+    from paper_1711_02751_gb300 import serving
+    free, _ = torch.cuda.mem_get_info()
+    reqs = serving.poisson_requests(n_requests, rate)
+    budget = int(0.5 * free)
+    srv = serving.Server(hbm_budget=budget, max_slots=slots, chunk=10)
+    summ = srv.serve(reqs)
+    busy = [e for e in srv.log if e["running"] > 0]
+    return summ, {"requests": n_requests, "arrival_rate_per_s": rate, "slots": slots, "hbm_budget_bytes": budget,
+                  "occupancy": len(busy) / max(1, len(srv.log))}
+
+
 def serving_line(args):
     """Serving workload: Poisson arrivals, N log-uniform in [32, 256], k in {2, 3, 4}, steps
     uniform in [50, 500], mixed form, admitted by device-memory budget into 8 slots."""
-    import torch
-    from paper_1711_02751_gb300 import hdgdg as hd
-    from paper_1711_02751_gb300 import serving
-    free, total = torch.cuda.mem_get_info()
-    reqs = serving.poisson_requests(args.serving_requests, args.serving_rate)
-    budget = int(0.5 * free)
-    srv = serving.Server(hbm_budget=budget, max_slots=8, chunk=10)
-    summ = srv.serve(reqs)
-    busy = [e for e in srv.log if e["running"] > 0]
+    summ, cfg = serving_summary(args.serving_requests, args.serving_rate)
     line = {"metric": "serving: DOF-steps/s and time to solution (p50/p99) under Poisson arrivals",
             "value": summ["throughput_dof_steps_per_s"], "unit": UNIT, "n_gpus": 1,
             "higher_is_better": True, "dtype": "f64+f32 (mixed form)", "data": "synthetic",
-            "config": {"workload": "serving: N log-uniform [32,256], k in {2,3,4}, steps U[50,500], "
-                                   "seeded bump + streamfunction states",
-                       "requests": args.serving_requests, "arrival_rate_per_s": args.serving_rate,
-                       "slots": 8, "hbm_budget_bytes": budget},
+            "config": dict({"workload": "serving: N log-uniform [32,256], k in {2,3,4}, steps U[50,500], "
+                                        "one seeded bump at rest, flat bottom"}, **cfg),
             "tts_p50_s": summ["tts_p50_s"], "tts_p99_s": summ["tts_p99_s"], "wall_s": summ["wall_s"],
             "completed": summ["completed"], "max_running": summ["max_running"],
-            "max_queued": summ["max_queued"], "errors": summ["errors"][:3],
-            "occupancy": len(busy) / max(1, len(srv.log))}
+            "max_queued": summ["max_queued"], "errors": summ["errors"][:3]}
     print(json.dumps(line), flush=True)
 
 
@@ -662,6 +717,7 @@ def main():
                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
         sim.close()
         forms[precision] = {"r": r, "clocks": c, "e2e": e2e}
+    stiff = stiff_block(args, stream, dist, world) if args.stiff_steps > 0 else None
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -698,6 +754,14 @@ def main():
     p50 = statistics.median(per_step)
     p99 = sorted(per_step)[min(len(per_step) - 1, math.ceil(0.99 * len(per_step)) - 1)]
 
+    serving_rec = None
+    if world == 1 and args.line_serving_requests > 0:
+        summ, cfg = serving_summary(args.line_serving_requests, args.line_serving_rate)
+        serving_rec = dict(cfg, **{k_: summ[k_] for k_ in ("tts_p50_s", "tts_p99_s", "throughput_dof_steps_per_s",
+                                                          "wall_s", "completed", "max_running", "max_queued")},
+                           errors=summ["errors"][:3],
+                           workload="Poisson arrivals, N log-uniform [32,256], k in {2,3,4}, steps U[50,500], "
+                                    "one seeded bump at rest, flat bottom, mixed form")
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         try:
@@ -724,7 +788,8 @@ def main():
                                         4: "cubic extrapolation", 5: "quartic extrapolation",
                                         6: "quintic extrapolation"}[args.guess],
                        "l2": "inputs larger than L2 (trace matrix GBs, local operators >= 0.5 GB)"},
-            "latency_ms": {"p50": p50, "p99": p99},
+            "latency_ms": {"p50": p50, "p99": p99, "what": "per time step of the headline workload"},
+            "serving": serving_rec, "stiff": stiff,
             "rel_l2_mixed_vs_fp64": err,
             "gpu_launches": summary[head]["gpu_launches"], "roofline": summary[head]["roofline"],
             "e2e": summary[head]["e2e"], "clocks": forms[head]["clocks"],

@@ -57,7 +57,7 @@ def poisson_requests(n, rate_per_s, seed=5000, n_range=(32, 256), degrees=(2, 3,
         N = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))))
         k = int(rng.choice(degrees))
         steps = int(rng.integers(steps_range[0], steps_range[1] + 1))
-        out.append(Request(i, N, k, steps, seed + 1 + i, t, precision))
+        out.append(Request(i, N, k, steps, seed + 1 + i, t, precision, bottom_amp=0.0))
     return out
 
 
@@ -71,16 +71,11 @@ def ensemble_requests(n=256, seed=4000, sides=(16, 32, 64, 128), degrees=(2, 3, 
 
 
 def initial_state(req):
-    """The request's seeded state: one seeded Gaussian bump over a sinusoidal bottom of the
-    request's amplitude, smooth streamfunction velocity, on the library's own nodes."""
+    """The request's seeded state on the library's own nodes: one seeded Gaussian bump on a lake
+    at rest over a sinusoidal bottom of the request's amplitude (flat for the Poisson serving
+    requests, like the 8 x 8 bump; U[0, 0.1] for the ensemble), and its advective time step."""
     x, y = hd.node_coords(req.N, req.k)
-    h, hu, hv, b = W.large_state(x, y, seed=req.seed, n_bumps=1, umax=0.05)
-    if req.bottom_amp != 0.1:                  # rescale the bottom, keep the bump and the velocity
-        bump = h - (W.H0 - b)
-        u, v = hu / h, hv / h
-        b = b * (req.bottom_amp / 0.1)
-        h = W.H0 - b + bump
-        hu, hv = h * u, h * v
+    h, hu, hv, b = W.bump_at_rest_state(x, y, req.seed, req.bottom_amp)
     dt = W.advective_dt(x, h, hu, hv, req.N)
     return h, hu, hv, b, dt
 

@@ -16,6 +16,10 @@ Workloads (unit square, periodic, g = 1, H0 = 1):
                  seeded Gaussian bumps (amplitude U[0.005, 0.02], width U[0.02, 0.08],
                  centre U[0,1]^2, minimum-image distance), velocity from a seeded smooth
                  random streamfunction scaled to max |u| = 0.05, 200 steps.
+* ``large512_stiff`` the large512 recipe with a slower flow, max |u| = 0.01 (same seeds), and
+                 the rest-state floor of the time-step rule lowered to 0.01 sqrt(g H0): the
+                 explicit part keeps its Courant number while the gravity Courant number of
+                 the implicit part rises to about 14 (the stiff regime of the method).
 * ``sized(N, k)`` the large512 recipe on another mesh (parity cases that span several
                  tiles and a ragged tail).
 
@@ -86,6 +90,16 @@ def large_state(x, y, seed=2000, n_bumps=16, umax=0.05):
     return h, h * u, h * v, b
 
 
+def bump_at_rest_state(x, y, seed, bottom_amp=0.0):
+    """Ensemble and serving requests: one seeded Gaussian bump (centre U[0,1]^2, amplitude
+    U[0.005, 0.02], width U[0.02, 0.08], minimum-image distance) on a lake at rest (u = v = 0)
+    over the bottom b = bottom_amp sin(2 pi x) sin(2 pi y) (0: flat, as the 8 x 8 bump)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    b = bottom_amp * np.sin(2.0 * math.pi * x) * np.sin(2.0 * math.pi * y)
+    h = H0 - b + gaussian_bumps(x, y, rng, 1)
+    return h, np.zeros_like(x), np.zeros_like(x), b
+
+
 def lake_at_rest_state(x, y, amp=0.1):
     """Still water over the sinusoidal bottom: h = H0 - b, u = v = 0."""
     b = amp * np.sin(2.0 * math.pi * x) * np.sin(2.0 * math.pi * y)
@@ -147,17 +161,17 @@ def vortex_state(x, y, t, H_inf=1.0, u_inf=1.0, v_inf=0.0, beta=5.0, g=2.0, xc=0
     return H, H * u, H * v, np.zeros_like(x)
 
 
-def advective_dt(x, h, hu, hv, n_side, cfl=0.5, g=G, H0_=H0):
+def advective_dt(x, h, hu, hv, n_side, cfl=0.5, g=G, H0_=H0, floor=0.05):
     """Explicit-part time step dt = cfl * h_e / ((2k+1) * lambda_NL) for states [n_el, (k+1)^2].
 
     h_e = 1/n_side is the element size and h_e/(2k+1) the standard explicit DG length scale
     for degree k.  lambda_NL is the spectral radius of the nonlinear flux Jacobian dF_NL/dq,
-    whose largest eigenvalue is 2|u| (from d(U^2/phi)/dU), floored at 0.05 sqrt(g H0) for
-    states at rest.  x is unused beyond its shape (kept for the call signature).
+    whose largest eigenvalue is 2|u| (from d(U^2/phi)/dU), floored at `floor` sqrt(g H0) for
+    states at rest (0.05 unless a workload states otherwise).  x is unused beyond its shape.
     """
     k = int(round(np.sqrt(np.shape(x)[1]))) - 1
     speed = np.sqrt(hu ** 2 + hv ** 2) / h
-    lam = max(2.0 * float(speed.max()), 0.05 * math.sqrt(g * H0_))
+    lam = max(2.0 * float(speed.max()), floor * math.sqrt(g * H0_))
     return cfl * (1.0 / n_side) / ((2 * k + 1) * lam)
 
 
@@ -166,9 +180,19 @@ def courant(dx_min, dt, max_speed_plus_celerity):
     return max_speed_plus_celerity * dt / dx_min
 
 
+STIFF_UMAX = 0.01    # large512_stiff: max |u| of the streamfunction flow
+STIFF_FLOOR = 0.01   # large512_stiff: rest-state floor of the time-step rule, in units of sqrt(g H0)
+
+
+def stiff_state(x, y, seed=2000):
+    """large512_stiff: the large recipe with the flow slowed to max |u| = STIFF_UMAX."""
+    return large_state(x, y, seed=seed, umax=STIFF_UMAX)
+
+
 WORKLOADS = {
     "bump8": {"N": 8, "k": 2, "steps": 100, "state": "bump8"},
     "large512": {"N": 512, "k": 3, "steps": 200, "state": "large"},
+    "large512_stiff": {"N": 512, "k": 3, "steps": 200, "state": "stiff", "dt_floor": STIFF_FLOOR},
 }
 
 
@@ -179,6 +203,8 @@ def make_state(name, x, y, seed=None):
         return bump8_state(x, y)
     if kind == "large":
         return large_state(x, y, seed=2000 if seed is None else seed)
+    if kind == "stiff":
+        return stiff_state(x, y, seed=2000 if seed is None else seed)
     if kind == "lake":
         return lake_at_rest_state(x, y)
     if kind == "standing":

@@ -3,8 +3,8 @@
 The DG residual is compared with the oracle over the whole mesh.  The implicit path is too
 large for the oracle's direct solve, so whole steps are checked by properties that hold at any
 size: finiteness and mass over the workload's 200 steps, bitwise reproducibility, and the
-mixed form within 1e-6 of the FP64 form.  (The 64 x 64 case in test_gpu_parity covers the
-implicit path against the oracle across many tiles.)
+mixed form within 1e-6 of the FP64 form.  (Whole steps of the implicit path against the oracle
+at production launch shapes -- 64 x 64, k = 3, both forms -- are in test_gpu_production_shapes.)
 """
 import numpy as np
 import pytest
