@@ -53,8 +53,14 @@ bool valid(const hdgdg_config* c) {
            (c->local_precision != HDGDG_LOCAL_BF16 || c->degree_k <= 4) &&   // tensor-core tiles: k <= 4
            c->krylov_guess >= -1 && c->krylov_guess <= 6 && (c->spmv_kernel == 0 || c->spmv_kernel == 1) &&
            (c->krylov_ortho == 0 || c->krylov_ortho == 1) && (c->residual_f32x2 == 0 || c->residual_f32x2 == 1) &&
-           (c->local_dense == 0 || c->local_dense == 1);
+           (c->local_dense == 0 || c->local_dense == 1) && (c->trace_operator == 0 || c->trace_operator == 1) &&
+           (c->trace_operator == 0 ||
+            (c->precision == HDGDG_MIXED && c->local_precision == HDGDG_LOCAL_F32X2 && !c->local_dense &&
+             c->scheme != HDGDG_RK2 && c->scheme != HDGDG_RK3));
 }
+
+// the mixed form's trace solve applies S M^{-1} element by element (kernels_mf.cu)
+bool matrix_free(const hdgdg_config* c) { return c->trace_operator == 1; }
 
 bool explicit_scheme(const hdgdg_config* c) { return c->scheme == HDGDG_RK2 || c->scheme == HDGDG_RK3; }
 
@@ -99,7 +105,7 @@ Plan make_plan(const hdgdg_config* c) {
     b += (5 + 2 * (size_t)p.s) * 3 * p.n * d;                 // q, q_new, R1, Z, Q, NL_i, L_i
     b += 5 * p.nt * d;                                        // g, x~, qhat, w, DG face fluxes
     if (c->precision == HDGDG_MIXED) {                        // FP32 S~, FP32 basis and work vector
-        b += n_edges * 6 * (size_t)p.NF * p.NF * sizeof(float);
+        if (!matrix_free(c)) b += n_edges * 6 * (size_t)p.NF * p.NF * sizeof(float);
         b += ((size_t)p.m + 2) * p.nt * sizeof(float);
     } else {
         b += ((size_t)p.m + 1) * p.nt * d;                    // FP64 Krylov basis
@@ -113,7 +119,13 @@ Plan make_plan(const hdgdg_config* c) {
     } else if (c->local_precision == HDGDG_LOCAL_F32X2) {
         b += 2 * n_el * (size_t)p.NV * p.NV * sizeof(float);
     }
-    if (c->precision == HDGDG_MIXED && c->residual_f32x2) b += n_edges * 6 * (size_t)p.NF * p.NF * sizeof(float);
+    if (c->precision == HDGDG_MIXED && c->residual_f32x2 && !matrix_free(c))
+        b += n_edges * 6 * (size_t)p.NF * p.NF * sizeof(float);
+    if (matrix_free(c)) {   // FP32 M^{-1}, FP32 Schur operators, the plus-side halves, one ticket per edge
+        b += n_edges * (size_t)p.NF * p.NF * sizeof(float);
+        b += (n_el * Np * Np + 4 * n_el * Np + 2 * B * Np) * sizeof(float);
+        b += p.nt * d + n_edges * sizeof(int);
+    }
     b += 2 * (size_t)guess_order(c) * p.s * p.nt * d;         // previous stage solutions and products
     p.persistent = b;
     p.setup_temp = n_el * (size_t)p.NT * p.NT * d + n_edges * 7 * (size_t)p.NF * p.NF * d;
@@ -307,6 +319,8 @@ struct hdgdg_sim {
     double *gvec = nullptr, *xt = nullptr, *lam = nullptr, *w = nullptr, *V = nullptr, *fface = nullptr;
     float *Stil32 = nullptr, *V32 = nullptr, *w32 = nullptr;   // mixed precision only
     float* Stil_lo = nullptr;   // residual_f32x2: S~ = Stil32 + Stil_lo
+    MfOps mf;                   // trace_operator = 1: the matrix-free operator's data
+    float* Minv32 = nullptr;    // its FP32 block-Jacobi inverse
     double *red = nullptr, *mred = nullptr, *dvals = nullptr;
     GmresCtl* ctl = nullptr;
     CycleGraph cycle_graph[4];   // [FP64 form, mixed form] x [timers off, on]
@@ -467,6 +481,9 @@ hdgdg_status norm2_to_host(hdgdg_sim* sim, const double* v, double* out) {
     return HDGDG_OK;
 }
 
+// Lift factor of the local solves: -B qhat = beta tau qhat on the boundary nodes, beta = dt a_ii (2/h)/w_0
+double beta_of(const hdgdg_sim* sim) { return sim->cfg.dt * sim->a_ii * sim->g.two_over_h * sim->g.inv_w0; }
+
 // Right-preconditioned GMRES(m) on S~ x~ = g with classical Gram-Schmidt applied twice, then
 // qhat = M^{-1} x~.  The Givens rotations, the residual estimate and the stop test run on the
 // device (GmresCtl), so a whole restart cycle is queued at once and the host waits once per
@@ -574,10 +591,12 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
             const T* Vj = V + (size_t)j * n;
             {
                 TimedGroup tg(sim, HDGDG_KT_SPMV, j);
-                if constexpr (kMixed)
-                    e = launch_spmv_pre(sim->g, St, sim->Scol, Vj, w, st, done,
-                                        sim->cfg.spmv_kernel == 1 ? spmv_error(sim) : nullptr);
-                else
+                if constexpr (kMixed) {
+                    if (matrix_free(&sim->cfg)) e = launch_mf_inner(sim->g, sim->mf, Vj, w, beta_of(sim), st, done);
+                    else
+                        e = launch_spmv_pre(sim->g, St, sim->Scol, Vj, w, st, done,
+                                            sim->cfg.spmv_kernel == 1 ? spmv_error(sim) : nullptr);
+                } else
                     e = launch_spmv_pre(sim->g, St, sim->Scol, Vj, w, st, done);
             }
             TimedGroup tg(sim, HDGDG_KT_ORTHO, j);
@@ -590,7 +609,10 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
         TimedGroup tg_end(sim, HDGDG_KT_RESIDUAL);
         if (e == cudaSuccess) e = launch_gmres_update(V, n, ctl, sim->xt, n, st);
         // the true residual w = g - S~ x~ that ends the cycle, and ||w||^2
-        if (kMixed && sim->Stil_lo) {   // one fused FP32-pair pass
+        if (kMixed && matrix_free(&sim->cfg)) {   // matrix-free in FP32-pair arithmetic, then the norm
+            if (e == cudaSuccess) e = launch_mf_residual(sim->g, sim->mf, sim->xt, g, sim->w, beta_of(sim), st);
+            if (e == cudaSuccess) e = launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st);
+        } else if (kMixed && sim->Stil_lo) {   // one fused FP32-pair pass
             if (e == cudaSuccess)
                 e = launch_residual_norm_x2(sim->g, sim->Stil32, sim->Stil_lo, sim->Scol, sim->xt, g, sim->w,
                                             sim->red, dv_nrm(sim), st);
@@ -666,7 +688,8 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
     }
     {
         TimedGroup tg(sim, HDGDG_KT_PRECOND);
-        CU(launch_block_diag(sim->g, sim->Minv, sim->xt, qhat, st, sim->minv_pairs));
+        if (kMixed && matrix_free(&sim->cfg)) CU(launch_mf_back(sim->g, sim->Minv32, sim->xt, qhat, st));
+        else CU(launch_block_diag(sim->g, sim->Minv, sim->xt, qhat, st, sim->minv_pairs));
     }
     const int order = guess_order(&sim->cfg);
     if (stage >= 0 && order > 0) {   // keep x~ and S~ x~ = g - r for the next steps' guesses
@@ -695,7 +718,6 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
     return HDGDG_OK;
 }
 
-double beta_of(const hdgdg_sim* sim) { return sim->cfg.dt * sim->a_ii * sim->g.two_over_h * sim->g.inv_w0; }
 
 // One implicit stage: R1 (device) -> Q, Lst = dt M^{-1} L (device); qhat left in sim->lam.
 hdgdg_status stage_solve_dev(hdgdg_sim* sim, const double* R1, double* Q, double* Lst, int* its,
@@ -887,8 +909,10 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
             TRY(dalloc(sim, &sim->yhist[i][h], p.nt));
         }
     if (c->precision == HDGDG_MIXED) {
-        TRY(dalloc(sim, &sim->Stil32, (size_t)g.n_edges * 6 * p.NF * p.NF));
-        if (c->residual_f32x2) TRY(dalloc(sim, &sim->Stil_lo, (size_t)g.n_edges * 6 * p.NF * p.NF));
+        if (!matrix_free(c)) {
+            TRY(dalloc(sim, &sim->Stil32, (size_t)g.n_edges * 6 * p.NF * p.NF));
+            if (c->residual_f32x2) TRY(dalloc(sim, &sim->Stil_lo, (size_t)g.n_edges * 6 * p.NF * p.NF));
+        }
         TRY(dalloc(sim, &sim->V32, (size_t)(p.m + 1) * p.nt));
         TRY(dalloc(sim, &sim->w32, p.nt));
     } else {
@@ -921,7 +945,9 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
     cudaError_t e = launch_build_local(g, sim->phiB, sim->tau, c->dt * sim->a_ii, sim->Ainv, Se, dsing, sim->stream);
     if (e == cudaSuccess)
         e = launch_assemble_trace(g, Se, S7, sim->Srr, sim->Minv, sim->Stil, sim->Scol, dsing, sim->stream);
-    if (e == cudaSuccess && c->precision == HDGDG_MIXED) {
+    if (e == cudaSuccess && c->precision == HDGDG_MIXED && matrix_free(c)) {
+        sim->Minv32 = nullptr;   // (allocated below, after the setup temporaries are released)
+    } else if (e == cudaSuccess && c->precision == HDGDG_MIXED) {
         if (sim->Stil_lo) {   // hi part = the FP32 copy of the inner cycles, lo part = the rest
             e = launch_split_f32x2(sim->Stil, sim->Stil32, sim->Stil_lo, (size_t)g.n_edges * 6 * p.NF * p.NF,
                                    sim->stream);
@@ -953,6 +979,33 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
         sim->ops.S = sim->Sphi;
         sim->ops.aux = sim->Saux;
         sim->ops.EG = sim->Seg;
+        if (matrix_free(c)) {   // FP32 copies (the pairs' high parts) for the inner cycles, FP32 M^{-1}
+            const size_t nS = (size_t)g.n_el * Np * Np, nA = 4 * (size_t)g.n_el * Np, nE = 2 * (size_t)g.batch * Np;
+            float *S32 = nullptr, *aux32 = nullptr, *EG32 = nullptr;
+            double* half = nullptr;
+            int* ticket = nullptr;
+            TRY(dalloc(sim, &S32, nS));
+            TRY(dalloc(sim, &aux32, nA));
+            TRY(dalloc(sim, &EG32, nE));
+            TRY(dalloc(sim, &sim->Minv32, (size_t)g.n_edges * p.NF * p.NF));
+            TRY(dalloc(sim, &half, p.nt));
+            TRY(dalloc(sim, &ticket, (size_t)g.n_edges));
+            CU(launch_pair_hi(sim->Sphi, S32, nS, sim->stream));
+            CU(launch_pair_hi(sim->Saux, aux32, nA, sim->stream));
+            CU(launch_pair_hi(sim->Seg, EG32, nE, sim->stream));
+            CU(launch_to_f32(sim->Minv, sim->Minv32, (size_t)g.n_edges * p.NF * p.NF, sim->stream));
+            CU(cudaMemsetAsync(ticket, 0, (size_t)g.n_edges * sizeof(int), sim->stream));
+            sim->mf.S32 = S32;
+            sim->mf.aux32 = aux32;
+            sim->mf.EG32 = EG32;
+            sim->mf.S2 = sim->Sphi;
+            sim->mf.aux2 = sim->Saux;
+            sim->mf.EG2 = sim->Seg;
+            sim->mf.Minv32 = sim->Minv32;
+            sim->mf.tau = sim->tau;
+            sim->mf.half = half;
+            sim->mf.ticket = ticket;
+        }
     } else if (c->local_precision == HDGDG_LOCAL_FP32) {
         const size_t n = (size_t)g.n_el * p.NV * p.NV;
         TRY(dalloc(sim, &sim->Ainv32, n));
@@ -1319,6 +1372,10 @@ hdgdg_status hdgdg_trace_apply(hdgdg_sim* sim, const double* x, double* y) {
     if (sim && explicit_scheme(&sim->cfg)) return fail(sim, HDGDG_EINVAL, "explicit scheme: no implicit stage");
     if (!sim || !x || !y) return fail(sim, HDGDG_EINVAL, "NULL argument to trace_apply");
     TRY(upload3(sim, sim->lam, x, sim->plan.nt));
+    if (matrix_free(&sim->cfg)) {   // the handle's own operator: element by element, FP64-class
+        CU(launch_mf_plain(sim->g, sim->mf, sim->lam, sim->gvec, beta_of(sim), sim->stream));
+        return download(sim, y, sim->gvec, sim->plan.nt);
+    }
     CU(launch_block_diag(sim->g, sim->Srr, sim->lam, sim->xt, sim->stream));          // u = S_rr x
     CU(launch_spmv_pre(sim->g, sim->Stil, sim->Scol, sim->xt, sim->gvec, sim->stream));  // y = S~ u
     return download(sim, y, sim->gvec, sim->plan.nt);

@@ -269,6 +269,28 @@ cudaError_t launch_recover(const Geom& g, const LocalOps& ops, const double* Z, 
 // records the fastest in ops.  No-op for other local arithmetic.
 cudaError_t launch_autotune_local(const Geom& g, LocalOps& ops, double* R1, double* Z, const double* tau_edge,
                                   const double* qhat, double* Q, double* Lst, cudaStream_t s);
+// Matrix-free trace operator (kernels_mf.cu): S x = D x - C A^{-1} B x element by element through
+// the Schur-complement local solve, with the block-Jacobi preconditioner M^{-1} applied first.
+struct MfOps {
+    const float *S32 = nullptr, *aux32 = nullptr, *EG32 = nullptr;   // Schur operators, FP32 (inner cycles)
+    const void *S2 = nullptr, *aux2 = nullptr, *EG2 = nullptr;       // the same as FP32 pairs (float2)
+    const float* Minv32 = nullptr;   // block-Jacobi inverse [edge][col][row], FP32
+    const double* tau = nullptr;     // tau_hat [edge][P]
+    void* half = nullptr;            // scratch: the plus sides' halves of the rows (n_edges * 3P doubles)
+    int* ticket = nullptr;           // one per edge, zero between products
+};
+// y = S M^{-1} x in FP32 (inner Krylov cycles); done as for launch_spmv_pre
+cudaError_t launch_mf_inner(const Geom& g, const MfOps& op, const float* x, float* y, double beta, cudaStream_t s,
+                            const int* done = nullptr);
+// w = rhs - S M^{-1} x in FP64-class FP32-pair arithmetic (the refinement's true residual)
+cudaError_t launch_mf_residual(const Geom& g, const MfOps& op, const double* x, const double* rhs, double* w,
+                               double beta, cudaStream_t s);
+// y = S x (no preconditioner), FP64-class
+cudaError_t launch_mf_plain(const Geom& g, const MfOps& op, const double* x, double* y, double beta, cudaStream_t s);
+// qhat = M^{-1} x~ with the FP32 blocks, FP64-class sums
+cudaError_t launch_mf_back(const Geom& g, const float* Minv32, const double* x, double* y, cudaStream_t s);
+// hi[t] = pairs[t].x for n FP32 pairs (float2)
+cudaError_t launch_pair_hi(const void* pairs, float* hi, size_t n, cudaStream_t s);
 // hi = (float)a, lo = (float)(a - hi): the FP32-pair copy of an FP64 array.
 cudaError_t launch_split_f32x2(const double* a, float* hi, float* lo, size_t n, cudaStream_t s);
 // Tensor-core tile of one shared operator: bytes of the BF16 image, and its build from the

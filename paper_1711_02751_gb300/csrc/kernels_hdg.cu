@@ -16,6 +16,7 @@
 // recovery (eq. recover_volume_unknowns): Q = A^{-1}(R1 - B Qhat).
 #include "compensated.h"
 #include "internal.h"
+#include "schur.h"
 
 namespace hdgdg {
 namespace {
@@ -471,53 +472,6 @@ __global__ void recover_kernel(Geom g, const T* __restrict__ Ainv, const double*
 // of operator data instead of (3 Np)^2; E and G depend only on the instance's time step.  Each
 // output is one dot product: s over 2P + 1 terms, phi over Np, d U and d V over P + 2.
 
-// Arithmetic of these solves.  ArithF64: FP64.  ArithF2: unevaluated FP32 pairs (hi, lo) with
-// the compensated Dot2 sums of compensated.h -- FP64-class results on the FP32 pipes.
-struct ArithF64 {
-    using T = double;
-    struct Acc {
-        double s = 0.0;
-        __device__ __forceinline__ void add(double a, double x) { s = fma(a, x, s); }
-        __device__ __forceinline__ double get() const { return s; }
-    };
-    __device__ __forceinline__ static double from(double v) { return v; }
-    __device__ __forceinline__ static double to(double v) { return v; }
-    __device__ __forceinline__ static double mul(double a, double b) { return a * b; }
-};
-
-struct ArithF2 {
-    using T = float2;
-    struct Acc {
-        Dot2 d;
-        __device__ __forceinline__ void add(float2 a, float2 x) { d.add(a.x, a.y, x.x, x.y); }
-        __device__ __forceinline__ float2 get() const {
-            float2 r;
-            two_sum(d.p, d.c, r.x, r.y);
-            return r;
-        }
-    };
-    __device__ __forceinline__ static float2 from(double v) {
-        float2 r;
-        split(v, r.x, r.y);
-        return r;
-    }
-    __device__ __forceinline__ static double to(float2 v) { return f32_to_f64(v.x) + f32_to_f64(v.y); }
-    // (a_hi + a_lo)(b_hi + b_lo): the exact a_hi b_hi (TwoProduct) plus the cross terms, renormalised
-    __device__ __forceinline__ static float2 mul(float2 a, float2 b) {
-        float p, e;
-        two_prod(a.x, b.x, p, e);
-        e = __fmaf_rn(a.x, b.y, e);
-        e = __fmaf_rn(a.y, b.x, e);
-        float2 r;
-        r.x = __fadd_rn(p, e);
-        r.y = __fsub_rn(e, __fsub_rn(r.x, p));
-        return r;
-    }
-};
-
-template <class A>
-__device__ __forceinline__ void store_from(typename A::T* dst, double v) { *dst = A::from(v); }
-
 // Setup, one thread per (element, node n): row n of the (phi, phi) block of A^{-1} into
 // S [n_el][col m][row n], and aux [n_el][4][Np] = (1/d, -cx, -cy, phi_B) at node n.
 template <int P, class A>
@@ -567,79 +521,6 @@ __global__ void schur_eg_kernel(Geom g, double dta, typename A::T* __restrict__ 
     store_from<A>(&EG[t], -v);
 }
 
-template <int P, int EPB, class A>
-struct SchurSmem {
-    using T = typename A::T;
-    static constexpr int Np = P * P;
-    T EG[EPB][2][Np];   // the element's -E, -G (P x P each, row major)
-    T t[EPB][2][Np];    // d^{-1} x_U, d^{-1} x_V
-    T s[EPB][Np];       // Schur right-hand side
-    T w[EPB][Np];       // phi_B phi
-};
-
-// A^{-1} x for the element of thread (le, n) with x = (x0, xU, xV) at node n (each thread its
-// own node's values); returns phi, U, V at node n.  Every thread of the block calls it (its
-// barriers are block-wide); live marks threads of real elements.
-template <int P, int EPB, class A>
-__device__ __forceinline__ void schur_solve(SchurSmem<P, EPB, A>& sm, const Geom& g, int e, int le, int n,
-                                            bool live, const typename A::T* __restrict__ S,
-                                            const typename A::T* __restrict__ aux,
-                                            const typename A::T* __restrict__ EG, typename A::T x0,
-                                            typename A::T xU, typename A::T xV, typename A::T& phi,
-                                            typename A::T& U, typename A::T& V) {
-    using T = typename A::T;
-    constexpr int Np = P * P;
-    const int i = n % P, j = n / P;
-    const T one = A::from(1.0);
-    T rd{}, ncx{}, ncy{}, pb{};
-    if (live) {
-        const T* ax = aux + (size_t)e * 4 * Np;
-        rd = ax[n];
-        ncx = ax[Np + n];
-        ncy = ax[2 * Np + n];
-        pb = ax[3 * Np + n];
-        const T* eg = EG + (size_t)g.by_el.div(e) * 2 * Np;
-        sm.EG[le][0][n] = eg[n];
-        sm.EG[le][1][n] = eg[Np + n];
-        sm.t[le][0][n] = A::mul(xU, rd);
-        sm.t[le][1][n] = A::mul(xV, rd);
-    }
-    __syncthreads();
-    if (live) {   // s = x_phi - Bx d^{-1} x_U - By d^{-1} x_V
-        typename A::Acc acc;
-        acc.add(one, x0);
-#pragma unroll
-        for (int a = 0; a < P; ++a) {
-            acc.add(sm.EG[le][0][i * P + a], sm.t[le][0][j * P + a]);
-            acc.add(sm.EG[le][0][j * P + a], sm.t[le][1][a * P + i]);
-        }
-        sm.s[le][n] = acc.get();
-    }
-    __syncthreads();
-    if (live) {   // phi = S^{-1} s
-        const T* Sn = S + (size_t)e * Np * Np + n;
-        typename A::Acc acc;
-#pragma unroll 4
-        for (int m = 0; m < Np; ++m) acc.add(Sn[(size_t)m * Np], sm.s[le][m]);
-        phi = acc.get();
-        sm.w[le][n] = A::mul(pb, phi);
-    }
-    __syncthreads();
-    if (live) {   // d U = x_U - Cx phi,  d V = x_V - Cy phi
-        typename A::Acc au, av;
-        au.add(one, xU);
-        au.add(ncx, phi);
-        av.add(one, xV);
-        av.add(ncy, phi);
-#pragma unroll
-        for (int a = 0; a < P; ++a) {
-            au.add(sm.EG[le][1][i * P + a], sm.w[le][j * P + a]);
-            av.add(sm.EG[le][1][j * P + a], sm.w[le][a * P + i]);
-        }
-        U = A::mul(au.get(), rd);
-        V = A::mul(av.get(), rd);
-    }
-}
 
 // Z = A^{-1} R1 through the Schur complement: one thread per (element, node), EPB elements per block.
 template <int P, int EPB, class A>

@@ -22,7 +22,8 @@ from _common import oracle_state, user_state
 pytestmark = pytest.mark.gpu
 hd = pytest.importorskip("paper_1711_02751_gb300.hdgdg")
 
-BENCH_MIXED = dict(precision="mixed", local_precision="f32x2", residual_f32x2=True)
+MIXED = {"assembled_mixed": dict(precision="mixed", local_precision="f32x2", residual_f32x2=True),
+         "bench_mixed": dict(precision="mixed", local_precision="f32x2", trace_operator=1)}
 
 
 def _oracle_run(kind, N, k, steps, solver, **kw):
@@ -55,10 +56,13 @@ def stiff32():
     return _oracle_run("stiff", 32, 3, 4, "lu")
 
 
-@pytest.mark.parametrize("form,bound", [("fp64", 1e-10), ("bench_mixed", 1e-6)])
+FORMS = [("fp64", 1e-10), ("assembled_mixed", 1e-6), ("bench_mixed", 1e-6)]
+
+
+@pytest.mark.parametrize("form,bound", FORMS)
 def test_64x64_four_steps_against_the_oracle(large64, form, bound):
     m, state, dt, qo = large64
-    kw = BENCH_MIXED if form == "bench_mixed" else {}
+    kw = MIXED.get(form, {})
     qa, st = _gpu_run(m, state, dt, 4, **kw)
     rel = [imex.rel_l2(m, qa[c], qo[c]) for c in range(3)]
     print(f"64x64 k=3 {form}: rel L2 eta {rel[0]:.2e} hu {rel[1]:.2e} hv {rel[2]:.2e}, "
@@ -67,14 +71,14 @@ def test_64x64_four_steps_against_the_oracle(large64, form, bound):
     assert max(rel) <= bound
 
 
-@pytest.mark.parametrize("form,bound", [("fp64", 1e-10), ("bench_mixed", 1e-6)])
+@pytest.mark.parametrize("form,bound", FORMS)
 def test_stiff_regime_against_the_oracle(stiff32, form, bound):
     """The stiff variant: gravity Courant number ~14 with the explicit part inside its bound."""
     m, state, dt, qo = stiff32
     h, hu, hv, b = state
     dx_min = m.h / 2 * np.diff(m.xi).min()
     assert np.sqrt(W.G * h).max() * dt / dx_min >= 10.0
-    kw = BENCH_MIXED if form == "bench_mixed" else {}
+    kw = MIXED.get(form, {})
     qa, st = _gpu_run(m, state, dt, 4, **kw)
     rel = [imex.rel_l2(m, qa[c], qo[c]) for c in range(3)]
     print(f"stiff 32x32 k=3 {form}: rel L2 eta {rel[0]:.2e} hu {rel[1]:.2e} hv {rel[2]:.2e}, "
