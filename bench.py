@@ -69,6 +69,8 @@ def _args():
                     help="Gram-Schmidt of the mixed form's inner cycles: 0 twice (CGS2), 1 once")
     ap.add_argument("--residual-f32x2", type=int, default=1, choices=[0, 1],
                     help="mixed form: refinement residual in FP32-pair (FP64-class) arithmetic")
+    ap.add_argument("--trace-operator", type=int, default=1, choices=[0, 1],
+                    help="mixed form's trace operator: 1 matrix-free (element by element), 0 assembled matrix")
     ap.add_argument("--local-dense", type=int, default=0, choices=[0, 1],
                     help="local solves: 0 Schur complement on phi (library default), 1 dense A^-1")
     ap.add_argument("--stiff-steps", type=int, default=10,
@@ -223,11 +225,16 @@ class ClockSampler:
 
 
 # ---- roofline --------------------------------------------------------------------------------
-def _algorithmic(N, k, cls, precision="fp64", dense=False, local="fp64"):
-    """(bytes, flops) one launch group of a kernel class moves / performs."""
+def _algorithmic(N, k, cls, precision="fp64", dense=False, local="fp64", mf=False):
+    """(bytes, flops) one launch group of a kernel class moves / performs.  mf: the mixed form's
+    matrix-free trace operator (per edge its FP32 M^{-1} block, tau and x, y once; per element the
+    FP32 Schur operators; the flops count the M^{-1} products, the local solve and the lift)."""
     P = k + 1
     NF, NV, Np = 3 * P, 3 * P * P, P * P
     n_el, n_edges = N * N, 2 * N * N
+    if cls == "spmv" and mf:   # matrix-free, FP32: M^{-1} blocks, Schur operators, tau, x and y once
+        return (n_edges * (NF * NF * 4 + P * 8 + 2 * NF * 4) + n_el * (Np * Np + 4 * Np) * 4,
+                n_el * (2 * 4 * NF * NF + 2 * (2 * Np * Np + Np * (8 * P + 26)) + 24 * P))
     if cls == "spmv":   # 6 off-diagonal NF x NF blocks + column ids + x and y once
         w = 4 if precision == "mixed" else 8
         return n_edges * (6 * NF * NF * w + 6 * 4 + 2 * NF * w), n_edges * NF * (12 * NF + 1)
@@ -260,19 +267,22 @@ def kernel_source(text, start):
     return text[i:j].encode()
 
 
-def _traffic_for(cls, N, k, precision="fp64"):
-    """dram bytes per launch from a committed ncu summary, if it is for the current kernel source."""
+def _traffic_for(cls, N, k, precision="fp64", mf=False):
+    """dram bytes per launch from a committed ncu summary, if it is for the current kernel source.
+    An entry may name its own source file and region (the matrix-free operator's kernel)."""
     try:
         d = json.load(open(PROFILE_TRAFFIC))
     except Exception:
         return None
-    src = os.path.join(ROOT, "paper_1711_02751_gb300", "csrc", d.get("source", ""))
+    e = d.get("kernels", {}).get(f"{cls}_{precision}" + ("_mf" if mf else ""))
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_1711_02751_gb300", "csrc", e.get("source", d.get("source", "")))
     try:
-        sha = hashlib.sha256(kernel_source(open(src).read(), d.get("region", ""))).hexdigest()[:16]
+        sha = hashlib.sha256(kernel_source(open(src).read(), e.get("region", d.get("region", "")))).hexdigest()[:16]
     except Exception:
         return None
-    e = d.get("kernels", {}).get(f"{cls}_{precision}")
-    if not e or e.get("source_sha") != sha:
+    if e.get("source_sha") != sha:
         return None
     return e["dram_bytes_per_launch"] * (N * N) / e["n_el"]
 
@@ -353,12 +363,13 @@ def _e2e(sim, stream, steps, dist, h, hu, hv):
     return ms, 3 * n * 8
 
 
-def _roofline(N, k, ktimes, precision, fp64_tflops, hbm, dense=False, local="fp64", fp32_peak=(None, 0, 0.0)):
-    dom = max((c for c in ktimes if ktimes[c][1] > 0 and _algorithmic(N, k, c, precision, dense, local)[0]),
+def _roofline(N, k, ktimes, precision, fp64_tflops, hbm, dense=False, local="fp64", fp32_peak=(None, 0, 0.0),
+              mf=False):
+    dom = max((c for c in ktimes if ktimes[c][1] > 0 and _algorithmic(N, k, c, precision, dense, local, mf)[0]),
               key=lambda c: ktimes[c][0])
     tot_ms, n_l = ktimes[dom]
     avg_s = tot_ms / n_l / 1e3
-    byt, flo = _algorithmic(N, k, dom, precision, dense, local)
+    byt, flo = _algorithmic(N, k, dom, precision, dense, local, mf)
     fp32_tflops, n_sm, mhz = fp32_peak
     alu_peak = fp64_tflops if (precision == "fp64" or dom != "spmv" or not fp32_tflops) else fp32_tflops
     t_hbm, t_alu = byt / (hbm * 1e9), flo / (alu_peak * 1e12)
@@ -367,7 +378,7 @@ def _roofline(N, k, ktimes, precision, fp64_tflops, hbm, dense=False, local="fp6
     else:
         roof = {"bound": "alu", "achieved": flo / avg_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = _traffic_for(dom, N, k, precision)
+    roof["traffic"] = _traffic_for(dom, N, k, precision, mf and dom == "spmv")
     roof.update({"kernel": dom, "avg_launch_ms": avg_s * 1e3, "algorithmic_bytes": byt,
                  "algorithmic_flops": flo,
                  "peak_source": ("FP64 FMA rate measured in bench.py by the library's probe (of measured)"
@@ -384,6 +395,13 @@ def _rel_l2_nodal(a, b, B):
         den = float(np.sqrt(np.sum(y * y)))
         out[name] = float(np.sqrt(np.sum((x - y) ** 2))) / den if den > 0 else float(np.sqrt(np.sum(x * x)))
     return out
+
+
+def _trace_operator(args, precision):
+    """Matrix-free trace operator for the mixed form when asked and available (FP32-pair local
+    solves through the Schur complement); the FP64 form always uses the assembled matrix."""
+    ok = precision == "mixed" and args.local == "f32x2" and not args.local_dense
+    return 1 if (args.trace_operator == 1 and ok) else 0
 
 
 def stiff_block(args, stream, dist, world):
@@ -410,7 +428,8 @@ def stiff_block(args, stream, dist, world):
     for precision in args.precisions.split(","):
         sim = hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, stream=stream.cuda_stream, precision=precision,
                      local_precision=args.local if precision == "mixed" else "fp64",
-                     residual_f32x2=bool(args.residual_f32x2) and precision == "mixed")
+                     residual_f32x2=bool(args.residual_f32x2) and precision == "mixed",
+                     trace_operator=_trace_operator(args, precision))
         sim.set_state(h, hu, hv)
         for _ in range(args.warmup):
             sim.step(1)
@@ -698,7 +717,8 @@ def main():
                      local_precision=args.local if precision == "mixed" else "fp64",
                      krylov_guess=args.guess, spmv_kernel=args.spmv_kernel, krylov_ortho=args.ortho,
                      residual_f32x2=bool(args.residual_f32x2) and precision == "mixed",
-                     local_dense=bool(args.local_dense))
+                     local_dense=bool(args.local_dense),
+                     trace_operator=_trace_operator(args, precision))
         sim.set_state(h, hu, hv)
         for _ in range(args.warmup):
             sim.step(1)
@@ -741,10 +761,11 @@ def main():
                       "krylov_iterations_per_stage": r["stats"]["krylov_iterations"] / max(1, 2 * r["stats"]["steps"]),
                       "kernel_breakdown_ms": {c: {"ms": round(v[0], 3), "groups": v[1]} for c, v in r["ktimes"].items()},
                       "roofline": _roofline(N, k, r["ktimes"], p, fp64_tflops, hbm, bool(args.local_dense),
-                                            args.local if p == "mixed" else "fp64", fp32_peak),
+                                            args.local if p == "mixed" else "fp64", fp32_peak,
+                                            bool(_trace_operator(args, p))),
                       "local_roofline": {c: _roofline(N, k, {c: r["ktimes"][c]}, p, fp64_tflops, hbm,
                                                       bool(args.local_dense), args.local if p == "mixed" else "fp64",
-                                                      fp32_peak)
+                                                      fp32_peak, bool(_trace_operator(args, p)))
                                          for c in ("condense", "recover") if r["ktimes"].get(c, (0, 0))[1] > 0},
                       "e2e": f["e2e"], "gpu_launches": r["launches"],
                       "local_tiles": {"condense": r["stats"].get("local_tile_condense", 0),

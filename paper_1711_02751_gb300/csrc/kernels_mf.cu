@@ -38,9 +38,10 @@ namespace {
 
 enum MfMode { kMfInner = 0, kMfResidual = 1, kMfPlain = 2 };
 
+// elements per block: 256 threads, at most 32 elements (the block's shared arrays stay under 48 KB)
 template <int P>
 constexpr int mf_epb() {
-    return 256 / (P * P) > 0 ? 256 / (P * P) : 1;
+    return 256 / (P * P) > 32 ? 32 : (256 / (P * P) > 0 ? 256 / (P * P) : 1);
 }
 
 template <class A>
