@@ -155,6 +155,15 @@ typedef struct {
                             7.2 KB (FP32) or 14.3 KB (FP32 pair) of matrix.  1 needs precision =
                             HDGDG_MIXED with local_precision = HDGDG_LOCAL_F32X2 and local_dense = 0
                             (EINVAL otherwise); the FP64 form always uses the assembled matrix. */
+    int host_steps;      /* 0 (default): each time step of an implicit scheme runs as ONE CUDA graph,
+                            captured at the first step with a given configuration of the solver's
+                            buffers (a handful of them, cached per handle) and replayed: the choice of
+                            each trace solve's start, its restart cycles (a conditional while node)
+                            and their stop tests run on the device, and the host waits once per step.
+                            1: host-driven steps (the host waits for each restart cycle).  Steps run
+                            host-driven anyway while the kernel-class timers are on and for
+                            prescribed time-dependent boundary traces (HDGDG_VORTEX).  Same results
+                            either way, bit for bit. */
 } hdgdg_config;
 
 /* HDGDG_VORTEX: the exact-solution boundary conditions of the paper's moving-vortex test

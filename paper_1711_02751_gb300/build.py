@@ -9,7 +9,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhdgdg.so")
-SOURCES = ["hdgdg_api.cu", "kernels_dg.cu", "kernels_hdg.cu", "kernels_mf.cu", "kernels_krylov.cu", "kernels_spmv.cu", "kernels_tc.cu", "peak.cu",
+SOURCES = ["hdgdg_api.cu", "kernels_dg.cu", "kernels_hdg.cu", "kernels_mf.cu", "kernels_ctl.cu", "kernels_krylov.cu", "kernels_spmv.cu", "kernels_tc.cu", "peak.cu",
            "noalloc.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-gencode", "arch=compute_103a,code=sm_103a",

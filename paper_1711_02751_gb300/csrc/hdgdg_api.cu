@@ -54,6 +54,7 @@ bool valid(const hdgdg_config* c) {
            c->krylov_guess >= -1 && c->krylov_guess <= 6 && (c->spmv_kernel == 0 || c->spmv_kernel == 1) &&
            (c->krylov_ortho == 0 || c->krylov_ortho == 1) && (c->residual_f32x2 == 0 || c->residual_f32x2 == 1) &&
            (c->local_dense == 0 || c->local_dense == 1) && (c->trace_operator == 0 || c->trace_operator == 1) &&
+           (c->host_steps == 0 || c->host_steps == 1) &&
            (c->trace_operator == 0 ||
             (c->precision == HDGDG_MIXED && c->local_precision == HDGDG_LOCAL_F32X2 && !c->local_dense &&
              c->scheme != HDGDG_RK2 && c->scheme != HDGDG_RK3));
@@ -289,6 +290,16 @@ struct CycleGraph {
     std::vector<TimerPair> timers; // event-record nodes of a graph captured with kernel timing on
 };
 
+// One time step captured as a CUDA graph with device-side solve control, keyed by the pointers and
+// history lengths it was captured with (they change from step to step in a fixed cycle).
+struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void*> key;
+    long long launches = 0;    // kernels captured (each restart-cycle body once)
+    long long per_cycle = 0;   // kernels of one restart-cycle body
+    int bodies = 0;            // restart-cycle bodies (one per implicit stage)
+};
+
 struct hdgdg_sim {
     hdgdg_config cfg;
     Plan plan;
@@ -324,6 +335,10 @@ struct hdgdg_sim {
     double *red = nullptr, *mred = nullptr, *dvals = nullptr;
     GmresCtl* ctl = nullptr;
     CycleGraph cycle_graph[4];   // [FP64 form, mixed form] x [timers off, on]
+    std::vector<StepGraph> step_graphs;   // whole-step graphs (host_steps = 0, timers off)
+    SolveCtl* sctl = nullptr;             // device-side control of the solve being replayed
+    StepStats* sstats = nullptr;          // counters of the replayed step
+    cudaStream_t body_stream = nullptr;   // captures the restart-cycle bodies of the conditional nodes
     std::vector<TimerPair>* capture_sink = nullptr;   // timers of the graph being captured
     unsigned* flags = nullptr;
     double* hbuf = nullptr;   // pinned host scratch
@@ -484,6 +499,77 @@ hdgdg_status norm2_to_host(hdgdg_sim* sim, const double* v, double* out) {
 // Lift factor of the local solves: -B qhat = beta tau qhat on the boundary nodes, beta = dt a_ii (2/h)/w_0
 double beta_of(const hdgdg_sim* sim) { return sim->cfg.dt * sim->a_ii * sim->g.two_over_h * sim->g.inv_w0; }
 
+// A restart cycle that cannot halve a true residual already below kStagnation * ||g|| has reached
+// the rounding floor of the FP64 residual: the solve accepts it.
+constexpr double kStagnationFloor = 1e-12;
+// Extrapolation coefficients of the initial guess, order q = 1..6: x_0 = sum_j c[q][j] x_{n-1-j}.
+constexpr double kGuessCoef[7][6] = {{0, 0, 0, 0, 0, 0},     {1, 0, 0, 0, 0, 0},     {2, -1, 0, 0, 0, 0},
+                                     {3, -3, 1, 0, 0, 0},    {4, -6, 4, -1, 0, 0},   {5, -10, 10, -5, 1, 0},
+                                     {6, -15, 20, -15, 6, -1}};
+inline double* dv_exact(hdgdg_sim* s) { return s->dvals + 3 * (s->plan.m + 2) + 15; }
+
+// One restart cycle on stream st: m Arnoldi steps (the ones after the cycle's stop return at
+// once), the correction, the true residual and its squared norm in dv_nrm; readback: also copy
+// the norm and the control flags to the pinned host buffer (the host-driven loop reads them).
+template <typename T>
+cudaError_t cycle_enqueue(hdgdg_sim* sim, const double* g, cudaStream_t st, bool readback) {
+    constexpr bool kMixed = sizeof(T) == sizeof(float);
+    const size_t n = sim->plan.nt;
+    const int m = sim->plan.m;
+    T* V = nullptr;
+    T* w = nullptr;
+    const T* St = nullptr;
+    if constexpr (kMixed) { V = sim->V32; w = sim->w32; St = sim->Stil32; }
+    else { V = sim->V; w = sim->w; St = sim->Stil; }
+    GmresCtl* ctl = sim->ctl;
+    const int* done = &ctl->done;
+    cudaError_t e = launch_gmres_cycle_init(ctl, dv_nrm(sim), st);
+    if (e == cudaSuccess) e = launch_scale_by_rnorm(sim->w, dv_nrm(sim), V, n, st);
+    for (int j = 0; j < m && e == cudaSuccess; ++j) {
+        const T* Vj = V + (size_t)j * n;
+        {
+            TimedGroup tg(sim, HDGDG_KT_SPMV, j);
+            if constexpr (kMixed) {
+                if (matrix_free(&sim->cfg)) e = launch_mf_inner(sim->g, sim->mf, Vj, w, beta_of(sim), st, done);
+                else
+                    e = launch_spmv_pre(sim->g, St, sim->Scol, Vj, w, st, done,
+                                        sim->cfg.spmv_kernel == 1 ? spmv_error(sim) : nullptr);
+            } else
+                e = launch_spmv_pre(sim->g, St, sim->Scol, Vj, w, st, done);
+        }
+        TimedGroup tg(sim, HDGDG_KT_ORTHO, j);
+        if (e == cudaSuccess) e = launch_multidot(V, n, j + 1, w, n, sim->red, dv_h1(sim), st, done);
+        if (e == cudaSuccess)   // second pass, norm, Hessenberg column j and stop test
+            e = launch_cgs2_tail(V, n, j + 1, dv_h1(sim), w, n, sim->red, dv_h2(sim), dv_nrm(sim) + 2,
+                                 dv_nrm(sim) + 1, V + (size_t)(j + 1) * n, ctl, j, m,
+                                 !(kMixed && sim->cfg.krylov_ortho == 1), st, done);
+    }
+    TimedGroup tg_end(sim, HDGDG_KT_RESIDUAL);
+    if (e == cudaSuccess) e = launch_gmres_update(V, n, ctl, sim->xt, n, st);
+    // the true residual w = g - S~ x~ that ends the cycle, and ||w||^2
+    if (kMixed && matrix_free(&sim->cfg)) {   // matrix-free in FP32-pair arithmetic, then the norm
+        if (e == cudaSuccess) e = launch_mf_residual(sim->g, sim->mf, sim->xt, g, sim->w, beta_of(sim), st);
+        if (e == cudaSuccess) e = launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st);
+    } else if (kMixed && sim->Stil_lo) {   // one fused FP32-pair pass
+        if (e == cudaSuccess)
+            e = launch_residual_norm_x2(sim->g, sim->Stil32, sim->Stil_lo, sim->Scol, sim->xt, g, sim->w,
+                                        sim->red, dv_nrm(sim), st);
+    } else {
+        if (e == cudaSuccess) e = launch_spmv_pre(sim->g, sim->Stil, sim->Scol, sim->xt, sim->w, st);
+        CombineTerms t{};
+        t.n = 1;
+        t.X[0] = sim->w;
+        t.c[0] = -1.0;
+        if (e == cudaSuccess) e = launch_combine(n, g, t, sim->w, nullptr, st);
+        if (e == cudaSuccess) e = launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st);
+    }
+    if (readback && e == cudaSuccess)
+        e = cudaMemcpyAsync(sim->hbuf, dv_nrm(sim), sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (readback && e == cudaSuccess)
+        e = cudaMemcpyAsync(sim->hbuf + 1, &ctl->done, 5 * sizeof(int), cudaMemcpyDeviceToHost, st);
+    return e;
+}
+
 // Right-preconditioned GMRES(m) on S~ x~ = g with classical Gram-Schmidt applied twice, then
 // qhat = M^{-1} x~.  The Givens rotations, the residual estimate and the stop test run on the
 // device (GmresCtl), so a whole restart cycle is queued at once and the host waits once per
@@ -496,29 +582,18 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
                          int stage) {
     constexpr bool kMixed = sizeof(T) == sizeof(float);
     const size_t n = sim->plan.nt;
-    const int m = sim->plan.m;
     const double rtol = sim->cfg.krylov_rtol > 0.0 ? sim->cfg.krylov_rtol : (kMixed ? 1e-9 : 1e-15);
     const int maxit = sim->cfg.krylov_maxit > 0 ? sim->cfg.krylov_maxit : 2000;
     // Mixed form: an FP32 cycle stops once it has reduced its starting residual 1e6 times.
     const double inner_rel = kMixed ? 1e-6 : 0.0;
-    // A restart cycle that cannot halve a true residual already below kStagnation * ||g|| has
-    // reached the rounding floor of the FP64 residual: accept it.
-    constexpr double kStagnation = 1e-12;
+    constexpr double kStagnation = kStagnationFloor;
     cudaStream_t st = sim->stream;
-    T* V = nullptr;
-    T* w = nullptr;
-    const T* St = nullptr;
-    if constexpr (kMixed) { V = sim->V32; w = sim->w32; St = sim->Stil32; }
-    else { V = sim->V; w = sim->w; St = sim->Stil; }
     GmresCtl* ctl = sim->ctl;
-    const int* done = &ctl->done;
     *iters = 0;
     // Initial guess: the extrapolation in time of the stage's previous solutions, at the order
     // (or zero) whose residual is smallest.  One pass over g and the stored products S~ x~_{n-j}
     // gives ||g||^2 and every candidate's residual norm; no matrix product is needed.
-    static const double coef[7][6] = {{0, 0, 0, 0, 0, 0},     {1, 0, 0, 0, 0, 0},     {2, -1, 0, 0, 0, 0},
-                                      {3, -3, 1, 0, 0, 0},    {4, -6, 4, -1, 0, 0},   {5, -10, 10, -5, 1, 0},
-                                      {6, -15, 20, -15, 6, -1}};
+    const auto& coef = kGuessCoef;
     const int avail = stage >= 0 ? std::min(guess_order(&sim->cfg), sim->n_hist[stage]) : 0;
     double cand[7] = {0, 0, 0, 0, 0, 0, 0};
     if (avail > 0) {
@@ -584,53 +659,7 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
     // One restart cycle: m Arnoldi steps (the ones after the cycle's stop return at once), the
     // correction, the FP64 true residual and its read-back.  Without kernel timing the cycle is
     // captured once per handle and form as a CUDA graph and replayed.
-    auto enqueue_cycle = [&]() -> cudaError_t {
-        cudaError_t e = launch_gmres_cycle_init(ctl, dv_nrm(sim), st);
-        if (e == cudaSuccess) e = launch_scale_by_rnorm(sim->w, dv_nrm(sim), V, n, st);
-        for (int j = 0; j < m && e == cudaSuccess; ++j) {
-            const T* Vj = V + (size_t)j * n;
-            {
-                TimedGroup tg(sim, HDGDG_KT_SPMV, j);
-                if constexpr (kMixed) {
-                    if (matrix_free(&sim->cfg)) e = launch_mf_inner(sim->g, sim->mf, Vj, w, beta_of(sim), st, done);
-                    else
-                        e = launch_spmv_pre(sim->g, St, sim->Scol, Vj, w, st, done,
-                                            sim->cfg.spmv_kernel == 1 ? spmv_error(sim) : nullptr);
-                } else
-                    e = launch_spmv_pre(sim->g, St, sim->Scol, Vj, w, st, done);
-            }
-            TimedGroup tg(sim, HDGDG_KT_ORTHO, j);
-            if (e == cudaSuccess) e = launch_multidot(V, n, j + 1, w, n, sim->red, dv_h1(sim), st, done);
-            if (e == cudaSuccess)   // second pass, norm, Hessenberg column j and stop test
-                e = launch_cgs2_tail(V, n, j + 1, dv_h1(sim), w, n, sim->red, dv_h2(sim), dv_nrm(sim) + 2,
-                                     dv_nrm(sim) + 1, V + (size_t)(j + 1) * n, ctl, j, m,
-                                     !(kMixed && sim->cfg.krylov_ortho == 1), st, done);
-        }
-        TimedGroup tg_end(sim, HDGDG_KT_RESIDUAL);
-        if (e == cudaSuccess) e = launch_gmres_update(V, n, ctl, sim->xt, n, st);
-        // the true residual w = g - S~ x~ that ends the cycle, and ||w||^2
-        if (kMixed && matrix_free(&sim->cfg)) {   // matrix-free in FP32-pair arithmetic, then the norm
-            if (e == cudaSuccess) e = launch_mf_residual(sim->g, sim->mf, sim->xt, g, sim->w, beta_of(sim), st);
-            if (e == cudaSuccess) e = launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st);
-        } else if (kMixed && sim->Stil_lo) {   // one fused FP32-pair pass
-            if (e == cudaSuccess)
-                e = launch_residual_norm_x2(sim->g, sim->Stil32, sim->Stil_lo, sim->Scol, sim->xt, g, sim->w,
-                                            sim->red, dv_nrm(sim), st);
-        } else {
-            if (e == cudaSuccess) e = launch_spmv_pre(sim->g, sim->Stil, sim->Scol, sim->xt, sim->w, st);
-            CombineTerms t{};
-            t.n = 1;
-            t.X[0] = sim->w;
-            t.c[0] = -1.0;
-            if (e == cudaSuccess) e = launch_combine(n, g, t, sim->w, nullptr, st);
-            if (e == cudaSuccess) e = launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st);
-        }
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(sim->hbuf, dv_nrm(sim), sizeof(double), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(sim->hbuf + 1, &ctl->done, 5 * sizeof(int), cudaMemcpyDeviceToHost, st);
-        return e;
-    };
+    auto enqueue_cycle = [&]() -> cudaError_t { return cycle_enqueue<T>(sim, g, st, true); };
     // one graph per form, captured with or without the kernel-class timers (event-record nodes)
     CycleGraph& cg = sim->cycle_graph[(kMixed ? 1 : 0) + (sim->timing ? 2 : 0)];
     while (rnorm > tol) {
@@ -738,6 +767,244 @@ hdgdg_status stage_solve_dev(hdgdg_sim* sim, const double* R1, double* Q, double
     return HDGDG_OK;
 }
 
+// ---- whole-step graphs ------------------------------------------------------------------------
+// The trace solve of gmres_solve with every host decision moved to the device (kernels_ctl.cu),
+// enqueued on st while a whole time step is being captured: the candidate norms, the choice of the
+// start, the restart cycles inside a conditional while node (body captured on the handle's body
+// stream), the counters, the back-transformation and the history copy into the slot that becomes
+// the newest when the host rotates the history after the step.
+template <typename T>
+cudaError_t solve_enqueue_graph(hdgdg_sim* sim, const double* g, double* qhat, int stage, cudaStream_t st,
+                                StepGraph& sg) {
+    constexpr bool kMixed = sizeof(T) == sizeof(float);
+    const size_t n = sim->plan.nt;
+    const double rtol = sim->cfg.krylov_rtol > 0.0 ? sim->cfg.krylov_rtol : (kMixed ? 1e-9 : 1e-15);
+    const int maxit = sim->cfg.krylov_maxit > 0 ? sim->cfg.krylov_maxit : 2000;
+    const double inner_rel = kMixed ? 1e-6 : 0.0;
+    const int order = guess_order(&sim->cfg);
+    const int avail = stage >= 0 ? std::min(order, sim->n_hist[stage]) : 0;
+    cudaError_t e = cudaSuccess;
+    if (avail > 0) {
+        GuessTerms gt{};
+        gt.nq = avail;
+        for (int j = 0; j < avail; ++j) gt.y[j] = sim->yhist[stage][j];
+        std::memcpy(gt.c, kGuessCoef, sizeof(kGuessCoef));
+        e = launch_guess_norms(n, g, gt, sim->red, dv_guess(sim), st, kMixed);
+    } else {
+        e = launch_multidot(g, 0, 1, g, n, sim->red, dv_guess(sim), st);
+    }
+    if (e == cudaSuccess)
+        e = launch_solve_begin(dv_guess(sim), avail, rtol, inner_rel, maxit, sim->ctl, sim->sctl, sim->sstats,
+                               dv_nrm(sim), st);
+    GuessHistory hist{};
+    for (int j = 0; j < avail; ++j) {
+        hist.x[j] = sim->xhist[stage][j];
+        hist.y[j] = sim->yhist[stage][j];
+    }
+    std::memcpy(hist.c, kGuessCoef, sizeof(kGuessCoef));
+    if (e == cudaSuccess) e = launch_guess_apply(n, g, hist, sim->sctl, sim->xt, sim->w, st);
+    if (kMixed && e == cudaSuccess)   // the exact start norm of an extrapolated start
+        e = launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_exact(sim), st);
+    // restart cycles while the true residual is above the tolerance
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t graph = nullptr;
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, nullptr, nullptr, nullptr);
+    cudaGraphConditionalHandle loop = 0;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&loop, graph, 0, 0);
+    if (e == cudaSuccess)
+        e = launch_loop_begin(dv_nrm(sim), dv_exact(sim), kMixed ? 1 : 0, sim->sctl, sim->sstats, loop, st);
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, nullptr, &ndeps);
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = loop;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &np);
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(sim->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const long long l0 = launches_total();
+            cudaError_t eb = cycle_enqueue<T>(sim, g, sim->body_stream, false);
+            if (eb == cudaSuccess)
+                eb = launch_cycle_end(dv_nrm(sim), sim->ctl, sim->sctl, sim->sstats, kStagnationFloor, loop,
+                                      sim->body_stream);
+            sg.per_cycle = launches_total() - l0;
+            sg.bodies += 1;
+            cudaGraph_t captured = nullptr;
+            const cudaError_t ee = cudaStreamEndCapture(sim->body_stream, &captured);
+            e = eb != cudaSuccess ? eb : ee;
+        }
+    }
+    if (e == cudaSuccess) e = launch_solve_end(sim->ctl, sim->sctl, sim->sstats, st);
+    if (e == cudaSuccess) {
+        if (kMixed && matrix_free(&sim->cfg)) e = launch_mf_back(sim->g, sim->Minv32, sim->xt, qhat, st);
+        else e = launch_block_diag(sim->g, sim->Minv, sim->xt, qhat, st, sim->minv_pairs);
+    }
+    if (e == cudaSuccess && stage >= 0 && order > 0) {   // x~ and S~ x~ = g - r into the slot that becomes newest
+        double* ox = sim->xhist[stage][order - 1];
+        double* oy = sim->yhist[stage][order - 1];
+        e = cudaMemcpyAsync(ox, sim->xt, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        CombineTerms r{};
+        r.n = 1;
+        r.X[0] = sim->w;
+        r.c[0] = -1.0;
+        if (e == cudaSuccess) e = launch_combine(n, g, r, oy, nullptr, st);
+    }
+    return e;
+}
+
+// One implicit time step (Algorithm 1) enqueued for capture: the host-driven step's launches,
+// with the trace solves of solve_enqueue_graph and no host waits; the step's flags and counters
+// are copied to the pinned host buffer at its end.
+cudaError_t step_enqueue_graph(hdgdg_sim* sim, cudaStream_t st, StepGraph& sg) {
+    const size_t n3 = 3 * sim->plan.n;
+    cudaError_t e = cudaMemsetAsync(sim->sstats, 0, sizeof(StepStats), st);
+    for (int i = 0; i < sim->s && e == cudaSuccess; ++i) {
+        const double* Qi = sim->q;
+        if (sim->At[i][i] != 0.0) {
+            CombineTerms t{};
+            for (int j = 0; j < i; ++j) {
+                if (sim->A[i][j] != 0.0 && !sim->cfg.linear_only) { t.X[t.n] = sim->NLs[j]; t.c[t.n++] = sim->A[i][j]; }
+                if (sim->At[i][j] != 0.0) { t.X[t.n] = sim->Ls[j]; t.c[t.n++] = sim->At[i][j]; }
+            }
+            e = launch_combine(n3, sim->q, t, sim->R1, nullptr, st);
+            if (e == cudaSuccess)
+                e = launch_condense(sim->g, sim->ops, sim->R1, sim->phiB, sim->tau, sim->Z, sim->gvec, st, 0.0);
+            if (e == cudaSuccess) {
+                if (sim->cfg.precision == HDGDG_MIXED) e = solve_enqueue_graph<float>(sim, sim->gvec, sim->lam, i, st, sg);
+                else e = solve_enqueue_graph<double>(sim, sim->gvec, sim->lam, i, st, sg);
+            }
+            if (e == cudaSuccess)
+                e = launch_recover(sim->g, sim->ops, sim->Z, sim->R1, sim->tau, sim->lam, beta_of(sim),
+                                   1.0 / sim->a_ii, sim->Qs, sim->Ls[i], st);
+            Qi = sim->Qs;
+        }
+        if (!sim->cfg.linear_only && e == cudaSuccess) {
+            if (sim->cfg.precision == HDGDG_MIXED)
+                e = launch_dg_nl_f32(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st, 0.0);
+            else
+                e = launch_dg_nl(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st, 0.0);
+        }
+    }
+    CombineTerms t{};
+    for (int i = 0; i < sim->s; ++i) {
+        if (sim->b[i] != 0.0 && !sim->cfg.linear_only) { t.X[t.n] = sim->NLs[i]; t.c[t.n++] = sim->b[i]; }
+        if (sim->bt[i] != 0.0) { t.X[t.n] = sim->Ls[i]; t.c[t.n++] = sim->bt[i]; }
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(sim->flags, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = launch_combine(n3, sim->q, t, sim->q_new, sim->flags, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sim->hbuf, sim->flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sim->hbuf + 4, sim->sstats, sizeof(StepStats), cudaMemcpyDeviceToHost, st);
+    return e;
+}
+
+std::vector<const void*> step_key(const hdgdg_sim* sim) {
+    std::vector<const void*> k{sim->q, sim->q_new};
+    const int order = guess_order(&sim->cfg);
+    for (int i = 0; i < sim->s; ++i) {
+        if (sim->At[i][i] == 0.0) continue;
+        k.push_back(reinterpret_cast<const void*>((uintptr_t)std::min(order, sim->n_hist[i])));
+        for (int j = 0; j < order; ++j) {
+            k.push_back(sim->xhist[i][j]);
+            k.push_back(sim->yhist[i][j]);
+        }
+    }
+    return k;
+}
+
+void drop_step_graphs(hdgdg_sim* sim) {
+    for (auto& sg : sim->step_graphs)
+        if (sg.exec) cudaGraphExecDestroy(sg.exec);
+    sim->step_graphs.clear();
+}
+
+// Whole-step graphs serve implicit schemes whose boundary data do not depend on time, with the
+// kernel-class timers off (their event records cannot sit inside a conditional node's body).
+bool use_step_graph(const hdgdg_sim* sim) {
+    return !sim->cfg.host_steps && !sim->timing && !explicit_scheme(&sim->cfg) && !sim->g.dirichlet &&
+           sim->body_stream != nullptr;
+}
+
+hdgdg_status one_step_graph(hdgdg_sim* sim) {
+    NvtxRange nv("time_step_graph");
+    cudaStream_t st = sim->stream;
+    const std::vector<const void*> key = step_key(sim);
+    StepGraph* sg = nullptr;
+    for (auto& c : sim->step_graphs)
+        if (c.key == key) sg = &c;
+    if (!sg) {
+        if (sim->step_graphs.size() >= 24) drop_step_graphs(sim);   // bounded cache
+        StepGraph fresh;
+        fresh.key = key;
+        const long long l0 = launches_total();
+        CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t e = step_enqueue_graph(sim, st, fresh);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+        fresh.launches = launches_total() - l0;
+        count_launches((int)-fresh.launches);   // counted again at every replay
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return fail(sim, HDGDG_ECUDA, "capturing the time step failed: %s",
+                        cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        const cudaError_t e3 = cudaGraphInstantiate(&fresh.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e3 != cudaSuccess) return fail(sim, HDGDG_ECUDA, "time-step graph: %s", cudaGetErrorString(e3));
+        sim->step_graphs.push_back(std::move(fresh));
+        sg = &sim->step_graphs.back();
+    }
+    CU(cudaGraphLaunch(sg->exec, st));
+    CU(cudaStreamSynchronize(st));
+    unsigned flag[4];
+    StepStats ss;
+    std::memcpy(flag, sim->hbuf, sizeof(flag));
+    std::memcpy(&ss, sim->hbuf + 4, sizeof(ss));
+    count_launches((int)(sg->launches + (long long)(ss.cycles - sg->bodies) * sg->per_cycle));
+    sim->stats.krylov_iterations += ss.its;
+    sim->stats.last_krylov_iterations = ss.last_its;
+    sim->stats.last_rel_residual = ss.last_rel;
+    sim->stats.last_guess_order = ss.last_guess;
+    const bool bad = flag[0] || flag[2] || flag[3] || ss.nonfinite || ss.notconv;
+    if (bad) {   // the history slots may hold this step's partial solves: start the next solves afresh
+        for (int i = 0; i < sim->s; ++i) sim->n_hist[i] = 0;
+        if (flag[2]) return fail(sim, HDGDG_ECUDA, "a bounded wait of the tensor-core local kernel ran out (%u)", flag[2]);
+        if (flag[3]) return fail(sim, HDGDG_ECUDA, "a bounded wait of the pipelined SpMV ran out (%u)", flag[3]);
+        if (ss.nonfinite) return fail(sim, HDGDG_ENONFINITE, "non-finite trace right-hand side or GMRES residual");
+        if (ss.notconv) {
+            sim->stats.last_krylov_iterations = ss.notconv_its;
+            sim->stats.last_rel_residual = ss.notconv_rel;
+            return fail(sim, HDGDG_ENOTCONVERGED, "GMRES: relative residual %.3e above the tolerance after %d iterations",
+                        ss.notconv_rel, ss.notconv_its);
+        }
+        return fail(sim, HDGDG_ENONFINITE, "step %lld produced a non-finite state", sim->stats.steps + 1);
+    }
+    const int order = guess_order(&sim->cfg);
+    for (int i = 0; i < sim->s && order > 0; ++i) {   // the slot written last becomes the newest
+        if (sim->At[i][i] == 0.0) continue;
+        double* ox = sim->xhist[i][order - 1];
+        double* oy = sim->yhist[i][order - 1];
+        for (int j = order - 1; j > 0; --j) {
+            sim->xhist[i][j] = sim->xhist[i][j - 1];
+            sim->yhist[i][j] = sim->yhist[i][j - 1];
+        }
+        sim->xhist[i][0] = ox;
+        sim->yhist[i][0] = oy;
+        sim->n_hist[i] = std::min(sim->n_hist[i] + 1, order);
+    }
+    std::swap(sim->q, sim->q_new);
+    sim->stats.steps += 1;
+    sim->t += sim->cfg.dt;
+    return HDGDG_OK;
+}
+
 // Explicit SSP Runge-Kutta on the whole DG residual (the paper's RK2 DG / RK3 DG), with the
 // stage increments K_i = dt M^{-1} R(q_i):
 //   RK2 (Heun):        q1 = q + K1;                 q' = q + K1/2 + K2/2
@@ -784,6 +1051,7 @@ hdgdg_status explicit_step(hdgdg_sim* sim) {
 }
 
 hdgdg_status one_step(hdgdg_sim* sim) {
+    if (use_step_graph(sim)) return one_step_graph(sim);
     NvtxRange nv("time_step");
     if (explicit_scheme(&sim->cfg)) return explicit_step(sim);
     const size_t n3 = 3 * sim->plan.n;
@@ -924,6 +1192,9 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
     TRY(dalloc(sim, &sim->dvals, 4 * (size_t)(p.m + 2) + 16));
     TRY(dalloc(sim, &sim->flags, 16));
     TRY(dalloc(sim, &sim->ctl, 1));
+    TRY(dalloc(sim, &sim->sctl, 1));
+    TRY(dalloc(sim, &sim->sstats, 1));
+    if (!c->host_steps) CU(cudaStreamCreateWithFlags(&sim->body_stream, cudaStreamNonBlocking));
     CU(cudaMallocHost(&sim->hbuf, (4 * (size_t)(p.m + 2) + 16) * sizeof(double)));
     for (int i = 0; i < p.s; ++i) {
         CU(cudaMemsetAsync(sim->NLs[i], 0, 3 * p.n * sizeof(double), sim->stream));
@@ -1121,6 +1392,8 @@ void hdgdg_destroy(hdgdg_sim* sim) {
     if (sim->stream) cudaStreamSynchronize(sim->stream);
     flush_timers(sim);
     for (auto& cg : sim->cycle_graph) drop_graph(sim, cg);
+    drop_step_graphs(sim);
+    if (sim->body_stream) cudaStreamDestroy(sim->body_stream);
     for (cudaEvent_t e : sim->ev_pool) cudaEventDestroy(e);
     for (void* p : sim->allocs) cudaFree(p);
     if (sim->hbuf) cudaFreeHost(sim->hbuf);

@@ -374,6 +374,35 @@ cudaError_t launch_cgs2_tail(const float* V, size_t ldv, int nv, const double* h
                              GmresCtl* ctl, int j, int m, bool twice, cudaStream_t s, const int* done = nullptr);
 
 
+// Whole-step graphs (kernels_ctl.cu): the trace solve's decisions taken on the device.
+struct SolveCtl {
+    double bnorm, tol, rnorm;
+    int guess;    // extrapolation order the solve started from (0: zero)
+    int active;   // 0 when g = 0 or not finite (nothing to solve)
+};
+struct StepStats {            // counters of one replayed step, read by the host after it
+    long long its;            // GMRES iterations over the step's solves
+    int last_its, last_guess, cycles;
+    double last_rel;
+    unsigned nonfinite, notconv;
+    int notconv_its;
+    double notconv_rel;
+};
+struct GuessHistory {         // the stage's stored solutions x~ and products S~x~, newest first
+    const double* x[6];
+    const double* y[6];
+    double c[7][6];           // extrapolation coefficients of each order
+};
+cudaError_t launch_solve_begin(const double* cand, int avail, double rtol, double inner_rel, int maxit, GmresCtl* ctl,
+                               SolveCtl* sc, StepStats* ss, double* nrm2, cudaStream_t s);
+cudaError_t launch_guess_apply(size_t n, const double* g, const GuessHistory& h, const SolveCtl* sc, double* xt,
+                               double* w, cudaStream_t s);
+cudaError_t launch_loop_begin(double* nrm2, const double* nrm_exact, int use_exact, SolveCtl* sc, StepStats* ss,
+                              cudaGraphConditionalHandle loop, cudaStream_t s);
+cudaError_t launch_cycle_end(const double* nrm2, const GmresCtl* ctl, SolveCtl* sc, StepStats* ss, double stagnation,
+                             cudaGraphConditionalHandle loop, cudaStream_t s);
+cudaError_t launch_solve_end(const GmresCtl* ctl, const SolveCtl* sc, StepStats* ss, cudaStream_t s);
+
 cudaError_t launch_gmres_solve_init(GmresCtl* c, double tol_abs, double inner_rel, int maxit, cudaStream_t s);
 cudaError_t launch_gmres_cycle_init(GmresCtl* c, const double* nrm2, cudaStream_t s);
 

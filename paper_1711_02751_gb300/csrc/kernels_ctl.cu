@@ -1,0 +1,162 @@
+// Device-side control of the trace solve inside a whole-step CUDA graph.
+//
+// A time step of Algorithm 1 is captured once per pointer configuration and replayed as ONE
+// graph: each implicit stage's trace solve chooses its initial guess, runs its restart cycles
+// inside a conditional (while) node and records its counters without returning to the host.
+// The decisions the host driver takes between restart cycles -- the extrapolation order whose
+// residual is smallest, the stop tests on the true residual, the iteration cap -- are taken here
+// by one-thread kernels, in the same order and with the same arithmetic, so a replayed step
+// gives the same numbers as the host-driven one.
+#include "internal.h"
+
+namespace hdgdg {
+namespace {
+
+// Begin a solve: ||g||^2 = cand[0], the candidates' squared residual norms cand[1..avail];
+// chooses the start (zero or the extrapolation order with the smallest finite residual), sets the
+// absolute tolerance and the GMRES control block, and writes the start's squared residual norm.
+__global__ void solve_begin_kernel(const double* __restrict__ cand, int avail, double rtol, double inner_rel,
+                                   int maxit, GmresCtl* ctl, SolveCtl* sc, StepStats* ss, double* nrm2) {
+    const double bn2 = cand[0];
+    sc->active = 0;
+    sc->guess = 0;
+    sc->bnorm = 0.0;
+    sc->tol = 0.0;
+    ctl->tol_abs = 0.0;
+    ctl->inner_rel = inner_rel;
+    ctl->maxit = maxit;
+    ctl->total = 0;
+    ctl->status = 0;
+    if (!isfinite(bn2)) {
+        ss->nonfinite = 1u;
+        *nrm2 = 0.0;
+        return;
+    }
+    if (bn2 == 0.0) {   // g = 0: qhat = 0
+        *nrm2 = 0.0;
+        return;
+    }
+    int guess = 0;
+    for (int q = 1; q <= avail; ++q)
+        if (isfinite(cand[q]) && cand[q] < cand[guess]) guess = q;
+    sc->active = 1;
+    sc->guess = guess;
+    sc->bnorm = sqrt(bn2);
+    sc->tol = rtol * sc->bnorm;
+    ctl->tol_abs = sc->tol;
+    ss->last_guess = guess;
+    *nrm2 = cand[guess];
+}
+
+// x~ = x_{n-1} + sum_j (c_qj - [j = 0]) x_{n-1-j} and w = g - sum_j c_qj S~x_{n-1-j} for the chosen
+// order q (the host driver's two combinations, term for term); q = 0: x~ = 0, w = g.
+__global__ void guess_apply_kernel(size_t n, const double* __restrict__ g, GuessHistory h,
+                                   const SolveCtl* __restrict__ sc, double* __restrict__ xt, double* __restrict__ w) {
+    const int q = sc->active ? sc->guess : 0;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        if (q == 0) {
+            xt[idx] = 0.0;
+            w[idx] = g[idx];
+            continue;
+        }
+        double ax = h.x[0][idx];
+        for (int j = 0; j < q; ++j) ax += (h.c[q][j] - (j == 0 ? 1.0 : 0.0)) * h.x[j][idx];
+        double aw = g[idx];
+        for (int j = 0; j < q; ++j) aw += (-h.c[q][j]) * h.y[j][idx];
+        xt[idx] = ax;
+        w[idx] = aw;
+    }
+}
+
+// The start of the restart loop: the start residual's squared norm is *nrm_exact when the
+// mixed form recomputed it exactly for an extrapolated start, else *nrm2 (the candidate's);
+// the loop runs while the residual is above the tolerance.
+__global__ void loop_begin_kernel(double* nrm2, const double* __restrict__ nrm_exact, int use_exact,
+                                  SolveCtl* sc, StepStats* ss, cudaGraphConditionalHandle loop) {
+    if (sc->active && use_exact && sc->guess > 0) *nrm2 = *nrm_exact;
+    const double rn = sqrt(*nrm2);
+    sc->rnorm = rn;
+    unsigned go = sc->active && rn > sc->tol ? 1u : 0u;
+    if (sc->active && !isfinite(rn)) {
+        ss->nonfinite = 1u;
+        go = 0u;
+    }
+    cudaGraphSetConditional(loop, go);
+}
+
+// End of a restart cycle: the host driver's tests on the cycle's true residual, in its order.
+__global__ void cycle_end_kernel(const double* __restrict__ nrm2, const GmresCtl* __restrict__ ctl, SolveCtl* sc,
+                                 StepStats* ss, double stagnation, cudaGraphConditionalHandle loop) {
+    ss->cycles += 1;
+    unsigned go = 1u;
+    const double rn = sqrt(*nrm2);
+    const double prev = sc->rnorm;
+    sc->rnorm = rn;
+    if (ctl->status != 0 || !isfinite(rn)) {
+        ss->nonfinite = 1u;
+        go = 0u;
+    } else if (rn <= sc->tol) {
+        go = 0u;
+    } else if (rn <= stagnation * sc->bnorm && rn > 0.5 * prev) {
+        go = 0u;
+    } else if (ctl->total >= ctl->maxit) {
+        ss->notconv = 1u;
+        ss->notconv_its = ctl->total;
+        ss->notconv_rel = rn / sc->bnorm;
+        go = 0u;
+    }
+    cudaGraphSetConditional(loop, go);
+}
+
+// Counters of the finished solve.
+__global__ void solve_end_kernel(const GmresCtl* __restrict__ ctl, const SolveCtl* __restrict__ sc, StepStats* ss) {
+    const int its = sc->active ? ctl->total : 0;
+    ss->its += its;
+    ss->last_its = its;
+    ss->last_rel = sc->active && sc->bnorm > 0.0 ? sc->rnorm / sc->bnorm : 0.0;
+}
+
+int grid_of(size_t n) {
+    size_t b = (n + 255) / 256;
+    if (b > 152 * 8) b = 152 * 8;
+    return b > 0 ? (int)b : 1;
+}
+
+}  // namespace
+
+cudaError_t launch_solve_begin(const double* cand, int avail, double rtol, double inner_rel, int maxit, GmresCtl* ctl,
+                               SolveCtl* sc, StepStats* ss, double* nrm2, cudaStream_t s) {
+    solve_begin_kernel<<<1, 1, 0, s>>>(cand, avail, rtol, inner_rel, maxit, ctl, sc, ss, nrm2);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_guess_apply(size_t n, const double* g, const GuessHistory& h, const SolveCtl* sc, double* xt,
+                               double* w, cudaStream_t s) {
+    guess_apply_kernel<<<grid_of(n), 256, 0, s>>>(n, g, h, sc, xt, w);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loop_begin(double* nrm2, const double* nrm_exact, int use_exact, SolveCtl* sc, StepStats* ss,
+                              cudaGraphConditionalHandle loop, cudaStream_t s) {
+    loop_begin_kernel<<<1, 1, 0, s>>>(nrm2, nrm_exact, use_exact, sc, ss, loop);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cycle_end(const double* nrm2, const GmresCtl* ctl, SolveCtl* sc, StepStats* ss, double stagnation,
+                             cudaGraphConditionalHandle loop, cudaStream_t s) {
+    cycle_end_kernel<<<1, 1, 0, s>>>(nrm2, ctl, sc, ss, stagnation, loop);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_end(const GmresCtl* ctl, const SolveCtl* sc, StepStats* ss, cudaStream_t s) {
+    solve_end_kernel<<<1, 1, 0, s>>>(ctl, sc, ss);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace hdgdg
