@@ -125,7 +125,7 @@ Plan make_plan(const hdgdg_config* c) {
     if (matrix_free(c)) {   // FP32 M^{-1}, FP32 Schur operators, the plus-side halves, one ticket per edge
         b += n_edges * (size_t)p.NF * p.NF * sizeof(float);
         b += (n_el * Np * Np + 4 * n_el * Np + 2 * B * Np) * sizeof(float);
-        b += p.nt * d + n_edges * sizeof(int);
+        b += 3 * p.nt * d;   // M^{-1} x and the two halves of S y
     }
     b += 2 * (size_t)guess_order(c) * p.s * p.nt * d;         // previous stage solutions and products
     p.persistent = b;
@@ -1253,19 +1253,18 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
         if (matrix_free(c)) {   // FP32 copies (the pairs' high parts) for the inner cycles, FP32 M^{-1}
             const size_t nS = (size_t)g.n_el * Np * Np, nA = 4 * (size_t)g.n_el * Np, nE = 2 * (size_t)g.batch * Np;
             float *S32 = nullptr, *aux32 = nullptr, *EG32 = nullptr;
-            double* half = nullptr;
-            int* ticket = nullptr;
+            double *ybuf = nullptr, *hm = nullptr, *hp = nullptr;
             TRY(dalloc(sim, &S32, nS));
             TRY(dalloc(sim, &aux32, nA));
             TRY(dalloc(sim, &EG32, nE));
             TRY(dalloc(sim, &sim->Minv32, (size_t)g.n_edges * p.NF * p.NF));
-            TRY(dalloc(sim, &half, p.nt));
-            TRY(dalloc(sim, &ticket, (size_t)g.n_edges));
+            TRY(dalloc(sim, &ybuf, p.nt));
+            TRY(dalloc(sim, &hm, p.nt));
+            TRY(dalloc(sim, &hp, p.nt));
             CU(launch_pair_hi(sim->Sphi, S32, nS, sim->stream));
             CU(launch_pair_hi(sim->Saux, aux32, nA, sim->stream));
             CU(launch_pair_hi(sim->Seg, EG32, nE, sim->stream));
             CU(launch_to_f32(sim->Minv, sim->Minv32, (size_t)g.n_edges * p.NF * p.NF, sim->stream));
-            CU(cudaMemsetAsync(ticket, 0, (size_t)g.n_edges * sizeof(int), sim->stream));
             sim->mf.S32 = S32;
             sim->mf.aux32 = aux32;
             sim->mf.EG32 = EG32;
@@ -1274,8 +1273,9 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
             sim->mf.EG2 = sim->Seg;
             sim->mf.Minv32 = sim->Minv32;
             sim->mf.tau = sim->tau;
-            sim->mf.half = half;
-            sim->mf.ticket = ticket;
+            sim->mf.ybuf = ybuf;
+            sim->mf.hm = hm;
+            sim->mf.hp = hp;
         }
     } else if (c->local_precision == HDGDG_LOCAL_FP32) {
         const size_t n = (size_t)g.n_el * p.NV * p.NV;

@@ -276,8 +276,9 @@ struct MfOps {
     const void *S2 = nullptr, *aux2 = nullptr, *EG2 = nullptr;       // the same as FP32 pairs (float2)
     const float* Minv32 = nullptr;   // block-Jacobi inverse [edge][col][row], FP32
     const double* tau = nullptr;     // tau_hat [edge][P]
-    void* half = nullptr;            // scratch: the plus sides' halves of the rows (n_edges * 3P doubles)
-    int* ticket = nullptr;           // one per edge, zero between products
+    void* ybuf = nullptr;            // scratch: M^{-1} x (n_edges * 3P values of 8 bytes)
+    void* hm = nullptr;              // scratch: the edges' minus-side halves of S y (8 bytes per value)
+    void* hp = nullptr;              // scratch: their plus-side halves
 };
 // y = S M^{-1} x in FP32 (inner Krylov cycles); done as for launch_spmv_pre
 cudaError_t launch_mf_inner(const Geom& g, const MfOps& op, const float* x, float* y, double beta, cudaStream_t s,

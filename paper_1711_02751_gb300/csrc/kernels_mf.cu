@@ -13,13 +13,15 @@
 // phi_hat and tangential terms and cancel the normal one), and a prescribed (Dirichlet) trace
 // row is the identity -- the rows the assembled matrix holds.
 //
-// One thread per (element, node), EPB elements per block, as the local solves.  An edge's row
-// needs both of its elements: each element leaves its half of the row in memory (the minus side
-// in the output vector, the plus side in a scratch vector) and takes a ticket (one int per edge);
-// the element that arrives second reads the other half and writes minus half + plus half, always
-// in that order, so the result does not depend on which element came first.  Nothing waits: the
-// first element's block simply moves on.
-//
+// Three launches per product, each short, so that no block waits on a chain of dependent
+// memory round trips:
+//   mf_pre_kernel   y = M^{-1} x, one thread per edge row (block-Jacobi inverse in FP32);
+//   mf_elem_kernel  one thread per (element, node): the node's traces y gathered straight into
+//                   registers, the operator data loaded before them, the lift, the local solve,
+//                   and the element's half of each face's row -- the edge's minus side (face 1 or
+//                   3) into hm, its plus side into hp (a boundary face's full row into hm, 0 into hp);
+//   mf_sum_kernel   y = hm + hp (residual mode: w = g - (hm + hp)), minus half first, so the
+//                   result is the same whatever order the elements ran in.
 // Modes (the Krylov solve applies the block-Jacobi-preconditioned operator S~ = S M^{-1}):
 //   kMfInner     y = S M^{-1} x        FP32 arithmetic and vectors (the mixed form's inner cycles)
 //   kMfResidual  w = g - S M^{-1} x    FP64-class FP32-pair arithmetic, FP64 vectors (refinement)
@@ -38,7 +40,10 @@ namespace {
 
 enum MfMode { kMfInner = 0, kMfResidual = 1, kMfPlain = 2 };
 
-// elements per block: 256 threads, at most 32 elements (the block's shared arrays stay under 48 KB)
+template <int MODE>
+using MfVec = std::conditional_t<MODE == kMfInner, float, double>;   // vectors of the mode
+
+// elements per block: 256 threads, at most 32 elements
 template <int P>
 constexpr int mf_epb() {
     return 256 / (P * P) > 32 ? 32 : (256 / (P * P) > 0 ? 256 / (P * P) : 1);
@@ -57,169 +62,178 @@ __device__ __forceinline__ typename A::T arith_load(const TX* p) {
     else return A::from(*p);
 }
 
-template <int P, int EPB, class A>
-struct MfSmem {
-    using T = typename A::T;
-    static constexpr int NF = 3 * P;
-    SchurSmem<P, EPB, A> sc;
-    T x[EPB][4][NF];     // the element's four face traces
-    T y[EPB][4][NF];     // M^{-1} x of each face (x itself in plain mode)
-    T h[EPB][4][NF];     // the element's half of each face's row of S y
-    int ed[EPB][4];      // edge of each face
-    int nb[EPB][4];      // neighbour across each face (-1: boundary)
-    int second[EPB][4];  // 1 when this element completes the face's row
-};
+// the element's half of a row, stored in the mode's vector type
+template <class A, typename TO>
+__device__ __forceinline__ TO arith_store(typename A::T v) {
+    if constexpr (sizeof(typename A::T) == sizeof(float) && sizeof(TO) == sizeof(float)) return v;
+    else return (TO)A::to(v);
+}
 
+// y = M^{-1} x per edge (one thread per row component), y in the arithmetic's own type
+template <int NF, class A, typename TX>
+__global__ void __launch_bounds__(256)
+mf_pre_kernel(int n_edges, const float* __restrict__ Minv, const TX* __restrict__ x, typename A::T* __restrict__ y,
+              const int* __restrict__ done) {
+    if (done && *done) return;
+    using T = typename A::T;
+    constexpr int EPB = 256 / NF;
+    __shared__ T xs[EPB][NF];
+    const int le = threadIdx.x / NF, ii = threadIdx.x % NF;
+    const int r = blockIdx.x * EPB + le;
+    const bool live = le < EPB && r < n_edges;
+    if (live) xs[le][ii] = arith_load<A>(x + (size_t)r * NF + ii);
+    __syncthreads();
+    if (!live) return;
+    const float* M = Minv + (size_t)r * NF * NF + ii;
+    typename A::Acc acc;
+#pragma unroll
+    for (int jj = 0; jj < NF; ++jj) acc.add(arith_of_f32<A>(__ldg(M + jj * NF)), xs[le][jj]);
+    y[(size_t)r * NF + ii] = acc.get();
+}
+
+// The element pass (see above).  PLAIN: y is the input vector itself (TX), else M^{-1} x (A::T).
 template <int P, int EPB, class A, int MODE>
 __global__ void __launch_bounds__(EPB * P * P)
-    mf_trace_kernel(Geom g, const typename A::T* __restrict__ S, const typename A::T* __restrict__ aux,
-                    const typename A::T* __restrict__ EG, const float* __restrict__ Minv,
-                    const double* __restrict__ tau_edge,
-                    const std::conditional_t<MODE == kMfInner, float, double>* __restrict__ x,
-                    const double* __restrict__ rhs,
-                    std::conditional_t<MODE == kMfInner, float, double>* __restrict__ out,
-                    std::conditional_t<MODE == kMfInner, float, double>* __restrict__ half,
-                    int* __restrict__ ticket, double beta, const int* __restrict__ done) {
+    mf_elem_kernel(Geom g, const typename A::T* __restrict__ S, const typename A::T* __restrict__ aux,
+                   const typename A::T* __restrict__ EG, const double* __restrict__ tau_edge,
+                   const void* __restrict__ yv, MfVec<MODE>* __restrict__ hm, MfVec<MODE>* __restrict__ hp,
+                   double beta, const int* __restrict__ done) {
     using T = typename A::T;
-    using TO = std::conditional_t<MODE == kMfInner, float, double>;
-    constexpr int Np = P * P, NF = 3 * P, NFACE = 4 * NF;
+    using TO = MfVec<MODE>;
+    constexpr int Np = P * P, NF = 3 * P;
+    constexpr bool kPref = Np <= 25;   // S^{-1} row held in registers
     if (done && *done) return;
-    __shared__ MfSmem<P, EPB, A> sm;
+    __shared__ SchurSmem<P, EPB, A> sm;
     const int le = threadIdx.x / Np, n = threadIdx.x % Np, i = n % P, j = n / P;
     const int e = blockIdx.x * EPB + le;
     const bool live = e < g.n_el;
-    if (live && n < 4) {
-        sm.ed[le][n] = edge_of_face(e, n, g);
-        sm.nb[le][n] = neighbour(e, n, g);
-    }
-    __syncthreads();
+    // operator data first: it does not depend on the traces
+    SchurNode<A> nd;
+    T srow[kPref ? Np : 1];
+    const T* Sn = S + (size_t)(live ? e : 0) * Np * Np + n;
     if (live) {
-        for (int t = n; t < NFACE; t += Np) {
-            const int f = t / NF, k = t % NF;
-            sm.x[le][f][k] = arith_load<A>(x + (size_t)sm.ed[le][f] * NF + k);
-        }
-    }
-    __syncthreads();
-    if (live) {   // y = M^{-1} x, face by face
-        for (int t = n; t < NFACE; t += Np) {
-            const int f = t / NF, row = t % NF;
-            if constexpr (MODE == kMfPlain) {
-                sm.y[le][f][row] = sm.x[le][f][row];
-            } else {
-                const float* M = Minv + (size_t)sm.ed[le][f] * NF * NF + row;
-                typename A::Acc acc;
+        nd.load(aux, e, n, Np);
+        if constexpr (kPref) {
 #pragma unroll
-                for (int col = 0; col < NF; ++col) acc.add(arith_of_f32<A>(__ldg(M + col * NF)), sm.x[le][f][col]);
-                sm.y[le][f][row] = acc.get();
-            }
+            for (int m = 0; m < Np; ++m) srow[m] = Sn[(size_t)m * Np];
         }
     }
-    __syncthreads();
-    // lift: u = sum over the faces through node n of tau y (the recovery's -B y / beta)
+    // the node's faces -- slot 0 its x-face (left or right), slot 1 its y-face (bottom or top) --
+    // with the edge, the position along it, tau and the three trace components
+    bool on[2];
+    int fc[2], bb[2], ed[2] = {0, 0};
+    on[0] = i == 0 || i == P - 1;
+    fc[0] = i == 0 ? 0 : 1;
+    bb[0] = j;
+    on[1] = j == 0 || j == P - 1;
+    fc[1] = j == 0 ? 2 : 3;
+    bb[1] = i;
+    T yv_[2][3];
+    T tau[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        on[k] = on[k] && live;
+        tau[k] = A::from(0.0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) yv_[k][c] = A::from(0.0);
+        if (!on[k]) continue;
+        const int r = edge_of_face(e, fc[k], g);
+        ed[k] = r;
+        tau[k] = A::from(tau_edge[(size_t)r * P + bb[k]]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const size_t o = (size_t)r * NF + c * P + bb[k];
+            if constexpr (MODE == kMfPlain) yv_[k][c] = A::from(static_cast<const double*>(yv)[o]);
+            else yv_[k][c] = static_cast<const T*>(yv)[o];
+        }
+    }
+    // lift: u = sum over the node's faces of tau y
     T u[3];
     {
         typename A::Acc a0, a1, a2;
-        if (live) {
-            for (int f = 0; f < 4; ++f) {
-                const bool on = (f == 0 && i == 0) || (f == 1 && i == P - 1) || (f == 2 && j == 0) ||
-                                (f == 3 && j == P - 1);
-                if (!on) continue;
-                const int b = (f < 2) ? j : i;
-                const T tau = A::from(tau_edge[(size_t)sm.ed[le][f] * P + b]);
-                a0.add(tau, sm.y[le][f][b]);
-                a1.add(tau, sm.y[le][f][P + b]);
-                a2.add(tau, sm.y[le][f][2 * P + b]);
-            }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (!on[k]) continue;
+            a0.add(tau[k], yv_[k][0]);
+            a1.add(tau[k], yv_[k][1]);
+            a2.add(tau[k], yv_[k][2]);
         }
         u[0] = a0.get();
         u[1] = a1.get();
         u[2] = a2.get();
     }
     T W[3];
-    schur_solve<P, EPB, A>(sm.sc, g, e, le, n, live, S, aux, EG, u[0], u[1], u[2], W[0], W[1], W[2]);
-    if (live) {
-        const T bt = A::from(beta * dt_factor(g, e));
-        W[0] = A::mul(bt, W[0]);
-        W[1] = A::mul(bt, W[1]);
-        W[2] = A::mul(bt, W[2]);
-        const T pb = aux[(size_t)e * 4 * Np + 3 * Np + n];
-        const T one = A::from(1.0), mone = A::from(-1.0);
-        for (int f = 0; f < 4; ++f) {
-            const bool on = (f == 0 && i == 0) || (f == 1 && i == P - 1) || (f == 2 && j == 0) ||
-                            (f == 3 && j == P - 1);
-            if (!on) continue;
-            const int b = (f < 2) ? j : i;
-            const bool xedge = f < 2, minus = (f == 1 || f == 3);   // minus side: outward normal +axis
-            const int cn = xedge ? 1 : 2, ct = xedge ? 2 : 1;
-            const double tau_d = tau_edge[(size_t)sm.ed[le][f] * P + b];
-            const T tau = A::from(tau_d), m2tau = A::from(-2.0 * tau_d);
-            const T Wn = W[cn], Wt = W[ct];
-            const T sg = minus ? one : mone;
-            const bool boundary = sm.nb[le][f] < 0;
-            if (boundary && g.dirichlet) {   // prescribed trace: the identity row
-                sm.h[le][f][b] = sm.y[le][f][b];
-                sm.h[le][f][P + b] = sm.y[le][f][P + b];
-                sm.h[le][f][2 * P + b] = sm.y[le][f][2 * P + b];
-                continue;
-            }
-            typename A::Acc r0, rn, rt;
-            r0.add(sg, Wn);                       // U.n
-            r0.add(tau, W[0]);                    // + tau phi
-            rn.add(A::mul(sg, pb), W[0]);         // phi_B phi n
-            rn.add(tau, Wn);                      // + tau U_n
-            rt.add(tau, Wt);                      // tau U_t
-            if (boundary) {                       // wall: element + mirror; then D = -2 tau on every row
-                r0.add(sg, Wn);
-                r0.add(tau, W[0]);
-                rt.add(tau, Wt);
-                rn = typename A::Acc();
-            }
-            if (minus || boundary) {              // D y enters with the edge's minus side (or its only side)
-                r0.add(m2tau, sm.y[le][f][b]);
-                rn.add(m2tau, sm.y[le][f][cn * P + b]);
-                rt.add(m2tau, sm.y[le][f][ct * P + b]);
-            }
-            sm.h[le][f][b] = r0.get();
-            sm.h[le][f][cn * P + b] = rn.get();
-            sm.h[le][f][ct * P + b] = rt.get();
-        }
-    }
-    __syncthreads();
-    // boundary rows are complete; interior rows: leave this half (minus side in out, plus side in
-    // half), then take the edge's ticket
-    if (live) {
-        for (int t = n; t < NFACE; t += Np) {
-            const int f = t / NF, k = t % NF;
-            const size_t o = (size_t)sm.ed[le][f] * NF + k;
-            const TO v = (TO)A::to(sm.h[le][f][k]);
-            if (sm.nb[le][f] < 0) {
-                if constexpr (MODE == kMfResidual) out[o] = rhs[o] - v;
-                else out[o] = v;
-            } else if (f == 1 || f == 3) {
-                out[o] = v;
-            } else {
-                half[o] = v;
-            }
-        }
-    }
-    __threadfence();
-    __syncthreads();
-    if (live && n < 4)
-        sm.second[le][n] = sm.nb[le][n] >= 0 ? atomicAdd(ticket + sm.ed[le][n], 1) : 0;
-    __syncthreads();
+    if constexpr (kPref)
+        schur_solve_with<P, EPB, A>(sm, g, e, le, n, live, nd, [&](int m) { return srow[m]; }, EG, u[0], u[1],
+                                    u[2], W[0], W[1], W[2]);
+    else
+        schur_solve_with<P, EPB, A>(sm, g, e, le, n, live, nd, [&](int m) { return Sn[(size_t)m * Np]; }, EG, u[0],
+                                    u[1], u[2], W[0], W[1], W[2]);
     if (!live) return;
-    __threadfence();
-    for (int t = n; t < NFACE; t += Np) {
-        const int f = t / NF, k = t % NF;
-        if (sm.nb[le][f] < 0 || sm.second[le][f] != 1) continue;
-        const size_t o = (size_t)sm.ed[le][f] * NF + k;
-        const TO mine = (TO)A::to(sm.h[le][f][k]);
-        const bool minus = f == 1 || f == 3;
-        const TO sum = minus ? mine + __ldcg(half + o) : __ldcg(out + o) + mine;   // minus half first
-        if constexpr (MODE == kMfResidual) out[o] = rhs[o] - sum;
-        else out[o] = sum;
+    const T bt = A::from(beta * dt_factor(g, e));
+    W[0] = A::mul(bt, W[0]);
+    W[1] = A::mul(bt, W[1]);
+    W[2] = A::mul(bt, W[2]);
+    const T one = A::from(1.0), mone = A::from(-1.0), mtwo = A::from(-2.0);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (!on[k]) continue;
+        const int f = fc[k], b = bb[k];
+        const bool xedge = f < 2, minus = (f == 1 || f == 3);   // minus side: outward normal +axis
+        const int cn = xedge ? 1 : 2, ct = xedge ? 2 : 1;
+        const bool boundary = g.walls && neighbour(e, f, g) < 0;
+        const size_t o = (size_t)ed[k] * NF + b;
+        if (boundary && g.dirichlet) {   // prescribed trace: the identity row
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                hm[o + c * P] = arith_store<A, TO>(yv_[k][c]);
+                hp[o + c * P] = TO(0);
+            }
+            continue;
+        }
+        const T Wn = W[cn], Wt = W[ct];
+        const T sg = minus ? one : mone;
+        const T m2tau = A::mul(mtwo, tau[k]);
+        typename A::Acc r0, rn, rt;
+        r0.add(sg, Wn);                       // U.n
+        r0.add(tau[k], W[0]);                 // + tau phi
+        rn.add(A::mul(sg, nd.pb), W[0]);      // phi_B phi n
+        rn.add(tau[k], Wn);                   // + tau U_n
+        rt.add(tau[k], Wt);                   // tau U_t
+        if (boundary) {                       // wall: element + mirror; then D = -2 tau on every row
+            r0.add(sg, Wn);
+            r0.add(tau[k], W[0]);
+            rt.add(tau[k], Wt);
+            rn = typename A::Acc();
+        }
+        if (minus || boundary) {              // D y enters with the edge's minus side (or its only side)
+            r0.add(m2tau, yv_[k][0]);
+            rn.add(m2tau, yv_[k][cn]);
+            rt.add(m2tau, yv_[k][ct]);
+        }
+        TO* dst = (minus || boundary) ? hm : hp;
+        dst[o] = arith_store<A, TO>(r0.get());
+        dst[o + cn * P] = arith_store<A, TO>(rn.get());
+        dst[o + ct * P] = arith_store<A, TO>(rt.get());
+        if (boundary) {
+            hp[o] = TO(0);
+            hp[o + cn * P] = TO(0);
+            hp[o + ct * P] = TO(0);
+        }
     }
-    if (n < 4 && sm.nb[le][n] >= 0 && sm.second[le][n] == 1) ticket[sm.ed[le][n]] = 0;   // ready for the next product
+}
+
+// y = hm + hp, or w = g - (hm + hp)
+template <typename TO, bool RESID>
+__global__ void __launch_bounds__(256)
+mf_sum_kernel(size_t n, const TO* __restrict__ hm, const TO* __restrict__ hp, const double* __restrict__ rhs,
+              TO* __restrict__ out, const int* __restrict__ done) {
+    if (done && *done) return;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        const TO v = hm[t] + hp[t];
+        if constexpr (RESID) out[t] = rhs[t] - v;
+        else out[t] = v;
+    }
 }
 
 // qhat = M^{-1} x~ with the FP32 block-Jacobi blocks, FP64-class sums (x split into FP32 pairs).
@@ -247,16 +261,34 @@ __global__ void pair_hi_kernel(const float2* __restrict__ a, float* __restrict__
         hi[t] = a[t].x;
 }
 
-template <int P, class A, int MODE, typename TX, typename TO>
-cudaError_t mf_launch(const Geom& g, const void* S, const void* aux, const void* EG, const float* Minv,
-                      const double* tau, const TX* x, const double* rhs, TO* out, void* half, int* ticket,
-                      double beta, cudaStream_t s, const int* done) {
+int sum_grid(size_t n) {
+    size_t b = (n + 255) / 256;
+    if (b > 152 * 8) b = 152 * 8;
+    return b > 0 ? (int)b : 1;
+}
+
+// One product: [y = M^{-1} x,] the element pass, the edge sum.
+template <int P, class A, int MODE>
+cudaError_t mf_launch(const Geom& g, const MfOps& op, const void* S, const void* aux, const void* EG, const void* x,
+                      const double* rhs, MfVec<MODE>* out, double beta, cudaStream_t s, const int* done) {
     using T = typename A::T;
-    constexpr int EPB = mf_epb<P>();
-    mf_trace_kernel<P, EPB, A, MODE><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(
-        g, static_cast<const T*>(S), static_cast<const T*>(aux), static_cast<const T*>(EG), Minv, tau, x, rhs, out,
-        reinterpret_cast<TO*>(half), ticket, beta, done);
-    count_launches(1);
+    using TO = MfVec<MODE>;
+    constexpr int NF = 3 * P, EPB = mf_epb<P>();
+    const void* yv = x;
+    if constexpr (MODE != kMfPlain) {
+        constexpr int EPE = 256 / NF;
+        mf_pre_kernel<NF, A, TO><<<(g.n_edges + EPE - 1) / EPE, EPE * NF, 0, s>>>(
+            g.n_edges, op.Minv32, static_cast<const TO*>(x), static_cast<T*>(op.ybuf), done);
+        yv = op.ybuf;
+    }
+    TO* hm = static_cast<TO*>(op.hm);
+    TO* hp = static_cast<TO*>(op.hp);
+    mf_elem_kernel<P, EPB, A, MODE><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(
+        g, static_cast<const T*>(S), static_cast<const T*>(aux), static_cast<const T*>(EG), op.tau, yv, hm, hp, beta,
+        done);
+    const size_t n = (size_t)g.n_edges * NF;
+    mf_sum_kernel<TO, MODE == kMfResidual><<<sum_grid(n), 256, 0, s>>>(n, hm, hp, rhs, out, done);
+    count_launches(MODE != kMfPlain ? 3 : 2);
     return cudaGetLastError();
 }
 
@@ -264,10 +296,8 @@ cudaError_t mf_launch(const Geom& g, const void* S, const void* aux, const void*
 
 cudaError_t launch_mf_inner(const Geom& g, const MfOps& op, const float* x, float* y, double beta, cudaStream_t s,
                             const int* done) {
-#define CASE(P)                                                                                               \
-    case P:                                                                                                   \
-        return mf_launch<P, ArithF32, kMfInner>(g, op.S32, op.aux32, op.EG32, op.Minv32, op.tau, x, nullptr, y, \
-                                                op.half, op.ticket, beta, s, done);
+#define CASE(P) \
+    case P: return mf_launch<P, ArithF32, kMfInner>(g, op, op.S32, op.aux32, op.EG32, x, nullptr, y, beta, s, done);
     switch (g.P) {
         CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9)
         default: return cudaErrorInvalidValue;
@@ -277,10 +307,8 @@ cudaError_t launch_mf_inner(const Geom& g, const MfOps& op, const float* x, floa
 
 cudaError_t launch_mf_residual(const Geom& g, const MfOps& op, const double* x, const double* rhs, double* w,
                                double beta, cudaStream_t s) {
-#define CASE(P)                                                                                                \
-    case P:                                                                                                    \
-        return mf_launch<P, ArithF2, kMfResidual>(g, op.S2, op.aux2, op.EG2, op.Minv32, op.tau, x, rhs, w, op.half, \
-                                                  op.ticket, beta, s, nullptr);
+#define CASE(P) \
+    case P: return mf_launch<P, ArithF2, kMfResidual>(g, op, op.S2, op.aux2, op.EG2, x, rhs, w, beta, s, nullptr);
     switch (g.P) {
         CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9)
         default: return cudaErrorInvalidValue;
@@ -289,10 +317,8 @@ cudaError_t launch_mf_residual(const Geom& g, const MfOps& op, const double* x, 
 }
 
 cudaError_t launch_mf_plain(const Geom& g, const MfOps& op, const double* x, double* y, double beta, cudaStream_t s) {
-#define CASE(P)                                                                                                \
-    case P:                                                                                                    \
-        return mf_launch<P, ArithF2, kMfPlain>(g, op.S2, op.aux2, op.EG2, op.Minv32, op.tau, x, nullptr, y, op.half, \
-                                               op.ticket, beta, s, nullptr);
+#define CASE(P) \
+    case P: return mf_launch<P, ArithF2, kMfPlain>(g, op, op.S2, op.aux2, op.EG2, x, nullptr, y, beta, s, nullptr);
     switch (g.P) {
         CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9)
         default: return cudaErrorInvalidValue;

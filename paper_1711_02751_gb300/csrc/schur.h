@@ -83,32 +83,40 @@ struct SchurSmem {
     T w[EPB][Np];       // phi_B phi
 };
 
-// A^{-1} x for the element of thread (le, n) with x = (x0, xU, xV) at node n (each thread its
-// own node's values); returns phi, U, V at node n.  Every thread of the block calls it (its
-// barriers are block-wide); live marks threads of real elements.
-template <int P, int EPB, class A>
-__device__ __forceinline__ void schur_solve(SchurSmem<P, EPB, A>& sm, const Geom& g, int e, int le, int n,
-                                            bool live, const typename A::T* __restrict__ S,
-                                            const typename A::T* __restrict__ aux,
-                                            const typename A::T* __restrict__ EG, typename A::T x0,
-                                            typename A::T xU, typename A::T xV, typename A::T& phi,
-                                            typename A::T& U, typename A::T& V) {
-    using T = typename A::T;
-    constexpr int Np = P * P;
-    const int i = n % P, j = n / P;
-    const T one = A::from(1.0);
-    T rd{}, ncx{}, ncy{}, pb{};
-    if (live) {
-        const T* ax = aux + (size_t)e * 4 * Np;
+// The four numbers per node the solve needs (1/d, -cx, -cy, phi_B), loaded at once.
+template <class A>
+struct SchurNode {
+    typename A::T rd{}, ncx{}, ncy{}, pb{};
+    __device__ __forceinline__ void load(const typename A::T* __restrict__ aux, int e, int n, int Np) {
+        const typename A::T* ax = aux + (size_t)e * 4 * Np;
         rd = ax[n];
         ncx = ax[Np + n];
         ncy = ax[2 * Np + n];
         pb = ax[3 * Np + n];
+    }
+};
+
+// A^{-1} x for the element of thread (le, n) with x = (x0, xU, xV) at node n (each thread its
+// own node's values); returns phi, U, V at node n.  Every thread of the block calls it (its
+// barriers are block-wide); live marks threads of real elements.  nd holds the node's numbers;
+// Srow(m) returns (S^{-1})_{n m}, the (phi, phi) block of A^{-1} (from memory or from registers
+// the caller filled early).
+template <int P, int EPB, class A, class SRow>
+__device__ __forceinline__ void schur_solve_with(SchurSmem<P, EPB, A>& sm, const Geom& g, int e, int le, int n,
+                                                 bool live, const SchurNode<A>& nd, SRow Srow,
+                                                 const typename A::T* __restrict__ EG, typename A::T x0,
+                                                 typename A::T xU, typename A::T xV, typename A::T& phi,
+                                                 typename A::T& U, typename A::T& V) {
+    using T = typename A::T;
+    constexpr int Np = P * P;
+    const int i = n % P, j = n / P;
+    const T one = A::from(1.0);
+    if (live) {
         const T* eg = EG + (size_t)g.by_el.div(e) * 2 * Np;
         sm.EG[le][0][n] = eg[n];
         sm.EG[le][1][n] = eg[Np + n];
-        sm.t[le][0][n] = A::mul(xU, rd);
-        sm.t[le][1][n] = A::mul(xV, rd);
+        sm.t[le][0][n] = A::mul(xU, nd.rd);
+        sm.t[le][1][n] = A::mul(xV, nd.rd);
     }
     __syncthreads();
     if (live) {   // s = x_phi - Bx d^{-1} x_U - By d^{-1} x_V
@@ -123,28 +131,43 @@ __device__ __forceinline__ void schur_solve(SchurSmem<P, EPB, A>& sm, const Geom
     }
     __syncthreads();
     if (live) {   // phi = S^{-1} s
-        const T* Sn = S + (size_t)e * Np * Np + n;
         typename A::Acc acc;
-#pragma unroll 4
-        for (int m = 0; m < Np; ++m) acc.add(Sn[(size_t)m * Np], sm.s[le][m]);
+#pragma unroll
+        for (int m = 0; m < Np; ++m) acc.add(Srow(m), sm.s[le][m]);
         phi = acc.get();
-        sm.w[le][n] = A::mul(pb, phi);
+        sm.w[le][n] = A::mul(nd.pb, phi);
     }
     __syncthreads();
     if (live) {   // d U = x_U - Cx phi,  d V = x_V - Cy phi
         typename A::Acc au, av;
         au.add(one, xU);
-        au.add(ncx, phi);
+        au.add(nd.ncx, phi);
         av.add(one, xV);
-        av.add(ncy, phi);
+        av.add(nd.ncy, phi);
 #pragma unroll
         for (int a = 0; a < P; ++a) {
             au.add(sm.EG[le][1][i * P + a], sm.w[le][j * P + a]);
             av.add(sm.EG[le][1][j * P + a], sm.w[le][a * P + i]);
         }
-        U = A::mul(au.get(), rd);
-        V = A::mul(av.get(), rd);
+        U = A::mul(au.get(), nd.rd);
+        V = A::mul(av.get(), nd.rd);
     }
+}
+
+// The same with the node's numbers and S^{-1} read from memory (S [n_el][col m][row n]).
+template <int P, int EPB, class A>
+__device__ __forceinline__ void schur_solve(SchurSmem<P, EPB, A>& sm, const Geom& g, int e, int le, int n,
+                                            bool live, const typename A::T* __restrict__ S,
+                                            const typename A::T* __restrict__ aux,
+                                            const typename A::T* __restrict__ EG, typename A::T x0,
+                                            typename A::T xU, typename A::T xV, typename A::T& phi,
+                                            typename A::T& U, typename A::T& V) {
+    constexpr int Np = P * P;
+    SchurNode<A> nd;
+    if (live) nd.load(aux, e, n, Np);
+    const typename A::T* Sn = S + (size_t)e * Np * Np + n;
+    schur_solve_with<P, EPB, A>(sm, g, e, le, n, live, nd, [&](int m) { return Sn[(size_t)m * Np]; }, EG, x0, xU,
+                                xV, phi, U, V);
 }
 
 }  // namespace hdgdg
