@@ -73,6 +73,8 @@ def _args():
                     help="mixed form's trace operator: 1 matrix-free (element by element), 0 assembled matrix")
     ap.add_argument("--local-dense", type=int, default=0, choices=[0, 1],
                     help="local solves: 0 Schur complement on phi (library default), 1 dense A^-1")
+    ap.add_argument("--breakdown-steps", type=int, default=10,
+                    help="steps timed again with the per-kernel-class CUDA-event timers on")
     ap.add_argument("--stiff-steps", type=int, default=10,
                     help="timed steps of the stiff variant (large512_stiff, gravity Courant ~14) "
                          "reported beside the headline; 0 skips it")
@@ -727,7 +729,8 @@ def main():
         if rank == 0:
             clocks.start()
             time.sleep(0.3)
-        r = _timed_steps(sim, stream, args.steps, dist)
+        # headline: the library as a user runs it (each step one replayed graph, timers off)
+        r = _timed_steps(sim, stream, args.steps, dist, timing=False)
         c = clocks.stop() if rank == 0 else None
         finals[precision] = sim.get_state()
         e2e = None
@@ -735,6 +738,11 @@ def main():
             ms_e2e, nbytes = _e2e(sim, stream, args.steps, dist, h, hu, hv)
             e2e = {"value": job_value(world, dof, args.steps, ms_e2e), "unit": UNIT,
                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+        # per-kernel-class breakdown: further steps with the CUDA-event timers on (host-driven
+        # restart cycles, since event records cannot sit in a graph's conditional body)
+        rk = _timed_steps(sim, stream, args.breakdown_steps, dist, timing=True)
+        r["ktimes"] = rk["ktimes"]
+        r["breakdown"] = {"steps": args.breakdown_steps, "ms_per_step_timers_on": rk["ms_total"] / args.breakdown_steps}
         sim.close()
         forms[precision] = {"r": r, "clocks": c, "e2e": e2e}
     stiff = stiff_block(args, stream, dist, world) if args.stiff_steps > 0 else None
@@ -760,6 +768,7 @@ def main():
                       "ms_per_step": r["ms_total"] / args.steps,
                       "krylov_iterations_per_stage": r["stats"]["krylov_iterations"] / max(1, 2 * r["stats"]["steps"]),
                       "kernel_breakdown_ms": {c: {"ms": round(v[0], 3), "groups": v[1]} for c, v in r["ktimes"].items()},
+                      "breakdown_run": r["breakdown"],
                       "roofline": _roofline(N, k, r["ktimes"], p, fp64_tflops, hbm, bool(args.local_dense),
                                             args.local if p == "mixed" else "fp64", fp32_peak,
                                             bool(_trace_operator(args, p))),
