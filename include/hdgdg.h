@@ -183,11 +183,17 @@ typedef struct {
     double time;                  /* simulated time since set_state (steps x dt) */
     int last_guess_order;         /* extrapolation order the most recent trace solve started from
                                      (0: zero start) */
-    /* HDGDG_LOCAL_F32X2 with local_dense = 1 on meshes of >= 4096 elements: elements per block
-     * of the condensation and recovery kernels, picked at create by timing each candidate tile on
-     * the handle's own operators (0: the default tile, not tuned). */
+    /* Meshes of >= 4096 elements: elements per block of the condensation and recovery kernels,
+     * picked at create by timing each candidate tile on the handle's own operators -- the
+     * Schur-complement kernels for degrees 2..4, the dense FP32-pair kernels for every degree
+     * (0: the default tile, not tuned). */
     int local_tile_condense;
     int local_tile_recover;
+    /* trace_operator = 1, meshes of >= 4096 elements, degrees 2..4: elements per block of the
+     * matrix-free operator's element pass in the inner cycles and whether it loads the local
+     * operator ahead of the traces (1) -- picked the same way (0, 0: the default, not tuned). */
+    int trace_tile;
+    int trace_tile_prefetch;
 } hdgdg_stats;
 
 /* Kernel classes of the per-kernel timers (hdgdg_kernel_time). */

@@ -331,6 +331,7 @@ struct hdgdg_sim {
     float *Stil32 = nullptr, *V32 = nullptr, *w32 = nullptr;   // mixed precision only
     float* Stil_lo = nullptr;   // residual_f32x2: S~ = Stil32 + Stil_lo
     MfOps mf;                   // trace_operator = 1: the matrix-free operator's data
+    int trace_tile = 0, trace_prefetch = 0;   // its autotuned element-pass tile (0: default)
     float* Minv32 = nullptr;    // its FP32 block-Jacobi inverse
     double *red = nullptr, *mred = nullptr, *dvals = nullptr;
     GmresCtl* ctl = nullptr;
@@ -1277,6 +1278,18 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
             sim->mf.hm = hm;
             sim->mf.hp = hp;
         }
+        if (g.n_el >= 4096) {   // pick the tiles on this handle's operators, then clear the scratch
+            CU(launch_autotune_local(g, sim->ops, sim->R1, sim->Z, sim->tau, sim->lam, sim->Qs, sim->NLs[0],
+                                     sim->stream));
+            if (matrix_free(c)) {
+                CU(cudaMemsetAsync(sim->V32, 0, p.nt * sizeof(float), sim->stream));
+                CU(launch_mf_autotune(g, sim->mf, sim->V32, sim->w32, beta_of(sim), sim->stream, &sim->trace_tile,
+                                      &sim->trace_prefetch));
+            }
+            for (double* v : {sim->R1, sim->Z, sim->Qs, sim->NLs[0]})
+                CU(cudaMemsetAsync(v, 0, 3 * p.n * sizeof(double), sim->stream));
+            CU(cudaMemsetAsync(sim->lam, 0, p.nt * sizeof(double), sim->stream));
+        }
     } else if (c->local_precision == HDGDG_LOCAL_FP32) {
         const size_t n = (size_t)g.n_el * p.NV * p.NV;
         TRY(dalloc(sim, &sim->Ainv32, n));
@@ -1622,6 +1635,8 @@ hdgdg_status hdgdg_get_stats(hdgdg_sim* sim, hdgdg_stats* out) {
     out->time = sim->t;
     out->local_tile_condense = sim->ops.tile_condense;
     out->local_tile_recover = sim->ops.tile_recover;
+    out->trace_tile = sim->trace_tile;
+    out->trace_tile_prefetch = sim->trace_prefetch;
     return HDGDG_OK;
 }
 

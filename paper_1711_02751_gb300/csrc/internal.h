@@ -248,6 +248,7 @@ struct LocalOps {
     // (1/d, -cx, -cy, phi_B) per node and EG [batch][2][P][P] = (-E, -G) per instance; the values
     // are double (kind 0) or FP32 pairs float2 (hi, lo) (kind 3).
     bool schur = false;
+    int schur_tile_c = 0, schur_tile_r = 0;   // tiles of the Schur kernels (launch_autotune_local)
     const void* S = nullptr;
     const void* aux = nullptr;
     const void* EG = nullptr;
@@ -264,9 +265,10 @@ cudaError_t launch_condense(const Geom& g, const LocalOps& ops, const double* R1
 cudaError_t launch_recover(const Geom& g, const LocalOps& ops, const double* Z, const double* R1,
                            const double* tau_edge, const double* qhat, double beta, double inv_aii,
                            double* Q, double* Lst, cudaStream_t s);
-// Autotuner of the FP32-pair local kernels' tile (elements per block): times each candidate on
-// the handle's operators, using R1, Z, Q, Lst as scratch (their contents are overwritten), and
-// records the fastest in ops.  No-op for other local arithmetic.
+// Autotuner of the local kernels' tile (elements per block): times each candidate on the handle's
+// operators, using R1, Z, Q, Lst as scratch (their contents are overwritten), and records the
+// fastest in ops: the Schur-complement kernels (FP64 or FP32 pairs, degrees 2..4) and the dense
+// FP32-pair kernels.  No-op for other local arithmetic.
 cudaError_t launch_autotune_local(const Geom& g, LocalOps& ops, double* R1, double* Z, const double* tau_edge,
                                   const double* qhat, double* Q, double* Lst, cudaStream_t s);
 // Matrix-free trace operator (kernels_mf.cu): S x = D x - C A^{-1} B x element by element through
@@ -279,6 +281,7 @@ struct MfOps {
     void* ybuf = nullptr;            // scratch: M^{-1} x (n_edges * 3P values of 8 bytes)
     void* hm = nullptr;              // scratch: the edges' minus-side halves of S y (8 bytes per value)
     void* hp = nullptr;              // scratch: their plus-side halves
+    int tile = 0;                    // tile of the inner cycles' element pass (launch_mf_autotune)
 };
 // y = S M^{-1} x in FP32 (inner Krylov cycles); done as for launch_spmv_pre
 cudaError_t launch_mf_inner(const Geom& g, const MfOps& op, const float* x, float* y, double beta, cudaStream_t s,
@@ -288,6 +291,10 @@ cudaError_t launch_mf_residual(const Geom& g, const MfOps& op, const double* x, 
                                double beta, cudaStream_t s);
 // y = S x (no preconditioner), FP64-class
 cudaError_t launch_mf_plain(const Geom& g, const MfOps& op, const double* x, double* y, double beta, cudaStream_t s);
+// Pick the inner element pass's tile by timing each candidate (degrees 2..4); *epb and *prefetch
+// report the choice (elements per block, S^{-1} row in registers).
+cudaError_t launch_mf_autotune(const Geom& g, MfOps& op, const float* x, float* y, double beta, cudaStream_t s,
+                               int* epb, int* prefetch);
 // qhat = M^{-1} x~ with the FP32 blocks, FP64-class sums
 cudaError_t launch_mf_back(const Geom& g, const float* Minv32, const double* x, double* y, cudaStream_t s);
 // hi[t] = pairs[t].x for n FP32 pairs (float2)

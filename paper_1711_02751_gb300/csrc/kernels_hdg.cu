@@ -591,29 +591,97 @@ __global__ void __launch_bounds__(EPB * P * P)
     }
 }
 
+// Tiles of the Schur-complement kernels: elements per block for about 256 (tile 0, the default),
+// 128 or 512 threads; the autotuner tries them at create for degrees 2..4.
+constexpr int schur_tile_threads(int t) { return t == 1 ? 128 : t == 2 ? 512 : 256; }
 template <int P>
-constexpr int schur_epb() {
-    return 256 / (P * P) > 0 ? 256 / (P * P) : 1;
+constexpr int schur_epb_for(int threads) {
+    return threads / (P * P) > 0 ? threads / (P * P) : 1;
 }
 
-template <int P, class A>
-void schur_condense(const Geom& g, const LocalOps& ops, const double* R1, double* Z, cudaStream_t s) {
+template <int P, class A, int TILE>
+void schur_condense_t(const Geom& g, const LocalOps& ops, const double* R1, double* Z, cudaStream_t s) {
     using T = typename A::T;
-    constexpr int EPB = schur_epb<P>();
+    constexpr int EPB = schur_epb_for<P>(schur_tile_threads(TILE));
     schur_condense_kernel<P, EPB, A><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(
         g, static_cast<const T*>(ops.S), static_cast<const T*>(ops.aux), static_cast<const T*>(ops.EG), R1, Z);
     count_launches(1);
 }
 
-template <int P, class A>
-void schur_recover(const Geom& g, const LocalOps& ops, const double* Z, const double* R1, const double* tau_edge,
-                   const double* qhat, double beta, double inv_aii, double* Q, double* Lst, cudaStream_t s) {
+template <int P, class A, int TILE>
+void schur_recover_t(const Geom& g, const LocalOps& ops, const double* Z, const double* R1, const double* tau_edge,
+                     const double* qhat, double beta, double inv_aii, double* Q, double* Lst, cudaStream_t s) {
     using T = typename A::T;
-    constexpr int EPB = schur_epb<P>();
+    constexpr int EPB = schur_epb_for<P>(schur_tile_threads(TILE));
     schur_recover_kernel<P, EPB, A><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(
         g, static_cast<const T*>(ops.S), static_cast<const T*>(ops.aux), static_cast<const T*>(ops.EG), Z, R1,
         tau_edge, qhat, beta, inv_aii, Q, Lst);
     count_launches(1);
+}
+
+template <int P, class A>
+void schur_condense(const Geom& g, const LocalOps& ops, const double* R1, double* Z, cudaStream_t s) {
+    if constexpr (P >= 3 && P <= 5) {
+        if (ops.schur_tile_c == 1) return schur_condense_t<P, A, 1>(g, ops, R1, Z, s);
+        if (ops.schur_tile_c == 2) return schur_condense_t<P, A, 2>(g, ops, R1, Z, s);
+    }
+    schur_condense_t<P, A, 0>(g, ops, R1, Z, s);
+}
+
+template <int P, class A>
+void schur_recover(const Geom& g, const LocalOps& ops, const double* Z, const double* R1, const double* tau_edge,
+                   const double* qhat, double beta, double inv_aii, double* Q, double* Lst, cudaStream_t s) {
+    if constexpr (P >= 3 && P <= 5) {
+        if (ops.schur_tile_r == 1) return schur_recover_t<P, A, 1>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s);
+        if (ops.schur_tile_r == 2) return schur_recover_t<P, A, 2>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s);
+    }
+    schur_recover_t<P, A, 0>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s);
+}
+
+// Time each tile of the Schur condensation and recovery (one warm-up and three timed launches
+// each, CUDA events) on the handle's operators and keep the fastest of each in ops.
+template <int P, class A>
+cudaError_t autotune_schur(const Geom& g, LocalOps& ops, double* R1, double* Z, const double* tau_edge,
+                           const double* qhat, double* Q, double* Lst, cudaStream_t s) {
+    if constexpr (P < 3 || P > 5) {
+        return cudaSuccess;
+    } else {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess) return cudaGetLastError();
+        if (cudaEventCreate(&b) != cudaSuccess) {
+            cudaEventDestroy(a);
+            return cudaGetLastError();
+        }
+        float best_c = 1e30f, best_r = 1e30f;
+        int tc = 0, tr = 0;
+        cudaError_t err = cudaSuccess;
+        for (int t = 0; t < 3 && err == cudaSuccess; ++t) {
+            ops.schur_tile_c = ops.schur_tile_r = t;
+            float ms_c = 0.f, ms_r = 0.f;
+            schur_condense<P, A>(g, ops, R1, Z, s);
+            cudaEventRecord(a, s);
+            for (int k = 0; k < 3; ++k) schur_condense<P, A>(g, ops, R1, Z, s);
+            cudaEventRecord(b, s);
+            err = cudaEventSynchronize(b);
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms_c, a, b);
+            schur_recover<P, A>(g, ops, Z, R1, tau_edge, qhat, 1.0, 1.0, Q, Lst, s);
+            cudaEventRecord(a, s);
+            for (int k = 0; k < 3; ++k) schur_recover<P, A>(g, ops, Z, R1, tau_edge, qhat, 1.0, 1.0, Q, Lst, s);
+            cudaEventRecord(b, s);
+            if (err == cudaSuccess) err = cudaEventSynchronize(b);
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms_r, a, b);
+            if (err == cudaSuccess && ms_c < best_c) { best_c = ms_c; tc = t; }
+            if (err == cudaSuccess && ms_r < best_r) { best_r = ms_r; tr = t; }
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        ops.schur_tile_c = tc;
+        ops.schur_tile_r = tr;
+        ops.tile_condense = schur_epb_for<P>(schur_tile_threads(tc));
+        ops.tile_recover = schur_epb_for<P>(schur_tile_threads(tr));
+        if (err == cudaSuccess) err = cudaGetLastError();
+        return err;
+    }
 }
 
 template <int P, class A>
@@ -822,7 +890,19 @@ cudaError_t recover_launch(const Geom& g, const LocalOps& ops, const double* Z, 
 
 cudaError_t launch_autotune_local(const Geom& g, LocalOps& ops, double* R1, double* Z, const double* tau_edge,
                                   const double* qhat, double* Q, double* Lst, cudaStream_t s) {
-    if (ops.kind != 3 || ops.schur) return cudaSuccess;
+    if (ops.schur) {
+#define SCALL(P)                                                                                  \
+    return ops.kind == 3 ? autotune_schur<P, ArithF2>(g, ops, R1, Z, tau_edge, qhat, Q, Lst, s)   \
+                         : autotune_schur<P, ArithF64>(g, ops, R1, Z, tau_edge, qhat, Q, Lst, s)
+        switch (g.P) {
+            case 3: SCALL(3);
+            case 4: SCALL(4);
+            case 5: SCALL(5);
+            default: return cudaSuccess;
+        }
+#undef SCALL
+    }
+    if (ops.kind != 3) return cudaSuccess;
 #define CALL(P) autotune_x2<P>(g, ops, R1, Z, tau_edge, qhat, Q, Lst, s)
     switch (g.P) {
         case 2: return CALL(2);

@@ -43,11 +43,20 @@ enum MfMode { kMfInner = 0, kMfResidual = 1, kMfPlain = 2 };
 template <int MODE>
 using MfVec = std::conditional_t<MODE == kMfInner, float, double>;   // vectors of the mode
 
-// elements per block: 256 threads, at most 32 elements
+// Tiles of the element pass: elements per block for about `threads` threads (at most 32 elements),
+// and whether the S^{-1} row is loaded into registers ahead of the traces.  Tile 0 is the default
+// (256 threads, registers); the autotuner tries the others at create for degrees 2..4.
+template <int P>
+constexpr int mf_epb_for(int threads) {
+    return threads / (P * P) > 32 ? 32 : (threads / (P * P) > 0 ? threads / (P * P) : 1);
+}
 template <int P>
 constexpr int mf_epb() {
-    return 256 / (P * P) > 32 ? 32 : (256 / (P * P) > 0 ? 256 / (P * P) : 1);
+    return mf_epb_for<P>(256);
 }
+constexpr int kMfTiles = 6;
+constexpr int mf_tile_threads(int t) { return t % 3 == 0 ? 256 : t % 3 == 1 ? 128 : 512; }
+constexpr bool mf_tile_pref(int t) { return t < 3; }
 
 template <class A>
 __device__ __forceinline__ typename A::T arith_of_f32(float v) {
@@ -92,7 +101,7 @@ mf_pre_kernel(int n_edges, const float* __restrict__ Minv, const TX* __restrict_
 }
 
 // The element pass (see above).  PLAIN: y is the input vector itself (TX), else M^{-1} x (A::T).
-template <int P, int EPB, class A, int MODE>
+template <int P, int EPB, class A, int MODE, bool PREF>
 __global__ void __launch_bounds__(EPB * P * P)
     mf_elem_kernel(Geom g, const typename A::T* __restrict__ S, const typename A::T* __restrict__ aux,
                    const typename A::T* __restrict__ EG, const double* __restrict__ tau_edge,
@@ -101,7 +110,7 @@ __global__ void __launch_bounds__(EPB * P * P)
     using T = typename A::T;
     using TO = MfVec<MODE>;
     constexpr int Np = P * P, NF = 3 * P;
-    constexpr bool kPref = Np <= 25;   // S^{-1} row held in registers
+    constexpr bool kPref = PREF && Np <= 25;   // S^{-1} row loaded into registers ahead of the traces
     if (done && *done) return;
     __shared__ SchurSmem<P, EPB, A> sm;
     const int le = threadIdx.x / Np, n = threadIdx.x % Np, i = n % P, j = n / P;
@@ -267,13 +276,40 @@ int sum_grid(size_t n) {
     return b > 0 ? (int)b : 1;
 }
 
+template <int P, class A, int MODE, int TILE>
+void mf_elem_launch(const Geom& g, const void* S, const void* aux, const void* EG, const double* tau, const void* yv,
+                    MfVec<MODE>* hm, MfVec<MODE>* hp, double beta, cudaStream_t s, const int* done) {
+    using T = typename A::T;
+    constexpr int EPB = mf_epb_for<P>(mf_tile_threads(TILE));
+    mf_elem_kernel<P, EPB, A, MODE, mf_tile_pref(TILE)><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(
+        g, static_cast<const T*>(S), static_cast<const T*>(aux), static_cast<const T*>(EG), tau, yv, hm, hp, beta,
+        done);
+}
+
+// the element pass with tile t (degrees 2..4 in the inner cycles; tile 0 elsewhere)
+template <int P, class A, int MODE>
+void mf_elem_tile(int t, const Geom& g, const void* S, const void* aux, const void* EG, const double* tau,
+                  const void* yv, MfVec<MODE>* hm, MfVec<MODE>* hp, double beta, cudaStream_t s, const int* done) {
+    if constexpr (MODE == kMfInner && P >= 3 && P <= 5) {
+        switch (t) {
+            case 1: return mf_elem_launch<P, A, MODE, 1>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
+            case 2: return mf_elem_launch<P, A, MODE, 2>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
+            case 3: return mf_elem_launch<P, A, MODE, 3>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
+            case 4: return mf_elem_launch<P, A, MODE, 4>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
+            case 5: return mf_elem_launch<P, A, MODE, 5>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
+            default: break;
+        }
+    }
+    mf_elem_launch<P, A, MODE, 0>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
+}
+
 // One product: [y = M^{-1} x,] the element pass, the edge sum.
 template <int P, class A, int MODE>
 cudaError_t mf_launch(const Geom& g, const MfOps& op, const void* S, const void* aux, const void* EG, const void* x,
                       const double* rhs, MfVec<MODE>* out, double beta, cudaStream_t s, const int* done) {
     using T = typename A::T;
     using TO = MfVec<MODE>;
-    constexpr int NF = 3 * P, EPB = mf_epb<P>();
+    constexpr int NF = 3 * P;
     const void* yv = x;
     if constexpr (MODE != kMfPlain) {
         constexpr int EPE = 256 / NF;
@@ -283,9 +319,7 @@ cudaError_t mf_launch(const Geom& g, const MfOps& op, const void* S, const void*
     }
     TO* hm = static_cast<TO*>(op.hm);
     TO* hp = static_cast<TO*>(op.hp);
-    mf_elem_kernel<P, EPB, A, MODE><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(
-        g, static_cast<const T*>(S), static_cast<const T*>(aux), static_cast<const T*>(EG), op.tau, yv, hm, hp, beta,
-        done);
+    mf_elem_tile<P, A, MODE>(MODE == kMfInner ? op.tile : 0, g, S, aux, EG, op.tau, yv, hm, hp, beta, s, done);
     const size_t n = (size_t)g.n_edges * NF;
     mf_sum_kernel<TO, MODE == kMfResidual><<<sum_grid(n), 256, 0, s>>>(n, hm, hp, rhs, out, done);
     count_launches(MODE != kMfPlain ? 3 : 2);
@@ -324,6 +358,47 @@ cudaError_t launch_mf_plain(const Geom& g, const MfOps& op, const double* x, dou
         default: return cudaErrorInvalidValue;
     }
 #undef CASE
+}
+
+// Time each tile of the inner cycles' element pass on the handle's own operators (one warm-up and
+// three timed products each, CUDA events on the stream; x and y are scratch trace vectors) and keep
+// the fastest in op.tile.  The tile changes no thread's arithmetic, only how elements share blocks.
+cudaError_t launch_mf_autotune(const Geom& g, MfOps& op, const float* x, float* y, double beta, cudaStream_t s,
+                               int* epb, int* prefetch) {
+    op.tile = 0;
+    *epb = 0;
+    *prefetch = 0;
+    if (g.P < 3 || g.P > 5) return cudaSuccess;
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return cudaGetLastError();
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return cudaGetLastError();
+    }
+    float best = 1e30f;
+    int best_t = 0;
+    cudaError_t err = cudaSuccess;
+    for (int t = 0; t < kMfTiles && err == cudaSuccess; ++t) {
+        op.tile = t;
+        err = launch_mf_inner(g, op, x, y, beta, s);
+        if (err == cudaSuccess) err = cudaEventRecord(a, s);
+        for (int k = 0; k < 3 && err == cudaSuccess; ++k) err = launch_mf_inner(g, op, x, y, beta, s);
+        if (err == cudaSuccess) err = cudaEventRecord(b, s);
+        if (err == cudaSuccess) err = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, a, b);
+        if (err == cudaSuccess && ms < best) {
+            best = ms;
+            best_t = t;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    op.tile = best_t;
+    const int P = g.P, th = mf_tile_threads(best_t);
+    *epb = th / (P * P) > 32 ? 32 : (th / (P * P) > 0 ? th / (P * P) : 1);
+    *prefetch = mf_tile_pref(best_t) ? 1 : 0;
+    return err;
 }
 
 cudaError_t launch_mf_back(const Geom& g, const float* Minv32, const double* x, double* y, cudaStream_t s) {

@@ -53,7 +53,8 @@ class Stats(ctypes.Structure):
                 ("last_krylov_iterations", ctypes.c_int), ("last_rel_residual", ctypes.c_double),
                 ("mass", ctypes.c_double), ("kernel_launches", ctypes.c_longlong), ("time", ctypes.c_double),
                 ("last_guess_order", ctypes.c_int), ("local_tile_condense", ctypes.c_int),
-                ("local_tile_recover", ctypes.c_int)]
+                ("local_tile_recover", ctypes.c_int), ("trace_tile", ctypes.c_int),
+                ("trace_tile_prefetch", ctypes.c_int)]
 
 
 _lib = None

@@ -162,3 +162,30 @@ def test_bitwise_reproducible():
         m, qa, _ = _steps("large", 32, 3, 3, **MF)
         outs.append(qa)
     assert np.array_equal(outs[0], outs[1])
+
+
+def test_autotuned_tiles_change_no_result():
+    """On a mesh of >= 4096 elements the element pass's tile and the Schur kernels' tiles are picked
+    at create by timing.  Whichever tiles win, the operator matches the assembled FP64 matrix and
+    three mixed-form steps stay within the solver tolerance of the assembled route."""
+    N, k = 64, 3
+    m, h, hu, hv, b = user_state(N, k, "large")
+    x = rng.standard_normal((m.n_edges, 3, m.P))
+    with hd.Sim(N, k, 0.01, bottom=b, g=W.G, H0=W.H0, **MF) as s:
+        st = s.stats()
+        assert st["trace_tile"] in (8, 16, 32) and st["trace_tile_prefetch"] in (0, 1)
+        assert st["local_tile_condense"] in (8, 16, 32) and st["local_tile_recover"] in (8, 16, 32)
+        got = s.trace_apply(x)
+        s.set_state(h, hu, hv)
+        s.step(3)
+        tuned = s.get_state()
+    with hd.Sim(N, k, 0.01, bottom=b, g=W.G, H0=W.H0) as s:
+        ref = s.trace_apply(x)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    with hd.Sim(N, k, 0.01, bottom=b, g=W.G, H0=W.H0, **ASSEMBLED) as s:
+        s.set_state(h, hu, hv)
+        s.step(3)
+        assembled = s.get_state()
+    B = W.H0 - b
+    for a_, c_ in zip((tuned[0] - B, tuned[1], tuned[2]), (assembled[0] - B, assembled[1], assembled[2])):
+        assert np.linalg.norm(a_ - c_) <= 1e-7 * np.linalg.norm(c_)
