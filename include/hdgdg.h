@@ -332,6 +332,39 @@ hdgdg_status hdgdg_measure_fp64_tflops(double* tflops);
  * failure, EINVAL for NULL. */
 hdgdg_status hdgdg_measure_conversion_rates(double* hardware_per_s, double* integer_per_s);
 
+/* ---- uneven ensembles ------------------------------------------------------------------------
+ * Many independent instances of different mesh sizes and degrees advanced together (the
+ * batched-ensemble workload; the paper runs one instance at a time).  Members sharing (N, k)
+ * form a group; every geometry-dependent kernel of a time step -- the DG residual, the
+ * condensation, the matrix-free trace operator's passes, the recovery -- runs as ONE persistent
+ * launch over all groups, walking a device work list of (group, block) items, and the stage
+ * combinations and Krylov vector operations cover the whole ensemble as one vector; each time step
+ * is one replayed CUDA graph (see host_steps).  The members' trace systems form one
+ * block-diagonal system solved by one GMRES whose stop test is on the whole ensemble's residual,
+ * so a member's result agrees with its lone run to the solver tolerance, not bit for bit.
+ * base: the shared configuration (g, H0, scheme ARS2 or ARS3, Krylov options, guess order); it
+ * must select the mixed form with FP32-pair local solves and the matrix-free trace operator
+ * (precision = HDGDG_MIXED, local_precision = HDGDG_LOCAL_F32X2, trace_operator = 1), a periodic
+ * boundary and the full method (linear_only = 0); its n_side, degree_k, dt, batch are ignored.
+ * Member m: n_side[m] >= 2, 2 <= degree_k[m] <= 4, its own time step dt[m] > 0 and bottom
+ * bottom_b[m] (host [N^2][(k+1)^2]; bottom_b or an entry may be NULL = flat); at most 32 distinct
+ * (N, k).  States are host arrays [N^2][(k+1)^2] per member as for hdgdg_set_state.
+ * set_state of any member drops the ensemble's solver history (the next solves start from zero)
+ * and restarts its counters; step advances every member by n_steps of its own time step.  Errors
+ * as for the lone handle; EINVAL for a configuration outside the above. */
+typedef struct hdgdg_ensemble hdgdg_ensemble;
+hdgdg_status hdgdg_ensemble_create(const hdgdg_config* base, int n_members, const int* n_side, const int* degree_k,
+                                   const double* dt, const double* const* bottom_b, void* cuda_stream,
+                                   hdgdg_ensemble** out);
+hdgdg_status hdgdg_ensemble_set_state(hdgdg_ensemble* ens, int member, const double* h, const double* hu,
+                                      const double* hv);
+hdgdg_status hdgdg_ensemble_step(hdgdg_ensemble* ens, int n_steps);
+hdgdg_status hdgdg_ensemble_get_state(hdgdg_ensemble* ens, int member, double* h, double* hu, double* hv);
+/* Counters of the whole ensemble (its mass field is 0: per-member masses follow from get_state). */
+hdgdg_status hdgdg_ensemble_get_stats(hdgdg_ensemble* ens, hdgdg_stats* out);
+const char* hdgdg_ensemble_last_error(const hdgdg_ensemble* ens);
+void hdgdg_ensemble_destroy(hdgdg_ensemble* ens);
+
 /* ---- allocation-free entry point ------------------------------------------------- */
 
 /* Mass sum_e J sum_ij w_i w_j phi_eta of ONE instance's state -- the mass hdgdg_get_stats

@@ -330,6 +330,7 @@ struct hdgdg_sim {
     double *gvec = nullptr, *xt = nullptr, *lam = nullptr, *w = nullptr, *V = nullptr, *fface = nullptr;
     float *Stil32 = nullptr, *V32 = nullptr, *w32 = nullptr;   // mixed precision only
     float* Stil_lo = nullptr;   // residual_f32x2: S~ = Stil32 + Stil_lo
+    const EnsHost* ens = nullptr;   // an ensemble's super-handle: its group table (kernels walk every group)
     MfOps mf;                   // trace_operator = 1: the matrix-free operator's data
     int trace_tile = 0, trace_prefetch = 0;   // its autotuned element-pass tile (0: default)
     float* Minv32 = nullptr;    // its FP32 block-Jacobi inverse
@@ -531,7 +532,8 @@ cudaError_t cycle_enqueue(hdgdg_sim* sim, const double* g, cudaStream_t st, bool
         {
             TimedGroup tg(sim, HDGDG_KT_SPMV, j);
             if constexpr (kMixed) {
-                if (matrix_free(&sim->cfg)) e = launch_mf_inner(sim->g, sim->mf, Vj, w, beta_of(sim), st, done);
+                if (sim->ens) e = launch_ens_mf_inner(*sim->ens, sim->mf, n, Vj, w, st, done);
+                else if (matrix_free(&sim->cfg)) e = launch_mf_inner(sim->g, sim->mf, Vj, w, beta_of(sim), st, done);
                 else
                     e = launch_spmv_pre(sim->g, St, sim->Scol, Vj, w, st, done,
                                         sim->cfg.spmv_kernel == 1 ? spmv_error(sim) : nullptr);
@@ -549,7 +551,9 @@ cudaError_t cycle_enqueue(hdgdg_sim* sim, const double* g, cudaStream_t st, bool
     if (e == cudaSuccess) e = launch_gmres_update(V, n, ctl, sim->xt, n, st);
     // the true residual w = g - S~ x~ that ends the cycle, and ||w||^2
     if (kMixed && matrix_free(&sim->cfg)) {   // matrix-free in FP32-pair arithmetic, then the norm
-        if (e == cudaSuccess) e = launch_mf_residual(sim->g, sim->mf, sim->xt, g, sim->w, beta_of(sim), st);
+        if (e == cudaSuccess)
+            e = sim->ens ? launch_ens_mf_residual(*sim->ens, sim->mf, n, sim->xt, g, sim->w, st)
+                         : launch_mf_residual(sim->g, sim->mf, sim->xt, g, sim->w, beta_of(sim), st);
         if (e == cudaSuccess) e = launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st);
     } else if (kMixed && sim->Stil_lo) {   // one fused FP32-pair pass
         if (e == cudaSuccess)
@@ -843,7 +847,8 @@ cudaError_t solve_enqueue_graph(hdgdg_sim* sim, const double* g, double* qhat, i
     }
     if (e == cudaSuccess) e = launch_solve_end(sim->ctl, sim->sctl, sim->sstats, st);
     if (e == cudaSuccess) {
-        if (kMixed && matrix_free(&sim->cfg)) e = launch_mf_back(sim->g, sim->Minv32, sim->xt, qhat, st);
+        if (sim->ens) e = launch_ens_mf_back(*sim->ens, sim->xt, qhat, st);
+        else if (kMixed && matrix_free(&sim->cfg)) e = launch_mf_back(sim->g, sim->Minv32, sim->xt, qhat, st);
         else e = launch_block_diag(sim->g, sim->Minv, sim->xt, qhat, st, sim->minv_pairs);
     }
     if (e == cudaSuccess && stage >= 0 && order > 0) {   // x~ and S~ x~ = g - r into the slot that becomes newest
@@ -875,18 +880,23 @@ cudaError_t step_enqueue_graph(hdgdg_sim* sim, cudaStream_t st, StepGraph& sg) {
             }
             e = launch_combine(n3, sim->q, t, sim->R1, nullptr, st);
             if (e == cudaSuccess)
-                e = launch_condense(sim->g, sim->ops, sim->R1, sim->phiB, sim->tau, sim->Z, sim->gvec, st, 0.0);
+                e = sim->ens ? launch_ens_condense(*sim->ens, sim->R1, sim->Z, sim->gvec, st)
+                             : launch_condense(sim->g, sim->ops, sim->R1, sim->phiB, sim->tau, sim->Z, sim->gvec, st, 0.0);
             if (e == cudaSuccess) {
                 if (sim->cfg.precision == HDGDG_MIXED) e = solve_enqueue_graph<float>(sim, sim->gvec, sim->lam, i, st, sg);
                 else e = solve_enqueue_graph<double>(sim, sim->gvec, sim->lam, i, st, sg);
             }
             if (e == cudaSuccess)
-                e = launch_recover(sim->g, sim->ops, sim->Z, sim->R1, sim->tau, sim->lam, beta_of(sim),
-                                   1.0 / sim->a_ii, sim->Qs, sim->Ls[i], st);
+                e = sim->ens ? launch_ens_recover(*sim->ens, sim->Z, sim->R1, sim->lam, 1.0 / sim->a_ii, sim->Qs,
+                                                  sim->Ls[i], st)
+                             : launch_recover(sim->g, sim->ops, sim->Z, sim->R1, sim->tau, sim->lam, beta_of(sim),
+                                              1.0 / sim->a_ii, sim->Qs, sim->Ls[i], st);
             Qi = sim->Qs;
         }
         if (!sim->cfg.linear_only && e == cudaSuccess) {
-            if (sim->cfg.precision == HDGDG_MIXED)
+            if (sim->ens)
+                e = launch_ens_dg_nl_f32(*sim->ens, Qi, sim->fface, sim->NLs[i], st);
+            else if (sim->cfg.precision == HDGDG_MIXED)
                 e = launch_dg_nl_f32(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st, 0.0);
             else
                 e = launch_dg_nl(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st, 0.0);
@@ -928,6 +938,7 @@ void drop_step_graphs(hdgdg_sim* sim) {
 // Whole-step graphs serve implicit schemes whose boundary data do not depend on time, with the
 // kernel-class timers off (their event records cannot sit inside a conditional node's body).
 bool use_step_graph(const hdgdg_sim* sim) {
+    if (sim->ens) return true;   // an ensemble's steps are always replayed graphs
     return !sim->cfg.host_steps && !sim->timing && !explicit_scheme(&sim->cfg) && !sim->g.dirichlet &&
            sim->body_stream != nullptr;
 }
@@ -1707,6 +1718,271 @@ hdgdg_status hdgdg_measure_fp64_tflops(double* tflops) {
 hdgdg_status hdgdg_measure_conversion_rates(double* hardware_per_s, double* integer_per_s) {
     if (!hardware_per_s || !integer_per_s) return HDGDG_EINVAL;
     return measure_conversions(hardware_per_s, integer_per_s) == cudaSuccess ? HDGDG_OK : HDGDG_ECUDA;
+}
+
+}  // extern "C"
+
+// ---- uneven ensembles ---------------------------------------------------------------------------
+// Members of different mesh sizes and degrees advanced together: the members are grouped by
+// (N, k) into batched handles, which hold each group's geometry and operators; a super-handle
+// holds the ensemble's vectors (the groups one after another) and runs the time step of Algorithm
+// 1 as one replayed graph whose geometry-dependent kernels each walk every group in one persistent
+// launch (EnsTable), while the stage combinations and the Krylov vector work cover the whole
+// ensemble as one vector.  The trace systems form one block-diagonal system solved by one GMRES,
+// so a member's result agrees with its lone run to the solver tolerance.
+struct hdgdg_ensemble {
+    hdgdg_sim* sup = nullptr;
+    std::vector<hdgdg_sim*> groups;
+    std::vector<int> member_group, member_pos;   // member -> (group, instance within the group)
+    std::vector<std::vector<double>> phiB;       // per member: phi_B at its nodes (host)
+    EnsHost host;
+    EnsGroup* d_grp = nullptr;
+    std::string err;
+};
+
+namespace {
+
+hdgdg_status ens_fail(hdgdg_ensemble* E, hdgdg_status st, const char* msg) {
+    if (E) E->err = msg;
+    return st;
+}
+
+// The super-handle: vectors for the whole ensemble, no operators of its own.
+hdgdg_status ens_super(hdgdg_ensemble* E, const hdgdg_config* base, size_t n_total, size_t nt_total,
+                       int edges_total, void* stream) {
+    hdgdg_sim* sim = new (std::nothrow) hdgdg_sim();
+    if (!sim) return HDGDG_ENOMEM;
+    E->sup = sim;
+    sim->cfg = *base;
+    sim->cfg.batch = 1;
+    sim->cfg.dt_per_instance = nullptr;
+    scheme_tables(base->scheme, sim->A, sim->At, sim->b, sim->bt, &sim->s);
+    sim->a_ii = sim->At[1][1];
+    Plan& p = sim->plan;
+    p.n = n_total;
+    p.nt = nt_total;
+    p.m = restart_of(base);
+    p.s = sim->s;
+    sim->g = host_geom(2, base->degree_k);   // not used by the ensemble's launches
+    if (stream) {
+        sim->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        CU(cudaStreamCreateWithFlags(&sim->stream, cudaStreamNonBlocking));
+        sim->own_stream = true;
+    }
+    for (double** v : {&sim->q, &sim->q_new, &sim->R1, &sim->Z, &sim->Qs}) TRY(dalloc(sim, v, 3 * p.n));
+    for (int i = 0; i < p.s; ++i) {
+        TRY(dalloc(sim, &sim->NLs[i], 3 * p.n));
+        TRY(dalloc(sim, &sim->Ls[i], 3 * p.n));
+        CU(cudaMemsetAsync(sim->NLs[i], 0, 3 * p.n * sizeof(double), sim->stream));
+        CU(cudaMemsetAsync(sim->Ls[i], 0, 3 * p.n * sizeof(double), sim->stream));
+    }
+    for (double** v : {&sim->gvec, &sim->xt, &sim->lam, &sim->w, &sim->fface}) TRY(dalloc(sim, v, p.nt));
+    for (int i = 0; i < p.s; ++i)
+        for (int h = 0; h < guess_order(base); ++h) {
+            TRY(dalloc(sim, &sim->xhist[i][h], p.nt));
+            TRY(dalloc(sim, &sim->yhist[i][h], p.nt));
+        }
+    TRY(dalloc(sim, &sim->V32, (size_t)(p.m + 1) * p.nt));
+    TRY(dalloc(sim, &sim->w32, p.nt));
+    TRY(dalloc(sim, &sim->red, reduction_scratch_doubles(p.m, edges_total, 3)));
+    CU(cudaMemset(sim->red, 0, sizeof(double)));
+    TRY(dalloc(sim, &sim->mred, mass_scratch_doubles()));
+    TRY(dalloc(sim, &sim->dvals, 4 * (size_t)(p.m + 2) + 16));
+    TRY(dalloc(sim, &sim->flags, 16));
+    TRY(dalloc(sim, &sim->ctl, 1));
+    TRY(dalloc(sim, &sim->sctl, 1));
+    TRY(dalloc(sim, &sim->sstats, 1));
+    CU(cudaMallocHost(&sim->hbuf, (4 * (size_t)(p.m + 2) + 16) * sizeof(double)));
+    CU(cudaStreamCreateWithFlags(&sim->body_stream, cudaStreamNonBlocking));
+    double *ybuf = nullptr, *hm = nullptr, *hp = nullptr;
+    TRY(dalloc(sim, &ybuf, p.nt));
+    TRY(dalloc(sim, &hm, p.nt));
+    TRY(dalloc(sim, &hp, p.nt));
+    sim->mf.ybuf = ybuf;
+    sim->mf.hm = hm;
+    sim->mf.hp = hp;
+    CU(cudaMemsetAsync(sim->flags, 0, 16, sim->stream));
+    CU(cudaStreamSynchronize(sim->stream));
+    return HDGDG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hdgdg_status hdgdg_ensemble_create(const hdgdg_config* base, int n_members, const int* n_side, const int* degree_k,
+                                   const double* dt, const double* const* bottom_b, void* cuda_stream,
+                                   hdgdg_ensemble** out) {
+    if (!out) return HDGDG_EINVAL;
+    *out = nullptr;
+    if (!base || n_members < 1 || !n_side || !degree_k || !dt) return HDGDG_EINVAL;
+    if (base->precision != HDGDG_MIXED || base->local_precision != HDGDG_LOCAL_F32X2 || base->trace_operator != 1 ||
+        base->local_dense || (base->scheme != HDGDG_ARS2 && base->scheme != HDGDG_ARS3) ||
+        base->boundary != HDGDG_PERIODIC || base->linear_only)
+        return HDGDG_EINVAL;
+    hdgdg_ensemble* E = new (std::nothrow) hdgdg_ensemble();
+    if (!E) return HDGDG_ENOMEM;
+    *out = E;
+    // groups of equal (N, k), in order of first appearance
+    std::vector<std::pair<int, int>> keys;
+    std::vector<std::vector<int>> members;
+    for (int i = 0; i < n_members; ++i) {
+        if (n_side[i] < 2 || degree_k[i] < 2 || degree_k[i] > 4 || !(dt[i] > 0.0) || !std::isfinite(dt[i]))
+            return ens_fail(E, HDGDG_EINVAL, "ensemble members need N >= 2, 2 <= k <= 4 and dt > 0");
+        int gi = -1;
+        for (size_t k = 0; k < keys.size(); ++k)
+            if (keys[k].first == n_side[i] && keys[k].second == degree_k[i]) gi = (int)k;
+        if (gi < 0) {
+            if ((int)keys.size() == kEnsMaxGroups) return ens_fail(E, HDGDG_EINVAL, "more than 32 (N, k) groups");
+            keys.push_back({n_side[i], degree_k[i]});
+            members.emplace_back();
+            gi = (int)keys.size() - 1;
+        }
+        E->member_group.push_back(gi);
+        E->member_pos.push_back((int)members[gi].size());
+        members[gi].push_back(i);
+    }
+    // one batched handle per group: geometry, bottoms, per-member time steps, operators
+    size_t off3 = 0, offt = 0, n_total = 0, nt_total = 0;
+    int edges_total = 0;
+    E->phiB.resize(n_members);
+    for (size_t gi = 0; gi < keys.size(); ++gi) {
+        const int N = keys[gi].first, k = keys[gi].second, B = (int)members[gi].size();
+        const size_t Np = (size_t)(k + 1) * (k + 1), nel = (size_t)N * N;
+        std::vector<double> bot(B * nel * Np, 0.0), dts(B);
+        double dtmax = 0.0;
+        for (int j = 0; j < B; ++j) {
+            const int m = members[gi][j];
+            dts[j] = dt[m];
+            dtmax = std::max(dtmax, dt[m]);
+            if (bottom_b && bottom_b[m]) std::memcpy(&bot[j * nel * Np], bottom_b[m], nel * Np * sizeof(double));
+            E->phiB[m].resize(nel * Np);
+            for (size_t t = 0; t < nel * Np; ++t) E->phiB[m][t] = base->g * (base->H0 - bot[j * nel * Np + t]);
+        }
+        hdgdg_config c = *base;
+        c.n_side = N;
+        c.degree_k = k;
+        c.batch = B;
+        c.dt = dtmax;
+        c.dt_per_instance = dts.data();
+        c.host_steps = 1;
+        hdgdg_sim* gs = nullptr;
+        const hdgdg_status st = hdgdg_create(&c, bot.data(), cuda_stream, &gs);
+        E->groups.push_back(gs);
+        if (st != HDGDG_OK) return ens_fail(E, st, gs ? gs->err.c_str() : "group create failed");
+        EnsGroup& G = E->host.h[gi];
+        G.g = gs->g;
+        G.off3 = off3;
+        G.offt = offt;
+        G.dt = gs->cfg.dt;
+        G.beta = beta_of(gs);
+        G.phiB = gs->phiB;
+        G.tau = gs->tau;
+        G.S2 = gs->ops.S;
+        G.aux2 = gs->ops.aux;
+        G.EG2 = gs->ops.EG;
+        G.S32 = gs->mf.S32;
+        G.aux32 = gs->mf.aux32;
+        G.EG32 = gs->mf.EG32;
+        G.Minv32 = gs->Minv32;
+        off3 += 3 * gs->plan.n;
+        offt += gs->plan.nt;
+        n_total += gs->plan.n;
+        nt_total += gs->plan.nt;
+        edges_total += gs->g.n_edges;
+    }
+    E->host.ngroups = (int)keys.size();
+    hdgdg_status st = ens_super(E, base, n_total, nt_total, edges_total, cuda_stream);
+    if (st != HDGDG_OK) return ens_fail(E, st, E->sup ? E->sup->err.c_str() : "ensemble vectors");
+    if (cudaMalloc(&E->d_grp, E->host.ngroups * sizeof(EnsGroup)) != cudaSuccess) {
+        cudaGetLastError();
+        return ens_fail(E, HDGDG_ENOMEM, "ensemble group table");
+    }
+    if (cudaMemcpy(E->d_grp, E->host.h, E->host.ngroups * sizeof(EnsGroup), cudaMemcpyHostToDevice) != cudaSuccess)
+        return ens_fail(E, HDGDG_ECUDA, "ensemble group table copy");
+    E->host.d_grp = E->d_grp;
+    E->sup->ens = &E->host;
+    return HDGDG_OK;
+}
+
+void hdgdg_ensemble_destroy(hdgdg_ensemble* E) {
+    if (!E) return;
+    if (E->sup) hdgdg_destroy(E->sup);
+    for (hdgdg_sim* g : E->groups) hdgdg_destroy(g);
+    if (E->d_grp) cudaFree(E->d_grp);
+    delete E;
+}
+
+const char* hdgdg_ensemble_last_error(const hdgdg_ensemble* E) {
+    if (!E) return "no ensemble";
+    if (!E->err.empty()) return E->err.c_str();
+    return E->sup ? E->sup->err.c_str() : "";
+}
+
+hdgdg_status hdgdg_ensemble_set_state(hdgdg_ensemble* E, int member, const double* h, const double* hu,
+                                      const double* hv) {
+    if (!E || !E->sup || member < 0 || member >= (int)E->member_group.size() || !h || !hu || !hv)
+        return ens_fail(E, HDGDG_EINVAL, "bad argument to ensemble_set_state");
+    const EnsGroup& G = E->host.h[E->member_group[member]];
+    const size_t nm = (size_t)G.g.n_el_inst * G.g.Np, ng = (size_t)G.g.n_el * G.g.Np;
+    const double gacc = E->sup->cfg.g;
+    const std::vector<double>& pb = E->phiB[member];
+    std::vector<double> q(3 * nm);
+    for (size_t t = 0; t < nm; ++t) {
+        const double phi = gacc * h[t];
+        const double U = gacc * hu[t], V = gacc * hv[t];
+        if (!std::isfinite(phi) || !std::isfinite(U) || !std::isfinite(V) || !(phi > 0.0))
+            return ens_fail(E, HDGDG_ENONFINITE, "state has a non-finite value or non-positive depth");
+        q[t] = phi - pb[t];
+        q[nm + t] = U;
+        q[2 * nm + t] = V;
+    }
+    hdgdg_sim* sim = E->sup;
+    const size_t base = G.off3 + (size_t)E->member_pos[member] * nm;
+    for (int c = 0; c < 3; ++c)
+        CU(cudaMemcpyAsync(sim->q + base + c * ng, q.data() + c * nm, nm * sizeof(double), cudaMemcpyHostToDevice,
+                           sim->stream));
+    CU(cudaStreamSynchronize(sim->stream));
+    sim->have_state = true;
+    sim->stats = hdgdg_stats{};
+    sim->t = 0.0;
+    for (int i = 0; i < kMaxStages; ++i) sim->n_hist[i] = 0;   // the ensemble's solver history starts afresh
+    return HDGDG_OK;
+}
+
+hdgdg_status hdgdg_ensemble_get_state(hdgdg_ensemble* E, int member, double* h, double* hu, double* hv) {
+    if (!E || !E->sup || member < 0 || member >= (int)E->member_group.size() || !h || !hu || !hv)
+        return ens_fail(E, HDGDG_EINVAL, "bad argument to ensemble_get_state");
+    const EnsGroup& G = E->host.h[E->member_group[member]];
+    const size_t nm = (size_t)G.g.n_el_inst * G.g.Np, ng = (size_t)G.g.n_el * G.g.Np;
+    hdgdg_sim* sim = E->sup;
+    std::vector<double> q(3 * nm);
+    const size_t base = G.off3 + (size_t)E->member_pos[member] * nm;
+    for (int c = 0; c < 3; ++c)
+        CU(cudaMemcpyAsync(q.data() + c * nm, sim->q + base + c * ng, nm * sizeof(double), cudaMemcpyDeviceToHost,
+                           sim->stream));
+    CU(cudaStreamSynchronize(sim->stream));
+    const double gacc = sim->cfg.g;
+    const std::vector<double>& pb = E->phiB[member];
+    for (size_t t = 0; t < nm; ++t) {
+        h[t] = (q[t] + pb[t]) / gacc;
+        hu[t] = q[nm + t] / gacc;
+        hv[t] = q[2 * nm + t] / gacc;
+    }
+    return HDGDG_OK;
+}
+
+hdgdg_status hdgdg_ensemble_step(hdgdg_ensemble* E, int n_steps) {
+    if (!E || !E->sup) return HDGDG_EINVAL;
+    return hdgdg_step(E->sup, n_steps);
+}
+
+hdgdg_status hdgdg_ensemble_get_stats(hdgdg_ensemble* E, hdgdg_stats* out) {
+    if (!E || !E->sup || !out) return ens_fail(E, HDGDG_EINVAL, "bad argument to ensemble_get_stats");
+    *out = E->sup->stats;
+    out->mass = 0.0;   // (per-member masses: hdgdg_ensemble_get_state; the ensemble reports none)
+    return HDGDG_OK;
 }
 
 }  // extern "C"

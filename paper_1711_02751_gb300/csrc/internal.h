@@ -382,6 +382,47 @@ cudaError_t launch_cgs2_tail(const float* V, size_t ldv, int nv, const double* h
                              GmresCtl* ctl, int j, int m, bool twice, cudaStream_t s, const int* done = nullptr);
 
 
+// ---- uneven ensembles: one persistent launch per kernel class over many mesh groups ----------
+// A group is a batch of instances of one mesh size and degree (its own geometry, operators and
+// time step); the ensemble's vectors hold the groups one after another (group-major), each
+// group's slice laid out as a lone handle's.  A launch covers every group: its work list is the
+// concatenation of the groups' blocks, and a persistent grid walks it, each block taking items
+// (group, block of that group) until the list is done.
+constexpr int kEnsMaxGroups = 32;
+struct EnsGroup {
+    Geom g;                     // the group's mesh (a batch of same-size instances)
+    size_t off3, offt;          // its slice: state vectors (3 fields), trace vectors
+    double dt, beta;            // its time step and lift factor dt a_ii (2/h) / w_0
+    const double* phiB;
+    const double* tau;
+    const void *S2, *aux2, *EG2;          // Schur-complement operators as FP32 pairs
+    const float *S32, *aux32, *EG32;      // and as FP32 (the inner cycles)
+    const float* Minv32;                  // block-Jacobi inverse, FP32
+};
+struct EnsTable {               // one launch: the groups and the first work item of each
+    const EnsGroup* grp;        // device array [ngroups]
+    int ngroups;
+    int start[kEnsMaxGroups + 1];
+};
+struct EnsHost {                // host copy of the group list, for building launch tables
+    const EnsGroup* d_grp = nullptr;
+    int ngroups = 0;
+    EnsGroup h[kEnsMaxGroups];
+};
+// DG residual of the nonlinear part in FP32 arithmetic over every group (face pass, element pass)
+cudaError_t launch_ens_dg_nl_f32(const EnsHost& E, const double* q, double* fface, double* out, cudaStream_t s);
+// condensation: Z = A^{-1} R1 (FP32-pair Schur route), g = -C Z
+cudaError_t launch_ens_condense(const EnsHost& E, const double* R1, double* Z, double* gvec, cudaStream_t s);
+// recovery: Q = Z + beta A^{-1}(tau qhat), Lst = (Q - R1)/a_ii
+cudaError_t launch_ens_recover(const EnsHost& E, const double* Z, const double* R1, const double* qhat,
+                               double inv_aii, double* Q, double* Lst, cudaStream_t s);
+// matrix-free trace operator over every group: inner (FP32), residual (FP32 pairs), back-transformation
+cudaError_t launch_ens_mf_inner(const EnsHost& E, const MfOps& scratch, size_t nt, const float* x, float* y,
+                                cudaStream_t s, const int* done);
+cudaError_t launch_ens_mf_residual(const EnsHost& E, const MfOps& scratch, size_t nt, const double* x,
+                                   const double* rhs, double* w, cudaStream_t s);
+cudaError_t launch_ens_mf_back(const EnsHost& E, const double* x, double* y, cudaStream_t s);
+
 // Whole-step graphs (kernels_ctl.cu): the trace solve's decisions taken on the device.
 struct SolveCtl {
     double bnorm, tol, rnorm;

@@ -11,6 +11,7 @@
 // tau_L* = max_pm sqrt(phi_B) is the per-edge-node tau_hat the library precomputes.
 #include <atomic>
 
+#include "ens.h"
 #include "fastcvt.h"
 #include "internal.h"
 
@@ -42,11 +43,11 @@ __device__ __forceinline__ void nl_flux(Tc ph, Tc U, Tc V, Tc phiB, Tc* fxU, Tc*
 //   the residual of the explicit RK DG scheme the paper compares with.
 //   Tc: arithmetic type (double; float for the mixed form's residual), storage stays FP64.
 template <int P, bool FULL, typename Tc>
-__global__ void __launch_bounds__(256)
-dg_face_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ phiB,
-               const double* __restrict__ tau_edge, double* __restrict__ fface, double t_bc) {
+__device__ __forceinline__ void dg_face_body(int bid, const Geom& g, const double* __restrict__ q,
+                                             const double* __restrict__ phiB, const double* __restrict__ tau_edge,
+                                             double* __restrict__ fface, double t_bc) {
     constexpr int Np = P * P;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = bid * 256 + threadIdx.x;
     if (t >= g.n_edges * P) return;
     const int r = t / P, b = t % P;
     int em, fm, ep, fp;
@@ -105,12 +106,19 @@ dg_face_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ 
     out[(xedge ? 2 : 1) * P + b] = to_f64(ft);
 }
 
+template <int P, bool FULL, typename Tc>
+__global__ void __launch_bounds__(256)
+dg_face_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ phiB,
+               const double* __restrict__ tau_edge, double* __restrict__ fface, double t_bc) {
+    dg_face_body<P, FULL, Tc>(blockIdx.x, g, q, phiB, tau_edge, fface, t_bc);
+}
+
 // Element pass: volume term from the nodal F_NL (shared memory), minus the lifted face fluxes.
 // FULL = true: the whole flux F and the source s = (0, phi_eta d_x phi_B, phi_eta d_y phi_B).
 template <int P, bool FULL, typename Tc>
-__global__ void __launch_bounds__(DgTile<P>::EPB * P * P)
-dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ phiB,
-                 const double* __restrict__ fface, double scale, double* __restrict__ out) {
+__device__ __forceinline__ void dg_volume_body(int bid, const Geom& g, const double* __restrict__ q,
+                                               const double* __restrict__ phiB, const double* __restrict__ fface,
+                                               double scale, double* __restrict__ out) {
     constexpr int Np = P * P;
     constexpr int EPB = DgTile<P>::EPB;
     // fxU, fxV, fyU, fyV (and, FULL: U, V, phi_B) per element, each element's row padded by one
@@ -127,8 +135,8 @@ dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict_
 
     const int le = threadIdx.x / Np;
     const int n = threadIdx.x % Np;
-    const int e = blockIdx.x * EPB + le;
-    const bool live = e < g.n_el;
+    const int e = bid * EPB + le;
+    const bool live = le < EPB && e < g.n_el;
     const size_t fs = (size_t)g.n_el * Np;
     const int i = n % P, j = n / P;
 
@@ -191,6 +199,13 @@ dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict_
     out[o] = sc * to_f64(rph);
     out[fs + o] = sc * to_f64(rU);
     out[2 * fs + o] = sc * to_f64(rV);
+}
+
+template <int P, bool FULL, typename Tc>
+__global__ void __launch_bounds__(DgTile<P>::EPB * P * P)
+dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ phiB,
+                 const double* __restrict__ fface, double scale, double* __restrict__ out) {
+    dg_volume_body<P, FULL, Tc>(blockIdx.x, g, q, phiB, fface, scale, out);
 }
 
 __global__ void combine_kernel(size_t n, const double* __restrict__ base, CombineTerms t,
@@ -289,7 +304,49 @@ int grid_for(size_t n, int threads) {
     return b > 0 ? (int)b : 1;
 }
 
+// ---- ensembles: every group's face and element passes in one persistent launch each ---------------
+template <int P>
+__device__ __forceinline__ void ens_face_item(const EnsGroup& G, int bid, const double* q, double* fface) {
+    dg_face_body<P, false, float>(bid, G.g, q + G.off3, G.phiB, G.tau, fface + G.offt, 0.0);
+}
+
+__global__ void __launch_bounds__(256) ens_dg_face_kernel(EnsTable t, const double* __restrict__ q,
+                                                          double* __restrict__ fface) {
+    ens_walk(t, [&](const EnsGroup& G, int bid) {
+        switch (G.g.P) {
+            case 3: ens_face_item<3>(G, bid, q, fface); break;
+            case 4: ens_face_item<4>(G, bid, q, fface); break;
+            case 5: ens_face_item<5>(G, bid, q, fface); break;
+            default: break;
+        }
+    });
+}
+
+__global__ void __launch_bounds__(256) ens_dg_volume_kernel(EnsTable t, const double* __restrict__ q,
+                                                            const double* __restrict__ fface, double* __restrict__ out) {
+    ens_walk(t, [&](const EnsGroup& G, int bid) {
+        switch (G.g.P) {
+            case 3: dg_volume_body<3, false, float>(bid, G.g, q + G.off3, G.phiB, fface + G.offt, G.dt, out + G.off3); break;
+            case 4: dg_volume_body<4, false, float>(bid, G.g, q + G.off3, G.phiB, fface + G.offt, G.dt, out + G.off3); break;
+            case 5: dg_volume_body<5, false, float>(bid, G.g, q + G.off3, G.phiB, fface + G.offt, G.dt, out + G.off3); break;
+            default: break;
+        }
+    });
+}
+
 }  // namespace
+
+cudaError_t launch_ens_dg_nl_f32(const EnsHost& E, const double* q, double* fface, double* out, cudaStream_t s) {
+    const EnsTable tf = ens_table(E, [](const EnsGroup& G) { return (G.g.n_edges * G.g.P + 255) / 256; });
+    const EnsTable tv = ens_table(E, [](const EnsGroup& G) {
+        const int epb = 256 / G.g.Np;
+        return (G.g.n_el + epb - 1) / epb;
+    });
+    ens_dg_face_kernel<<<ens_grid(ens_dg_face_kernel, tf.start[tf.ngroups]), 256, 0, s>>>(tf, q, fface);
+    ens_dg_volume_kernel<<<ens_grid(ens_dg_volume_kernel, tv.start[tv.ngroups]), 256, 0, s>>>(tv, q, fface, out);
+    count_launches(2);
+    return cudaGetLastError();
+}
 
 namespace {
 std::atomic<long long> g_launches{0};

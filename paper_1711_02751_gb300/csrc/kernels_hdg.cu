@@ -17,6 +17,7 @@
 #include "compensated.h"
 #include "internal.h"
 #include "schur.h"
+#include "ens.h"
 
 namespace hdgdg {
 namespace {
@@ -364,10 +365,11 @@ __global__ void recover_x2_kernel(Geom g, const float* __restrict__ Ahi, const f
 
 // g = -C Z at every trace node: one thread per (edge, b).
 template <int P>
-__global__ void edge_rhs_kernel(Geom g, const double* __restrict__ Z, const double* __restrict__ phiB,
-                                const double* __restrict__ tau_edge, double* __restrict__ gvec, double t_bc) {
+__device__ __forceinline__ void edge_rhs_body(int bid, const Geom& g, const double* __restrict__ Z,
+                                              const double* __restrict__ phiB, const double* __restrict__ tau_edge,
+                                              double* __restrict__ gvec, double t_bc) {
     constexpr int Np = P * P, NF = 3 * P;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = bid * 256 + threadIdx.x;
     if (t >= g.n_edges * P) return;
     const int r = t / P, b = t % P;
     int em, fm, ep, fp;
@@ -410,6 +412,13 @@ __global__ void edge_rhs_kernel(Geom g, const double* __restrict__ Z, const doub
     out[b] = g0;
     out[(xedge ? 1 : 2) * P + b] = gn;
     out[(xedge ? 2 : 1) * P + b] = gt;
+}
+
+template <int P>
+__global__ void __launch_bounds__(256)
+edge_rhs_kernel(Geom g, const double* __restrict__ Z, const double* __restrict__ phiB,
+                const double* __restrict__ tau_edge, double* __restrict__ gvec, double t_bc) {
+    edge_rhs_body<P>(blockIdx.x, g, Z, phiB, tau_edge, gvec, t_bc);
 }
 
 // Q = Z + beta A^{-1}_{:, boundary} (tau qhat);  Lst = (Q - R1) * inv_aii.  T as above.
@@ -524,16 +533,16 @@ __global__ void schur_eg_kernel(Geom g, double dta, typename A::T* __restrict__ 
 
 // Z = A^{-1} R1 through the Schur complement: one thread per (element, node), EPB elements per block.
 template <int P, int EPB, class A>
-__global__ void __launch_bounds__(EPB * P * P)
-    schur_condense_kernel(Geom g, const typename A::T* __restrict__ S, const typename A::T* __restrict__ aux,
-                          const typename A::T* __restrict__ EG, const double* __restrict__ R1,
-                          double* __restrict__ Z) {
+__device__ __forceinline__ void schur_condense_body(int bid, const Geom& g, const typename A::T* __restrict__ S,
+                                                    const typename A::T* __restrict__ aux,
+                                                    const typename A::T* __restrict__ EG,
+                                                    const double* __restrict__ R1, double* __restrict__ Z) {
     using T = typename A::T;
     constexpr int Np = P * P;
     __shared__ SchurSmem<P, EPB, A> sm;
     const int le = threadIdx.x / Np, n = threadIdx.x % Np;
-    const int e = blockIdx.x * EPB + le;
-    const bool live = e < g.n_el;
+    const int e = bid * EPB + le;
+    const bool live = le < EPB && e < g.n_el;
     const size_t fs = (size_t)g.n_el * Np, o = (size_t)e * Np + n;
     T x0{}, xU{}, xV{};
     if (live) {
@@ -550,20 +559,28 @@ __global__ void __launch_bounds__(EPB * P * P)
     }
 }
 
-// Q = Z + beta A^{-1} (tau qhat), Lst = (Q - R1) / a_ii through the Schur complement.
 template <int P, int EPB, class A>
 __global__ void __launch_bounds__(EPB * P * P)
-    schur_recover_kernel(Geom g, const typename A::T* __restrict__ S, const typename A::T* __restrict__ aux,
-                         const typename A::T* __restrict__ EG, const double* __restrict__ Z,
-                         const double* __restrict__ R1, const double* __restrict__ tau_edge,
-                         const double* __restrict__ qhat, double beta, double inv_aii, double* __restrict__ Q,
-                         double* __restrict__ Lst) {
+    schur_condense_kernel(Geom g, const typename A::T* __restrict__ S, const typename A::T* __restrict__ aux,
+                          const typename A::T* __restrict__ EG, const double* __restrict__ R1,
+                          double* __restrict__ Z) {
+    schur_condense_body<P, EPB, A>(blockIdx.x, g, S, aux, EG, R1, Z);
+}
+
+// Q = Z + beta A^{-1} (tau qhat), Lst = (Q - R1) / a_ii through the Schur complement.
+template <int P, int EPB, class A>
+__device__ __forceinline__ void schur_recover_body(int bid, const Geom& g, const typename A::T* __restrict__ S,
+                                                   const typename A::T* __restrict__ aux,
+                                                   const typename A::T* __restrict__ EG, const double* __restrict__ Z,
+                                                   const double* __restrict__ R1, const double* __restrict__ tau_edge,
+                                                   const double* __restrict__ qhat, double beta, double inv_aii,
+                                                   double* __restrict__ Q, double* __restrict__ Lst) {
     using T = typename A::T;
     constexpr int Np = P * P, NF = 3 * P;
     __shared__ SchurSmem<P, EPB, A> sm;
     const int le = threadIdx.x / Np, n = threadIdx.x % Np, i = n % P, j = n / P;
-    const int e = blockIdx.x * EPB + le;
-    const bool live = e < g.n_el;
+    const int e = bid * EPB + le;
+    const bool live = le < EPB && e < g.n_el;
     const size_t fs = (size_t)g.n_el * Np, o = (size_t)e * Np + n;
     double u[3] = {0.0, 0.0, 0.0};
     if (live) {
@@ -589,6 +606,16 @@ __global__ void __launch_bounds__(EPB * P * P)
             Lst[oc] = (q - R1[oc]) * inv_aii;
         }
     }
+}
+
+template <int P, int EPB, class A>
+__global__ void __launch_bounds__(EPB * P * P)
+    schur_recover_kernel(Geom g, const typename A::T* __restrict__ S, const typename A::T* __restrict__ aux,
+                         const typename A::T* __restrict__ EG, const double* __restrict__ Z,
+                         const double* __restrict__ R1, const double* __restrict__ tau_edge,
+                         const double* __restrict__ qhat, double beta, double inv_aii, double* __restrict__ Q,
+                         double* __restrict__ Lst) {
+    schur_recover_body<P, EPB, A>(blockIdx.x, g, S, aux, EG, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst);
 }
 
 // Tiles of the Schur-complement kernels: elements per block for about 256 (tile 0, the default),
@@ -886,7 +913,82 @@ cudaError_t recover_launch(const Geom& g, const LocalOps& ops, const double* Z, 
     return cudaGetLastError();
 }
 
+// ---- ensembles: condensation and recovery of every group in one persistent launch each ------------
+template <int P>
+__host__ __device__ constexpr int ens_schur_epb() {
+    return 256 / (P * P);
+}
+
+__global__ void __launch_bounds__(256) ens_condense_kernel(EnsTable t, const double* __restrict__ R1,
+                                                           double* __restrict__ Z) {
+    ens_walk(t, [&](const EnsGroup& G, int bid) {
+        using T = float2;
+        const T* S = static_cast<const T*>(G.S2);
+        const T* aux = static_cast<const T*>(G.aux2);
+        const T* EG = static_cast<const T*>(G.EG2);
+        switch (G.g.P) {
+            case 3: schur_condense_body<3, ens_schur_epb<3>(), ArithF2>(bid, G.g, S, aux, EG, R1 + G.off3, Z + G.off3); break;
+            case 4: schur_condense_body<4, ens_schur_epb<4>(), ArithF2>(bid, G.g, S, aux, EG, R1 + G.off3, Z + G.off3); break;
+            case 5: schur_condense_body<5, ens_schur_epb<5>(), ArithF2>(bid, G.g, S, aux, EG, R1 + G.off3, Z + G.off3); break;
+            default: break;
+        }
+    });
+}
+
+__global__ void __launch_bounds__(256) ens_edge_rhs_kernel(EnsTable t, const double* __restrict__ Z,
+                                                           double* __restrict__ gvec) {
+    ens_walk(t, [&](const EnsGroup& G, int bid) {
+        switch (G.g.P) {
+            case 3: edge_rhs_body<3>(bid, G.g, Z + G.off3, G.phiB, G.tau, gvec + G.offt, 0.0); break;
+            case 4: edge_rhs_body<4>(bid, G.g, Z + G.off3, G.phiB, G.tau, gvec + G.offt, 0.0); break;
+            case 5: edge_rhs_body<5>(bid, G.g, Z + G.off3, G.phiB, G.tau, gvec + G.offt, 0.0); break;
+            default: break;
+        }
+    });
+}
+
+__global__ void __launch_bounds__(256) ens_recover_kernel(EnsTable t, const double* __restrict__ Z,
+                                                          const double* __restrict__ R1, const double* __restrict__ qhat,
+                                                          double inv_aii, double* __restrict__ Q, double* __restrict__ Lst) {
+    ens_walk(t, [&](const EnsGroup& G, int bid) {
+        using T = float2;
+        const T* S = static_cast<const T*>(G.S2);
+        const T* aux = static_cast<const T*>(G.aux2);
+        const T* EG = static_cast<const T*>(G.EG2);
+        const size_t o = G.off3, ot = G.offt;
+        switch (G.g.P) {
+            case 3: schur_recover_body<3, ens_schur_epb<3>(), ArithF2>(bid, G.g, S, aux, EG, Z + o, R1 + o, G.tau, qhat + ot, G.beta, inv_aii, Q + o, Lst + o); break;
+            case 4: schur_recover_body<4, ens_schur_epb<4>(), ArithF2>(bid, G.g, S, aux, EG, Z + o, R1 + o, G.tau, qhat + ot, G.beta, inv_aii, Q + o, Lst + o); break;
+            case 5: schur_recover_body<5, ens_schur_epb<5>(), ArithF2>(bid, G.g, S, aux, EG, Z + o, R1 + o, G.tau, qhat + ot, G.beta, inv_aii, Q + o, Lst + o); break;
+            default: break;
+        }
+    });
+}
+
+int ens_elem_blocks(const EnsGroup& G) {
+    const int epb = 256 / G.g.Np;
+    return (G.g.n_el + epb - 1) / epb;
+}
+
 }  // namespace
+
+cudaError_t launch_ens_condense(const EnsHost& E, const double* R1, double* Z, double* gvec, cudaStream_t s) {
+    const EnsTable te = ens_table(E, ens_elem_blocks);
+    const EnsTable tr = ens_table(E, [](const EnsGroup& G) { return (G.g.n_edges * G.g.P + 255) / 256; });
+    ens_condense_kernel<<<ens_grid(ens_condense_kernel, te.start[te.ngroups]), 256, 0, s>>>(te, R1, Z);
+    ens_edge_rhs_kernel<<<ens_grid(ens_edge_rhs_kernel, tr.start[tr.ngroups]), 256, 0, s>>>(tr, Z, gvec);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ens_recover(const EnsHost& E, const double* Z, const double* R1, const double* qhat,
+                               double inv_aii, double* Q, double* Lst, cudaStream_t s) {
+    const EnsTable te = ens_table(E, ens_elem_blocks);
+    ens_recover_kernel<<<ens_grid(ens_recover_kernel, te.start[te.ngroups]), 256, 0, s>>>(te, Z, R1, qhat, inv_aii, Q,
+                                                                                          Lst);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_autotune_local(const Geom& g, LocalOps& ops, double* R1, double* Z, const double* tau_edge,
                                   const double* qhat, double* Q, double* Lst, cudaStream_t s) {

@@ -34,6 +34,7 @@
 #include "compensated.h"
 #include "internal.h"
 #include "schur.h"
+#include "ens.h"
 
 namespace hdgdg {
 namespace {
@@ -47,11 +48,11 @@ using MfVec = std::conditional_t<MODE == kMfInner, float, double>;   // vectors 
 // and whether the S^{-1} row is loaded into registers ahead of the traces.  Tile 0 is the default
 // (256 threads, registers); the autotuner tries the others at create for degrees 2..4.
 template <int P>
-constexpr int mf_epb_for(int threads) {
+__host__ __device__ constexpr int mf_epb_for(int threads) {
     return threads / (P * P) > 32 ? 32 : (threads / (P * P) > 0 ? threads / (P * P) : 1);
 }
 template <int P>
-constexpr int mf_epb() {
+__host__ __device__ constexpr int mf_epb() {
     return mf_epb_for<P>(256);
 }
 constexpr int kMfTiles = 6;
@@ -80,15 +81,13 @@ __device__ __forceinline__ TO arith_store(typename A::T v) {
 
 // y = M^{-1} x per edge (one thread per row component), y in the arithmetic's own type
 template <int NF, class A, typename TX>
-__global__ void __launch_bounds__(256)
-mf_pre_kernel(int n_edges, const float* __restrict__ Minv, const TX* __restrict__ x, typename A::T* __restrict__ y,
-              const int* __restrict__ done) {
-    if (done && *done) return;
+__device__ __forceinline__ void mf_pre_body(int bid, int n_edges, const float* __restrict__ Minv,
+                                            const TX* __restrict__ x, typename A::T* __restrict__ y) {
     using T = typename A::T;
     constexpr int EPB = 256 / NF;
     __shared__ T xs[EPB][NF];
     const int le = threadIdx.x / NF, ii = threadIdx.x % NF;
-    const int r = blockIdx.x * EPB + le;
+    const int r = bid * EPB + le;
     const bool live = le < EPB && r < n_edges;
     if (live) xs[le][ii] = arith_load<A>(x + (size_t)r * NF + ii);
     __syncthreads();
@@ -100,22 +99,29 @@ mf_pre_kernel(int n_edges, const float* __restrict__ Minv, const TX* __restrict_
     y[(size_t)r * NF + ii] = acc.get();
 }
 
+template <int NF, class A, typename TX>
+__global__ void __launch_bounds__(256)
+mf_pre_kernel(int n_edges, const float* __restrict__ Minv, const TX* __restrict__ x, typename A::T* __restrict__ y,
+              const int* __restrict__ done) {
+    if (done && *done) return;
+    mf_pre_body<NF, A, TX>(blockIdx.x, n_edges, Minv, x, y);
+}
+
 // The element pass (see above).  PLAIN: y is the input vector itself (TX), else M^{-1} x (A::T).
 template <int P, int EPB, class A, int MODE, bool PREF>
-__global__ void __launch_bounds__(EPB * P * P)
-    mf_elem_kernel(Geom g, const typename A::T* __restrict__ S, const typename A::T* __restrict__ aux,
-                   const typename A::T* __restrict__ EG, const double* __restrict__ tau_edge,
-                   const void* __restrict__ yv, MfVec<MODE>* __restrict__ hm, MfVec<MODE>* __restrict__ hp,
-                   double beta, const int* __restrict__ done) {
+__device__ __forceinline__ void mf_elem_body(int bid, const Geom& g, const typename A::T* __restrict__ S,
+                                             const typename A::T* __restrict__ aux,
+                                             const typename A::T* __restrict__ EG, const double* __restrict__ tau_edge,
+                                             const void* __restrict__ yv, MfVec<MODE>* __restrict__ hm,
+                                             MfVec<MODE>* __restrict__ hp, double beta) {
     using T = typename A::T;
     using TO = MfVec<MODE>;
     constexpr int Np = P * P, NF = 3 * P;
     constexpr bool kPref = PREF && Np <= 25;   // S^{-1} row loaded into registers ahead of the traces
-    if (done && *done) return;
     __shared__ SchurSmem<P, EPB, A> sm;
     const int le = threadIdx.x / Np, n = threadIdx.x % Np, i = n % P, j = n / P;
-    const int e = blockIdx.x * EPB + le;
-    const bool live = e < g.n_el;
+    const int e = bid * EPB + le;
+    const bool live = le < EPB && e < g.n_el;
     // operator data first: it does not depend on the traces
     SchurNode<A> nd;
     T srow[kPref ? Np : 1];
@@ -232,6 +238,16 @@ __global__ void __launch_bounds__(EPB * P * P)
     }
 }
 
+template <int P, int EPB, class A, int MODE, bool PREF>
+__global__ void __launch_bounds__(EPB * P * P)
+    mf_elem_kernel(Geom g, const typename A::T* __restrict__ S, const typename A::T* __restrict__ aux,
+                   const typename A::T* __restrict__ EG, const double* __restrict__ tau_edge,
+                   const void* __restrict__ yv, MfVec<MODE>* __restrict__ hm, MfVec<MODE>* __restrict__ hp,
+                   double beta, const int* __restrict__ done) {
+    if (done && *done) return;
+    mf_elem_body<P, EPB, A, MODE, PREF>(blockIdx.x, g, S, aux, EG, tau_edge, yv, hm, hp, beta);
+}
+
 // y = hm + hp, or w = g - (hm + hp)
 template <typename TO, bool RESID>
 __global__ void __launch_bounds__(256)
@@ -247,12 +263,12 @@ mf_sum_kernel(size_t n, const TO* __restrict__ hm, const TO* __restrict__ hp, co
 
 // qhat = M^{-1} x~ with the FP32 block-Jacobi blocks, FP64-class sums (x split into FP32 pairs).
 template <int NF>
-__global__ void __launch_bounds__(256)
-mf_back_kernel(int n_edges, const float* __restrict__ Minv, const double* __restrict__ x, double* __restrict__ y) {
+__device__ __forceinline__ void mf_back_body(int bid, int n_edges, const float* __restrict__ Minv,
+                                             const double* __restrict__ x, double* __restrict__ y) {
     constexpr int EPB = 256 / NF;
     __shared__ float sxh[EPB][NF], sxl[EPB][NF];
     const int le = threadIdx.x / NF, ii = threadIdx.x % NF;
-    const int r = blockIdx.x * EPB + le;
+    const int r = bid * EPB + le;
     const bool live = le < EPB && r < n_edges;
     if (live) split(x[(size_t)r * NF + ii], sxh[le][ii], sxl[le][ii]);
     __syncthreads();
@@ -262,6 +278,12 @@ mf_back_kernel(int n_edges, const float* __restrict__ Minv, const double* __rest
 #pragma unroll
     for (int jj = 0; jj < NF; ++jj) acc.add(M[jj * NF + ii], 0.f, sxh[le][jj], sxl[le][jj]);
     y[(size_t)r * NF + ii] = acc.value();
+}
+
+template <int NF>
+__global__ void __launch_bounds__(256)
+mf_back_kernel(int n_edges, const float* __restrict__ Minv, const double* __restrict__ x, double* __restrict__ y) {
+    mf_back_body<NF>(blockIdx.x, n_edges, Minv, x, y);
 }
 
 // hi parts of FP32 pairs
@@ -323,6 +345,81 @@ cudaError_t mf_launch(const Geom& g, const MfOps& op, const void* S, const void*
     const size_t n = (size_t)g.n_edges * NF;
     mf_sum_kernel<TO, MODE == kMfResidual><<<sum_grid(n), 256, 0, s>>>(n, hm, hp, rhs, out, done);
     count_launches(MODE != kMfPlain ? 3 : 2);
+    return cudaGetLastError();
+}
+
+// ---- ensembles: the operator's three passes over every group, one persistent launch each -----------
+template <class A, typename TX>
+__global__ void __launch_bounds__(256) ens_mf_pre_kernel(EnsTable t, const TX* __restrict__ x,
+                                                         typename A::T* __restrict__ y, const int* __restrict__ done) {
+    if (done && *done) return;
+    ens_walk(t, [&](const EnsGroup& G, int bid) {
+        switch (G.g.P) {
+            case 3: mf_pre_body<9, A, TX>(bid, G.g.n_edges, G.Minv32, x + G.offt, y + G.offt); break;
+            case 4: mf_pre_body<12, A, TX>(bid, G.g.n_edges, G.Minv32, x + G.offt, y + G.offt); break;
+            case 5: mf_pre_body<15, A, TX>(bid, G.g.n_edges, G.Minv32, x + G.offt, y + G.offt); break;
+            default: break;
+        }
+    });
+}
+
+template <class A, int MODE>
+__global__ void __launch_bounds__(256) ens_mf_elem_kernel(EnsTable t, const typename A::T* __restrict__ y,
+                                                          MfVec<MODE>* __restrict__ hm, MfVec<MODE>* __restrict__ hp,
+                                                          const int* __restrict__ done) {
+    if (done && *done) return;
+    constexpr bool k32 = sizeof(typename A::T) == sizeof(float);
+    ens_walk(t, [&](const EnsGroup& G, int bid) {
+        using T = typename A::T;
+        const T* S = k32 ? reinterpret_cast<const T*>(G.S32) : static_cast<const T*>(G.S2);
+        const T* aux = k32 ? reinterpret_cast<const T*>(G.aux32) : static_cast<const T*>(G.aux2);
+        const T* EG = k32 ? reinterpret_cast<const T*>(G.EG32) : static_cast<const T*>(G.EG2);
+        const size_t o = G.offt;
+        switch (G.g.P) {
+            case 3: mf_elem_body<3, mf_epb<3>(), A, MODE, true>(bid, G.g, S, aux, EG, G.tau, y + o, hm + o, hp + o, G.beta); break;
+            case 4: mf_elem_body<4, mf_epb<4>(), A, MODE, true>(bid, G.g, S, aux, EG, G.tau, y + o, hm + o, hp + o, G.beta); break;
+            case 5: mf_elem_body<5, mf_epb<5>(), A, MODE, true>(bid, G.g, S, aux, EG, G.tau, y + o, hm + o, hp + o, G.beta); break;
+            default: break;
+        }
+    });
+}
+
+__global__ void __launch_bounds__(256) ens_mf_back_kernel(EnsTable t, const double* __restrict__ x, double* __restrict__ y) {
+    ens_walk(t, [&](const EnsGroup& G, int bid) {
+        switch (G.g.P) {
+            case 3: mf_back_body<9>(bid, G.g.n_edges, G.Minv32, x + G.offt, y + G.offt); break;
+            case 4: mf_back_body<12>(bid, G.g.n_edges, G.Minv32, x + G.offt, y + G.offt); break;
+            case 5: mf_back_body<15>(bid, G.g.n_edges, G.Minv32, x + G.offt, y + G.offt); break;
+            default: break;
+        }
+    });
+}
+
+int ens_edge_blocks(const EnsGroup& G) {
+    const int epb = 256 / (3 * G.g.P);
+    return (G.g.n_edges + epb - 1) / epb;
+}
+
+int ens_mf_elem_blocks(const EnsGroup& G) {
+    const int P = G.g.P, epb = 256 / (P * P) > 32 ? 32 : 256 / (P * P);
+    return (G.g.n_el + epb - 1) / epb;
+}
+
+template <class A, int MODE>
+cudaError_t ens_mf_launch(const EnsHost& E, const MfOps& op, size_t nt, const MfVec<MODE>* x, const double* rhs,
+                          MfVec<MODE>* out, cudaStream_t s, const int* done) {
+    using T = typename A::T;
+    using TO = MfVec<MODE>;
+    const EnsTable te = ens_table(E, ens_edge_blocks);
+    const EnsTable tm = ens_table(E, ens_mf_elem_blocks);
+    T* y = static_cast<T*>(op.ybuf);
+    TO* hm = static_cast<TO*>(op.hm);
+    TO* hp = static_cast<TO*>(op.hp);
+    ens_mf_pre_kernel<A, TO><<<ens_grid(ens_mf_pre_kernel<A, TO>, te.start[te.ngroups]), 256, 0, s>>>(te, x, y, done);
+    ens_mf_elem_kernel<A, MODE><<<ens_grid(ens_mf_elem_kernel<A, MODE>, tm.start[tm.ngroups]), 256, 0, s>>>(tm, y, hm,
+                                                                                                         hp, done);
+    mf_sum_kernel<TO, MODE == kMfResidual><<<sum_grid(nt), 256, 0, s>>>(nt, hm, hp, rhs, out, done);
+    count_launches(3);
     return cudaGetLastError();
 }
 
@@ -399,6 +496,23 @@ cudaError_t launch_mf_autotune(const Geom& g, MfOps& op, const float* x, float* 
     *epb = th / (P * P) > 32 ? 32 : (th / (P * P) > 0 ? th / (P * P) : 1);
     *prefetch = mf_tile_pref(best_t) ? 1 : 0;
     return err;
+}
+
+cudaError_t launch_ens_mf_inner(const EnsHost& E, const MfOps& scratch, size_t nt, const float* x, float* y,
+                                cudaStream_t s, const int* done) {
+    return ens_mf_launch<ArithF32, kMfInner>(E, scratch, nt, x, nullptr, y, s, done);
+}
+
+cudaError_t launch_ens_mf_residual(const EnsHost& E, const MfOps& scratch, size_t nt, const double* x,
+                                   const double* rhs, double* w, cudaStream_t s) {
+    return ens_mf_launch<ArithF2, kMfResidual>(E, scratch, nt, x, rhs, w, s, nullptr);
+}
+
+cudaError_t launch_ens_mf_back(const EnsHost& E, const double* x, double* y, cudaStream_t s) {
+    const EnsTable te = ens_table(E, ens_edge_blocks);
+    ens_mf_back_kernel<<<ens_grid(ens_mf_back_kernel, te.start[te.ngroups]), 256, 0, s>>>(te, x, y);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_mf_back(const Geom& g, const float* Minv32, const double* x, double* y, cudaStream_t s) {

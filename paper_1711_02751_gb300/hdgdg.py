@@ -23,7 +23,9 @@ EXPORTS = ["hdgdg_bytes_required", "hdgdg_node_coords", "hdgdg_create", "hdgdg_s
            "hdgdg_update_state", "hdgdg_eval_nl", "hdgdg_condense_rhs", "hdgdg_trace_apply", "hdgdg_stage_solve",
            "hdgdg_measure_fp64_tflops", "hdgdg_measure_conversion_rates", "hdgdg_set_kernel_timing", "hdgdg_kernel_time",
            "hdgdg_mass_noalloc", "hdgdg_gll", "hdgdg_checkpoint_bytes", "hdgdg_save_checkpoint",
-           "hdgdg_load_checkpoint"]
+           "hdgdg_load_checkpoint", "hdgdg_ensemble_create", "hdgdg_ensemble_set_state", "hdgdg_ensemble_step",
+           "hdgdg_ensemble_get_state", "hdgdg_ensemble_get_stats", "hdgdg_ensemble_last_error",
+           "hdgdg_ensemble_destroy"]
 KERNEL_CLASSES = ["spmv", "ortho", "condense", "recover", "dg", "combine", "residual", "guess", "precond"]
 
 
@@ -96,6 +98,17 @@ def lib():
         L.hdgdg_kernel_time.argtypes = [ctypes.c_void_p, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_longlong)]
         L.hdgdg_mass_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p]
+        L.hdgdg_ensemble_create.argtypes = [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_int), _P, ctypes.POINTER(_P), ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_void_p)]
+        L.hdgdg_ensemble_set_state.argtypes = [ctypes.c_void_p, ctypes.c_int, _P, _P, _P]
+        L.hdgdg_ensemble_get_state.argtypes = [ctypes.c_void_p, ctypes.c_int, _P, _P, _P]
+        L.hdgdg_ensemble_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.hdgdg_ensemble_get_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(Stats)]
+        L.hdgdg_ensemble_last_error.restype = ctypes.c_char_p
+        L.hdgdg_ensemble_last_error.argtypes = [ctypes.c_void_p]
+        L.hdgdg_ensemble_destroy.restype = None
+        L.hdgdg_ensemble_destroy.argtypes = [ctypes.c_void_p]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
         _lib = L
@@ -328,3 +341,75 @@ class Sim:
         its = ctypes.c_int(0)
         self._check(lib().hdgdg_stage_solve(self._h, _ptr(R1), _ptr(Q), _ptr(lam), ctypes.byref(its)))
         return Q, lam, its.value
+
+
+class Ensemble:
+    """Uneven ensemble (hdgdg_ensemble_create ... hdgdg_ensemble_destroy): members of different
+    mesh sizes and degrees advanced together, one persistent launch per kernel class per stage."""
+
+    def __init__(self, sides, degrees, dts, bottoms=None, g=1.0, H0=1.0, scheme="ars2", stream=None,
+                 krylov_rtol=0.0, krylov_restart=0, krylov_maxit=0, krylov_guess=0):
+        self.sides = [int(v) for v in sides]
+        self.degrees = [int(v) for v in degrees]
+        n = len(self.sides)
+        base = make_config(2, 2, 1.0, g, H0, scheme, krylov_rtol, krylov_restart, krylov_maxit,
+                           precision="mixed", local_precision="f32x2", krylov_guess=krylov_guess,
+                           trace_operator=1)
+        ns = (ctypes.c_int * n)(*self.sides)
+        ks = (ctypes.c_int * n)(*self.degrees)
+        d = _f64(dts, (n,))
+        self._bots = [None if bottoms is None or bottoms[i] is None else
+                      _f64(bottoms[i], (self.sides[i] ** 2, (self.degrees[i] + 1) ** 2)) for i in range(n)]
+        barr = (_P * n)(*[(_ptr(b) if b is not None else _P()) for b in self._bots])
+        self._h = ctypes.c_void_p(None)
+        st = lib().hdgdg_ensemble_create(ctypes.byref(base), n, ns, ks, _ptr(d), barr,
+                                         ctypes.c_void_p(stream) if stream else None, ctypes.byref(self._h))
+        if st != OK:
+            msg = self.last_error() if self._h else "ensemble_create"
+            self.close()
+            raise HdgdgError(st, msg)
+
+    def close(self):
+        if self._h:
+            lib().hdgdg_ensemble_destroy(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def last_error(self):
+        return lib().hdgdg_ensemble_last_error(self._h).decode()
+
+    def _check(self, st):
+        if st != OK:
+            raise HdgdgError(st, self.last_error())
+
+    def _shape(self, m):
+        return (self.sides[m] ** 2, (self.degrees[m] + 1) ** 2)
+
+    def set_state(self, m, h, hu, hv):
+        sh = self._shape(m)
+        h, hu, hv = _f64(h, sh), _f64(hu, sh), _f64(hv, sh)
+        self._check(lib().hdgdg_ensemble_set_state(self._h, int(m), _ptr(h), _ptr(hu), _ptr(hv)))
+
+    def step(self, n_steps=1):
+        self._check(lib().hdgdg_ensemble_step(self._h, int(n_steps)))
+
+    def get_state(self, m):
+        out = [np.empty(self._shape(m)) for _ in range(3)]
+        self._check(lib().hdgdg_ensemble_get_state(self._h, int(m), *[_ptr(a) for a in out]))
+        return tuple(out)
+
+    def stats(self):
+        s = Stats()
+        self._check(lib().hdgdg_ensemble_get_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
