@@ -84,8 +84,18 @@ enum { HDGDG_FP64 = 0, HDGDG_MIXED = 1 };
  *                   compensated Dot2 scheme (exact products by FMA, TwoSum accumulation; Ogita,
  *                   Rump and Oishi 2005), about 1e-13 relative, at the HBM bound.
  * Vectors stay FP64 in every case; the precision variants of the paper's workloads report
- * their error against the FP64 form. */
-enum { HDGDG_LOCAL_FP64 = 0, HDGDG_LOCAL_FP32 = 1, HDGDG_LOCAL_BF16 = 2, HDGDG_LOCAL_F32X2 = 3 };
+ * their error against the FP64 form.
+ * HDGDG_LOCAL_BF16_SPLIT: FP64-class on the tensor cores, for the same shared operator as
+ *                   HDGDG_LOCAL_BF16 (flat bottom, one time step, k <= 4): every input row and
+ *                   every operator column is scaled by a power of two and cut into five seven-bit
+ *                   integer slices, exact in BF16 (the splitting of Ozaki, Ogita, Oishi and Rump,
+ *                   Numer. Algorithms 2012); the slices' pairwise products with i + j < 5 run as
+ *                   tcgen05 BF16 MMAs whose FP32 accumulators hold their sums exactly, and the
+ *                   epilogue adds the five accumulators in 64-bit integers and scales in FP64:
+ *                   about 35 bits, 3e-11 relative to the row and column scales.
+ */
+enum { HDGDG_LOCAL_FP64 = 0, HDGDG_LOCAL_FP32 = 1, HDGDG_LOCAL_BF16 = 2, HDGDG_LOCAL_F32X2 = 3,
+       HDGDG_LOCAL_BF16_SPLIT = 4 };
 
 typedef struct {
     int n_side;          /* N >= 2: elements per side of the periodic unit square */
@@ -164,6 +174,13 @@ typedef struct {
                             host-driven anyway while the kernel-class timers are on and for
                             prescribed time-dependent boundary traces (HDGDG_VORTEX).  Same results
                             either way, bit for bit. */
+    int dg_precision;    /* DG residual of the nonlinear part: 0 = the form's own (FP64 in HDGDG_FP64,
+                            FP32 arithmetic in HDGDG_MIXED); 1 = BF16 inputs (the state, phi_B and
+                            tau rounded to BF16) with FP32 arithmetic and accumulation -- the BF16
+                            variant of the mixed form (HDGDG_MIXED and k <= 4 only, else EINVAL).
+                            The residual is a nonlinear flux evaluation with P x P derivative
+                            applications (P = k + 1 <= 5), not a dense contraction, so it runs on the
+                            CUDA cores in every variant. */
 } hdgdg_config;
 
 /* HDGDG_VORTEX: the exact-solution boundary conditions of the paper's moving-vortex test

@@ -49,12 +49,14 @@ bool valid(const hdgdg_config* c) {
            c->boundary >= HDGDG_PERIODIC && c->boundary <= HDGDG_VORTEX && std::isfinite(c->x0) &&
            std::isfinite(c->length) && c->batch >= 0 && c->batch <= (1 << 20) &&
            c->krylov_restart <= kMaxRestart && c->local_precision >= HDGDG_LOCAL_FP64 &&
-           c->local_precision <= HDGDG_LOCAL_F32X2 &&
-           (c->local_precision != HDGDG_LOCAL_BF16 || c->degree_k <= 4) &&   // tensor-core tiles: k <= 4
+           c->local_precision <= HDGDG_LOCAL_BF16_SPLIT &&
+           ((c->local_precision != HDGDG_LOCAL_BF16 && c->local_precision != HDGDG_LOCAL_BF16_SPLIT) ||
+            c->degree_k <= 4) &&   // tensor-core tiles: k <= 4
            c->krylov_guess >= -1 && c->krylov_guess <= 6 && (c->spmv_kernel == 0 || c->spmv_kernel == 1) &&
            (c->krylov_ortho == 0 || c->krylov_ortho == 1) && (c->residual_f32x2 == 0 || c->residual_f32x2 == 1) &&
            (c->local_dense == 0 || c->local_dense == 1) && (c->trace_operator == 0 || c->trace_operator == 1) &&
            (c->host_steps == 0 || c->host_steps == 1) &&
+           (c->dg_precision == 0 || (c->dg_precision == 1 && c->precision == HDGDG_MIXED && c->degree_k <= 4)) &&
            (c->trace_operator == 0 ||
             (c->precision == HDGDG_MIXED && c->local_precision == HDGDG_LOCAL_F32X2 && !c->local_dense &&
              c->scheme != HDGDG_RK2 && c->scheme != HDGDG_RK3));
@@ -115,6 +117,7 @@ Plan make_plan(const hdgdg_config* c) {
     b += 64 + sizeof(GmresCtl);                               // flags, GMRES control block
     if (c->local_precision == HDGDG_LOCAL_FP32) b += n_el * (size_t)p.NV * p.NV * sizeof(float);
     if (c->local_precision == HDGDG_LOCAL_BF16) b += tc_image_bytes((int)P);
+    if (c->local_precision == HDGDG_LOCAL_BF16_SPLIT) b += tc_split_image_bytes((int)P);
     if (local_schur(c)) {   // (phi, phi) block of A^{-1}, 4 numbers per node, 2 P x P per instance
         b += (n_el * Np * Np + 4 * n_el * Np + 2 * B * Np) * d;   // FP64 or FP32 pairs: 8 bytes each
     } else if (c->local_precision == HDGDG_LOCAL_F32X2) {
@@ -896,6 +899,8 @@ cudaError_t step_enqueue_graph(hdgdg_sim* sim, cudaStream_t st, StepGraph& sg) {
         if (!sim->cfg.linear_only && e == cudaSuccess) {
             if (sim->ens)
                 e = launch_ens_dg_nl_f32(*sim->ens, Qi, sim->fface, sim->NLs[i], st);
+            else if (sim->cfg.dg_precision == 1)
+                e = launch_dg_nl_bf16(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st, 0.0);
             else if (sim->cfg.precision == HDGDG_MIXED)
                 e = launch_dg_nl_f32(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st, 0.0);
             else
@@ -1089,7 +1094,9 @@ hdgdg_status one_step(hdgdg_sim* sim) {
         }
         if (!sim->cfg.linear_only) {
             TimedGroup tg(sim, HDGDG_KT_DG);
-            if (sim->cfg.precision == HDGDG_MIXED)
+            if (sim->cfg.dg_precision == 1)
+                CU(launch_dg_nl_bf16(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st, ti));
+            else if (sim->cfg.precision == HDGDG_MIXED)
                 CU(launch_dg_nl_f32(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st, ti));
             else
                 CU(launch_dg_nl(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st, ti));
@@ -1322,20 +1329,22 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
                 CU(cudaMemsetAsync(v, 0, 3 * p.n * sizeof(double), sim->stream));
             CU(cudaMemsetAsync(sim->lam, 0, p.nt * sizeof(double), sim->stream));
         }
-    } else if (c->local_precision == HDGDG_LOCAL_BF16) {
+    } else if (c->local_precision == HDGDG_LOCAL_BF16 || c->local_precision == HDGDG_LOCAL_BF16_SPLIT) {
         // one operator for every element: phi_B constant and one time step
         for (size_t k = 1; k < p.n; ++k)
             if (phiB[k] != phiB[0])
-                return fail(sim, HDGDG_EINVAL, "BF16 tensor-core local contractions need a flat bottom");
+                return fail(sim, HDGDG_EINVAL, "tensor-core local contractions need a flat bottom");
         if (c->dt_per_instance)
             for (int i = 0; i < g.batch; ++i)
                 if (c->dt_per_instance[i] != c->dt)
-                    return fail(sim, HDGDG_EINVAL, "BF16 tensor-core local contractions need one time step");
+                    return fail(sim, HDGDG_EINVAL, "tensor-core local contractions need one time step");
+        const bool split = c->local_precision == HDGDG_LOCAL_BF16_SPLIT;
         uint8_t* img = nullptr;
-        TRY(dalloc(sim, &img, tc_image_bytes(P)));
+        TRY(dalloc(sim, &img, split ? tc_split_image_bytes(P) : tc_image_bytes(P)));
         sim->tc_image = img;
-        CU(launch_tc_image(g, sim->Ainv, img, sim->stream));
-        sim->ops.kind = 2;
+        if (split) CU(launch_tc_split_image(g, sim->Ainv, img, sim->stream));
+        else CU(launch_tc_image(g, sim->Ainv, img, sim->stream));
+        sim->ops.kind = split ? 4 : 2;
         sim->ops.image = img;
         sim->ops.error = reinterpret_cast<int*>(sim->flags) + 2;
     }

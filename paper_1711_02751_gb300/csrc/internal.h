@@ -210,6 +210,9 @@ cudaError_t launch_dg_nl(const Geom& g, const double* q, const double* phiB, con
 // the same residual computed in FP32 arithmetic (FP64 storage): the mixed form's DG residual
 cudaError_t launch_dg_nl_f32(const Geom& g, const double* q, const double* phiB, const double* tau_edge,
                              double scale, double* fface, double* out, cudaStream_t s, double t = 0.0);
+// the same residual with its inputs (state, phi_B, tau) rounded to BF16 and FP32 arithmetic (k <= 4)
+cudaError_t launch_dg_nl_bf16(const Geom& g, const double* q, const double* phiB, const double* tau_edge,
+                              double scale, double* fface, double* out, cudaStream_t s, double t = 0.0);
 // out = scale * M^{-1} (the explicit DG residual of the whole flux with the source term)
 cudaError_t launch_dg_full(const Geom& g, const double* q, const double* phiB, double scale,
                            double* fface, double* out, cudaStream_t s, double t = 0.0);
@@ -234,7 +237,8 @@ cudaError_t launch_assemble_trace(const Geom& g, const double* Se, double* S7, d
 // The local operators as the condensation and recovery kernels apply them.
 struct LocalOps {
     int kind = 0;                   // 0: per-element FP64; 1: per-element FP32; 2: shared, tensor cores;
-                                    // 3: per-element FP32 pairs (FP64-class, compensated dot products)
+                                    // 3: per-element FP32 pairs (FP64-class, compensated dot products);
+                                    // 4: shared, tensor cores on BF16 slices (FP64-class)
     const double* Ainv = nullptr;   // kind 0: [n_el][col s][row r] = (A^{-1})_{rs}
     const float* Ainv32 = nullptr;  // kind 1: same layout in FP32
     const float* Ahi = nullptr;     // kind 3: A^{-1} = Ahi + Alo, same layout
@@ -305,6 +309,13 @@ cudaError_t launch_split_f32x2(const double* a, float* hi, float* lo, size_t n, 
 // FP64 A^{-1} of element 0 (setup).
 size_t tc_image_bytes(int P);
 cudaError_t launch_tc_image(const Geom& g, const double* Ainv, void* image, cudaStream_t s);
+// The FP64-class variant: the operator as five seven-bit BF16 slices with column exponents (the
+// Ozaki splitting), its image bytes and build; the products of the slices on the tensor cores.
+size_t tc_split_image_bytes(int P);
+cudaError_t launch_tc_split_image(const Geom& g, const double* Ainv, void* image, cudaStream_t s);
+cudaError_t launch_local_tc_split(const Geom& g, int mode, const void* image, const double* R1, const double* Z,
+                                  const double* tau_edge, const double* qhat, double beta, double inv_aii,
+                                  double* out0, double* out1, int* error, cudaStream_t s);
 // Z = A^{-1} R1 (mode 0) or Q = Z + beta A^{-1}(tau qhat), Lst = (Q - R1)/a_ii (mode 1) on the
 // tensor cores with the shared operator image.
 cudaError_t launch_local_tc(const Geom& g, int mode, const void* image, const double* R1,

@@ -11,6 +11,8 @@
 // tau_L* = max_pm sqrt(phi_B) is the per-edge-node tau_hat the library precomputes.
 #include <atomic>
 
+#include <cuda_bf16.h>
+
 #include "ens.h"
 #include "fastcvt.h"
 #include "internal.h"
@@ -23,6 +25,14 @@ struct DgTile {
     static constexpr int Np = P * P;
     static constexpr int EPB = (256 / Np) > 0 ? (256 / Np) : 1;   // elements per block
 };
+
+// An input of the residual in the arithmetic type; BF: rounded to BF16 first (8 significant bits,
+// nearest even), the BF16-input variant of the mixed form.
+template <typename Tc, bool BF>
+__device__ __forceinline__ Tc dg_in(double v) {
+    if constexpr (BF) return __bfloat162float(__float2bfloat16_rn(f64_to_f32(v)));
+    else return from_f64<Tc>(v);
+}
 
 // F_NL components along x (fx) and y (fy) for the momentum rows (the mass row is zero).
 template <typename Tc>
@@ -42,7 +52,7 @@ __device__ __forceinline__ void nl_flux(Tc ph, Tc U, Tc V, Tc phiB, Tc* fxU, Tc*
 //   FULL = true: the Rusanov flux F* . n of the whole flux F = F_NL + F_L (eq. Full_russanov),
 //   the residual of the explicit RK DG scheme the paper compares with.
 //   Tc: arithmetic type (double; float for the mixed form's residual), storage stays FP64.
-template <int P, bool FULL, typename Tc>
+template <int P, bool FULL, typename Tc, bool BF = false>
 __device__ __forceinline__ void dg_face_body(int bid, const Geom& g, const double* __restrict__ q,
                                              const double* __restrict__ phiB, const double* __restrict__ tau_edge,
                                              double* __restrict__ fface, double t_bc) {
@@ -78,12 +88,12 @@ __device__ __forceinline__ void dg_face_body(int bid, const Geom& g, const doubl
         if (ep < 0) { php = phm; pbp = pbm; Up = xedge ? -Um : Um; Vp = xedge ? Vm : -Vm; }
     }
     // (conversions to the arithmetic type on the integer pipes, fastcvt.h)
-    const Tc pm = from_f64<Tc>(phm), pp = from_f64<Tc>(php);
-    const Tc Phm = pm + from_f64<Tc>(pbm), Php = pp + from_f64<Tc>(pbp);
+    const Tc pm = dg_in<Tc, BF>(phm), pp = dg_in<Tc, BF>(php);
+    const Tc Phm = pm + dg_in<Tc, BF>(pbm), Php = pp + dg_in<Tc, BF>(pbp);
     const Tc im = Tc(1) / Phm, ip = Tc(1) / Php;
     // normal (n) and tangential (t) momentum components along this edge's +axis
-    const Tc Unm = from_f64<Tc>(xedge ? Um : Vm), Utm = from_f64<Tc>(xedge ? Vm : Um);
-    const Tc Unp = from_f64<Tc>(xedge ? Up : Vp), Utp = from_f64<Tc>(xedge ? Vp : Up);
+    const Tc Unm = dg_in<Tc, BF>(xedge ? Um : Vm), Utm = dg_in<Tc, BF>(xedge ? Vm : Um);
+    const Tc Unp = dg_in<Tc, BF>(xedge ? Up : Vp), Utp = dg_in<Tc, BF>(xedge ? Vp : Up);
     // F_NL . n: (0, Un Un / phi + phi_eta^2 / 2, Un Ut / phi) in (normal, tangential) order
     Tc Fnm = Unm * Unm * im + Tc(0.5) * pm * pm, Ftm = Unm * Utm * im;
     Tc Fnp = Unp * Unp * ip + Tc(0.5) * pp * pp, Ftp = Unp * Utp * ip;
@@ -95,7 +105,7 @@ __device__ __forceinline__ void dg_face_body(int bid, const Geom& g, const doubl
         hd = Tc(0.5) * tau_star;
         fph = Tc(0.5) * (Unm + Unp) + hd * (pm - pp);
     } else {
-        hd = Tc(0.5) * (tau_star - from_f64<Tc>(tau_edge[(size_t)r * P + b]));
+        hd = Tc(0.5) * (tau_star - dg_in<Tc, BF>(tau_edge[(size_t)r * P + b]));
         fph = hd * (pm - pp);
     }
     const Tc fn = Tc(0.5) * (Fnm + Fnp) + hd * (Unm - Unp);
@@ -106,16 +116,16 @@ __device__ __forceinline__ void dg_face_body(int bid, const Geom& g, const doubl
     out[(xedge ? 2 : 1) * P + b] = to_f64(ft);
 }
 
-template <int P, bool FULL, typename Tc>
+template <int P, bool FULL, typename Tc, bool BF = false>
 __global__ void __launch_bounds__(256)
 dg_face_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ phiB,
                const double* __restrict__ tau_edge, double* __restrict__ fface, double t_bc) {
-    dg_face_body<P, FULL, Tc>(blockIdx.x, g, q, phiB, tau_edge, fface, t_bc);
+    dg_face_body<P, FULL, Tc, BF>(blockIdx.x, g, q, phiB, tau_edge, fface, t_bc);
 }
 
 // Element pass: volume term from the nodal F_NL (shared memory), minus the lifted face fluxes.
 // FULL = true: the whole flux F and the source s = (0, phi_eta d_x phi_B, phi_eta d_y phi_B).
-template <int P, bool FULL, typename Tc>
+template <int P, bool FULL, typename Tc, bool BF = false>
 __device__ __forceinline__ void dg_volume_body(int bid, const Geom& g, const double* __restrict__ q,
                                                const double* __restrict__ phiB, const double* __restrict__ fface,
                                                double scale, double* __restrict__ out) {
@@ -143,8 +153,8 @@ __device__ __forceinline__ void dg_volume_body(int bid, const Geom& g, const dou
     Tc ph_own = Tc(0);
     if (live) {
         const size_t o = (size_t)e * Np + n;
-        const Tc ph = from_f64<Tc>(q[o]), U = from_f64<Tc>(q[fs + o]), V = from_f64<Tc>(q[2 * fs + o]),
-                 pb = from_f64<Tc>(phiB[o]);
+        const Tc ph = dg_in<Tc, BF>(q[o]), U = dg_in<Tc, BF>(q[fs + o]), V = dg_in<Tc, BF>(q[2 * fs + o]),
+                 pb = dg_in<Tc, BF>(phiB[o]);
         nl_flux<Tc>(ph, U, V, pb, &sFr[le][0 * Np + n], &sFr[le][1 * Np + n], &sFr[le][2 * Np + n], &sFr[le][3 * Np + n]);
         if (FULL) {
             sFr[le][0 * Np + n] += ph * pb;
@@ -201,11 +211,11 @@ __device__ __forceinline__ void dg_volume_body(int bid, const Geom& g, const dou
     out[2 * fs + o] = sc * to_f64(rV);
 }
 
-template <int P, bool FULL, typename Tc>
+template <int P, bool FULL, typename Tc, bool BF = false>
 __global__ void __launch_bounds__(DgTile<P>::EPB * P * P)
 dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ phiB,
                  const double* __restrict__ fface, double scale, double* __restrict__ out) {
-    dg_volume_body<P, FULL, Tc>(blockIdx.x, g, q, phiB, fface, scale, out);
+    dg_volume_body<P, FULL, Tc, BF>(blockIdx.x, g, q, phiB, fface, scale, out);
 }
 
 __global__ void combine_kernel(size_t n, const double* __restrict__ base, CombineTerms t,
@@ -286,14 +296,14 @@ __global__ void mass_final_kernel(const double* partial, int nb, double J, doubl
     if (threadIdx.x == 0) *out = J * acc;
 }
 
-template <int P, bool FULL, typename Tc = double>
+template <int P, bool FULL, typename Tc = double, bool BF = false>
 cudaError_t dg_launch(const Geom& g, const double* q, const double* phiB, const double* tau_edge,
                       double scale, double* fface, double* out, cudaStream_t s, double t) {
     constexpr int EPB = DgTile<P>::EPB;
     const int nf = g.n_edges * P;
-    dg_face_kernel<P, FULL, Tc><<<(nf + 255) / 256, 256, 0, s>>>(g, q, phiB, tau_edge, fface, t);
+    dg_face_kernel<P, FULL, Tc, BF><<<(nf + 255) / 256, 256, 0, s>>>(g, q, phiB, tau_edge, fface, t);
     count_launches(1);
-    dg_volume_kernel<P, FULL, Tc><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(g, q, phiB, fface, scale, out);
+    dg_volume_kernel<P, FULL, Tc, BF><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(g, q, phiB, fface, scale, out);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -381,6 +391,17 @@ cudaError_t launch_dg_nl_f32(const Geom& g, const double* q, const double* phiB,
         case 7: return dg_launch<7, false, float>(g, q, phiB, tau_edge, scale, fface, out, s, t);
         case 8: return dg_launch<8, false, float>(g, q, phiB, tau_edge, scale, fface, out, s, t);
         case 9: return dg_launch<9, false, float>(g, q, phiB, tau_edge, scale, fface, out, s, t);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_dg_nl_bf16(const Geom& g, const double* q, const double* phiB, const double* tau_edge,
+                              double scale, double* fface, double* out, cudaStream_t s, double t) {
+    switch (g.P) {
+        case 2: return dg_launch<2, false, float, true>(g, q, phiB, tau_edge, scale, fface, out, s, t);
+        case 3: return dg_launch<3, false, float, true>(g, q, phiB, tau_edge, scale, fface, out, s, t);
+        case 4: return dg_launch<4, false, float, true>(g, q, phiB, tau_edge, scale, fface, out, s, t);
+        case 5: return dg_launch<5, false, float, true>(g, q, phiB, tau_edge, scale, fface, out, s, t);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -866,9 +866,11 @@ cudaError_t condense_launch(const Geom& g, const LocalOps& ops, const double* R1
     if (ops.schur) {
         if (ops.kind == 3) schur_condense<P, ArithF2>(g, ops, R1, Z, s);
         else schur_condense<P, ArithF64>(g, ops, R1, Z, s);
-    } else if (ops.kind == 2) {
-        cudaError_t e = launch_local_tc(g, 0, ops.image, R1, nullptr, nullptr, nullptr, 0.0, 0.0, Z, nullptr,
-                                        ops.error, s);
+    } else if (ops.kind == 2 || ops.kind == 4) {
+        cudaError_t e = ops.kind == 2 ? launch_local_tc(g, 0, ops.image, R1, nullptr, nullptr, nullptr, 0.0, 0.0, Z,
+                                                        nullptr, ops.error, s)
+                                      : launch_local_tc_split(g, 0, ops.image, R1, nullptr, nullptr, nullptr, 0.0,
+                                                              0.0, Z, nullptr, ops.error, s);
         if (e != cudaSuccess) return e;
     } else if (ops.kind == 3) {
         x2_apply_tile<P>(ops.tile_condense_index, g, ops, R1, Z, s);
@@ -899,6 +901,8 @@ cudaError_t recover_launch(const Geom& g, const LocalOps& ops, const double* Z, 
     }
     if (ops.kind == 2)
         return launch_local_tc(g, 1, ops.image, R1, Z, tau_edge, qhat, beta, inv_aii, Q, Lst, ops.error, s);
+    if (ops.kind == 4)
+        return launch_local_tc_split(g, 1, ops.image, R1, Z, tau_edge, qhat, beta, inv_aii, Q, Lst, ops.error, s);
     if (ops.kind == 3) {
         x2_recover_tile<P>(ops.tile_recover_index, g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s);
         return cudaGetLastError();

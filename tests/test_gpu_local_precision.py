@@ -215,3 +215,119 @@ def test_f32x2_autotuned_tile():
         Q64, _, _ = s.stage_solve(R1)
     assert np.abs(gx - g64).max() <= 1e-12 * np.abs(g64).max()
     assert np.abs(Qx - Q64).max() <= 1e-12 * np.abs(Q64).max()
+
+
+# ---- FP64-class products on the tensor cores: BF16 slices (Ozaki splitting) ----------------------
+SLICES = 5
+
+
+def _exp_above(v):
+    """e with |v| < 2^e for the largest |v| (numpy frexp), -1074 for all zeros."""
+    m = np.abs(v).max(axis=-1)
+    _, e = np.frexp(m)
+    return np.where(m == 0.0, -1074, e)
+
+
+def _slices(v, e):
+    """Seven-bit integer slices t_i of v / 2^e, rounding to nearest even, as the device cuts them."""
+    u = np.ldexp(v, -np.where(e < -1000, 0, e)[..., None])
+    out = []
+    for _ in range(SLICES):
+        w = u * 128.0
+        r = np.rint(w)
+        out.append(r.astype(np.int64))
+        u = w - r
+    return out
+
+
+def _split_product(X, B):
+    """X @ B^T with the device's arithmetic, emulated exactly: rows of X (elements) and rows of B
+    (outputs; B[r][k] = (A^{-1})_{rk}) scaled and sliced, D_s = sum_{i+j=s} t_i s_j^T in integers,
+    combined and scaled by powers of two."""
+    er = _exp_above(X)                                   # [rows]
+    ec = _exp_above(B)                                   # [outputs]
+    tx = _slices(X, er)
+    tb = _slices(B, ec)
+    acc = np.zeros((X.shape[0], B.shape[0]), dtype=object)
+    for s in range(SLICES):
+        D = sum(tx[i].astype(object) @ tb[s - i].astype(object).T for i in range(s + 1))
+        acc = acc * 128 + D
+    scale = (er[:, None] + ec[None, :] - 7 * (SLICES + 1))
+    out = np.array([[float(np.ldexp(float(acc[a, b]), int(scale[a, b]))) for b in range(acc.shape[1])]
+                    for a in range(acc.shape[0])])
+    zero = (er[:, None] < -1000) | (ec[None, :] < -1000)
+    return np.where(zero, 0.0, out)
+
+
+@pytest.mark.parametrize("N,k", [(6, 3), (12, 2), (4, 4), (17, 3)])
+def test_split_tensor_core_condensation_matches_exact_emulation(N, k):
+    """Condensation with the sliced operator on the tensor cores: Z equals the exact emulation of the
+    slices' products (so g = -C Z equals it to the FP64 rounding of C), and Z is FP64-class: its
+    distance to the FP64 route is below 1e-9 of the field, 1e4 times below the BF16 variant's."""
+    m, h, hu, hv, b = _flat_case(N, k)
+    q, phiB = oracle_state(m, h, hu, hv, b)
+    dt = 0.4 / N
+    st = imex.Stepper(m, phiB, dt, solver="dense")
+    R1 = q + 0.01 * rng.standard_normal(q.shape)
+    Ainv, C = st.cond.Ainv, st.cond.C
+    Z = _split_product(_elem(R1), Ainv[0])               # the shared operator: every element's is the same
+    loc = -np.einsum("etv,ev->et", C, Z)
+    ref = np.bincount(st.cond.gi.ravel(), weights=loc.ravel(), minlength=st.cond.n)
+    ref = ref.reshape(m.n_edges, 3, m.P) / (m.face_jac * m.w)[None, None, :]
+    with hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, local_precision="bf16split") as s:
+        got = s.condense_rhs(flat(R1))
+    with hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0) as s:
+        g64 = s.condense_rhs(flat(R1))
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-13 * scale
+    assert np.abs(got - g64).max() <= 1e-9 * scale
+
+
+@pytest.mark.parametrize("N,k", [(6, 3), (12, 2)])
+def test_split_tensor_core_stage_solve_is_fp64_class(N, k):
+    m, h, hu, hv, b = _flat_case(N, k)
+    q, phiB = oracle_state(m, h, hu, hv, b)
+    dt = 0.4 / N
+    R1 = q + 0.01 * rng.standard_normal(q.shape)
+    with hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, local_precision="bf16split") as s:
+        Qs, lams, _ = s.stage_solve(flat(R1))
+    with hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0) as s:
+        Q64, lam64, _ = s.stage_solve(flat(R1))
+    assert np.abs(Qs - Q64).max() <= 1e-9 * np.abs(Q64).max()
+
+
+def test_split_tensor_core_bump8_200_steps_against_the_oracle():
+    """The precision variant of the 8x8 bump with the local contractions on the tensor cores as BF16
+    slices: every field within 1e-6 of the FP64 oracle after the 200 steps (BF16 operands: 1.0;
+    FP32 CUDA-core operands: 2.7e-5)."""
+    e, r_max = _bump8_run("bf16split", 200)
+    print(f"local bf16split, 200 steps: energy-norm rel {e:.3e}, largest field rel {r_max:.3e}")
+    assert e <= 1e-6 and r_max <= 1e-6
+
+
+def test_bf16_input_dg_residual_variant():
+    """The mixed form with the DG residual's inputs rounded to BF16 (FP32 arithmetic): its error
+    against the FP64 oracle after one step sits at the BF16 rounding of the nonlinear increment --
+    above the FP32 residual's and below 1e-3 -- and the 200 steps stay finite and within 1e-2."""
+    m, h, hu, hv, b = user_state(8, 2, "bump8")
+    hu = hu + 0.01 * np.sin(2 * np.pi * m.y.reshape(m.n_el, -1))    # a flow, so that the NL term is not zero
+    q, phiB = oracle_state(m, h, hu, hv, b)
+    dt = dt_of(m, h, hu, hv)
+    errs = {}
+    for dgp in ("default", "bf16"):
+        with hd.Sim(8, 2, dt, bottom=b, g=W.G, H0=W.H0, precision="mixed", local_precision="f32x2",
+                    trace_operator=1, dg_precision=dgp) as s:
+            s.set_state(h, hu, hv)
+            s.step(1)
+            one = swe.to_state(*s.get_state(), b, W.G, W.H0)[0]
+            s.step(199)
+            two = swe.to_state(*s.get_state(), b, W.G, W.H0)[0]
+        errs[dgp] = (one, two)
+    st = imex.Stepper(m, phiB, dt, solver="lu")
+    q1 = st.step(q)
+    q200 = st.run(q1, 199)
+    e1 = {k_: max(imex.rel_l2(m, v[0][c], q1[c]) for c in range(3)) for k_, v in errs.items()}
+    e200 = {k_: max(imex.rel_l2(m, v[1][c], q200[c]) for c in range(3)) for k_, v in errs.items()}
+    print(f"DG residual variants, 1 step: {e1}; 200 steps: {e200}")
+    assert e1["bf16"] <= 1e-3 and e1["bf16"] >= 10 * e1["default"]
+    assert e200["bf16"] <= 1e-2
