@@ -631,10 +631,11 @@ def paper_table_line():
 
 def precision_table_line(args):
     """Precision variants (the 8x8 bump recipe, flat bottom, 200 ARS2 steps): FP64 form, mixed form
-    with FP64 / FP32 / BF16 (tensor-core) local contractions -- relative L2 of eta, hu, hv and the
-    energy-norm error against the FP64 form (itself within 1e-9 of the oracle); and the time of
-    the local contractions per implicit stage on a 512x512, k = 3 flat-bottom case (the large
-    recipe with b = 0) for each local arithmetic."""
+    with FP64 / FP32 / BF16 (tensor cores) / BF16 slices (tensor cores, FP64-class) / FP32-pair local
+    contractions, and with the DG residual's inputs in BF16 -- relative L2 of eta, hu, hv and the
+    energy-norm error against the FP64 form (itself within 1e-9 of the oracle, as the tests
+    enforce); and the time of the local contractions per implicit stage on a 512x512, k = 3
+    flat-bottom case (the large recipe with b = 0) for each local arithmetic."""
     import torch
     from paper_1711_02751_gb300 import hdgdg as hd
     from paper_1711_02751_gb300 import workloads as W
@@ -644,8 +645,9 @@ def precision_table_line(args):
     dt = W.advective_dt(x, h, hu, hv, 8)
     wq = np.tile(np.outer(*(2 * [hd.gll(2)[1]])).ravel(), (64, 1))
 
-    def run(precision, local):
-        with hd.Sim(8, 2, dt, bottom=b, g=W.G, H0=W.H0, precision=precision, local_precision=local) as s:
+    def run(precision, local, dgp="default"):
+        with hd.Sim(8, 2, dt, bottom=b, g=W.G, H0=W.H0, precision=precision, local_precision=local,
+                    dg_precision=dgp) as s:
             s.set_state(h, hu, hv)
             t0 = time.perf_counter()
             s.step(200)
@@ -660,12 +662,14 @@ def precision_table_line(args):
         return float(np.sqrt(np.sum(wq * (a - r) ** 2) / np.sum(wq * r ** 2)))
 
     rows.append({"form": "fp64", "local": "fp64", "wall_s_200_steps": t_ref})
-    for local in ("fp64", "fp32", "bf16"):
-        out, t = run("mixed", local)
+    for local, dgp in (("fp64", "default"), ("fp32", "default"), ("bf16", "default"), ("bf16split", "default"),
+                       ("f32x2", "default"), ("f32x2", "bf16")):
+        out, t = run("mixed", local, dgp)
         e = (out[0] - B, out[1], out[2])
         num = np.sum(wq * ((e[0] - eref[0]) ** 2 + ((e[1] - eref[1]) ** 2 + (e[2] - eref[2]) ** 2) / (W.G * B)))
         den = np.sum(wq * (eref[0] ** 2 + (eref[1] ** 2 + eref[2] ** 2) / (W.G * B)))
-        rows.append({"form": "mixed", "local": local, "wall_s_200_steps": t,
+        rows.append({"form": "mixed", "local": local, "dg": "fp32" if dgp == "default" else "bf16 inputs",
+                     "wall_s_200_steps": t,
                      "rel_l2_vs_fp64": {"eta": rel(e[0], eref[0]), "hu": rel(e[1], eref[1]), "hv": rel(e[2], eref[2])},
                      "energy_rel_vs_fp64": float(np.sqrt(num / den))})
     # the local contractions' time on a large flat-bottom case
@@ -678,7 +682,7 @@ def precision_table_line(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     timing = []
-    for local in ("fp64", "fp32", "bf16"):
+    for local in ("fp64", "fp32", "bf16", "bf16split", "f32x2"):
         with hd.Sim(N, k, dtl, bottom=b, g=W.G, H0=W.H0, precision="mixed", local_precision=local,
                     stream=stream.cuda_stream) as s:
             s.set_state(h, hu, hv)
