@@ -14,6 +14,8 @@
 // B acts only on boundary volume nodes: B = -beta tau with beta = dt a (2/h) / w_0.
 // Schur complement (eq. linearizedHDGsystem_schur): S = D - C A^{-1} B, rhs -C A^{-1} R1;
 // recovery (eq. recover_volume_unknowns): Q = A^{-1}(R1 - B Qhat).
+#include <type_traits>
+
 #include "compensated.h"
 #include "internal.h"
 #include "schur.h"
@@ -599,11 +601,24 @@ __device__ __forceinline__ void schur_recover_body(int bid, const Geom& g, const
                            y[1], y[2]);
     if (live) {
         const double kk = beta * dt_factor(g, e);
-        for (int c = 0; c < 3; ++c) {
-            const size_t oc = c * fs + o;
-            const double q = Z[oc] + kk * A::to(y[c]);
-            Q[oc] = q;
-            Lst[oc] = (q - R1[oc]) * inv_aii;
+        if constexpr (std::is_same<T, float2>::value) {
+            // FP32 pairs to the end: Q = Z + kk y and L = (Q - R1) / a_ii as pair sums and products,
+            // one FP64 add per output (the pair's value) instead of five FP64 operations
+            const T kkp = A::from(kk), iap = A::from(inv_aii);
+            for (int c = 0; c < 3; ++c) {
+                const size_t oc = c * fs + o;
+                const T q = pair_add(A::from(Z[oc]), A::mul(kkp, y[c]));
+                const T r = A::from(R1[oc]);
+                Q[oc] = A::to(q);
+                Lst[oc] = A::to(A::mul(pair_add(q, float2{-r.x, -r.y}), iap));
+            }
+        } else {
+            for (int c = 0; c < 3; ++c) {
+                const size_t oc = c * fs + o;
+                const double q = Z[oc] + kk * A::to(y[c]);
+                Q[oc] = q;
+                Lst[oc] = (q - R1[oc]) * inv_aii;
+            }
         }
     }
 }
