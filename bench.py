@@ -820,7 +820,9 @@ def main():
                                          for c in ("condense", "recover") if r["ktimes"].get(c, (0, 0))[1] > 0},
                       "e2e": f["e2e"], "gpu_launches": r["launches"],
                       "local_tiles": {"condense": r["stats"].get("local_tile_condense", 0),
-                                      "recover": r["stats"].get("local_tile_recover", 0)}}
+                                      "recover": r["stats"].get("local_tile_recover", 0),
+                                      "trace_operator": r["stats"].get("trace_tile", 0),
+                                      "trace_operator_prefetch": r["stats"].get("trace_tile_prefetch", 0)}}
     hr = forms[head]["r"]
     per_step = hr["per_step"]
     p50 = statistics.median(per_step)

@@ -371,8 +371,9 @@ struct GuessTerms {
     int nq;
 };
 size_t guess_scratch_doubles();
-// f32x2: the candidates and sums in FP32-pair arithmetic (compensated Dot2; each candidate to
-// ~1e-13 ||g||, against ~1e-15 ||g|| in FP64) -- the mixed form, whose tolerance is 1e-9 ||g||.
+// f32x2 (the mixed form, whose tolerance is 1e-9 ||g||): the candidates formed in FP32 from the
+// differences g - y_0 and y_0 - y_j taken from FP32 pairs -- each candidate norm to FP32 relative
+// accuracy, enough to choose the start, whose norm the solve then takes exactly.
 cudaError_t launch_guess_norms(size_t n, const double* g, const GuessTerms& t, double* scratch, double* out,
                                cudaStream_t s, bool f32x2 = false);
 cudaError_t launch_multidot(const double* V, size_t ldv, int nv, const double* w, size_t n,

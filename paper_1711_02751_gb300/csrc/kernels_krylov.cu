@@ -317,10 +317,12 @@ guess_norms_kernel(size_t n, const double* __restrict__ g, GuessTerms t, double*
     }
 }
 
-// The same norms in FP32-pair arithmetic: g and the y_j split into FP32 pairs as they are loaded
-// (integer-pipe conversions), each candidate g - sum_j c[q][j] y_j formed as one compensated Dot2
-// sum (the binomial coefficients are exact in FP32) and its square summed the same way.  GB300's
-// FP64 rate would otherwise bound this pass (about 21 FP64 operations per trace entry at order 5).
+// The same norms for the mixed form, whose tolerance is 1e-9 ||g||: the candidates only choose the
+// start, and an extrapolated start's norm is then taken exactly.  Every order's coefficients sum to
+// one, so g - sum_j c[q][j] y_j = (g - y_0) + sum_{j>=1} c[q][j] (y_0 - y_j): the differences of
+// nearly equal vectors are formed first from FP32 pairs (the high parts subtract exactly, the low
+// parts' difference is added), which keeps each small difference to FP32 relative accuracy; the
+// candidates and their squares then run in plain FP32, and the sums across threads in FP64.
 __global__ void __launch_bounds__(kDotThreads)
 guess_norms_x2_kernel(size_t n, const double* __restrict__ g, GuessTerms t, double* __restrict__ scratch,
                       double* __restrict__ out) {
@@ -328,38 +330,44 @@ guess_norms_x2_kernel(size_t n, const double* __restrict__ g, GuessTerms t, doub
     unsigned* counter = reinterpret_cast<unsigned*>(scratch);
     double* partial = scratch + 1;
     __shared__ double sh[NQ][kDotThreads / 32];
-    __shared__ float nc[NQ][6];   // -c[q][j]
-    if (threadIdx.x < NQ * 6) nc[threadIdx.x / 6][threadIdx.x % 6] = -f64_to_f32(t.c[threadIdx.x / 6][threadIdx.x % 6]);
+    __shared__ float cf[NQ][6];   // c[q][j] (binomial coefficients: exact in FP32)
+    if (threadIdx.x < NQ * 6) cf[threadIdx.x / 6][threadIdx.x % 6] = f64_to_f32(t.c[threadIdx.x / 6][threadIdx.x % 6]);
     __syncthreads();
-    Dot2 acc[NQ];
+    float acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.f;
     for (size_t idx = blockIdx.x * (size_t)kDotThreads + threadIdx.x; idx < n;
          idx += (size_t)gridDim.x * kDotThreads) {
-        float gh, gl, yh[6], yl[6];
+        float gh, gl, y0h = 0.f, y0l = 0.f;
         split(g[idx], gh, gl);
+        split(t.y[0][idx], y0h, y0l);
+        const float e = __fadd_rn(__fsub_rn(gh, y0h), __fsub_rn(gl, y0l));   // g - y_0
+        float d[6];                                                         // y_0 - y_j
+        d[0] = 0.f;
 #pragma unroll
-        for (int j = 0; j < 6; ++j) {
-            yh[j] = 0.f;
-            yl[j] = 0.f;
-            if (j < t.nq) split(t.y[j][idx], yh[j], yl[j]);
+        for (int j = 1; j < 6; ++j) {
+            d[j] = 0.f;
+            if (j < t.nq) {
+                float yh, yl;
+                split(t.y[j][idx], yh, yl);
+                d[j] = __fadd_rn(__fsub_rn(y0h, yh), __fsub_rn(y0l, yl));
+            }
         }
-        acc[0].add(gh, gl, gh, gl);
+        acc[0] = __fmaf_rn(gh, gh, acc[0]);
 #pragma unroll
         for (int q = 1; q < NQ; ++q) {
             if (q > t.nq) break;
-            Dot2 r;
-            r.add(1.f, 0.f, gh, gl);
+            float r = e;
 #pragma unroll
-            for (int j = 0; j < 6; ++j)
-                if (j < q) r.add(nc[q][j], 0.f, yh[j], yl[j]);
-            float rh, rl;
-            two_sum(r.p, r.c, rh, rl);
-            acc[q].add(rh, rl, rh, rl);
+            for (int j = 1; j < 6; ++j)
+                if (j < q) r = __fmaf_rn(cf[q][j], d[j], r);
+            acc[q] = __fmaf_rn(r, r, acc[q]);
         }
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-        const double s = warp_sum(acc[q].value());
+        const double s = warp_sum(f32_to_f64(acc[q]));
         if (lane == 0) sh[q][wid] = s;
     }
     __syncthreads();

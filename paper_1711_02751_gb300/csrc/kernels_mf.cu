@@ -55,9 +55,11 @@ template <int P>
 __host__ __device__ constexpr int mf_epb() {
     return mf_epb_for<P>(256);
 }
-constexpr int kMfTiles = 6;
+// tiles 6..8: no prefetch, registers capped for a full SM (64 warps) -- more elements in flight
+constexpr int kMfTiles = 9;
 constexpr int mf_tile_threads(int t) { return t % 3 == 0 ? 256 : t % 3 == 1 ? 128 : 512; }
 constexpr bool mf_tile_pref(int t) { return t < 3; }
+constexpr int mf_tile_minb(int t) { return t >= 6 ? 2048 / mf_tile_threads(t) : 1; }
 
 template <class A>
 __device__ __forceinline__ typename A::T arith_of_f32(float v) {
@@ -238,8 +240,8 @@ __device__ __forceinline__ void mf_elem_body(int bid, const Geom& g, const typen
     }
 }
 
-template <int P, int EPB, class A, int MODE, bool PREF>
-__global__ void __launch_bounds__(EPB * P * P)
+template <int P, int EPB, class A, int MODE, bool PREF, int MINB = 1>
+__global__ void __launch_bounds__(EPB * P * P, MINB)
     mf_elem_kernel(Geom g, const typename A::T* __restrict__ S, const typename A::T* __restrict__ aux,
                    const typename A::T* __restrict__ EG, const double* __restrict__ tau_edge,
                    const void* __restrict__ yv, MfVec<MODE>* __restrict__ hm, MfVec<MODE>* __restrict__ hp,
@@ -303,7 +305,7 @@ void mf_elem_launch(const Geom& g, const void* S, const void* aux, const void* E
                     MfVec<MODE>* hm, MfVec<MODE>* hp, double beta, cudaStream_t s, const int* done) {
     using T = typename A::T;
     constexpr int EPB = mf_epb_for<P>(mf_tile_threads(TILE));
-    mf_elem_kernel<P, EPB, A, MODE, mf_tile_pref(TILE)><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(
+    mf_elem_kernel<P, EPB, A, MODE, mf_tile_pref(TILE), mf_tile_minb(TILE)><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(
         g, static_cast<const T*>(S), static_cast<const T*>(aux), static_cast<const T*>(EG), tau, yv, hm, hp, beta,
         done);
 }
@@ -319,6 +321,9 @@ void mf_elem_tile(int t, const Geom& g, const void* S, const void* aux, const vo
             case 3: return mf_elem_launch<P, A, MODE, 3>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
             case 4: return mf_elem_launch<P, A, MODE, 4>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
             case 5: return mf_elem_launch<P, A, MODE, 5>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
+            case 6: return mf_elem_launch<P, A, MODE, 6>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
+            case 7: return mf_elem_launch<P, A, MODE, 7>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
+            case 8: return mf_elem_launch<P, A, MODE, 8>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
             default: break;
         }
     }
