@@ -601,24 +601,11 @@ __device__ __forceinline__ void schur_recover_body(int bid, const Geom& g, const
                            y[1], y[2]);
     if (live) {
         const double kk = beta * dt_factor(g, e);
-        if constexpr (std::is_same<T, float2>::value) {
-            // FP32 pairs to the end: Q = Z + kk y and L = (Q - R1) / a_ii as pair sums and products,
-            // one FP64 add per output (the pair's value) instead of five FP64 operations
-            const T kkp = A::from(kk), iap = A::from(inv_aii);
-            for (int c = 0; c < 3; ++c) {
-                const size_t oc = c * fs + o;
-                const T q = pair_add(A::from(Z[oc]), A::mul(kkp, y[c]));
-                const T r = A::from(R1[oc]);
-                Q[oc] = A::to(q);
-                Lst[oc] = A::to(A::mul(pair_add(q, float2{-r.x, -r.y}), iap));
-            }
-        } else {
-            for (int c = 0; c < 3; ++c) {
-                const size_t oc = c * fs + o;
-                const double q = Z[oc] + kk * A::to(y[c]);
-                Q[oc] = q;
-                Lst[oc] = (q - R1[oc]) * inv_aii;
-            }
+        for (int c = 0; c < 3; ++c) {
+            const size_t oc = c * fs + o;
+            const double q = Z[oc] + kk * A::to(y[c]);
+            Q[oc] = q;
+            Lst[oc] = (q - R1[oc]) * inv_aii;
         }
     }
 }
@@ -680,7 +667,7 @@ void schur_recover(const Geom& g, const LocalOps& ops, const double* Z, const do
     schur_recover_t<P, A, 0>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s);
 }
 
-// Time each tile of the Schur condensation and recovery (one warm-up and three timed launches
+// Time each tile of the Schur condensation and recovery (two warm-up and five timed launches
 // each, CUDA events) on the handle's operators and keep the fastest of each in ops.
 template <int P, class A>
 cudaError_t autotune_schur(const Geom& g, LocalOps& ops, double* R1, double* Z, const double* tau_edge,
@@ -700,15 +687,15 @@ cudaError_t autotune_schur(const Geom& g, LocalOps& ops, double* R1, double* Z, 
         for (int t = 0; t < 3 && err == cudaSuccess; ++t) {
             ops.schur_tile_c = ops.schur_tile_r = t;
             float ms_c = 0.f, ms_r = 0.f;
-            schur_condense<P, A>(g, ops, R1, Z, s);
+            for (int k = 0; k < 2; ++k) schur_condense<P, A>(g, ops, R1, Z, s);
             cudaEventRecord(a, s);
-            for (int k = 0; k < 3; ++k) schur_condense<P, A>(g, ops, R1, Z, s);
+            for (int k = 0; k < 5; ++k) schur_condense<P, A>(g, ops, R1, Z, s);
             cudaEventRecord(b, s);
             err = cudaEventSynchronize(b);
             if (err == cudaSuccess) err = cudaEventElapsedTime(&ms_c, a, b);
-            schur_recover<P, A>(g, ops, Z, R1, tau_edge, qhat, 1.0, 1.0, Q, Lst, s);
+            for (int k = 0; k < 2; ++k) schur_recover<P, A>(g, ops, Z, R1, tau_edge, qhat, 1.0, 1.0, Q, Lst, s);
             cudaEventRecord(a, s);
-            for (int k = 0; k < 3; ++k) schur_recover<P, A>(g, ops, Z, R1, tau_edge, qhat, 1.0, 1.0, Q, Lst, s);
+            for (int k = 0; k < 5; ++k) schur_recover<P, A>(g, ops, Z, R1, tau_edge, qhat, 1.0, 1.0, Q, Lst, s);
             cudaEventRecord(b, s);
             if (err == cudaSuccess) err = cudaEventSynchronize(b);
             if (err == cudaSuccess) err = cudaEventElapsedTime(&ms_r, a, b);

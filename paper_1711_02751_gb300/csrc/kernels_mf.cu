@@ -462,8 +462,8 @@ cudaError_t launch_mf_plain(const Geom& g, const MfOps& op, const double* x, dou
 #undef CASE
 }
 
-// Time each tile of the inner cycles' element pass on the handle's own operators (one warm-up and
-// three timed products each, CUDA events on the stream; x and y are scratch trace vectors) and keep
+// Time each tile of the inner cycles' element pass on the handle's own operators (two warm-up and
+// five timed products each, CUDA events on the stream; x and y are scratch trace vectors) and keep
 // the fastest in op.tile.  The tile changes no thread's arithmetic, only how elements share blocks.
 cudaError_t launch_mf_autotune(const Geom& g, MfOps& op, const float* x, float* y, double beta, cudaStream_t s,
                                int* epb, int* prefetch) {
@@ -482,9 +482,9 @@ cudaError_t launch_mf_autotune(const Geom& g, MfOps& op, const float* x, float* 
     cudaError_t err = cudaSuccess;
     for (int t = 0; t < kMfTiles && err == cudaSuccess; ++t) {
         op.tile = t;
-        err = launch_mf_inner(g, op, x, y, beta, s);
+        for (int k = 0; k < 2 && err == cudaSuccess; ++k) err = launch_mf_inner(g, op, x, y, beta, s);
         if (err == cudaSuccess) err = cudaEventRecord(a, s);
-        for (int k = 0; k < 3 && err == cudaSuccess; ++k) err = launch_mf_inner(g, op, x, y, beta, s);
+        for (int k = 0; k < 5 && err == cudaSuccess; ++k) err = launch_mf_inner(g, op, x, y, beta, s);
         if (err == cudaSuccess) err = cudaEventRecord(b, s);
         if (err == cudaSuccess) err = cudaEventSynchronize(b);
         float ms = 0.f;

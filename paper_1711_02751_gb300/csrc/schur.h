@@ -60,18 +60,6 @@ struct ArithF2 {
 template <class A>
 __device__ __forceinline__ void store_from(typename A::T* dst, double v) { *dst = A::from(v); }
 
-// (a_hi + a_lo) + (b_hi + b_lo) as an FP32 pair: TwoSum of the high parts, the low parts added to its
-// error, renormalised (about 2^-44 relative; the summands' low parts are not summed exactly)
-__device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
-    float s, e;
-    two_sum(a.x, b.x, s, e);
-    e = __fadd_rn(e, __fadd_rn(a.y, b.y));
-    float2 r;
-    r.x = __fadd_rn(s, e);
-    r.y = __fsub_rn(e, __fsub_rn(r.x, s));
-    return r;
-}
-
 // ArithF32: plain FP32 arithmetic (the inner cycles of the mixed form's trace solve).
 struct ArithF32 {
     using T = float;
