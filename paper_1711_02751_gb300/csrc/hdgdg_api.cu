@@ -125,8 +125,8 @@ Plan make_plan(const hdgdg_config* c) {
     }
     if (c->precision == HDGDG_MIXED && c->residual_f32x2 && !matrix_free(c))
         b += n_edges * 6 * (size_t)p.NF * p.NF * sizeof(float);
-    if (matrix_free(c)) {   // FP32 M^{-1}, FP32 Schur operators, the plus-side halves, one ticket per edge
-        b += n_edges * (size_t)p.NF * p.NF * sizeof(float);
+    if (matrix_free(c)) {   // FP16 M^{-1} and scales, FP32 Schur operators, the operator's scratch
+        b += n_edges * (size_t)p.NF * p.NF * sizeof(__half) + n_edges * sizeof(float);
         b += (n_el * Np * Np + 4 * n_el * Np + 2 * B * Np) * sizeof(float);
         b += 3 * p.nt * d;   // M^{-1} x and the two halves of S y
     }
@@ -336,7 +336,8 @@ struct hdgdg_sim {
     const EnsHost* ens = nullptr;   // an ensemble's super-handle: its group table (kernels walk every group)
     MfOps mf;                   // trace_operator = 1: the matrix-free operator's data
     int trace_tile = 0, trace_prefetch = 0;   // its autotuned element-pass tile (0: default)
-    float* Minv32 = nullptr;    // its FP32 block-Jacobi inverse
+    __half* Minv16 = nullptr;   // its block-Jacobi inverse: FP16 blocks ...
+    float* Mscale = nullptr;    // ... and their power-of-two scales
     double *red = nullptr, *mred = nullptr, *dvals = nullptr;
     GmresCtl* ctl = nullptr;
     CycleGraph cycle_graph[4];   // [FP64 form, mixed form] x [timers off, on]
@@ -725,7 +726,7 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
     }
     {
         TimedGroup tg(sim, HDGDG_KT_PRECOND);
-        if (kMixed && matrix_free(&sim->cfg)) CU(launch_mf_back(sim->g, sim->Minv32, sim->xt, qhat, st));
+        if (kMixed && matrix_free(&sim->cfg)) CU(launch_mf_back(sim->g, sim->mf.Minv, sim->xt, qhat, st));
         else CU(launch_block_diag(sim->g, sim->Minv, sim->xt, qhat, st, sim->minv_pairs));
     }
     const int order = guess_order(&sim->cfg);
@@ -851,7 +852,7 @@ cudaError_t solve_enqueue_graph(hdgdg_sim* sim, const double* g, double* qhat, i
     if (e == cudaSuccess) e = launch_solve_end(sim->ctl, sim->sctl, sim->sstats, st);
     if (e == cudaSuccess) {
         if (sim->ens) e = launch_ens_mf_back(*sim->ens, sim->xt, qhat, st);
-        else if (kMixed && matrix_free(&sim->cfg)) e = launch_mf_back(sim->g, sim->Minv32, sim->xt, qhat, st);
+        else if (kMixed && matrix_free(&sim->cfg)) e = launch_mf_back(sim->g, sim->mf.Minv, sim->xt, qhat, st);
         else e = launch_block_diag(sim->g, sim->Minv, sim->xt, qhat, st, sim->minv_pairs);
     }
     if (e == cudaSuccess && stage >= 0 && order > 0) {   // x~ and S~ x~ = g - r into the slot that becomes newest
@@ -1236,7 +1237,7 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
     if (e == cudaSuccess)
         e = launch_assemble_trace(g, Se, S7, sim->Srr, sim->Minv, sim->Stil, sim->Scol, dsing, sim->stream);
     if (e == cudaSuccess && c->precision == HDGDG_MIXED && matrix_free(c)) {
-        sim->Minv32 = nullptr;   // (allocated below, after the setup temporaries are released)
+        sim->Minv16 = nullptr;   // (allocated below, after the setup temporaries are released)
     } else if (e == cudaSuccess && c->precision == HDGDG_MIXED) {
         if (sim->Stil_lo) {   // hi part = the FP32 copy of the inner cycles, lo part = the rest
             e = launch_split_f32x2(sim->Stil, sim->Stil32, sim->Stil_lo, (size_t)g.n_edges * 6 * p.NF * p.NF,
@@ -1276,21 +1277,23 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
             TRY(dalloc(sim, &S32, nS));
             TRY(dalloc(sim, &aux32, nA));
             TRY(dalloc(sim, &EG32, nE));
-            TRY(dalloc(sim, &sim->Minv32, (size_t)g.n_edges * p.NF * p.NF));
+            TRY(dalloc(sim, &sim->Minv16, (size_t)g.n_edges * p.NF * p.NF));
+            TRY(dalloc(sim, &sim->Mscale, (size_t)g.n_edges));
             TRY(dalloc(sim, &ybuf, p.nt));
             TRY(dalloc(sim, &hm, p.nt));
             TRY(dalloc(sim, &hp, p.nt));
             CU(launch_pair_hi(sim->Sphi, S32, nS, sim->stream));
             CU(launch_pair_hi(sim->Saux, aux32, nA, sim->stream));
             CU(launch_pair_hi(sim->Seg, EG32, nE, sim->stream));
-            CU(launch_to_f32(sim->Minv, sim->Minv32, (size_t)g.n_edges * p.NF * p.NF, sim->stream));
+            CU(launch_precond_f16(sim->Minv, g.n_edges, p.NF, sim->Minv16, sim->Mscale, sim->stream));
             sim->mf.S32 = S32;
             sim->mf.aux32 = aux32;
             sim->mf.EG32 = EG32;
             sim->mf.S2 = sim->Sphi;
             sim->mf.aux2 = sim->Saux;
             sim->mf.EG2 = sim->Seg;
-            sim->mf.Minv32 = sim->Minv32;
+            sim->mf.Minv.h = sim->Minv16;
+            sim->mf.Minv.scale = sim->Mscale;
             sim->mf.tau = sim->tau;
             sim->mf.ybuf = ybuf;
             sim->mf.hm = hm;
@@ -1894,7 +1897,7 @@ hdgdg_status hdgdg_ensemble_create(const hdgdg_config* base, int n_members, cons
         G.S32 = gs->mf.S32;
         G.aux32 = gs->mf.aux32;
         G.EG32 = gs->mf.EG32;
-        G.Minv32 = gs->Minv32;
+        G.Minv = gs->mf.Minv;
         off3 += 3 * gs->plan.n;
         offt += gs->plan.nt;
         n_total += gs->plan.n;

@@ -15,6 +15,7 @@
 // face 1/3 is the edge's "minus" side (normal +x / +y), the element on face 0/2 its "plus" side.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -275,12 +276,20 @@ cudaError_t launch_recover(const Geom& g, const LocalOps& ops, const double* Z, 
 // FP32-pair kernels.  No-op for other local arithmetic.
 cudaError_t launch_autotune_local(const Geom& g, LocalOps& ops, double* R1, double* Z, const double* tau_edge,
                                   const double* qhat, double* Q, double* Lst, cudaStream_t s);
+// The block-Jacobi inverse of the matrix-free operator: per edge its NF x NF block (column major) as
+// FP16 values of the block divided by a power of two, and that power of two (the block's scale).
+// The values are the preconditioner -- every use (inner cycles, refinement residual,
+// back-transformation) reads these same numbers.
+struct PrecondBlocks {
+    const __half* h = nullptr;
+    const float* scale = nullptr;
+};
 // Matrix-free trace operator (kernels_mf.cu): S x = D x - C A^{-1} B x element by element through
 // the Schur-complement local solve, with the block-Jacobi preconditioner M^{-1} applied first.
 struct MfOps {
     const float *S32 = nullptr, *aux32 = nullptr, *EG32 = nullptr;   // Schur operators, FP32 (inner cycles)
     const void *S2 = nullptr, *aux2 = nullptr, *EG2 = nullptr;       // the same as FP32 pairs (float2)
-    const float* Minv32 = nullptr;   // block-Jacobi inverse [edge][col][row], FP32
+    PrecondBlocks Minv;              // block-Jacobi inverse [edge][col][row], FP16 with a scale per edge
     const double* tau = nullptr;     // tau_hat [edge][P]
     void* ybuf = nullptr;            // scratch: M^{-1} x (n_edges * 3P values of 8 bytes)
     void* hm = nullptr;              // scratch: the edges' minus-side halves of S y (8 bytes per value)
@@ -300,7 +309,9 @@ cudaError_t launch_mf_plain(const Geom& g, const MfOps& op, const double* x, dou
 cudaError_t launch_mf_autotune(const Geom& g, MfOps& op, const float* x, float* y, double beta, cudaStream_t s,
                                int* epb, int* prefetch);
 // qhat = M^{-1} x~ with the FP32 blocks, FP64-class sums
-cudaError_t launch_mf_back(const Geom& g, const float* Minv32, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_mf_back(const Geom& g, const PrecondBlocks& M, const double* x, double* y, cudaStream_t s);
+// The FP16 blocks and scales from the FP64 block-Jacobi inverse (setup).
+cudaError_t launch_precond_f16(const double* Minv, int n_edges, int NF, __half* h, float* scale, cudaStream_t s);
 // hi[t] = pairs[t].x for n FP32 pairs (float2)
 cudaError_t launch_pair_hi(const void* pairs, float* hi, size_t n, cudaStream_t s);
 // hi = (float)a, lo = (float)(a - hi): the FP32-pair copy of an FP64 array.
@@ -409,7 +420,7 @@ struct EnsGroup {
     const double* tau;
     const void *S2, *aux2, *EG2;          // Schur-complement operators as FP32 pairs
     const float *S32, *aux32, *EG32;      // and as FP32 (the inner cycles)
-    const float* Minv32;                  // block-Jacobi inverse, FP32
+    PrecondBlocks Minv;                   // block-Jacobi inverse, FP16 blocks and scales
 };
 struct EnsTable {               // one launch: the groups and the first work item of each
     const EnsGroup* grp;        // device array [ngroups]

@@ -15,7 +15,7 @@
 //
 // Three launches per product, each short, so that no block waits on a chain of dependent
 // memory round trips:
-//   mf_pre_kernel   y = M^{-1} x, one thread per edge row (block-Jacobi inverse in FP32);
+//   mf_pre_kernel   y = M^{-1} x, one thread per edge row (block-Jacobi inverse in scaled FP16);
 //   mf_elem_kernel  one thread per (element, node): the node's traces y gathered straight into
 //                   registers, the operator data loaded before them, the lift, the local solve,
 //                   and the element's half of each face's row -- the edge's minus side (face 1 or
@@ -26,9 +26,10 @@
 //   kMfInner     y = S M^{-1} x        FP32 arithmetic and vectors (the mixed form's inner cycles)
 //   kMfResidual  w = g - S M^{-1} x    FP64-class FP32-pair arithmetic, FP64 vectors (refinement)
 //   kMfPlain     y = S x               FP64-class, FP64 vectors (the row-level entry point)
-// M^{-1} is the block-Jacobi inverse held in FP32 [edge][col][row]; the residual and the final
-// back-transformation qhat = M^{-1} x~ use exactly these FP32 values, so the preconditioner is
-// the same matrix on every path.
+// M^{-1} is the block-Jacobi inverse held per edge as FP16 values of the block scaled by a power of
+// two (PrecondBlocks); the inner cycles, the residual and the final back-transformation
+// qhat = M^{-1} x~ use exactly these values, so the preconditioner is the same matrix on every path.
+#include <cuda_fp16.h>
 #include <type_traits>
 
 #include "compensated.h"
@@ -74,6 +75,13 @@ __device__ __forceinline__ typename A::T arith_load(const TX* p) {
     else return A::from(*p);
 }
 
+// v * 2^k for an arithmetic value (exact: a power of two)
+template <class A>
+__device__ __forceinline__ typename A::T arith_scale(typename A::T v, float s) {
+    if constexpr (std::is_same<typename A::T, float2>::value) return float2{v.x * s, v.y * s};
+    else return v * (typename A::T)s;
+}
+
 // the element's half of a row, stored in the mode's vector type
 template <class A, typename TO>
 __device__ __forceinline__ TO arith_store(typename A::T v) {
@@ -83,7 +91,7 @@ __device__ __forceinline__ TO arith_store(typename A::T v) {
 
 // y = M^{-1} x per edge (one thread per row component), y in the arithmetic's own type
 template <int NF, class A, typename TX>
-__device__ __forceinline__ void mf_pre_body(int bid, int n_edges, const float* __restrict__ Minv,
+__device__ __forceinline__ void mf_pre_body(int bid, int n_edges, PrecondBlocks Minv,
                                             const TX* __restrict__ x, typename A::T* __restrict__ y) {
     using T = typename A::T;
     constexpr int EPB = 256 / NF;
@@ -94,16 +102,16 @@ __device__ __forceinline__ void mf_pre_body(int bid, int n_edges, const float* _
     if (live) xs[le][ii] = arith_load<A>(x + (size_t)r * NF + ii);
     __syncthreads();
     if (!live) return;
-    const float* M = Minv + (size_t)r * NF * NF + ii;
+    const __half* M = Minv.h + (size_t)r * NF * NF + ii;
     typename A::Acc acc;
 #pragma unroll
-    for (int jj = 0; jj < NF; ++jj) acc.add(arith_of_f32<A>(__ldg(M + jj * NF)), xs[le][jj]);
-    y[(size_t)r * NF + ii] = acc.get();
+    for (int jj = 0; jj < NF; ++jj) acc.add(arith_of_f32<A>(__half2float(M[jj * NF])), xs[le][jj]);
+    y[(size_t)r * NF + ii] = arith_scale<A>(acc.get(), __ldg(Minv.scale + r));
 }
 
 template <int NF, class A, typename TX>
 __global__ void __launch_bounds__(256)
-mf_pre_kernel(int n_edges, const float* __restrict__ Minv, const TX* __restrict__ x, typename A::T* __restrict__ y,
+mf_pre_kernel(int n_edges, PrecondBlocks Minv, const TX* __restrict__ x, typename A::T* __restrict__ y,
               const int* __restrict__ done) {
     if (done && *done) return;
     mf_pre_body<NF, A, TX>(blockIdx.x, n_edges, Minv, x, y);
@@ -265,7 +273,7 @@ mf_sum_kernel(size_t n, const TO* __restrict__ hm, const TO* __restrict__ hp, co
 
 // qhat = M^{-1} x~ with the FP32 block-Jacobi blocks, FP64-class sums (x split into FP32 pairs).
 template <int NF>
-__device__ __forceinline__ void mf_back_body(int bid, int n_edges, const float* __restrict__ Minv,
+__device__ __forceinline__ void mf_back_body(int bid, int n_edges, PrecondBlocks Minv,
                                              const double* __restrict__ x, double* __restrict__ y) {
     constexpr int EPB = 256 / NF;
     __shared__ float sxh[EPB][NF], sxl[EPB][NF];
@@ -275,17 +283,40 @@ __device__ __forceinline__ void mf_back_body(int bid, int n_edges, const float* 
     if (live) split(x[(size_t)r * NF + ii], sxh[le][ii], sxl[le][ii]);
     __syncthreads();
     if (!live) return;
-    const float* M = Minv + (size_t)r * NF * NF;
+    const __half* M = Minv.h + (size_t)r * NF * NF;
     Dot2 acc;
 #pragma unroll
-    for (int jj = 0; jj < NF; ++jj) acc.add(M[jj * NF + ii], 0.f, sxh[le][jj], sxl[le][jj]);
-    y[(size_t)r * NF + ii] = acc.value();
+    for (int jj = 0; jj < NF; ++jj) acc.add(__half2float(M[jj * NF + ii]), 0.f, sxh[le][jj], sxl[le][jj]);
+    const float sc = Minv.scale[r];   // a power of two: scaling the pair is exact
+    y[(size_t)r * NF + ii] = f32_to_f64(acc.p * sc) + f32_to_f64(acc.c * sc);
 }
 
 template <int NF>
 __global__ void __launch_bounds__(256)
-mf_back_kernel(int n_edges, const float* __restrict__ Minv, const double* __restrict__ x, double* __restrict__ y) {
+mf_back_kernel(int n_edges, PrecondBlocks Minv, const double* __restrict__ x, double* __restrict__ y) {
     mf_back_body<NF>(blockIdx.x, n_edges, Minv, x, y);
+}
+
+// Setup: per edge (one block) the FP16 block-Jacobi inverse scaled by the power of two 2^e with
+// max |entry| / 2^e in [0.5, 1), and that scale.
+__global__ void precond_f16_kernel(const double* __restrict__ Minv, int NF, __half* __restrict__ h,
+                                   float* __restrict__ scale) {
+    const int r = blockIdx.x;
+    const double* M = Minv + (size_t)r * NF * NF;
+    __shared__ double red[256];
+    double m = 0.0;
+    for (int t = threadIdx.x; t < NF * NF; t += blockDim.x) m = fmax(m, fabs(M[t]));
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + k]);
+        __syncthreads();
+    }
+    int e = 0;
+    (void)frexp(red[0], &e);
+    if (red[0] == 0.0) e = 0;
+    for (int t = threadIdx.x; t < NF * NF; t += blockDim.x) h[(size_t)r * NF * NF + t] = __double2half(ldexp(M[t], -e));
+    if (threadIdx.x == 0) scale[r] = ldexpf(1.0f, e);
 }
 
 // hi parts of FP32 pairs
@@ -341,7 +372,7 @@ cudaError_t mf_launch(const Geom& g, const MfOps& op, const void* S, const void*
     if constexpr (MODE != kMfPlain) {
         constexpr int EPE = 256 / NF;
         mf_pre_kernel<NF, A, TO><<<(g.n_edges + EPE - 1) / EPE, EPE * NF, 0, s>>>(
-            g.n_edges, op.Minv32, static_cast<const TO*>(x), static_cast<T*>(op.ybuf), done);
+            g.n_edges, op.Minv, static_cast<const TO*>(x), static_cast<T*>(op.ybuf), done);
         yv = op.ybuf;
     }
     TO* hm = static_cast<TO*>(op.hm);
@@ -360,9 +391,9 @@ __global__ void __launch_bounds__(256) ens_mf_pre_kernel(EnsTable t, const TX* _
     if (done && *done) return;
     ens_walk(t, [&](const EnsGroup& G, int bid) {
         switch (G.g.P) {
-            case 3: mf_pre_body<9, A, TX>(bid, G.g.n_edges, G.Minv32, x + G.offt, y + G.offt); break;
-            case 4: mf_pre_body<12, A, TX>(bid, G.g.n_edges, G.Minv32, x + G.offt, y + G.offt); break;
-            case 5: mf_pre_body<15, A, TX>(bid, G.g.n_edges, G.Minv32, x + G.offt, y + G.offt); break;
+            case 3: mf_pre_body<9, A, TX>(bid, G.g.n_edges, G.Minv, x + G.offt, y + G.offt); break;
+            case 4: mf_pre_body<12, A, TX>(bid, G.g.n_edges, G.Minv, x + G.offt, y + G.offt); break;
+            case 5: mf_pre_body<15, A, TX>(bid, G.g.n_edges, G.Minv, x + G.offt, y + G.offt); break;
             default: break;
         }
     });
@@ -392,9 +423,9 @@ __global__ void __launch_bounds__(256) ens_mf_elem_kernel(EnsTable t, const type
 __global__ void __launch_bounds__(256) ens_mf_back_kernel(EnsTable t, const double* __restrict__ x, double* __restrict__ y) {
     ens_walk(t, [&](const EnsGroup& G, int bid) {
         switch (G.g.P) {
-            case 3: mf_back_body<9>(bid, G.g.n_edges, G.Minv32, x + G.offt, y + G.offt); break;
-            case 4: mf_back_body<12>(bid, G.g.n_edges, G.Minv32, x + G.offt, y + G.offt); break;
-            case 5: mf_back_body<15>(bid, G.g.n_edges, G.Minv32, x + G.offt, y + G.offt); break;
+            case 3: mf_back_body<9>(bid, G.g.n_edges, G.Minv, x + G.offt, y + G.offt); break;
+            case 4: mf_back_body<12>(bid, G.g.n_edges, G.Minv, x + G.offt, y + G.offt); break;
+            case 5: mf_back_body<15>(bid, G.g.n_edges, G.Minv, x + G.offt, y + G.offt); break;
             default: break;
         }
     });
@@ -520,11 +551,11 @@ cudaError_t launch_ens_mf_back(const EnsHost& E, const double* x, double* y, cud
     return cudaGetLastError();
 }
 
-cudaError_t launch_mf_back(const Geom& g, const float* Minv32, const double* x, double* y, cudaStream_t s) {
+cudaError_t launch_mf_back(const Geom& g, const PrecondBlocks& Minv, const double* x, double* y, cudaStream_t s) {
 #define CASE(P, NF)                                                                                      \
     case P: {                                                                                            \
         constexpr int EPB = 256 / NF;                                                                    \
-        mf_back_kernel<NF><<<(g.n_edges + EPB - 1) / EPB, EPB * NF, 0, s>>>(g.n_edges, Minv32, x, y);   \
+        mf_back_kernel<NF><<<(g.n_edges + EPB - 1) / EPB, EPB * NF, 0, s>>>(g.n_edges, Minv, x, y);     \
         count_launches(1);                                                                               \
         return cudaGetLastError();                                                                       \
     }
@@ -533,6 +564,12 @@ cudaError_t launch_mf_back(const Geom& g, const float* Minv32, const double* x, 
         default: return cudaErrorInvalidValue;
     }
 #undef CASE
+}
+
+cudaError_t launch_precond_f16(const double* Minv, int n_edges, int NF, __half* h, float* scale, cudaStream_t s) {
+    precond_f16_kernel<<<n_edges, 256, 0, s>>>(Minv, NF, h, scale);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pair_hi(const void* pairs, float* hi, size_t n, cudaStream_t s) {
