@@ -59,7 +59,7 @@ def _args():
                     help="refinement tolerance of the mixed form (0: library default 1e-9)")
     ap.add_argument("--precisions", default="fp64,mixed",
                     help="forms to time; the headline is mixed when within 1e-6 of fp64")
-    ap.add_argument("--local", default="f32x2", choices=["fp64", "fp32", "bf16", "f32x2"],
+    ap.add_argument("--local", default="f32x2", choices=["fp64", "fp32", "bf16", "bf16split", "f32x2"],
                     help="arithmetic of the local condensation / recovery in the mixed form")
     ap.add_argument("--guess", type=int, default=0, choices=[-1, 0, 1, 2, 3, 4, 5, 6],
                     help="trace-solve initial guess: extrapolation order 1-3, -1 zero, 0 library default")
@@ -272,7 +272,8 @@ def kernel_source(text, start):
 
 def _traffic_for(cls, N, k, precision="fp64", mf=False):
     """dram bytes per launch from a committed ncu summary, if it is for the current kernel source.
-    An entry may name its own source file and region (the matrix-free operator's kernel)."""
+    An entry may name its own source file and regions (the matrix-free operator's three kernel
+    bodies, hashed together)."""
     try:
         d = json.load(open(PROFILE_TRAFFIC))
     except Exception:
@@ -281,8 +282,10 @@ def _traffic_for(cls, N, k, precision="fp64", mf=False):
     if not e:
         return None
     src = os.path.join(ROOT, "paper_1711_02751_gb300", "csrc", e.get("source", d.get("source", "")))
+    regions = e.get("regions", [e.get("region", d.get("region", ""))])
     try:
-        sha = hashlib.sha256(kernel_source(open(src).read(), e.get("region", d.get("region", "")))).hexdigest()[:16]
+        text = open(src).read()
+        sha = hashlib.sha256(b"".join(kernel_source(text, r) for r in regions)).hexdigest()[:16]
     except Exception:
         return None
     if e.get("source_sha") != sha:

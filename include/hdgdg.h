@@ -158,10 +158,12 @@ typedef struct {
     int trace_operator;  /* how the mixed form's trace Krylov solve applies the preconditioned trace
                             matrix S M^{-1}: 0 = the assembled edge-block matrix (FP32 copy in the
                             inner cycles, FP32 pair in the refinement residual); 1 = matrix-free,
-                            element by element: M^{-1} (block-Jacobi, held in FP32) edge by edge,
+                            element by element: M^{-1} (block-Jacobi, held per edge as FP16 values
+                            of the block scaled by a power of two -- the same numbers on every
+                            path) edge by edge,
                             then per element the lift B, the Schur-complement local solve, C and D,
                             each edge row summed from its two elements' halves (FP32 in the inner
-                            cycles, FP32 pairs in the refinement residual).  About 2.7 KB per element (k = 3) instead of
+                            cycles, FP32 pairs in the refinement residual).  About 2.1 KB per element (k = 3) instead of
                             7.2 KB (FP32) or 14.3 KB (FP32 pair) of matrix.  1 needs precision =
                             HDGDG_MIXED with local_precision = HDGDG_LOCAL_F32X2 and local_dense = 0
                             (EINVAL otherwise); the FP64 form always uses the assembled matrix. */
