@@ -1304,8 +1304,10 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
                                      sim->stream));
             if (matrix_free(c)) {
                 CU(cudaMemsetAsync(sim->V32, 0, p.nt * sizeof(float), sim->stream));
-                CU(launch_mf_autotune(g, sim->mf, sim->V32, sim->w32, beta_of(sim), sim->stream, &sim->trace_tile,
-                                      &sim->trace_prefetch));
+                CU(cudaMemsetAsync(sim->xt, 0, p.nt * sizeof(double), sim->stream));
+                CU(cudaMemsetAsync(sim->gvec, 0, p.nt * sizeof(double), sim->stream));
+                CU(launch_mf_autotune(g, sim->mf, sim->V32, sim->w32, sim->xt, sim->gvec, sim->w, beta_of(sim),
+                                      sim->stream, &sim->trace_tile, &sim->trace_prefetch));
             }
             for (double* v : {sim->R1, sim->Z, sim->Qs, sim->NLs[0]})
                 CU(cudaMemsetAsync(v, 0, 3 * p.n * sizeof(double), sim->stream));

@@ -295,6 +295,7 @@ struct MfOps {
     void* hm = nullptr;              // scratch: the edges' minus-side halves of S y (8 bytes per value)
     void* hp = nullptr;              // scratch: their plus-side halves
     int tile = 0;                    // tile of the inner cycles' element pass (launch_mf_autotune)
+    int tile_res = 0;                // tile of the refinement residual's element pass
 };
 // y = S M^{-1} x in FP32 (inner Krylov cycles); done as for launch_spmv_pre
 cudaError_t launch_mf_inner(const Geom& g, const MfOps& op, const float* x, float* y, double beta, cudaStream_t s,
@@ -306,8 +307,8 @@ cudaError_t launch_mf_residual(const Geom& g, const MfOps& op, const double* x, 
 cudaError_t launch_mf_plain(const Geom& g, const MfOps& op, const double* x, double* y, double beta, cudaStream_t s);
 // Pick the inner element pass's tile by timing each candidate (degrees 2..4); *epb and *prefetch
 // report the choice (elements per block, S^{-1} row in registers).
-cudaError_t launch_mf_autotune(const Geom& g, MfOps& op, const float* x, float* y, double beta, cudaStream_t s,
-                               int* epb, int* prefetch);
+cudaError_t launch_mf_autotune(const Geom& g, MfOps& op, const float* x, float* y, const double* xd,
+                               const double* rhs, double* w, double beta, cudaStream_t s, int* epb, int* prefetch);
 // qhat = M^{-1} x~ with the FP32 blocks, FP64-class sums
 cudaError_t launch_mf_back(const Geom& g, const PrecondBlocks& M, const double* x, double* y, cudaStream_t s);
 // The FP16 blocks and scales from the FP64 block-Jacobi inverse (setup).

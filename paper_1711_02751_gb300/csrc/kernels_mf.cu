@@ -341,10 +341,21 @@ void mf_elem_launch(const Geom& g, const void* S, const void* aux, const void* E
         done);
 }
 
-// the element pass with tile t (degrees 2..4 in the inner cycles; tile 0 elsewhere)
+// the element pass with tile t (degrees 2..4: tiles 0..8 in the inner cycles, 0..5 in the
+// refinement residual; tile 0 elsewhere)
 template <int P, class A, int MODE>
 void mf_elem_tile(int t, const Geom& g, const void* S, const void* aux, const void* EG, const double* tau,
                   const void* yv, MfVec<MODE>* hm, MfVec<MODE>* hp, double beta, cudaStream_t s, const int* done) {
+    if constexpr (MODE == kMfResidual && P >= 3 && P <= 5) {
+        switch (t) {
+            case 1: return mf_elem_launch<P, A, MODE, 1>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
+            case 2: return mf_elem_launch<P, A, MODE, 2>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
+            case 3: return mf_elem_launch<P, A, MODE, 3>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
+            case 4: return mf_elem_launch<P, A, MODE, 4>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
+            case 5: return mf_elem_launch<P, A, MODE, 5>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
+            default: break;
+        }
+    }
     if constexpr (MODE == kMfInner && P >= 3 && P <= 5) {
         switch (t) {
             case 1: return mf_elem_launch<P, A, MODE, 1>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
@@ -377,7 +388,8 @@ cudaError_t mf_launch(const Geom& g, const MfOps& op, const void* S, const void*
     }
     TO* hm = static_cast<TO*>(op.hm);
     TO* hp = static_cast<TO*>(op.hp);
-    mf_elem_tile<P, A, MODE>(MODE == kMfInner ? op.tile : 0, g, S, aux, EG, op.tau, yv, hm, hp, beta, s, done);
+    mf_elem_tile<P, A, MODE>(MODE == kMfInner ? op.tile : MODE == kMfResidual ? op.tile_res : 0, g, S, aux, EG,
+                             op.tau, yv, hm, hp, beta, s, done);
     const size_t n = (size_t)g.n_edges * NF;
     mf_sum_kernel<TO, MODE == kMfResidual><<<sum_grid(n), 256, 0, s>>>(n, hm, hp, rhs, out, done);
     count_launches(MODE != kMfPlain ? 3 : 2);
@@ -495,10 +507,12 @@ cudaError_t launch_mf_plain(const Geom& g, const MfOps& op, const double* x, dou
 
 // Time each tile of the inner cycles' element pass on the handle's own operators (two warm-up and
 // five timed products each, CUDA events on the stream; x and y are scratch trace vectors) and keep
-// the fastest in op.tile.  The tile changes no thread's arithmetic, only how elements share blocks.
-cudaError_t launch_mf_autotune(const Geom& g, MfOps& op, const float* x, float* y, double beta, cudaStream_t s,
-                               int* epb, int* prefetch) {
+// the fastest in op.tile; then the refinement residual's tiles (xd, rhs, w: scratch FP64 trace
+// vectors) into op.tile_res.  The tile changes no thread's arithmetic, only how elements share blocks.
+cudaError_t launch_mf_autotune(const Geom& g, MfOps& op, const float* x, float* y, const double* xd,
+                               const double* rhs, double* w, double beta, cudaStream_t s, int* epb, int* prefetch) {
     op.tile = 0;
+    op.tile_res = 0;
     *epb = 0;
     *prefetch = 0;
     if (g.P < 3 || g.P > 5) return cudaSuccess;
@@ -525,9 +539,27 @@ cudaError_t launch_mf_autotune(const Geom& g, MfOps& op, const float* x, float* 
             best_t = t;
         }
     }
+    op.tile = best_t;
+    // the refinement residual's element pass (FP32 pairs): tiles 0..5
+    best = 1e30f;
+    int best_r = 0;
+    for (int t = 0; t < 6 && err == cudaSuccess; ++t) {
+        op.tile_res = t;
+        for (int k = 0; k < 2 && err == cudaSuccess; ++k) err = launch_mf_residual(g, op, xd, rhs, w, beta, s);
+        if (err == cudaSuccess) err = cudaEventRecord(a, s);
+        for (int k = 0; k < 5 && err == cudaSuccess; ++k) err = launch_mf_residual(g, op, xd, rhs, w, beta, s);
+        if (err == cudaSuccess) err = cudaEventRecord(b, s);
+        if (err == cudaSuccess) err = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, a, b);
+        if (err == cudaSuccess && ms < best) {
+            best = ms;
+            best_r = t;
+        }
+    }
+    op.tile_res = best_r;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    op.tile = best_t;
     const int P = g.P, th = mf_tile_threads(best_t);
     *epb = th / (P * P) > 32 ? 32 : (th / (P * P) > 0 ? th / (P * P) : 1);
     *prefetch = mf_tile_pref(best_t) ? 1 : 0;
