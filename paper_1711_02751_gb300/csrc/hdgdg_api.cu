@@ -109,7 +109,7 @@ Plan make_plan(const hdgdg_config* c) {
     b += 5 * p.nt * d;                                        // g, x~, qhat, w, DG face fluxes
     if (c->precision == HDGDG_MIXED) {                        // FP32 S~, FP32 basis and work vector
         if (!matrix_free(c)) b += n_edges * 6 * (size_t)p.NF * p.NF * sizeof(float);
-        b += ((size_t)p.m + 2) * p.nt * sizeof(float);
+        b += ((size_t)p.m + (matrix_free(c) ? 3 : 2)) * p.nt * sizeof(float);   // basis and w (two, matrix-free)
     } else {
         b += ((size_t)p.m + 1) * p.nt * d;                    // FP64 Krylov basis
     }
@@ -529,15 +529,24 @@ cudaError_t cycle_enqueue(hdgdg_sim* sim, const double* g, cudaStream_t st, bool
     else { V = sim->V; w = sim->w; St = sim->Stil; }
     GmresCtl* ctl = sim->ctl;
     const int* done = &ctl->done;
+    // The fused matrix-free product adds into its output, so the products alternate between two
+    // vectors (w32 holds both): the cycle's first launch zeroes the first, and iteration j's
+    // Gram-Schmidt tail zeroes the one product j + 1 adds into.
+    const bool fused = kMixed && matrix_free(&sim->cfg) && !sim->ens;
     cudaError_t e = launch_gmres_cycle_init(ctl, dv_nrm(sim), st);
-    if (e == cudaSuccess) e = launch_scale_by_rnorm(sim->w, dv_nrm(sim), V, n, st);
+    if (e == cudaSuccess) {
+        if constexpr (kMixed) e = launch_scale_by_rnorm(sim->w, dv_nrm(sim), V, n, st, fused ? w : nullptr);
+        else e = launch_scale_by_rnorm(sim->w, dv_nrm(sim), V, n, st);
+    }
+    T* const w_base = w;
     for (int j = 0; j < m && e == cudaSuccess; ++j) {
         const T* Vj = V + (size_t)j * n;
+        if (fused) w = w_base + (size_t)(j % 2) * n;
         {
             TimedGroup tg(sim, HDGDG_KT_SPMV, j);
             if constexpr (kMixed) {
                 if (sim->ens) e = launch_ens_mf_inner(*sim->ens, sim->mf, n, Vj, w, st, done);
-                else if (matrix_free(&sim->cfg)) e = launch_mf_inner(sim->g, sim->mf, Vj, w, beta_of(sim), st, done);
+                else if (fused) e = launch_mf_inner(sim->g, sim->mf, Vj, w, beta_of(sim), st, done, true);
                 else
                     e = launch_spmv_pre(sim->g, St, sim->Scol, Vj, w, st, done,
                                         sim->cfg.spmv_kernel == 1 ? spmv_error(sim) : nullptr);
@@ -546,10 +555,16 @@ cudaError_t cycle_enqueue(hdgdg_sim* sim, const double* g, cudaStream_t st, bool
         }
         TimedGroup tg(sim, HDGDG_KT_ORTHO, j);
         if (e == cudaSuccess) e = launch_multidot(V, n, j + 1, w, n, sim->red, dv_h1(sim), st, done);
-        if (e == cudaSuccess)   // second pass, norm, Hessenberg column j and stop test
-            e = launch_cgs2_tail(V, n, j + 1, dv_h1(sim), w, n, sim->red, dv_h2(sim), dv_nrm(sim) + 2,
-                                 dv_nrm(sim) + 1, V + (size_t)(j + 1) * n, ctl, j, m,
-                                 !(kMixed && sim->cfg.krylov_ortho == 1), st, done);
+        if (e == cudaSuccess) {   // second pass, norm, Hessenberg column j and stop test
+            if constexpr (kMixed)
+                e = launch_cgs2_tail(V, n, j + 1, dv_h1(sim), w, n, sim->red, dv_h2(sim), dv_nrm(sim) + 2,
+                                     dv_nrm(sim) + 1, V + (size_t)(j + 1) * n, ctl, j, m,
+                                     sim->cfg.krylov_ortho != 1, st, done,
+                                     fused ? w_base + (size_t)((j + 1) % 2) * n : nullptr);
+            else
+                e = launch_cgs2_tail(V, n, j + 1, dv_h1(sim), w, n, sim->red, dv_h2(sim), dv_nrm(sim) + 2,
+                                     dv_nrm(sim) + 1, V + (size_t)(j + 1) * n, ctl, j, m, true, st, done);
+        }
     }
     TimedGroup tg_end(sim, HDGDG_KT_RESIDUAL);
     if (e == cudaSuccess) e = launch_gmres_update(V, n, ctl, sim->xt, n, st);
@@ -1202,7 +1217,7 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
             if (c->residual_f32x2) TRY(dalloc(sim, &sim->Stil_lo, (size_t)g.n_edges * 6 * p.NF * p.NF));
         }
         TRY(dalloc(sim, &sim->V32, (size_t)(p.m + 1) * p.nt));
-        TRY(dalloc(sim, &sim->w32, p.nt));
+        TRY(dalloc(sim, &sim->w32, (matrix_free(c) ? 2 : 1) * p.nt));   // matrix-free: two alternating outputs
     } else {
         TRY(dalloc(sim, &sim->V, (size_t)(p.m + 1) * p.nt));
     }

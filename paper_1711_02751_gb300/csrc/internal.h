@@ -297,9 +297,11 @@ struct MfOps {
     int tile = 0;                    // tile of the inner cycles' element pass (launch_mf_autotune)
     int tile_res = 0;                // tile of the refinement residual's element pass
 };
-// y = S M^{-1} x in FP32 (inner Krylov cycles); done as for launch_spmv_pre
+// y = S M^{-1} x in FP32 (inner Krylov cycles), one fused launch that adds into y; done as for
+// launch_spmv_pre.  y_zeroed: the caller guarantees y = 0 (else a zeroing launch comes first).
+// With 3(k + 1) a multiple of 4, x must start on 16 bytes (cudaErrorMisalignedAddress otherwise).
 cudaError_t launch_mf_inner(const Geom& g, const MfOps& op, const float* x, float* y, double beta, cudaStream_t s,
-                            const int* done = nullptr);
+                            const int* done = nullptr, bool y_zeroed = false);
 // w = rhs - S M^{-1} x in FP64-class FP32-pair arithmetic (the refinement's true residual)
 cudaError_t launch_mf_residual(const Geom& g, const MfOps& op, const double* x, const double* rhs, double* w,
                                double beta, cudaStream_t s);
@@ -401,9 +403,11 @@ cudaError_t launch_multidot(const float* V, size_t ldv, int nv, const float* w, 
 cudaError_t launch_cgs2_tail(const double* V, size_t ldv, int nv, const double* h1, double* w, size_t n,
                              double* scratch, double* h2, double* nw1, double* hn, double* vout,
                              GmresCtl* ctl, int j, int m, bool twice, cudaStream_t s, const int* done = nullptr);
+// zero: a vector other than w set to 0 in the same pass (the next fused matrix-free product adds into it)
 cudaError_t launch_cgs2_tail(const float* V, size_t ldv, int nv, const double* h1, float* w, size_t n,
                              double* scratch, double* h2, double* nw1, double* hn, float* vout,
-                             GmresCtl* ctl, int j, int m, bool twice, cudaStream_t s, const int* done = nullptr);
+                             GmresCtl* ctl, int j, int m, bool twice, cudaStream_t s, const int* done = nullptr,
+                             float* zero = nullptr);
 
 
 // ---- uneven ensembles: one persistent launch per kernel class over many mesh groups ----------
@@ -485,8 +489,9 @@ cudaError_t launch_gmres_update(const float* V, size_t ldv, GmresCtl* c, double*
 // v = w / sqrt(*nrm2), w in FP64
 cudaError_t launch_scale_by_rnorm(const double* w, const double* nrm2, double* v, size_t n,
                                   cudaStream_t s);
+// (and zero = 0 when given: the output of the cycle's first fused matrix-free product)
 cudaError_t launch_scale_by_rnorm(const double* w, const double* nrm2, float* v, size_t n,
-                                  cudaStream_t s);
+                                  cudaStream_t s, float* zero = nullptr);
 cudaError_t launch_to_f32(const double* a, float* b, size_t n, cudaStream_t s);
 
 // User-state conversion and diagnostics.

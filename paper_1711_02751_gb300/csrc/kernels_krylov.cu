@@ -150,14 +150,16 @@ multidot_kernel(const T* __restrict__ V, size_t ldv, int j0, int nj, const T* __
     }
 }
 
-// v = w / sqrt(*nrm2) (w in FP64, v in T)
+// v = w / sqrt(*nrm2) (w in FP64, v in T); zero[idx] = 0 when given
 template <typename T>
 __global__ void scale_kernel(const double* __restrict__ w, const double* __restrict__ nrm2,
-                             T* __restrict__ v, size_t n) {
+                             T* __restrict__ v, size_t n, T* __restrict__ zero) {
     const double s = 1.0 / sqrt(*nrm2);
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
-         idx += (size_t)gridDim.x * blockDim.x)
+         idx += (size_t)gridDim.x * blockDim.x) {
         v[idx] = from_f64<T>(w[idx] * s);
+        if (zero) zero[idx] = T(0);
+    }
 }
 
 __global__ void to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, size_t n) {
@@ -232,24 +234,26 @@ axpy_dot_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict__ 
     }
 }
 
-// V_{j+1} = w1 / hn (classical Gram-Schmidt once)
+// V_{j+1} = w1 / hn (classical Gram-Schmidt once); zero = 0 when given (another vector than w)
 template <typename T>
 __global__ void __launch_bounds__(256)
 scale_out_kernel(const double* __restrict__ hn, const T* __restrict__ w, T* __restrict__ vout, size_t n,
-                 const int* __restrict__ done) {
+                 const int* __restrict__ done, T* __restrict__ zero) {
     if (done && *done) return;
     const T inv = T(1.0 / *hn);
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
-         idx += (size_t)gridDim.x * blockDim.x)
+         idx += (size_t)gridDim.x * blockDim.x) {
         vout[idx] = w[idx] * inv;
+        if (zero) zero[idx] = T(0);
+    }
 }
 
-// V_{j+1} = (w1 - sum_j h2_j V_j) / hn
+// V_{j+1} = (w1 - sum_j h2_j V_j) / hn; zero = 0 when given (another vector than w)
 template <int NJ, typename T, int VW = 1>
 __global__ void __launch_bounds__(256)
 axpy_scale_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict__ h2,
                   const double* __restrict__ hn, const T* __restrict__ w, T* __restrict__ vout, size_t n,
-                  const int* __restrict__ done) {
+                  const int* __restrict__ done, T* __restrict__ zero) {
     if (done && *done) return;
     T hc[NJ];
 #pragma unroll
@@ -258,6 +262,12 @@ axpy_scale_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict_
     for (size_t iv = blockIdx.x * (size_t)blockDim.x + threadIdx.x; iv < n / VW;
          iv += (size_t)gridDim.x * blockDim.x) {
         Lanes<T, VW> x = load_lanes<T, VW>(w, iv);
+        if (zero) {
+            Lanes<T, VW> z;
+#pragma unroll
+            for (int k = 0; k < VW; ++k) z.v[k] = T(0);
+            store_lanes<T, VW>(zero, iv, z);
+        }
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
             const Lanes<T, VW> v = load_lanes<T, VW>(V + (size_t)j * ldv, iv);
@@ -489,13 +499,13 @@ bool lanes4(size_t n, size_t ldv, std::initializer_list<const void*> ptrs) {
 template <int NJ, typename T>
 cudaError_t cgs2_tail_launch(const T* V, size_t ldv, const double* h1, T* w, size_t n, double* scratch,
                              double* h2, double* nw1, double* hn, T* vout, GmresCtl* ctl, int j, int m,
-                             bool twice, cudaStream_t s, const int* done) {
+                             bool twice, cudaStream_t s, const int* done, T* zero) {
     // the NJ x 4 basis lanes stay in registers (80 at NJ = 10: three blocks per SM, hence the grid)
     if constexpr (sizeof(T) == 4 && NJ <= 10) {
-        if (twice && lanes4<T>(n, ldv, {V, w, vout})) {
+        if (twice && lanes4<T>(n, ldv, {V, w, vout, zero ? zero : vout})) {
             axpy_dot_kernel<NJ, T, true, 4><<<152 * 3, kDotThreads, 0, s>>>(V, ldv, h1, w, n, scratch, h2, nw1, hn,
                                                                              ctl, j, m, done);
-            axpy_scale_kernel<NJ, T, 4><<<stream_grid(n / 4), 256, 0, s>>>(V, ldv, h2, hn, w, vout, n, done);
+            axpy_scale_kernel<NJ, T, 4><<<stream_grid(n / 4), 256, 0, s>>>(V, ldv, h2, hn, w, vout, n, done, zero);
             count_launches(2);
             return cudaGetLastError();
         }
@@ -504,12 +514,12 @@ cudaError_t cgs2_tail_launch(const T* V, size_t ldv, const double* h1, T* w, siz
         axpy_dot_kernel<NJ, T, true><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, h1, w, n, scratch, h2, nw1, hn,
                                                                         ctl, j, m, done);
         count_launches(1);
-        axpy_scale_kernel<NJ, T><<<stream_grid(n), 256, 0, s>>>(V, ldv, h2, hn, w, vout, n, done);
+        axpy_scale_kernel<NJ, T><<<stream_grid(n), 256, 0, s>>>(V, ldv, h2, hn, w, vout, n, done, zero);
     } else {
         axpy_dot_kernel<NJ, T, false><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, h1, w, n, scratch, h2, nw1, hn,
                                                                          ctl, j, m, done);
         count_launches(1);
-        scale_out_kernel<T><<<stream_grid(n), 256, 0, s>>>(hn, w, vout, n, done);
+        scale_out_kernel<T><<<stream_grid(n), 256, 0, s>>>(hn, w, vout, n, done, zero);
     }
     count_launches(1);
     return cudaGetLastError();
@@ -518,9 +528,10 @@ cudaError_t cgs2_tail_launch(const T* V, size_t ldv, const double* h1, T* w, siz
 template <typename T>
 cudaError_t cgs2_tail_dispatch(const T* V, size_t ldv, int nv, const double* h1, T* w, size_t n,
                                double* scratch, double* h2, double* nw1, double* hn, T* vout,
-                               GmresCtl* ctl, int j, int m, bool twice, cudaStream_t s, const int* done) {
+                               GmresCtl* ctl, int j, int m, bool twice, cudaStream_t s, const int* done,
+                               T* zero) {
     switch (nv) {
-#define CASE(J) case J: return cgs2_tail_launch<J, T>(V, ldv, h1, w, n, scratch, h2, nw1, hn, vout, ctl, j, m, twice, s, done);
+#define CASE(J) case J: return cgs2_tail_launch<J, T>(V, ldv, h1, w, n, scratch, h2, nw1, hn, vout, ctl, j, m, twice, s, done, zero);
         CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
         CASE(12) CASE(13) CASE(14) CASE(15) CASE(16) CASE(17) CASE(18) CASE(19) CASE(20) CASE(21)
         CASE(22) CASE(23) CASE(24) CASE(25) CASE(26) CASE(27) CASE(28) CASE(29) CASE(30) CASE(31)
@@ -575,13 +586,16 @@ cudaError_t launch_guess_norms(size_t n, const double* g, const GuessTerms& t, d
 cudaError_t launch_cgs2_tail(const double* V, size_t ldv, int nv, const double* h1, double* w, size_t n,
                              double* scratch, double* h2, double* nw1, double* hn, double* vout,
                              GmresCtl* ctl, int j, int m, bool twice, cudaStream_t s, const int* done) {
-    return cgs2_tail_dispatch<double>(V, ldv, nv, h1, w, n, scratch, h2, nw1, hn, vout, ctl, j, m, twice, s, done);
+    return cgs2_tail_dispatch<double>(V, ldv, nv, h1, w, n, scratch, h2, nw1, hn, vout, ctl, j, m, twice, s, done,
+                                      nullptr);
 }
 
 cudaError_t launch_cgs2_tail(const float* V, size_t ldv, int nv, const double* h1, float* w, size_t n,
                              double* scratch, double* h2, double* nw1, double* hn, float* vout,
-                             GmresCtl* ctl, int j, int m, bool twice, cudaStream_t s, const int* done) {
-    return cgs2_tail_dispatch<float>(V, ldv, nv, h1, w, n, scratch, h2, nw1, hn, vout, ctl, j, m, twice, s, done);
+                             GmresCtl* ctl, int j, int m, bool twice, cudaStream_t s, const int* done,
+                             float* zero) {
+    return cgs2_tail_dispatch<float>(V, ldv, nv, h1, w, n, scratch, h2, nw1, hn, vout, ctl, j, m, twice, s, done,
+                                     zero);
 }
 
 cudaError_t launch_block_diag(const Geom& g, const double* Bd, const double* x, double* y,
@@ -619,14 +633,14 @@ cudaError_t launch_multidot(const float* V, size_t ldv, int nv, const float* w, 
 
 cudaError_t launch_scale_by_rnorm(const double* w, const double* nrm2, double* v, size_t n,
                                   cudaStream_t s) {
-    scale_kernel<double><<<stream_grid(n), 256, 0, s>>>(w, nrm2, v, n);
+    scale_kernel<double><<<stream_grid(n), 256, 0, s>>>(w, nrm2, v, n, nullptr);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scale_by_rnorm(const double* w, const double* nrm2, float* v, size_t n,
-                                  cudaStream_t s) {
-    scale_kernel<float><<<stream_grid(n), 256, 0, s>>>(w, nrm2, v, n);
+                                  cudaStream_t s, float* zero) {
+    scale_kernel<float><<<stream_grid(n), 256, 0, s>>>(w, nrm2, v, n, zero);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -13,8 +13,8 @@
 // phi_hat and tangential terms and cancel the normal one), and a prescribed (Dirichlet) trace
 // row is the identity -- the rows the assembled matrix holds.
 //
-// Three launches per product, each short, so that no block waits on a chain of dependent
-// memory round trips:
+// Three launches per product in the refinement residual and the plain product, each short, so
+// that no block waits on a chain of dependent memory round trips:
 //   mf_pre_kernel   y = M^{-1} x, one thread per edge row (block-Jacobi inverse in scaled FP16);
 //   mf_elem_kernel  one thread per (element, node): the node's traces y gathered straight into
 //                   registers, the operator data loaded before them, the lift, the local solve,
@@ -22,6 +22,13 @@
 //                   3) into hm, its plus side into hp (a boundary face's full row into hm, 0 into hp);
 //   mf_sum_kernel   y = hm + hp (residual mode: w = g - (hm + hp)), minus half first, so the
 //                   result is the same whatever order the elements ran in.
+// The inner cycles' product is ONE launch: the element pass first forms y = M^{-1} x on each face
+// of its block's elements in shared memory (the same sums as mf_pre_kernel, term for term), and
+// adds its half of each face's row into the output with a global reduction.  The output is zero
+// beforehand and every row receives at most two addends, so the sum is the same in whichever order
+// the two sides arrive (IEEE addition is commutative) and equals hm + hp of the three-pass form
+// bit for bit -- apart from the sign of an exact zero, and halves below the FP32 normal range,
+// which the reduction flushes to zero.
 // Modes (the Krylov solve applies the block-Jacobi-preconditioned operator S~ = S M^{-1}):
 //   kMfInner     y = S M^{-1} x        FP32 arithmetic and vectors (the mixed form's inner cycles)
 //   kMfResidual  w = g - S M^{-1} x    FP64-class FP32-pair arithmetic, FP64 vectors (refinement)
@@ -30,6 +37,7 @@
 // two (PrecondBlocks); the inner cycles, the residual and the final back-transformation
 // qhat = M^{-1} x~ use exactly these values, so the preconditioner is the same matrix on every path.
 #include <cuda_fp16.h>
+#include <cstdint>
 #include <type_traits>
 
 #include "compensated.h"
@@ -117,18 +125,150 @@ mf_pre_kernel(int n_edges, PrecondBlocks Minv, const TX* __restrict__ x, typenam
     mf_pre_body<NF, A, TX>(blockIdx.x, n_edges, Minv, x, y);
 }
 
+// y = M^{-1} x on each face (slot le * 4 + f) of the block's elements, into ys -- the sums of
+// mf_pre_body in the same order.  NF % 4 == 0: four rows per thread with 8-byte FP16 loads (x and
+// M^{-1} 16- and 8-byte aligned, checked by the launcher); else one row per thread.
+template <int P, int EPB>
+__device__ __forceinline__ void mf_face_pre(int bid, const Geom& g, const PrecondBlocks& Minv,
+                                            const float* __restrict__ x, float (*ys)[4][3 * P]) {
+    constexpr int NF = 3 * P, NT = EPB * P * P;
+    if constexpr (NF % 4 == 0) {
+        constexpr int Q = NF / 4;
+        for (int u = threadIdx.x; u < EPB * 4 * Q; u += NT) {
+            const int slot = u / Q, q = u % Q, le = slot / 4, f = slot % 4;
+            const int e = bid * EPB + le;
+            if (e >= g.n_el) continue;
+            const int r = edge_of_face(e, f, g);
+            const float4* xr = reinterpret_cast<const float4*>(x + (size_t)r * NF);
+            const __half* M = Minv.h + (size_t)r * NF * NF + 4 * q;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+            for (int jq = 0; jq < Q; ++jq) {
+                const float4 xv = xr[jq];
+                const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const uint2 mv = *reinterpret_cast<const uint2*>(M + (size_t)(4 * jq + t) * NF);
+                    const float2 m01 = __half22float2(*reinterpret_cast<const __half2*>(&mv.x));
+                    const float2 m23 = __half22float2(*reinterpret_cast<const __half2*>(&mv.y));
+                    a0 = __fmaf_rn(m01.x, xs[t], a0);
+                    a1 = __fmaf_rn(m01.y, xs[t], a1);
+                    a2 = __fmaf_rn(m23.x, xs[t], a2);
+                    a3 = __fmaf_rn(m23.y, xs[t], a3);
+                }
+            }
+            const float sc = __ldg(Minv.scale + r);
+            ys[le][f][4 * q] = a0 * sc;
+            ys[le][f][4 * q + 1] = a1 * sc;
+            ys[le][f][4 * q + 2] = a2 * sc;
+            ys[le][f][4 * q + 3] = a3 * sc;
+        }
+    } else {
+        for (int u = threadIdx.x; u < EPB * 4 * NF; u += NT) {
+            const int slot = u / NF, ii = u % NF, le = slot / 4, f = slot % 4;
+            const int e = bid * EPB + le;
+            if (e >= g.n_el) continue;
+            const int r = edge_of_face(e, f, g);
+            const float* xr = x + (size_t)r * NF;
+            const __half* M = Minv.h + (size_t)r * NF * NF + ii;
+            float a = 0.f;
+#pragma unroll
+            for (int jj = 0; jj < NF; ++jj) a = __fmaf_rn(__half2float(M[jj * NF]), xr[jj], a);
+            ys[le][f][ii] = a * __ldg(Minv.scale + r);
+        }
+    }
+}
+
+// The element's half of each of its faces' rows at its node (see above): stored into hm / hp, or,
+// FUSE, added into hm (the zeroed output).
+template <int P, int EPB, class A, int MODE, bool FUSE>
+__device__ __forceinline__ void mf_elem_rows(const Geom& g, int e, int le, const SchurNode<A>& nd, const bool* on,
+                                             const int* fc, const int* bb, const int* ed,
+                                             const typename A::T (*yv_)[3], const typename A::T* tau,
+                                             typename A::T* W, double beta, MfVec<MODE>* __restrict__ hm,
+                                             MfVec<MODE>* __restrict__ hp) {
+    using T = typename A::T;
+    using TO = MfVec<MODE>;
+    constexpr int NF = 3 * P;
+    const T bt = A::from(beta * dt_factor(g, e));
+    W[0] = A::mul(bt, W[0]);
+    W[1] = A::mul(bt, W[1]);
+    W[2] = A::mul(bt, W[2]);
+    const T one = A::from(1.0), mone = A::from(-1.0), mtwo = A::from(-2.0);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (!on[k]) continue;
+        const int f = fc[k], b = bb[k];
+        const bool xedge = f < 2, minus = (f == 1 || f == 3);   // minus side: outward normal +axis
+        const int cn = xedge ? 1 : 2, ct = xedge ? 2 : 1;
+        const bool boundary = g.walls && neighbour(e, f, g) < 0;
+        const size_t o = (size_t)ed[k] * NF + b;
+        if (boundary && g.dirichlet) {   // prescribed trace: the identity row
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if constexpr (FUSE) {
+                    atomicAdd(hm + o + c * P, yv_[k][c]);
+                } else {
+                    hm[o + c * P] = arith_store<A, TO>(yv_[k][c]);
+                    hp[o + c * P] = TO(0);
+                }
+            }
+            continue;
+        }
+        const T Wn = W[cn], Wt = W[ct];
+        const T sg = minus ? one : mone;
+        const T m2tau = A::mul(mtwo, tau[k]);
+        typename A::Acc r0, rn, rt;
+        r0.add(sg, Wn);                       // U.n
+        r0.add(tau[k], W[0]);                 // + tau phi
+        rn.add(A::mul(sg, nd.pb), W[0]);      // phi_B phi n
+        rn.add(tau[k], Wn);                   // + tau U_n
+        rt.add(tau[k], Wt);                   // tau U_t
+        if (boundary) {                       // wall: element + mirror; then D = -2 tau on every row
+            r0.add(sg, Wn);
+            r0.add(tau[k], W[0]);
+            rt.add(tau[k], Wt);
+            rn = typename A::Acc();
+        }
+        if (minus || boundary) {              // D y enters with the edge's minus side (or its only side)
+            r0.add(m2tau, yv_[k][0]);
+            rn.add(m2tau, yv_[k][cn]);
+            rt.add(m2tau, yv_[k][ct]);
+        }
+        if constexpr (FUSE) {   // both sides into the zeroed output (a wall's one side is its whole row)
+            atomicAdd(hm + o, r0.get());
+            atomicAdd(hm + o + cn * P, rn.get());
+            atomicAdd(hm + o + ct * P, rt.get());
+            continue;
+        }
+        TO* dst = (minus || boundary) ? hm : hp;
+        dst[o] = arith_store<A, TO>(r0.get());
+        dst[o + cn * P] = arith_store<A, TO>(rn.get());
+        dst[o + ct * P] = arith_store<A, TO>(rt.get());
+        if (boundary) {
+            hp[o] = TO(0);
+            hp[o + cn * P] = TO(0);
+            hp[o + ct * P] = TO(0);
+        }
+    }
+}
+
 // The element pass (see above).  PLAIN: y is the input vector itself (TX), else M^{-1} x (A::T).
-template <int P, int EPB, class A, int MODE, bool PREF>
+// FUSE (inner mode): yv is x itself, y = M^{-1} x is formed per face in shared memory, and both
+// halves of each row are added into hm (the zeroed output; hp unused).
+template <int P, int EPB, class A, int MODE, bool PREF, bool FUSE = false>
 __device__ __forceinline__ void mf_elem_body(int bid, const Geom& g, const typename A::T* __restrict__ S,
                                              const typename A::T* __restrict__ aux,
                                              const typename A::T* __restrict__ EG, const double* __restrict__ tau_edge,
                                              const void* __restrict__ yv, MfVec<MODE>* __restrict__ hm,
-                                             MfVec<MODE>* __restrict__ hp, double beta) {
+                                             MfVec<MODE>* __restrict__ hp, double beta, PrecondBlocks Minv = {}) {
     using T = typename A::T;
     using TO = MfVec<MODE>;
     constexpr int Np = P * P, NF = 3 * P;
     constexpr bool kPref = PREF && Np <= 25;   // S^{-1} row loaded into registers ahead of the traces
+    static_assert(!FUSE || (MODE == kMfInner && sizeof(T) == sizeof(float)), "the fused pass is the FP32 inner product");
     __shared__ SchurSmem<P, EPB, A> sm;
+    __shared__ float ys[FUSE ? EPB : 1][4][FUSE ? NF : 1];
     const int le = threadIdx.x / Np, n = threadIdx.x % Np, i = n % P, j = n / P;
     const int e = bid * EPB + le;
     const bool live = le < EPB && e < g.n_el;
@@ -142,6 +282,10 @@ __device__ __forceinline__ void mf_elem_body(int bid, const Geom& g, const typen
 #pragma unroll
             for (int m = 0; m < Np; ++m) srow[m] = Sn[(size_t)m * Np];
         }
+    }
+    if constexpr (FUSE) {
+        mf_face_pre<P, EPB>(bid, g, Minv, static_cast<const float*>(yv), ys);
+        __syncthreads();
     }
     // the node's faces -- slot 0 its x-face (left or right), slot 1 its y-face (bottom or top) --
     // with the edge, the position along it, tau and the three trace components
@@ -168,7 +312,8 @@ __device__ __forceinline__ void mf_elem_body(int bid, const Geom& g, const typen
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const size_t o = (size_t)r * NF + c * P + bb[k];
-            if constexpr (MODE == kMfPlain) yv_[k][c] = A::from(static_cast<const double*>(yv)[o]);
+            if constexpr (FUSE) yv_[k][c] = ys[le][fc[k]][c * P + bb[k]];
+            else if constexpr (MODE == kMfPlain) yv_[k][c] = A::from(static_cast<const double*>(yv)[o]);
             else yv_[k][c] = static_cast<const T*>(yv)[o];
         }
     }
@@ -194,68 +339,24 @@ __device__ __forceinline__ void mf_elem_body(int bid, const Geom& g, const typen
     else
         schur_solve_with<P, EPB, A>(sm, g, e, le, n, live, nd, [&](int m) { return Sn[(size_t)m * Np]; }, EG, u[0],
                                     u[1], u[2], W[0], W[1], W[2]);
-    if (!live) return;
-    const T bt = A::from(beta * dt_factor(g, e));
-    W[0] = A::mul(bt, W[0]);
-    W[1] = A::mul(bt, W[1]);
-    W[2] = A::mul(bt, W[2]);
-    const T one = A::from(1.0), mone = A::from(-1.0), mtwo = A::from(-2.0);
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        if (!on[k]) continue;
-        const int f = fc[k], b = bb[k];
-        const bool xedge = f < 2, minus = (f == 1 || f == 3);   // minus side: outward normal +axis
-        const int cn = xedge ? 1 : 2, ct = xedge ? 2 : 1;
-        const bool boundary = g.walls && neighbour(e, f, g) < 0;
-        const size_t o = (size_t)ed[k] * NF + b;
-        if (boundary && g.dirichlet) {   // prescribed trace: the identity row
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                hm[o + c * P] = arith_store<A, TO>(yv_[k][c]);
-                hp[o + c * P] = TO(0);
-            }
-            continue;
-        }
-        const T Wn = W[cn], Wt = W[ct];
-        const T sg = minus ? one : mone;
-        const T m2tau = A::mul(mtwo, tau[k]);
-        typename A::Acc r0, rn, rt;
-        r0.add(sg, Wn);                       // U.n
-        r0.add(tau[k], W[0]);                 // + tau phi
-        rn.add(A::mul(sg, nd.pb), W[0]);      // phi_B phi n
-        rn.add(tau[k], Wn);                   // + tau U_n
-        rt.add(tau[k], Wt);                   // tau U_t
-        if (boundary) {                       // wall: element + mirror; then D = -2 tau on every row
-            r0.add(sg, Wn);
-            r0.add(tau[k], W[0]);
-            rt.add(tau[k], Wt);
-            rn = typename A::Acc();
-        }
-        if (minus || boundary) {              // D y enters with the edge's minus side (or its only side)
-            r0.add(m2tau, yv_[k][0]);
-            rn.add(m2tau, yv_[k][cn]);
-            rt.add(m2tau, yv_[k][ct]);
-        }
-        TO* dst = (minus || boundary) ? hm : hp;
-        dst[o] = arith_store<A, TO>(r0.get());
-        dst[o + cn * P] = arith_store<A, TO>(rn.get());
-        dst[o + ct * P] = arith_store<A, TO>(rt.get());
-        if (boundary) {
-            hp[o] = TO(0);
-            hp[o + cn * P] = TO(0);
-            hp[o + ct * P] = TO(0);
-        }
-    }
+    if (live) mf_elem_rows<P, EPB, A, MODE, FUSE>(g, e, le, nd, on, fc, bb, ed, yv_, tau, W, beta, hm, hp);
 }
 
-template <int P, int EPB, class A, int MODE, bool PREF, int MINB = 1>
+template <int P, int EPB, class A, int MODE, bool PREF, int MINB = 1, bool FUSE = false>
 __global__ void __launch_bounds__(EPB * P * P, MINB)
     mf_elem_kernel(Geom g, const typename A::T* __restrict__ S, const typename A::T* __restrict__ aux,
                    const typename A::T* __restrict__ EG, const double* __restrict__ tau_edge,
                    const void* __restrict__ yv, MfVec<MODE>* __restrict__ hm, MfVec<MODE>* __restrict__ hp,
-                   double beta, const int* __restrict__ done) {
+                   double beta, PrecondBlocks Minv, const int* __restrict__ done) {
     if (done && *done) return;
-    mf_elem_body<P, EPB, A, MODE, PREF>(blockIdx.x, g, S, aux, EG, tau_edge, yv, hm, hp, beta);
+    mf_elem_body<P, EPB, A, MODE, PREF, FUSE>(blockIdx.x, g, S, aux, EG, tau_edge, yv, hm, hp, beta, Minv);
+}
+
+// y = 0 (the fused product's output, when the caller has not zeroed it)
+__global__ void __launch_bounds__(256) zero_f32_kernel(float* __restrict__ y, size_t n, const int* __restrict__ done) {
+    if (done && *done) return;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        y[t] = 0.f;
 }
 
 // y = hm + hp, or w = g - (hm + hp)
@@ -333,52 +434,72 @@ int sum_grid(size_t n) {
 
 template <int P, class A, int MODE, int TILE>
 void mf_elem_launch(const Geom& g, const void* S, const void* aux, const void* EG, const double* tau, const void* yv,
-                    MfVec<MODE>* hm, MfVec<MODE>* hp, double beta, cudaStream_t s, const int* done) {
+                    MfVec<MODE>* hm, MfVec<MODE>* hp, double beta, cudaStream_t s, const int* done,
+                    const PrecondBlocks& Minv) {
     using T = typename A::T;
     constexpr int EPB = mf_epb_for<P>(mf_tile_threads(TILE));
-    mf_elem_kernel<P, EPB, A, MODE, mf_tile_pref(TILE), mf_tile_minb(TILE)><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(
-        g, static_cast<const T*>(S), static_cast<const T*>(aux), static_cast<const T*>(EG), tau, yv, hm, hp, beta,
-        done);
+    constexpr bool kFuse = MODE == kMfInner;
+    mf_elem_kernel<P, EPB, A, MODE, mf_tile_pref(TILE), mf_tile_minb(TILE), kFuse>
+        <<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(g, static_cast<const T*>(S), static_cast<const T*>(aux),
+                                                          static_cast<const T*>(EG), tau, yv, hm, hp, beta, Minv,
+                                                          done);
 }
 
 // the element pass with tile t (degrees 2..4: tiles 0..8 in the inner cycles, 0..5 in the
 // refinement residual; tile 0 elsewhere)
 template <int P, class A, int MODE>
 void mf_elem_tile(int t, const Geom& g, const void* S, const void* aux, const void* EG, const double* tau,
-                  const void* yv, MfVec<MODE>* hm, MfVec<MODE>* hp, double beta, cudaStream_t s, const int* done) {
+                  const void* yv, MfVec<MODE>* hm, MfVec<MODE>* hp, double beta, cudaStream_t s, const int* done,
+                  const PrecondBlocks& Minv) {
     if constexpr (MODE == kMfResidual && P >= 3 && P <= 5) {
         switch (t) {
-            case 1: return mf_elem_launch<P, A, MODE, 1>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
-            case 2: return mf_elem_launch<P, A, MODE, 2>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
-            case 3: return mf_elem_launch<P, A, MODE, 3>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
-            case 4: return mf_elem_launch<P, A, MODE, 4>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
-            case 5: return mf_elem_launch<P, A, MODE, 5>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
+            case 1: return mf_elem_launch<P, A, MODE, 1>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done, Minv);
+            case 2: return mf_elem_launch<P, A, MODE, 2>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done, Minv);
+            case 3: return mf_elem_launch<P, A, MODE, 3>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done, Minv);
+            case 4: return mf_elem_launch<P, A, MODE, 4>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done, Minv);
+            case 5: return mf_elem_launch<P, A, MODE, 5>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done, Minv);
             default: break;
         }
     }
     if constexpr (MODE == kMfInner && P >= 3 && P <= 5) {
         switch (t) {
-            case 1: return mf_elem_launch<P, A, MODE, 1>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
-            case 2: return mf_elem_launch<P, A, MODE, 2>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
-            case 3: return mf_elem_launch<P, A, MODE, 3>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
-            case 4: return mf_elem_launch<P, A, MODE, 4>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
-            case 5: return mf_elem_launch<P, A, MODE, 5>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
-            case 6: return mf_elem_launch<P, A, MODE, 6>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
-            case 7: return mf_elem_launch<P, A, MODE, 7>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
-            case 8: return mf_elem_launch<P, A, MODE, 8>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
+            case 1: return mf_elem_launch<P, A, MODE, 1>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done, Minv);
+            case 2: return mf_elem_launch<P, A, MODE, 2>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done, Minv);
+            case 3: return mf_elem_launch<P, A, MODE, 3>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done, Minv);
+            case 4: return mf_elem_launch<P, A, MODE, 4>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done, Minv);
+            case 5: return mf_elem_launch<P, A, MODE, 5>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done, Minv);
+            case 6: return mf_elem_launch<P, A, MODE, 6>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done, Minv);
+            case 7: return mf_elem_launch<P, A, MODE, 7>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done, Minv);
+            case 8: return mf_elem_launch<P, A, MODE, 8>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done, Minv);
             default: break;
         }
     }
-    mf_elem_launch<P, A, MODE, 0>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done);
+    mf_elem_launch<P, A, MODE, 0>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done, Minv);
 }
 
-// One product: [y = M^{-1} x,] the element pass, the edge sum.
+// One product: [y = M^{-1} x,] the element pass, the edge sum; the inner mode's fused pass alone
+// (after zeroing the output unless out_zeroed).
 template <int P, class A, int MODE>
 cudaError_t mf_launch(const Geom& g, const MfOps& op, const void* S, const void* aux, const void* EG, const void* x,
-                      const double* rhs, MfVec<MODE>* out, double beta, cudaStream_t s, const int* done) {
+                      const double* rhs, MfVec<MODE>* out, double beta, cudaStream_t s, const int* done,
+                      bool out_zeroed = false) {
     using T = typename A::T;
     using TO = MfVec<MODE>;
     constexpr int NF = 3 * P;
+    if constexpr (MODE == kMfInner) {
+        // the fused pass's vector loads (NF % 4 == 0): x on 16 bytes, the FP16 blocks on 8
+        if (NF % 4 == 0 &&
+            (reinterpret_cast<uintptr_t>(x) % 16 != 0 || reinterpret_cast<uintptr_t>(op.Minv.h) % 8 != 0))
+            return cudaErrorMisalignedAddress;
+        const size_t n = (size_t)g.n_edges * NF;
+        if (!out_zeroed) {
+            zero_f32_kernel<<<sum_grid(n), 256, 0, s>>>(reinterpret_cast<float*>(out), n, done);
+            count_launches(1);
+        }
+        mf_elem_tile<P, A, MODE>(op.tile, g, S, aux, EG, op.tau, x, out, nullptr, beta, s, done, op.Minv);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     const void* yv = x;
     if constexpr (MODE != kMfPlain) {
         constexpr int EPE = 256 / NF;
@@ -388,8 +509,8 @@ cudaError_t mf_launch(const Geom& g, const MfOps& op, const void* S, const void*
     }
     TO* hm = static_cast<TO*>(op.hm);
     TO* hp = static_cast<TO*>(op.hp);
-    mf_elem_tile<P, A, MODE>(MODE == kMfInner ? op.tile : MODE == kMfResidual ? op.tile_res : 0, g, S, aux, EG,
-                             op.tau, yv, hm, hp, beta, s, done);
+    mf_elem_tile<P, A, MODE>(MODE == kMfResidual ? op.tile_res : 0, g, S, aux, EG, op.tau, yv, hm, hp, beta, s, done,
+                             op.Minv);
     const size_t n = (size_t)g.n_edges * NF;
     mf_sum_kernel<TO, MODE == kMfResidual><<<sum_grid(n), 256, 0, s>>>(n, hm, hp, rhs, out, done);
     count_launches(MODE != kMfPlain ? 3 : 2);
@@ -474,9 +595,11 @@ cudaError_t ens_mf_launch(const EnsHost& E, const MfOps& op, size_t nt, const Mf
 }  // namespace
 
 cudaError_t launch_mf_inner(const Geom& g, const MfOps& op, const float* x, float* y, double beta, cudaStream_t s,
-                            const int* done) {
-#define CASE(P) \
-    case P: return mf_launch<P, ArithF32, kMfInner>(g, op, op.S32, op.aux32, op.EG32, x, nullptr, y, beta, s, done);
+                            const int* done, bool y_zeroed) {
+#define CASE(P)                                                                                                 \
+    case P:                                                                                                     \
+        return mf_launch<P, ArithF32, kMfInner>(g, op, op.S32, op.aux32, op.EG32, x, nullptr, y, beta, s, done, \
+                                                y_zeroed);
     switch (g.P) {
         CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9)
         default: return cudaErrorInvalidValue;
