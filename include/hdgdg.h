@@ -322,6 +322,14 @@ hdgdg_status hdgdg_condense_rhs(hdgdg_sim* sim, const double* R1, double* out);
  * of hdgdg_condense_rhs.  x, y: [edge][c][b]. */
 hdgdg_status hdgdg_trace_apply(hdgdg_sim* sim, const double* x, double* y);
 
+/* Select the tile of the matrix-free operator's element pass in the inner Krylov cycles
+ * (trace_operator = 1), overriding the one picked at create: 0 the default; 1..8 (degrees
+ * 2..4) blocks of 128, 256 or 512 threads, with or without the local operator's row loaded into
+ * registers ahead of the traces, under different register caps.  Every tile gives the same
+ * result bit for bit.  Cached step graphs are dropped.  HDGDG_EINVAL when the handle has no such
+ * pass or the tile is not available. */
+hdgdg_status hdgdg_set_trace_tile(hdgdg_sim* sim, int tile);
+
 /* One implicit stage solve (Algorithm 1, the "else" branch): condense, GMRES on the trace
  * system, recover Q = A^{-1}(R1 - B qhat).  R1, Q: [3][n_el][(k+1)^2]; qhat: [edge][c][b]
  * (may be NULL).  *iterations (may be NULL) receives the GMRES iteration count. */

@@ -1709,6 +1709,21 @@ hdgdg_status hdgdg_trace_apply(hdgdg_sim* sim, const double* x, double* y) {
     return download(sim, y, sim->gvec, sim->plan.nt);
 }
 
+hdgdg_status hdgdg_set_trace_tile(hdgdg_sim* sim, int tile) {
+    if (!sim) return fail(sim, HDGDG_EINVAL, "NULL handle");
+    if (!matrix_free(&sim->cfg) || sim->ens)
+        return fail(sim, HDGDG_EINVAL, "set_trace_tile: the handle has no matrix-free inner product");
+    if (!mf_tile_ready(sim->g.P, tile))
+        return fail(sim, HDGDG_EINVAL, "set_trace_tile: tile %d is not available at degree %d", tile, sim->g.P - 1);
+    CU(cudaStreamSynchronize(sim->stream));
+    for (auto& cg : sim->cycle_graph) drop_graph(sim, cg);   // the captured launches name the old tile
+    drop_step_graphs(sim);
+    sim->mf.tile = tile;
+    if (tile == 0) sim->trace_tile = sim->trace_prefetch = 0;
+    else mf_tile_info(sim->g.P, tile, &sim->trace_tile, &sim->trace_prefetch);
+    return HDGDG_OK;
+}
+
 hdgdg_status hdgdg_stage_solve(hdgdg_sim* sim, const double* R1, double* Q, double* qhat, int* iterations) {
     if (sim && explicit_scheme(&sim->cfg)) return fail(sim, HDGDG_EINVAL, "explicit scheme: no implicit stage");
     if (!sim || !R1 || !Q) return fail(sim, HDGDG_EINVAL, "NULL argument to stage_solve");

@@ -307,6 +307,10 @@ cudaError_t launch_mf_residual(const Geom& g, const MfOps& op, const double* x, 
                                double beta, cudaStream_t s);
 // y = S x (no preconditioner), FP64-class
 cudaError_t launch_mf_plain(const Geom& g, const MfOps& op, const double* x, double* y, double beta, cudaStream_t s);
+// Whether tile t of the inner element pass can run at degree P - 1, and its elements per block and
+// whether it loads the S^{-1} row into registers ahead of the traces.
+bool mf_tile_ready(int P, int t);
+void mf_tile_info(int P, int t, int* epb, int* prefetch);
 // Pick the inner element pass's tile by timing each candidate (degrees 2..4); *epb and *prefetch
 // report the choice (elements per block, S^{-1} row in registers).
 cudaError_t launch_mf_autotune(const Geom& g, MfOps& op, const float* x, float* y, const double* xd,

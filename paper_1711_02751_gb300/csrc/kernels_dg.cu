@@ -423,6 +423,7 @@ cudaError_t launch_dg_full(const Geom& g, const double* q, const double* phiB, d
 
 cudaError_t launch_combine(size_t n, const double* base, const CombineTerms& t, double* out,
                            unsigned* nonfinite_flag, cudaStream_t s) {
+    if (t.n < 0 || t.n > 10) return cudaErrorInvalidValue;
     combine_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, base, t, out, nonfinite_flag);
     count_launches(1);
     return cudaGetLastError();

@@ -42,6 +42,11 @@ __device__ __forceinline__ Lanes<T, VW> load_lanes(const T* __restrict__ p, size
         r.v[1] = q.y;
         r.v[2] = q.z;
         r.v[3] = q.w;
+    } else if constexpr (VW == 2) {
+        static_assert(sizeof(T) == 8, "16-byte lanes of FP64");
+        const double2 q = reinterpret_cast<const double2*>(p)[i];
+        r.v[0] = q.x;
+        r.v[1] = q.y;
     } else {
         r.v[0] = p[i];
     }
@@ -51,6 +56,7 @@ __device__ __forceinline__ Lanes<T, VW> load_lanes(const T* __restrict__ p, size
 template <typename T, int VW>
 __device__ __forceinline__ void store_lanes(T* __restrict__ p, size_t i, const Lanes<T, VW>& r) {
     if constexpr (VW == 4) reinterpret_cast<float4*>(p)[i] = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+    else if constexpr (VW == 2) reinterpret_cast<double2*>(p)[i] = make_double2(r.v[0], r.v[1]);
     else p[i] = r.v[0];
 }
 
@@ -348,9 +354,13 @@ guess_norms_x2_kernel(size_t n, const double* __restrict__ g, GuessTerms t, doub
     for (int q = 0; q < NQ; ++q) acc[q] = 0.f;
     for (size_t idx = blockIdx.x * (size_t)kDotThreads + threadIdx.x; idx < n;
          idx += (size_t)gridDim.x * kDotThreads) {
+        const double gv = g[idx];   // every load first
+        double yv[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) yv[j] = j < t.nq ? t.y[j][idx] : 0.0;
         float gh, gl, y0h = 0.f, y0l = 0.f;
-        split(g[idx], gh, gl);
-        split(t.y[0][idx], y0h, y0l);
+        split(gv, gh, gl);
+        split(yv[0], y0h, y0l);
         const float e = __fadd_rn(__fsub_rn(gh, y0h), __fsub_rn(gl, y0l));   // g - y_0
         float d[6];                                                         // y_0 - y_j
         d[0] = 0.f;
@@ -359,7 +369,7 @@ guess_norms_x2_kernel(size_t n, const double* __restrict__ g, GuessTerms t, doub
             d[j] = 0.f;
             if (j < t.nq) {
                 float yh, yl;
-                split(t.y[j][idx], yh, yl);
+                split(yv[j], yh, yl);
                 d[j] = __fadd_rn(__fsub_rn(y0h, yh), __fsub_rn(y0l, yl));
             }
         }
@@ -496,6 +506,15 @@ bool lanes4(size_t n, size_t ldv, std::initializer_list<const void*> ptrs) {
     return true;
 }
 
+// 16-byte lanes of FP64 vectors: every vector on a 16-byte boundary, n and the stride even
+template <typename T>
+bool lanes2d(size_t n, size_t ldv, std::initializer_list<const void*> ptrs) {
+    if (sizeof(T) != 8 || n % 2 != 0 || ldv % 2 != 0) return false;
+    for (const void* p : ptrs)
+        if (reinterpret_cast<uintptr_t>(p) % 16 != 0) return false;
+    return true;
+}
+
 template <int NJ, typename T>
 cudaError_t cgs2_tail_launch(const T* V, size_t ldv, const double* h1, T* w, size_t n, double* scratch,
                              double* h2, double* nw1, double* hn, T* vout, GmresCtl* ctl, int j, int m,
@@ -547,6 +566,7 @@ cudaError_t multidot_impl(const T* V, size_t ldv, int nv, const T* w, size_t n, 
     // one instance per column count: a runtime bound on the column loop would leave predicated-off
     // FMAs in the kernel, and on GB300 those still occupy the slow FP64 pipe
     const bool v4 = lanes4<T>(n, ldv, {V, w});
+    const bool v2 = lanes2d<T>(n, ldv, {V, w});
     for (int j0 = 0; j0 < nv; j0 += kDotChunk) {
         const int nj = nv - j0 < kDotChunk ? nv - j0 : kDotChunk;
         switch (nj) {
@@ -555,6 +575,12 @@ cudaError_t multidot_impl(const T* V, size_t ldv, int nv, const T* w, size_t n, 
         if constexpr (sizeof(T) == 4) {                                                                           \
             if (v4) {                                                                                             \
                 multidot_kernel<C, T, 4><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, j0, nj, w, n, scratch, nv, out, \
+                                                                           done);                                 \
+                break;                                                                                            \
+            }                                                                                                     \
+        } else {                                                                                                  \
+            if (v2) {                                                                                             \
+                multidot_kernel<C, T, 2><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, j0, nj, w, n, scratch, nv, out, \
                                                                            done);                                 \
                 break;                                                                                            \
             }                                                                                                     \

@@ -359,6 +359,7 @@ __global__ void __launch_bounds__(256) zero_f32_kernel(float* __restrict__ y, si
         y[t] = 0.f;
 }
 
+
 // y = hm + hp, or w = g - (hm + hp)
 template <typename TO, bool RESID>
 __global__ void __launch_bounds__(256)
@@ -683,10 +684,16 @@ cudaError_t launch_mf_autotune(const Geom& g, MfOps& op, const float* x, float* 
     op.tile_res = best_r;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    const int P = g.P, th = mf_tile_threads(best_t);
-    *epb = th / (P * P) > 32 ? 32 : (th / (P * P) > 0 ? th / (P * P) : 1);
-    *prefetch = mf_tile_pref(best_t) ? 1 : 0;
+    mf_tile_info(g.P, best_t, epb, prefetch);
     return err;
+}
+
+bool mf_tile_ready(int P, int t) { return t == 0 || (P >= 3 && P <= 5 && t > 0 && t < kMfTiles); }
+
+void mf_tile_info(int P, int t, int* epb, int* prefetch) {
+    const int th = mf_tile_threads(t);
+    *epb = th / (P * P) > 32 ? 32 : (th / (P * P) > 0 ? th / (P * P) : 1);
+    *prefetch = mf_tile_pref(t) ? 1 : 0;
 }
 
 cudaError_t launch_ens_mf_inner(const EnsHost& E, const MfOps& scratch, size_t nt, const float* x, float* y,
