@@ -330,6 +330,14 @@ hdgdg_status hdgdg_trace_apply(hdgdg_sim* sim, const double* x, double* y);
  * pass or the tile is not available. */
 hdgdg_status hdgdg_set_trace_tile(hdgdg_sim* sim, int tile);
 
+/* Select the tiles of the Schur-complement condensation and recovery kernels (local solves
+ * through the Schur complement on phi), overriding the ones picked at create: 0 the default;
+ * 1, 2 (degrees 2..4) blocks of 128 or 512 threads; 3 (degree 3) 128 threads with the element
+ * operators staged in shared memory by bulk asynchronous copies.  Every tile gives the same
+ * result bit for bit.  Cached step graphs are dropped.  HDGDG_EINVAL when the handle's local
+ * solves are not these kernels or a tile is not available. */
+hdgdg_status hdgdg_set_local_tiles(hdgdg_sim* sim, int condense_tile, int recover_tile);
+
 /* One implicit stage solve (Algorithm 1, the "else" branch): condense, GMRES on the trace
  * system, recover Q = A^{-1}(R1 - B qhat).  R1, Q: [3][n_el][(k+1)^2]; qhat: [edge][c][b]
  * (may be NULL).  *iterations (may be NULL) receives the GMRES iteration count. */

@@ -1008,7 +1008,7 @@ hdgdg_status one_step_graph(hdgdg_sim* sim) {
     const bool bad = flag[0] || flag[2] || flag[3] || ss.nonfinite || ss.notconv;
     if (bad) {   // the history slots may hold this step's partial solves: start the next solves afresh
         for (int i = 0; i < sim->s; ++i) sim->n_hist[i] = 0;
-        if (flag[2]) return fail(sim, HDGDG_ECUDA, "a bounded wait of the tensor-core local kernel ran out (%u)", flag[2]);
+        if (flag[2]) return fail(sim, HDGDG_ECUDA, "a bounded wait of a local kernel ran out (%u)", flag[2]);
         if (flag[3]) return fail(sim, HDGDG_ECUDA, "a bounded wait of the pipelined SpMV ran out (%u)", flag[3]);
         if (ss.nonfinite) return fail(sim, HDGDG_ENONFINITE, "non-finite trace right-hand side or GMRES residual");
         if (ss.notconv) {
@@ -1132,7 +1132,7 @@ hdgdg_status one_step(hdgdg_sim* sim) {
     CU(cudaMemcpyAsync(&sim->hbuf[0], sim->flags, sizeof(flag), cudaMemcpyDeviceToHost, st));
     TRY(sync(sim));
     std::memcpy(flag, &sim->hbuf[0], sizeof(flag));
-    if (flag[2]) return fail(sim, HDGDG_ECUDA, "a bounded wait of the tensor-core local kernel ran out (%u)", flag[2]);
+    if (flag[2]) return fail(sim, HDGDG_ECUDA, "a bounded wait of a local kernel ran out (%u)", flag[2]);
     if (flag[3]) return fail(sim, HDGDG_ECUDA, "a bounded wait of the pipelined SpMV ran out (%u)", flag[3]);
     if (flag[0]) return fail(sim, HDGDG_ENONFINITE, "step %lld produced a non-finite state", sim->stats.steps + 1);
     std::swap(sim->q, sim->q_new);
@@ -1282,6 +1282,7 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
                               sim->Seg, sim->stream));
         sim->ops.kind = x2 ? 3 : 0;
         sim->ops.schur = true;
+        sim->ops.error = reinterpret_cast<int*>(sim->flags) + 2;   // the staged tile's bounded waits
         sim->ops.S = sim->Sphi;
         sim->ops.aux = sim->Saux;
         sim->ops.EG = sim->Seg;
@@ -1721,6 +1722,23 @@ hdgdg_status hdgdg_set_trace_tile(hdgdg_sim* sim, int tile) {
     sim->mf.tile = tile;
     if (tile == 0) sim->trace_tile = sim->trace_prefetch = 0;
     else mf_tile_info(sim->g.P, tile, &sim->trace_tile, &sim->trace_prefetch);
+    return HDGDG_OK;
+}
+
+hdgdg_status hdgdg_set_local_tiles(hdgdg_sim* sim, int condense_tile, int recover_tile) {
+    if (!sim) return fail(sim, HDGDG_EINVAL, "NULL handle");
+    if (!sim->ops.schur || sim->ens)
+        return fail(sim, HDGDG_EINVAL, "set_local_tiles: the handle's local solves are not the Schur kernels");
+    for (int t : {condense_tile, recover_tile})
+        if (!schur_tile_ready(sim->g.P, sim->ops.kind == 3, t))
+            return fail(sim, HDGDG_EINVAL, "set_local_tiles: tile %d is not available at degree %d", t, sim->g.P - 1);
+    CU(cudaStreamSynchronize(sim->stream));
+    for (auto& cg : sim->cycle_graph) drop_graph(sim, cg);
+    drop_step_graphs(sim);
+    sim->ops.schur_tile_c = condense_tile;
+    sim->ops.schur_tile_r = recover_tile;
+    sim->ops.tile_condense = condense_tile == 0 ? 0 : schur_tile_epb(sim->g.P, condense_tile);
+    sim->ops.tile_recover = recover_tile == 0 ? 0 : schur_tile_epb(sim->g.P, recover_tile);
     return HDGDG_OK;
 }
 

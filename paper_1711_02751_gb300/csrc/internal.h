@@ -247,7 +247,7 @@ struct LocalOps {
     int tile_condense = 0, tile_recover = 0;              // kind 3: elements per block (0: default)
     int tile_condense_index = 0, tile_recover_index = 0;  // their index in the candidate list
     const void* image = nullptr;    // kind 2: the shared A^{-1} as a BF16 tensor-core operand tile
-    int* error = nullptr;           // kind 2: set when a bounded wait of the tensor-core kernel ran out
+    int* error = nullptr;           // kinds 2, 4 and the staged Schur tile: set when a bounded wait ran out
     // Kinds 0 and 3 with schur set: A^{-1} applied through the Schur complement on phi.  Only the
     // (phi, phi) block of A^{-1} is kept, S [n_el][col m][row n], with aux [n_el][4][Np] =
     // (1/d, -cx, -cy, phi_B) per node and EG [batch][2][P][P] = (-E, -G) per instance; the values
@@ -258,6 +258,10 @@ struct LocalOps {
     const void* aux = nullptr;
     const void* EG = nullptr;
 };
+// Whether tile t of the Schur kernels runs at degree P - 1 (pairs: FP32-pair operators), and its
+// elements per block.
+bool schur_tile_ready(int P, bool pairs, int t);
+int schur_tile_epb(int P, int t);
 // Setup of the Schur-complement local operators (LocalOps::S, aux, EG) from the FP64 A^{-1}, as
 // double or, with f32x2, as FP32 pairs (float2).  dta = dt a_ii.
 cudaError_t launch_schur_setup(const Geom& g, const double* Ainv, const double* phiB, const double* tau_edge,

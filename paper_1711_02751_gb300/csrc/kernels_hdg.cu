@@ -19,6 +19,7 @@
 #include "compensated.h"
 #include "internal.h"
 #include "schur.h"
+#include "staged.h"
 #include "ens.h"
 
 namespace hdgdg {
@@ -620,9 +621,97 @@ __global__ void __launch_bounds__(EPB * P * P)
     schur_recover_body<P, EPB, A>(blockIdx.x, g, S, aux, EG, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst);
 }
 
+// The same two passes with the element operators staged into shared memory by bulk copies
+// (staged.h) while each thread loads its own stage data and traces: the arithmetic is the
+// kernels' above, operand for operand.  err: the handle's word for a wait that ran out.
+template <int P, int EPB, class A>
+__global__ void __launch_bounds__(EPB * P * P)
+    schur_condense_staged_kernel(Geom g, const typename A::T* __restrict__ S, const typename A::T* __restrict__ aux,
+                                 const typename A::T* __restrict__ EG, const double* __restrict__ R1,
+                                 double* __restrict__ Z, unsigned* err) {
+    using T = typename A::T;
+    constexpr int Np = P * P;
+    __shared__ SchurSmem<P, EPB, A> sm;
+    __shared__ StagedOps<P, EPB, A> so;
+    const int le = threadIdx.x / Np, n = threadIdx.x % Np;
+    const int e0 = blockIdx.x * EPB, e = e0 + le;
+    const int ne = g.n_el - e0 < EPB ? g.n_el - e0 : EPB;
+    const bool live = le < EPB && e < g.n_el;
+    so.issue(S, aux, e0, ne);
+    const size_t fs = (size_t)g.n_el * Np, o = (size_t)e * Np + n;
+    T x0{}, xU{}, xV{};
+    if (live) {
+        x0 = A::from(R1[o]);
+        xU = A::from(R1[fs + o]);
+        xV = A::from(R1[2 * fs + o]);
+    }
+    if (!so.wait(err)) return;
+    SchurNode<A> nd;
+    if (live) so.load_node(nd, le, n);
+    T phi{}, U{}, V{};
+    schur_solve_with<P, EPB, A>(sm, g, e, le, n, live, nd, [&](int m) { return so.srow(le, n, m); }, EG, x0, xU, xV,
+                                phi, U, V);
+    if (live) {
+        Z[o] = A::to(phi);
+        Z[fs + o] = A::to(U);
+        Z[2 * fs + o] = A::to(V);
+    }
+}
+
+template <int P, int EPB, class A>
+__global__ void __launch_bounds__(EPB * P * P)
+    schur_recover_staged_kernel(Geom g, const typename A::T* __restrict__ S, const typename A::T* __restrict__ aux,
+                                const typename A::T* __restrict__ EG, const double* __restrict__ Z,
+                                const double* __restrict__ R1, const double* __restrict__ tau_edge,
+                                const double* __restrict__ qhat, double beta, double inv_aii, double* __restrict__ Q,
+                                double* __restrict__ Lst, unsigned* err) {
+    using T = typename A::T;
+    constexpr int Np = P * P, NF = 3 * P;
+    __shared__ SchurSmem<P, EPB, A> sm;
+    __shared__ StagedOps<P, EPB, A> so;
+    const int le = threadIdx.x / Np, n = threadIdx.x % Np, i = n % P, j = n / P;
+    const int e0 = blockIdx.x * EPB, e = e0 + le;
+    const int ne = g.n_el - e0 < EPB ? g.n_el - e0 : EPB;
+    const bool live = le < EPB && e < g.n_el;
+    so.issue(S, aux, e0, ne);
+    const size_t fs = (size_t)g.n_el * Np, o = (size_t)e * Np + n;
+    double u[3] = {0.0, 0.0, 0.0}, zv[3] = {0.0, 0.0, 0.0}, rv[3] = {0.0, 0.0, 0.0};
+    if (live) {
+        for (int c = 0; c < 3; ++c) {
+            zv[c] = Z[c * fs + o];
+            rv[c] = R1[c * fs + o];
+        }
+        for (int f = 0; f < 4; ++f) {
+            const bool on = (f == 0 && i == 0) || (f == 1 && i == P - 1) || (f == 2 && j == 0) ||
+                            (f == 3 && j == P - 1);
+            if (!on) continue;
+            const int b = (f < 2) ? j : i;
+            const int ed = edge_of_face(e, f, g);
+            const double tau = tau_edge[(size_t)ed * P + b];
+            for (int c = 0; c < 3; ++c) u[c] += tau * qhat[(size_t)ed * NF + c * P + b];
+        }
+    }
+    if (!so.wait(err)) return;
+    SchurNode<A> nd;
+    if (live) so.load_node(nd, le, n);
+    T y[3];
+    schur_solve_with<P, EPB, A>(sm, g, e, le, n, live, nd, [&](int m) { return so.srow(le, n, m); }, EG,
+                                A::from(u[0]), A::from(u[1]), A::from(u[2]), y[0], y[1], y[2]);
+    if (live) {
+        const double kk = beta * dt_factor(g, e);
+        for (int c = 0; c < 3; ++c) {
+            const size_t oc = c * fs + o;
+            const double q = zv[c] + kk * A::to(y[c]);
+            Q[oc] = q;
+            Lst[oc] = (q - rv[c]) * inv_aii;
+        }
+    }
+}
+
 // Tiles of the Schur-complement kernels: elements per block for about 256 (tile 0, the default),
-// 128 or 512 threads; the autotuner tries them at create for degrees 2..4.
-constexpr int schur_tile_threads(int t) { return t == 1 ? 128 : t == 2 ? 512 : 256; }
+// 128 or 512 threads; the autotuner tries them at create for degrees 2..4.  Tile 3 (degree 3):
+// 128 threads with the operators staged in shared memory.
+constexpr int schur_tile_threads(int t) { return t == 1 || t == 3 ? 128 : t == 2 ? 512 : 256; }
 template <int P>
 constexpr int schur_epb_for(int threads) {
     return threads / (P * P) > 0 ? threads / (P * P) : 1;
@@ -649,7 +738,23 @@ void schur_recover_t(const Geom& g, const LocalOps& ops, const double* Z, const 
 }
 
 template <int P, class A>
+constexpr bool schur_staged_ok() {
+    return P == 4 && StagedOps<P, schur_epb_for<P>(128), A>::kFits;
+}
+
+template <int P, class A>
 void schur_condense(const Geom& g, const LocalOps& ops, const double* R1, double* Z, cudaStream_t s) {
+    if constexpr (schur_staged_ok<P, A>()) {
+        if (ops.schur_tile_c == 3) {
+            using T = typename A::T;
+            constexpr int EPB = schur_epb_for<P>(128);
+            schur_condense_staged_kernel<P, EPB, A><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(
+                g, static_cast<const T*>(ops.S), static_cast<const T*>(ops.aux), static_cast<const T*>(ops.EG), R1, Z,
+                reinterpret_cast<unsigned*>(ops.error));
+            count_launches(1);
+            return;
+        }
+    }
     if constexpr (P >= 3 && P <= 5) {
         if (ops.schur_tile_c == 1) return schur_condense_t<P, A, 1>(g, ops, R1, Z, s);
         if (ops.schur_tile_c == 2) return schur_condense_t<P, A, 2>(g, ops, R1, Z, s);
@@ -660,6 +765,17 @@ void schur_condense(const Geom& g, const LocalOps& ops, const double* R1, double
 template <int P, class A>
 void schur_recover(const Geom& g, const LocalOps& ops, const double* Z, const double* R1, const double* tau_edge,
                    const double* qhat, double beta, double inv_aii, double* Q, double* Lst, cudaStream_t s) {
+    if constexpr (schur_staged_ok<P, A>()) {
+        if (ops.schur_tile_r == 3) {
+            using T = typename A::T;
+            constexpr int EPB = schur_epb_for<P>(128);
+            schur_recover_staged_kernel<P, EPB, A><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(
+                g, static_cast<const T*>(ops.S), static_cast<const T*>(ops.aux), static_cast<const T*>(ops.EG), Z, R1,
+                tau_edge, qhat, beta, inv_aii, Q, Lst, reinterpret_cast<unsigned*>(ops.error));
+            count_launches(1);
+            return;
+        }
+    }
     if constexpr (P >= 3 && P <= 5) {
         if (ops.schur_tile_r == 1) return schur_recover_t<P, A, 1>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s);
         if (ops.schur_tile_r == 2) return schur_recover_t<P, A, 2>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s);
@@ -684,7 +800,8 @@ cudaError_t autotune_schur(const Geom& g, LocalOps& ops, double* R1, double* Z, 
         float best_c = 1e30f, best_r = 1e30f;
         int tc = 0, tr = 0;
         cudaError_t err = cudaSuccess;
-        for (int t = 0; t < 3 && err == cudaSuccess; ++t) {
+        const int n_tiles = schur_staged_ok<P, A>() ? 4 : 3;
+        for (int t = 0; t < n_tiles && err == cudaSuccess; ++t) {
             ops.schur_tile_c = ops.schur_tile_r = t;
             float ms_c = 0.f, ms_r = 0.f;
             for (int k = 0; k < 2; ++k) schur_condense<P, A>(g, ops, R1, Z, s);
@@ -977,6 +1094,19 @@ int ens_elem_blocks(const EnsGroup& G) {
 }
 
 }  // namespace
+
+bool schur_tile_ready(int P, bool pairs, int t) {
+    if (t == 0) return true;
+    if (P < 3 || P > 5 || t < 0) return false;
+    if (t < 3) return true;
+    return t == 3 && (pairs ? schur_staged_ok<4, ArithF2>() : schur_staged_ok<4, ArithF64>()) && P == 4;
+}
+
+int schur_tile_epb(int P, int t) {
+    const int th = schur_tile_threads(t);
+    return th / (P * P) > 0 ? th / (P * P) : 1;
+}
+
 
 cudaError_t launch_ens_condense(const EnsHost& E, const double* R1, double* Z, double* gvec, cudaStream_t s) {
     const EnsTable te = ens_table(E, ens_elem_blocks);

@@ -21,7 +21,7 @@ DG_PRECISIONS = {"default": 0, "bf16": 1}
 
 EXPORTS = ["hdgdg_bytes_required", "hdgdg_node_coords", "hdgdg_create", "hdgdg_set_state",
            "hdgdg_step", "hdgdg_get_state", "hdgdg_get_stats", "hdgdg_last_error", "hdgdg_destroy",
-           "hdgdg_update_state", "hdgdg_eval_nl", "hdgdg_condense_rhs", "hdgdg_trace_apply", "hdgdg_set_trace_tile",
+           "hdgdg_update_state", "hdgdg_eval_nl", "hdgdg_condense_rhs", "hdgdg_trace_apply", "hdgdg_set_trace_tile", "hdgdg_set_local_tiles",
            "hdgdg_stage_solve",
            "hdgdg_measure_fp64_tflops", "hdgdg_measure_conversion_rates", "hdgdg_set_kernel_timing", "hdgdg_kernel_time",
            "hdgdg_mass_noalloc", "hdgdg_gll", "hdgdg_checkpoint_bytes", "hdgdg_save_checkpoint",
@@ -94,6 +94,7 @@ def lib():
         L.hdgdg_condense_rhs.argtypes = [ctypes.c_void_p, _P, _P]
         L.hdgdg_trace_apply.argtypes = [ctypes.c_void_p, _P, _P]
         L.hdgdg_set_trace_tile.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.hdgdg_set_local_tiles.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
         L.hdgdg_stage_solve.argtypes = [ctypes.c_void_p, _P, _P, _P, ctypes.POINTER(ctypes.c_int)]
         L.hdgdg_measure_fp64_tflops.argtypes = [_P]
         L.hdgdg_measure_conversion_rates.argtypes = [_P, _P]
@@ -342,6 +343,10 @@ class Sim:
     def set_trace_tile(self, tile):
         """Select the inner cycles' element-pass tile (0 the default, 1..8 at degrees 2..4)."""
         self._check(lib().hdgdg_set_trace_tile(self._h, int(tile)))
+
+    def set_local_tiles(self, condense, recover):
+        """Select the Schur condensation and recovery tiles (0 the default, 1..2, 3 staged at k = 3)."""
+        self._check(lib().hdgdg_set_local_tiles(self._h, int(condense), int(recover)))
 
     def stage_solve(self, R1):
         R1 = _f64(R1, (3, self.n_el, self.Np))

@@ -128,3 +128,27 @@ def test_schur_batch_with_per_instance_time_steps():
             out.append(s.get_state())
     for a, b in zip(out[0], out[1]):
         assert _close(a, b, 1e-12)
+
+
+@pytest.mark.parametrize("boundary", ["periodic", "wall"])
+@pytest.mark.parametrize("kw", [{}, {"precision": "mixed", "local_precision": "f32x2", "trace_operator": 1}])
+def test_every_schur_tile_gives_the_same_steps(boundary, kw):
+    """The condensation and recovery kernels in each tile -- 256, 128 and 512 threads, and 128
+    threads with the element operators staged in shared memory by bulk asynchronous copies -- give
+    the same three steps bit for bit, in the FP64 form (FP64 Schur operators) and in the mixed
+    form (FP32-pair operators), on a mesh of 4356 elements (N = 66, k = 3) whose last block is
+    partial in every tile."""
+    N, k = 66, 3
+    m, h, hu, hv, b = user_state(N, k, "large")
+    out = {}
+    with hd.Sim(N, k, 0.01, bottom=b, g=W.G, H0=W.H0, boundary=boundary, **kw) as s:
+        for t in range(4):
+            s.set_local_tiles(t, t)
+            s.set_state(h, hu, hv)
+            s.step(3)
+            out[t] = s.get_state()
+        with pytest.raises(hd.HdgdgError):
+            s.set_local_tiles(4, 0)
+    for t in range(1, 4):
+        for a_, c_ in zip(out[t], out[0]):
+            assert np.array_equal(a_, c_), t
