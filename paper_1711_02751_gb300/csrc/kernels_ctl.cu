@@ -49,23 +49,64 @@ __global__ void solve_begin_kernel(const double* __restrict__ cand, int avail, d
 }
 
 // x~ = x_{n-1} + sum_j (c_qj - [j = 0]) x_{n-1-j} and w = g - sum_j c_qj S~x_{n-1-j} for the chosen
-// order q (the host driver's two combinations, term for term); q = 0: x~ = 0, w = g.
+// order q (the host driver's two combinations, term for term); q = 0: x~ = 0, w = g.  One loop
+// per order, its terms indexed by constants.
+template <int Q>
+__device__ __forceinline__ void guess_apply_order(size_t n, const double* __restrict__ g, const GuessHistory& h,
+                                                  double* __restrict__ xt, double* __restrict__ w) {
+    constexpr int U = 2;   // entries a grid apart per pass, every load issued before the sums
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i0 < n; i0 += U * stride) {
+        if constexpr (Q == 0) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const size_t idx = i0 + u * stride;
+                if (idx < n) {
+                    xt[idx] = 0.0;
+                    w[idx] = g[idx];
+                }
+            }
+        } else {
+            double xv[U][Q], yv[U][Q], gv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const size_t idx = i0 + u * stride;
+                if (idx < n) {
+                    gv[u] = g[idx];
+#pragma unroll
+                    for (int j = 0; j < Q; ++j) {
+                        xv[u][j] = h.x[j][idx];
+                        yv[u][j] = h.y[j][idx];
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const size_t idx = i0 + u * stride;
+                if (idx >= n) continue;
+                double ax = xv[u][0];
+#pragma unroll
+                for (int j = 0; j < Q; ++j) ax += (h.c[Q][j] - (j == 0 ? 1.0 : 0.0)) * xv[u][j];
+                double aw = gv[u];
+#pragma unroll
+                for (int j = 0; j < Q; ++j) aw += (-h.c[Q][j]) * yv[u][j];
+                xt[idx] = ax;
+                w[idx] = aw;
+            }
+        }
+    }
+}
+
 __global__ void guess_apply_kernel(size_t n, const double* __restrict__ g, GuessHistory h,
                                    const SolveCtl* __restrict__ sc, double* __restrict__ xt, double* __restrict__ w) {
-    const int q = sc->active ? sc->guess : 0;
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        if (q == 0) {
-            xt[idx] = 0.0;
-            w[idx] = g[idx];
-            continue;
-        }
-        double ax = h.x[0][idx];
-        for (int j = 0; j < q; ++j) ax += (h.c[q][j] - (j == 0 ? 1.0 : 0.0)) * h.x[j][idx];
-        double aw = g[idx];
-        for (int j = 0; j < q; ++j) aw += (-h.c[q][j]) * h.y[j][idx];
-        xt[idx] = ax;
-        w[idx] = aw;
+    switch (sc->active ? sc->guess : 0) {
+        case 1: return guess_apply_order<1>(n, g, h, xt, w);
+        case 2: return guess_apply_order<2>(n, g, h, xt, w);
+        case 3: return guess_apply_order<3>(n, g, h, xt, w);
+        case 4: return guess_apply_order<4>(n, g, h, xt, w);
+        case 5: return guess_apply_order<5>(n, g, h, xt, w);
+        case 6: return guess_apply_order<6>(n, g, h, xt, w);
+        default: return guess_apply_order<0>(n, g, h, xt, w);
     }
 }
 

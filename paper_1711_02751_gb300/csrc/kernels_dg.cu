@@ -15,6 +15,8 @@
 
 #include "ens.h"
 #include "fastcvt.h"
+#include <cstdint>
+
 #include "internal.h"
 
 namespace hdgdg {
@@ -218,14 +220,51 @@ dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict_
     dg_volume_body<P, FULL, Tc, BF>(blockIdx.x, g, q, phiB, fface, scale, out);
 }
 
+// One instance per term count NT (0..10), the terms indexed by constants.  Each thread takes U
+// lanes of L entries (L = 2: 16-byte loads, every vector 16-byte aligned and n even) a grid apart
+// per pass and issues all their loads before the first sum; each entry's terms are added in their
+// order, so the lane width changes no result.
+template <int L>
+__device__ __forceinline__ void load_l(const double* __restrict__ p, size_t i, double* v) {
+    if constexpr (L == 2) {
+        const double2 q = reinterpret_cast<const double2*>(p)[i];
+        v[0] = q.x;
+        v[1] = q.y;
+    } else {
+        v[0] = p[i];
+    }
+}
+
+template <int NT, int L>
 __global__ void combine_kernel(size_t n, const double* __restrict__ base, CombineTerms t,
                                double* out, unsigned* nonfinite) {
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        double acc = base[idx];
-        for (int k = 0; k < t.n; ++k) acc += t.c[k] * t.X[k][idx];
-        out[idx] = acc;
-        if (nonfinite && !isfinite(acc)) *nonfinite = 1u;
+    constexpr int U = NT <= 2 ? 4 : 2;
+    const size_t stride = (size_t)gridDim.x * blockDim.x, nl = n / L;
+    for (size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i0 < nl; i0 += U * stride) {
+        double acc[U][L], xv[U][NT > 0 ? NT : 1][L];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t il = i0 + u * stride;
+            if (il < nl) {
+                load_l<L>(base, il, acc[u]);
+#pragma unroll
+                for (int k = 0; k < NT; ++k) load_l<L>(t.X[k], il, xv[u][k]);
+            }
+        }
+        bool bad = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t il = i0 + u * stride;
+            if (il >= nl) continue;
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+#pragma unroll
+                for (int k = 0; k < NT; ++k) acc[u][l] += t.c[k] * xv[u][k][l];
+                out[il * L + l] = acc[u][l];
+                bad |= !isfinite(acc[u][l]);
+            }
+        }
+        if (nonfinite && bad) *nonfinite = 1u;
     }
 }
 
@@ -424,7 +463,19 @@ cudaError_t launch_dg_full(const Geom& g, const double* q, const double* phiB, d
 cudaError_t launch_combine(size_t n, const double* base, const CombineTerms& t, double* out,
                            unsigned* nonfinite_flag, cudaStream_t s) {
     if (t.n < 0 || t.n > 10) return cudaErrorInvalidValue;
-    combine_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, base, t, out, nonfinite_flag);
+    bool l2 = n % 2 == 0 && reinterpret_cast<uintptr_t>(base) % 16 == 0 && reinterpret_cast<uintptr_t>(out) % 16 == 0;
+    for (int k = 0; k < t.n; ++k) l2 = l2 && reinterpret_cast<uintptr_t>(t.X[k]) % 16 == 0;
+    const int grid = grid_for(l2 ? n / 2 : n, 256);
+    switch (t.n) {
+#define CASE(K)                                                                                 \
+    case K:                                                                                     \
+        if (l2) combine_kernel<K, 2><<<grid, 256, 0, s>>>(n, base, t, out, nonfinite_flag); \
+        else combine_kernel<K, 1><<<grid, 256, 0, s>>>(n, base, t, out, nonfinite_flag);     \
+        break;
+        CASE(0) CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
     count_launches(1);
     return cudaGetLastError();
 }

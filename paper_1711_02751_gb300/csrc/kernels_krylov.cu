@@ -288,6 +288,8 @@ axpy_scale_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict_
 
 // ||g||^2 and the residual norms of every candidate initial guess in one pass over g and the
 // stored products (no matrix product): out[0] = ||g||^2, out[q] = ||g - sum_j c[q][j] y[j]||^2.
+// NQT = the number of stored products (one instance each, the loops bounded by constants).
+template <int NQT>
 __global__ void __launch_bounds__(kDotThreads)
 guess_norms_kernel(size_t n, const double* __restrict__ g, GuessTerms t, double* __restrict__ scratch,
                    double* __restrict__ out) {
@@ -303,11 +305,11 @@ guess_norms_kernel(size_t n, const double* __restrict__ g, GuessTerms t, double*
         const double gv = g[idx];
         double yv[6];
 #pragma unroll
-        for (int j = 0; j < 6; ++j) yv[j] = j < t.nq ? t.y[j][idx] : 0.0;
+        for (int j = 0; j < 6; ++j) yv[j] = j < NQT ? t.y[j][idx] : 0.0;
         acc[0] += gv * gv;
 #pragma unroll
         for (int q = 1; q < NQ; ++q) {
-            if (q > t.nq) break;
+            if (q > NQT) break;
             double r = gv;
 #pragma unroll
             for (int j = 0; j < 6; ++j)
@@ -328,7 +330,7 @@ guess_norms_kernel(size_t n, const double* __restrict__ g, GuessTerms t, double*
         partial[(size_t)blockIdx.x * NQ + threadIdx.x] = s;
     }
     if (last_block_arrives(counter)) {
-        reduce_partials(partial, gridDim.x, NQ, 0, t.nq + 1, out);
+        reduce_partials(partial, gridDim.x, NQ, 0, NQT + 1, out);
         if (threadIdx.x == 0) *counter = 0u;
     }
 }
@@ -336,9 +338,11 @@ guess_norms_kernel(size_t n, const double* __restrict__ g, GuessTerms t, double*
 // The same norms for the mixed form, whose tolerance is 1e-9 ||g||: the candidates only choose the
 // start, and an extrapolated start's norm is then taken exactly.  Every order's coefficients sum to
 // one, so g - sum_j c[q][j] y_j = (g - y_0) + sum_{j>=1} c[q][j] (y_0 - y_j): the differences of
-// nearly equal vectors are formed first from FP32 pairs (the high parts subtract exactly, the low
-// parts' difference is added), which keeps each small difference to FP32 relative accuracy; the
-// candidates and their squares then run in plain FP32, and the sums across threads in FP64.
+// nearly equal vectors are formed first in FP64 (exact when the two are within a factor of two,
+// Sterbenz) and rounded once to FP32 (fastcvt.h), which keeps each small difference to FP32
+// relative accuracy; the candidates and their squares then run in plain FP32, and the sums across
+// threads in FP64.
+template <int NQT>
 __global__ void __launch_bounds__(kDotThreads)
 guess_norms_x2_kernel(size_t n, const double* __restrict__ g, GuessTerms t, double* __restrict__ scratch,
                       double* __restrict__ out) {
@@ -357,26 +361,17 @@ guess_norms_x2_kernel(size_t n, const double* __restrict__ g, GuessTerms t, doub
         const double gv = g[idx];   // every load first
         double yv[6];
 #pragma unroll
-        for (int j = 0; j < 6; ++j) yv[j] = j < t.nq ? t.y[j][idx] : 0.0;
-        float gh, gl, y0h = 0.f, y0l = 0.f;
-        split(gv, gh, gl);
-        split(yv[0], y0h, y0l);
-        const float e = __fadd_rn(__fsub_rn(gh, y0h), __fsub_rn(gl, y0l));   // g - y_0
-        float d[6];                                                         // y_0 - y_j
+        for (int j = 0; j < 6; ++j) yv[j] = j < NQT ? t.y[j][idx] : 0.0;
+        const float gh = f64_to_f32(gv);
+        const float e = f64_to_f32(gv - yv[0]);   // g - y_0
+        float d[6];                                // y_0 - y_j
         d[0] = 0.f;
 #pragma unroll
-        for (int j = 1; j < 6; ++j) {
-            d[j] = 0.f;
-            if (j < t.nq) {
-                float yh, yl;
-                split(yv[j], yh, yl);
-                d[j] = __fadd_rn(__fsub_rn(y0h, yh), __fsub_rn(y0l, yl));
-            }
-        }
+        for (int j = 1; j < 6; ++j) d[j] = j < NQT ? f64_to_f32(yv[0] - yv[j]) : 0.f;
         acc[0] = __fmaf_rn(gh, gh, acc[0]);
 #pragma unroll
         for (int q = 1; q < NQ; ++q) {
-            if (q > t.nq) break;
+            if (q > NQT) break;
             float r = e;
 #pragma unroll
             for (int j = 1; j < 6; ++j)
@@ -397,7 +392,7 @@ guess_norms_x2_kernel(size_t n, const double* __restrict__ g, GuessTerms t, doub
         partial[(size_t)blockIdx.x * NQ + threadIdx.x] = s;
     }
     if (last_block_arrives(counter)) {
-        reduce_partials(partial, gridDim.x, NQ, 0, t.nq + 1, out);
+        reduce_partials(partial, gridDim.x, NQ, 0, NQT + 1, out);
         if (threadIdx.x == 0) *counter = 0u;
     }
 }
@@ -462,18 +457,34 @@ __global__ void gmres_solve_y_kernel(GmresCtl* c) {
 // x += sum_{j < jend} y_j V_j.  FP64 basis: FP64 sums.  FP32 basis (the mixed form's inner
 // cycles): the correction is summed in FP32 -- the cycle that produced it is FP32 throughout --
 // and added to the FP64 iterate once, one conversion (fastcvt.h) and one FP64 add per entry.
-template <typename T>
+// VW entries per thread (16-byte lanes of FP32 bases); the basis loads are issued four vectors at a
+// time and added in their order.
+template <typename T, int VW = 1>
 __global__ void gmres_update_x_kernel(const T* __restrict__ V, size_t ldv, const GmresCtl* __restrict__ c,
                                       double* __restrict__ x, size_t n) {
     const int nv = c->jend;
     __shared__ T sy[GmresCtl::kM];
     for (int j = threadIdx.x; j < nv; j += blockDim.x) sy[j] = T(c->y[j]);
     __syncthreads();
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        T acc = T(0);
-        for (int j = 0; j < nv; ++j) acc += sy[j] * V[(size_t)j * ldv + idx];
-        x[idx] += to_f64(acc);
+    for (size_t iv = blockIdx.x * (size_t)blockDim.x + threadIdx.x; iv < n / VW;
+         iv += (size_t)gridDim.x * blockDim.x) {
+        T acc[VW];
+#pragma unroll
+        for (int k = 0; k < VW; ++k) acc[k] = T(0);
+        for (int j0 = 0; j0 < nv; j0 += 4) {
+            Lanes<T, VW> v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (j0 + u < nv) v[u] = load_lanes<T, VW>(V + (size_t)(j0 + u) * ldv, iv);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (j0 + u < nv) {
+#pragma unroll
+                    for (int k = 0; k < VW; ++k) acc[k] += sy[j0 + u] * v[u].v[k];
+                }
+        }
+#pragma unroll
+        for (int k = 0; k < VW; ++k) x[iv * VW + k] += to_f64(acc[k]);
     }
 }
 
@@ -602,9 +613,16 @@ size_t guess_scratch_doubles() { return 1 + (size_t)kDotBlocks * 7; }
 
 cudaError_t launch_guess_norms(size_t n, const double* g, const GuessTerms& t, double* scratch, double* out,
                                cudaStream_t s, bool f32x2) {
-    if (t.nq < 1 || t.nq > 6) return cudaErrorInvalidValue;
-    if (f32x2) guess_norms_x2_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(n, g, t, scratch, out);
-    else guess_norms_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(n, g, t, scratch, out);
+    switch (t.nq) {
+#define CASE(Q)                                                                                   \
+    case Q:                                                                                       \
+        if (f32x2) guess_norms_x2_kernel<Q><<<kDotBlocks, kDotThreads, 0, s>>>(n, g, t, scratch, out); \
+        else guess_norms_kernel<Q><<<kDotBlocks, kDotThreads, 0, s>>>(n, g, t, scratch, out);          \
+        break;
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -693,7 +711,8 @@ cudaError_t launch_gmres_update(const double* V, size_t ldv, GmresCtl* c, double
 
 cudaError_t launch_gmres_update(const float* V, size_t ldv, GmresCtl* c, double* x, size_t n, cudaStream_t s) {
     gmres_solve_y_kernel<<<1, 1, 0, s>>>(c);
-    gmres_update_x_kernel<float><<<stream_grid(n), 256, 0, s>>>(V, ldv, c, x, n);
+    if (lanes4<float>(n, ldv, {V})) gmres_update_x_kernel<float, 4><<<stream_grid(n / 4), 256, 0, s>>>(V, ldv, c, x, n);
+    else gmres_update_x_kernel<float><<<stream_grid(n), 256, 0, s>>>(V, ldv, c, x, n);
     count_launches(2);
     return cudaGetLastError();
 }
