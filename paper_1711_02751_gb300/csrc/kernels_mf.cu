@@ -399,6 +399,59 @@ mf_back_kernel(int n_edges, PrecondBlocks Minv, const double* __restrict__ x, do
     mf_back_body<NF>(blockIdx.x, n_edges, Minv, x, y);
 }
 
+// The two FP64-class block-Jacobi products -- the refinement residual's y = M^{-1} x as FP32 pairs
+// (PAIRS) and the back-transformation qhat = M^{-1} x~ in FP64 -- with four rows per thread
+// (NF % 4 == 0): the edge's x split into FP32 pairs in shared memory by its threads, then four
+// Dot2 sums over the edge's NF columns from 8-byte FP16 loads.  Each row's sum is mf_pre_body's
+// (ArithF2) or mf_back_body's, term for term.
+template <int NF, bool PAIRS>
+__global__ void __launch_bounds__(256)
+    mf_edge_quad_kernel(int n_edges, PrecondBlocks Minv, const double* __restrict__ x, void* __restrict__ yv) {
+    static_assert(NF % 4 == 0, "four rows per thread");
+    constexpr int Q = NF / 4, EPB = 256 / Q;
+    __shared__ float sxh[EPB][NF], sxl[EPB][NF];
+    const int le = threadIdx.x / Q, q = threadIdx.x % Q;
+    const int r = blockIdx.x * EPB + le;
+    const bool live = le < EPB && r < n_edges;
+    if (live) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) split(x[(size_t)r * NF + 4 * q + t], sxh[le][4 * q + t], sxl[le][4 * q + t]);
+    }
+    __syncthreads();
+    if (!live) return;
+    const __half* M = Minv.h + (size_t)r * NF * NF + 4 * q;
+    Dot2 acc[4];
+#pragma unroll
+    for (int jj = 0; jj < NF; ++jj) {
+        const uint2 mv = *reinterpret_cast<const uint2*>(M + jj * NF);
+        const float2 m01 = __half22float2(*reinterpret_cast<const __half2*>(&mv.x));
+        const float2 m23 = __half22float2(*reinterpret_cast<const __half2*>(&mv.y));
+        const float xh = sxh[le][jj], xl = sxl[le][jj];
+        acc[0].add(m01.x, 0.f, xh, xl);
+        acc[1].add(m01.y, 0.f, xh, xl);
+        acc[2].add(m23.x, 0.f, xh, xl);
+        acc[3].add(m23.y, 0.f, xh, xl);
+    }
+    const float sc = Minv.scale[r];   // a power of two: scaling the pair is exact
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const size_t o = (size_t)r * NF + 4 * q + t;
+        if constexpr (PAIRS) {
+            float2 pr;
+            two_sum(acc[t].p, acc[t].c, pr.x, pr.y);
+            static_cast<float2*>(yv)[o] = float2{pr.x * sc, pr.y * sc};
+        } else {
+            static_cast<double*>(yv)[o] = f32_to_f64(acc[t].p * sc) + f32_to_f64(acc[t].c * sc);
+        }
+    }
+}
+
+template <int NF, bool PAIRS>
+void mf_edge_quad_launch(int n_edges, const PrecondBlocks& Minv, const double* x, void* y, cudaStream_t s) {
+    constexpr int EPB = 256 / (NF / 4);
+    mf_edge_quad_kernel<NF, PAIRS><<<(n_edges + EPB - 1) / EPB, EPB * (NF / 4), 0, s>>>(n_edges, Minv, x, y);
+}
+
 // Setup: per edge (one block) the FP16 block-Jacobi inverse scaled by the power of two 2^e with
 // max |entry| / 2^e in [0.5, 1), and that scale.
 __global__ void precond_f16_kernel(const double* __restrict__ Minv, int NF, __half* __restrict__ h,
@@ -503,9 +556,13 @@ cudaError_t mf_launch(const Geom& g, const MfOps& op, const void* S, const void*
     }
     const void* yv = x;
     if constexpr (MODE != kMfPlain) {
-        constexpr int EPE = 256 / NF;
-        mf_pre_kernel<NF, A, TO><<<(g.n_edges + EPE - 1) / EPE, EPE * NF, 0, s>>>(
-            g.n_edges, op.Minv, static_cast<const TO*>(x), static_cast<T*>(op.ybuf), done);
+        if constexpr (MODE == kMfResidual && NF % 4 == 0) {
+            mf_edge_quad_launch<NF, true>(g.n_edges, op.Minv, static_cast<const double*>(x), op.ybuf, s);
+        } else {
+            constexpr int EPE = 256 / NF;
+            mf_pre_kernel<NF, A, TO><<<(g.n_edges + EPE - 1) / EPE, EPE * NF, 0, s>>>(
+                g.n_edges, op.Minv, static_cast<const TO*>(x), static_cast<T*>(op.ybuf), done);
+        }
         yv = op.ybuf;
     }
     TO* hm = static_cast<TO*>(op.hm);
@@ -717,7 +774,8 @@ cudaError_t launch_mf_back(const Geom& g, const PrecondBlocks& Minv, const doubl
 #define CASE(P, NF)                                                                                      \
     case P: {                                                                                            \
         constexpr int EPB = 256 / NF;                                                                    \
-        mf_back_kernel<NF><<<(g.n_edges + EPB - 1) / EPB, EPB * NF, 0, s>>>(g.n_edges, Minv, x, y);     \
+        if constexpr (NF % 4 == 0) mf_edge_quad_launch<NF, false>(g.n_edges, Minv, x, y, s);             \
+        else mf_back_kernel<NF><<<(g.n_edges + EPB - 1) / EPB, EPB * NF, 0, s>>>(g.n_edges, Minv, x, y); \
         count_launches(1);                                                                               \
         return cudaGetLastError();                                                                       \
     }
