@@ -148,7 +148,7 @@ __device__ __forceinline__ void mf_face_pre(int bid, const Geom& g, const Precon
                 const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    const uint2 mv = *reinterpret_cast<const uint2*>(M + (size_t)(4 * jq + t) * NF);
+                    const uint2 mv = ld_stream(reinterpret_cast<const uint2*>(M + (size_t)(4 * jq + t) * NF));
                     const float2 m01 = __half22float2(*reinterpret_cast<const __half2*>(&mv.x));
                     const float2 m23 = __half22float2(*reinterpret_cast<const __half2*>(&mv.y));
                     a0 = __fmaf_rn(m01.x, xs[t], a0);
@@ -277,10 +277,10 @@ __device__ __forceinline__ void mf_elem_body(int bid, const Geom& g, const typen
     T srow[kPref ? Np : 1];
     const T* Sn = S + (size_t)(live ? e : 0) * Np * Np + n;
     if (live) {
-        nd.load(aux, e, n, Np);
+        nd.template load<true>(aux, e, n, Np);
         if constexpr (kPref) {
 #pragma unroll
-            for (int m = 0; m < Np; ++m) srow[m] = Sn[(size_t)m * Np];
+            for (int m = 0; m < Np; ++m) srow[m] = ld_stream(Sn + (size_t)m * Np);
         }
     }
     if constexpr (FUSE) {
@@ -337,8 +337,8 @@ __device__ __forceinline__ void mf_elem_body(int bid, const Geom& g, const typen
         schur_solve_with<P, EPB, A>(sm, g, e, le, n, live, nd, [&](int m) { return srow[m]; }, EG, u[0], u[1],
                                     u[2], W[0], W[1], W[2]);
     else
-        schur_solve_with<P, EPB, A>(sm, g, e, le, n, live, nd, [&](int m) { return Sn[(size_t)m * Np]; }, EG, u[0],
-                                    u[1], u[2], W[0], W[1], W[2]);
+        schur_solve_with<P, EPB, A>(sm, g, e, le, n, live, nd, [&](int m) { return ld_stream(Sn + (size_t)m * Np); },
+                                    EG, u[0], u[1], u[2], W[0], W[1], W[2]);
     if (live) mf_elem_rows<P, EPB, A, MODE, FUSE>(g, e, le, nd, on, fc, bb, ed, yv_, tau, W, beta, hm, hp);
 }
 
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(256)
     Dot2 acc[4];
 #pragma unroll
     for (int jj = 0; jj < NF; ++jj) {
-        const uint2 mv = *reinterpret_cast<const uint2*>(M + jj * NF);
+        const uint2 mv = ld_stream(reinterpret_cast<const uint2*>(M + jj * NF));
         const float2 m01 = __half22float2(*reinterpret_cast<const __half2*>(&mv.x));
         const float2 m23 = __half22float2(*reinterpret_cast<const __half2*>(&mv.y));
         const float xh = sxh[le][jj], xl = sxl[le][jj];

@@ -83,16 +83,32 @@ struct SchurSmem {
     T w[EPB][Np];       // phi_B phi
 };
 
-// The four numbers per node the solve needs (1/d, -cx, -cy, phi_B), loaded at once.
+// A load of operator data read once per pass, marked evict-first (ld.global.cs) so that it does
+// not push out of L2 the vectors that the passes around it reuse.
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T* p) {
+    return __ldcs(p);
+}
+
+// The four numbers per node the solve needs (1/d, -cx, -cy, phi_B), loaded at once (STREAM: as
+// evict-first loads).
 template <class A>
 struct SchurNode {
     typename A::T rd{}, ncx{}, ncy{}, pb{};
+    template <bool STREAM = false>
     __device__ __forceinline__ void load(const typename A::T* __restrict__ aux, int e, int n, int Np) {
         const typename A::T* ax = aux + (size_t)e * 4 * Np;
-        rd = ax[n];
-        ncx = ax[Np + n];
-        ncy = ax[2 * Np + n];
-        pb = ax[3 * Np + n];
+        if constexpr (STREAM) {
+            rd = ld_stream(ax + n);
+            ncx = ld_stream(ax + Np + n);
+            ncy = ld_stream(ax + 2 * Np + n);
+            pb = ld_stream(ax + 3 * Np + n);
+        } else {
+            rd = ax[n];
+            ncx = ax[Np + n];
+            ncy = ax[2 * Np + n];
+            pb = ax[3 * Np + n];
+        }
     }
 };
 
