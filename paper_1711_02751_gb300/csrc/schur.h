@@ -170,7 +170,8 @@ __device__ __forceinline__ void schur_solve_with(SchurSmem<P, EPB, A>& sm, const
     }
 }
 
-// The same with the node's numbers and S^{-1} read from memory (S [n_el][col m][row n]).
+// The same with the node's numbers and S^{-1} read from memory (S [n_el][col m][row n]), as
+// evict-first loads (each pass reads them once).
 template <int P, int EPB, class A>
 __device__ __forceinline__ void schur_solve(SchurSmem<P, EPB, A>& sm, const Geom& g, int e, int le, int n,
                                             bool live, const typename A::T* __restrict__ S,
@@ -180,10 +181,10 @@ __device__ __forceinline__ void schur_solve(SchurSmem<P, EPB, A>& sm, const Geom
                                             typename A::T& U, typename A::T& V) {
     constexpr int Np = P * P;
     SchurNode<A> nd;
-    if (live) nd.load(aux, e, n, Np);
+    if (live) nd.template load<true>(aux, e, n, Np);
     const typename A::T* Sn = S + (size_t)e * Np * Np + n;
-    schur_solve_with<P, EPB, A>(sm, g, e, le, n, live, nd, [&](int m) { return Sn[(size_t)m * Np]; }, EG, x0, xU,
-                                xV, phi, U, V);
+    schur_solve_with<P, EPB, A>(sm, g, e, le, n, live, nd, [&](int m) { return ld_stream(Sn + (size_t)m * Np); },
+                                EG, x0, xU, xV, phi, U, V);
 }
 
 }  // namespace hdgdg
