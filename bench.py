@@ -229,14 +229,14 @@ class ClockSampler:
 # ---- roofline --------------------------------------------------------------------------------
 def _algorithmic(N, k, cls, precision="fp64", dense=False, local="fp64", mf=False):
     """(bytes, flops) one launch group of a kernel class moves / performs.  mf: the mixed form's
-    matrix-free trace operator (per edge its FP16 M^{-1} block and scale, tau and x, y once; per
-    element the FP32 Schur operators; the flops count the M^{-1} products, the local solve and the
-    lift)."""
+    matrix-free trace operator (per edge its FP16 M^{-1} block and scale, tau in FP32 and x, y
+    once; per element the FP32 Schur operators; the flops count the M^{-1} products, the local
+    solve and the lift)."""
     P = k + 1
     NF, NV, Np = 3 * P, 3 * P * P, P * P
     n_el, n_edges = N * N, 2 * N * N
     if cls == "spmv" and mf:   # matrix-free: FP16 M^{-1} blocks and scales, FP32 Schur operators, tau, x and y once
-        return (n_edges * (NF * NF * 2 + 4 + P * 8 + 2 * NF * 4) + n_el * (Np * Np + 4 * Np) * 4,
+        return (n_edges * (NF * NF * 2 + 4 + P * 4 + 2 * NF * 4) + n_el * (Np * Np + 4 * Np) * 4,
                 n_el * (2 * 4 * NF * NF + 2 * (2 * Np * Np + Np * (8 * P + 26)) + 24 * P))
     if cls == "spmv":   # 6 off-diagonal NF x NF blocks + column ids + x and y once
         w = 4 if precision == "mixed" else 8

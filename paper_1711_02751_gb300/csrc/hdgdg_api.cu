@@ -129,6 +129,7 @@ Plan make_plan(const hdgdg_config* c) {
         b += n_edges * (size_t)p.NF * p.NF * sizeof(__half) + n_edges * sizeof(float);
         b += (n_el * Np * Np + 4 * n_el * Np + 2 * B * Np) * sizeof(float);
         b += 3 * p.nt * d;   // M^{-1} x and the two halves of S y
+        b += n_edges * P * sizeof(float);   // tau_hat in FP32 (the fused inner pass)
     }
     b += 2 * (size_t)guess_order(c) * p.s * p.nt * d;         // previous stage solutions and products
     p.persistent = b;
@@ -1296,6 +1297,10 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
             TRY(dalloc(sim, &sim->Minv16, (size_t)g.n_edges * p.NF * p.NF));
             TRY(dalloc(sim, &sim->Mscale, (size_t)g.n_edges));
             TRY(dalloc(sim, &ybuf, p.nt));
+            float* tau32 = nullptr;
+            TRY(dalloc(sim, &tau32, (size_t)g.n_edges * g.P));
+            CU(launch_to_f32(sim->tau, tau32, (size_t)g.n_edges * g.P, sim->stream));
+            sim->mf.tau32 = tau32;
             TRY(dalloc(sim, &hm, p.nt));
             TRY(dalloc(sim, &hp, p.nt));
             CU(launch_pair_hi(sim->Sphi, S32, nS, sim->stream));

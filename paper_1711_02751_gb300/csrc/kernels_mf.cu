@@ -194,7 +194,7 @@ __device__ __forceinline__ void mf_elem_rows(const Geom& g, int e, int le, const
     W[0] = A::mul(bt, W[0]);
     W[1] = A::mul(bt, W[1]);
     W[2] = A::mul(bt, W[2]);
-    const T one = A::from(1.0), mone = A::from(-1.0), mtwo = A::from(-2.0);
+    const T one = A::cst(1.0), mone = A::cst(-1.0), mtwo = A::cst(-2.0);
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         if (!on[k]) continue;
@@ -259,7 +259,7 @@ __device__ __forceinline__ void mf_elem_rows(const Geom& g, int e, int le, const
 template <int P, int EPB, class A, int MODE, bool PREF, bool FUSE = false>
 __device__ __forceinline__ void mf_elem_body(int bid, const Geom& g, const typename A::T* __restrict__ S,
                                              const typename A::T* __restrict__ aux,
-                                             const typename A::T* __restrict__ EG, const double* __restrict__ tau_edge,
+                                             const typename A::T* __restrict__ EG, const void* __restrict__ tau_v,
                                              const void* __restrict__ yv, MfVec<MODE>* __restrict__ hm,
                                              MfVec<MODE>* __restrict__ hp, double beta, PrecondBlocks Minv = {}) {
     using T = typename A::T;
@@ -302,13 +302,14 @@ __device__ __forceinline__ void mf_elem_body(int bid, const Geom& g, const typen
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         on[k] = on[k] && live;
-        tau[k] = A::from(0.0);
+        tau[k] = A::cst(0.0);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) yv_[k][c] = A::from(0.0);
+        for (int c = 0; c < 3; ++c) yv_[k][c] = A::cst(0.0);
         if (!on[k]) continue;
         const int r = edge_of_face(e, fc[k], g);
         ed[k] = r;
-        tau[k] = A::from(tau_edge[(size_t)r * P + bb[k]]);
+        if constexpr (FUSE) tau[k] = static_cast<const float*>(tau_v)[(size_t)r * P + bb[k]];   // FP32 copy
+        else tau[k] = A::from(static_cast<const double*>(tau_v)[(size_t)r * P + bb[k]]);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const size_t o = (size_t)r * NF + c * P + bb[k];
@@ -345,7 +346,7 @@ __device__ __forceinline__ void mf_elem_body(int bid, const Geom& g, const typen
 template <int P, int EPB, class A, int MODE, bool PREF, int MINB = 1, bool FUSE = false>
 __global__ void __launch_bounds__(EPB * P * P, MINB)
     mf_elem_kernel(Geom g, const typename A::T* __restrict__ S, const typename A::T* __restrict__ aux,
-                   const typename A::T* __restrict__ EG, const double* __restrict__ tau_edge,
+                   const typename A::T* __restrict__ EG, const void* __restrict__ tau_edge,
                    const void* __restrict__ yv, MfVec<MODE>* __restrict__ hm, MfVec<MODE>* __restrict__ hp,
                    double beta, PrecondBlocks Minv, const int* __restrict__ done) {
     if (done && *done) return;
@@ -487,7 +488,7 @@ int sum_grid(size_t n) {
 }
 
 template <int P, class A, int MODE, int TILE>
-void mf_elem_launch(const Geom& g, const void* S, const void* aux, const void* EG, const double* tau, const void* yv,
+void mf_elem_launch(const Geom& g, const void* S, const void* aux, const void* EG, const void* tau, const void* yv,
                     MfVec<MODE>* hm, MfVec<MODE>* hp, double beta, cudaStream_t s, const int* done,
                     const PrecondBlocks& Minv) {
     using T = typename A::T;
@@ -502,7 +503,7 @@ void mf_elem_launch(const Geom& g, const void* S, const void* aux, const void* E
 // the element pass with tile t (degrees 2..4: tiles 0..8 in the inner cycles, 0..5 in the
 // refinement residual; tile 0 elsewhere)
 template <int P, class A, int MODE>
-void mf_elem_tile(int t, const Geom& g, const void* S, const void* aux, const void* EG, const double* tau,
+void mf_elem_tile(int t, const Geom& g, const void* S, const void* aux, const void* EG, const void* tau,
                   const void* yv, MfVec<MODE>* hm, MfVec<MODE>* hp, double beta, cudaStream_t s, const int* done,
                   const PrecondBlocks& Minv) {
     if constexpr (MODE == kMfResidual && P >= 3 && P <= 5) {
@@ -550,7 +551,8 @@ cudaError_t mf_launch(const Geom& g, const MfOps& op, const void* S, const void*
             zero_f32_kernel<<<sum_grid(n), 256, 0, s>>>(reinterpret_cast<float*>(out), n, done);
             count_launches(1);
         }
-        mf_elem_tile<P, A, MODE>(op.tile, g, S, aux, EG, op.tau, x, out, nullptr, beta, s, done, op.Minv);
+        if (!op.tau32) return cudaErrorInvalidValue;   // the fused pass reads the FP32 copy of tau
+        mf_elem_tile<P, A, MODE>(op.tile, g, S, aux, EG, op.tau32, x, out, nullptr, beta, s, done, op.Minv);
         count_launches(1);
         return cudaGetLastError();
     }

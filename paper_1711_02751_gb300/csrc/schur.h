@@ -25,6 +25,8 @@ struct ArithF64 {
     __device__ __forceinline__ static double from(double v) { return v; }
     __device__ __forceinline__ static double to(double v) { return v; }
     __device__ __forceinline__ static double mul(double a, double b) { return a * b; }
+    // a small constant exact in FP32 (0, +-1, -2), at compile time
+    __host__ __device__ static constexpr double cst(double v) { return v; }
 };
 
 struct ArithF2 {
@@ -44,6 +46,7 @@ struct ArithF2 {
         return r;
     }
     __device__ __forceinline__ static double to(float2 v) { return f32_to_f64(v.x) + f32_to_f64(v.y); }
+    __host__ __device__ static constexpr float2 cst(double v) { return float2{(float)v, 0.f}; }
     // (a_hi + a_lo)(b_hi + b_lo): the exact a_hi b_hi (TwoProduct) plus the cross terms, renormalised
     __device__ __forceinline__ static float2 mul(float2 a, float2 b) {
         float p, e;
@@ -71,6 +74,7 @@ struct ArithF32 {
     __device__ __forceinline__ static float from(double v) { return f64_to_f32(v); }
     __device__ __forceinline__ static double to(float v) { return f32_to_f64(v); }
     __device__ __forceinline__ static float mul(float a, float b) { return __fmul_rn(a, b); }
+    __host__ __device__ static constexpr float cst(double v) { return (float)v; }
 };
 
 template <int P, int EPB, class A>
@@ -126,7 +130,7 @@ __device__ __forceinline__ void schur_solve_with(SchurSmem<P, EPB, A>& sm, const
     using T = typename A::T;
     constexpr int Np = P * P;
     const int i = n % P, j = n / P;
-    const T one = A::from(1.0);
+    const T one = A::cst(1.0);
     if (live) {
         const T* eg = EG + (size_t)g.by_el.div(e) * 2 * Np;
         sm.EG[le][0][n] = eg[n];
