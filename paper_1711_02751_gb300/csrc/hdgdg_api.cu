@@ -129,7 +129,7 @@ Plan make_plan(const hdgdg_config* c) {
         b += n_edges * (size_t)p.NF * p.NF * sizeof(__half) + n_edges * sizeof(float);
         b += (n_el * Np * Np + 4 * n_el * Np + 2 * B * Np) * sizeof(float);
         b += 3 * p.nt * d;   // M^{-1} x and the two halves of S y
-        b += n_edges * P * sizeof(float);   // tau_hat in FP32 (the fused inner pass)
+        b += n_edges * P * (sizeof(float) + d);   // tau_hat in FP32 and as FP32 pairs
     }
     b += 2 * (size_t)guess_order(c) * p.s * p.nt * d;         // previous stage solutions and products
     p.persistent = b;
@@ -1301,6 +1301,12 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
             TRY(dalloc(sim, &tau32, (size_t)g.n_edges * g.P));
             CU(launch_to_f32(sim->tau, tau32, (size_t)g.n_edges * g.P, sim->stream));
             sim->mf.tau32 = tau32;
+            double* tau2 = nullptr;   // FP32 pairs in place of a copy of tau
+            TRY(dalloc(sim, &tau2, (size_t)g.n_edges * g.P));
+            CU(cudaMemcpyAsync(tau2, sim->tau, (size_t)g.n_edges * g.P * sizeof(double), cudaMemcpyDeviceToDevice,
+                               sim->stream));
+            CU(launch_split_pairs_inplace(tau2, (size_t)g.n_edges * g.P, sim->stream));
+            sim->mf.tau2 = tau2;
             TRY(dalloc(sim, &hm, p.nt));
             TRY(dalloc(sim, &hp, p.nt));
             CU(launch_pair_hi(sim->Sphi, S32, nS, sim->stream));

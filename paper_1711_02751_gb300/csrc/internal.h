@@ -296,6 +296,7 @@ struct MfOps {
     PrecondBlocks Minv;              // block-Jacobi inverse [edge][col][row], FP16 with a scale per edge
     const double* tau = nullptr;     // tau_hat [edge][P]
     const float* tau32 = nullptr;    // the same rounded to FP32 (the inner cycles' fused pass)
+    const void* tau2 = nullptr;      // and as FP32 pairs (float2; the refinement residual)
     void* ybuf = nullptr;            // scratch: M^{-1} x (n_edges * 3P values of 8 bytes)
     void* hm = nullptr;              // scratch: the edges' minus-side halves of S y (8 bytes per value)
     void* hp = nullptr;              // scratch: their plus-side halves

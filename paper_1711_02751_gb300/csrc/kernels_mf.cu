@@ -256,7 +256,9 @@ __device__ __forceinline__ void mf_elem_rows(const Geom& g, int e, int le, const
 // The element pass (see above).  PLAIN: y is the input vector itself (TX), else M^{-1} x (A::T).
 // FUSE (inner mode): yv is x itself, y = M^{-1} x is formed per face in shared memory, and both
 // halves of each row are added into hm (the zeroed output; hp unused).
-template <int P, int EPB, class A, int MODE, bool PREF, bool FUSE = false>
+// TAUN: tau_v holds tau_hat already in the arithmetic's type (FP32 for the fused pass, FP32 pairs
+// for the refinement residual; converted once at setup), else in FP64.
+template <int P, int EPB, class A, int MODE, bool PREF, bool FUSE = false, bool TAUN = FUSE>
 __device__ __forceinline__ void mf_elem_body(int bid, const Geom& g, const typename A::T* __restrict__ S,
                                              const typename A::T* __restrict__ aux,
                                              const typename A::T* __restrict__ EG, const void* __restrict__ tau_v,
@@ -308,7 +310,7 @@ __device__ __forceinline__ void mf_elem_body(int bid, const Geom& g, const typen
         if (!on[k]) continue;
         const int r = edge_of_face(e, fc[k], g);
         ed[k] = r;
-        if constexpr (FUSE) tau[k] = static_cast<const float*>(tau_v)[(size_t)r * P + bb[k]];   // FP32 copy
+        if constexpr (TAUN) tau[k] = static_cast<const T*>(tau_v)[(size_t)r * P + bb[k]];
         else tau[k] = A::from(static_cast<const double*>(tau_v)[(size_t)r * P + bb[k]]);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -343,14 +345,14 @@ __device__ __forceinline__ void mf_elem_body(int bid, const Geom& g, const typen
     if (live) mf_elem_rows<P, EPB, A, MODE, FUSE>(g, e, le, nd, on, fc, bb, ed, yv_, tau, W, beta, hm, hp);
 }
 
-template <int P, int EPB, class A, int MODE, bool PREF, int MINB = 1, bool FUSE = false>
+template <int P, int EPB, class A, int MODE, bool PREF, int MINB = 1, bool FUSE = false, bool TAUN = FUSE>
 __global__ void __launch_bounds__(EPB * P * P, MINB)
     mf_elem_kernel(Geom g, const typename A::T* __restrict__ S, const typename A::T* __restrict__ aux,
                    const typename A::T* __restrict__ EG, const void* __restrict__ tau_edge,
                    const void* __restrict__ yv, MfVec<MODE>* __restrict__ hm, MfVec<MODE>* __restrict__ hp,
                    double beta, PrecondBlocks Minv, const int* __restrict__ done) {
     if (done && *done) return;
-    mf_elem_body<P, EPB, A, MODE, PREF, FUSE>(blockIdx.x, g, S, aux, EG, tau_edge, yv, hm, hp, beta, Minv);
+    mf_elem_body<P, EPB, A, MODE, PREF, FUSE, TAUN>(blockIdx.x, g, S, aux, EG, tau_edge, yv, hm, hp, beta, Minv);
 }
 
 // y = 0 (the fused product's output, when the caller has not zeroed it)
@@ -494,7 +496,8 @@ void mf_elem_launch(const Geom& g, const void* S, const void* aux, const void* E
     using T = typename A::T;
     constexpr int EPB = mf_epb_for<P>(mf_tile_threads(TILE));
     constexpr bool kFuse = MODE == kMfInner;
-    mf_elem_kernel<P, EPB, A, MODE, mf_tile_pref(TILE), mf_tile_minb(TILE), kFuse>
+    constexpr bool kTauN = MODE != kMfPlain;   // the inner and residual modes read their own copy of tau
+    mf_elem_kernel<P, EPB, A, MODE, mf_tile_pref(TILE), mf_tile_minb(TILE), kFuse, kTauN>
         <<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(g, static_cast<const T*>(S), static_cast<const T*>(aux),
                                                           static_cast<const T*>(EG), tau, yv, hm, hp, beta, Minv,
                                                           done);
@@ -569,8 +572,10 @@ cudaError_t mf_launch(const Geom& g, const MfOps& op, const void* S, const void*
     }
     TO* hm = static_cast<TO*>(op.hm);
     TO* hp = static_cast<TO*>(op.hp);
-    mf_elem_tile<P, A, MODE>(MODE == kMfResidual ? op.tile_res : 0, g, S, aux, EG, op.tau, yv, hm, hp, beta, s, done,
-                             op.Minv);
+    if (MODE == kMfResidual && !op.tau2) return cudaErrorInvalidValue;
+    mf_elem_tile<P, A, MODE>(MODE == kMfResidual ? op.tile_res : 0, g, S, aux, EG,
+                             MODE == kMfResidual ? op.tau2 : static_cast<const void*>(op.tau), yv, hm, hp, beta, s,
+                             done, op.Minv);
     const size_t n = (size_t)g.n_edges * NF;
     mf_sum_kernel<TO, MODE == kMfResidual><<<sum_grid(n), 256, 0, s>>>(n, hm, hp, rhs, out, done);
     count_launches(MODE != kMfPlain ? 3 : 2);
