@@ -344,6 +344,8 @@ struct hdgdg_sim {
     CycleGraph cycle_graph[4];   // [FP64 form, mixed form] x [timers off, on]
     std::vector<StepGraph> step_graphs;   // whole-step graphs (host_steps = 0, timers off)
     SolveCtl* sctl = nullptr;             // device-side control of the solve being replayed
+    DevHist* dhist = nullptr;             // each stage's guess history, as the step graph reads it
+    DevHist* hhist = nullptr;             // its pinned host copy, written before every replay
     StepStats* sstats = nullptr;          // counters of the replayed step
     cudaStream_t body_stream = nullptr;   // captures the restart-cycle bodies of the conditional nodes
     std::vector<TimerPair>* capture_sink = nullptr;   // timers of the graph being captured
@@ -807,27 +809,27 @@ cudaError_t solve_enqueue_graph(hdgdg_sim* sim, const double* g, double* qhat, i
     const int maxit = sim->cfg.krylov_maxit > 0 ? sim->cfg.krylov_maxit : 2000;
     const double inner_rel = kMixed ? 1e-6 : 0.0;
     const int order = guess_order(&sim->cfg);
-    const int avail = stage >= 0 ? std::min(order, sim->n_hist[stage]) : 0;
+    const bool history = stage >= 0 && order > 0;
     cudaError_t e = cudaSuccess;
-    if (avail > 0) {
-        GuessTerms gt{};
-        gt.nq = avail;
-        for (int j = 0; j < avail; ++j) gt.y[j] = sim->yhist[stage][j];
-        std::memcpy(gt.c, kGuessCoef, sizeof(kGuessCoef));
-        e = launch_guess_norms(n, g, gt, sim->red, dv_guess(sim), st, kMixed);
+    if (history) {   // the history's length and pointers come from the stage's device table
+        const DevHist* dh = sim->dhist + stage;
+        // ||g||^2 alone when the history is empty (the kernel returns at once otherwise), else the
+        // candidates' norms
+        e = launch_multidot(g, 0, 1, g, n, sim->red, dv_guess(sim), st, &dh->has_history);
+        if (e == cudaSuccess) e = launch_guess_norms_dev(n, g, dh, kGuessCoef, sim->red, dv_guess(sim), st, kMixed);
+        if (e == cudaSuccess)
+            e = launch_solve_begin_dev(dv_guess(sim), dh, rtol, inner_rel, maxit, sim->ctl, sim->sctl, sim->sstats,
+                                       dv_nrm(sim), st);
+        if (e == cudaSuccess) e = launch_guess_apply_dev(n, g, dh, kGuessCoef, sim->sctl, sim->xt, sim->w, st);
     } else {
         e = launch_multidot(g, 0, 1, g, n, sim->red, dv_guess(sim), st);
+        if (e == cudaSuccess)
+            e = launch_solve_begin(dv_guess(sim), 0, rtol, inner_rel, maxit, sim->ctl, sim->sctl, sim->sstats,
+                                   dv_nrm(sim), st);
+        GuessHistory hist{};
+        std::memcpy(hist.c, kGuessCoef, sizeof(kGuessCoef));
+        if (e == cudaSuccess) e = launch_guess_apply(n, g, hist, sim->sctl, sim->xt, sim->w, st);
     }
-    if (e == cudaSuccess)
-        e = launch_solve_begin(dv_guess(sim), avail, rtol, inner_rel, maxit, sim->ctl, sim->sctl, sim->sstats,
-                               dv_nrm(sim), st);
-    GuessHistory hist{};
-    for (int j = 0; j < avail; ++j) {
-        hist.x[j] = sim->xhist[stage][j];
-        hist.y[j] = sim->yhist[stage][j];
-    }
-    std::memcpy(hist.c, kGuessCoef, sizeof(kGuessCoef));
-    if (e == cudaSuccess) e = launch_guess_apply(n, g, hist, sim->sctl, sim->xt, sim->w, st);
     if (kMixed && e == cudaSuccess)   // the exact start norm of an extrapolated start
         e = launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_exact(sim), st);
     // restart cycles while the true residual is above the tolerance
@@ -871,16 +873,8 @@ cudaError_t solve_enqueue_graph(hdgdg_sim* sim, const double* g, double* qhat, i
         else if (kMixed && matrix_free(&sim->cfg)) e = launch_mf_back(sim->g, sim->mf.Minv, sim->xt, qhat, st);
         else e = launch_block_diag(sim->g, sim->Minv, sim->xt, qhat, st, sim->minv_pairs);
     }
-    if (e == cudaSuccess && stage >= 0 && order > 0) {   // x~ and S~ x~ = g - r into the slot that becomes newest
-        double* ox = sim->xhist[stage][order - 1];
-        double* oy = sim->yhist[stage][order - 1];
-        e = cudaMemcpyAsync(ox, sim->xt, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
-        CombineTerms r{};
-        r.n = 1;
-        r.X[0] = sim->w;
-        r.c[0] = -1.0;
-        if (e == cudaSuccess) e = launch_combine(n, g, r, oy, nullptr, st);
-    }
+    if (e == cudaSuccess && history)   // x~ and S~ x~ = g - r into the slot that becomes newest
+        e = launch_hist_store_dev(n, sim->xt, g, sim->w, sim->dhist + stage, st);
     return e;
 }
 
@@ -937,18 +931,28 @@ cudaError_t step_enqueue_graph(hdgdg_sim* sim, cudaStream_t st, StepGraph& sg) {
     return e;
 }
 
-std::vector<const void*> step_key(const hdgdg_sim* sim) {
-    std::vector<const void*> k{sim->q, sim->q_new};
+// The captured step depends on the state buffers only: the guess history is read through the
+// device table (DevHist) that one_step_graph writes before each replay.
+std::vector<const void*> step_key(const hdgdg_sim* sim) { return {sim->q, sim->q_new}; }
+
+// Each implicit stage's history table for the next replay: the host's rotated pointers, the
+// number of usable solutions and the slot the step writes.
+cudaError_t upload_history(hdgdg_sim* sim, cudaStream_t st) {
     const int order = guess_order(&sim->cfg);
     for (int i = 0; i < sim->s; ++i) {
-        if (sim->At[i][i] == 0.0) continue;
-        k.push_back(reinterpret_cast<const void*>((uintptr_t)std::min(order, sim->n_hist[i])));
+        DevHist& h = sim->hhist[i];
+        h = DevHist{};
+        if (sim->At[i][i] == 0.0 || order <= 0) continue;
         for (int j = 0; j < order; ++j) {
-            k.push_back(sim->xhist[i][j]);
-            k.push_back(sim->yhist[i][j]);
+            h.x[j] = sim->xhist[i][j];
+            h.y[j] = sim->yhist[i][j];
         }
+        h.xw = sim->xhist[i][order - 1];
+        h.yw = sim->yhist[i][order - 1];
+        h.avail = std::min(order, sim->n_hist[i]);
+        h.has_history = h.avail > 0 ? 1 : 0;
     }
-    return k;
+    return cudaMemcpyAsync(sim->dhist, sim->hhist, sim->s * sizeof(DevHist), cudaMemcpyHostToDevice, st);
 }
 
 void drop_step_graphs(hdgdg_sim* sim) {
@@ -995,6 +999,7 @@ hdgdg_status one_step_graph(hdgdg_sim* sim) {
         sim->step_graphs.push_back(std::move(fresh));
         sg = &sim->step_graphs.back();
     }
+    CU(upload_history(sim, st));
     CU(cudaGraphLaunch(sg->exec, st));
     CU(cudaStreamSynchronize(st));
     unsigned flag[4];
@@ -1230,6 +1235,8 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
     TRY(dalloc(sim, &sim->ctl, 1));
     TRY(dalloc(sim, &sim->sctl, 1));
     TRY(dalloc(sim, &sim->sstats, 1));
+    TRY(dalloc(sim, &sim->dhist, kMaxStages));
+    CU(cudaMallocHost(&sim->hhist, kMaxStages * sizeof(DevHist)));
     if (!c->host_steps) CU(cudaStreamCreateWithFlags(&sim->body_stream, cudaStreamNonBlocking));
     CU(cudaMallocHost(&sim->hbuf, (4 * (size_t)(p.m + 2) + 16) * sizeof(double)));
     for (int i = 0; i < p.s; ++i) {
@@ -1462,6 +1469,7 @@ void hdgdg_destroy(hdgdg_sim* sim) {
     for (cudaEvent_t e : sim->ev_pool) cudaEventDestroy(e);
     for (void* p : sim->allocs) cudaFree(p);
     if (sim->hbuf) cudaFreeHost(sim->hbuf);
+    if (sim->hhist) cudaFreeHost(sim->hhist);
     if (sim->own_stream && sim->stream) cudaStreamDestroy(sim->stream);
     delete sim;
 }
@@ -1866,6 +1874,8 @@ hdgdg_status ens_super(hdgdg_ensemble* E, const hdgdg_config* base, size_t n_tot
     TRY(dalloc(sim, &sim->ctl, 1));
     TRY(dalloc(sim, &sim->sctl, 1));
     TRY(dalloc(sim, &sim->sstats, 1));
+    TRY(dalloc(sim, &sim->dhist, kMaxStages));
+    CU(cudaMallocHost(&sim->hhist, kMaxStages * sizeof(DevHist)));
     CU(cudaMallocHost(&sim->hbuf, (4 * (size_t)(p.m + 2) + 16) * sizeof(double)));
     CU(cudaStreamCreateWithFlags(&sim->body_stream, cudaStreamNonBlocking));
     double *ybuf = nullptr, *hm = nullptr, *hp = nullptr;

@@ -480,10 +480,33 @@ struct GuessHistory {         // the stage's stored solutions x~ and products S~
     const double* y[6];
     double c[7][6];           // extrapolation coefficients of each order
 };
+// A stage's guess history as the replayed step graph reads it, from device memory: the host
+// rotates its pointers after every step and copies this table before the replay, so one captured
+// graph serves every rotation and history length.
+struct DevHist {
+    const double* x[6];   // stored solutions x~, newest first (the first `avail` are valid)
+    const double* y[6];   // their products S~ x~
+    double* xw;           // the slot this step's solution goes to (it becomes the newest)
+    double* yw;
+    int avail;            // candidates of the start (<= the extrapolation order)
+    int has_history;      // avail > 0 (gates the plain norm of g, read as a `done` flag)
+};
 cudaError_t launch_solve_begin(const double* cand, int avail, double rtol, double inner_rel, int maxit, GmresCtl* ctl,
                                SolveCtl* sc, StepStats* ss, double* nrm2, cudaStream_t s);
 cudaError_t launch_guess_apply(size_t n, const double* g, const GuessHistory& h, const SolveCtl* sc, double* xt,
                                double* w, cudaStream_t s);
+// The same two steps with the history's length and pointers read from dh (the step graph's form).
+cudaError_t launch_solve_begin_dev(const double* cand, const DevHist* dh, double rtol, double inner_rel, int maxit,
+                                   GmresCtl* ctl, SolveCtl* sc, StepStats* ss, double* nrm2, cudaStream_t s);
+cudaError_t launch_guess_apply_dev(size_t n, const double* g, const DevHist* dh, const double (*coef)[6],
+                                   const SolveCtl* sc, double* xt, double* w, cudaStream_t s);
+// out[0..avail] = ||g||^2 and the candidates' squared residual norms (launch_guess_norms), for
+// avail = dh->avail > 0; returns at once when there is no history.
+cudaError_t launch_guess_norms_dev(size_t n, const double* g, const DevHist* dh, const double (*coef)[6],
+                                   double* scratch, double* out, cudaStream_t s, bool f32x2);
+// dh->xw = xt, dh->yw = g - w (the solve's S~ x~ from its final true residual w)
+cudaError_t launch_hist_store_dev(size_t n, const double* xt, const double* g, const double* w, const DevHist* dh,
+                                  cudaStream_t s);
 cudaError_t launch_loop_begin(double* nrm2, const double* nrm_exact, int use_exact, SolveCtl* sc, StepStats* ss,
                               cudaGraphConditionalHandle loop, cudaStream_t s);
 cudaError_t launch_cycle_end(const double* nrm2, const GmresCtl* ctl, SolveCtl* sc, StepStats* ss, double stagnation,

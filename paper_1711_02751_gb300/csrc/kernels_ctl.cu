@@ -15,8 +15,9 @@ namespace {
 // Begin a solve: ||g||^2 = cand[0], the candidates' squared residual norms cand[1..avail];
 // chooses the start (zero or the extrapolation order with the smallest finite residual), sets the
 // absolute tolerance and the GMRES control block, and writes the start's squared residual norm.
-__global__ void solve_begin_kernel(const double* __restrict__ cand, int avail, double rtol, double inner_rel,
-                                   int maxit, GmresCtl* ctl, SolveCtl* sc, StepStats* ss, double* nrm2) {
+__device__ __forceinline__ void solve_begin_body(const double* __restrict__ cand, int avail, double rtol,
+                                                 double inner_rel, int maxit, GmresCtl* ctl, SolveCtl* sc,
+                                                 StepStats* ss, double* nrm2) {
     const double bn2 = cand[0];
     sc->active = 0;
     sc->guess = 0;
@@ -46,6 +47,18 @@ __global__ void solve_begin_kernel(const double* __restrict__ cand, int avail, d
     ctl->tol_abs = sc->tol;
     ss->last_guess = guess;
     *nrm2 = cand[guess];
+}
+
+__global__ void solve_begin_kernel(const double* __restrict__ cand, int avail, double rtol, double inner_rel,
+                                   int maxit, GmresCtl* ctl, SolveCtl* sc, StepStats* ss, double* nrm2) {
+    solve_begin_body(cand, avail, rtol, inner_rel, maxit, ctl, sc, ss, nrm2);
+}
+
+// the same with the number of candidates read from the step's history table
+__global__ void solve_begin_dev_kernel(const double* __restrict__ cand, const DevHist* __restrict__ dh, double rtol,
+                                       double inner_rel, int maxit, GmresCtl* ctl, SolveCtl* sc, StepStats* ss,
+                                       double* nrm2) {
+    solve_begin_body(cand, dh->avail, rtol, inner_rel, maxit, ctl, sc, ss, nrm2);
 }
 
 // x~ = x_{n-1} + sum_j (c_qj - [j = 0]) x_{n-1-j} and w = g - sum_j c_qj S~x_{n-1-j} for the chosen
@@ -97,8 +110,9 @@ __device__ __forceinline__ void guess_apply_order(size_t n, const double* __rest
     }
 }
 
-__global__ void guess_apply_kernel(size_t n, const double* __restrict__ g, GuessHistory h,
-                                   const SolveCtl* __restrict__ sc, double* __restrict__ xt, double* __restrict__ w) {
+__device__ __forceinline__ void guess_apply_body(size_t n, const double* __restrict__ g, const GuessHistory& h,
+                                                 const SolveCtl* __restrict__ sc, double* __restrict__ xt,
+                                                 double* __restrict__ w) {
     switch (sc->active ? sc->guess : 0) {
         case 1: return guess_apply_order<1>(n, g, h, xt, w);
         case 2: return guess_apply_order<2>(n, g, h, xt, w);
@@ -107,6 +121,45 @@ __global__ void guess_apply_kernel(size_t n, const double* __restrict__ g, Guess
         case 5: return guess_apply_order<5>(n, g, h, xt, w);
         case 6: return guess_apply_order<6>(n, g, h, xt, w);
         default: return guess_apply_order<0>(n, g, h, xt, w);
+    }
+}
+
+__global__ void guess_apply_kernel(size_t n, const double* __restrict__ g, GuessHistory h,
+                                   const SolveCtl* __restrict__ sc, double* __restrict__ xt, double* __restrict__ w) {
+    guess_apply_body(n, g, h, sc, xt, w);
+}
+
+struct GuessCoefTable {
+    double c[7][6];
+};
+
+// the same with the history's pointers read from the step's table
+__global__ void guess_apply_dev_kernel(size_t n, const double* __restrict__ g, const DevHist* __restrict__ dh,
+                                       GuessCoefTable cf, const SolveCtl* __restrict__ sc, double* __restrict__ xt,
+                                       double* __restrict__ w) {
+    GuessHistory h;
+    const int avail = dh->avail;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        h.x[j] = j < avail ? dh->x[j] : nullptr;
+        h.y[j] = j < avail ? dh->y[j] : nullptr;
+    }
+#pragma unroll
+    for (int q = 0; q < 7; ++q)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) h.c[q][j] = cf.c[q][j];
+    guess_apply_body(n, g, h, sc, xt, w);
+}
+
+// The solve's x~ and S~ x~ = g - w into the slot that becomes the newest.
+__global__ void hist_store_dev_kernel(size_t n, const double* __restrict__ xt, const double* __restrict__ g,
+                                      const double* __restrict__ w, const DevHist* __restrict__ dh) {
+    double* __restrict__ xw = dh->xw;
+    double* __restrict__ yw = dh->yw;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        xw[idx] = xt[idx];
+        yw[idx] = g[idx] - w[idx];
     }
 }
 
@@ -176,6 +229,30 @@ cudaError_t launch_solve_begin(const double* cand, int avail, double rtol, doubl
 cudaError_t launch_guess_apply(size_t n, const double* g, const GuessHistory& h, const SolveCtl* sc, double* xt,
                                double* w, cudaStream_t s) {
     guess_apply_kernel<<<grid_of(n), 256, 0, s>>>(n, g, h, sc, xt, w);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_begin_dev(const double* cand, const DevHist* dh, double rtol, double inner_rel, int maxit,
+                                   GmresCtl* ctl, SolveCtl* sc, StepStats* ss, double* nrm2, cudaStream_t s) {
+    solve_begin_dev_kernel<<<1, 1, 0, s>>>(cand, dh, rtol, inner_rel, maxit, ctl, sc, ss, nrm2);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_guess_apply_dev(size_t n, const double* g, const DevHist* dh, const double (*coef)[6],
+                                   const SolveCtl* sc, double* xt, double* w, cudaStream_t s) {
+    GuessCoefTable cf;
+    for (int q = 0; q < 7; ++q)
+        for (int j = 0; j < 6; ++j) cf.c[q][j] = coef[q][j];
+    guess_apply_dev_kernel<<<grid_of(n), 256, 0, s>>>(n, g, dh, cf, sc, xt, w);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hist_store_dev(size_t n, const double* xt, const double* g, const double* w, const DevHist* dh,
+                                  cudaStream_t s) {
+    hist_store_dev_kernel<<<grid_of(n), 256, 0, s>>>(n, xt, g, w, dh);
     count_launches(1);
     return cudaGetLastError();
 }

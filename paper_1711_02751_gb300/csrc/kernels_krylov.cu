@@ -290,9 +290,8 @@ axpy_scale_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict_
 // stored products (no matrix product): out[0] = ||g||^2, out[q] = ||g - sum_j c[q][j] y[j]||^2.
 // NQT = the number of stored products (one instance each, the loops bounded by constants).
 template <int NQT>
-__global__ void __launch_bounds__(kDotThreads)
-guess_norms_kernel(size_t n, const double* __restrict__ g, GuessTerms t, double* __restrict__ scratch,
-                   double* __restrict__ out) {
+__device__ __forceinline__ void guess_norms_body(size_t n, const double* __restrict__ g, const GuessTerms& t,
+                                                 double* __restrict__ scratch, double* __restrict__ out) {
     constexpr int NQ = 7;
     unsigned* counter = reinterpret_cast<unsigned*>(scratch);
     double* partial = scratch + 1;
@@ -343,9 +342,8 @@ guess_norms_kernel(size_t n, const double* __restrict__ g, GuessTerms t, double*
 // relative accuracy; the candidates and their squares then run in plain FP32, and the sums across
 // threads in FP64.
 template <int NQT>
-__global__ void __launch_bounds__(kDotThreads)
-guess_norms_x2_kernel(size_t n, const double* __restrict__ g, GuessTerms t, double* __restrict__ scratch,
-                      double* __restrict__ out) {
+__device__ __forceinline__ void guess_norms_x2_body(size_t n, const double* __restrict__ g, const GuessTerms& t,
+                                                    double* __restrict__ scratch, double* __restrict__ out) {
     constexpr int NQ = 7;
     unsigned* counter = reinterpret_cast<unsigned*>(scratch);
     double* partial = scratch + 1;
@@ -394,6 +392,52 @@ guess_norms_x2_kernel(size_t n, const double* __restrict__ g, GuessTerms t, doub
     if (last_block_arrives(counter)) {
         reduce_partials(partial, gridDim.x, NQ, 0, NQT + 1, out);
         if (threadIdx.x == 0) *counter = 0u;
+    }
+}
+
+template <int NQT>
+__global__ void __launch_bounds__(kDotThreads)
+guess_norms_kernel(size_t n, const double* __restrict__ g, GuessTerms t, double* __restrict__ scratch,
+                   double* __restrict__ out) {
+    guess_norms_body<NQT>(n, g, t, scratch, out);
+}
+
+template <int NQT>
+__global__ void __launch_bounds__(kDotThreads)
+guess_norms_x2_kernel(size_t n, const double* __restrict__ g, GuessTerms t, double* __restrict__ scratch,
+                      double* __restrict__ out) {
+    guess_norms_x2_body<NQT>(n, g, t, scratch, out);
+}
+
+struct GuessCoef {
+    double c[7][6];
+};
+
+// The step graph's form: the history's length and pointers from device memory (DevHist); the
+// same sums as the kernels above for that length, nothing when there is no history.
+template <bool X2>
+__global__ void __launch_bounds__(kDotThreads)
+guess_norms_dev_kernel(size_t n, const double* __restrict__ g, const DevHist* __restrict__ dh, GuessCoef cf,
+                       double* __restrict__ scratch, double* __restrict__ out) {
+    const int avail = dh->avail;
+    if (avail <= 0 || avail > 6) return;
+    GuessTerms t;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) t.y[j] = j < avail ? dh->y[j] : nullptr;
+#pragma unroll
+    for (int q = 0; q < 7; ++q)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) t.c[q][j] = cf.c[q][j];
+    t.nq = avail;
+    switch (avail) {
+#define CASE(Q)                                                   \
+    case Q:                                                       \
+        if constexpr (X2) guess_norms_x2_body<Q>(n, g, t, scratch, out); \
+        else guess_norms_body<Q>(n, g, t, scratch, out);          \
+        break;
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6)
+#undef CASE
+        default: break;
     }
 }
 
@@ -623,6 +667,17 @@ cudaError_t launch_guess_norms(size_t n, const double* g, const GuessTerms& t, d
 #undef CASE
         default: return cudaErrorInvalidValue;
     }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_guess_norms_dev(size_t n, const double* g, const DevHist* dh, const double (*coef)[6],
+                                   double* scratch, double* out, cudaStream_t s, bool f32x2) {
+    GuessCoef cf;
+    for (int q = 0; q < 7; ++q)
+        for (int j = 0; j < 6; ++j) cf.c[q][j] = coef[q][j];
+    if (f32x2) guess_norms_dev_kernel<true><<<kDotBlocks, kDotThreads, 0, s>>>(n, g, dh, cf, scratch, out);
+    else guess_norms_dev_kernel<false><<<kDotBlocks, kDotThreads, 0, s>>>(n, g, dh, cf, scratch, out);
     count_launches(1);
     return cudaGetLastError();
 }
