@@ -1397,18 +1397,37 @@ hdgdg_status upload3(hdgdg_sim* sim, double* dst, const double* src, size_t coun
     return HDGDG_OK;
 }
 
+// The device's address of a pinned host buffer (page-locked, mapped: the GPU reads and writes it
+// directly over the host link), or nullptr for other host memory.
+const void* device_view(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // User (h, hu, hv) on the host -> state q = (phi_eta, U, V) in dst; *ok false when a value is
-// not finite or the depth is not positive.
+// not finite or the depth is not positive.  Pinned host buffers are read by the conversion kernel
+// itself; other host memory is first copied to the device.
 hdgdg_status load_user_state(hdgdg_sim* sim, const double* h, const double* hu, const double* hv, double* dst,
                              bool* ok) {
     const size_t n = sim->plan.n;
-    double* stg = sim->NLs[0];
-    TRY(upload3(sim, stg, h, n));
-    TRY(upload3(sim, stg + n, hu, n));
-    TRY(upload3(sim, stg + 2 * n, hv, n));
+    const double* dh = static_cast<const double*>(device_view(h));
+    const double* dhu = static_cast<const double*>(device_view(hu));
+    const double* dhv = static_cast<const double*>(device_view(hv));
+    if (!dh || !dhu || !dhv) {
+        double* stg = sim->NLs[0];
+        TRY(upload3(sim, stg, h, n));
+        TRY(upload3(sim, stg + n, hu, n));
+        TRY(upload3(sim, stg + 2 * n, hv, n));
+        dh = stg;
+        dhu = stg + n;
+        dhv = stg + 2 * n;
+    }
     CU(cudaMemsetAsync(sim->flags, 0, sizeof(unsigned), sim->stream));
-    CU(launch_user_to_state(sim->g, stg, stg + n, stg + 2 * n, sim->phiB, sim->cfg.g, dst, sim->flags,
-                            sim->stream));
+    CU(launch_user_to_state(sim->g, dh, dhu, dhv, sim->phiB, sim->cfg.g, dst, sim->flags, sim->stream));
     CU(cudaMemcpyAsync(sim->hbuf, sim->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, sim->stream));
     TRY(sync(sim));
     unsigned bad = 0;
@@ -1560,6 +1579,13 @@ hdgdg_status hdgdg_get_state(hdgdg_sim* sim, double* h, double* hu, double* hv) 
     if (!sim || !h || !hu || !hv) return fail(sim, HDGDG_EINVAL, "NULL argument to get_state");
     if (!sim->have_state) return fail(sim, HDGDG_ESTATE, "get_state before set_state");
     const size_t n = sim->plan.n;
+    double* dh = static_cast<double*>(const_cast<void*>(device_view(h)));
+    double* dhu = static_cast<double*>(const_cast<void*>(device_view(hu)));
+    double* dhv = static_cast<double*>(const_cast<void*>(device_view(hv)));
+    if (dh && dhu && dhv) {   // pinned: the conversion kernel writes the caller's buffers
+        CU(launch_state_to_user(sim->g, sim->q, sim->phiB, sim->cfg.g, dh, dhu, dhv, sim->stream));
+        return sync(sim);
+    }
     double* stg = sim->NLs[0];
     CU(launch_state_to_user(sim->g, sim->q, sim->phiB, sim->cfg.g, stg, stg + n, stg + 2 * n, sim->stream));
     CU(cudaMemcpyAsync(h, stg, n * sizeof(double), cudaMemcpyDeviceToHost, sim->stream));
