@@ -354,27 +354,38 @@ __device__ __forceinline__ void guess_norms_x2_body(size_t n, const double* __re
     float acc[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) acc[q] = 0.f;
-    for (size_t idx = blockIdx.x * (size_t)kDotThreads + threadIdx.x; idx < n;
-         idx += (size_t)gridDim.x * kDotThreads) {
-        const double gv = g[idx];   // every load first
-        double yv[6];
+    // two entries a grid apart per pass, every load of both issued first; each entry is added
+    // to the thread's sums in the order of the one-entry loop
+    const size_t stride = (size_t)gridDim.x * kDotThreads;
+    for (size_t i0 = blockIdx.x * (size_t)kDotThreads + threadIdx.x; i0 < n; i0 += 2 * stride) {
+        double gv[2], yv[2][6];
 #pragma unroll
-        for (int j = 0; j < 6; ++j) yv[j] = j < NQT ? t.y[j][idx] : 0.0;
-        const float gh = f64_to_f32(gv);
-        const float e = f64_to_f32(gv - yv[0]);   // g - y_0
-        float d[6];                                // y_0 - y_j
-        d[0] = 0.f;
+        for (int u = 0; u < 2; ++u) {
+            const size_t idx = i0 + u * stride;
+            const bool on = idx < n;
+            gv[u] = on ? g[idx] : 0.0;
 #pragma unroll
-        for (int j = 1; j < 6; ++j) d[j] = j < NQT ? f64_to_f32(yv[0] - yv[j]) : 0.f;
-        acc[0] = __fmaf_rn(gh, gh, acc[0]);
+            for (int j = 0; j < 6; ++j) yv[u][j] = (j < NQT && on) ? t.y[j][idx] : 0.0;
+        }
 #pragma unroll
-        for (int q = 1; q < NQ; ++q) {
-            if (q > NQT) break;
-            float r = e;
+        for (int u = 0; u < 2; ++u) {
+            if (i0 + u * stride >= n) continue;
+            const float gh = f64_to_f32(gv[u]);
+            const float e = f64_to_f32(gv[u] - yv[u][0]);   // g - y_0
+            float d[6];                                      // y_0 - y_j
+            d[0] = 0.f;
 #pragma unroll
-            for (int j = 1; j < 6; ++j)
-                if (j < q) r = __fmaf_rn(cf[q][j], d[j], r);
-            acc[q] = __fmaf_rn(r, r, acc[q]);
+            for (int j = 1; j < 6; ++j) d[j] = j < NQT ? f64_to_f32(yv[u][0] - yv[u][j]) : 0.f;
+            acc[0] = __fmaf_rn(gh, gh, acc[0]);
+#pragma unroll
+            for (int q = 1; q < NQ; ++q) {
+                if (q > NQT) break;
+                float r = e;
+#pragma unroll
+                for (int j = 1; j < 6; ++j)
+                    if (j < q) r = __fmaf_rn(cf[q][j], d[j], r);
+                acc[q] = __fmaf_rn(r, r, acc[q]);
+            }
         }
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
