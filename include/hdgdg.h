@@ -183,6 +183,13 @@ typedef struct {
                             The residual is a nonlinear flux evaluation with P x P derivative
                             applications (P = k + 1 <= 5), not a dense contraction, so it runs on the
                             CUDA cores in every variant. */
+    int krylov_guess_ls; /* 1 (HDGDG_MIXED only, krylov_guess >= 0): start each trace solve from the
+                            least-squares projection on the affine span of the stored solutions --
+                            the x_0 = sum_j alpha_j x_{n-j} (sum alpha = 1) whose residual
+                            ||g - sum_j alpha_j S x_{n-j}|| is smallest, from one pass over g and
+                            the stored products and a small solve -- or from zero when that is
+                            smaller; every polynomial extrapolation of the same solutions is one
+                            candidate of the projection.  0: the polynomial candidates (default). */
 } hdgdg_config;
 
 /* HDGDG_VORTEX: the exact-solution boundary conditions of the paper's moving-vortex test

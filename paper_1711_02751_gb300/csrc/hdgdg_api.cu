@@ -56,6 +56,7 @@ bool valid(const hdgdg_config* c) {
            (c->krylov_ortho == 0 || c->krylov_ortho == 1) && (c->residual_f32x2 == 0 || c->residual_f32x2 == 1) &&
            (c->local_dense == 0 || c->local_dense == 1) && (c->trace_operator == 0 || c->trace_operator == 1) &&
            (c->host_steps == 0 || c->host_steps == 1) &&
+           (c->krylov_guess_ls == 0 || (c->krylov_guess_ls == 1 && c->precision == HDGDG_MIXED && c->krylov_guess >= 0)) &&
            (c->dg_precision == 0 || (c->dg_precision == 1 && c->precision == HDGDG_MIXED && c->degree_k <= 4)) &&
            (c->trace_operator == 0 ||
             (c->precision == HDGDG_MIXED && c->local_precision == HDGDG_LOCAL_F32X2 && !c->local_dense &&
@@ -346,6 +347,7 @@ struct hdgdg_sim {
     SolveCtl* sctl = nullptr;             // device-side control of the solve being replayed
     DevHist* dhist = nullptr;             // each stage's guess history, as the step graph reads it
     DevHist* hhist = nullptr;             // its pinned host copy, written before every replay
+    double* dls = nullptr;                // the least-squares start's sums, choice and coefficients
     StepStats* sstats = nullptr;          // counters of the replayed step
     cudaStream_t body_stream = nullptr;   // captures the restart-cycle bodies of the conditional nodes
     std::vector<TimerPair>* capture_sink = nullptr;   // timers of the graph being captured
@@ -623,7 +625,23 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
     const auto& coef = kGuessCoef;
     const int avail = stage >= 0 ? std::min(guess_order(&sim->cfg), sim->n_hist[stage]) : 0;
     double cand[7] = {0, 0, 0, 0, 0, 0, 0};
-    if (avail > 0) {
+    const bool ls = kMixed && sim->cfg.krylov_guess_ls && avail > 0;   // the least-squares start
+    double alpha[6] = {0, 0, 0, 0, 0, 0};
+    if (ls) {
+        GuessTerms gt{};
+        gt.nq = avail;
+        for (int j = 0; j < avail; ++j) gt.y[j] = sim->yhist[stage][j];
+        {
+            TimedGroup tg(sim, HDGDG_KT_GUESS);
+            CU(launch_guess_gram(n, g, gt, sim->red, sim->dls, st));
+            CU(launch_ls_solve(sim->dls, avail, st));
+            CU(cudaMemcpyAsync(sim->hbuf, sim->dls + 32, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        }
+        TRY(sync(sim));
+        cand[0] = sim->hbuf[0];
+        cand[1] = sim->hbuf[1];
+        std::memcpy(alpha, sim->hbuf + 2, sizeof(alpha));
+    } else if (avail > 0) {
         GuessTerms gt{};
         gt.nq = avail;
         for (int j = 0; j < avail; ++j) gt.y[j] = sim->yhist[stage][j];
@@ -647,7 +665,7 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
     }
     const double bnorm = std::sqrt(bn2), tol = rtol * bnorm;
     int guess = 0;
-    for (int q = 1; q <= avail; ++q)
+    for (int q = 1; q <= (ls ? 1 : avail); ++q)
         if (std::isfinite(cand[q]) && cand[q] < cand[guess]) guess = q;
     sim->stats.last_guess_order = guess;
     const double rnorm0 = std::sqrt(cand[guess]);
@@ -658,7 +676,23 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
             CU(cudaMemsetAsync(sim->xt, 0, n * sizeof(double), st));
             CU(cudaMemcpyAsync(sim->w, g, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
             if (avail > 0)   // ||g||^2 for the cycle's first basis vector (norm2_to_host left it otherwise)
-                CU(cudaMemcpyAsync(dv_nrm(sim), dv_guess(sim), sizeof(double), cudaMemcpyDeviceToDevice, st));
+                CU(cudaMemcpyAsync(dv_nrm(sim), ls ? sim->dls + 32 : dv_guess(sim), sizeof(double),
+                                   cudaMemcpyDeviceToDevice, st));
+        } else if (ls) {
+            // x0 = sum_j alpha_j x_{n-j} and r0 = g - sum_j alpha_j S~ x~_{n-j}, the graph's sums
+            CombineTerms t{};
+            for (int j = 0; j < avail; ++j) {
+                t.X[t.n] = sim->xhist[stage][j];
+                t.c[t.n++] = alpha[j] - (j == 0 ? 1.0 : 0.0);
+            }
+            CU(launch_combine(n, sim->xhist[stage][0], t, sim->xt, nullptr, st));
+            CombineTerms r{};
+            for (int j = 0; j < avail; ++j) {
+                r.X[r.n] = sim->yhist[stage][j];
+                r.c[r.n++] = -alpha[j];
+            }
+            CU(launch_combine(n, g, r, sim->w, nullptr, st));
+            CU(launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st));   // the exact start norm
         } else {
             // x0 = sum_j c_j x_{n-j}: the extrapolation polynomial through the last `guess` solutions
             CombineTerms t{};
@@ -811,7 +845,14 @@ cudaError_t solve_enqueue_graph(hdgdg_sim* sim, const double* g, double* qhat, i
     const int order = guess_order(&sim->cfg);
     const bool history = stage >= 0 && order > 0;
     cudaError_t e = cudaSuccess;
-    if (history) {   // the history's length and pointers come from the stage's device table
+    if (history && kMixed && sim->cfg.krylov_guess_ls) {   // the least-squares start, from the device table
+        const DevHist* dh = sim->dhist + stage;
+        e = launch_multidot(g, 0, 1, g, n, sim->red, sim->dls + 32, st, &dh->has_history);
+        if (e == cudaSuccess) e = launch_guess_gram_dev(n, g, dh, sim->red, sim->dls, st);
+        if (e == cudaSuccess)
+            e = launch_ls_start_dev(n, g, dh, sim->dls, rtol, inner_rel, maxit, sim->ctl, sim->sctl, sim->sstats,
+                                    dv_nrm(sim), sim->xt, sim->w, st);
+    } else if (history) {   // the history's length and pointers come from the stage's device table
         const DevHist* dh = sim->dhist + stage;
         // ||g||^2 alone when the history is empty (the kernel returns at once otherwise), else the
         // candidates' norms
@@ -1237,6 +1278,7 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
     TRY(dalloc(sim, &sim->sstats, 1));
     TRY(dalloc(sim, &sim->dhist, kMaxStages));
     CU(cudaMallocHost(&sim->hhist, kMaxStages * sizeof(DevHist)));
+    TRY(dalloc(sim, &sim->dls, kLsSlots));
     if (!c->host_steps) CU(cudaStreamCreateWithFlags(&sim->body_stream, cudaStreamNonBlocking));
     CU(cudaMallocHost(&sim->hbuf, (4 * (size_t)(p.m + 2) + 16) * sizeof(double)));
     for (int i = 0; i < p.s; ++i) {
@@ -1902,6 +1944,7 @@ hdgdg_status ens_super(hdgdg_ensemble* E, const hdgdg_config* base, size_t n_tot
     TRY(dalloc(sim, &sim->sstats, 1));
     TRY(dalloc(sim, &sim->dhist, kMaxStages));
     CU(cudaMallocHost(&sim->hhist, kMaxStages * sizeof(DevHist)));
+    TRY(dalloc(sim, &sim->dls, kLsSlots));
     CU(cudaMallocHost(&sim->hbuf, (4 * (size_t)(p.m + 2) + 16) * sizeof(double)));
     CU(cudaStreamCreateWithFlags(&sim->body_stream, cudaStreamNonBlocking));
     double *ybuf = nullptr, *hm = nullptr, *hp = nullptr;

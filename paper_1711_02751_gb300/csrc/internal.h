@@ -504,6 +504,19 @@ cudaError_t launch_guess_apply_dev(size_t n, const double* g, const DevHist* dh,
 // avail = dh->avail > 0; returns at once when there is no history.
 cudaError_t launch_guess_norms_dev(size_t n, const double* g, const DevHist* dh, const double (*coef)[6],
                                    double* scratch, double* out, cudaStream_t s, bool f32x2);
+// The least-squares start (krylov_guess_ls, mixed form): the Gram sums of the stored products'
+// differences into ls[0..31] (launch_guess_gram: t.nq stored products; _dev: from dh), the
+// small solve into ls[32..39] (zero start's and the projection's squared residuals, the affine
+// coefficients alpha), and for the step graph the choice and its application.
+cudaError_t launch_guess_gram(size_t n, const double* g, const GuessTerms& t, double* scratch, double* out,
+                              cudaStream_t s);
+cudaError_t launch_guess_gram_dev(size_t n, const double* g, const DevHist* dh, double* scratch, double* out,
+                                  cudaStream_t s);
+cudaError_t launch_ls_solve(double* ls, int avail, cudaStream_t s);
+cudaError_t launch_ls_start_dev(size_t n, const double* g, const DevHist* dh, double* ls, double rtol,
+                                double inner_rel, int maxit, GmresCtl* ctl, SolveCtl* sc, StepStats* ss, double* nrm2,
+                                double* xt, double* w, cudaStream_t s);
+constexpr int kLsSlots = 40;
 // dh->xw = xt, dh->yw = g - w (the solve's S~ x~ from its final true residual w)
 cudaError_t launch_hist_store_dev(size_t n, const double* xt, const double* g, const double* w, const DevHist* dh,
                                   cudaStream_t s);

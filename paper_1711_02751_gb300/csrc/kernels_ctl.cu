@@ -151,6 +151,143 @@ __global__ void guess_apply_dev_kernel(size_t n, const double* __restrict__ g, c
     guess_apply_body(n, g, h, sc, xt, w);
 }
 
+// The least-squares start (krylov_guess_ls; see guess_gram_body): from the sums in ls[0..31],
+// gamma with G gamma = -b, solved on the unit-diagonal scaling of G (a difference whose norm is
+// zero is left out) with 1e-6 added to that diagonal -- the sums carry FP32 rounding, and only
+// directions closer than that to dependent are damped -- by Cholesky in FP64; the candidate's
+// squared residual ||e||^2 + 2 gamma.b + gamma.G gamma; and the coefficients on the stored
+// solutions, x0 = sum_j alpha_j x_{n-1-j}, alpha_j = [j = 0] - sum_{p >= max(j,1)} gamma_p (-1)^j C(p, j).
+// Writes ls[32] = ||g||^2 (with avail > 0; the plain norm of g is already there otherwise),
+// ls[33] = the candidate's squared residual, ls[34..39] = alpha.
+__device__ __forceinline__ void ls_solve_body(double* ls, int avail) {
+    if (avail <= 0) return;
+    const double* sg = ls;
+    const int D = avail - 1;
+    double gam[5] = {0, 0, 0, 0, 0};
+    double r2 = sg[1];
+    if (D > 0) {
+        double G[5][5], L[5][5], b[5], sc[5];
+        bool use[5];
+        for (int i = 0; i < D; ++i) {
+            b[i] = sg[2 + i];
+            for (int j = i; j < D; ++j) G[i][j] = G[j][i] = sg[7 + 5 * i + j];
+        }
+        for (int i = 0; i < D; ++i) {
+            use[i] = isfinite(G[i][i]) && G[i][i] > 0.0;
+            sc[i] = use[i] ? 1.0 / sqrt(G[i][i]) : 0.0;
+        }
+        bool ok = true;
+        for (int i = 0; i < D && ok; ++i) {   // Cholesky of the scaled G + 1e-6 I (dropped rows: identity)
+            for (int j = 0; j <= i; ++j) {
+                double v = (use[i] && use[j]) ? G[i][j] * sc[i] * sc[j] : (i == j ? 1.0 : 0.0);
+                if (i == j && use[i]) v += 1e-6;
+                for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+                if (i == j) {
+                    if (!(v > 0.0)) ok = false;
+                    else L[i][i] = sqrt(v);
+                } else {
+                    L[i][j] = v / L[j][j];
+                }
+            }
+        }
+        if (ok) {
+            double z[5], t[5];
+            for (int i = 0; i < D; ++i) {   // L z = -(scaled b)
+                double v = use[i] ? -b[i] * sc[i] : 0.0;
+                for (int k = 0; k < i; ++k) v -= L[i][k] * z[k];
+                z[i] = v / L[i][i];
+            }
+            for (int i = D - 1; i >= 0; --i) {   // L^T t = z
+                double v = z[i];
+                for (int k = i + 1; k < D; ++k) v -= L[k][i] * t[k];
+                t[i] = v / L[i][i];
+            }
+            for (int i = 0; i < D; ++i) gam[i] = use[i] ? t[i] * sc[i] : 0.0;
+            double gb = 0.0, ggg = 0.0;
+            for (int i = 0; i < D; ++i) {
+                gb += gam[i] * b[i];
+                double gi = 0.0;
+                for (int j = 0; j < D; ++j) gi += G[i][j] * gam[j];
+                ggg += gam[i] * gi;
+            }
+            r2 = sg[1] + 2.0 * gb + ggg;
+            if (r2 < 0.0) r2 = 0.0;
+        } else {
+            for (int i = 0; i < D; ++i) gam[i] = 0.0;
+        }
+    }
+    double* alpha = ls + 34;
+    const double binom[6][6] = {{1, 0, 0, 0, 0, 0},  {1, 1, 0, 0, 0, 0},  {1, 2, 1, 0, 0, 0},
+                                {1, 3, 3, 1, 0, 0},  {1, 4, 6, 4, 1, 0},  {1, 5, 10, 10, 5, 1}};
+    for (int j = 0; j < 6; ++j) {
+        double a = j == 0 ? 1.0 : 0.0;
+        for (int p = j > 1 ? j : 1; p <= D; ++p) a -= gam[p - 1] * ((j & 1) ? -binom[p][j] : binom[p][j]);
+        alpha[j] = j <= D ? a : 0.0;
+    }
+    ls[32] = sg[0];
+    ls[33] = isfinite(r2) ? r2 : INFINITY;
+}
+
+__global__ void ls_solve_kernel(double* ls, int avail) { ls_solve_body(ls, avail); }
+
+__global__ void ls_solve_dev_kernel(double* ls, const DevHist* __restrict__ dh) { ls_solve_body(ls, dh->avail); }
+
+// the least-squares start's choice: solve_begin over ls[32] (zero start) and ls[33] (the projection)
+__global__ void solve_begin_ls_dev_kernel(const double* __restrict__ ls, const DevHist* __restrict__ dh,
+                                          double rtol, double inner_rel, int maxit, GmresCtl* ctl, SolveCtl* sc,
+                                          StepStats* ss, double* nrm2) {
+    solve_begin_body(ls + 32, dh->avail > 0 ? 1 : 0, rtol, inner_rel, maxit, ctl, sc, ss, nrm2);
+}
+
+// x~ = x_0 + sum_j (alpha_j - [j = 0]) x_j and w = g - sum_j alpha_j y_j over the Q stored solutions
+template <int Q>
+__device__ __forceinline__ void apply_alpha(size_t n, const double* __restrict__ g, const DevHist& h,
+                                            const double* __restrict__ alpha, double* __restrict__ xt,
+                                            double* __restrict__ w) {
+    double a[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) a[j] = alpha[j];
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        double xv[Q], yv[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            xv[j] = h.x[j][idx];
+            yv[j] = h.y[j][idx];
+        }
+        double ax = xv[0];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) ax += (a[j] - (j == 0 ? 1.0 : 0.0)) * xv[j];
+        double aw = g[idx];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) aw += (-a[j]) * yv[j];
+        xt[idx] = ax;
+        w[idx] = aw;
+    }
+}
+
+__global__ void guess_apply_ls_dev_kernel(size_t n, const double* __restrict__ g, const DevHist* __restrict__ dh,
+                                          const double* __restrict__ ls, const SolveCtl* __restrict__ sc,
+                                          double* __restrict__ xt, double* __restrict__ w) {
+    const int q = sc->active && sc->guess == 1 ? dh->avail : 0;
+    DevHist h = *dh;
+    const double* alpha = ls + 34;
+    switch (q) {
+        case 1: return apply_alpha<1>(n, g, h, alpha, xt, w);
+        case 2: return apply_alpha<2>(n, g, h, alpha, xt, w);
+        case 3: return apply_alpha<3>(n, g, h, alpha, xt, w);
+        case 4: return apply_alpha<4>(n, g, h, alpha, xt, w);
+        case 5: return apply_alpha<5>(n, g, h, alpha, xt, w);
+        case 6: return apply_alpha<6>(n, g, h, alpha, xt, w);
+        default:
+            for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
+                 idx += (size_t)gridDim.x * blockDim.x) {
+                xt[idx] = 0.0;
+                w[idx] = g[idx];
+            }
+    }
+}
+
 // The solve's x~ and S~ x~ = g - w into the slot that becomes the newest.
 __global__ void hist_store_dev_kernel(size_t n, const double* __restrict__ xt, const double* __restrict__ g,
                                       const double* __restrict__ w, const DevHist* __restrict__ dh) {
@@ -247,6 +384,22 @@ cudaError_t launch_guess_apply_dev(size_t n, const double* g, const DevHist* dh,
         for (int j = 0; j < 6; ++j) cf.c[q][j] = coef[q][j];
     guess_apply_dev_kernel<<<grid_of(n), 256, 0, s>>>(n, g, dh, cf, sc, xt, w);
     count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ls_solve(double* ls, int avail, cudaStream_t s) {
+    ls_solve_kernel<<<1, 1, 0, s>>>(ls, avail);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ls_start_dev(size_t n, const double* g, const DevHist* dh, double* ls, double rtol,
+                                double inner_rel, int maxit, GmresCtl* ctl, SolveCtl* sc, StepStats* ss, double* nrm2,
+                                double* xt, double* w, cudaStream_t s) {
+    ls_solve_dev_kernel<<<1, 1, 0, s>>>(ls, dh);
+    solve_begin_ls_dev_kernel<<<1, 1, 0, s>>>(ls, dh, rtol, inner_rel, maxit, ctl, sc, ss, nrm2);
+    guess_apply_ls_dev_kernel<<<grid_of(n), 256, 0, s>>>(n, g, dh, ls, sc, xt, w);
+    count_launches(3);
     return cudaGetLastError();
 }
 

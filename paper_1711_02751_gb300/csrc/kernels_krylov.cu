@@ -420,6 +420,128 @@ guess_norms_x2_kernel(size_t n, const double* __restrict__ g, GuessTerms t, doub
     guess_norms_x2_body<NQT>(n, g, t, scratch, out);
 }
 
+// The least-squares start (krylov_guess_ls): over the affine span of the stored solutions,
+// written in Newton's backward differences f_p = nabla^p y_0 (y_j = S~ x~_{n-1-j}),
+// x0 = x_0 - sum_{p>=1} gamma_p nabla^p x_0 has the residual e + sum_p gamma_p f_p with
+// e = g - y_0, and the gamma minimising it solves G gamma = -b, G_pq = f_p . f_q, b_p = f_p . e
+// (the polynomial extrapolation through the same solutions is gamma = (-1, ..., -1); the
+// differences of successive orders are far from parallel, unlike y_0 - y_j).  One pass over g and
+// the NQT stored products gives, with the first differences y_{j-1} - y_j formed in FP64 (exact
+// for nearly equal values) and rounded once to FP32, the higher ones and every sum in FP32 per
+// thread, FP64 across threads:
+//   s[0] = ||g||^2, s[1] = ||e||^2, s[2 + p - 1] = b_p, s[7 + 5 (p-1) + (q-1)] = G_pq (p <= q).
+constexpr int kGramSlots = 32;
+
+template <int NQT>
+__device__ __forceinline__ void guess_gram_body(size_t n, const double* __restrict__ g, const GuessTerms& t,
+                                                double* __restrict__ scratch, double* __restrict__ out) {
+    constexpr int D = NQT - 1, NA = 2 + D + D * (D + 1) / 2;
+    unsigned* counter = reinterpret_cast<unsigned*>(scratch);
+    double* partial = scratch + 1;
+    __shared__ double sh[NA][kDotThreads / 32];
+    float acc[NA];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) acc[a] = 0.f;
+    const size_t stride = (size_t)gridDim.x * kDotThreads;
+    for (size_t i0 = blockIdx.x * (size_t)kDotThreads + threadIdx.x; i0 < n; i0 += 2 * stride) {
+        double gv[2], yv[2][6];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const size_t idx = i0 + u * stride;
+            const bool on = idx < n;
+            gv[u] = on ? g[idx] : 0.0;
+#pragma unroll
+            for (int j = 0; j < 6; ++j) yv[u][j] = (j < NQT && on) ? t.y[j][idx] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (i0 + u * stride >= n) continue;
+            const float gh = f64_to_f32(gv[u]);
+            const float e = f64_to_f32(gv[u] - yv[u][0]);
+            // the difference table: row r holds nabla^(r+1) at y_0, y_1, ...; d[p-1] = nabla^p y_0
+            float tab[D > 0 ? D : 1], d[D > 0 ? D : 1];
+#pragma unroll
+            for (int j = 0; j < D; ++j) tab[j] = f64_to_f32(yv[u][j] - yv[u][j + 1]);
+#pragma unroll
+            for (int r = 0; r < D; ++r) {
+                d[r] = tab[0];
+#pragma unroll
+                for (int j = 0; j + 1 < D - r; ++j) tab[j] = __fsub_rn(tab[j], tab[j + 1]);
+            }
+            acc[0] = __fmaf_rn(gh, gh, acc[0]);
+            acc[1] = __fmaf_rn(e, e, acc[1]);
+#pragma unroll
+            for (int i = 0; i < D; ++i) acc[2 + i] = __fmaf_rn(d[i], e, acc[2 + i]);
+            int a = 2 + D;
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = i; j < D; ++j) {
+                    acc[a] = __fmaf_rn(d[i], d[j], acc[a]);
+                    ++a;
+                }
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        const double v = warp_sum(f32_to_f64(acc[a]));
+        if (lane == 0) sh[a][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NA) {
+        double v = 0.0;
+        for (int k = 0; k < kDotThreads / 32; ++k) v += sh[threadIdx.x][k];
+        partial[(size_t)blockIdx.x * kGramSlots + threadIdx.x] = v;
+    }
+    if (last_block_arrives(counter)) {
+        // the partial columns in their compact order, written to the fixed slots of `out`
+        const int lane2 = threadIdx.x & 31, wid2 = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int a = wid2; a < NA; a += nw) {
+            double v = strided_sum(partial + a, lane2, 32, gridDim.x, (size_t)kGramSlots, 0.0);
+            v = warp_sum(v);
+            if (lane2 == 0) {
+                int slot = a;   // 0, 1 and the b's keep their index; G_ij goes to 7 + 5 i + j
+                if (a >= 2 + D) {
+                    int r = a - (2 + D), i = 0;
+                    while (r >= D - i) {
+                        r -= D - i;
+                        ++i;
+                    }
+                    slot = 7 + 5 * i + (i + r);
+                }
+                out[slot] = v;
+            }
+        }
+        if (threadIdx.x == 0) *counter = 0u;
+    }
+}
+
+template <int NQT>
+__global__ void __launch_bounds__(kDotThreads)
+guess_gram_kernel(size_t n, const double* __restrict__ g, GuessTerms t, double* __restrict__ scratch,
+                  double* __restrict__ out) {
+    guess_gram_body<NQT>(n, g, t, scratch, out);
+}
+
+__global__ void __launch_bounds__(kDotThreads)
+guess_gram_dev_kernel(size_t n, const double* __restrict__ g, const DevHist* __restrict__ dh,
+                      double* __restrict__ scratch, double* __restrict__ out) {
+    const int avail = dh->avail;
+    if (avail <= 0 || avail > 6) return;
+    GuessTerms t;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) t.y[j] = j < avail ? dh->y[j] : nullptr;
+    t.nq = avail;
+    switch (avail) {
+#define CASE(Q) \
+    case Q: guess_gram_body<Q>(n, g, t, scratch, out); break;
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6)
+#undef CASE
+        default: break;
+    }
+}
+
 struct GuessCoef {
     double c[7][6];
 };
@@ -664,7 +786,27 @@ cudaError_t multidot_impl(const T* V, size_t ldv, int nv, const T* w, size_t n, 
 
 }  // namespace
 
-size_t guess_scratch_doubles() { return 1 + (size_t)kDotBlocks * 7; }
+size_t guess_scratch_doubles() { return 1 + (size_t)kDotBlocks * kGramSlots; }
+
+cudaError_t launch_guess_gram(size_t n, const double* g, const GuessTerms& t, double* scratch, double* out,
+                              cudaStream_t s) {
+    switch (t.nq) {
+#define CASE(Q) \
+    case Q: guess_gram_kernel<Q><<<kDotBlocks, kDotThreads, 0, s>>>(n, g, t, scratch, out); break;
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_guess_gram_dev(size_t n, const double* g, const DevHist* dh, double* scratch, double* out,
+                                  cudaStream_t s) {
+    guess_gram_dev_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(n, g, dh, scratch, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_guess_norms(size_t n, const double* g, const GuessTerms& t, double* scratch, double* out,
                                cudaStream_t s, bool f32x2) {

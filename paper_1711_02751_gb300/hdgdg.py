@@ -49,7 +49,7 @@ class Config(ctypes.Structure):
                 ("local_precision", ctypes.c_int), ("krylov_guess", ctypes.c_int), ("spmv_kernel", ctypes.c_int),
                 ("krylov_ortho", ctypes.c_int), ("residual_f32x2", ctypes.c_int),
                 ("local_dense", ctypes.c_int), ("trace_operator", ctypes.c_int),
-                ("host_steps", ctypes.c_int), ("dg_precision", ctypes.c_int)]
+                ("host_steps", ctypes.c_int), ("dg_precision", ctypes.c_int), ("krylov_guess_ls", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -134,7 +134,7 @@ def make_config(N, k, dt, g=1.0, H0=1.0, scheme="ars2", krylov_rtol=0.0, krylov_
                 krylov_maxit=0, linear_only=False, precision="fp64", boundary="periodic", x0=0.0,
                 length=1.0, bc_params=(0.0, 0.0, 0.0, 0.0, 0.0), batch=1, dt_per_instance=None,
                 local_precision="fp64", krylov_guess=0, spmv_kernel=0, krylov_ortho=0, residual_f32x2=False,
-                local_dense=False, trace_operator=0, host_steps=False, dg_precision="default"):
+                local_dense=False, trace_operator=0, host_steps=False, dg_precision="default", krylov_guess_ls=False):
     """bc_params (boundary='vortex'): beta, u_inf, v_inf, x_c, y_c of the moving vortex.
     batch > 1: that many instances in one handle; dt_per_instance (length batch) overrides dt
     instance by instance (dt then only sets the scale the factors are taken against)."""
@@ -149,7 +149,7 @@ def make_config(N, k, dt, g=1.0, H0=1.0, scheme="ars2", krylov_rtol=0.0, krylov_
                  int(batch), _ptr(dts) if dts is not None else None, LOCAL_PRECISIONS[local_precision],
                  int(krylov_guess), int(spmv_kernel), int(krylov_ortho), int(bool(residual_f32x2)),
                  int(bool(local_dense)), int(trace_operator), int(bool(host_steps)),
-                 DG_PRECISIONS[dg_precision])
+                 DG_PRECISIONS[dg_precision], int(bool(krylov_guess_ls)))
     cfg._dts = dts                     # keeps the array alive as long as the config
     return cfg
 
@@ -210,7 +210,7 @@ class Sim:
                  boundary="periodic", x0=0.0, length=1.0, bc_params=(0.0, 0.0, 0.0, 0.0, 0.0),
                  batch=1, dt_per_instance=None, local_precision="fp64", krylov_guess=0, spmv_kernel=0,
                  krylov_ortho=0, residual_f32x2=False, local_dense=False, trace_operator=0, host_steps=False,
-                 dg_precision="default"):
+                 dg_precision="default", krylov_guess_ls=False):
         """batch > 1 holds that many independent instances of the mesh (one launch per kernel
         per stage covers all of them); arrays are then [batch * N * N, (k+1)^2], instance-major,
         and the bottom and the time step (dt_per_instance) may differ from instance to instance."""
@@ -221,7 +221,8 @@ class Sim:
         self.cfg = make_config(N, k, dt, g, H0, scheme, krylov_rtol, krylov_restart, krylov_maxit,
                                linear_only, precision, boundary, x0, length, bc_params, batch,
                                dt_per_instance, local_precision, krylov_guess, spmv_kernel, krylov_ortho,
-                               residual_f32x2, local_dense, trace_operator, host_steps, dg_precision)
+                               residual_f32x2, local_dense, trace_operator, host_steps, dg_precision,
+                               krylov_guess_ls)
         self._h = ctypes.c_void_p(None)
         b = None if bottom is None else _f64(bottom, (self.n_el, self.Np))
         st = lib().hdgdg_create(ctypes.byref(self.cfg), None if b is None else _ptr(b),

@@ -177,3 +177,28 @@ def test_adaptive_guess_order():
             its[guess] = s.stats()["krylov_iterations"]
         assert all(0 <= o <= max(guess, 0) for o in orders)
     assert its[6] <= its[-1]
+
+
+@pytest.mark.parametrize("kw", [dict(local_precision="f32x2", trace_operator=1), dict(local_precision="f32x2")])
+def test_least_squares_start_matches_oracle(kw):
+    """The least-squares start (krylov_guess_ls): the projection of the trace solution on the affine
+    span of the stored solutions, chosen when its residual beats the zero start.  The stop test is
+    unchanged, so the mixed form stays within its tolerance of the oracle; each polynomial
+    extrapolation is a candidate of the projection, so the solves take no more Krylov iterations
+    than from the best polynomial start (two spare for rounding of the FP32 Gram sums)."""
+    N, k, steps = 12, 3, 10
+    m, h, hu, hv, b = user_state(N, k, "large")
+    dt = dt_of(m, h, hu, hv)
+    res = {}
+    for ls in (False, True):
+        with hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, precision="mixed", krylov_guess_ls=ls, **kw) as s:
+            s.set_state(h, hu, hv)
+            s.step(steps)
+            res[ls] = (swe.to_state(*s.get_state(), b, W.G, W.H0)[0], s.stats())
+    q, phiB = oracle_state(m, h, hu, hv, b)
+    qo = imex.Stepper(m, phiB, dt, solver="lu").run(q, steps)
+    assert max(imex.rel_l2(m, res[True][0][c], qo[c]) for c in range(3)) <= 1e-6
+    assert res[True][1]["krylov_iterations"] <= res[False][1]["krylov_iterations"] + 2
+    with pytest.raises(hd.HdgdgError):   # the FP64 form keeps the polynomial candidates
+        hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, krylov_guess_ls=True)
+

@@ -49,6 +49,8 @@ def _run(N, k, kind, steps, host_steps, boundary="periodic", **kw):
     ("ars3", 10, 3, "large", 7, dict(scheme="ars3")),
     ("linear_only", 8, 3, "standing", 6, dict(linear_only=True)),
     ("bump8_stiff_guess3", 8, 2, "bump8", 8, dict(krylov_guess=3)),
+    ("mixed_matrix_free_ls", 16, 3, "large", 9, dict(MF, krylov_guess_ls=True)),
+    ("mixed_assembled_ls_guess2", 12, 3, "large", 7, dict(ASSEMBLED, krylov_guess_ls=True, krylov_guess=2)),
 ])
 def test_graph_steps_equal_host_driven_steps(name, N, k, kind, steps, kw):
     a, sa, ga = _run(N, k, kind, steps, False, **kw)
