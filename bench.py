@@ -63,6 +63,8 @@ def _args():
                     help="arithmetic of the local condensation / recovery in the mixed form")
     ap.add_argument("--guess", type=int, default=0, choices=[-1, 0, 1, 2, 3, 4, 5, 6],
                     help="trace-solve initial guess: extrapolation order 1-3, -1 zero, 0 library default")
+    ap.add_argument("--guess-ls", action="store_true",
+                    help="mixed form: start the trace solves from the least-squares projection on the stored solutions")
     ap.add_argument("--spmv-kernel", type=int, default=0, choices=[0, 1],
                     help="FP32 inner SpMV: 0 plain (x gathered through shared memory), 1 pipelined bulk copies")
     ap.add_argument("--ortho", type=int, default=0, choices=[0, 1],
@@ -435,7 +437,8 @@ def stiff_block(args, stream, dist, world):
         sim = hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, stream=stream.cuda_stream, precision=precision,
                      local_precision=args.local if precision == "mixed" else "fp64",
                      residual_f32x2=bool(args.residual_f32x2) and precision == "mixed",
-                     trace_operator=_trace_operator(args, precision))
+                     trace_operator=_trace_operator(args, precision),
+                     krylov_guess_ls=bool(args.guess_ls) and precision == "mixed")
         sim.set_state(h, hu, hv)
         for _ in range(args.warmup):
             sim.step(1)
