@@ -130,7 +130,10 @@ Plan make_plan(const hdgdg_config* c) {
         b += n_edges * (size_t)p.NF * p.NF * sizeof(__half) + n_edges * sizeof(float);
         b += (n_el * Np * Np + 4 * n_el * Np + 2 * B * Np) * sizeof(float);
         b += 3 * p.nt * d;   // M^{-1} x and the two halves of S y
-        b += n_edges * P * (sizeof(float) + d);   // tau_hat in FP32 and as FP32 pairs
+        b += n_edges * P * d;   // tau_hat as FP32 pairs
+    }
+    if (c->precision == HDGDG_MIXED && local_schur(c)) {   // FP32 stage values, phi_B and tau_hat
+        b += (4 * p.n + n_edges * P) * sizeof(float);
     }
     b += 2 * (size_t)guess_order(c) * p.s * p.nt * d;         // previous stage solutions and products
     p.persistent = b;
@@ -348,6 +351,11 @@ struct hdgdg_sim {
     DevHist* dhist = nullptr;             // each stage's guess history, as the step graph reads it
     DevHist* hhist = nullptr;             // its pinned host copy, written before every replay
     double* dls = nullptr;                // the least-squares start's sums, choice and coefficients
+    // mixed form with the Schur-complement local solves: the DG residual's FP32 copies (phi_B,
+    // tau) and the recovery's FP32 stage values; the face fluxes then sit in fface as FP32
+    float* Qs32 = nullptr;
+    float* phiB32 = nullptr;
+    float* tau32 = nullptr;
     StepStats* sstats = nullptr;          // counters of the replayed step
     cudaStream_t body_stream = nullptr;   // captures the restart-cycle bodies of the conditional nodes
     std::vector<TimerPair>* capture_sink = nullptr;   // timers of the graph being captured
@@ -811,7 +819,7 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
 
 // One implicit stage: R1 (device) -> Q, Lst = dt M^{-1} L (device); qhat left in sim->lam.
 hdgdg_status stage_solve_dev(hdgdg_sim* sim, const double* R1, double* Q, double* Lst, int* its,
-                             double t_stage = 0.0, int stage = -1) {
+                             double t_stage = 0.0, int stage = -1, float* Q32 = nullptr) {
     NvtxRange nv("stage_solve");
     double rr;
     {
@@ -823,9 +831,24 @@ hdgdg_status stage_solve_dev(hdgdg_sim* sim, const double* R1, double* Q, double
     {
         TimedGroup tg(sim, HDGDG_KT_RECOVER);
         CU(launch_recover(sim->g, sim->ops, sim->Z, R1, sim->tau, sim->lam, beta_of(sim), 1.0 / sim->a_ii,
-                          Q, Lst, sim->stream));
+                          Q, Lst, sim->stream, Q32));
     }
     return HDGDG_OK;
+}
+
+// The nonlinear DG residual of stage value Qi into out.  stage_value: Qi came from this step's
+// recovery (with the FP32 copies, its FP32 copy in Qs32 is the one written).
+cudaError_t dg_nl_enqueue(hdgdg_sim* sim, const double* Qi, bool stage_value, double* out, cudaStream_t st,
+                          double t) {
+    if (sim->ens) return launch_ens_dg_nl_f32(*sim->ens, Qi, sim->fface, out, st);
+    if (sim->cfg.dg_precision == 1)
+        return launch_dg_nl_bf16(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, out, st, t);
+    if (sim->cfg.precision == HDGDG_MIXED && sim->Qs32)
+        return launch_dg_nl_f32io(sim->g, Qi, stage_value ? sim->Qs32 : nullptr, sim->phiB32, sim->tau32, sim->cfg.dt,
+                                  reinterpret_cast<float*>(sim->fface), out, st, t);
+    if (sim->cfg.precision == HDGDG_MIXED)
+        return launch_dg_nl_f32(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, out, st, t);
+    return launch_dg_nl(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, out, st, t);
 }
 
 // ---- whole-step graphs ------------------------------------------------------------------------
@@ -945,19 +968,10 @@ cudaError_t step_enqueue_graph(hdgdg_sim* sim, cudaStream_t st, StepGraph& sg) {
                 e = sim->ens ? launch_ens_recover(*sim->ens, sim->Z, sim->R1, sim->lam, 1.0 / sim->a_ii, sim->Qs,
                                                   sim->Ls[i], st)
                              : launch_recover(sim->g, sim->ops, sim->Z, sim->R1, sim->tau, sim->lam, beta_of(sim),
-                                              1.0 / sim->a_ii, sim->Qs, sim->Ls[i], st);
+                                              1.0 / sim->a_ii, sim->Qs, sim->Ls[i], st, sim->Qs32);
             Qi = sim->Qs;
         }
-        if (!sim->cfg.linear_only && e == cudaSuccess) {
-            if (sim->ens)
-                e = launch_ens_dg_nl_f32(*sim->ens, Qi, sim->fface, sim->NLs[i], st);
-            else if (sim->cfg.dg_precision == 1)
-                e = launch_dg_nl_bf16(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st, 0.0);
-            else if (sim->cfg.precision == HDGDG_MIXED)
-                e = launch_dg_nl_f32(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st, 0.0);
-            else
-                e = launch_dg_nl(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st, 0.0);
-        }
+        if (!sim->cfg.linear_only && e == cudaSuccess) e = dg_nl_enqueue(sim, Qi, Qi == sim->Qs, sim->NLs[i], st, 0.0);
     }
     CombineTerms t{};
     for (int i = 0; i < sim->s; ++i) {
@@ -1152,17 +1166,12 @@ hdgdg_status one_step(hdgdg_sim* sim) {
                 CU(launch_combine(n3, sim->q, t, sim->R1, nullptr, st));
             }
             int its = 0;
-            TRY(stage_solve_dev(sim, sim->R1, sim->Qs, sim->Ls[i], &its, ti, i));
+            TRY(stage_solve_dev(sim, sim->R1, sim->Qs, sim->Ls[i], &its, ti, i, sim->Qs32));
             Qi = sim->Qs;
         }
         if (!sim->cfg.linear_only) {
             TimedGroup tg(sim, HDGDG_KT_DG);
-            if (sim->cfg.dg_precision == 1)
-                CU(launch_dg_nl_bf16(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st, ti));
-            else if (sim->cfg.precision == HDGDG_MIXED)
-                CU(launch_dg_nl_f32(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st, ti));
-            else
-                CU(launch_dg_nl(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, sim->NLs[i], st, ti));
+            CU(dg_nl_enqueue(sim, Qi, Qi == sim->Qs, sim->NLs[i], st, ti));
         }
     }
     CombineTerms t{};
@@ -1333,6 +1342,15 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
         sim->ops.kind = x2 ? 3 : 0;
         sim->ops.schur = true;
         sim->ops.error = reinterpret_cast<int*>(sim->flags) + 2;   // the staged tile's bounded waits
+        if (c->precision == HDGDG_MIXED && c->dg_precision == 0 && !explicit_scheme(c)) {
+            // the DG residual's FP32 copies and the recovery's FP32 stage values (the same roundings
+            // the FP32 residual took from the FP64 values)
+            TRY(dalloc(sim, &sim->Qs32, 3 * p.n));
+            TRY(dalloc(sim, &sim->phiB32, p.n));
+            TRY(dalloc(sim, &sim->tau32, (size_t)g.n_edges * g.P));
+            CU(launch_to_f32(sim->phiB, sim->phiB32, p.n, sim->stream));
+            CU(launch_to_f32(sim->tau, sim->tau32, (size_t)g.n_edges * g.P, sim->stream));
+        }
         sim->ops.S = sim->Sphi;
         sim->ops.aux = sim->Saux;
         sim->ops.EG = sim->Seg;
@@ -1346,10 +1364,11 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
             TRY(dalloc(sim, &sim->Minv16, (size_t)g.n_edges * p.NF * p.NF));
             TRY(dalloc(sim, &sim->Mscale, (size_t)g.n_edges));
             TRY(dalloc(sim, &ybuf, p.nt));
-            float* tau32 = nullptr;
-            TRY(dalloc(sim, &tau32, (size_t)g.n_edges * g.P));
-            CU(launch_to_f32(sim->tau, tau32, (size_t)g.n_edges * g.P, sim->stream));
-            sim->mf.tau32 = tau32;
+            if (!sim->tau32) {
+                TRY(dalloc(sim, &sim->tau32, (size_t)g.n_edges * g.P));
+                CU(launch_to_f32(sim->tau, sim->tau32, (size_t)g.n_edges * g.P, sim->stream));
+            }
+            sim->mf.tau32 = sim->tau32;
             double* tau2 = nullptr;   // FP32 pairs in place of a copy of tau
             TRY(dalloc(sim, &tau2, (size_t)g.n_edges * g.P));
             CU(cudaMemcpyAsync(tau2, sim->tau, (size_t)g.n_edges * g.P * sizeof(double), cudaMemcpyDeviceToDevice,

@@ -209,6 +209,12 @@ void count_launches(int n);
 cudaError_t launch_dg_nl(const Geom& g, const double* q, const double* phiB, const double* tau_edge,
                          double scale, double* fface, double* out, cudaStream_t s, double t = 0.0);
 // the same residual computed in FP32 arithmetic (FP64 storage): the mixed form's DG residual
+// The mixed form's residual on FP32 copies (launch_dg_nl_f32 term for term): phi_B, tau and the
+// face fluxes in FP32, the state in FP32 (q32, when given: the recovery's FP32 stage values) or
+// FP64 (q64).
+cudaError_t launch_dg_nl_f32io(const Geom& g, const double* q64, const float* q32, const float* phiB32,
+                               const float* tau32, double scale, float* fface32, double* out, cudaStream_t s,
+                               double t);
 cudaError_t launch_dg_nl_f32(const Geom& g, const double* q, const double* phiB, const double* tau_edge,
                              double scale, double* fface, double* out, cudaStream_t s, double t = 0.0);
 // the same residual with its inputs (state, phi_B, tau) rounded to BF16 and FP32 arithmetic (k <= 4)
@@ -273,7 +279,7 @@ cudaError_t launch_condense(const Geom& g, const LocalOps& ops, const double* R1
 // Recovery: Q = Z + beta A^{-1} (tau qhat) on boundary nodes; Lst = (Q - R1) / a_ii.
 cudaError_t launch_recover(const Geom& g, const LocalOps& ops, const double* Z, const double* R1,
                            const double* tau_edge, const double* qhat, double beta, double inv_aii,
-                           double* Q, double* Lst, cudaStream_t s);
+                           double* Q, double* Lst, cudaStream_t s, float* Q32 = nullptr);
 // Autotuner of the local kernels' tile (elements per block): times each candidate on the handle's
 // operators, using R1, Z, Q, Lst as scratch (their contents are overwritten), and records the
 // fastest in ops: the Schur-complement kernels (FP64 or FP32 pairs, degrees 2..4) and the dense

@@ -16,6 +16,7 @@
 #include "ens.h"
 #include "fastcvt.h"
 #include <cstdint>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -29,11 +30,25 @@ struct DgTile {
 };
 
 // An input of the residual in the arithmetic type; BF: rounded to BF16 first (8 significant bits,
-// nearest even), the BF16-input variant of the mixed form.
+// nearest even), the BF16-input variant of the mixed form.  An input already stored in FP32 (the
+// mixed form's FP32 copies, rounded the same way) passes as it is.
 template <typename Tc, bool BF>
 __device__ __forceinline__ Tc dg_in(double v) {
     if constexpr (BF) return __bfloat162float(__float2bfloat16_rn(f64_to_f32(v)));
     else return from_f64<Tc>(v);
+}
+template <typename Tc, bool BF>
+__device__ __forceinline__ Tc dg_in(float v) {
+    static_assert(sizeof(Tc) == 4 && !BF, "FP32 inputs feed the FP32 residual");
+    return v;
+}
+
+// A stored value as the local type TV of the face pass (double, or float for FP32 inputs).
+template <typename TV, typename TI>
+__device__ __forceinline__ TV as_tv(TI v) {
+    if constexpr (sizeof(TV) == sizeof(TI)) return v;
+    else if constexpr (sizeof(TV) == 4) return f64_to_f32(v);
+    else return (double)v;
 }
 
 // F_NL components along x (fx) and y (fy) for the momentum rows (the mass row is zero).
@@ -54,10 +69,15 @@ __device__ __forceinline__ void nl_flux(Tc ph, Tc U, Tc V, Tc phiB, Tc* fxU, Tc*
 //   FULL = true: the Rusanov flux F* . n of the whole flux F = F_NL + F_L (eq. Full_russanov),
 //   the residual of the explicit RK DG scheme the paper compares with.
 //   Tc: arithmetic type (double; float for the mixed form's residual), storage stays FP64.
-template <int P, bool FULL, typename Tc, bool BF = false>
-__device__ __forceinline__ void dg_face_body(int bid, const Geom& g, const double* __restrict__ q,
-                                             const double* __restrict__ phiB, const double* __restrict__ tau_edge,
-                                             double* __restrict__ fface, double t_bc) {
+// A32: phi_B, tau and the face fluxes stored in FP32 (the mixed form's copies; Tc = float);
+// TQ: the type the state q is stored in (FP32: the recovery's FP32 stage values).
+template <int P, bool FULL, typename Tc, bool BF = false, typename TQ = double, bool A32 = false>
+__device__ __forceinline__ void dg_face_body(int bid, const Geom& g, const TQ* __restrict__ q,
+                                             const std::conditional_t<A32, float, double>* __restrict__ phiB,
+                                             const std::conditional_t<A32, float, double>* __restrict__ tau_edge,
+                                             std::conditional_t<A32, float, double>* __restrict__ fface,
+                                             double t_bc) {
+    using TV = std::conditional_t<A32, float, double>;   // the node values as the pass holds them
     constexpr int Np = P * P;
     const int t = bid * 256 + threadIdx.x;
     if (t >= g.n_edges * P) return;
@@ -66,14 +86,14 @@ __device__ __forceinline__ void dg_face_body(int bid, const Geom& g, const doubl
     edge_sides(r, g, &em, &fm, &ep, &fp);
     const size_t fs = (size_t)g.n_el * Np;
     const bool xedge = fm == 1;
-    double phm, Um, Vm, pbm, php, Up, Vp, pbp;
+    TV phm, Um, Vm, pbm, php, Up, Vp, pbp;
     if (em >= 0) {
         const size_t om = (size_t)em * Np + face_node(fm, b, P);
-        phm = q[om]; Um = q[fs + om]; Vm = q[2 * fs + om]; pbm = phiB[om];
+        phm = as_tv<TV>(q[om]); Um = as_tv<TV>(q[fs + om]); Vm = as_tv<TV>(q[2 * fs + om]); pbm = phiB[om];
     }
     if (ep >= 0) {
         const size_t op = (size_t)ep * Np + face_node(fp, b, P);
-        php = q[op]; Up = q[fs + op]; Vp = q[2 * fs + op]; pbp = phiB[op];
+        php = as_tv<TV>(q[op]); Up = as_tv<TV>(q[fs + op]); Vp = as_tv<TV>(q[2 * fs + op]); pbp = phiB[op];
     }
     if (g.dirichlet && (em < 0 || ep < 0)) {
         // Dirichlet boundary: the other side is the prescribed exact state at the node
@@ -81,8 +101,8 @@ __device__ __forceinline__ void dg_face_body(int bid, const Geom& g, const doubl
         face_node_xy(g, em >= 0 ? em : ep, em >= 0 ? fm : fp, b, &x, &y);
         double ph, U, V;
         vortex_state(g, x, y, t_bc * dt_factor(g, em >= 0 ? em : ep), &ph, &U, &V);
-        if (em < 0) { phm = ph; Um = U; Vm = V; pbm = pbp; }
-        else { php = ph; Up = U; Vp = V; pbp = pbm; }
+        if (em < 0) { phm = as_tv<TV>(ph); Um = as_tv<TV>(U); Vm = as_tv<TV>(V); pbm = pbp; }
+        else { php = as_tv<TV>(ph); Up = as_tv<TV>(U); Vp = as_tv<TV>(V); pbp = pbm; }
     } else {
         // a wall edge sees the mirror state of its one element (eq. reflection): same phi and
         // tangential momentum, opposite normal momentum
@@ -102,8 +122,8 @@ __device__ __forceinline__ void dg_face_body(int bid, const Geom& g, const doubl
     const Tc tau_star = fmax(fabs(Unm) * im + sqrt(Phm), fabs(Unp) * ip + sqrt(Php));
     Tc hd, fph;
     if (FULL) {   // add F_L . n = (U_n, phi_eta phi_B, 0)
-        Fnm += pm * from_f64<Tc>(pbm);
-        Fnp += pp * from_f64<Tc>(pbp);
+        Fnm += pm * dg_in<Tc, false>(pbm);
+        Fnp += pp * dg_in<Tc, false>(pbp);
         hd = Tc(0.5) * tau_star;
         fph = Tc(0.5) * (Unm + Unp) + hd * (pm - pp);
     } else {
@@ -112,24 +132,32 @@ __device__ __forceinline__ void dg_face_body(int bid, const Geom& g, const doubl
     }
     const Tc fn = Tc(0.5) * (Fnm + Fnp) + hd * (Unm - Unp);
     const Tc ft = Tc(0.5) * (Ftm + Ftp) + hd * (Utm - Utp);
-    double* out = fface + (size_t)r * 3 * P;
-    out[b] = to_f64(fph);
-    out[(xedge ? 1 : 2) * P + b] = to_f64(fn);
-    out[(xedge ? 2 : 1) * P + b] = to_f64(ft);
+    TV* out = fface + (size_t)r * 3 * P;
+    if constexpr (A32) {   // FP32 storage: the values the FP64 storage's round trip gives back
+        out[b] = fph;
+        out[(xedge ? 1 : 2) * P + b] = fn;
+        out[(xedge ? 2 : 1) * P + b] = ft;
+    } else {
+        out[b] = to_f64(fph);
+        out[(xedge ? 1 : 2) * P + b] = to_f64(fn);
+        out[(xedge ? 2 : 1) * P + b] = to_f64(ft);
+    }
 }
 
-template <int P, bool FULL, typename Tc, bool BF = false>
+template <int P, bool FULL, typename Tc, bool BF = false, typename TQ = double, bool A32 = false>
 __global__ void __launch_bounds__(256)
-dg_face_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ phiB,
-               const double* __restrict__ tau_edge, double* __restrict__ fface, double t_bc) {
-    dg_face_body<P, FULL, Tc, BF>(blockIdx.x, g, q, phiB, tau_edge, fface, t_bc);
+dg_face_kernel(Geom g, const TQ* __restrict__ q, const std::conditional_t<A32, float, double>* __restrict__ phiB,
+               const std::conditional_t<A32, float, double>* __restrict__ tau_edge,
+               std::conditional_t<A32, float, double>* __restrict__ fface, double t_bc) {
+    dg_face_body<P, FULL, Tc, BF, TQ, A32>(blockIdx.x, g, q, phiB, tau_edge, fface, t_bc);
 }
 
 // Element pass: volume term from the nodal F_NL (shared memory), minus the lifted face fluxes.
 // FULL = true: the whole flux F and the source s = (0, phi_eta d_x phi_B, phi_eta d_y phi_B).
-template <int P, bool FULL, typename Tc, bool BF = false>
-__device__ __forceinline__ void dg_volume_body(int bid, const Geom& g, const double* __restrict__ q,
-                                               const double* __restrict__ phiB, const double* __restrict__ fface,
+template <int P, bool FULL, typename Tc, bool BF = false, typename TQ = double, bool A32 = false>
+__device__ __forceinline__ void dg_volume_body(int bid, const Geom& g, const TQ* __restrict__ q,
+                                               const std::conditional_t<A32, float, double>* __restrict__ phiB,
+                                               const std::conditional_t<A32, float, double>* __restrict__ fface,
                                                double scale, double* __restrict__ out) {
     constexpr int Np = P * P;
     constexpr int EPB = DgTile<P>::EPB;
@@ -200,11 +228,11 @@ __device__ __forceinline__ void dg_volume_body(int bid, const Geom& g, const dou
                         (f == 3 && j == P - 1);
         if (!on) continue;
         const int b = (f < 2) ? j : i;
-        const double* fl = fface + (size_t)edge_of_face(e, f, g) * 3 * P;
+        const auto* fl = fface + (size_t)edge_of_face(e, f, g) * 3 * P;
         const Tc sgn = (f & 1) ? lift : -lift;   // outward normal is + on faces 1, 3
-        rph -= sgn * from_f64<Tc>(fl[b]);
-        rU -= sgn * from_f64<Tc>(fl[P + b]);
-        rV -= sgn * from_f64<Tc>(fl[2 * P + b]);
+        rph -= sgn * dg_in<Tc, false>(fl[b]);
+        rU -= sgn * dg_in<Tc, false>(fl[P + b]);
+        rV -= sgn * dg_in<Tc, false>(fl[2 * P + b]);
     }
     const size_t o = (size_t)e * Np + n;
     const double sc = scale * dt_factor(g, e);   // this instance's time step
@@ -213,11 +241,12 @@ __device__ __forceinline__ void dg_volume_body(int bid, const Geom& g, const dou
     out[2 * fs + o] = sc * to_f64(rV);
 }
 
-template <int P, bool FULL, typename Tc, bool BF = false>
+template <int P, bool FULL, typename Tc, bool BF = false, typename TQ = double, bool A32 = false>
 __global__ void __launch_bounds__(DgTile<P>::EPB * P * P)
-dg_volume_kernel(Geom g, const double* __restrict__ q, const double* __restrict__ phiB,
-                 const double* __restrict__ fface, double scale, double* __restrict__ out) {
-    dg_volume_body<P, FULL, Tc, BF>(blockIdx.x, g, q, phiB, fface, scale, out);
+dg_volume_kernel(Geom g, const TQ* __restrict__ q, const std::conditional_t<A32, float, double>* __restrict__ phiB,
+                 const std::conditional_t<A32, float, double>* __restrict__ fface, double scale,
+                 double* __restrict__ out) {
+    dg_volume_body<P, FULL, Tc, BF, TQ, A32>(blockIdx.x, g, q, phiB, fface, scale, out);
 }
 
 // One instance per term count NT (0..10), the terms indexed by constants.  Each thread takes U
@@ -347,6 +376,26 @@ cudaError_t dg_launch(const Geom& g, const double* q, const double* phiB, const 
     return cudaGetLastError();
 }
 
+// The mixed form's residual on FP32 copies: phi_B, tau and the face fluxes in FP32, the state
+// in FP32 (q32, the recovery's FP32 stage values) or FP64 (q64, the step's start).
+template <int P>
+cudaError_t dg_launch_f32io(const Geom& g, const double* q64, const float* q32, const float* phiB,
+                            const float* tau_edge, double scale, float* fface, double* out, cudaStream_t s,
+                            double t) {
+    constexpr int EPB = DgTile<P>::EPB;
+    const int nf = g.n_edges * P;
+    const int gf = (nf + 255) / 256, gv = (g.n_el + EPB - 1) / EPB, tv = EPB * P * P;
+    if (q32) {
+        dg_face_kernel<P, false, float, false, float, true><<<gf, 256, 0, s>>>(g, q32, phiB, tau_edge, fface, t);
+        dg_volume_kernel<P, false, float, false, float, true><<<gv, tv, 0, s>>>(g, q32, phiB, fface, scale, out);
+    } else {
+        dg_face_kernel<P, false, float, false, double, true><<<gf, 256, 0, s>>>(g, q64, phiB, tau_edge, fface, t);
+        dg_volume_kernel<P, false, float, false, double, true><<<gv, tv, 0, s>>>(g, q64, phiB, fface, scale, out);
+    }
+    count_launches(2);
+    return cudaGetLastError();
+}
+
 int grid_for(size_t n, int threads) {
     size_t b = (n + threads - 1) / threads;
     if (b > 152 * 16) b = 152 * 16;
@@ -415,6 +464,18 @@ cudaError_t launch_dg_nl(const Geom& g, const double* q, const double* phiB, con
         case 7: return dg_launch<7, false>(g, q, phiB, tau_edge, scale, fface, out, s, t);
         case 8: return dg_launch<8, false>(g, q, phiB, tau_edge, scale, fface, out, s, t);
         case 9: return dg_launch<9, false>(g, q, phiB, tau_edge, scale, fface, out, s, t);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_dg_nl_f32io(const Geom& g, const double* q64, const float* q32, const float* phiB32,
+                               const float* tau32, double scale, float* fface32, double* out, cudaStream_t s,
+                               double t) {
+    switch (g.P) {
+#define CASE(P) \
+    case P: return dg_launch_f32io<P>(g, q64, q32, phiB32, tau32, scale, fface32, out, s, t);
+        CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9)
+#undef CASE
         default: return cudaErrorInvalidValue;
     }
 }

@@ -577,7 +577,8 @@ __device__ __forceinline__ void schur_recover_body(int bid, const Geom& g, const
                                                    const typename A::T* __restrict__ EG, const double* __restrict__ Z,
                                                    const double* __restrict__ R1, const double* __restrict__ tau_edge,
                                                    const double* __restrict__ qhat, double beta, double inv_aii,
-                                                   double* __restrict__ Q, double* __restrict__ Lst) {
+                                                   double* __restrict__ Q, double* __restrict__ Lst,
+                                                   float* __restrict__ Q32 = nullptr) {
     using T = typename A::T;
     constexpr int Np = P * P, NF = 3 * P;
     __shared__ SchurSmem<P, EPB, A> sm;
@@ -605,7 +606,8 @@ __device__ __forceinline__ void schur_recover_body(int bid, const Geom& g, const
         for (int c = 0; c < 3; ++c) {
             const size_t oc = c * fs + o;
             const double q = Z[oc] + kk * A::to(y[c]);
-            Q[oc] = q;
+            if (Q32) Q32[oc] = f64_to_f32(q);   // the FP32 stage value the mixed form's DG residual reads
+            else Q[oc] = q;
             Lst[oc] = (q - R1[oc]) * inv_aii;
         }
     }
@@ -617,8 +619,8 @@ __global__ void __launch_bounds__(EPB * P * P)
                          const typename A::T* __restrict__ EG, const double* __restrict__ Z,
                          const double* __restrict__ R1, const double* __restrict__ tau_edge,
                          const double* __restrict__ qhat, double beta, double inv_aii, double* __restrict__ Q,
-                         double* __restrict__ Lst) {
-    schur_recover_body<P, EPB, A>(blockIdx.x, g, S, aux, EG, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst);
+                         double* __restrict__ Lst, float* __restrict__ Q32) {
+    schur_recover_body<P, EPB, A>(blockIdx.x, g, S, aux, EG, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, Q32);
 }
 
 // The same two passes with the element operators staged into shared memory by bulk copies
@@ -664,7 +666,7 @@ __global__ void __launch_bounds__(EPB * P * P)
                                 const typename A::T* __restrict__ EG, const double* __restrict__ Z,
                                 const double* __restrict__ R1, const double* __restrict__ tau_edge,
                                 const double* __restrict__ qhat, double beta, double inv_aii, double* __restrict__ Q,
-                                double* __restrict__ Lst, unsigned* err) {
+                                double* __restrict__ Lst, unsigned* err, float* __restrict__ Q32) {
     using T = typename A::T;
     constexpr int Np = P * P, NF = 3 * P;
     __shared__ SchurSmem<P, EPB, A> sm;
@@ -702,7 +704,8 @@ __global__ void __launch_bounds__(EPB * P * P)
         for (int c = 0; c < 3; ++c) {
             const size_t oc = c * fs + o;
             const double q = zv[c] + kk * A::to(y[c]);
-            Q[oc] = q;
+            if (Q32) Q32[oc] = f64_to_f32(q);
+            else Q[oc] = q;
             Lst[oc] = (q - rv[c]) * inv_aii;
         }
     }
@@ -728,12 +731,13 @@ void schur_condense_t(const Geom& g, const LocalOps& ops, const double* R1, doub
 
 template <int P, class A, int TILE>
 void schur_recover_t(const Geom& g, const LocalOps& ops, const double* Z, const double* R1, const double* tau_edge,
-                     const double* qhat, double beta, double inv_aii, double* Q, double* Lst, cudaStream_t s) {
+                     const double* qhat, double beta, double inv_aii, double* Q, double* Lst, cudaStream_t s,
+                     float* Q32) {
     using T = typename A::T;
     constexpr int EPB = schur_epb_for<P>(schur_tile_threads(TILE));
     schur_recover_kernel<P, EPB, A><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(
         g, static_cast<const T*>(ops.S), static_cast<const T*>(ops.aux), static_cast<const T*>(ops.EG), Z, R1,
-        tau_edge, qhat, beta, inv_aii, Q, Lst);
+        tau_edge, qhat, beta, inv_aii, Q, Lst, Q32);
     count_launches(1);
 }
 
@@ -764,23 +768,26 @@ void schur_condense(const Geom& g, const LocalOps& ops, const double* R1, double
 
 template <int P, class A>
 void schur_recover(const Geom& g, const LocalOps& ops, const double* Z, const double* R1, const double* tau_edge,
-                   const double* qhat, double beta, double inv_aii, double* Q, double* Lst, cudaStream_t s) {
+                   const double* qhat, double beta, double inv_aii, double* Q, double* Lst, cudaStream_t s,
+                   float* Q32 = nullptr) {
     if constexpr (schur_staged_ok<P, A>()) {
         if (ops.schur_tile_r == 3) {
             using T = typename A::T;
             constexpr int EPB = schur_epb_for<P>(128);
             schur_recover_staged_kernel<P, EPB, A><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(
                 g, static_cast<const T*>(ops.S), static_cast<const T*>(ops.aux), static_cast<const T*>(ops.EG), Z, R1,
-                tau_edge, qhat, beta, inv_aii, Q, Lst, reinterpret_cast<unsigned*>(ops.error));
+                tau_edge, qhat, beta, inv_aii, Q, Lst, reinterpret_cast<unsigned*>(ops.error), Q32);
             count_launches(1);
             return;
         }
     }
     if constexpr (P >= 3 && P <= 5) {
-        if (ops.schur_tile_r == 1) return schur_recover_t<P, A, 1>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s);
-        if (ops.schur_tile_r == 2) return schur_recover_t<P, A, 2>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s);
+        if (ops.schur_tile_r == 1)
+            return schur_recover_t<P, A, 1>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s, Q32);
+        if (ops.schur_tile_r == 2)
+            return schur_recover_t<P, A, 2>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s, Q32);
     }
-    schur_recover_t<P, A, 0>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s);
+    schur_recover_t<P, A, 0>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s, Q32);
 }
 
 // Time each tile of the Schur condensation and recovery (two warm-up and five timed launches
@@ -1009,15 +1016,16 @@ cudaError_t condense_launch(const Geom& g, const LocalOps& ops, const double* R1
 template <int P>
 cudaError_t recover_launch(const Geom& g, const LocalOps& ops, const double* Z, const double* R1,
                            const double* tau_edge, const double* qhat, double beta, double inv_aii,
-                           double* Q, double* Lst, cudaStream_t s) {
+                           double* Q, double* Lst, cudaStream_t s, float* Q32) {
     constexpr int NV = 3 * P * P;
     constexpr int EPB = (256 / NV) > 0 ? 256 / NV : 1;
     const int blocks = (g.n_el + EPB - 1) / EPB;
     if (ops.schur) {
-        if (ops.kind == 3) schur_recover<P, ArithF2>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s);
-        else schur_recover<P, ArithF64>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s);
+        if (ops.kind == 3) schur_recover<P, ArithF2>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s, Q32);
+        else schur_recover<P, ArithF64>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s, Q32);
         return cudaGetLastError();
     }
+    if (Q32) return cudaErrorInvalidValue;   // the FP32 stage output is the Schur kernels' only
     if (ops.kind == 2)
         return launch_local_tc(g, 1, ops.image, R1, Z, tau_edge, qhat, beta, inv_aii, Q, Lst, ops.error, s);
     if (ops.kind == 4)
@@ -1237,8 +1245,8 @@ cudaError_t launch_condense(const Geom& g, const LocalOps& ops, const double* R1
 
 cudaError_t launch_recover(const Geom& g, const LocalOps& ops, const double* Z, const double* R1,
                            const double* tau_edge, const double* qhat, double beta, double inv_aii,
-                           double* Q, double* Lst, cudaStream_t s) {
-#define CALL(P) recover_launch<P>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s)
+                           double* Q, double* Lst, cudaStream_t s, float* Q32) {
+#define CALL(P) recover_launch<P>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s, Q32)
     switch (g.P) {
         case 2: return CALL(2);
         case 3: return CALL(3);
