@@ -255,7 +255,9 @@ def _algorithmic(N, k, cls, precision="fp64", dense=False, local="fp64", mf=Fals
         nb = 3 * (4 * P - 4)
         if dense:
             return n_el * (NV * nb * 8 + 4 * NV * 8) + n_edges * NF * 8, n_el * 2 * NV * nb
-        return op_b + n_el * 4 * NV * 8 + n_edges * NF * 8, n_el * Np * (40 if pair else 2 * Np + 8 * P + 32)
+        q_b = 4 if precision == "mixed" and local in ("f32x2", "fp64") else 8   # the mixed form writes Q in FP32
+        return (op_b + n_el * (3 * NV * 8 + NV * q_b) + n_edges * NF * 8,
+                n_el * Np * (40 if pair else 2 * Np + 8 * P + 32))
     if cls == "dg":
         return n_el * (2 * NV + Np) * 8, n_el * Np * 60
     return None, None

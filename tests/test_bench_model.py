@@ -6,7 +6,8 @@ the per-unit counts written out by hand from the layouts (no GPU):
   flops per row (the identity adds x).
 * Schur-complement local solves: per element the (phi, phi) block of A^{-1} ((k+1)^4 numbers)
   and four numbers per node, R1 in and Z out (condensation) or Z, R1 in and Q, L out
-  (recovery), eight bytes each, plus the trace traffic per edge.
+  (recovery), eight bytes each -- Q four in the mixed form, whose DG residual reads it in FP32 --
+  plus the trace traffic per edge.
 * dense route: the whole (3 (k+1)^2)^2 A^{-1} for the condensation and its boundary columns for
   the recovery.
 """
@@ -45,7 +46,7 @@ def test_local_solve_bytes(bench, k):
     sc, _ = bench._algorithmic(N, k, "condense", "mixed", dense=False, local="f32x2")
     sr, _ = bench._algorithmic(N, k, "recover", "mixed", dense=False, local="f32x2")
     assert sc == n_el * ((Np * Np + 4 * Np) * 8 + 2 * NV * 8) + edges * NF * 8 * 3
-    assert sr == n_el * ((Np * Np + 4 * Np) * 8 + 4 * NV * 8) + edges * NF * 8
+    assert sr == n_el * ((Np * Np + 4 * Np) * 8 + 3 * NV * 8 + NV * 4) + edges * NF * 8
     dc, _ = bench._algorithmic(N, k, "condense", "fp64", dense=True)
     dr, _ = bench._algorithmic(N, k, "recover", "fp64", dense=True)
     nb = 3 * (4 * P - 4)                                          # boundary columns of A^{-1}
