@@ -583,10 +583,14 @@ cudaError_t cycle_enqueue(hdgdg_sim* sim, const double* g, cudaStream_t st, bool
     if (e == cudaSuccess) e = launch_gmres_update(V, n, ctl, sim->xt, n, st);
     // the true residual w = g - S~ x~ that ends the cycle, and ||w||^2
     if (kMixed && matrix_free(&sim->cfg)) {   // matrix-free in FP32-pair arithmetic, then the norm
-        if (e == cudaSuccess)
-            e = sim->ens ? launch_ens_mf_residual(*sim->ens, sim->mf, n, sim->xt, g, sim->w, st)
-                         : launch_mf_residual(sim->g, sim->mf, sim->xt, g, sim->w, beta_of(sim), st);
-        if (e == cudaSuccess) e = launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st);
+        if (e == cudaSuccess) {
+            if (sim->ens) {
+                e = launch_ens_mf_residual(*sim->ens, sim->mf, n, sim->xt, g, sim->w, st);
+                if (e == cudaSuccess) e = launch_multidot(sim->w, 0, 1, sim->w, n, sim->red, dv_nrm(sim), st);
+            } else {   // the last pass also forms ||w||^2
+                e = launch_mf_residual(sim->g, sim->mf, sim->xt, g, sim->w, beta_of(sim), st, sim->red, dv_nrm(sim));
+            }
+        }
     } else if (kMixed && sim->Stil_lo) {   // one fused FP32-pair pass
         if (e == cudaSuccess)
             e = launch_residual_norm_x2(sim->g, sim->Stil32, sim->Stil_lo, sim->Scol, sim->xt, g, sim->w,

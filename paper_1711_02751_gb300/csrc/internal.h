@@ -314,9 +314,13 @@ struct MfOps {
 // With 3(k + 1) a multiple of 4, x must start on 16 bytes (cudaErrorMisalignedAddress otherwise).
 cudaError_t launch_mf_inner(const Geom& g, const MfOps& op, const float* x, float* y, double beta, cudaStream_t s,
                             const int* done = nullptr, bool y_zeroed = false);
-// w = rhs - S M^{-1} x in FP64-class FP32-pair arithmetic (the refinement's true residual)
+// w = rhs - S M^{-1} x in FP64-class FP32-pair arithmetic (the refinement's true residual); with
+// nrm_scratch (a reduction scratch, as launch_multidot's) also ||w||^2 into *nrm_out, in the last pass
 cudaError_t launch_mf_residual(const Geom& g, const MfOps& op, const double* x, const double* rhs, double* w,
-                               double beta, cudaStream_t s);
+                               double beta, cudaStream_t s, double* nrm_scratch = nullptr, double* nrm_out = nullptr);
+// w = rhs - (hm + hp) and ||w||^2 (16-byte aligned vectors; cudaErrorMisalignedAddress otherwise)
+cudaError_t launch_sum_residual_norm(size_t n, const double* hm, const double* hp, const double* rhs, double* w,
+                                     double* scratch, double* out, cudaStream_t s);
 // y = S x (no preconditioner), FP64-class
 cudaError_t launch_mf_plain(const Geom& g, const MfOps& op, const double* x, double* y, double beta, cudaStream_t s);
 // Whether tile t of the inner element pass can run at degree P - 1, and its elements per block and

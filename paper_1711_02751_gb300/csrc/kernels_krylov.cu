@@ -542,6 +542,44 @@ guess_gram_dev_kernel(size_t n, const double* __restrict__ g, const DevHist* __r
     }
 }
 
+// The refinement residual's last pass: w = rhs - (hm + hp) (the two halves of each row of S~ x~,
+// minus side first, as mf_sum_kernel) and ||w||^2, 16-byte lanes, grid sum finished by the last block.
+__global__ void __launch_bounds__(kDotThreads)
+sum_residual_norm_kernel(size_t n, const double* __restrict__ hm, const double* __restrict__ hp,
+                         const double* __restrict__ rhs, double* __restrict__ w, double* __restrict__ scratch,
+                         double* __restrict__ out) {
+    unsigned* counter = reinterpret_cast<unsigned*>(scratch);
+    double* partial = scratch + 1;
+    __shared__ double sh[kDotThreads / 32];
+    double acc = 0.0;
+    for (size_t iv = blockIdx.x * (size_t)kDotThreads + threadIdx.x; iv < n / 2; iv += (size_t)gridDim.x * kDotThreads) {
+        const double2 a = reinterpret_cast<const double2*>(hm)[iv], b = reinterpret_cast<const double2*>(hp)[iv];
+        const double2 g = reinterpret_cast<const double2*>(rhs)[iv];
+        const double r0 = g.x - (a.x + b.x), r1 = g.y - (a.y + b.y);
+        reinterpret_cast<double2*>(w)[iv] = make_double2(r0, r1);
+        acc += r0 * r0;
+        acc += r1 * r1;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) {   // an odd last entry
+        const double r = rhs[n - 1] - (hm[n - 1] + hp[n - 1]);
+        w[n - 1] = r;
+        acc += r * r;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const double v = warp_sum(acc);
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kDotThreads / 32; ++k) t += sh[k];
+        partial[blockIdx.x] = t;
+    }
+    if (last_block_arrives(counter)) {
+        reduce_partials(partial, gridDim.x, 1, 0, 1, out);
+        if (threadIdx.x == 0) *counter = 0u;
+    }
+}
+
 struct GuessCoef {
     double c[7][6];
 };
@@ -787,6 +825,16 @@ cudaError_t multidot_impl(const T* V, size_t ldv, int nv, const T* w, size_t n, 
 }  // namespace
 
 size_t guess_scratch_doubles() { return 1 + (size_t)kDotBlocks * kGramSlots; }
+
+cudaError_t launch_sum_residual_norm(size_t n, const double* hm, const double* hp, const double* rhs, double* w,
+                                     double* scratch, double* out, cudaStream_t s) {
+    for (const void* p : {static_cast<const void*>(hm), static_cast<const void*>(hp), static_cast<const void*>(rhs),
+                          static_cast<const void*>(w)})
+        if (reinterpret_cast<uintptr_t>(p) % 16 != 0) return cudaErrorMisalignedAddress;
+    sum_residual_norm_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(n, hm, hp, rhs, w, scratch, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_guess_gram(size_t n, const double* g, const GuessTerms& t, double* scratch, double* out,
                               cudaStream_t s) {

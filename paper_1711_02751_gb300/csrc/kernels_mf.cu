@@ -540,7 +540,7 @@ void mf_elem_tile(int t, const Geom& g, const void* S, const void* aux, const vo
 template <int P, class A, int MODE>
 cudaError_t mf_launch(const Geom& g, const MfOps& op, const void* S, const void* aux, const void* EG, const void* x,
                       const double* rhs, MfVec<MODE>* out, double beta, cudaStream_t s, const int* done,
-                      bool out_zeroed = false) {
+                      bool out_zeroed = false, double* nrm_scratch = nullptr, double* nrm_out = nullptr) {
     using T = typename A::T;
     using TO = MfVec<MODE>;
     constexpr int NF = 3 * P;
@@ -577,6 +577,14 @@ cudaError_t mf_launch(const Geom& g, const MfOps& op, const void* S, const void*
                              MODE == kMfResidual ? op.tau2 : static_cast<const void*>(op.tau), yv, hm, hp, beta, s,
                              done, op.Minv);
     const size_t n = (size_t)g.n_edges * NF;
+    if constexpr (MODE == kMfResidual) {
+        if (nrm_scratch) {   // the last pass with ||w||^2
+            count_launches(2);
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            return launch_sum_residual_norm(n, hm, hp, rhs, out, nrm_scratch, nrm_out, s);
+        }
+    }
     mf_sum_kernel<TO, MODE == kMfResidual><<<sum_grid(n), 256, 0, s>>>(n, hm, hp, rhs, out, done);
     count_launches(MODE != kMfPlain ? 3 : 2);
     return cudaGetLastError();
@@ -673,9 +681,11 @@ cudaError_t launch_mf_inner(const Geom& g, const MfOps& op, const float* x, floa
 }
 
 cudaError_t launch_mf_residual(const Geom& g, const MfOps& op, const double* x, const double* rhs, double* w,
-                               double beta, cudaStream_t s) {
-#define CASE(P) \
-    case P: return mf_launch<P, ArithF2, kMfResidual>(g, op, op.S2, op.aux2, op.EG2, x, rhs, w, beta, s, nullptr);
+                               double beta, cudaStream_t s, double* nrm_scratch, double* nrm_out) {
+#define CASE(P)                                                                                                 \
+    case P:                                                                                                     \
+        return mf_launch<P, ArithF2, kMfResidual>(g, op, op.S2, op.aux2, op.EG2, x, rhs, w, beta, s, nullptr, \
+                                                  false, nrm_scratch, nrm_out);
     switch (g.P) {
         CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9)
         default: return cudaErrorInvalidValue;
