@@ -960,10 +960,16 @@ cudaError_t step_enqueue_graph(hdgdg_sim* sim, cudaStream_t st, StepGraph& sg) {
                 if (sim->A[i][j] != 0.0 && !sim->cfg.linear_only) { t.X[t.n] = sim->NLs[j]; t.c[t.n++] = sim->A[i][j]; }
                 if (sim->At[i][j] != 0.0) { t.X[t.n] = sim->Ls[j]; t.c[t.n++] = sim->At[i][j]; }
             }
-            e = launch_combine(n3, sim->q, t, sim->R1, nullptr, st);
-            if (e == cudaSuccess)
-                e = sim->ens ? launch_ens_condense(*sim->ens, sim->R1, sim->Z, sim->gvec, st)
-                             : launch_condense(sim->g, sim->ops, sim->R1, sim->phiB, sim->tau, sim->Z, sim->gvec, st, 0.0);
+            if (sim->ens || t.n > kR1FusedTerms) {
+                e = launch_combine(n3, sim->q, t, sim->R1, nullptr, st);
+                if (e == cudaSuccess)
+                    e = sim->ens ? launch_ens_condense(*sim->ens, sim->R1, sim->Z, sim->gvec, st)
+                                 : launch_condense(sim->g, sim->ops, sim->R1, sim->phiB, sim->tau, sim->Z,
+                                                   sim->gvec, st, 0.0);
+            } else {   // the Schur kernels form R1 as they read it; the others after a combine launch
+                const R1Source src{sim->q, t};
+                e = launch_condense(sim->g, sim->ops, sim->R1, sim->phiB, sim->tau, sim->Z, sim->gvec, st, 0.0, &src);
+            }
             if (e == cudaSuccess) {
                 if (sim->cfg.precision == HDGDG_MIXED) e = solve_enqueue_graph<float>(sim, sim->gvec, sim->lam, i, st, sg);
                 else e = solve_enqueue_graph<double>(sim, sim->gvec, sim->lam, i, st, sg);

@@ -274,8 +274,17 @@ cudaError_t launch_schur_setup(const Geom& g, const double* Ainv, const double* 
                                double dta, bool f32x2, void* S, void* aux, void* EG, cudaStream_t s);
 // Condensation: Z = A^{-1} R1 per element, then g = -C Z edge by edge (pointwise rows).
 // t: time of the prescribed boundary traces (Dirichlet boundaries only)
+// The stage's right-hand side formed inside the condensation (the Schur-complement kernels):
+// R1 = base + sum_k t.c[k] t.X[k], term by term as launch_combine, written to R1 as it is read;
+// at most kR1FusedTerms terms (an ARS2 stage has three).
+constexpr int kR1FusedTerms = 4;
+struct R1Source {
+    const double* base = nullptr;   // nullptr: R1 is read as it stands
+    CombineTerms t{};
+};
 cudaError_t launch_condense(const Geom& g, const LocalOps& ops, const double* R1, const double* phiB,
-                            const double* tau_edge, double* Z, double* gvec, cudaStream_t s, double t = 0.0);
+                            const double* tau_edge, double* Z, double* gvec, cudaStream_t s, double t = 0.0,
+                            const R1Source* src = nullptr);
 // Recovery: Q = Z + beta A^{-1} (tau qhat) on boundary nodes; Lst = (Q - R1) / a_ii.
 cudaError_t launch_recover(const Geom& g, const LocalOps& ops, const double* Z, const double* R1,
                            const double* tau_edge, const double* qhat, double beta, double inv_aii,

@@ -534,12 +534,41 @@ __global__ void schur_eg_kernel(Geom g, double dta, typename A::T* __restrict__ 
 }
 
 
+// The three fields of R1 at node o (field stride fs): read, or (src.base set) formed term by term
+// as launch_combine forms them and written back to R1.  Every load is issued before the first
+// store so that they overlap (R1 may alias nothing the terms read, but the compiler cannot know).
+__device__ __forceinline__ void r1_fields(const double* __restrict__ R1, const R1Source& src, size_t o, size_t fs,
+                                          double v[3]) {
+    if (!src.base) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c] = R1[o + c * fs];
+        return;
+    }
+    double x[kR1FusedTerms][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = src.base[o + c * fs];
+#pragma unroll
+    for (int k = 0; k < kR1FusedTerms; ++k)   // constant indices keep the terms in the parameter bank
+        if (k < src.t.n) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) x[k][c] = src.t.X[k][o + c * fs];
+        }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+        for (int k = 0; k < kR1FusedTerms; ++k)
+            if (k < src.t.n) v[c] += src.t.c[k] * x[k][c];
+        const_cast<double*>(R1)[o + c * fs] = v[c];
+    }
+}
+
 // Z = A^{-1} R1 through the Schur complement: one thread per (element, node), EPB elements per block.
 template <int P, int EPB, class A>
 __device__ __forceinline__ void schur_condense_body(int bid, const Geom& g, const typename A::T* __restrict__ S,
                                                     const typename A::T* __restrict__ aux,
                                                     const typename A::T* __restrict__ EG,
-                                                    const double* __restrict__ R1, double* __restrict__ Z) {
+                                                    const double* __restrict__ R1, double* __restrict__ Z,
+                                                    const R1Source& src = R1Source{}) {
     using T = typename A::T;
     constexpr int Np = P * P;
     __shared__ SchurSmem<P, EPB, A> sm;
@@ -549,9 +578,11 @@ __device__ __forceinline__ void schur_condense_body(int bid, const Geom& g, cons
     const size_t fs = (size_t)g.n_el * Np, o = (size_t)e * Np + n;
     T x0{}, xU{}, xV{};
     if (live) {
-        x0 = A::from(R1[o]);
-        xU = A::from(R1[fs + o]);
-        xV = A::from(R1[2 * fs + o]);
+        double r[3];
+        r1_fields(R1, src, o, fs, r);
+        x0 = A::from(r[0]);
+        xU = A::from(r[1]);
+        xV = A::from(r[2]);
     }
     T phi{}, U{}, V{};
     schur_solve<P, EPB, A>(sm, g, e, le, n, live, S, aux, EG, x0, xU, xV, phi, U, V);
@@ -566,8 +597,8 @@ template <int P, int EPB, class A>
 __global__ void __launch_bounds__(EPB * P * P)
     schur_condense_kernel(Geom g, const typename A::T* __restrict__ S, const typename A::T* __restrict__ aux,
                           const typename A::T* __restrict__ EG, const double* __restrict__ R1,
-                          double* __restrict__ Z) {
-    schur_condense_body<P, EPB, A>(blockIdx.x, g, S, aux, EG, R1, Z);
+                          double* __restrict__ Z, R1Source src) {
+    schur_condense_body<P, EPB, A>(blockIdx.x, g, S, aux, EG, R1, Z, src);
 }
 
 // Q = Z + beta A^{-1} (tau qhat), Lst = (Q - R1) / a_ii through the Schur complement.
@@ -630,7 +661,7 @@ template <int P, int EPB, class A>
 __global__ void __launch_bounds__(EPB * P * P)
     schur_condense_staged_kernel(Geom g, const typename A::T* __restrict__ S, const typename A::T* __restrict__ aux,
                                  const typename A::T* __restrict__ EG, const double* __restrict__ R1,
-                                 double* __restrict__ Z, unsigned* err) {
+                                 double* __restrict__ Z, unsigned* err, R1Source src) {
     using T = typename A::T;
     constexpr int Np = P * P;
     __shared__ SchurSmem<P, EPB, A> sm;
@@ -643,9 +674,11 @@ __global__ void __launch_bounds__(EPB * P * P)
     const size_t fs = (size_t)g.n_el * Np, o = (size_t)e * Np + n;
     T x0{}, xU{}, xV{};
     if (live) {
-        x0 = A::from(R1[o]);
-        xU = A::from(R1[fs + o]);
-        xV = A::from(R1[2 * fs + o]);
+        double r[3];
+        r1_fields(R1, src, o, fs, r);
+        x0 = A::from(r[0]);
+        xU = A::from(r[1]);
+        xV = A::from(r[2]);
     }
     if (!so.wait(err)) return;
     SchurNode<A> nd;
@@ -721,11 +754,12 @@ constexpr int schur_epb_for(int threads) {
 }
 
 template <int P, class A, int TILE>
-void schur_condense_t(const Geom& g, const LocalOps& ops, const double* R1, double* Z, cudaStream_t s) {
+void schur_condense_t(const Geom& g, const LocalOps& ops, const double* R1, double* Z, cudaStream_t s,
+                      const R1Source& src) {
     using T = typename A::T;
     constexpr int EPB = schur_epb_for<P>(schur_tile_threads(TILE));
     schur_condense_kernel<P, EPB, A><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(
-        g, static_cast<const T*>(ops.S), static_cast<const T*>(ops.aux), static_cast<const T*>(ops.EG), R1, Z);
+        g, static_cast<const T*>(ops.S), static_cast<const T*>(ops.aux), static_cast<const T*>(ops.EG), R1, Z, src);
     count_launches(1);
 }
 
@@ -747,23 +781,24 @@ constexpr bool schur_staged_ok() {
 }
 
 template <int P, class A>
-void schur_condense(const Geom& g, const LocalOps& ops, const double* R1, double* Z, cudaStream_t s) {
+void schur_condense(const Geom& g, const LocalOps& ops, const double* R1, double* Z, cudaStream_t s,
+                    const R1Source& src = R1Source{}) {
     if constexpr (schur_staged_ok<P, A>()) {
         if (ops.schur_tile_c == 3) {
             using T = typename A::T;
             constexpr int EPB = schur_epb_for<P>(128);
             schur_condense_staged_kernel<P, EPB, A><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(
                 g, static_cast<const T*>(ops.S), static_cast<const T*>(ops.aux), static_cast<const T*>(ops.EG), R1, Z,
-                reinterpret_cast<unsigned*>(ops.error));
+                reinterpret_cast<unsigned*>(ops.error), src);
             count_launches(1);
             return;
         }
     }
     if constexpr (P >= 3 && P <= 5) {
-        if (ops.schur_tile_c == 1) return schur_condense_t<P, A, 1>(g, ops, R1, Z, s);
-        if (ops.schur_tile_c == 2) return schur_condense_t<P, A, 2>(g, ops, R1, Z, s);
+        if (ops.schur_tile_c == 1) return schur_condense_t<P, A, 1>(g, ops, R1, Z, s, src);
+        if (ops.schur_tile_c == 2) return schur_condense_t<P, A, 2>(g, ops, R1, Z, s, src);
     }
-    schur_condense_t<P, A, 0>(g, ops, R1, Z, s);
+    schur_condense_t<P, A, 0>(g, ops, R1, Z, s, src);
 }
 
 template <int P, class A>
@@ -985,13 +1020,21 @@ cudaError_t autotune_x2(const Geom& g, LocalOps& ops, double* R1, double* Z, con
 
 template <int P>
 cudaError_t condense_launch(const Geom& g, const LocalOps& ops, const double* R1, const double* phiB,
-                            const double* tau_edge, double* Z, double* gvec, cudaStream_t s, double t) {
+                            const double* tau_edge, double* Z, double* gvec, cudaStream_t s, double t,
+                            const R1Source* src) {
     constexpr int NV = 3 * P * P;
     constexpr int EPB = (256 / NV) > 0 ? 256 / NV : 1;
     const int blocks = (g.n_el + EPB - 1) / EPB;
+    if (src && src->base && !ops.schur) {   // the other kernels read R1 as it stands: form it first
+        const cudaError_t e = launch_combine((size_t)3 * g.n_el * g.Np, src->base, src->t, const_cast<double*>(R1),
+                                             nullptr, s);
+        if (e != cudaSuccess) return e;
+    }
+    const R1Source none{};
     if (ops.schur) {
-        if (ops.kind == 3) schur_condense<P, ArithF2>(g, ops, R1, Z, s);
-        else schur_condense<P, ArithF64>(g, ops, R1, Z, s);
+        const R1Source& rs = src ? *src : none;
+        if (ops.kind == 3) schur_condense<P, ArithF2>(g, ops, R1, Z, s, rs);
+        else schur_condense<P, ArithF64>(g, ops, R1, Z, s, rs);
     } else if (ops.kind == 2 || ops.kind == 4) {
         cudaError_t e = ops.kind == 2 ? launch_local_tc(g, 0, ops.image, R1, nullptr, nullptr, nullptr, 0.0, 0.0, Z,
                                                         nullptr, ops.error, s)
@@ -1227,8 +1270,10 @@ cudaError_t launch_assemble_trace(const Geom& g, const double* Se, double* S7, d
 }
 
 cudaError_t launch_condense(const Geom& g, const LocalOps& ops, const double* R1, const double* phiB,
-                            const double* tau_edge, double* Z, double* gvec, cudaStream_t s, double t) {
-#define CALL(P) condense_launch<P>(g, ops, R1, phiB, tau_edge, Z, gvec, s, t)
+                            const double* tau_edge, double* Z, double* gvec, cudaStream_t s, double t,
+                            const R1Source* src) {
+    if (src && src->base && (src->t.n < 0 || src->t.n > kR1FusedTerms)) return cudaErrorInvalidValue;
+#define CALL(P) condense_launch<P>(g, ops, R1, phiB, tau_edge, Z, gvec, s, t, src)
     switch (g.P) {
         case 2: return CALL(2);
         case 3: return CALL(3);
