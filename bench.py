@@ -30,7 +30,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DOF-steps/s of IMEX HDG-DG at rel L2≤1e-6 vs FP64 form; p50/p99 latency"
 UNIT = "DOF-steps/s"
-WORKLOADS = {"large512": (512, 3), "bump8": (8, 2), "mid128": (128, 3), "flat512": (512, 3), "flat256": (256, 3)}
+WORKLOADS = {"large512": (512, 3), "bump8": (8, 2), "mid128": (128, 3), "mid256": (256, 3), "flat512": (512, 3),
+             "flat256": (256, 3)}
 CPU_SAMPLE = (64, 3)       # oracle sample: the large512 recipe on 64 x 64, k = 3
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes of one Blackwell SM (4 partitions x 32)
@@ -73,6 +74,8 @@ def _args():
                     help="mixed form: refinement residual in FP32-pair (FP64-class) arithmetic")
     ap.add_argument("--trace-operator", type=int, default=1, choices=[0, 1],
                     help="mixed form's trace operator: 1 matrix-free (element by element), 0 assembled matrix")
+    ap.add_argument("--trace-tile", type=int, default=-1,
+                    help="inner matrix-free pass tile for every form (-1: the create-time autotuner's)")
     ap.add_argument("--local-dense", type=int, default=0, choices=[0, 1],
                     help="local solves: 0 Schur complement on phi (library default), 1 dense A^-1")
     ap.add_argument("--breakdown-steps", type=int, default=10,
@@ -229,11 +232,18 @@ class ClockSampler:
 
 
 # ---- roofline --------------------------------------------------------------------------------
-def _algorithmic(N, k, cls, precision="fp64", dense=False, local="fp64", mf=False):
+# ARS(2,3,2)'s implicit stages combine 1 and 3 vectors into their right-hand side R1 (stage 1:
+# a_10 N_0; stage 2: a_20 N_0, a_21 N_1, a~_21 L_1), which the FP32-pair Schur condensation forms
+# itself.
+ARS2_R1_TERMS = (1 + 3) / 2
+
+
+def _algorithmic(N, k, cls, precision="fp64", dense=False, local="fp64", mf=False, r1_terms=0.0):
     """(bytes, flops) one launch group of a kernel class moves / performs.  mf: the mixed form's
     matrix-free trace operator (per edge its FP16 M^{-1} block and scale, tau in FP32 and x, y
     once; per element the FP32 Schur operators; the flops count the M^{-1} products, the local
-    solve and the lift)."""
+    solve and the lift).  r1_terms: the condensation forms R1 = q + sum_k c_k X_k itself from
+    that many terms on average (reads q and the terms, writes R1) instead of reading R1."""
     P = k + 1
     NF, NV, Np = 3 * P, 3 * P * P, P * P
     n_el, n_edges = N * N, 2 * N * N
@@ -248,9 +258,11 @@ def _algorithmic(N, k, cls, precision="fp64", dense=False, local="fp64", mf=Fals
     op_b = n_el * NV * NV * 8 if dense else n_el * (Np * Np + 4 * Np) * 8
     # FP32-pair Schur solves: the FP64 pipe only splits the inputs and forms the outputs
     pair = local == "f32x2" and not dense
-    if cls == "condense":   # operator once, R1 in, Z out; then Z face values + phiB in, g out
-        return (op_b + n_el * 2 * NV * 8 + n_edges * NF * 8 * 3,
-                n_el * 2 * NV * NV if dense else n_el * Np * (12 if pair else 2 * Np + 8 * P + 26))
+    if cls == "condense":   # operator once, R1 in (or formed), Z out; then Z face values + phiB in, g out
+        vec = 2 if not r1_terms else 3 + r1_terms
+        return (op_b + int(n_el * vec * NV * 8) + n_edges * NF * 8 * 3,
+                (n_el * 2 * NV * NV if dense else n_el * Np * (12 if pair else 2 * Np + 8 * P + 26))
+                + int(n_el * NV * 2 * r1_terms))
     if cls == "recover":    # operator (dense: its boundary columns), Z, R1 in, Q, L out, traces in
         nb = 3 * (4 * P - 4)
         if dense:
@@ -374,12 +386,12 @@ def _e2e(sim, stream, steps, dist, h, hu, hv):
 
 
 def _roofline(N, k, ktimes, precision, fp64_tflops, hbm, dense=False, local="fp64", fp32_peak=(None, 0, 0.0),
-              mf=False):
+              mf=False, r1_terms=0.0):
     dom = max((c for c in ktimes if ktimes[c][1] > 0 and _algorithmic(N, k, c, precision, dense, local, mf)[0]),
               key=lambda c: ktimes[c][0])
     tot_ms, n_l = ktimes[dom]
     avg_s = tot_ms / n_l / 1e3
-    byt, flo = _algorithmic(N, k, dom, precision, dense, local, mf)
+    byt, flo = _algorithmic(N, k, dom, precision, dense, local, mf, r1_terms)
     fp32_tflops, n_sm, mhz = fp32_peak
     alu_peak = fp64_tflops if (precision == "fp64" or dom != "spmv" or not fp32_tflops) else fp32_tflops
     t_hbm, t_alu = byt / (hbm * 1e9), flo / (alu_peak * 1e12)
@@ -772,6 +784,8 @@ def main():
                      residual_f32x2=bool(args.residual_f32x2) and precision == "mixed",
                      local_dense=bool(args.local_dense),
                      trace_operator=_trace_operator(args, precision))
+        if args.trace_tile >= 0 and _trace_operator(args, precision):
+            sim.set_trace_tile(args.trace_tile)
         sim.set_state(h, hu, hv)
         for _ in range(args.warmup):
             sim.step(1)
@@ -815,6 +829,8 @@ def main():
     summary = {}
     for p, f in forms.items():
         r = f["r"]
+        # the FP32-pair Schur condensation forms the stage right-hand side itself (ARS2, nonlinear)
+        r1 = ARS2_R1_TERMS if (p == "mixed" and args.local == "f32x2" and not args.local_dense) else 0.0
         summary[p] = {"value": job_value(world, dof, args.steps, r["ms_total"]),
                       "ms_per_step": r["ms_total"] / args.steps,
                       "krylov_iterations_per_stage": r["stats"]["krylov_iterations"] / max(1, 2 * r["stats"]["steps"]),
@@ -822,10 +838,10 @@ def main():
                       "breakdown_run": r["breakdown"],
                       "roofline": _roofline(N, k, r["ktimes"], p, fp64_tflops, hbm, bool(args.local_dense),
                                             args.local if p == "mixed" else "fp64", fp32_peak,
-                                            bool(_trace_operator(args, p))),
+                                            bool(_trace_operator(args, p)), r1),
                       "local_roofline": {c: _roofline(N, k, {c: r["ktimes"][c]}, p, fp64_tflops, hbm,
                                                       bool(args.local_dense), args.local if p == "mixed" else "fp64",
-                                                      fp32_peak, bool(_trace_operator(args, p)))
+                                                      fp32_peak, bool(_trace_operator(args, p)), r1)
                                          for c in ("condense", "recover") if r["ktimes"].get(c, (0, 0))[1] > 0},
                       "e2e": f["e2e"], "gpu_launches": r["launches"],
                       "local_tiles": {"condense": r["stats"].get("local_tile_condense", 0),

@@ -822,13 +822,23 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
 
 
 // One implicit stage: R1 (device) -> Q, Lst = dt M^{-1} L (device); qhat left in sim->lam.
+// Whether an implicit stage's condensation forms R1 from its terms (launch_condense's src): the
+// FP32-pair Schur kernels, whose time goes to FP32 work and latency, absorb the combination's
+// streams; the FP64 ones are bound by the FP64 pipe, which its FMAs would lengthen.
+bool r1_fused(const hdgdg_sim* sim, const CombineTerms& t) {
+    return sim->ops.schur && sim->ops.kind == 3 && t.n <= kR1FusedTerms;
+}
+
+// src: R1 is formed by the condensation from these terms (launch_condense) instead of read.
 hdgdg_status stage_solve_dev(hdgdg_sim* sim, const double* R1, double* Q, double* Lst, int* its,
-                             double t_stage = 0.0, int stage = -1, float* Q32 = nullptr) {
+                             double t_stage = 0.0, int stage = -1, float* Q32 = nullptr,
+                             const R1Source* src = nullptr) {
     NvtxRange nv("stage_solve");
     double rr;
     {
         TimedGroup tg(sim, HDGDG_KT_CONDENSE);
-        CU(launch_condense(sim->g, sim->ops, R1, sim->phiB, sim->tau, sim->Z, sim->gvec, sim->stream, t_stage));
+        CU(launch_condense(sim->g, sim->ops, R1, sim->phiB, sim->tau, sim->Z, sim->gvec, sim->stream, t_stage,
+                           src));
     }
     if (sim->cfg.precision == HDGDG_MIXED) TRY(gmres_solve<float>(sim, sim->gvec, sim->lam, its, &rr, stage));
     else TRY(gmres_solve<double>(sim, sim->gvec, sim->lam, its, &rr, stage));
@@ -960,13 +970,13 @@ cudaError_t step_enqueue_graph(hdgdg_sim* sim, cudaStream_t st, StepGraph& sg) {
                 if (sim->A[i][j] != 0.0 && !sim->cfg.linear_only) { t.X[t.n] = sim->NLs[j]; t.c[t.n++] = sim->A[i][j]; }
                 if (sim->At[i][j] != 0.0) { t.X[t.n] = sim->Ls[j]; t.c[t.n++] = sim->At[i][j]; }
             }
-            if (sim->ens || t.n > kR1FusedTerms) {
+            if (sim->ens || !r1_fused(sim, t)) {
                 e = launch_combine(n3, sim->q, t, sim->R1, nullptr, st);
                 if (e == cudaSuccess)
                     e = sim->ens ? launch_ens_condense(*sim->ens, sim->R1, sim->Z, sim->gvec, st)
                                  : launch_condense(sim->g, sim->ops, sim->R1, sim->phiB, sim->tau, sim->Z,
                                                    sim->gvec, st, 0.0);
-            } else {   // the Schur kernels form R1 as they read it; the others after a combine launch
+            } else {   // the FP32-pair Schur condensation forms R1 as it reads it
                 const R1Source src{sim->q, t};
                 e = launch_condense(sim->g, sim->ops, sim->R1, sim->phiB, sim->tau, sim->Z, sim->gvec, st, 0.0, &src);
             }
@@ -1171,12 +1181,15 @@ hdgdg_status one_step(hdgdg_sim* sim) {
                 if (sim->A[i][j] != 0.0 && !sim->cfg.linear_only) { t.X[t.n] = sim->NLs[j]; t.c[t.n++] = sim->A[i][j]; }
                 if (sim->At[i][j] != 0.0) { t.X[t.n] = sim->Ls[j]; t.c[t.n++] = sim->At[i][j]; }
             }
-            {
+            // the FP32-pair Schur condensation forms R1 itself, as in the step graph
+            const bool fused = r1_fused(sim, t);
+            if (!fused) {
                 TimedGroup tg(sim, HDGDG_KT_COMBINE);
                 CU(launch_combine(n3, sim->q, t, sim->R1, nullptr, st));
             }
+            const R1Source src{sim->q, t};
             int its = 0;
-            TRY(stage_solve_dev(sim, sim->R1, sim->Qs, sim->Ls[i], &its, ti, i, sim->Qs32));
+            TRY(stage_solve_dev(sim, sim->R1, sim->Qs, sim->Ls[i], &its, ti, i, sim->Qs32, fused ? &src : nullptr));
             Qi = sim->Qs;
         }
         if (!sim->cfg.linear_only) {

@@ -46,6 +46,10 @@ def test_local_solve_bytes(bench, k):
     sc, _ = bench._algorithmic(N, k, "condense", "mixed", dense=False, local="f32x2")
     sr, _ = bench._algorithmic(N, k, "recover", "mixed", dense=False, local="f32x2")
     assert sc == n_el * ((Np * Np + 4 * Np) * 8 + 2 * NV * 8) + edges * NF * 8 * 3
+    # forming R1 from q and two terms on average: q, the terms and R1 out replace R1 in
+    sf, ff = bench._algorithmic(N, k, "condense", "mixed", dense=False, local="f32x2", r1_terms=2.0)
+    assert sf == sc + n_el * NV * 8 * 3 and ff == n_el * Np * 12 + n_el * NV * 4
+    assert bench.ARS2_R1_TERMS == 2.0
     assert sr == n_el * ((Np * Np + 4 * Np) * 8 + 3 * NV * 8 + NV * 4) + edges * NF * 8
     dc, _ = bench._algorithmic(N, k, "condense", "fp64", dense=True)
     dr, _ = bench._algorithmic(N, k, "recover", "fp64", dense=True)
