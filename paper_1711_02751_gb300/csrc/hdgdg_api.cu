@@ -358,6 +358,10 @@ struct hdgdg_sim {
     float* tau32 = nullptr;
     StepStats* sstats = nullptr;          // counters of the replayed step
     cudaStream_t body_stream = nullptr;   // captures the restart-cycle bodies of the conditional nodes
+    // the step graph's branch beside the recovery: each stage's guess-history store (fork and join
+    // events per stage)
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t fork_ev[kMaxStages] = {}, join_ev[kMaxStages] = {};
     std::vector<TimerPair>* capture_sink = nullptr;   // timers of the graph being captured
     unsigned* flags = nullptr;
     double* hbuf = nullptr;   // pinned host scratch
@@ -871,9 +875,10 @@ cudaError_t dg_nl_enqueue(hdgdg_sim* sim, const double* Qi, bool stage_value, do
 // start, the restart cycles inside a conditional while node (body captured on the handle's body
 // stream), the counters, the back-transformation and the history copy into the slot that becomes
 // the newest when the host rotates the history after the step.
+// defer_hist: the history store is left to the caller (step_enqueue_graph's side branch).
 template <typename T>
 cudaError_t solve_enqueue_graph(hdgdg_sim* sim, const double* g, double* qhat, int stage, cudaStream_t st,
-                                StepGraph& sg) {
+                                StepGraph& sg, bool defer_hist = false) {
     constexpr bool kMixed = sizeof(T) == sizeof(float);
     const size_t n = sim->plan.nt;
     const double rtol = sim->cfg.krylov_rtol > 0.0 ? sim->cfg.krylov_rtol : (kMixed ? 1e-9 : 1e-15);
@@ -951,7 +956,7 @@ cudaError_t solve_enqueue_graph(hdgdg_sim* sim, const double* g, double* qhat, i
         else if (kMixed && matrix_free(&sim->cfg)) e = launch_mf_back(sim->g, sim->mf.Minv, sim->xt, qhat, st);
         else e = launch_block_diag(sim->g, sim->Minv, sim->xt, qhat, st, sim->minv_pairs);
     }
-    if (e == cudaSuccess && history)   // x~ and S~ x~ = g - r into the slot that becomes newest
+    if (e == cudaSuccess && history && !defer_hist)   // x~ and S~ x~ = g - r into the slot that becomes newest
         e = launch_hist_store_dev(n, sim->xt, g, sim->w, sim->dhist + stage, st);
     return e;
 }
@@ -962,9 +967,18 @@ cudaError_t solve_enqueue_graph(hdgdg_sim* sim, const double* g, double* qhat, i
 cudaError_t step_enqueue_graph(hdgdg_sim* sim, cudaStream_t st, StepGraph& sg) {
     const size_t n3 = 3 * sim->plan.n;
     cudaError_t e = cudaMemsetAsync(sim->sstats, 0, sizeof(StepStats), st);
+    // each stage's history store reads x~, g and r, which nothing overwrites before the next
+    // stage's condensation: it runs on a branch beside the recovery and the DG residual
+    const bool branch = !sim->ens && sim->side_stream && guess_order(&sim->cfg) > 0;
+    int pending = -1;   // the stage whose store has not joined yet
     for (int i = 0; i < sim->s && e == cudaSuccess; ++i) {
         const double* Qi = sim->q;
         if (sim->At[i][i] != 0.0) {
+            if (pending >= 0) {
+                e = cudaStreamWaitEvent(st, sim->join_ev[pending], 0);
+                pending = -1;
+                if (e != cudaSuccess) break;
+            }
             CombineTerms t{};
             for (int j = 0; j < i; ++j) {
                 if (sim->A[i][j] != 0.0 && !sim->cfg.linear_only) { t.X[t.n] = sim->NLs[j]; t.c[t.n++] = sim->A[i][j]; }
@@ -981,8 +995,18 @@ cudaError_t step_enqueue_graph(hdgdg_sim* sim, cudaStream_t st, StepGraph& sg) {
                 e = launch_condense(sim->g, sim->ops, sim->R1, sim->phiB, sim->tau, sim->Z, sim->gvec, st, 0.0, &src);
             }
             if (e == cudaSuccess) {
-                if (sim->cfg.precision == HDGDG_MIXED) e = solve_enqueue_graph<float>(sim, sim->gvec, sim->lam, i, st, sg);
-                else e = solve_enqueue_graph<double>(sim, sim->gvec, sim->lam, i, st, sg);
+                if (sim->cfg.precision == HDGDG_MIXED)
+                    e = solve_enqueue_graph<float>(sim, sim->gvec, sim->lam, i, st, sg, branch);
+                else e = solve_enqueue_graph<double>(sim, sim->gvec, sim->lam, i, st, sg, branch);
+            }
+            if (branch && e == cudaSuccess) {
+                e = cudaEventRecord(sim->fork_ev[i], st);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(sim->side_stream, sim->fork_ev[i], 0);
+                if (e == cudaSuccess)
+                    e = launch_hist_store_dev(sim->plan.nt, sim->xt, sim->gvec, sim->w, sim->dhist + i,
+                                              sim->side_stream);
+                if (e == cudaSuccess) e = cudaEventRecord(sim->join_ev[i], sim->side_stream);
+                if (e == cudaSuccess) pending = i;
             }
             if (e == cudaSuccess)
                 e = sim->ens ? launch_ens_recover(*sim->ens, sim->Z, sim->R1, sim->lam, 1.0 / sim->a_ii, sim->Qs,
@@ -993,6 +1017,7 @@ cudaError_t step_enqueue_graph(hdgdg_sim* sim, cudaStream_t st, StepGraph& sg) {
         }
         if (!sim->cfg.linear_only && e == cudaSuccess) e = dg_nl_enqueue(sim, Qi, Qi == sim->Qs, sim->NLs[i], st, 0.0);
     }
+    if (pending >= 0 && e == cudaSuccess) e = cudaStreamWaitEvent(st, sim->join_ev[pending], 0);
     CombineTerms t{};
     for (int i = 0; i < sim->s; ++i) {
         if (sim->b[i] != 0.0 && !sim->cfg.linear_only) { t.X[t.n] = sim->NLs[i]; t.c[t.n++] = sim->b[i]; }
@@ -1311,7 +1336,14 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
     TRY(dalloc(sim, &sim->dhist, kMaxStages));
     CU(cudaMallocHost(&sim->hhist, kMaxStages * sizeof(DevHist)));
     TRY(dalloc(sim, &sim->dls, kLsSlots));
-    if (!c->host_steps) CU(cudaStreamCreateWithFlags(&sim->body_stream, cudaStreamNonBlocking));
+    if (!c->host_steps) {
+        CU(cudaStreamCreateWithFlags(&sim->body_stream, cudaStreamNonBlocking));
+        CU(cudaStreamCreateWithFlags(&sim->side_stream, cudaStreamNonBlocking));
+        for (int i = 0; i < kMaxStages; ++i) {
+            CU(cudaEventCreateWithFlags(&sim->fork_ev[i], cudaEventDisableTiming));
+            CU(cudaEventCreateWithFlags(&sim->join_ev[i], cudaEventDisableTiming));
+        }
+    }
     CU(cudaMallocHost(&sim->hbuf, (4 * (size_t)(p.m + 2) + 16) * sizeof(double)));
     for (int i = 0; i < p.s; ++i) {
         CU(cudaMemsetAsync(sim->NLs[i], 0, 3 * p.n * sizeof(double), sim->stream));
@@ -1569,6 +1601,11 @@ void hdgdg_destroy(hdgdg_sim* sim) {
     for (auto& cg : sim->cycle_graph) drop_graph(sim, cg);
     drop_step_graphs(sim);
     if (sim->body_stream) cudaStreamDestroy(sim->body_stream);
+    if (sim->side_stream) cudaStreamDestroy(sim->side_stream);
+    for (int i = 0; i < kMaxStages; ++i) {
+        if (sim->fork_ev[i]) cudaEventDestroy(sim->fork_ev[i]);
+        if (sim->join_ev[i]) cudaEventDestroy(sim->join_ev[i]);
+    }
     for (cudaEvent_t e : sim->ev_pool) cudaEventDestroy(e);
     for (void* p : sim->allocs) cudaFree(p);
     if (sim->hbuf) cudaFreeHost(sim->hbuf);
