@@ -110,7 +110,7 @@ Plan make_plan(const hdgdg_config* c) {
     b += 5 * p.nt * d;                                        // g, x~, qhat, w, DG face fluxes
     if (c->precision == HDGDG_MIXED) {                        // FP32 S~, FP32 basis and work vector
         if (!matrix_free(c)) b += n_edges * 6 * (size_t)p.NF * p.NF * sizeof(float);
-        b += ((size_t)p.m + (matrix_free(c) ? 3 : 2)) * p.nt * sizeof(float);   // basis and w (two, matrix-free)
+        b += ((size_t)p.m + (matrix_free(c) ? 4 : 2)) * p.nt * sizeof(float);   // basis and w (three, matrix-free)
     } else {
         b += ((size_t)p.m + 1) * p.nt * d;                    // FP64 Krylov basis
     }
@@ -556,7 +556,31 @@ cudaError_t cycle_enqueue(hdgdg_sim* sim, const double* g, cudaStream_t st, bool
         else e = launch_scale_by_rnorm(sim->w, dv_nrm(sim), V, n, st);
     }
     T* const w_base = w;
-    for (int j = 0; j < m && e == cudaSuccess; ++j) {
+    // FP32 matrix-free cycles with Gram-Schmidt twice: the second pass is delayed into the next
+    // step (launch_dcgs_fused), whose product is taken of w1 (always in w32's first vector); the
+    // products then alternate between the second and third vectors, each zeroed one step ahead
+    const bool delayed = fused && sim->cfg.krylov_ortho != 1;
+    if constexpr (kMixed) {
+        if (delayed && e == cudaSuccess) e = cudaMemsetAsync(w_base + n, 0, n * sizeof(T), st);
+        for (int j = 0; delayed && j < m && e == cudaSuccess; ++j) {
+            T* const A = w_base;
+            T* const Tj = w_base + (size_t)(1 + (j + 1) % 2) * n;   // this step's product (j >= 1)
+            T* const Tn = w_base + (size_t)(1 + j % 2) * n;         // the next step's
+            {
+                TimedGroup tg(sim, HDGDG_KT_SPMV, j);
+                e = launch_mf_inner(sim->g, sim->mf, j == 0 ? V : A, j == 0 ? A : Tj, beta_of(sim), st, done, true);
+            }
+            TimedGroup tg(sim, HDGDG_KT_ORTHO, j);
+            if (e == cudaSuccess)
+                e = j == 0 ? launch_multidot(V, n, 1, A, n, sim->red, dv_h1(sim), st, done)
+                           : launch_dcgs_fused(V, n, j, dv_h2(sim), dv_nrm(sim) + 1, ctl, A, Tj, V + (size_t)j * n, Tn,
+                                               n, sim->red, dv_h1(sim), st, done);
+            if (e == cudaSuccess)
+                e = launch_cgs2_update(V, n, j + 1, dv_h1(sim), A, n, sim->red, dv_h2(sim), dv_nrm(sim) + 2,
+                                       dv_nrm(sim) + 1, ctl, j, m, st, done);
+        }
+    }
+    for (int j = 0; !delayed && j < m && e == cudaSuccess; ++j) {
         const T* Vj = V + (size_t)j * n;
         if (fused) w = w_base + (size_t)(j % 2) * n;
         {
@@ -1321,7 +1345,7 @@ hdgdg_status setup(hdgdg_sim* sim, const double* bottom_b) {
             if (c->residual_f32x2) TRY(dalloc(sim, &sim->Stil_lo, (size_t)g.n_edges * 6 * p.NF * p.NF));
         }
         TRY(dalloc(sim, &sim->V32, (size_t)(p.m + 1) * p.nt));
-        TRY(dalloc(sim, &sim->w32, (matrix_free(c) ? 2 : 1) * p.nt));   // matrix-free: two alternating outputs
+        TRY(dalloc(sim, &sim->w32, (matrix_free(c) ? 3 : 1) * p.nt));   // matrix-free: w1 and two alternating outputs
     } else {
         TRY(dalloc(sim, &sim->V, (size_t)(p.m + 1) * p.nt));
     }

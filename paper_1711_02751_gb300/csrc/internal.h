@@ -391,6 +391,8 @@ cudaError_t launch_split_pairs_inplace(double* a, size_t n, cudaStream_t s);
 struct GmresCtl {
     static constexpr int kM = 32;
     double H[kM + 1][kM];
+    double Hr[kM + 1][kM];   // the Hessenberg columns before the Givens rotations
+    double cdl[kM + 1];      // H h2 of the last column (launch_dcgs_fused)
     double cs[kM], sn[kM], s[kM + 1], y[kM];
     double tol_abs;     // the solve stops when the residual estimate is <= tol_abs
     double inner_rel;   // a cycle also stops at inner_rel * (its starting residual); 0 = off
@@ -437,6 +439,18 @@ cudaError_t launch_cgs2_tail(const float* V, size_t ldv, int nv, const double* h
                              double* scratch, double* h2, double* nw1, double* hn, float* vout,
                              GmresCtl* ctl, int j, int m, bool twice, cudaStream_t s, const int* done = nullptr,
                              float* zero = nullptr);
+// Classical Gram-Schmidt twice with the second pass delayed (the FP32 inner cycles of the
+// matrix-free form).  launch_cgs2_update: w1 = w - V h1 in place, h2 = V^T w1, hn = ||w1 - V h2||
+// (for an orthonormal V), the Hessenberg column j with its rotation and stop test, and
+// ctl->cdl = H h2 -- the second pass itself is left to launch_dcgs_fused, which, given the
+// product z of w1, forms v = (w1 - V h2) / hn into vout, the product of v in place of w1, and
+// V_k . (A v) for k <= nj into h1n (the next step's first pass); zero = 0 when given.  nj <= 31.
+cudaError_t launch_cgs2_update(const float* V, size_t ldv, int nv, const double* h1, float* w, size_t n,
+                               double* scratch, double* h2, double* nw1, double* hn, GmresCtl* ctl, int j, int m,
+                               cudaStream_t s, const int* done);
+cudaError_t launch_dcgs_fused(const float* V, size_t ldv, int nj, const double* h2, const double* hn,
+                              const GmresCtl* ctl, float* w, const float* z, float* vout, float* zero, size_t n,
+                              double* scratch, double* h1n, cudaStream_t s, const int* done);
 
 
 // ---- uneven ensembles: one persistent launch per kernel class over many mesh groups ----------

@@ -286,6 +286,82 @@ axpy_scale_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict_
     }
 }
 
+// Classical Gram-Schmidt twice with the second pass delayed by one Arnoldi step (the DCGS2
+// arrangement of Swirydowicz, Langou, Ananthan, Yang and Thomas, "Low synchronization
+// Gram-Schmidt and GMRES algorithms", 2021): the step that formed w1 = w - V h1 left its second
+// pass v = (w1 - V h2) / hn undone, and the next product was taken of w1 instead of v.  One pass
+// over the NJ basis vectors then forms v into vout, the product of v from the product z of w1
+// through the Arnoldi relation A V_NJ = V_{NJ+1} H -- A v = (z - V c - c_NJ v) / hn with c = H h2
+// (ctl->cdl, formed with the Hessenberg column) -- in place of w1, and the next step's first-pass
+// dots V_k . A v for k <= NJ (v the last) into h1n; zero = 0 when given (the next product's output).
+template <int NJ, typename T, int VW = 1>
+__global__ void __launch_bounds__(kDotThreads)
+dcgs_fused_kernel(const T* __restrict__ V, size_t ldv, const double* __restrict__ h2, const double* __restrict__ hn,
+                  const GmresCtl* __restrict__ ctl, T* __restrict__ w, const T* __restrict__ z,
+                  T* __restrict__ vout, T* __restrict__ zero, size_t n, double* __restrict__ scratch,
+                  double* __restrict__ h1n, const int* __restrict__ done) {
+    if (done && *done) return;
+    constexpr int ldp = NJ + 1;
+    unsigned* counter = reinterpret_cast<unsigned*>(scratch);
+    double* partial = scratch + 1;
+    __shared__ double sh[NJ + 1][kDotThreads / 32];
+    T a[NJ], cc[NJ + 1], acc[NJ + 1];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) a[j] = T(__ldg(h2 + j));
+#pragma unroll
+    for (int j = 0; j <= NJ; ++j) { cc[j] = T(ctl->cdl[j]); acc[j] = T(0); }
+    const T inv = T(1.0 / *hn);
+    for (size_t iv = blockIdx.x * (size_t)kDotThreads + threadIdx.x; iv < n / VW;
+         iv += (size_t)gridDim.x * kDotThreads) {
+        Lanes<T, VW> v[NJ];
+        Lanes<T, VW> x = load_lanes<T, VW>(w, iv), y = load_lanes<T, VW>(z, iv);
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            v[j] = load_lanes<T, VW>(V + (size_t)j * ldv, iv);
+#pragma unroll
+            for (int k = 0; k < VW; ++k) {
+                x.v[k] -= a[j] * v[j].v[k];
+                y.v[k] -= cc[j] * v[j].v[k];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+            x.v[k] *= inv;
+            y.v[k] = (y.v[k] - cc[NJ] * x.v[k]) * inv;
+        }
+        store_lanes<T, VW>(vout, iv, x);
+        store_lanes<T, VW>(w, iv, y);
+        if (zero) {
+            Lanes<T, VW> zz;
+#pragma unroll
+            for (int k = 0; k < VW; ++k) zz.v[k] = T(0);
+            store_lanes<T, VW>(zero, iv, zz);
+        }
+#pragma unroll
+        for (int j = 0; j < NJ; ++j)
+#pragma unroll
+            for (int k = 0; k < VW; ++k) acc[j] += v[j].v[k] * y.v[k];
+#pragma unroll
+        for (int k = 0; k < VW; ++k) acc[NJ] += x.v[k] * y.v[k];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c <= NJ; ++c) {
+        const double s = warp_sum((double)acc[c]);
+        if (lane == 0) sh[c][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x <= NJ) {
+        double s = 0.0;
+        for (int k = 0; k < kDotThreads / 32; ++k) s += sh[threadIdx.x][k];
+        partial[(size_t)blockIdx.x * ldp + threadIdx.x] = s;
+    }
+    if (last_block_arrives(counter)) {
+        reduce_partials(partial, gridDim.x, ldp, 0, NJ + 1, h1n);
+        if (threadIdx.x == 0) *counter = 0u;
+    }
+}
+
 // ||g||^2 and the residual norms of every candidate initial guess in one pass over g and the
 // stored products (no matrix product): out[0] = ||g||^2, out[q] = ||g - sum_j c[q][j] y[j]||^2.
 // NQT = the number of stored products (one instance each, the loops bounded by constants).
@@ -637,8 +713,14 @@ __global__ void gmres_cycle_init_kernel(GmresCtl* c, const double* nrm2) {
 __device__ void gmres_arnoldi_update(GmresCtl* c, int j, int m, const double* h1, const double* h2,
                                      const double* hn) {
     if (c->done) return;
-    for (int i = 0; i <= j; ++i) c->H[i][j] = h1[i] + h2[i];
-    c->H[j + 1][j] = *hn;
+    for (int i = 0; i <= j; ++i) c->H[i][j] = c->Hr[i][j] = h1[i] + h2[i];
+    c->H[j + 1][j] = c->Hr[j + 1][j] = *hn;
+    // c = H h2 over the raw columns 0..j (the delayed second pass's correction of the next product)
+    for (int i = 0; i <= j + 1; ++i) {
+        double t = 0.0;
+        for (int k = i > 0 ? i - 1 : 0; k <= j; ++k) t += c->Hr[i][k] * h2[k];
+        c->cdl[i] = t;
+    }
     for (int i = 0; i < j; ++i) {
         const double t = c->cs[i] * c->H[i][j] + c->sn[i] * c->H[i + 1][j];
         c->H[i + 1][j] = -c->sn[i] * c->H[i][j] + c->cs[i] * c->H[i + 1][j];
@@ -786,6 +868,44 @@ cudaError_t cgs2_tail_dispatch(const T* V, size_t ldv, int nv, const double* h1,
     }
 }
 
+template <int NJ>
+cudaError_t cgs2_update_launch(const float* V, size_t ldv, const double* h1, float* w, size_t n, double* scratch,
+                               double* h2, double* nw1, double* hn, GmresCtl* ctl, int j, int m, cudaStream_t s,
+                               const int* done) {
+    if constexpr (NJ <= 10) {
+        if (lanes4<float>(n, ldv, {V, w})) {
+            axpy_dot_kernel<NJ, float, true, 4><<<152 * 3, kDotThreads, 0, s>>>(V, ldv, h1, w, n, scratch, h2, nw1, hn,
+                                                                                 ctl, j, m, done);
+            count_launches(1);
+            return cudaGetLastError();
+        }
+    }
+    axpy_dot_kernel<NJ, float, true><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, h1, w, n, scratch, h2, nw1, hn, ctl, j,
+                                                                         m, done);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <int NJ>
+cudaError_t dcgs_fused_launch(const float* V, size_t ldv, const double* h2, const double* hn, const GmresCtl* ctl,
+                              float* w, const float* z, float* vout, float* zero, size_t n, double* scratch,
+                              double* h1n, cudaStream_t s, const int* done) {
+    if constexpr (NJ <= 10) {
+        if (lanes4<float>(n, ldv, {V, w, z, vout, zero ? zero : vout})) {
+            // up to 80 registers a thread through NJ = 8: three blocks per SM; two above
+            constexpr int kGrid = 152 * (NJ <= 8 ? 3 : 2);
+            dcgs_fused_kernel<NJ, float, 4><<<kGrid, kDotThreads, 0, s>>>(V, ldv, h2, hn, ctl, w, z, vout, zero, n,
+                                                                         scratch, h1n, done);
+            count_launches(1);
+            return cudaGetLastError();
+        }
+    }
+    dcgs_fused_kernel<NJ, float><<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, h2, hn, ctl, w, z, vout, zero, n, scratch,
+                                                                   h1n, done);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t multidot_impl(const T* V, size_t ldv, int nv, const T* w, size_t n, double* scratch, double* out,
                           cudaStream_t s, const int* done) {
@@ -896,6 +1016,33 @@ cudaError_t launch_cgs2_tail(const float* V, size_t ldv, int nv, const double* h
                              float* zero) {
     return cgs2_tail_dispatch<float>(V, ldv, nv, h1, w, n, scratch, h2, nw1, hn, vout, ctl, j, m, twice, s, done,
                                      zero);
+}
+
+cudaError_t launch_cgs2_update(const float* V, size_t ldv, int nv, const double* h1, float* w, size_t n,
+                               double* scratch, double* h2, double* nw1, double* hn, GmresCtl* ctl, int j, int m,
+                               cudaStream_t s, const int* done) {
+    switch (nv) {
+#define CASE(J) case J: return cgs2_update_launch<J>(V, ldv, h1, w, n, scratch, h2, nw1, hn, ctl, j, m, s, done);
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
+        CASE(12) CASE(13) CASE(14) CASE(15) CASE(16) CASE(17) CASE(18) CASE(19) CASE(20) CASE(21)
+        CASE(22) CASE(23) CASE(24) CASE(25) CASE(26) CASE(27) CASE(28) CASE(29) CASE(30) CASE(31)
+        CASE(32)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_dcgs_fused(const float* V, size_t ldv, int nj, const double* h2, const double* hn,
+                              const GmresCtl* ctl, float* w, const float* z, float* vout, float* zero, size_t n,
+                              double* scratch, double* h1n, cudaStream_t s, const int* done) {
+    switch (nj) {
+#define CASE(J) case J: return dcgs_fused_launch<J>(V, ldv, h2, hn, ctl, w, z, vout, zero, n, scratch, h1n, s, done);
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11)
+        CASE(12) CASE(13) CASE(14) CASE(15) CASE(16) CASE(17) CASE(18) CASE(19) CASE(20) CASE(21)
+        CASE(22) CASE(23) CASE(24) CASE(25) CASE(26) CASE(27) CASE(28) CASE(29) CASE(30) CASE(31)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_block_diag(const Geom& g, const double* Bd, const double* x, double* y,
