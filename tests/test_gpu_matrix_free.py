@@ -131,6 +131,35 @@ def test_matches_the_assembled_route(N, k, n):
         assert imex.rel_l2(m, qa[c], qb[c]) <= 1e-7
 
 
+def _steps_its(N, k, n, **kw):
+    m, h, hu, hv, b = user_state(N, k, "large")
+    dt = dt_of(m, h, hu, hv)
+    with hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, **kw) as s:
+        s.set_state(h, hu, hv)
+        s.step(n)
+        out, its = s.get_state(), s.stats()["krylov_iterations"]
+    return m, swe.to_state(*out, b, W.G, W.H0)[0], its
+
+
+@pytest.mark.parametrize("N,k,n", [(64, 3, 6), (20, 3, 12), (9, 3, 4)])
+def test_delayed_gram_schmidt(N, k, n):
+    """The matrix-free FP32 cycles run Gram-Schmidt twice with the second pass delayed into the
+    next Arnoldi step: the product is taken of the once-projected vector and corrected through
+    the Arnoldi relation (A v = (A w1 - V H h2) / hn).  Over several steps, on meshes whose last
+    reduction blocks are partial, that needs the inner iterations of Gram-Schmidt twice done in
+    place (the assembled route, whose cycles keep it) to within one per stage, and of the single
+    pass (krylov_ortho = 1, matrix-free), and the states agree within the solver tolerance."""
+    m, q_del, its_del = _steps_its(N, k, n, **MF)
+    _, q_in, its_in = _steps_its(N, k, n, **ASSEMBLED)
+    _, q_one, its_one = _steps_its(N, k, n, krylov_ortho=1, **MF)
+    stages = 2 * n
+    print(f"delayed {its_del}, in place {its_in}, single pass {its_one} iterations over {stages} stages")
+    assert abs(its_del - its_in) <= stages and abs(its_del - its_one) <= stages
+    for c in range(3):
+        assert imex.rel_l2(m, q_del[c], q_in[c]) <= 1e-7
+        assert imex.rel_l2(m, q_del[c], q_one[c]) <= 1e-7
+
+
 def test_walls_and_vortex_steps_against_the_oracle():
     m = swe.Mesh(6, 3, boundary="wall")
     x_, y_ = m.x.reshape(m.n_el, -1), m.y.reshape(m.n_el, -1)
