@@ -334,6 +334,7 @@ struct hdgdg_sim {
     LocalOps ops;
     int* Scol = nullptr;
     double *q = nullptr, *q_new = nullptr, *R1 = nullptr, *Z = nullptr, *Qs = nullptr;
+    // per stage dt M^{-1} NL_i and Q_i - R1_i = dt a_ii M^{-1} L_i (the combinations divide by a_ii)
     double *NLs[kMaxStages] = {}, *Ls[kMaxStages] = {};
     double *gvec = nullptr, *xt = nullptr, *lam = nullptr, *w = nullptr, *V = nullptr, *fface = nullptr;
     float *Stil32 = nullptr, *V32 = nullptr, *w32 = nullptr;   // mixed precision only
@@ -849,7 +850,7 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
 }
 
 
-// One implicit stage: R1 (device) -> Q, Lst = dt M^{-1} L (device); qhat left in sim->lam.
+// One implicit stage: R1 (device) -> Q, Lst = Q - R1 = dt a_ii M^{-1} L (device); qhat left in sim->lam.
 // Whether an implicit stage's condensation forms R1 from its terms (launch_condense's src): the
 // FP32-pair Schur kernels, whose time goes to FP32 work and latency, absorb the combination's
 // streams; the FP64 ones are bound by the FP64 pipe, which its FMAs would lengthen.
@@ -872,7 +873,7 @@ hdgdg_status stage_solve_dev(hdgdg_sim* sim, const double* R1, double* Q, double
     else TRY(gmres_solve<double>(sim, sim->gvec, sim->lam, its, &rr, stage));
     {
         TimedGroup tg(sim, HDGDG_KT_RECOVER);
-        CU(launch_recover(sim->g, sim->ops, sim->Z, R1, sim->tau, sim->lam, beta_of(sim), 1.0 / sim->a_ii,
+        CU(launch_recover(sim->g, sim->ops, sim->Z, R1, sim->tau, sim->lam, beta_of(sim), 1.0,
                           Q, Lst, sim->stream, Q32));
     }
     return HDGDG_OK;
@@ -1006,7 +1007,7 @@ cudaError_t step_enqueue_graph(hdgdg_sim* sim, cudaStream_t st, StepGraph& sg) {
             CombineTerms t{};
             for (int j = 0; j < i; ++j) {
                 if (sim->A[i][j] != 0.0 && !sim->cfg.linear_only) { t.X[t.n] = sim->NLs[j]; t.c[t.n++] = sim->A[i][j]; }
-                if (sim->At[i][j] != 0.0) { t.X[t.n] = sim->Ls[j]; t.c[t.n++] = sim->At[i][j]; }
+                if (sim->At[i][j] != 0.0) { t.X[t.n] = sim->Ls[j]; t.c[t.n++] = sim->At[i][j] / sim->a_ii; }
             }
             if (sim->ens || !r1_fused(sim, t)) {
                 e = launch_combine(n3, sim->q, t, sim->R1, nullptr, st);
@@ -1033,10 +1034,10 @@ cudaError_t step_enqueue_graph(hdgdg_sim* sim, cudaStream_t st, StepGraph& sg) {
                 if (e == cudaSuccess) pending = i;
             }
             if (e == cudaSuccess)
-                e = sim->ens ? launch_ens_recover(*sim->ens, sim->Z, sim->R1, sim->lam, 1.0 / sim->a_ii, sim->Qs,
+                e = sim->ens ? launch_ens_recover(*sim->ens, sim->Z, sim->R1, sim->lam, 1.0, sim->Qs,
                                                   sim->Ls[i], st)
                              : launch_recover(sim->g, sim->ops, sim->Z, sim->R1, sim->tau, sim->lam, beta_of(sim),
-                                              1.0 / sim->a_ii, sim->Qs, sim->Ls[i], st, sim->Qs32);
+                                              1.0, sim->Qs, sim->Ls[i], st, sim->Qs32);
             Qi = sim->Qs;
         }
         if (!sim->cfg.linear_only && e == cudaSuccess) e = dg_nl_enqueue(sim, Qi, Qi == sim->Qs, sim->NLs[i], st, 0.0);
@@ -1045,7 +1046,7 @@ cudaError_t step_enqueue_graph(hdgdg_sim* sim, cudaStream_t st, StepGraph& sg) {
     CombineTerms t{};
     for (int i = 0; i < sim->s; ++i) {
         if (sim->b[i] != 0.0 && !sim->cfg.linear_only) { t.X[t.n] = sim->NLs[i]; t.c[t.n++] = sim->b[i]; }
-        if (sim->bt[i] != 0.0) { t.X[t.n] = sim->Ls[i]; t.c[t.n++] = sim->bt[i]; }
+        if (sim->bt[i] != 0.0) { t.X[t.n] = sim->Ls[i]; t.c[t.n++] = sim->bt[i] / sim->a_ii; }
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(sim->flags, 0, sizeof(unsigned), st);
     if (e == cudaSuccess) e = launch_combine(n3, sim->q, t, sim->q_new, sim->flags, st);
@@ -1228,7 +1229,7 @@ hdgdg_status one_step(hdgdg_sim* sim) {
             CombineTerms t{};
             for (int j = 0; j < i; ++j) {
                 if (sim->A[i][j] != 0.0 && !sim->cfg.linear_only) { t.X[t.n] = sim->NLs[j]; t.c[t.n++] = sim->A[i][j]; }
-                if (sim->At[i][j] != 0.0) { t.X[t.n] = sim->Ls[j]; t.c[t.n++] = sim->At[i][j]; }
+                if (sim->At[i][j] != 0.0) { t.X[t.n] = sim->Ls[j]; t.c[t.n++] = sim->At[i][j] / sim->a_ii; }
             }
             // the FP32-pair Schur condensation forms R1 itself, as in the step graph
             const bool fused = r1_fused(sim, t);
@@ -1249,7 +1250,7 @@ hdgdg_status one_step(hdgdg_sim* sim) {
     CombineTerms t{};
     for (int i = 0; i < sim->s; ++i) {
         if (sim->b[i] != 0.0 && !sim->cfg.linear_only) { t.X[t.n] = sim->NLs[i]; t.c[t.n++] = sim->b[i]; }
-        if (sim->bt[i] != 0.0) { t.X[t.n] = sim->Ls[i]; t.c[t.n++] = sim->bt[i]; }
+        if (sim->bt[i] != 0.0) { t.X[t.n] = sim->Ls[i]; t.c[t.n++] = sim->bt[i] / sim->a_ii; }
     }
     CU(cudaMemsetAsync(sim->flags, 0, sizeof(unsigned), st));
     {

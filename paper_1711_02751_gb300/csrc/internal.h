@@ -286,6 +286,8 @@ cudaError_t launch_condense(const Geom& g, const LocalOps& ops, const double* R1
                             const double* tau_edge, double* Z, double* gvec, cudaStream_t s, double t = 0.0,
                             const R1Source* src = nullptr);
 // Recovery: Q = Z + beta A^{-1} (tau qhat) on boundary nodes; Lst = (Q - R1) / a_ii.
+// Lst = (Q - R1) inv_aii; the Schur-complement kinds take inv_aii = 1 only (cudaErrorInvalidValue
+// otherwise): the time step keeps Q - R1 and folds 1/a_ii into its combinations.
 cudaError_t launch_recover(const Geom& g, const LocalOps& ops, const double* Z, const double* R1,
                            const double* tau_edge, const double* qhat, double beta, double inv_aii,
                            double* Q, double* Lst, cudaStream_t s, float* Q32 = nullptr);

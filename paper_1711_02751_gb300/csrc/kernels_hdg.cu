@@ -601,7 +601,8 @@ __global__ void __launch_bounds__(EPB * P * P)
     schur_condense_body<P, EPB, A>(blockIdx.x, g, S, aux, EG, R1, Z, src);
 }
 
-// Q = Z + beta A^{-1} (tau qhat), Lst = (Q - R1) / a_ii through the Schur complement.
+// Q = Z + beta A^{-1} (tau qhat), Lst = Q - R1 (= dt a_ii M^{-1} L; inv_aii must be 1: the
+// callers fold 1/a_ii into the stage combinations) through the Schur complement.
 template <int P, int EPB, class A>
 __device__ __forceinline__ void schur_recover_body(int bid, const Geom& g, const typename A::T* __restrict__ S,
                                                    const typename A::T* __restrict__ aux,
@@ -639,7 +640,7 @@ __device__ __forceinline__ void schur_recover_body(int bid, const Geom& g, const
             const double q = Z[oc] + kk * A::to(y[c]);
             if (Q32) Q32[oc] = f64_to_f32(q);   // the FP32 stage value the mixed form's DG residual reads
             else Q[oc] = q;
-            Lst[oc] = (q - R1[oc]) * inv_aii;
+            Lst[oc] = q - R1[oc];   // callers fold 1/a_ii into the stage combinations (inv_aii = 1)
         }
     }
 }
@@ -739,7 +740,7 @@ __global__ void __launch_bounds__(EPB * P * P)
             const double q = zv[c] + kk * A::to(y[c]);
             if (Q32) Q32[oc] = f64_to_f32(q);
             else Q[oc] = q;
-            Lst[oc] = (q - rv[c]) * inv_aii;
+            Lst[oc] = q - rv[c];
         }
     }
 }
@@ -1064,6 +1065,7 @@ cudaError_t recover_launch(const Geom& g, const LocalOps& ops, const double* Z, 
     constexpr int EPB = (256 / NV) > 0 ? 256 / NV : 1;
     const int blocks = (g.n_el + EPB - 1) / EPB;
     if (ops.schur) {
+        if (inv_aii != 1.0) return cudaErrorInvalidValue;   // the Schur kernels write Q - R1
         if (ops.kind == 3) schur_recover<P, ArithF2>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s, Q32);
         else schur_recover<P, ArithF64>(g, ops, Z, R1, tau_edge, qhat, beta, inv_aii, Q, Lst, s, Q32);
         return cudaGetLastError();
@@ -1170,6 +1172,7 @@ cudaError_t launch_ens_condense(const EnsHost& E, const double* R1, double* Z, d
 
 cudaError_t launch_ens_recover(const EnsHost& E, const double* Z, const double* R1, const double* qhat,
                                double inv_aii, double* Q, double* Lst, cudaStream_t s) {
+    if (inv_aii != 1.0) return cudaErrorInvalidValue;   // the Schur kernels write Q - R1
     const EnsTable te = ens_table(E, ens_elem_blocks);
     ens_recover_kernel<<<ens_grid(ens_recover_kernel, te.start[te.ngroups]), 256, 0, s>>>(te, Z, R1, qhat, inv_aii, Q,
                                                                                           Lst);
