@@ -850,7 +850,6 @@ hdgdg_status gmres_solve(hdgdg_sim* sim, const double* g, double* qhat, int* ite
 }
 
 
-// One implicit stage: R1 (device) -> Q, Lst = Q - R1 = dt a_ii M^{-1} L (device); qhat left in sim->lam.
 // Whether an implicit stage's condensation forms R1 from its terms (launch_condense's src): the
 // FP32-pair Schur kernels, whose time goes to FP32 work and latency, absorb the combination's
 // streams; the FP64 ones are bound by the FP64 pipe, which its FMAs would lengthen.
@@ -858,7 +857,8 @@ bool r1_fused(const hdgdg_sim* sim, const CombineTerms& t) {
     return sim->ops.schur && sim->ops.kind == 3 && t.n <= kR1FusedTerms;
 }
 
-// src: R1 is formed by the condensation from these terms (launch_condense) instead of read.
+// One implicit stage: R1 (device) -> Q, Lst = Q - R1 = dt a_ii M^{-1} L (device); qhat left in
+// sim->lam.  src: R1 is formed by the condensation from these terms (launch_condense) instead of read.
 hdgdg_status stage_solve_dev(hdgdg_sim* sim, const double* R1, double* Q, double* Lst, int* its,
                              double t_stage = 0.0, int stage = -1, float* Q32 = nullptr,
                              const R1Source* src = nullptr) {

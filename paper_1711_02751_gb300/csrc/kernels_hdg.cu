@@ -536,7 +536,8 @@ __global__ void schur_eg_kernel(Geom g, double dta, typename A::T* __restrict__ 
 
 // The three fields of R1 at node o (field stride fs): read, or (src.base set) formed term by term
 // as launch_combine forms them and written back to R1.  Every load is issued before the first
-// store so that they overlap (R1 may alias nothing the terms read, but the compiler cannot know).
+// store so that they overlap (the terms' pointers sit in a struct: the compiler cannot prove that
+// the stores to R1 leave them alone).
 __device__ __forceinline__ void r1_fields(const double* __restrict__ R1, const R1Source& src, size_t o, size_t fs,
                                           double v[3]) {
     if (!src.base) {
