@@ -449,6 +449,7 @@ def stiff_block(args, stream, dist, world):
     finals = {}
     for precision in args.precisions.split(","):
         sim = hd.Sim(N, k, dt, bottom=b, g=W.G, H0=W.H0, stream=stream.cuda_stream, precision=precision,
+                     krylov_restart=args.restart,
                      local_precision=args.local if precision == "mixed" else "fp64",
                      residual_f32x2=bool(args.residual_f32x2) and precision == "mixed",
                      trace_operator=_trace_operator(args, precision),
