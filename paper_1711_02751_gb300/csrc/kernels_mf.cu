@@ -69,6 +69,10 @@ constexpr int kMfTiles = 9;
 constexpr int mf_tile_threads(int t) { return t % 3 == 0 ? 256 : t % 3 == 1 ? 128 : 512; }
 constexpr bool mf_tile_pref(int t) { return t < 3; }
 constexpr int mf_tile_minb(int t) { return t >= 6 ? 2048 / mf_tile_threads(t) : 1; }
+// the refinement residual's FP32-pair pass holds ~112 registers a thread: its tiles 6..8 cap them
+// at 85 (256 threads, 3 blocks an SM), 85 (128 threads, 6 blocks) and 64 (256 threads, 4 blocks)
+constexpr int mf_res_threads(int t) { return t == 7 ? 128 : t >= 6 ? 256 : mf_tile_threads(t); }
+constexpr int mf_res_minb(int t) { return t == 6 ? 3 : t == 7 ? 6 : t == 8 ? 4 : 1; }
 
 template <class A>
 __device__ __forceinline__ typename A::T arith_of_f32(float v) {
@@ -494,16 +498,18 @@ void mf_elem_launch(const Geom& g, const void* S, const void* aux, const void* E
                     MfVec<MODE>* hm, MfVec<MODE>* hp, double beta, cudaStream_t s, const int* done,
                     const PrecondBlocks& Minv) {
     using T = typename A::T;
-    constexpr int EPB = mf_epb_for<P>(mf_tile_threads(TILE));
+    constexpr bool kRes = MODE == kMfResidual;
+    constexpr int EPB = mf_epb_for<P>(kRes ? mf_res_threads(TILE) : mf_tile_threads(TILE));
+    constexpr int kMinB = kRes ? mf_res_minb(TILE) : mf_tile_minb(TILE);
     constexpr bool kFuse = MODE == kMfInner;
     constexpr bool kTauN = MODE != kMfPlain;   // the inner and residual modes read their own copy of tau
-    mf_elem_kernel<P, EPB, A, MODE, mf_tile_pref(TILE), mf_tile_minb(TILE), kFuse, kTauN>
+    mf_elem_kernel<P, EPB, A, MODE, mf_tile_pref(TILE), kMinB, kFuse, kTauN>
         <<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(g, static_cast<const T*>(S), static_cast<const T*>(aux),
                                                           static_cast<const T*>(EG), tau, yv, hm, hp, beta, Minv,
                                                           done);
 }
 
-// the element pass with tile t (degrees 2..4: tiles 0..8 in the inner cycles, 0..5 in the
+// the element pass with tile t (degrees 2..4: tiles 0..8 in the inner cycles and in the
 // refinement residual; tile 0 elsewhere)
 template <int P, class A, int MODE>
 void mf_elem_tile(int t, const Geom& g, const void* S, const void* aux, const void* EG, const void* tau,
@@ -516,6 +522,9 @@ void mf_elem_tile(int t, const Geom& g, const void* S, const void* aux, const vo
             case 3: return mf_elem_launch<P, A, MODE, 3>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done, Minv);
             case 4: return mf_elem_launch<P, A, MODE, 4>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done, Minv);
             case 5: return mf_elem_launch<P, A, MODE, 5>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done, Minv);
+            case 6: return mf_elem_launch<P, A, MODE, 6>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done, Minv);
+            case 7: return mf_elem_launch<P, A, MODE, 7>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done, Minv);
+            case 8: return mf_elem_launch<P, A, MODE, 8>(g, S, aux, EG, tau, yv, hm, hp, beta, s, done, Minv);
             default: break;
         }
     }
@@ -738,10 +747,10 @@ cudaError_t launch_mf_autotune(const Geom& g, MfOps& op, const float* x, float* 
         }
     }
     op.tile = best_t;
-    // the refinement residual's element pass (FP32 pairs): tiles 0..5
+    // the refinement residual's element pass (FP32 pairs): tiles 0..8 (6..8 with capped registers)
     best = 1e30f;
     int best_r = 0;
-    for (int t = 0; t < 6 && err == cudaSuccess; ++t) {
+    for (int t = 0; t < kMfTiles && err == cudaSuccess; ++t) {
         op.tile_res = t;
         for (int k = 0; k < 2 && err == cudaSuccess; ++k) err = launch_mf_residual(g, op, xd, rhs, w, beta, s);
         if (err == cudaSuccess) err = cudaEventRecord(a, s);
