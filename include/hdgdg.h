@@ -142,8 +142,11 @@ typedef struct {
                             shared memory with bulk (TMA) copies, two stages deep.  Identical
                             results (same summation order). */
     int krylov_ortho;    /* Gram-Schmidt of the mixed form's FP32 inner cycles: 0 = classical,
-                            applied twice (CGS2); 1 = classical, once.  The FP64 form and the
-                            FP64 refinement residuals are not affected. */
+                            applied twice (CGS2; with the matrix-free operator the second pass
+                            is delayed into the next Arnoldi step, whose product is taken of the
+                            once-projected vector and corrected through the Arnoldi relation:
+                            one pass over the basis fewer a step); 1 = classical, once.  The
+                            FP64 form and the FP64 refinement residuals are not affected. */
     int residual_f32x2;  /* mixed form: 1 = the refinement's true residual g - S qhat in FP64-class
                             arithmetic on the FP32 pipes (S as an FP32 pair, compensated Dot2
                             sums, ~1e-13 relative; see HDGDG_LOCAL_F32X2); 0 = FP64. */
