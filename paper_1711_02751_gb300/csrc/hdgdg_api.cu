@@ -881,14 +881,18 @@ hdgdg_status stage_solve_dev(hdgdg_sim* sim, const double* R1, double* Q, double
 
 // The nonlinear DG residual of stage value Qi into out.  stage_value: Qi came from this step's
 // recovery (with the FP32 copies, its FP32 copy in Qs32 is the one written).
+// fin: the step's final update formed by the element pass (dg_final_fusable).
 cudaError_t dg_nl_enqueue(hdgdg_sim* sim, const double* Qi, bool stage_value, double* out, cudaStream_t st,
-                          double t) {
+                          double t, const FinalSource* fin = nullptr) {
+    if (fin && !(sim->cfg.precision == HDGDG_MIXED && sim->Qs32 && stage_value && !sim->ens &&
+                 sim->cfg.dg_precision != 1))
+        return cudaErrorInvalidValue;
     if (sim->ens) return launch_ens_dg_nl_f32(*sim->ens, Qi, sim->fface, out, st);
     if (sim->cfg.dg_precision == 1)
         return launch_dg_nl_bf16(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, out, st, t);
     if (sim->cfg.precision == HDGDG_MIXED && sim->Qs32)
         return launch_dg_nl_f32io(sim->g, Qi, stage_value ? sim->Qs32 : nullptr, sim->phiB32, sim->tau32, sim->cfg.dt,
-                                  reinterpret_cast<float*>(sim->fface), out, st, t);
+                                  reinterpret_cast<float*>(sim->fface), out, st, t, fin);
     if (sim->cfg.precision == HDGDG_MIXED)
         return launch_dg_nl_f32(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, out, st, t);
     return launch_dg_nl(sim->g, Qi, sim->phiB, sim->tau, sim->cfg.dt, sim->fface, out, st, t);
@@ -992,6 +996,20 @@ cudaError_t solve_enqueue_graph(hdgdg_sim* sim, const double* g, double* qhat, i
 cudaError_t step_enqueue_graph(hdgdg_sim* sim, cudaStream_t st, StepGraph& sg) {
     const size_t n3 = 3 * sim->plan.n;
     cudaError_t e = cudaMemsetAsync(sim->sstats, 0, sizeof(StepStats), st);
+    // the final update's terms, in their order; where the last stage's DG residual is one of them
+    // and the mixed form's FP32-input element pass computes it, that pass forms q_new itself
+    CombineTerms tf{};
+    int slot = -1;
+    for (int i = 0; i < sim->s; ++i) {
+        if (sim->b[i] != 0.0 && !sim->cfg.linear_only) {
+            if (i == sim->s - 1) slot = tf.n;
+            tf.X[tf.n] = sim->NLs[i];
+            tf.c[tf.n++] = sim->b[i];
+        }
+        if (sim->bt[i] != 0.0) { tf.X[tf.n] = sim->Ls[i]; tf.c[tf.n++] = sim->bt[i] / sim->a_ii; }
+    }
+    const bool fuse_final = slot >= 0 && tf.n <= kFinalTerms && !sim->ens && sim->cfg.precision == HDGDG_MIXED &&
+                            sim->Qs32 && sim->cfg.dg_precision != 1 && sim->At[sim->s - 1][sim->s - 1] != 0.0;
     // each stage's history store reads x~, g and r, which nothing overwrites before the next
     // stage's condensation: it runs on a branch beside the recovery and the DG residual
     const bool branch = !sim->ens && sim->side_stream && guess_order(&sim->cfg) > 0;
@@ -1040,16 +1058,19 @@ cudaError_t step_enqueue_graph(hdgdg_sim* sim, cudaStream_t st, StepGraph& sg) {
                                               1.0, sim->Qs, sim->Ls[i], st, sim->Qs32);
             Qi = sim->Qs;
         }
-        if (!sim->cfg.linear_only && e == cudaSuccess) e = dg_nl_enqueue(sim, Qi, Qi == sim->Qs, sim->NLs[i], st, 0.0);
+        if (fuse_final && i == sim->s - 1) {
+            const FinalSource fin{sim->q, tf, slot, sim->q_new, sim->flags};
+            if (e == cudaSuccess) e = cudaMemsetAsync(sim->flags, 0, sizeof(unsigned), st);
+            if (e == cudaSuccess) e = dg_nl_enqueue(sim, Qi, Qi == sim->Qs, sim->NLs[i], st, 0.0, &fin);
+        } else if (!sim->cfg.linear_only && e == cudaSuccess) {
+            e = dg_nl_enqueue(sim, Qi, Qi == sim->Qs, sim->NLs[i], st, 0.0);
+        }
     }
     if (pending >= 0 && e == cudaSuccess) e = cudaStreamWaitEvent(st, sim->join_ev[pending], 0);
-    CombineTerms t{};
-    for (int i = 0; i < sim->s; ++i) {
-        if (sim->b[i] != 0.0 && !sim->cfg.linear_only) { t.X[t.n] = sim->NLs[i]; t.c[t.n++] = sim->b[i]; }
-        if (sim->bt[i] != 0.0) { t.X[t.n] = sim->Ls[i]; t.c[t.n++] = sim->bt[i] / sim->a_ii; }
+    if (!fuse_final) {
+        if (e == cudaSuccess) e = cudaMemsetAsync(sim->flags, 0, sizeof(unsigned), st);
+        if (e == cudaSuccess) e = launch_combine(n3, sim->q, tf, sim->q_new, sim->flags, st);
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(sim->flags, 0, sizeof(unsigned), st);
-    if (e == cudaSuccess) e = launch_combine(n3, sim->q, t, sim->q_new, sim->flags, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sim->hbuf, sim->flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(sim->hbuf + 4, sim->sstats, sizeof(StepStats), cudaMemcpyDeviceToHost, st);

@@ -212,9 +212,15 @@ cudaError_t launch_dg_nl(const Geom& g, const double* q, const double* phiB, con
 // The mixed form's residual on FP32 copies (launch_dg_nl_f32 term for term): phi_B, tau and the
 // face fluxes in FP32, the state in FP32 (q32, when given: the recovery's FP32 stage values) or
 // FP64 (q64).
+// fin (given, base set): the step's final update q_new = base + sum_k t.c[k] t.X[k] is formed by
+// the element pass, term by term as launch_combine forms it, with this residual as term `slot`
+// (t.X[slot] is not read); q_new goes to fin->qn, a non-finite entry sets *fin->nonfinite, and
+// the residual itself is not written (out unused).  At most kFinalTerms terms.
+constexpr int kFinalTerms = 4;
+struct FinalSource;   // below, after CombineTerms
 cudaError_t launch_dg_nl_f32io(const Geom& g, const double* q64, const float* q32, const float* phiB32,
                                const float* tau32, double scale, float* fface32, double* out, cudaStream_t s,
-                               double t);
+                               double t, const FinalSource* fin = nullptr);
 cudaError_t launch_dg_nl_f32(const Geom& g, const double* q, const double* phiB, const double* tau_edge,
                              double scale, double* fface, double* out, cudaStream_t s, double t = 0.0);
 // the same residual with its inputs (state, phi_B, tau) rounded to BF16 and FP32 arithmetic (k <= 4)
@@ -228,6 +234,13 @@ struct CombineTerms {
     const double* X[10];
     double c[10];
     int n;
+};
+struct FinalSource {   // launch_dg_nl_f32io's final update
+    const double* base = nullptr;
+    CombineTerms t{};
+    int slot = -1;
+    double* qn = nullptr;
+    unsigned* nonfinite = nullptr;
 };
 // out = base + sum_t c_t X_t over n doubles (out may alias base)
 cudaError_t launch_combine(size_t n, const double* base, const CombineTerms& t, double* out,

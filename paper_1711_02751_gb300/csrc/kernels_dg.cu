@@ -152,13 +152,39 @@ dg_face_kernel(Geom g, const TQ* __restrict__ q, const std::conditional_t<A32, f
     dg_face_body<P, FULL, Tc, BF, TQ, A32>(blockIdx.x, g, q, phiB, tau_edge, fface, t_bc);
 }
 
+// The step's final update at node o (field stride fs) with this pass's residual v as term
+// fin.slot: every other term's loads issued before the sums, each field's terms added in their
+// order as combine_kernel adds them.
+__device__ __forceinline__ void dg_final_update(const FinalSource& fin, size_t o, size_t fs, const double v[3]) {
+    double acc[3], x[kFinalTerms][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] = fin.base[o + c * fs];
+#pragma unroll
+    for (int k = 0; k < kFinalTerms; ++k)   // constant indices keep the terms in the parameter bank
+        if (k < fin.t.n && k != fin.slot) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) x[k][c] = fin.t.X[k][o + c * fs];
+        }
+    bool bad = false;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+        for (int k = 0; k < kFinalTerms; ++k)
+            if (k < fin.t.n) acc[c] += fin.t.c[k] * (k == fin.slot ? v[c] : x[k][c]);
+        fin.qn[o + c * fs] = acc[c];
+        bad |= !isfinite(acc[c]);
+    }
+    if (bad && fin.nonfinite) *fin.nonfinite = 1u;
+}
+
 // Element pass: volume term from the nodal F_NL (shared memory), minus the lifted face fluxes.
 // FULL = true: the whole flux F and the source s = (0, phi_eta d_x phi_B, phi_eta d_y phi_B).
-template <int P, bool FULL, typename Tc, bool BF = false, typename TQ = double, bool A32 = false>
+template <int P, bool FULL, typename Tc, bool BF = false, typename TQ = double, bool A32 = false, bool FIN = false>
 __device__ __forceinline__ void dg_volume_body(int bid, const Geom& g, const TQ* __restrict__ q,
                                                const std::conditional_t<A32, float, double>* __restrict__ phiB,
                                                const std::conditional_t<A32, float, double>* __restrict__ fface,
-                                               double scale, double* __restrict__ out) {
+                                               double scale, double* __restrict__ out,
+                                               const FinalSource& fin = FinalSource{}) {
     constexpr int Np = P * P;
     constexpr int EPB = DgTile<P>::EPB;
     // fxU, fxV, fyU, fyV (and, FULL: U, V, phi_B) per element, each element's row padded by one
@@ -236,17 +262,22 @@ __device__ __forceinline__ void dg_volume_body(int bid, const Geom& g, const TQ*
     }
     const size_t o = (size_t)e * Np + n;
     const double sc = scale * dt_factor(g, e);   // this instance's time step
-    out[o] = sc * to_f64(rph);
-    out[fs + o] = sc * to_f64(rU);
-    out[2 * fs + o] = sc * to_f64(rV);
+    const double v[3] = {sc * to_f64(rph), sc * to_f64(rU), sc * to_f64(rV)};
+    if constexpr (FIN) {   // its own instance: the other passes keep their registers
+        dg_final_update(fin, o, fs, v);
+        return;
+    }
+    out[o] = v[0];
+    out[fs + o] = v[1];
+    out[2 * fs + o] = v[2];
 }
 
-template <int P, bool FULL, typename Tc, bool BF = false, typename TQ = double, bool A32 = false>
+template <int P, bool FULL, typename Tc, bool BF = false, typename TQ = double, bool A32 = false, bool FIN = false>
 __global__ void __launch_bounds__(DgTile<P>::EPB * P * P)
 dg_volume_kernel(Geom g, const TQ* __restrict__ q, const std::conditional_t<A32, float, double>* __restrict__ phiB,
                  const std::conditional_t<A32, float, double>* __restrict__ fface, double scale,
-                 double* __restrict__ out) {
-    dg_volume_body<P, FULL, Tc, BF, TQ, A32>(blockIdx.x, g, q, phiB, fface, scale, out);
+                 double* __restrict__ out, FinalSource fin) {
+    dg_volume_body<P, FULL, Tc, BF, TQ, A32, FIN>(blockIdx.x, g, q, phiB, fface, scale, out, fin);
 }
 
 // One instance per term count NT (0..10), the terms indexed by constants.  Each thread takes U
@@ -371,7 +402,8 @@ cudaError_t dg_launch(const Geom& g, const double* q, const double* phiB, const 
     const int nf = g.n_edges * P;
     dg_face_kernel<P, FULL, Tc, BF><<<(nf + 255) / 256, 256, 0, s>>>(g, q, phiB, tau_edge, fface, t);
     count_launches(1);
-    dg_volume_kernel<P, FULL, Tc, BF><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(g, q, phiB, fface, scale, out);
+    dg_volume_kernel<P, FULL, Tc, BF><<<(g.n_el + EPB - 1) / EPB, EPB * P * P, 0, s>>>(g, q, phiB, fface, scale, out,
+                                                                                      FinalSource{});
     count_launches(1);
     return cudaGetLastError();
 }
@@ -381,16 +413,22 @@ cudaError_t dg_launch(const Geom& g, const double* q, const double* phiB, const 
 template <int P>
 cudaError_t dg_launch_f32io(const Geom& g, const double* q64, const float* q32, const float* phiB,
                             const float* tau_edge, double scale, float* fface, double* out, cudaStream_t s,
-                            double t) {
+                            double t, const FinalSource& fin) {
     constexpr int EPB = DgTile<P>::EPB;
     const int nf = g.n_edges * P;
     const int gf = (nf + 255) / 256, gv = (g.n_el + EPB - 1) / EPB, tv = EPB * P * P;
     if (q32) {
         dg_face_kernel<P, false, float, false, float, true><<<gf, 256, 0, s>>>(g, q32, phiB, tau_edge, fface, t);
-        dg_volume_kernel<P, false, float, false, float, true><<<gv, tv, 0, s>>>(g, q32, phiB, fface, scale, out);
+        if (fin.base)
+            dg_volume_kernel<P, false, float, false, float, true, true><<<gv, tv, 0, s>>>(g, q32, phiB, fface, scale,
+                                                                                        out, fin);
+        else
+            dg_volume_kernel<P, false, float, false, float, true><<<gv, tv, 0, s>>>(g, q32, phiB, fface, scale, out,
+                                                                                  fin);
     } else {
         dg_face_kernel<P, false, float, false, double, true><<<gf, 256, 0, s>>>(g, q64, phiB, tau_edge, fface, t);
-        dg_volume_kernel<P, false, float, false, double, true><<<gv, tv, 0, s>>>(g, q64, phiB, fface, scale, out);
+        dg_volume_kernel<P, false, float, false, double, true><<<gv, tv, 0, s>>>(g, q64, phiB, fface, scale, out,
+                                                                                 fin);
     }
     count_launches(2);
     return cudaGetLastError();
@@ -470,10 +508,15 @@ cudaError_t launch_dg_nl(const Geom& g, const double* q, const double* phiB, con
 
 cudaError_t launch_dg_nl_f32io(const Geom& g, const double* q64, const float* q32, const float* phiB32,
                                const float* tau32, double scale, float* fface32, double* out, cudaStream_t s,
-                               double t) {
+                               double t, const FinalSource* fin) {
+    const FinalSource none{};
+    if (fin && fin->base && (fin->t.n < 1 || fin->t.n > kFinalTerms || fin->slot < 0 || fin->slot >= fin->t.n ||
+                             !fin->qn))
+        return cudaErrorInvalidValue;
+    const FinalSource& f = fin ? *fin : none;
     switch (g.P) {
 #define CASE(P) \
-    case P: return dg_launch_f32io<P>(g, q64, q32, phiB32, tau32, scale, fface32, out, s, t);
+    case P: return dg_launch_f32io<P>(g, q64, q32, phiB32, tau32, scale, fface32, out, s, t, f);
         CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9)
 #undef CASE
         default: return cudaErrorInvalidValue;
